@@ -1,0 +1,435 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each check uses a closed form, an
+exact invariant, a library special case or a brute-force computation written a
+different way.  A plausible slip in the oracle (a dropped neighbour, a wrong sign,
+a wrong step size, a transposed index, a missing wall image) fails at least one.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.sparse
+import scipy.sparse.linalg
+
+import workloads as W
+
+
+# ----------------------------------------------------------------------------- diffusion
+def _dct_closed_form(u0, dims, dx, T, nsteps, scheme):
+    """Exact discrete solution: the zero-flux 7-point Laplacian is diagonalised by
+    the separable orthonormal DCT-II, eigenvalue -(4/dx^2) sin^2(pi j / (2N)) per axis."""
+    nx, ny, nz = dims
+    u = u0.reshape(nz, ny, nx)
+    uh = scipy.fft.dctn(u, type=2, norm="ortho")
+    lam = np.zeros((nz, ny, nx))
+    for axis, n in zip((2, 1, 0), (nx, ny, nz)):
+        j = np.arange(n)
+        l1 = -(4.0 / dx ** 2) * np.sin(np.pi * j / (2.0 * n)) ** 2
+        shape = [1, 1, 1]
+        shape[axis] = n
+        lam = lam + l1.reshape(shape)
+    dt = T / nsteps
+    if scheme == 0:
+        g = 1.0 / (1.0 - dt * lam)
+    elif scheme == 1:
+        g = (1.0 + 0.5 * dt * lam) / (1.0 - 0.5 * dt * lam)
+    else:
+        g = 1.0 + dt * lam
+    return scipy.fft.idctn(uh * g ** nsteps, type=2, norm="ortho").ravel()
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("dims", [(13, 7, 5), (8, 8, 8), (1, 9, 6)])
+def test_structured_diffusion_matches_dct_closed_form(orc, scheme, dims):
+    rng = np.random.default_rng(11)
+    dx = 0.37
+    u0 = rng.random(np.prod(dims)) - 0.3
+    # explicit Euler is only stable for dtau <= dx^2/6: choose T accordingly
+    T = 0.9 * dx ** 2 if scheme == 2 else 2.3 * dx ** 2
+    nsteps = 7
+    got, _ = orc.diffuse_structured(u0, dims, dx, T, nsteps, scheme=scheme, tol=1e-15)
+    ref = _dct_closed_form(u0, dims, dx, T, nsteps, scheme)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_point_source_variance_is_exactly_2T(orc, scheme, axis):
+    """Eq. (solutionGi): the diffused point source has variance 2T per axis.  On the
+    discrete grid this holds exactly: every step keeps the mass and the mean and adds
+    2*dtau*mass to the second moment along each axis.  The 7-point operator is
+    separable, so the marginal along the long axis obeys the 1-D law whatever the
+    (short, walled) cross-section; the long axis keeps the wall leakage of the
+    implicit schemes' exponential tails below 1e-20."""
+    long_n = 121
+    dims = [9, 7, 5]
+    dims[axis] = long_n
+    dx = 0.5
+    u0 = np.zeros((dims[2], dims[1], dims[0]))
+    src = [3, 2, 1]
+    src[axis] = long_n // 2
+    u0[src[2], src[1], src[0]] = 3.0
+    T = (3 * dx) ** 2 / 4.0
+    nsteps = 12 if scheme == 2 else 6
+    u, _ = orc.diffuse_structured(u0.ravel(), tuple(dims), dx, T, nsteps, scheme=scheme, tol=1e-15)
+    u = u.reshape(dims[2], dims[1], dims[0])
+    x = (np.arange(long_n) - long_n // 2) * dx
+    mass = u.sum()
+    assert abs(mass - 3.0) <= 1e-13 * 3.0
+    np_axis = 2 - axis
+    marg = u.sum(axis=tuple(a for a in range(3) if a != np_axis))
+    mean = (marg * x).sum() / mass
+    var = (marg * x ** 2).sum() / mass
+    assert abs(mean) <= 1e-12
+    assert abs(var - 2.0 * T) <= 1e-11 * 2.0 * T
+
+
+def test_conservation_nonnegativity_symmetry_linearity(orc):
+    dims = (12, 12, 12)
+    dx = 1.0 / 12
+    n = 12 ** 3
+    rng = np.random.default_rng(3)
+    u0 = np.zeros(n)
+    u0[rng.integers(0, n, 40)] += rng.random(40)
+    T = (3 * dx) ** 2 / 4
+    u, _ = orc.diffuse_structured(u0, dims, dx, T, 10)
+    # Eq. (conserve): zero-flux walls keep sum V_c eps
+    assert abs(u.sum() - u0.sum()) <= 1e-13 * u0.sum()
+    # implicit Euler of an M-matrix keeps eps >= 0
+    assert u.min() >= -1e-15 * u.max()
+    # mirror symmetry of a centred source on an even grid
+    v0 = np.zeros((12, 12, 12))
+    v0[5:7, 5:7, 5:7] = 1.0
+    v, _ = orc.diffuse_structured(v0.ravel(), dims, dx, T, 10)
+    v = v.reshape(12, 12, 12)
+    for ax in range(3):
+        assert np.max(np.abs(v - np.flip(v, axis=ax))) <= 1e-14
+    # per-component linearity (Section 3.2.1: each component is diffused alone)
+    w0 = rng.random(n)
+    both, _ = orc.diffuse_structured(np.stack([u0, w0, 2.5 * u0 - w0]), dims, dx, T, 10, tol=1e-15)
+    assert np.max(np.abs(both[2] - (2.5 * both[0] - both[1]))) <= 1e-12 * np.max(np.abs(both[2]))
+
+
+def test_equivalence_to_gaussian_kernel_with_images_converges_second_order(orc):
+    """Section 3.2 / Section 4.1: the diffused PCM field of sources at cell centres
+    approaches the image-summed Gaussian kernel of bandwidth b = sqrt(4T) at
+    O(dx^2/b^2) + O(dtau/T).  Paper-shaped slab: 135 x 135 x 1 (d_p = 1), one cell
+    layer of thickness d_p, b = 18; meshes of 15, 45 and 135 cells per side share
+    the coarse cell centres; dtau is refined with dx^2."""
+    L = 135.0
+    b = 18.0
+    T = b * b / 4.0
+    rng = np.random.default_rng(5)
+    coarse = rng.integers(0, 15, size=(20, 2))
+    coarse[0] = (0, 0)        # corner source: needs the 2-D corner images
+    coarse[1] = (7, 0)        # wall source
+    src = np.zeros((20, 3))
+    src[:, :2] = (coarse + 0.5) * 9.0
+    src[:, 2] = 0.5
+    wts = rng.random(20) + 0.5
+    ev = np.zeros((15 * 15, 3))
+    gx, gy = np.meshgrid((np.arange(15) + 0.5) * 9.0, (np.arange(15) + 0.5) * 9.0, indexing="xy")
+    ev[:, 0] = gx.ravel()
+    ev[:, 1] = gy.ravel()
+    ev[:, 2] = 0.5
+    exact = orc.kernel_sum(src, wts, ev, (L, L, 1.0), b, mmax=60)
+    errs = []
+    for r, nsteps in ((1, 4), (3, 36), (9, 324)):       # r fine cells per coarse cell
+        N = 15 * r
+        dx = L / N
+        u0 = np.zeros(N * N)
+        fine = coarse * r + r // 2                       # the coarse centre, on the fine grid
+        np.add.at(u0, fine[:, 1] * N + fine[:, 0], wts / (dx * dx * 1.0))
+        # the slab cells are dx x dx x 1 (dz != dx): diffuse with the generic CSR oracle
+        u, _ = _diffuse_slab(orc, u0, N, dx, T, nsteps)
+        u2 = u.reshape(N, N)[r // 2::r, r // 2::r].ravel()
+        errs.append(np.max(np.abs(u2 - exact)) / np.max(exact))
+    assert errs[2] < (9.0 / 9 / b) ** 2     # O((dx/b)^2) on the finest mesh
+    order1 = math.log(errs[0] / errs[1]) / math.log(3)
+    order2 = math.log(errs[1] / errs[2]) / math.log(3)
+    assert 1.6 < order2 < 2.4, errs
+    assert order1 > 1.3, errs
+
+
+def _slab_csr(N, dx):
+    """TPFA Laplacian of an N x N x 1 slab with cells dx x dx x 1: transmissibility of a
+    face = area / distance = (dx * 1) / dx = 1 across x and y faces."""
+    idx = np.arange(N * N).reshape(N, N)
+    rows, cols = [], []
+    for a, b_ in ((idx[:, :-1], idx[:, 1:]), (idx[:-1, :], idx[1:, :])):
+        rows += [a.ravel(), b_.ravel()]
+        cols += [b_.ravel(), a.ravel()]
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    off = scipy.sparse.csr_matrix((np.ones(len(r)), (r, c)), shape=(N * N, N * N))
+    Lm = off - scipy.sparse.diags(np.asarray(off.sum(axis=1)).ravel())
+    Lm = Lm.tocsr()
+    Lm.sort_indices()
+    return Lm
+
+
+def _diffuse_slab(orc, u0, N, dx, T, nsteps):
+    Lm = _slab_csr(N, dx)
+    vc = np.full(N * N, dx * dx * 1.0)
+    return orc.diffuse_csr(u0, vc, Lm.indptr.astype(np.int64), Lm.indices.astype(np.int32), Lm.data,
+                           T, nsteps, tol=1e-14)
+
+
+def test_structured_and_csr_oracles_agree_on_a_hex_grid(orc):
+    """The uniform 7-point operator is the two-point-flux FV operator with T_f = dx
+    (face dx^2 over distance dx) and V_c = dx^3; the two oracle paths must agree."""
+    n = 7
+    dx = 0.2
+    dims = (n, n, n)
+    idx = np.arange(n ** 3).reshape(n, n, n)
+    rows, cols = [], []
+    for a, b_ in ((idx[:, :, :-1], idx[:, :, 1:]), (idx[:, :-1, :], idx[:, 1:, :]),
+                  (idx[:-1, :, :], idx[1:, :, :])):
+        rows += [a.ravel(), b_.ravel()]
+        cols += [b_.ravel(), a.ravel()]
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    off = scipy.sparse.csr_matrix((np.full(len(r), dx), (r, c)), shape=(n ** 3, n ** 3))
+    Lm = (off - scipy.sparse.diags(np.asarray(off.sum(axis=1)).ravel())).tocsr()
+    Lm.sort_indices()
+    rng = np.random.default_rng(2)
+    u0 = rng.random(n ** 3)
+    T = 0.05
+    for scheme in (0, 1, 2):
+        Ts = T if scheme != 2 else 0.002
+        a, _ = orc.diffuse_structured(u0, dims, dx, Ts, 5, scheme=scheme, tol=1e-15)
+        b2, _ = orc.diffuse_csr(u0, np.full(n ** 3, dx ** 3), Lm.indptr.astype(np.int64),
+                                Lm.indices.astype(np.int32), Lm.data, Ts, 5, scheme=scheme,
+                                tol=1e-15)
+        assert np.max(np.abs(a - b2)) <= 1e-12 * np.max(np.abs(a))
+
+
+# ----------------------------------------------------------------------------- locate / deposit
+def test_locate_structured_edge_cases(orc):
+    dims = (4, 3, 2)
+    dx = 0.25
+    origin = (-0.5, 0.0, 1.0)
+    pts = np.array([
+        [-0.5, 0.0, 1.0],            # lower corner -> cell 0
+        [0.5, 0.75, 1.5],            # upper corner (on the walls) clamps into the last cell
+        [-0.25, 0.25, 1.25],         # exactly on interior faces -> the upper cell
+        [-0.5 - 1e-12, 0.1, 1.1],    # just outside
+        [0.5 + 1e-12, 0.1, 1.1],     # just outside
+        [np.nan, 0.1, 1.1],          # NaN is out of domain
+        [0.1, 0.2, 1.4],
+    ]).T
+    cell, nout = orc.locate_structured(dims, origin, dx, pts)
+    assert nout == 3
+    assert list(cell) == [0, 23, (1 * 3 + 1) * 4 + 1, -1, -1, -1, (1 * 3 + 0) * 4 + 2]
+
+
+def test_locate_structured_matches_exact_rational_floor(orc):
+    """With dx a power of two every step of the cell computation is exact, so the
+    oracle must match the exact floor((x - x0)/dx) computed in rationals."""
+    rng = np.random.default_rng(4)
+    dims = (32, 16, 8)
+    dx = 1.0 / 32
+    pos = rng.random((3, 3000)) * np.array([1.0, 0.5, 0.25])[:, None]
+    pos[:, :50] = np.round(pos[:, :50] * 32) / 32          # points on faces
+    cell, nout = orc.locate_structured(dims, (0, 0, 0), dx, pos)
+    assert nout == 0
+    for i in range(pos.shape[1]):
+        ijk = []
+        for a in range(3):
+            k = math.floor(Fraction(pos[a, i]) / Fraction(dx))
+            ijk.append(min(k, dims[a] - 1))
+        assert cell[i] == (ijk[2] * dims[1] + ijk[1]) * dims[0] + ijk[0]
+
+
+def test_deposit_mode0_matches_python_sequential_sum(orc):
+    rng = np.random.default_rng(7)
+    n, ncells = 500, 27
+    cell = rng.integers(-1, ncells, n).astype(np.int32)
+    w = rng.standard_normal((2, n)) * 10.0 ** rng.integers(-3, 3, (2, n))
+    vc = rng.random(ncells) + 0.1
+    got, _ = orc.deposit(cell, w, ncells, vc=vc, mode=0)
+    for f in range(2):
+        s = [0.0] * ncells
+        for i in range(n):              # plain Python floats: IEEE doubles, in order
+            if cell[i] >= 0:
+                s[cell[i]] = s[cell[i]] + float(w[f, i])
+        ref = np.array([s[k] / vc[k] for k in range(ncells)])
+        assert np.array_equal(got[f].view(np.int64), ref.view(np.int64))
+
+
+def test_deposit_mode1_is_exact_fixed_point(orc):
+    rng = np.random.default_rng(8)
+    n, ncells = 700, 13
+    cell = rng.integers(0, ncells, n).astype(np.int32)
+    w = rng.standard_normal((3, n)) * np.array([1e-7, 1.0, 3e5])[:, None]
+    vcu = 0.125
+    got, fbits = orc.deposit(cell, w, ncells, vc_uniform=vcu, mode=1)
+    for f in range(3):
+        F = fbits[f]
+        m = Fraction(float(np.max(np.abs(w[f]))))
+        # n * max|w| * 2^F < 2^61 and F is within 2 of the largest such exponent
+        assert n * m * Fraction(2) ** F < 2 ** 61
+        assert n * m * Fraction(2) ** (F + 2) >= 2 ** 61
+        acc = [0] * ncells
+        for i in range(n):
+            acc[cell[i]] += round(float(w[f, i]) * 2.0 ** F)   # Python round: half to even
+        ref = np.array([(float(a) * 2.0 ** (-F)) / vcu for a in acc])
+        assert np.array_equal(got[f].view(np.int64), ref.view(np.int64))
+        # conservation is exact in the integer domain
+        assert sum(acc) == sum(round(float(x) * 2.0 ** F) for x in w[f])
+
+
+def test_fixed_point_bits_limits(orc):
+    assert orc.fixed_point_bits(0, 1.0) == 0
+    assert orc.fixed_point_bits(10, 0.0) == 0
+    assert orc.fixed_point_bits(1, 5e-324) == 1000
+    for n, m in ((1, 1e308), (3, 7.0), (2_000_000, 3.35e-8), (5, 1e-300)):
+        F = orc.fixed_point_bits(n, m)
+        assert n * Fraction(m) * Fraction(2) ** F < 2 ** 61
+        if -1000 < F < 1000:               # not clamped: within 2 of the largest exponent
+            assert 2 ** 61 <= n * Fraction(m) * Fraction(2) ** (F + 2)
+        else:
+            assert F == 1000 and m == 1e-300
+
+
+def test_deposit_conservation_cfg_small(orc):
+    c = W.uniform_cube()
+    cell, nout = orc.locate_structured(c.dims, c.origin, c.dx, c.pos)
+    eps, _ = orc.deposit(cell, c.w, c.ncells, vc_uniform=(c.dx * c.dx) * c.dx)
+    assert nout == 0
+    assert abs(eps.sum() * c.dx ** 3 - c.w.sum()) <= 1e-12 * c.w.sum()
+
+
+def test_paper_slab_smoothing_caps_pcm_extremes(orc):
+    """Section 4.4: on a mesh finer than the particles (dx = d_p/2) PCM gives cells with
+    eps far above 1; the diffused field (b = 6 d_p) stays smooth and below the PCM
+    maximum, and on meshes dx = 1 and 0.5 the fields agree (mesh convergence)."""
+    rng = np.random.default_rng(0)
+    L = 135.0
+    pos = np.zeros((3, 1000))
+    pos[:2] = 30.0 + 75.0 * rng.random((2, 1000))
+    pos[2] = 0.5
+    vp = math.pi / 6.0
+    fields = {}
+    for N in (135, 270):
+        dx = L / N
+        cell, nout = orc.locate_structured((N, N, 1), (0, 0, 0), dx, np.vstack([pos[:2], pos[2:] * 0 + 0.5 * dx]))
+        assert nout == 0
+        u0, _ = orc.deposit(cell, np.full((1, 1000), vp), N * N, vc_uniform=dx * dx * dx)
+        # thickness of the layer is dx here: keep the slab a single layer of cells
+        u, _ = orc.diffuse_structured(u0, (N, N, 1), dx, 9.0, 3)
+        fields[N] = (u0[0].reshape(N, N), u.reshape(N, N))
+    pcm_max = fields[270][0].max()
+    assert pcm_max > 1.0
+    assert fields[270][1].max() < 0.5 * pcm_max
+    # one cell layer: compare areal densities eps * thickness on the common 135 grid
+    fine = fields[270][1].reshape(135, 2, 135, 2).mean(axis=(1, 3)) * 0.5
+    c135 = fields[135][1] * 1.0
+    assert np.max(np.abs(fine - c135)) <= 0.1 * np.max(c135)
+
+
+# ----------------------------------------------------------------------------- tetrahedra
+def _heron_face(a, b, c):
+    la, lb, lc = np.linalg.norm(b - c), np.linalg.norm(a - c), np.linalg.norm(a - b)
+    s = 0.5 * (la + lb + lc)
+    return math.sqrt(max(s * (s - la) * (s - lb) * (s - lc), 0.0))
+
+
+def test_tet_mesh_geometry_and_operator(orc):
+    xyz, tets = W.kuhn_tet_mesh(5, jitter=0.2, seed=1)
+    vc, cent, rowptr, col, val = orc.tet_build(xyz, tets)
+    nt = tets.shape[0]
+    assert abs(vc.sum() - 1.0) <= 1e-13                      # tets tile the unit cube
+    A = scipy.sparse.csr_matrix((val, col, rowptr), shape=(nt, nt))
+    assert abs(A - A.T).max() == 0.0                          # symmetric by construction
+    assert np.max(np.abs(A @ np.ones(nt))) <= 1e-13 * np.max(np.abs(val))   # L 1 = 0
+    off = A - scipy.sparse.diags(A.diagonal())
+    assert off.data.min() > 0.0                               # every T_f > 0 (M-matrix)
+    # interior tets have 4 face neighbours, all have at least 1
+    deg = np.diff(rowptr) - 1
+    assert deg.max() == 4 and deg.min() >= 1
+    # independent geometry for a few faces: area by Heron, normal by SVD of the plane
+    rng = np.random.default_rng(0)
+    for k in rng.integers(0, nt, 25):
+        for e in range(rowptr[k], rowptr[k + 1]):
+            l = col[e]
+            if l == k:
+                continue
+            shared = sorted(set(tets[k]) & set(tets[l]))
+            assert len(shared) == 3
+            p = xyz[shared]
+            area = _heron_face(*p)
+            centred = p - p.mean(axis=0)
+            nrm = np.linalg.svd(centred)[2][-1]
+            d = cent[l] - cent[k]
+            T = area / abs(np.dot(nrm, d))
+            assert abs(A[k, l] - T) <= 1e-11 * T
+    # undeformed Kuhn tets: each is one sixth of its hex
+    xyz0, tets0 = W.kuhn_tet_mesh(3, jitter=0.0)
+    vc0, *_ = orc.tet_build(xyz0, tets0)
+    assert np.max(np.abs(vc0 - (1.0 / 27) / 6)) <= 1e-16
+
+
+def test_tet_diffusion_matches_sparse_direct_solve(orc):
+    xyz, tets = W.kuhn_tet_mesh(4, jitter=0.2, seed=2)
+    vc, cent, rowptr, col, val = orc.tet_build(xyz, tets)
+    nt = len(vc)
+    Lm = scipy.sparse.csr_matrix((val, col, rowptr), shape=(nt, nt))
+    rng = np.random.default_rng(1)
+    u0 = rng.random(nt)
+    T, nsteps = 0.004, 4
+    dt = T / nsteps
+    for scheme in (0, 1):
+        got, _ = orc.diffuse_csr(u0, vc, rowptr, col, val, T, nsteps, scheme=scheme, tol=1e-15)
+        M = scipy.sparse.diags(vc)
+        th = 1.0 if scheme == 0 else 0.5
+        A = (M - th * dt * Lm).tocsc()
+        u = u0.copy()
+        for _ in range(nsteps):
+            rhs = vc * u + ((1 - th) * dt * (Lm @ u) if scheme == 1 else 0.0)
+            u = scipy.sparse.linalg.spsolve(A, rhs)
+        assert np.max(np.abs(got - u)) <= 1e-12 * np.max(np.abs(u))
+        assert abs((vc * got).sum() - (vc * u0).sum()) <= 1e-13 * (vc * u0).sum()
+
+
+def test_tet_locate_matches_independent_barycentric(orc):
+    xyz, tets = W.kuhn_tet_mesh(4, jitter=0.2, seed=3)
+    rng = np.random.default_rng(9)
+    pos = rng.random((3, 300))
+    cell, nout = orc.locate_tet(xyz, tets, pos)
+    assert nout == 0
+    for i in range(pos.shape[1]):
+        # barycentric coordinates by a linear solve (not by orientation determinants)
+        best, bestm = -1, -np.inf
+        for t in range(tets.shape[0]):
+            v = xyz[tets[t]]
+            Mt = np.vstack([(v[1:] - v[0]).T])
+            lam = np.linalg.solve(Mt, pos[:, i] - v[0])
+            m = min(1.0 - lam.sum(), lam.min())
+            if m > bestm:
+                best, bestm = t, m
+        if bestm > 1e-9:                      # unambiguous interior point
+            assert cell[i] == best
+    # outside the cube: out of domain
+    _, nout = orc.locate_tet(xyz, tets, np.array([[1.5], [0.5], [0.5]]))
+    assert nout == 1
+
+
+def test_image_kernel_is_normalised_over_the_box(orc):
+    """Eq. (normal) with Eq. (hi-bound): the image-summed kernel of a particle near a
+    corner integrates to its volume over the box (midpoint quadrature, 60^3 points)."""
+    L = (1.0, 0.8, 0.6)
+    b = 0.15
+    n = 60
+    pts = []
+    for a in range(3):
+        pts.append((np.arange(n) + 0.5) * L[a] / n)
+    X, Y, Z = np.meshgrid(*pts, indexing="ij")
+    ev = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    src = np.array([[0.03, 0.75, 0.31]])
+    vals = orc.kernel_sum(src, np.array([2.0]), ev, L, b, mmax=2)
+    integral = vals.sum() * (L[0] * L[1] * L[2]) / n ** 3
+    assert abs(integral - 2.0) <= 1e-6
