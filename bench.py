@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 diffusion-based coarse-graining path.
+
+One step = the whole method (locate + ordered deposition + implicit-Euler diffusion
+to T = b^2/4, 10 pseudo-steps) on the 128^3 clustered unit-cube workload
+(2,000,000 spheres of d = 0.004 in 20 Gaussian clusters), once for each bandwidth
+b/dx in {1, 2, 4, 8}, in the mixed path (FP32 Chebyshev inner solves with FP64
+iterative refinement to ||r|| <= 1e-13 ||b|| per pseudo-step).
+
+Metric: diffusion cell-updates/s (one cell-update = one application of the implicit
+operator at one cell for one field), whole job over all ranks.  The same line carries
+the FP64 GPU path, end-to-end throughput through the host-pointer C entry point, a
+roofline entry for the dominant kernel, the oracle CPU baseline and the SM clocks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+B_OVER_DX = (1.0, 2.0, 4.0, 8.0)
+NSTEPS = 10
+TOL = 1e-13
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-side", type=int, default=128)
+    ap.add_argument("--n-particles", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return ("clustered_cube_%d: %d^3 unit cube, %d spheres d=0.004 in 20 Gaussian clusters "
+            "(sigma 0.05, <=8 per cell), b/dx in {1,2,4,8}, %d implicit-Euler pseudo-steps, "
+            "tol 1e-13" % (a.n_side, a.n_side, a.n_particles, NSTEPS))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(a):
+    """The oracle (plain FP64 C, single thread) as the reference arm: each step is a
+    bounded sample of the workload -- the full deposition of every particle and the
+    first 2 of the 10 implicit-Euler pseudo-steps at b/dx = 2 (same dtau)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    oracle.build()
+    c = W.clustered_cube(n_side=a.n_side, n_particles=a.n_particles)
+    b = 2.0 * c.dx
+    T_full = b * b / 4.0
+    k_sample = 2
+
+    def step():
+        cell, _ = oracle.locate_structured(c.dims, c.origin, c.dx, c.pos)
+        eps0, _ = oracle.deposit(cell, c.w, c.ncells, vc_uniform=(c.dx * c.dx) * c.dx)
+        _, iters = oracle.diffuse_structured(eps0, c.dims, c.dx, T_full * k_sample / NSTEPS,
+                                             k_sample, tol=TOL)
+        return iters
+
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    total_updates = 0
+    for _ in range(a.steps):
+        iters = step()
+        total_updates += (iters + k_sample) * c.ncells   # CG iterations + one residual per step
+    dt = time.perf_counter() - t0
+    v = total_updates / dt
+    line = {"impl": "reference", "metric": "diffusion cell-updates/s", "value": v,
+            "unit": "cell-updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": dt * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: locate+deposit all %d particles, 2 of 10 "
+                                       "implicit-Euler steps at b/dx=2, FP64 CG to 1e-13"
+                                       % a.n_particles},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_1409_0001_gb300 as cg
+    import workloads as W
+    from paper_1409_0001_gb300 import build as libbuild
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    libbuild.build()
+    lib = cg.load_library()
+
+    c = W.clustered_cube(n_side=a.n_side, n_particles=a.n_particles, seed=rank)
+    mesh = cg.StructuredMesh(c.dims, c.origin, c.dx)
+    pos = torch.from_numpy(c.pos).cuda()
+    w = torch.from_numpy(c.w).cuda()
+    outs = [torch.empty((1, c.ncells), dtype=torch.float64, device="cuda") for _ in B_OVER_DX]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def params(bdx, precision):
+        return cg.Params(bandwidth=bdx * c.dx, nsteps=NSTEPS, precision=precision, tol=TOL)
+
+    def one_step(precision, reps):
+        for i, bdx in enumerate(B_OVER_DX):
+            _, r = cg.coarse_grain(mesh, pos, w, params(bdx, precision), out=outs[i], report=True)
+            reps.append(r)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        """Per-step CUDA-event time (L2 flushed before every step, outside the events)."""
+        stream = torch.cuda.current_stream()
+        tot = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---------------- warm-up
+    for _ in range(a.warmup):
+        one_step(cg.PREC_FP32_REFINE, [])
+    barrier()
+
+    # ---------------- timed region (clean: no per-kernel events)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    lib.cg_launch_count_reset()
+    reps = []
+    barrier()
+    ms = timed(lambda: one_step(cg.PREC_FP32_REFINE, reps), a.steps)
+    barrier()
+    launches = int(lib.cg_launch_count())
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms)
+    updates = sum_over_ranks(float(sum(r["cell_updates"] for r in reps)))
+    value = updates / (ms * 1e-3)
+    rounds = sum(r["refine_rounds"] for r in reps) / max(len(reps), 1)
+    worst_res = max(r["final_rel_residual"] for r in reps)
+    mass_err = max(abs(r["mass_out"][0] - r["mass_in"][0]) / r["mass_in"][0] for r in reps)
+    ms_phase = {k: sum(r[k] for r in reps) / a.steps for k in ("ms_locate", "ms_deposit",
+                                                               "ms_diffuse")}
+
+    # ---------------- per-kernel device time: the same steps again with event pairs
+    cg.profile_reset()
+    cg.profile_enable(True)
+    prof_reps = []
+    ms_prof = timed(lambda: one_step(cg.PREC_FP32_REFINE, prof_reps), a.steps)
+    cg.profile_enable(False)
+    kern = cg.profile_read()
+
+    # ---------------- FP64 GPU path, same workload
+    fp64_reps = []
+    ms64 = timed(lambda: one_step(cg.PREC_FP64, fp64_reps), max(a.fp64_steps, 1))
+    ms64 = max_over_ranks(ms64) / max(a.fp64_steps, 1)
+    one_step(cg.PREC_FP32_REFINE, [])
+    mixed_out = [o.clone() for o in outs]
+    one_step(cg.PREC_FP64, [])
+    fp64_out = [o.clone() for o in outs]
+    mixed_vs_fp64 = max(float((m - f).abs().max() / f.abs().max())
+                        for m, f in zip(mixed_out, fp64_out))
+
+    # ---------------- end to end through the host-pointer entry point
+    pos_h = torch.from_numpy(c.pos).pin_memory()
+    w_h = torch.from_numpy(c.w).pin_memory()
+    out_h = [torch.empty((1, c.ncells), dtype=torch.float64).pin_memory() for _ in B_OVER_DX]
+
+    def e2e_step(reps_e):
+        for i, bdx in enumerate(B_OVER_DX):
+            _, r = cg.coarse_grain_host(mesh, pos_h, w_h, params(bdx, cg.PREC_FP32_REFINE),
+                                        out=out_h[i], report=True)
+            reps_e.append(r)
+
+    e2e_step([])
+    reps_e = []
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        e2e_step(reps_e)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_updates = sum_over_ranks(float(sum(r["cell_updates"] for r in reps_e)))
+    h2d = len(B_OVER_DX) * (pos_h.numel() + w_h.numel()) * 8
+    d2h = len(B_OVER_DX) * c.ncells * 8
+
+    # ---------------- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    top = max(kern.items(), key=lambda kv: kv[1]["ms"]) if kern else (None, None)
+    roof = None
+    if top[0] is not None:
+        name, k = top
+        achieved = k["bytes"] / (k["ms"] * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
+                "avg_launch_us": k["ms"] * 1e3 / k["launches"],
+                "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kern.values())}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not a.no_cpu_baseline and ws == 1:
+            cpu = cpu_baseline(c, outs, fp64_out)
+        ncells = c.ncells
+        cps = ws * a.steps * len(B_OVER_DX) * NSTEPS * ncells / (ms * 1e-3)
+        line = {
+            "metric": "diffusion cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "precision": "fp32 Chebyshev + fp64 refinement",
+                       "l2": "flushed before every step (256 MB write, outside the timed events)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "e2e": {"value": e2e_updates / e2e_s, "unit": "cell-updates/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "entry_point": "cg_coarse_grain_host (pinned host buffers)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "cell_pseudo_steps_per_s": cps,
+            "particles_per_s": ws * a.steps * len(B_OVER_DX) * c.n / (ms * 1e-3),
+            "ms_per_phase_per_step": ms_phase,
+            "refine_rounds_per_solve": rounds,
+            "worst_rel_residual": worst_res,
+            "worst_rel_mass_error": mass_err,
+            "fp64_gpu": {"ms_per_step": ms64,
+                         "cell_pseudo_steps_per_s": len(B_OVER_DX) * NSTEPS * ncells / (ms64 * 1e-3),
+                         "mixed_speedup": ms64 / (ms / a.steps),
+                         "mixed_vs_fp64_maxrel": mixed_vs_fp64},
+            "profiled_ms_per_step": ms_prof / a.steps,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                            "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                        for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])},
+        }
+        print(json.dumps(line))
+    mesh.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(c, outs, fp64_out):
+    """The oracle as it stands, single-threaded on this host: locate + deposit of all
+    particles and the full 10-step implicit-Euler diffusion at b/dx = 2.  Also gives
+    the max-relative error of the GPU results for that bandwidth."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    cell, _ = oracle.locate_structured(c.dims, c.origin, c.dx, c.pos)
+    eps0, _ = oracle.deposit(cell, c.w, c.ncells, vc_uniform=(c.dx * c.dx) * c.dx)
+    b = 2.0 * c.dx
+    ref, iters = oracle.diffuse_structured(eps0, c.dims, c.dx, b * b / 4, NSTEPS, tol=TOL)
+    dt = time.perf_counter() - t0
+    updates = (iters + NSTEPS) * c.ncells
+    i = B_OVER_DX.index(2.0)
+    mixed = outs[i].cpu().numpy()[0]
+    f64 = fp64_out[i].cpu().numpy()[0]
+    scale = np.max(np.abs(ref))
+    return {"value": updates / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "locate+deposit all %d particles and 10 implicit-Euler steps at b/dx=2 "
+                      "(FP64 CG to 1e-13), %.1f s" % (c.n, dt),
+            "mixed_maxrel_vs_oracle": float(np.max(np.abs(mixed - ref)) / scale),
+            "fp64_maxrel_vs_oracle": float(np.max(np.abs(f64 - ref)) / scale)}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * cg.h -- C ABI of the GB300 (sm_103a) library for diffusion-based coarse graining
+ * (Sun & Xiao, "Diffusion-Based Coarse Graining in Hybrid Continuum-Discrete
+ * Solvers").
+ *
+ * The method (Section 2.6): (1) deposit every particle's quantity into the mesh cell
+ * holding its centroid and divide by the cell volume (particle centroid method,
+ * Section 2.2, Section 3.1 Eq. (pcm-k)); (2) smooth the deposited field by
+ * integrating the diffusion equation d(eps)/d(tau) = Laplacian(eps) (Section 3.2.1
+ * Eq. (diffusion)) over pseudo-time T = b^2/4 (b the equivalent Gaussian kernel
+ * bandwidth, Section 3.2.1) with zero-flux walls (Section 3.2.2).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are CALLER-OWNED DEVICE memory unless the name ends in _host.
+ *    Mesh-construction inputs are host memory and are copied.
+ *  - The library owns the mesh and its workspace (allocated on first use, grown as
+ *    needed, freed by cg_destroy_mesh).  Calls that use the same mesh must not run
+ *    concurrently.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it, and every call synchronises that stream before it returns
+ *    (the status depends on device results), so outputs are complete on return.
+ *  - Every function returns a cg_status and never aborts.  Validation runs before
+ *    any output is written: on an error status the output arrays are untouched,
+ *    except CG_ENOCONV / CG_ETIMEOUT, which leave the last iterate in place.
+ *  - FP64 particle positions are SoA: pos[0..n) = x, pos[n..2n) = y, pos[2n..3n) = z.
+ *    Carried quantities are field-major: w[f*n + i].  Cell fields are field-major:
+ *    cells[f*ncells + k].  Weights are extensive (V_p, V_p*u, F_d); cell fields are
+ *    intensive (per unit cell volume), as in Eq. (pcm-k).
+ *  - Structured cells are numbered k = (iz*ny + iy)*nx + ix.
+ */
+#ifndef CG_H
+#define CG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CG_OK = 0,
+    CG_EINVAL = 1,    /* bad argument, size, pointer, non-finite input, invalid mesh */
+    CG_ENOMEM = 2,    /* device or host allocation failed */
+    CG_ECUDA = 3,     /* a CUDA runtime call failed (see cg_last_error) */
+    CG_ENOCONV = 4,   /* an implicit step did not reach params.tol within the limits */
+    CG_ETIMEOUT = 5,  /* a bounded device-side wait gave up (persistent kernels) */
+    CG_EDOMAIN = 6    /* particles outside the mesh; report->n_out_of_domain has the count */
+} cg_status;
+
+/* Human-readable name of a status code (static string). */
+const char *cg_status_string(cg_status s);
+
+/* Detail of the last error raised in the calling thread (static per-thread buffer). */
+const char *cg_last_error(void);
+
+/* ------------------------------------------------------------------------ meshes */
+
+typedef struct cg_mesh cg_mesh; /* opaque, library-owned */
+
+/* Uniform Cartesian hex mesh of nx*ny*nz cubic cells of edge dx with lower corner
+ * origin[3] (host).  The paper's structured tests use such meshes (Section 4,
+ * Table (apriori-indep)).  Requires nx, ny, nz >= 1, nx*ny*nz < 2^31, dx > 0 finite.
+ * Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
+cg_status cg_create_mesh_structured(int nx, int ny, int nz, const double origin[3], double dx,
+                                    cg_mesh **out);
+
+/* Unstructured tetrahedral mesh (Section 4.3 uses unstructured cells; the build
+ * uses tets).  xyz_host is [nverts][3] FP64, tv_host is [ntets][4] int32 vertex ids
+ * (either orientation).  The library derives cell volumes V_c, centroids (vertex
+ * means), faces, and the two-point-flux finite-volume Laplacian
+ * T_f = |S_f|^2 / (S_f . d_f) between face neighbours (S_f the face area vector out
+ * of the first cell, d_f the centroid-to-centroid vector), M = diag(V_c); boundary
+ * faces carry no flux.  Also builds the point-location buckets.
+ * Errors: CG_EINVAL (vertex id out of range, a face shared by more than two tets, a
+ * zero-volume tet, a non-positive transmissibility), CG_ENOMEM, CG_ECUDA. */
+cg_status cg_create_mesh_tet(int64_t nverts, const double *xyz_host, int64_t ntets,
+                             const int32_t *tv_host, cg_mesh **out);
+
+cg_status cg_destroy_mesh(cg_mesh *mesh);
+
+/* Number of cells (structured: nx*ny*nz; tet: ntets); -1 for NULL. */
+int64_t cg_mesh_num_cells(const cg_mesh *mesh);
+
+/* Copies the cell volumes V_c into out_host[ncells] (FP64). */
+cg_status cg_mesh_cell_volumes(const cg_mesh *mesh, double *out_host);
+
+/* Copies the tet mesh's Laplacian in CSR form to host arrays: rowptr_host[ncells+1],
+ * col_host[nnz], val_host[nnz]; *nnz_out receives nnz.  Pass NULL arrays to query
+ * nnz only.  CG_EINVAL for a structured mesh. */
+cg_status cg_mesh_tet_operator(const cg_mesh *mesh, int64_t *rowptr_host, int32_t *col_host,
+                               double *val_host, int64_t *nnz_out);
+
+/* ------------------------------------------------------------------------ parameters */
+
+enum { CG_SCHEME_IMPLICIT_EULER = 0, CG_SCHEME_CRANK_NICOLSON = 1, CG_SCHEME_EXPLICIT_EULER = 2 };
+enum { CG_PREC_FP64 = 0, CG_PREC_FP32_REFINE = 1, CG_PREC_BF16_REFINE = 2 };
+enum { CG_DEPOSIT_ORDERED = 0, CG_DEPOSIT_FIXED_POINT = 1 };
+
+typedef struct {
+    double bandwidth;   /* b; T = b^2/4 (Section 3.2.1).  If <= 0, T below is used. */
+    double T;           /* pseudo-time span (used when bandwidth <= 0) */
+    int nsteps;         /* number of equal pseudo-steps, dtau = T/nsteps (Section 5.1) */
+    int scheme;         /* CG_SCHEME_*: implicit Euler (default), Crank-Nicolson (the
+                           paper's choice, Section 5.1), explicit Euler */
+    int precision;      /* CG_PREC_*: FP64 conjugate gradients; FP32 (or BF16-stored)
+                           inner solves with FP64 iterative refinement */
+    int deposit_mode;   /* CG_DEPOSIT_ORDERED: FP64 sum per cell in ascending particle
+                           index; CG_DEPOSIT_FIXED_POINT: exact 64-bit integer sum of
+                           w * 2^F (F per field, see cg_report.fixed_point_bits) */
+    double tol;         /* per implicit step: stop when ||b - A x||_2 <= tol ||b||_2
+                           (FP64 residual); default 1e-13 */
+    int max_iter;       /* FP64 CG: iteration cap per step; mixed: inner iteration cap */
+    int max_rounds;     /* mixed: refinement-round cap per step (default 12) */
+    int fused_k;        /* mixed, structured: inner iterations fused per sweep (0 = auto) */
+    int reserved0;
+    long long debug_barrier_budget; /* persistent batched kernel: spin budget per grid
+                                       barrier in clock cycles; <= 0 = default */
+} cg_params;
+
+/* Fills the defaults: bandwidth 0, T 0, nsteps 10, implicit Euler, FP64, ordered
+ * deposition, tol 1e-13, max_iter 10000, max_rounds 12, fused_k 0. */
+void cg_params_default(cg_params *p);
+
+#define CG_REPORT_MAX_FIELDS 8
+
+typedef struct {
+    double ms_locate, ms_deposit, ms_diffuse;   /* device time per phase (CUDA events) */
+    long long iters;          /* total operator applications per field, summed over fields */
+    long long refine_rounds;  /* mixed precision: refinement rounds, summed over steps */
+    long long cell_updates;   /* operator applications x cells, all fields (the metric unit) */
+    double final_rel_residual;/* max over steps and fields of ||b - A x||_2 / ||b||_2 */
+    double mass_in[CG_REPORT_MAX_FIELDS];   /* sum_k V_c,k eps_k before smoothing */
+    double mass_out[CG_REPORT_MAX_FIELDS];  /* ... after smoothing (Eq. (conserve)) */
+    long long n_out_of_domain;
+    int fixed_point_bits[CG_REPORT_MAX_FIELDS];
+    int inner_iters_per_round;/* mixed: Chebyshev iterations per refinement round */
+    int reserved;
+} cg_report;
+
+/* ------------------------------------------------------------------------ the path */
+
+/* Step 1a (Section 2.2, Section 3.1): host cell of each particle centroid.
+ * pos: device [3][n] FP64.  cell_out: device [n] int32, -1 for a particle outside
+ * the mesh.  Structured: per axis i = floor((x - x0) * (1/dx)) clamped into
+ * [0, n-1]; a particle is outside unless x0 <= x <= x0 + n*dx on every axis (a NaN
+ * is outside).  Tet: the lowest-index tet whose bounding box holds x and whose four
+ * barycentric coordinates (signed-volume ratios) are all >= 0; if none, the tet
+ * with the largest minimum barycentric coordinate (lowest index on ties) when that
+ * value is >= -1e-10; else outside.  *n_out_host receives the outside count.
+ * Errors: CG_EINVAL, CG_ECUDA. */
+cg_status cg_locate(cg_mesh *mesh, int64_t n, const double *pos, int32_t *cell_out,
+                    int64_t *n_out_host, void *stream);
+
+/* Step 1 (Section 3.1 Eq. (pcm-k)): eps_k,f = (sum over particles i in cell k of
+ * w_f,i) / V_c,k for nfields fields.  pos: device [3][n]; w: device [nfields][n];
+ * cells_out: device [nfields][ncells] FP64.  params->deposit_mode selects the
+ * ordered FP64 sum (bit-identical to a sequential loop over particles) or the
+ * 64-bit fixed-point sum.  report may be NULL.
+ * Errors: CG_EINVAL (sizes, NULL pointers, non-finite weights), CG_EDOMAIN
+ * (particles outside the mesh; nothing written), CG_ENOMEM, CG_ECUDA. */
+cg_status cg_deposit(cg_mesh *mesh, int64_t n, const double *pos, int nfields, const double *w,
+                     double *cells_out, const cg_params *params, cg_report *report, void *stream);
+
+/* Step 2 (Section 2.6 step 2, Section 3.2): smooth nfields cell fields in place by
+ * params->nsteps steps of the chosen scheme of Eq. (diffusion) to T, zero-flux walls.
+ * Implicit Euler solves (M - dtau L) u^{n+1} = M u^n per step, Crank-Nicolson
+ * (M - dtau/2 L) u^{n+1} = (M + dtau/2 L) u^n, explicit Euler u += dtau M^{-1} L u
+ * (requires dtau <= dx^2/6 on hex meshes).  cells: device [nfields][ncells] FP64.
+ * Errors: CG_EINVAL, CG_ENOCONV (report->final_rel_residual says how far it got),
+ * CG_ENOMEM, CG_ECUDA. */
+cg_status cg_diffuse(cg_mesh *mesh, int nfields, double *cells, const cg_params *params,
+                     cg_report *report, void *stream);
+
+/* cg_deposit followed by cg_diffuse (Section 2.6): the whole method. */
+cg_status cg_coarse_grain(cg_mesh *mesh, int64_t n, const double *pos, int nfields,
+                          const double *w, double *cells_out, const cg_params *params,
+                          cg_report *report, void *stream);
+
+/* cg_coarse_grain with HOST inputs and outputs: copies pos_host [3][n] and w_host
+ * [nfields][n] to library-owned device buffers, runs the method, and copies the
+ * result to cells_host [nfields][ncells].  Pinned host memory gives the fastest
+ * copies; pageable memory works. */
+cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host, int nfields,
+                               const double *w_host, double *cells_host, const cg_params *params,
+                               cg_report *report, void *stream);
+
+/* ------------------------------------------------------------------------ diagnostics */
+
+/* Per-kernel device timing (no counterpart in the paper; a measurement aid).  When
+ * enabled, every kernel launch of the library is bracketed by a CUDA event pair on its
+ * launching stream; after each call the elapsed times are accumulated per kernel name
+ * with the launch count and the launch's algorithmic bytes (the minimum DRAM traffic
+ * the kernel's definition implies: each input element read once, each output element
+ * written once).  Process-wide; adds a little host overhead per launch while enabled. */
+cg_status cg_profile_enable(int on);
+void cg_profile_reset(void);
+int cg_profile_count(void);
+/* Entry i: name (NUL-terminated, truncated to name_len), launches, total ms, total
+ * algorithmic bytes.  Any out pointer may be NULL.  CG_EINVAL for a bad index. */
+cg_status cg_profile_get(int i, char *name, int name_len, long long *launches, double *ms,
+                         double *bytes);
+
+/* Number of kernels the library has launched in this process since the last reset
+ * (counted whether or not profiling is enabled). */
+long long cg_launch_count(void);
+void cg_launch_count_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CG_H */

@@ -1,0 +1,336 @@
+"""Python binding of the GB300 diffusion-based coarse-graining library (include/cg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libcgdiff.so``.  PyTorch supplies device memory and the stream.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+
+    import paper_1409_0001_gb300 as cg
+    mesh = cg.StructuredMesh((128, 128, 128), (0, 0, 0), 1 / 128)
+    eps = cg.coarse_grain(mesh, pos, w, cg.Params(bandwidth=2 / 128, nsteps=10))
+
+Method (Section 2.6): particle centroid deposition, Eq. (pcm-k), then diffusion,
+Eq. (diffusion), to pseudo-time T = b^2/4 with zero-flux walls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB_PATH
+
+SCHEME_IMPLICIT_EULER, SCHEME_CRANK_NICOLSON, SCHEME_EXPLICIT_EULER = 0, 1, 2
+PREC_FP64, PREC_FP32_REFINE, PREC_BF16_REFINE = 0, 1, 2
+DEPOSIT_ORDERED, DEPOSIT_FIXED_POINT = 0, 1
+MAX_REPORT_FIELDS = 8
+
+STATUS = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_ENOCONV",
+          5: "CG_ETIMEOUT", 6: "CG_EDOMAIN"}
+
+
+class CgParams(ctypes.Structure):
+    _fields_ = [("bandwidth", ctypes.c_double), ("T", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("precision", ctypes.c_int),
+                ("deposit_mode", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("max_rounds", ctypes.c_int),
+                ("fused_k", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("debug_barrier_budget", ctypes.c_longlong)]
+
+
+class CgReport(ctypes.Structure):
+    _fields_ = [("ms_locate", ctypes.c_double), ("ms_deposit", ctypes.c_double),
+                ("ms_diffuse", ctypes.c_double), ("iters", ctypes.c_longlong),
+                ("refine_rounds", ctypes.c_longlong), ("cell_updates", ctypes.c_longlong),
+                ("final_rel_residual", ctypes.c_double),
+                ("mass_in", ctypes.c_double * MAX_REPORT_FIELDS),
+                ("mass_out", ctypes.c_double * MAX_REPORT_FIELDS),
+                ("n_out_of_domain", ctypes.c_longlong),
+                ("fixed_point_bits", ctypes.c_int * MAX_REPORT_FIELDS),
+                ("inner_iters_per_round", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+class CGError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        self.code = STATUS.get(status, "CG_UNKNOWN")
+        super().__init__("%s: %s (%s)" % (where, self.code, detail))
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libcgdiff.so (built in-tree by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libcgdiff.so not found at %s: run paper_1409_0001_gb300.build.build() "
+                           "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sigs = {
+        "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "cg_last_error": (ctypes.c_char_p, []),
+        "cg_params_default": (None, [P(CgParams)]),
+        "cg_create_mesh_structured": (i32, [i32, i32, i32, P(dbl), dbl, P(vp)]),
+        "cg_create_mesh_tet": (i32, [i64, vp, i64, vp, P(vp)]),
+        "cg_destroy_mesh": (i32, [vp]),
+        "cg_mesh_num_cells": (i64, [vp]),
+        "cg_mesh_cell_volumes": (i32, [vp, vp]),
+        "cg_mesh_tet_operator": (i32, [vp, vp, vp, vp, P(i64)]),
+        "cg_locate": (i32, [vp, i64, vp, vp, P(i64), vp]),
+        "cg_deposit": (i32, [vp, i64, vp, i32, vp, vp, P(CgParams), P(CgReport), vp]),
+        "cg_diffuse": (i32, [vp, i32, vp, P(CgParams), P(CgReport), vp]),
+        "cg_coarse_grain": (i32, [vp, i64, vp, i32, vp, vp, P(CgParams), P(CgReport), vp]),
+        "cg_coarse_grain_host": (i32, [vp, i64, vp, i32, vp, vp, P(CgParams), P(CgReport), vp]),
+        "cg_profile_enable": (i32, [i32]),
+        "cg_profile_reset": (None, []),
+        "cg_profile_count": (i32, []),
+        "cg_profile_get": (i32, [i32, ctypes.c_char_p, i32, P(ctypes.c_longlong), P(dbl), P(dbl)]),
+        "cg_launch_count": (ctypes.c_longlong, []),
+        "cg_launch_count_reset": (None, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the C header declares (used by the ABI test)."""
+    return ["cg_status_string", "cg_last_error", "cg_params_default", "cg_create_mesh_structured",
+            "cg_create_mesh_tet", "cg_destroy_mesh", "cg_mesh_num_cells", "cg_mesh_cell_volumes",
+            "cg_mesh_tet_operator", "cg_locate", "cg_deposit", "cg_diffuse", "cg_coarse_grain",
+            "cg_coarse_grain_host", "cg_profile_enable", "cg_profile_reset", "cg_profile_count",
+            "cg_profile_get", "cg_launch_count", "cg_launch_count_reset"]
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        detail = load_library().cg_last_error().decode(errors="replace")
+        raise CGError(status, where, detail)
+
+
+@dataclass
+class Params:
+    """Mirror of cg_params (see include/cg.h)."""
+    bandwidth: float = 0.0
+    T: float = 0.0
+    nsteps: int = 10
+    scheme: int = SCHEME_IMPLICIT_EULER
+    precision: int = PREC_FP64
+    deposit_mode: int = DEPOSIT_ORDERED
+    tol: float = 1e-13
+    max_iter: int = 10000
+    max_rounds: int = 12
+    fused_k: int = 0
+    debug_barrier_budget: int = 0
+
+    def to_c(self) -> CgParams:
+        p = CgParams()
+        load_library().cg_params_default(ctypes.byref(p))
+        for k in ("bandwidth", "T", "nsteps", "scheme", "precision", "deposit_mode", "tol",
+                  "max_iter", "max_rounds", "fused_k", "debug_barrier_budget"):
+            setattr(p, k, getattr(self, k))
+        return p
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("%s must be a CUDA float64 tensor" % name)
+    if not t.is_contiguous():
+        raise TypeError("%s must be contiguous" % name)
+    return t
+
+
+class _MeshBase:
+    _h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def ncells(self) -> int:
+        return int(load_library().cg_mesh_num_cells(self._h))
+
+    def cell_volumes(self):
+        import numpy as np
+        out = np.empty(self.ncells, dtype=np.float64)
+        _check(load_library().cg_mesh_cell_volumes(self._h, out.ctypes.data), "cg_mesh_cell_volumes")
+        return out
+
+    def close(self):
+        if self._h:
+            load_library().cg_destroy_mesh(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class StructuredMesh(_MeshBase):
+    """Uniform Cartesian hex mesh (cg_create_mesh_structured)."""
+
+    def __init__(self, dims, origin, dx):
+        lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        self.origin = tuple(float(o) for o in origin)
+        self.dx = float(dx)
+        h = ctypes.c_void_p()
+        org = (ctypes.c_double * 3)(*self.origin)
+        _check(lib.cg_create_mesh_structured(self.dims[0], self.dims[1], self.dims[2], org, self.dx,
+                                             ctypes.byref(h)), "cg_create_mesh_structured")
+        self._h = h
+
+
+class TetMesh(_MeshBase):
+    """Unstructured tetrahedral mesh (cg_create_mesh_tet); xyz [nv,3] f64, tets [nt,4] i32."""
+
+    def __init__(self, xyz, tets):
+        import numpy as np
+        lib = load_library()
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.tets = np.ascontiguousarray(tets, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.cg_create_mesh_tet(self.xyz.shape[0], self.xyz.ctypes.data, self.tets.shape[0],
+                                      self.tets.ctypes.data, ctypes.byref(h)), "cg_create_mesh_tet")
+        self._h = h
+
+    def operator(self):
+        import numpy as np
+        lib = load_library()
+        nnz = ctypes.c_int64()
+        _check(lib.cg_mesh_tet_operator(self._h, None, None, None, ctypes.byref(nnz)), "operator")
+        rp = np.empty(self.ncells + 1, dtype=np.int64)
+        col = np.empty(nnz.value, dtype=np.int32)
+        val = np.empty(nnz.value, dtype=np.float64)
+        _check(lib.cg_mesh_tet_operator(self._h, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                        ctypes.byref(nnz)), "operator")
+        return rp, col, val
+
+
+def locate(mesh, pos, out=None, stream=None):
+    """Host cell per particle (cg_locate).  pos: CUDA f64 [3, n].  Returns (cell i32, n_out)."""
+    import torch
+    _dev_f64(pos, "pos")
+    n = pos.shape[1]
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=pos.device)
+    nout = ctypes.c_int64()
+    _check(load_library().cg_locate(mesh.handle, n, pos.data_ptr(), out.data_ptr(),
+                                    ctypes.byref(nout), _stream_handle(stream)), "cg_locate")
+    return out, int(nout.value)
+
+
+def deposit(mesh, pos, w, params: Params | None = None, out=None, stream=None, report=False):
+    """Particle centroid deposition, Eq. (pcm-k).  pos [3,n], w [nf,n] CUDA f64."""
+    import torch
+    params = params or Params()
+    _dev_f64(pos, "pos")
+    _dev_f64(w, "w")
+    nf, n = w.shape
+    if out is None:
+        out = torch.empty((nf, mesh.ncells), dtype=torch.float64, device=w.device)
+    rep = CgReport()
+    cp = params.to_c()
+    _check(load_library().cg_deposit(mesh.handle, n, pos.data_ptr(), nf, w.data_ptr(),
+                                     out.data_ptr(), ctypes.byref(cp), ctypes.byref(rep),
+                                     _stream_handle(stream)), "cg_deposit")
+    return (out, rep.as_dict()) if report else out
+
+
+def diffuse(mesh, cells, params: Params, stream=None, report=False):
+    """Diffusion smoothing in place, Eq. (diffusion) to T.  cells [nf, ncells] CUDA f64."""
+    _dev_f64(cells, "cells")
+    nf = cells.shape[0] if cells.dim() == 2 else 1
+    rep = CgReport()
+    cp = params.to_c()
+    _check(load_library().cg_diffuse(mesh.handle, nf, cells.data_ptr(), ctypes.byref(cp),
+                                     ctypes.byref(rep), _stream_handle(stream)), "cg_diffuse")
+    return (cells, rep.as_dict()) if report else cells
+
+
+def coarse_grain(mesh, pos, w, params: Params, out=None, stream=None, report=False):
+    """The whole method (Section 2.6): deposition then diffusion."""
+    import torch
+    _dev_f64(pos, "pos")
+    _dev_f64(w, "w")
+    nf, n = w.shape
+    if out is None:
+        out = torch.empty((nf, mesh.ncells), dtype=torch.float64, device=w.device)
+    rep = CgReport()
+    cp = params.to_c()
+    _check(load_library().cg_coarse_grain(mesh.handle, n, pos.data_ptr(), nf, w.data_ptr(),
+                                          out.data_ptr(), ctypes.byref(cp), ctypes.byref(rep),
+                                          _stream_handle(stream)), "cg_coarse_grain")
+    return (out, rep.as_dict()) if report else out
+
+
+def coarse_grain_host(mesh, pos, w, params: Params, out=None, stream=None, report=False):
+    """The whole method on HOST arrays (numpy or CPU tensors, f64, contiguous)."""
+    import numpy as np
+    pos = np.ascontiguousarray(pos, dtype=np.float64) if not hasattr(pos, "data_ptr") else pos
+    w = np.ascontiguousarray(w, dtype=np.float64) if not hasattr(w, "data_ptr") else w
+    nf, n = w.shape
+
+    def ptr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+    if out is None:
+        out = np.empty((nf, mesh.ncells), dtype=np.float64)
+    rep = CgReport()
+    cp = params.to_c()
+    _check(load_library().cg_coarse_grain_host(mesh.handle, n, ptr(pos), nf, ptr(w), ptr(out),
+                                               ctypes.byref(cp), ctypes.byref(rep),
+                                               _stream_handle(stream)), "cg_coarse_grain_host")
+    return (out, rep.as_dict()) if report else out
+
+
+def profile_enable(on: bool = True):
+    """Per-kernel device timing (cg_profile_enable)."""
+    load_library().cg_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load_library().cg_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: {"launches", "ms", "bytes"}} accumulated while profiling was on."""
+    lib = load_library()
+    out = {}
+    for i in range(lib.cg_profile_count()):
+        name = ctypes.create_string_buffer(64)
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        _check(lib.cg_profile_get(i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)),
+               "cg_profile_get")
+        out[name.value.decode()] = {"launches": int(n.value), "ms": ms.value, "bytes": by.value}
+    return out

@@ -1,0 +1,486 @@
+// capi.cu -- the extern "C" entry points of include/cg.h: argument validation, mesh
+// objects, workspace management and phase orchestration.  The arithmetic of the
+// method lives in deposit.cu (Section 3.1), stencil.cu and tet.cu (Section 3.2).
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+namespace cgk {
+
+static thread_local char g_last_error[512] = "";
+
+cg_status fail(cg_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+cg_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what,
+             cudaGetErrorString(e), file, line);
+    return e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA;
+}
+
+cg_status DevBuf::ensure(size_t n) {
+    if (n <= bytes) return CG_OK;
+    if (p) {
+        cudaError_t e = cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree", __FILE__, __LINE__);
+    }
+    size_t want = n + n / 8;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(CG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    bytes = want;
+    return CG_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+cg_status HostBuf::ensure(size_t n) {
+    if (n <= bytes) return CG_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMallocHost(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(CG_ENOMEM, "cudaMallocHost of %zu bytes failed", n);
+    }
+    bytes = n;
+    return CG_OK;
+}
+
+void HostBuf::release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+int num_sms() {
+    static thread_local int dev = -1, sms = 0;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0)
+            v = 148;
+        dev = d;
+        sms = v;
+    }
+    return sms;
+}
+
+// ----------------------------------------------------------------------------- profiler
+namespace {
+struct ProfEntry {
+    std::string name;
+    long long launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+struct Pending {
+    cudaEvent_t a, b;
+    int entry;
+    double bytes;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_enabled{false};
+std::vector<ProfEntry> g_prof;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t pool_get() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+std::atomic<long long> g_launches{0};
+
+bool prof_on() { return g_prof_enabled.load(std::memory_order_relaxed); }
+
+ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : st(s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!prof_on()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int entry = -1;
+    for (size_t i = 0; i < g_prof.size(); ++i)
+        if (g_prof[i].name == name) entry = (int)i;
+    if (entry < 0) {
+        g_prof.push_back(ProfEntry{name});
+        entry = (int)g_prof.size() - 1;
+    }
+    Pending pe{pool_get(), pool_get(), entry, bytes};
+    cudaEventRecord(pe.a, st);
+    g_pending.push_back(pe);
+    slot = (int)g_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_pending[slot].b, st);
+}
+
+void prof_collect() {
+    if (!prof_on()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &pe : g_pending) {
+        cudaEventSynchronize(pe.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pe.a, pe.b);
+        ProfEntry &e = g_prof[pe.entry];
+        e.launches += 1;
+        e.ms += ms;
+        e.bytes += pe.bytes;
+        g_event_pool.push_back(pe.a);
+        g_event_pool.push_back(pe.b);
+    }
+    g_pending.clear();
+}
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static cg_status check_params(const cg_params *p) {
+    if (!p) return fail(CG_EINVAL, "params is NULL");
+    if (p->nsteps < 1) return fail(CG_EINVAL, "nsteps must be >= 1 (got %d)", p->nsteps);
+    if (p->scheme < 0 || p->scheme > 2) return fail(CG_EINVAL, "unknown scheme %d", p->scheme);
+    if (p->precision < 0 || p->precision > 2)
+        return fail(CG_EINVAL, "unknown precision %d", p->precision);
+    if (p->deposit_mode < 0 || p->deposit_mode > 1)
+        return fail(CG_EINVAL, "unknown deposit_mode %d", p->deposit_mode);
+    double T = p->bandwidth > 0.0 ? p->bandwidth * p->bandwidth / 4.0 : p->T;
+    if (!(T >= 0.0) || !std::isfinite(T)) return fail(CG_EINVAL, "pseudo-time T must be finite and >= 0");
+    if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(CG_EINVAL, "tol must be in (0, 1)");
+    if (p->max_iter < 1) return fail(CG_EINVAL, "max_iter must be >= 1");
+    return CG_OK;
+}
+
+}  // namespace cgk
+
+using namespace cgk;
+
+extern "C" {
+
+const char *cg_status_string(cg_status s) {
+    switch (s) {
+        case CG_OK: return "CG_OK";
+        case CG_EINVAL: return "CG_EINVAL";
+        case CG_ENOMEM: return "CG_ENOMEM";
+        case CG_ECUDA: return "CG_ECUDA";
+        case CG_ENOCONV: return "CG_ENOCONV";
+        case CG_ETIMEOUT: return "CG_ETIMEOUT";
+        case CG_EDOMAIN: return "CG_EDOMAIN";
+    }
+    return "CG_UNKNOWN";
+}
+
+const char *cg_last_error(void) { return g_last_error; }
+
+cg_status cg_profile_enable(int on) {
+    prof_collect();
+    g_prof_enabled.store(on != 0);
+    return CG_OK;
+}
+
+long long cg_launch_count(void) { return g_launches.load(); }
+
+void cg_launch_count_reset(void) { g_launches.store(0); }
+
+void cg_profile_reset(void) {
+    prof_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.clear();
+}
+
+int cg_profile_count(void) {
+    prof_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return (int)g_prof.size();
+}
+
+cg_status cg_profile_get(int i, char *name, int name_len, long long *launches, double *ms,
+                         double *bytes) {
+    prof_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (i < 0 || i >= (int)g_prof.size()) return fail(CG_EINVAL, "profile index out of range");
+    const ProfEntry &e = g_prof[i];
+    if (name && name_len > 0) {
+        std::strncpy(name, e.name.c_str(), (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    if (launches) *launches = e.launches;
+    if (ms) *ms = e.ms;
+    if (bytes) *bytes = e.bytes;
+    return CG_OK;
+}
+
+void cg_params_default(cg_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nsteps = 10;
+    p->scheme = CG_SCHEME_IMPLICIT_EULER;
+    p->precision = CG_PREC_FP64;
+    p->deposit_mode = CG_DEPOSIT_ORDERED;
+    p->tol = 1e-13;
+    p->max_iter = 10000;
+    p->max_rounds = 12;
+    p->fused_k = 0;
+    p->debug_barrier_budget = 0;
+}
+
+cg_status cg_create_mesh_structured(int nx, int ny, int nz, const double origin[3], double dx,
+                                    cg_mesh **out) {
+    if (!out) return fail(CG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!origin) return fail(CG_EINVAL, "origin is NULL");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(CG_EINVAL, "mesh dimensions must be >= 1");
+    if ((int64_t)nx * ny * nz >= ((int64_t)1 << 31))
+        return fail(CG_EINVAL, "mesh too large: nx*ny*nz must be < 2^31");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(CG_EINVAL, "dx must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin[a])) return fail(CG_EINVAL, "origin must be finite");
+    cg_mesh *m = new (std::nothrow) cg_mesh();
+    if (!m) return fail(CG_ENOMEM, "host allocation failed");
+    m->kind = MESH_STRUCTURED;
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    for (int a = 0; a < 3; ++a) m->origin[a] = origin[a];
+    m->dx = dx;
+    m->ncells = (int64_t)nx * ny * nz;
+    *out = m;
+    return CG_OK;
+}
+
+cg_status cg_create_mesh_tet(int64_t nverts, const double *xyz_host, int64_t ntets,
+                             const int32_t *tv_host, cg_mesh **out) {
+    if (!out) return fail(CG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nverts < 4 || ntets < 1 || !xyz_host || !tv_host)
+        return fail(CG_EINVAL, "a tet mesh needs >= 4 vertices, >= 1 tet and host arrays");
+    if (ntets >= ((int64_t)1 << 31) / 5 || nverts >= ((int64_t)1 << 31))
+        return fail(CG_EINVAL, "tet mesh too large");
+    cg_mesh *m = new (std::nothrow) cg_mesh();
+    if (!m) return fail(CG_ENOMEM, "host allocation failed");
+    m->kind = MESH_TET;
+    m->ncells = ntets;
+    m->nverts = nverts;
+    cg_status s = tet_build(m, nverts, xyz_host, ntets, tv_host);
+    if (s != CG_OK) {
+        tet_release(m);
+        delete m;
+        return s;
+    }
+    *out = m;
+    return CG_OK;
+}
+
+cg_status cg_destroy_mesh(cg_mesh *m) {
+    if (!m) return CG_OK;
+    m->ws_locate.release();
+    m->ws_sort.release();
+    m->ws_diffuse.release();
+    m->ws_small.release();
+    m->ws_stage.release();
+    m->h_small.release();
+    if (m->kind == MESH_TET) tet_release(m);
+    delete m;
+    return CG_OK;
+}
+
+int64_t cg_mesh_num_cells(const cg_mesh *m) { return m ? m->ncells : -1; }
+
+cg_status cg_mesh_cell_volumes(const cg_mesh *m, double *out_host) {
+    if (!m || !out_host) return fail(CG_EINVAL, "NULL argument");
+    if (m->kind == MESH_STRUCTURED) {
+        double v = (m->dx * m->dx) * m->dx;
+        for (int64_t k = 0; k < m->ncells; ++k) out_host[k] = v;
+    } else {
+        std::memcpy(out_host, m->h_vc.data(), (size_t)m->ncells * sizeof(double));
+    }
+    return CG_OK;
+}
+
+cg_status cg_mesh_tet_operator(const cg_mesh *m, int64_t *rowptr_host, int32_t *col_host,
+                               double *val_host, int64_t *nnz_out) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    if (m->kind != MESH_TET) return fail(CG_EINVAL, "not a tet mesh");
+    if (nnz_out) *nnz_out = (int64_t)m->h_col.size();
+    if (rowptr_host)
+        for (int64_t k = 0; k <= m->ncells; ++k) rowptr_host[k] = m->h_rowptr[k];
+    if (col_host) std::memcpy(col_host, m->h_col.data(), m->h_col.size() * sizeof(int32_t));
+    if (val_host) std::memcpy(val_host, m->h_val.data(), m->h_val.size() * sizeof(double));
+    return CG_OK;
+}
+
+cg_status cg_locate(cg_mesh *m, int64_t n, const double *pos, int32_t *cell_out,
+                    int64_t *n_out_host, void *stream) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
+    if (n > 0 && (!is_device_ptr(pos) || !is_device_ptr(cell_out)))
+        return fail(CG_EINVAL, "pos and cell_out must be device pointers");
+    int64_t nout = 0;
+    CGK_TRY(locate_run(m, n, pos, 0, nullptr, cell_out, nullptr, &nout, nullptr,
+                       (cudaStream_t)stream));
+    prof_collect();
+    if (n_out_host) *n_out_host = nout;
+    return CG_OK;
+}
+
+static cg_status check_deposit_args(cg_mesh *m, int64_t n, const double *pos, int nfields,
+                                    const double *w, double *cells, const cg_params *p) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    CGK_TRY(check_params(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
+    if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
+    if ((int64_t)nfields * m->ncells >= ((int64_t)1 << 40))
+        return fail(CG_EINVAL, "nfields * ncells too large");
+    if (!is_device_ptr(cells)) return fail(CG_EINVAL, "cells must be a device pointer");
+    if (n > 0 && (!is_device_ptr(pos) || !is_device_ptr(w)))
+        return fail(CG_EINVAL, "pos and w must be device pointers");
+    return CG_OK;
+}
+
+cg_status cg_deposit(cg_mesh *m, int64_t n, const double *pos, int nfields, const double *w,
+                     double *cells_out, const cg_params *p, cg_report *rep, void *stream) {
+    CGK_TRY(check_deposit_args(m, n, pos, nfields, w, cells_out, p));
+    cg_status s = deposit_run(m, n, pos, nfields, w, cells_out, p, rep, (cudaStream_t)stream);
+    prof_collect();
+    return s;
+}
+
+static cg_status diffuse_impl(cg_mesh *m, int nf, double *cells, const cg_params *p,
+                              cg_report *rep, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rep) {
+        CGK_TRY(field_mass(m, nf < CG_REPORT_MAX_FIELDS ? nf : CG_REPORT_MAX_FIELDS, cells,
+                           rep->mass_in, st));
+        CGK_CUDA(cudaEventCreate(&e0));
+        CGK_CUDA(cudaEventCreate(&e1));
+        CGK_CUDA(cudaEventRecord(e0, st));
+    }
+    cg_status s;
+    double T = p->bandwidth > 0.0 ? p->bandwidth * p->bandwidth / 4.0 : p->T;
+    if (T == 0.0) {
+        s = CG_OK;   // nothing to smooth
+    } else if (m->kind == MESH_STRUCTURED) {
+        s = diffuse_structured_run(m, nf, cells, p, rep, st);
+    } else {
+        s = diffuse_tet_run(m, nf, cells, p, rep, st);
+    }
+    if (rep) {
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        rep->ms_diffuse = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (s == CG_OK || s == CG_ENOCONV) {
+            cg_status s2 = field_mass(m, nf < CG_REPORT_MAX_FIELDS ? nf : CG_REPORT_MAX_FIELDS,
+                                      cells, rep->mass_out, st);
+            if (s == CG_OK) s = s2;
+        }
+    }
+    return s;
+}
+
+cg_status cg_diffuse(cg_mesh *m, int nfields, double *cells, const cg_params *p, cg_report *rep,
+                     void *stream) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    CGK_TRY(check_params(p));
+    if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
+    if (!is_device_ptr(cells)) return fail(CG_EINVAL, "cells must be a device pointer");
+    if (rep) {
+        double keep_loc = rep->ms_locate, keep_dep = rep->ms_deposit;
+        long long keep_out = rep->n_out_of_domain;
+        int keep_bits[CG_REPORT_MAX_FIELDS];
+        std::memcpy(keep_bits, rep->fixed_point_bits, sizeof(keep_bits));
+        std::memset(rep, 0, sizeof(*rep));
+        rep->ms_locate = keep_loc;
+        rep->ms_deposit = keep_dep;
+        rep->n_out_of_domain = keep_out;
+        std::memcpy(rep->fixed_point_bits, keep_bits, sizeof(keep_bits));
+    }
+    cg_status s = diffuse_impl(m, nfields, cells, p, rep, (cudaStream_t)stream);
+    prof_collect();
+    return s;
+}
+
+cg_status cg_coarse_grain(cg_mesh *m, int64_t n, const double *pos, int nfields, const double *w,
+                          double *cells_out, const cg_params *p, cg_report *rep, void *stream) {
+    CGK_TRY(check_deposit_args(m, n, pos, nfields, w, cells_out, p));
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    cudaStream_t st = (cudaStream_t)stream;
+    cg_status s = deposit_run(m, n, pos, nfields, w, cells_out, p, rep, st);
+    if (s == CG_OK) s = diffuse_impl(m, nfields, cells_out, p, rep, st);
+    prof_collect();
+    return s;
+}
+
+cg_status cg_coarse_grain_host(cg_mesh *m, int64_t n, const double *pos_host, int nfields,
+                               const double *w_host, double *cells_host, const cg_params *p,
+                               cg_report *rep, void *stream) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    CGK_TRY(check_params(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
+    if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
+    if (!cells_host || (n > 0 && (!pos_host || !w_host)))
+        return fail(CG_EINVAL, "NULL host array");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t b_pos = ((size_t)3 * n * 8 + 255) / 256 * 256;
+    size_t b_w = ((size_t)nfields * n * 8 + 255) / 256 * 256;
+    size_t b_c = (size_t)nfields * m->ncells * 8;
+    CGK_TRY(m->ws_stage.ensure(b_pos + b_w + b_c + 256));
+    char *base = m->ws_stage.as<char>();
+    double *dpos = (double *)base, *dw = (double *)(base + b_pos), *dc = (double *)(base + b_pos + b_w);
+    if (n > 0) {
+        CGK_CUDA(cudaMemcpyAsync(dpos, pos_host, (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
+        CGK_CUDA(cudaMemcpyAsync(dw, w_host, (size_t)nfields * n * 8, cudaMemcpyHostToDevice, st));
+    }
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    CGK_TRY(deposit_run(m, n, dpos, nfields, dw, dc, p, rep, st));
+    cg_status s = diffuse_impl(m, nfields, dc, p, rep, st);
+    if (s != CG_OK && s != CG_ENOCONV) return s;
+    CGK_CUDA(cudaMemcpyAsync(cells_host, dc, b_c, cudaMemcpyDeviceToHost, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    prof_collect();
+    return s;
+}
+
+}  // extern "C"

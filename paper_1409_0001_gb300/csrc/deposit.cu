@@ -1,0 +1,530 @@
+// deposit.cu -- particle centroid method on the GPU (Section 2.2, Section 3.1
+// Eq. (pcm-k)): locate each particle's host cell, then sum the particles' carried
+// quantities per cell and divide by the cell volume.
+//
+// Ordered mode reproduces a sequential loop over particles bit for bit: the
+// (cell, particle) pairs are put in cell order by a stable LSD radix sort on the
+// cell id (particle order is kept inside a cell), and one thread per cell adds its
+// segment's weights in that order, in FP64 starting from +0.0, then divides by V_c
+// with an IEEE division.  Fixed-point mode quantises w * 2^F to int64 (round half to
+// even) and adds with 64-bit integer atomics, which is exact and order-free.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace cgk {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int per_block = kThreads, int max_blocks_per_sm = 8) {
+    int64_t b = (n + per_block - 1) / per_block;
+    int64_t cap = (int64_t)num_sms() * max_blocks_per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// --------------------------------------------------------------------------- locate
+// Host cell per axis: i = floor((x - x0) * inv_dx) clamped into [0, n-1]; outside
+// unless x0 <= x <= hi on every axis (NaN is outside).  Every FP64 operation is an
+// explicitly rounded intrinsic so that no multiply-add is contracted.
+__global__ void k_locate_structured(int64_t n, const double *__restrict__ pos, int nx, int ny,
+                                    int nz, double ox, double oy, double oz, double inv_dx,
+                                    double hx, double hy, double hz, int nf,
+                                    const double *__restrict__ w, int32_t *__restrict__ cell,
+                                    uint32_t *__restrict__ counts,
+                                    unsigned long long *__restrict__ bad) {
+    unsigned long long n_out = 0, n_nonfinite = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
+        for (int f = 0; f < nf; ++f)
+            if (!isfinite(w[(int64_t)f * n + i])) ++n_nonfinite;
+        bool inside = (x >= ox) && (x <= hx) && (y >= oy) && (y <= hy) && (z >= oz) && (z <= hz);
+        int32_t c = -1;
+        if (inside) {
+            int ix = (int)floor(__dmul_rn(__dsub_rn(x, ox), inv_dx));
+            int iy = (int)floor(__dmul_rn(__dsub_rn(y, oy), inv_dx));
+            int iz = (int)floor(__dmul_rn(__dsub_rn(z, oz), inv_dx));
+            ix = min(max(ix, 0), nx - 1);
+            iy = min(max(iy, 0), ny - 1);
+            iz = min(max(iz, 0), nz - 1);
+            c = (int32_t)(((int64_t)iz * ny + iy) * nx + ix);
+            if (counts) atomicAdd(&counts[c], 1u);
+        } else {
+            ++n_out;
+        }
+        cell[i] = c;
+    }
+    // warp-aggregate the rare error counters
+    for (int o = 16; o > 0; o >>= 1) {
+        n_out += __shfl_down_sync(0xffffffffu, n_out, o);
+        n_nonfinite += __shfl_down_sync(0xffffffffu, n_nonfinite, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_out) atomicAdd(&bad[0], n_out);
+        if (n_nonfinite) atomicAdd(&bad[1], n_nonfinite);
+    }
+}
+
+// --------------------------------------------------------------------------- scan
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kThreads * kScanItems;  // 4096 values per block
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[kThreads / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < kThreads / 32 ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t warp_off = warp ? warp_sums[warp - 1] : 0;
+    uint32_t tot = warp_sums[kThreads / 32 - 1];
+    __syncthreads();
+    if (total) *total = tot;
+    return warp_off + inc - v;
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
+                              uint32_t *__restrict__ block_sums) {
+    int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+    for (int j = threadIdx.x; j < kScanChunk; j += kThreads) {
+        int64_t i = base + j;
+        if (i < n) s += in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ uint32_t ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        block_sums[blockIdx.x] = t;
+    }
+}
+
+// single block: exclusive scan of nb block sums, in place
+__global__ void k_scan_top(uint32_t *__restrict__ sums, int64_t nb) {
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kThreads) {
+        int64_t i = base + threadIdx.x;
+        uint32_t v = i < nb ? sums[i] : 0;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nb) sums[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void k_scan_down(const uint32_t *in, uint32_t *out, int64_t n,
+                            const uint32_t *__restrict__ block_off) {
+    __shared__ uint32_t tile[kScanChunk + kScanChunk / 32];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    for (int j = threadIdx.x; j < kScanChunk; j += kThreads) {
+        int64_t i = base + j;
+        tile[j + (j >> 5)] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+    int t0 = threadIdx.x * kScanItems;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int j = t0 + q;
+        v[q] = tile[j + (j >> 5)];
+        s += v[q];
+    }
+    __syncthreads();
+    uint32_t ex = block_exclusive_scan(s, nullptr) + block_off[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int j = t0 + q;
+        tile[j + (j >> 5)] = ex;
+        ex += v[q];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kScanChunk; j += kThreads) {
+        int64_t i = base + j;
+        if (i < n) out[i] = tile[j + (j >> 5)];
+    }
+}
+
+// --------------------------------------------------------------------------- radix sort
+// Stable LSD radix sort of 32-bit keys (cell ids) carrying 32-bit values (particle
+// ids), 8-bit digits.  A tile of 4096 keys per 256-thread block; inside a tile warp w
+// owns keys [w*512, (w+1)*512) in 16 rounds of 32 consecutive keys, and ranks each
+// key among equal digits with __match_any_sync, so ranks follow input order.
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortItems = 16;
+constexpr int kSortWarps = kThreads / 32;
+constexpr int kTile = kThreads * kSortItems;
+
+__global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                           int64_t n, int shift,
+                                                           uint32_t *__restrict__ hist,
+                                                           int ntiles) {
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int j = threadIdx.x; j < kTile; j += kThreads) {
+        int64_t i = base + j;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) k_radix_downsweep(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
+    const uint32_t *__restrict__ hist_scan, int ntiles) {
+    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    __shared__ uint32_t gbase[kRadix];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < kSortWarps * kRadix; j += kThreads) (&wcnt[0][0])[j] = 0;
+    gbase[threadIdx.x] = hist_scan[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+
+    const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)warp * (32 * kSortItems);
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t k[kSortItems], v[kSortItems], rk[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = wbase + r * 32 + lane;
+        bool valid = i < n;
+        uint32_t key = valid ? keys_in[i] : 0u;
+        uint32_t d = (key >> shift) & (kRadix - 1);
+        uint32_t tag = valid ? d : (0x10000u + lane);   // invalid lanes stay alone
+        unsigned peers = __match_any_sync(0xffffffffu, tag);
+        unsigned rank = __popc(peers & lt);
+        uint32_t old = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[warp][d] = old + __popc(peers);
+        __syncwarp();
+        k[r] = key;
+        v[r] = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+        rk[r] = old + rank;
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps for digit threadIdx.x
+        uint32_t run = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t t = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = wbase + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = (k[r] >> shift) & (kRadix - 1);
+            uint32_t dst = gbase[d] + wcnt[warp][d] + rk[r];
+            keys_out[dst] = k[r];
+            vals_out[dst] = v[r];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- sums
+// One thread per cell: S = +0.0; S += w[f][idx] over the cell's segment in ascending
+// particle index; eps = S / V_c.
+__global__ void k_segment_sum(int64_t ncells, const uint32_t *__restrict__ start,
+                              const uint32_t *__restrict__ counts,
+                              const uint32_t *__restrict__ sorted_idx, int nf,
+                              const double *__restrict__ w, int64_t n,
+                              const double *__restrict__ vc, double vc_uniform,
+                              double *__restrict__ out) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t s = start[c], e = s + counts[c];
+        double v = vc ? vc[c] : vc_uniform;
+        for (int f = 0; f < nf; ++f) {
+            const double *wf = w + (int64_t)f * n;
+            double acc = 0.0;
+            for (uint32_t p = s; p < e; ++p) acc = __dadd_rn(acc, wf[sorted_idx[p]]);
+            out[(int64_t)f * ncells + c] = __ddiv_rn(acc, v);
+        }
+    }
+}
+
+// max |w| per field as the bit pattern of a non-negative double (orders like uint64)
+__global__ void k_absmax(int64_t n, int nf, const double *__restrict__ w,
+                         unsigned long long *__restrict__ out) {
+    int f = blockIdx.y;
+    const double *wf = w + (int64_t)f * n;
+    unsigned long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(fabs(wf[i]));
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_down_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&out[f], m);
+}
+
+__global__ void k_fixed_accum(int64_t n, const int32_t *__restrict__ cell, int nf,
+                              const double *__restrict__ w, const double *__restrict__ scale,
+                              unsigned long long *__restrict__ acc, int64_t ncells) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = cell[i];
+        if (c < 0) continue;
+        for (int f = 0; f < nf; ++f) {
+            long long q = __double2ll_rn(__dmul_rn(w[(int64_t)f * n + i], scale[f]));
+            atomicAdd(&acc[(int64_t)f * ncells + c], (unsigned long long)q);
+        }
+    }
+}
+
+__global__ void k_fixed_finalize(int64_t ncells, int nf,
+                                 const unsigned long long *__restrict__ acc,
+                                 const double *__restrict__ unscale,
+                                 const double *__restrict__ vc, double vc_uniform,
+                                 double *__restrict__ out) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        double v = vc ? vc[c] : vc_uniform;
+        for (int f = 0; f < nf; ++f) {
+            long long s = (long long)acc[(int64_t)f * ncells + c];
+            double x = __dmul_rn(__ll2double_rn(s), unscale[f]);
+            out[(int64_t)f * ncells + c] = __ddiv_rn(x, v);
+        }
+    }
+}
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+// ============================================================================ host side
+size_t scan_tmp_words(int64_t n) {
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    return (size_t)(nb > 0 ? nb : 1);
+}
+
+cg_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
+                             cudaStream_t st) {
+    if (n <= 0) return CG_OK;
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    CGK_LAUNCH("scan_reduce", (double)n * 4, st,
+               k_scan_reduce<<<(unsigned)nb, kThreads, 0, st>>>(in, n, tmp));
+    CGK_LAUNCH("scan_top", (double)nb * 8, st, k_scan_top<<<1, kThreads, 0, st>>>(tmp, nb));
+    CGK_LAUNCH("scan_down", (double)n * 8, st,
+               k_scan_down<<<(unsigned)nb, kThreads, 0, st>>>(in, out, n, tmp));
+    CGK_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+// Forward declaration of the tet locate launcher (tet.cu).
+cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                            int32_t *cell_out, uint32_t *counts, unsigned long long *bad,
+                            cudaStream_t st);
+
+cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                     int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
+                     cudaStream_t st) {
+    CGK_TRY(m->ws_small.ensure(4096));
+    CGK_TRY(m->h_small.ensure(4096));
+    unsigned long long *bad = m->ws_small.as<unsigned long long>();
+    CGK_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), st));
+    if (n > 0) {
+        if (m->kind == MESH_STRUCTURED) {
+            double hi[3];
+            const int dims[3] = {m->nx, m->ny, m->nz};
+            for (int a = 0; a < 3; ++a) {
+                volatile double len = (double)dims[a] * m->dx;   // two roundings, as defined
+                hi[a] = m->origin[a] + len;
+            }
+            double inv_dx = 1.0 / m->dx;
+            CGK_LAUNCH("locate_structured", (double)n * (24 + 8 * nf + 4), st,
+                       k_locate_structured<<<grid_for(n), kThreads, 0, st>>>(
+                           n, pos, m->nx, m->ny, m->nz, m->origin[0], m->origin[1],
+                           m->origin[2], inv_dx, hi[0], hi[1], hi[2], nf, w, cell_out, counts,
+                           bad));
+            CGK_CUDA(cudaGetLastError());
+        } else {
+            CGK_TRY(tet_locate_launch(m, n, pos, nf, w, cell_out, counts, bad, st));
+        }
+    }
+    unsigned long long *hb = m->h_small.as<unsigned long long>();
+    CGK_CUDA(cudaMemcpyAsync(hb, bad, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    if (n_out) *n_out = (int64_t)hb[0];
+    if (n_nonfinite) *n_nonfinite = (int64_t)hb[1];
+    return CG_OK;
+}
+
+// Scale exponent of the fixed-point mode: with m = max|w| = fm*2^em, n = fn*2^en
+// (frexp), F = 61 - em - en (so n*m*2^F < 2^61), F = 0 if m == 0, clamped to
+// [-1000, 1000] so that the scales and every rescaled non-zero sum stay normal.
+static int fixed_bits(int64_t n, double maxabs) {
+    if (n <= 0 || !(maxabs > 0.0)) return 0;
+    int em = 0, en = 0;
+    std::frexp(maxabs, &em);
+    std::frexp((double)n, &en);
+    int F = 61 - em - en;
+    return F > 1000 ? 1000 : (F < -1000 ? -1000 : F);
+}
+
+cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                      double *out, const cg_params *p, cg_report *rep, cudaStream_t st) {
+    const int64_t ncells = m->ncells;
+    const int mode = p->deposit_mode;
+    const double *vc = m->kind == MESH_TET ? m->tet.vc : nullptr;
+    const double vcu = m->kind == MESH_TET ? 0.0 : (m->dx * m->dx) * m->dx;
+
+    // workspace: cell[n] (int32) | counts[ncells] | start[ncells] | scan tmp
+    size_t off_cell = 0;
+    size_t off_counts = align_up(off_cell + (size_t)n * 4);
+    size_t off_start = align_up(off_counts + (size_t)ncells * 4);
+    size_t off_tmp = align_up(off_start + (size_t)ncells * 4);
+    size_t need = align_up(off_tmp + scan_tmp_words(ncells) * 4);
+    CGK_TRY(m->ws_locate.ensure(need));
+    char *base = m->ws_locate.as<char>();
+    int32_t *cell = (int32_t *)(base + off_cell);
+    uint32_t *counts = (uint32_t *)(base + off_counts);
+    uint32_t *start = (uint32_t *)(base + off_start);
+    uint32_t *tmp = (uint32_t *)(base + off_tmp);
+
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (rep) {
+        for (auto &e : ev) CGK_CUDA(cudaEventCreate(&e));
+        CGK_CUDA(cudaEventRecord(ev[0], st));
+    }
+    if (mode == CG_DEPOSIT_ORDERED) CGK_CUDA(cudaMemsetAsync(counts, 0, (size_t)ncells * 4, st));
+    int64_t n_out = 0, n_bad = 0;
+    CGK_TRY(locate_run(m, n, pos, nf, w, cell, mode == CG_DEPOSIT_ORDERED ? counts : nullptr,
+                       &n_out, &n_bad, st));
+    if (rep) {
+        CGK_CUDA(cudaEventRecord(ev[1], st));
+        rep->n_out_of_domain = n_out;
+    }
+    if (n_bad) return fail(CG_EINVAL, "cg_deposit: %lld non-finite weights", (long long)n_bad);
+    if (n_out)
+        return fail(CG_EDOMAIN, "cg_deposit: %lld particles outside the mesh", (long long)n_out);
+
+    if (mode == CG_DEPOSIT_ORDERED) {
+        // stable sort of (cell, particle) by cell
+        int bits = 1;
+        while (bits < 32 && ((int64_t)1 << bits) < ncells) ++bits;
+        int passes = (bits + kRadixBits - 1) / kRadixBits;
+        int64_t ntiles = (n + kTile - 1) / kTile;
+        if (ntiles < 1) ntiles = 1;
+        int64_t hist_n = (int64_t)kRadix * ntiles;
+        size_t s_keys = align_up((size_t)n * 4);
+        size_t s_hist = align_up((size_t)hist_n * 4);
+        size_t s_htmp = align_up(scan_tmp_words(hist_n) * 4);
+        CGK_TRY(m->ws_sort.ensure(4 * s_keys + s_hist + s_htmp));
+        char *sb = m->ws_sort.as<char>();
+        uint32_t *ka = (uint32_t *)sb, *kb = (uint32_t *)(sb + s_keys);
+        uint32_t *va = (uint32_t *)(sb + 2 * s_keys), *vb = (uint32_t *)(sb + 3 * s_keys);
+        uint32_t *hist = (uint32_t *)(sb + 4 * s_keys);
+        uint32_t *htmp = (uint32_t *)(sb + 4 * s_keys + s_hist);
+        const uint32_t *kin = (const uint32_t *)cell;   // no cell is negative here
+        const uint32_t *vin = nullptr;                  // identity on the first pass
+        uint32_t *kout = ka, *vout = va;
+        if (n > 0) {
+            for (int ps = 0; ps < passes; ++ps) {
+                int shift = ps * kRadixBits;
+                CGK_LAUNCH("radix_upsweep", (double)n * 4, st,
+                           k_radix_upsweep<<<(unsigned)ntiles, kThreads, 0, st>>>(
+                               kin, n, shift, hist, (int)ntiles));
+                CGK_TRY(exclusive_scan_u32(hist, hist, hist_n, htmp, st));
+                CGK_LAUNCH("radix_downsweep", (double)n * (vin ? 16 : 12), st,
+                           k_radix_downsweep<<<(unsigned)ntiles, kThreads, 0, st>>>(
+                               kin, vin, kout, vout, n, shift, hist, (int)ntiles));
+                CGK_CUDA(cudaGetLastError());
+                kin = kout;
+                vin = vout;
+                kout = (kout == ka) ? kb : ka;
+                vout = (vout == va) ? vb : va;
+            }
+        }
+        CGK_TRY(exclusive_scan_u32(counts, start, ncells, tmp, st));
+        CGK_LAUNCH("segment_sum", (double)n * (4 + 8 * nf) + (double)ncells * (8 + 8 * nf), st,
+                   k_segment_sum<<<grid_for(ncells), kThreads, 0, st>>>(
+                       ncells, start, counts, vin, nf, w, n, vc, vcu, out));
+        CGK_CUDA(cudaGetLastError());
+        if (rep)
+            for (int f = 0; f < nf && f < CG_REPORT_MAX_FIELDS; ++f) rep->fixed_point_bits[f] = 0;
+    } else {
+        // fixed point: F per field from max|w|
+        size_t s_acc = align_up((size_t)ncells * nf * 8);
+        CGK_TRY(m->ws_sort.ensure(s_acc + 4096));
+        unsigned long long *acc = m->ws_sort.as<unsigned long long>();
+        unsigned long long *mx = (unsigned long long *)(m->ws_sort.as<char>() + s_acc);
+        double *scales = (double *)(mx + 64);
+        CGK_CUDA(cudaMemsetAsync(mx, 0, 64 * 8, st));
+        if (n > 0) {
+            dim3 g(grid_for(n), nf);
+            CGK_LAUNCH("absmax", (double)n * nf * 8, st,
+                       k_absmax<<<g, kThreads, 0, st>>>(n, nf, w, mx));
+            CGK_CUDA(cudaGetLastError());
+        }
+        CGK_TRY(m->h_small.ensure(4096));
+        unsigned long long *hmx = m->h_small.as<unsigned long long>();
+        CGK_CUDA(cudaMemcpyAsync(hmx, mx, nf * 8, cudaMemcpyDeviceToHost, st));
+        CGK_CUDA(cudaStreamSynchronize(st));
+        double hs[2 * 64];
+        for (int f = 0; f < nf; ++f) {
+            double mabs;
+            std::memcpy(&mabs, &hmx[f], 8);
+            int F = fixed_bits(n, mabs);
+            hs[f] = std::ldexp(1.0, F);
+            hs[64 + f] = std::ldexp(1.0, -F);
+            if (rep && f < CG_REPORT_MAX_FIELDS) rep->fixed_point_bits[f] = F;
+        }
+        CGK_CUDA(cudaMemcpyAsync(scales, hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+        CGK_CUDA(cudaMemsetAsync(acc, 0, (size_t)ncells * nf * 8, st));
+        if (n > 0) {
+            CGK_LAUNCH("fixed_accum", (double)n * (4 + 8 * nf), st,
+                       k_fixed_accum<<<grid_for(n), kThreads, 0, st>>>(n, cell, nf, w, scales,
+                                                                        acc, ncells));
+            CGK_CUDA(cudaGetLastError());
+        }
+        CGK_LAUNCH("fixed_finalize", (double)ncells * nf * 16, st,
+                   k_fixed_finalize<<<grid_for(ncells), kThreads, 0, st>>>(
+                       ncells, nf, acc, scales + 64, vc, vcu, out));
+        CGK_CUDA(cudaGetLastError());
+        // the host array hs must outlive the async copy
+        CGK_CUDA(cudaStreamSynchronize(st));
+    }
+    if (rep) {
+        CGK_CUDA(cudaEventRecord(ev[2], st));
+        CGK_CUDA(cudaEventSynchronize(ev[2]));
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        rep->ms_locate = a;
+        rep->ms_deposit = b;
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+    return CG_OK;
+}
+
+}  // namespace cgk

@@ -1,0 +1,157 @@
+// internal.cuh -- shared declarations of the CUDA library behind include/cg.h.
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+
+#include "cg.h"
+
+namespace cgk {
+
+// ----------------------------------------------------------------------------- errors
+// Records a message for cg_last_error() (per thread) and returns the status.
+cg_status fail(cg_status s, const char *fmt, ...);
+cg_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define CGK_CUDA(call)                                                          \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) return ::cgk::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define CGK_TRY(call)                                                           \
+    do {                                                                        \
+        cg_status s_ = (call);                                                  \
+        if (s_ != CG_OK) return s_;                                             \
+    } while (0)
+
+// ----------------------------------------------------------------------------- buffers
+// A device buffer that only grows.  Owned by a mesh; freed in cg_destroy_mesh.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cg_status ensure(size_t n);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// A pinned host buffer that only grows (readback of scalars, flags, counters).
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cg_status ensure(size_t n);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ----------------------------------------------------------------------------- meshes
+enum MeshKind { MESH_STRUCTURED = 0, MESH_TET = 1 };
+
+struct TetDevice {
+    // cell geometry and operator (device)
+    double *vc = nullptr;        // [ncells]
+    int32_t *rowptr = nullptr;   // [ncells+1]
+    int32_t *col = nullptr;      // [nnz]
+    double *val = nullptr;       // [nnz]  entries of L (diagonal included)
+    int64_t nnz = 0;
+    // point location (device)
+    double *xyz = nullptr;       // [nverts][3]
+    int32_t *tv = nullptr;       // [ntets][4]
+    double *box = nullptr;       // [ntets][6] lo.x lo.y lo.z hi.x hi.y hi.z
+    int32_t *bucket_start = nullptr;  // [nbuckets+1]
+    int32_t *bucket_tets = nullptr;   // [..] tet ids, ascending per bucket
+    int nb[3] = {0, 0, 0};
+    double blo[3] = {0, 0, 0};
+    double binv[3] = {0, 0, 0};
+};
+
+}  // namespace cgk
+
+struct cg_mesh {
+    int kind = cgk::MESH_STRUCTURED;
+    int nx = 0, ny = 0, nz = 0;
+    double origin[3] = {0, 0, 0};
+    double dx = 0;
+    int64_t ncells = 0;
+    int64_t nverts = 0;
+
+    cgk::TetDevice tet;
+    std::vector<double> h_vc;            // host copy of V_c (tet)
+    std::vector<int32_t> h_rowptr, h_col;
+    std::vector<double> h_val;
+
+    // workspaces (grown on demand)
+    cgk::DevBuf ws_locate;   // cell ids / keys / values / counts
+    cgk::DevBuf ws_sort;     // radix sort ping-pong and histograms
+    cgk::DevBuf ws_diffuse;  // solver vectors
+    cgk::DevBuf ws_small;    // scalars, partials, counters
+    cgk::DevBuf ws_stage;    // device staging for the host-pointer entry point
+    cgk::HostBuf h_small;    // pinned readback
+};
+
+namespace cgk {
+
+// ----------------------------------------------------------------------------- device props
+int num_sms();
+
+// ----------------------------------------------------------------------------- profiling
+// Opt-in per-kernel device timing (cg_profile_enable).  A scope records a CUDA event
+// pair on the launching stream around one launch and remembers the launch's
+// algorithmic bytes; prof_collect() (called after the stream is synchronised)
+// accumulates the elapsed times per kernel name.
+bool prof_on();
+struct ProfScope {
+    ProfScope(const char *name, double bytes, cudaStream_t st);
+    ~ProfScope();
+    int slot = -1;
+    cudaStream_t st = nullptr;
+};
+void prof_collect();
+
+// Launch with an optional profiling scope: CGK_LAUNCH("name", algorithmic_bytes, stream,
+// kernel<<<grid, block, smem, stream>>>(args...));
+#define CGK_LAUNCH(name, bytes, st, ...)                                        \
+    do {                                                                        \
+        ::cgk::ProfScope ps_(name, (double)(bytes), st);                        \
+        __VA_ARGS__;                                                            \
+    } while (0)
+
+// ----------------------------------------------------------------------------- phases
+// Locate (structured or tet).  Writes cell ids (int32, -1 outside) to cell_out and the
+// number outside / number of non-finite weights to the host.  If counts != nullptr
+// also accumulates per-cell particle counts (must be zeroed by the caller).
+cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                     int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
+                     cudaStream_t st);
+
+// Deposition (Eq. (pcm-k)) given particles; validates and writes out[nf][ncells].
+cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                      double *out, const cg_params *p, cg_report *rep, cudaStream_t st);
+
+// Diffusion on a structured mesh (in place).
+cg_status diffuse_structured_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
+                                 cg_report *rep, cudaStream_t st);
+
+// Diffusion on a tet mesh (in place).
+cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
+                          cg_report *rep, cudaStream_t st);
+
+// sum_k V_c,k u_f,k for each field (FP64, deterministic order), written to host.
+cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host,
+                     cudaStream_t st);
+
+// Tet mesh construction (host C++), fills m->tet and the host copies.
+cg_status tet_build(cg_mesh *m, int64_t nverts, const double *xyz, int64_t ntets,
+                    const int32_t *tv);
+void tet_release(cg_mesh *m);
+
+// Exclusive scan of n uint32 values (in and out may alias).  tmp needs
+// scan_tmp_words(n) words.
+size_t scan_tmp_words(int64_t n);
+cg_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
+                             cudaStream_t st);
+
+}  // namespace cgk

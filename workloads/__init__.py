@@ -87,27 +87,29 @@ def clustered_cube(n_side=128, n_particles=2_000_000, d=0.004, n_clusters=20, si
     centres = 0.1 + 0.8 * rng.random((n_clusters, 3))
     which = rng.integers(0, n_clusters, size=n_particles)
     pos = centres[which].T + sigma * rng.standard_normal((3, n_particles))
-    redo = np.ones(n_particles, dtype=bool)
-    for _ in range(max_tries + 1):
-        inside = np.all((pos >= 0.0) & (pos <= 1.0), axis=0)
-        # occupancy rank of each centroid in its (coarse, generator-only) bin, in order
-        ijk = np.clip(np.floor(np.where(inside, pos, 0.0) * n_side).astype(np.int64), 0, n_side - 1)
+    occupancy = np.zeros(n_side ** 3, dtype=np.int64)     # accepted centroids per bin
+    todo = np.arange(n_particles)                          # not yet accepted, in order
+    for attempt in range(max_tries + 1):
+        p = pos[:, todo]
+        inside = np.all((p >= 0.0) & (p <= 1.0), axis=0)
+        ijk = np.clip(np.floor(np.where(inside, p, 0.0) * n_side).astype(np.int64), 0, n_side - 1)
         binid = (ijk[2] * n_side + ijk[1]) * n_side + ijk[0]
-        binid = np.where(inside, binid, -1)
+        # rank of each candidate among this round's candidates of its bin, in index order
         order = np.argsort(binid, kind="stable")
         sb = binid[order]
-        starts = np.r_[0, np.flatnonzero(np.diff(sb)) + 1]
+        starts = np.r_[0, np.flatnonzero(np.diff(sb)) + 1] if len(sb) else np.zeros(0, np.int64)
         run_start = np.repeat(starts, np.diff(np.r_[starts, len(sb)]))
-        rank = np.empty(n_particles, dtype=np.int64)
-        rank[order] = np.arange(n_particles) - run_start
-        redo = (~inside) | (rank >= cap)
-        k = int(redo.sum())
-        if k == 0:
+        rank = np.empty(len(todo), dtype=np.int64)
+        rank[order] = np.arange(len(todo)) - run_start
+        ok = inside & (occupancy[binid] + rank < cap)
+        np.add.at(occupancy, binid[ok], 1)
+        todo = todo[~ok]
+        if len(todo) == 0:
             break
-        if _ == max_tries:
-            pos[:, redo] = rng.random((3, k))
+        if attempt == max_tries:
+            pos[:, todo] = rng.random((3, len(todo)))
             break
-        pos[:, redo] = centres[which[redo]].T + sigma * rng.standard_normal((3, k))
+        pos[:, todo] = centres[which[todo]].T + sigma * rng.standard_normal((3, len(todo)))
     w = np.full((1, n_particles), vp)
     return StructuredCase("clustered_cube_%d" % n_side, (n_side,) * 3, (0.0, 0.0, 0.0), dx, pos, w,
                           b_over_dx * dx, nsteps, {"cap": cap, "sigma": sigma})
