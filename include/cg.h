@@ -184,6 +184,43 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
                                const double *w_host, double *cells_host, const cg_params *params,
                                cg_report *report, void *stream);
 
+/* ------------------------------------------------------------------------ no allocation */
+
+/* Limits of cg_deposit_fixed_noalloc's static scratch. */
+#define CG_NOALLOC_MAX_FIELDS 8
+#define CG_NOALLOC_MAX_CELL_FIELDS 2097152   /* nfields * ncells, 64-bit accumulators */
+
+/* Fixed-point particle-centroid deposition on a uniform hex mesh that allocates
+ * nothing.  The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run -- for example a solver whose memory
+ * manager (such as a caching allocator) already owns the free device memory, or one
+ * that forbids allocation after start-up because cudaMalloc and cudaFree may
+ * synchronise the device and may fail under memory pressure.  Such callers cannot
+ * use cg_deposit, which grows a mesh-owned workspace on first use.
+ *
+ * It computes exactly what cg_deposit computes with deposit_mode =
+ * CG_DEPOSIT_FIXED_POINT on the mesh cg_create_mesh_structured(nx, ny, nz, origin, dx)
+ * (same locate rule, same scale exponents F, same result bit for bit), without a mesh
+ * object: pos is device [3][n] FP64, w device [nfields][n] FP64, cells_out device
+ * [nfields][nx*ny*nz] FP64, all caller-owned.  fixed_point_bits_host (may be NULL)
+ * receives F per field.
+ *
+ * Scratch: a file-scope static device array of 128 + CG_NOALLOC_MAX_CELL_FIELDS
+ * 64-bit words (about 16 MiB), which every GPU that loads the library holds until the
+ * process exits.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make that first call before any
+ * stream capture.  Every call on a device shares the array and clears the part it
+ * uses; calls whose work overlaps on the GPU race on it, so serialise them.  The call
+ * makes no cudaMalloc, cudaFree or other allocating call; it synchronises `stream`
+ * before returning, like every entry point here.
+ *
+ * Errors: CG_EINVAL (nfields outside [1, CG_NOALLOC_MAX_FIELDS], nfields * ncells >
+ * CG_NOALLOC_MAX_CELL_FIELDS, bad sizes or NULL pointers, non-finite weights),
+ * CG_EDOMAIN (particles outside the mesh; nothing written), CG_ECUDA. */
+cg_status cg_deposit_fixed_noalloc(int nx, int ny, int nz, const double origin[3], double dx,
+                                   int64_t n, const double *pos, int nfields, const double *w,
+                                   double *cells_out, int *fixed_point_bits_host, void *stream);
+
 /* ------------------------------------------------------------------------ diagnostics */
 
 /* Per-kernel device timing (no counterpart in the paper; a measurement aid).  When

@@ -101,6 +101,8 @@ def load_library(path: str | None = None):
         "cg_profile_count": (i32, []),
         "cg_profile_get": (i32, [i32, ctypes.c_char_p, i32, P(ctypes.c_longlong), P(dbl), P(dbl)]),
         "cg_launch_count": (ctypes.c_longlong, []),
+        "cg_deposit_fixed_noalloc": (i32, [i32, i32, i32, P(dbl), dbl, i64, vp, i32, vp, vp,
+                                           P(ctypes.c_int), vp]),
         "cg_launch_count_reset": (None, []),
     }
     for name, (res, args) in sigs.items():
@@ -117,7 +119,8 @@ def exported_symbols():
             "cg_create_mesh_tet", "cg_destroy_mesh", "cg_mesh_num_cells", "cg_mesh_cell_volumes",
             "cg_mesh_tet_operator", "cg_locate", "cg_deposit", "cg_diffuse", "cg_coarse_grain",
             "cg_coarse_grain_host", "cg_profile_enable", "cg_profile_reset", "cg_profile_count",
-            "cg_profile_get", "cg_launch_count", "cg_launch_count_reset"]
+            "cg_profile_get", "cg_launch_count", "cg_launch_count_reset",
+            "cg_deposit_fixed_noalloc"]
 
 
 def _check(status: int, where: str):
@@ -334,3 +337,26 @@ def profile_read() -> dict:
                "cg_profile_get")
         out[name.value.decode()] = {"launches": int(n.value), "ms": ms.value, "bytes": by.value}
     return out
+
+
+NOALLOC_MAX_FIELDS = 8
+NOALLOC_MAX_CELL_FIELDS = 2097152
+
+
+def deposit_fixed_noalloc(dims, origin, dx, pos, w, out=None, stream=None):
+    """Fixed-point deposition that allocates nothing inside the library
+    (cg_deposit_fixed_noalloc); returns (cells [nf, ncells], F per field)."""
+    import torch
+    _dev_f64(pos, "pos")
+    _dev_f64(w, "w")
+    nf, n = w.shape
+    ncells = int(dims[0]) * int(dims[1]) * int(dims[2])
+    if out is None:
+        out = torch.empty((nf, ncells), dtype=torch.float64, device=w.device)
+    bits = (ctypes.c_int * max(nf, 1))()
+    org = (ctypes.c_double * 3)(*[float(o) for o in origin])
+    _check(load_library().cg_deposit_fixed_noalloc(int(dims[0]), int(dims[1]), int(dims[2]), org,
+                                                   float(dx), n, pos.data_ptr(), nf, w.data_ptr(),
+                                                   out.data_ptr(), bits, _stream_handle(stream)),
+           "cg_deposit_fixed_noalloc")
+    return out, list(bits)[:nf]
