@@ -113,12 +113,14 @@ typedef struct {
     int max_rounds;     /* mixed: refinement-round cap per step (default 12) */
     int fused_k;        /* mixed, structured: inner iterations fused per sweep (0 = auto) */
     int reserved0;
-    long long debug_barrier_budget; /* persistent batched kernel: spin budget per grid
-                                       barrier in clock cycles; <= 0 = default */
+    long long barrier_budget; /* > 0: run each structured inner solve as one persistent
+                                 cooperative launch whose grid barriers give up after this
+                                 many clock cycles of waiting (then CG_ETIMEOUT); 0: one
+                                 launch per inner iteration (default) */
 } cg_params;
 
 /* Fills the defaults: bandwidth 0, T 0, nsteps 10, implicit Euler, FP64, ordered
- * deposition, tol 1e-13, max_iter 10000, max_rounds 12, fused_k 0. */
+ * deposition, tol 1e-13, max_iter 10000, max_rounds 12, fused_k 0, barrier_budget 0. */
 void cg_params_default(cg_params *p);
 
 #define CG_REPORT_MAX_FIELDS 8

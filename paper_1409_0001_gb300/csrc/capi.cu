@@ -260,7 +260,7 @@ void cg_params_default(cg_params *p) {
     p->max_iter = 10000;
     p->max_rounds = 12;
     p->fused_k = 0;
-    p->debug_barrier_budget = 0;
+    p->barrier_budget = 0;
 }
 
 cg_status cg_create_mesh_structured(int nx, int ny, int nz, const double origin[3], double dx,

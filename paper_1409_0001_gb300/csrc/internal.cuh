@@ -51,18 +51,20 @@ struct HostBuf {
 enum MeshKind { MESH_STRUCTURED = 0, MESH_TET = 1 };
 
 struct TetDevice {
-    // cell geometry and operator (device)
-    double *vc = nullptr;        // [ncells]
-    int32_t *rowptr = nullptr;   // [ncells+1]
-    int32_t *col = nullptr;      // [nnz]
-    double *val = nullptr;       // [nnz]  entries of L (diagonal included)
-    int64_t nnz = 0;
-    // point location (device)
+    // operator in ELL-4 form (slot s = the face opposite local vertex s); a boundary
+    // face points at the cell itself with a zero transmissibility
+    double *vc = nullptr;        // [ncells] cell volumes V_c
+    double *diagL = nullptr;     // [ncells] L_kk = -sum_f T_f
+    int32_t *offc = nullptr;     // [4][ncells] neighbour across face s
+    double *offv = nullptr;      // [4][ncells] T_f across face s (FP64)
+    float *offv32 = nullptr;     // [4][ncells] the same in FP32
+    double max_rate = 0.0;       // max_k (-L_kk / V_k): explicit Euler needs dtau <= 1/max_rate
+    // point location
     double *xyz = nullptr;       // [nverts][3]
     int32_t *tv = nullptr;       // [ntets][4]
     double *box = nullptr;       // [ntets][6] lo.x lo.y lo.z hi.x hi.y hi.z
     int32_t *bucket_start = nullptr;  // [nbuckets+1]
-    int32_t *bucket_tets = nullptr;   // [..] tet ids, ascending per bucket
+    int32_t *bucket_tets = nullptr;   // tet ids, ascending within a bucket
     int nb[3] = {0, 0, 0};
     double blo[3] = {0, 0, 0};
     double binv[3] = {0, 0, 0};

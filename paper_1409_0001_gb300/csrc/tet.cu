@@ -1,18 +1,908 @@
-// tet.cu -- unstructured tetrahedral meshes (placeholder until the tet path lands).
+// tet.cu -- unstructured tetrahedral meshes: mesh construction (host), point location
+// of particle centroids, and diffusion smoothing with the cell-centred two-point-flux
+// finite-volume operator (the paper's method on unstructured cells, Section 4.3).
+//
+// Operator: (L u)_k = sum over the faces f of cell k shared with cell l of
+// T_f (u_l - u_k), T_f = |S_f|^2 / (S_f . d_f) with S_f the face area vector pointing
+// out of k and d_f = c_l - c_k the vector between the tet centroids (vertex means);
+// boundary faces carry no flux (zero-flux walls, Section 3.2.2).  With M = diag(V_c)
+// an implicit-Euler pseudo-step solves (M - dtau L) u^{n+1} = M u^n, Crank-Nicolson
+// (M - dtau/2 L) u^{n+1} = (M + dtau/2 L) u^n (Section 5.1), explicit Euler
+// u += dtau M^{-1} L u.  The system matrix is symmetric positive definite (an M-matrix
+// when every T_f > 0), so it is solved by Jacobi-preconditioned conjugate gradients:
+// in FP64, or in FP32/BF16 storage inside FP64 iterative refinement.
+//
+// Layout: each cell has at most four face neighbours; they are stored as four
+// structure-of-arrays slots (slot s = the face opposite local vertex s), so a thread
+// per cell reads its neighbour ids and transmissibilities with coalesced loads.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace cgk {
 
-cg_status tet_build(cg_mesh *, int64_t, const double *, int64_t, const int32_t *) {
-    return fail(CG_EINVAL, "tetrahedral meshes are not built yet");
+namespace {
+
+template <class T> cg_status upload(T **dst, const T *src, size_t n) {
+    *dst = nullptr;
+    if (n == 0) return CG_OK;
+    cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *dst = nullptr;
+        cudaGetLastError();
+        return fail(CG_ENOMEM, "cudaMalloc of %zu bytes failed", n * sizeof(T));
+    }
+    CGK_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return CG_OK;
 }
-void tet_release(cg_mesh *) {}
-cg_status tet_locate_launch(cg_mesh *, int64_t, const double *, int, const double *, int32_t *,
-                            uint32_t *, unsigned long long *, cudaStream_t) {
-    return fail(CG_EINVAL, "tetrahedral meshes are not built yet");
+
+inline int grid1d(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)num_sms() * 8;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
-cg_status diffuse_tet_run(cg_mesh *, int, double *, const cg_params *, cg_report *, cudaStream_t) {
-    return fail(CG_EINVAL, "tetrahedral meshes are not built yet");
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// ============================================================================ locate
+// orient(p0,p1,p2,p3) = det[p1-p0; p2-p0; p3-p0], cofactor expansion along the first
+// row in this exact order, every operation explicitly rounded (no contraction).
+__device__ __forceinline__ double orient3(const double *p0, const double *p1, const double *p2,
+                                          const double *p3) {
+    double a0 = __dsub_rn(p1[0], p0[0]), a1 = __dsub_rn(p1[1], p0[1]), a2 = __dsub_rn(p1[2], p0[2]);
+    double b0 = __dsub_rn(p2[0], p0[0]), b1 = __dsub_rn(p2[1], p0[1]), b2 = __dsub_rn(p2[2], p0[2]);
+    double c0 = __dsub_rn(p3[0], p0[0]), c1 = __dsub_rn(p3[1], p0[1]), c2 = __dsub_rn(p3[2], p0[2]);
+    double m0 = __dsub_rn(__dmul_rn(b1, c2), __dmul_rn(b2, c1));
+    double m1 = __dsub_rn(__dmul_rn(b0, c2), __dmul_rn(b2, c0));
+    double m2 = __dsub_rn(__dmul_rn(b0, c1), __dmul_rn(b1, c0));
+    return __dadd_rn(__dsub_rn(__dmul_rn(a0, m0), __dmul_rn(a1, m1)), __dmul_rn(a2, m2));
+}
+
+// Host tet of each particle: the lowest-index tet whose axis-aligned box holds x and
+// whose four barycentric coordinates lambda_j = orient(tet with v_j -> x) / orient(tet)
+// are all >= 0; else the tet (box holding x) with the largest min_j lambda_j, lowest
+// index on ties, if that value is >= -1e-10; else outside (-1).  Candidates come from
+// the bucket of x, which holds every tet whose box overlaps it, in ascending order.
+__global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevice t, int nf,
+                             const double *__restrict__ w, int32_t *__restrict__ cell,
+                             uint32_t *__restrict__ counts, unsigned long long *__restrict__ bad) {
+    unsigned long long n_out = 0, n_nonfinite = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int f = 0; f < nf; ++f)
+            if (!isfinite(w[(int64_t)f * n + i])) ++n_nonfinite;
+        double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+        int32_t found = -1;
+        bool ok = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+        if (ok) {
+            int bi[3];
+            for (int a = 0; a < 3; ++a) {
+                double q = floor(__dmul_rn(__dsub_rn(x[a], t.blo[a]), t.binv[a]));
+                int v = q < 0.0 ? 0 : (q > (double)(t.nb[a] - 1) ? t.nb[a] - 1 : (int)q);
+                bi[a] = v;
+            }
+            int b = (bi[2] * t.nb[1] + bi[1]) * t.nb[0] + bi[0];
+            int32_t best = -1;
+            double best_m = -INFINITY;
+            for (int c = t.bucket_start[b]; c < t.bucket_start[b + 1]; ++c) {
+                int32_t tt = t.bucket_tets[c];
+                const double *bx = t.box + 6 * (size_t)tt;
+                if (!(x[0] >= bx[0] && x[0] <= bx[3] && x[1] >= bx[1] && x[1] <= bx[4] &&
+                      x[2] >= bx[2] && x[2] <= bx[5]))
+                    continue;
+                const double *v0 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 0];
+                const double *v1 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 1];
+                const double *v2 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 2];
+                const double *v3 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 3];
+                double D = orient3(v0, v1, v2, v3);
+                double l0 = __ddiv_rn(orient3(x, v1, v2, v3), D);
+                double l1 = __ddiv_rn(orient3(v0, x, v2, v3), D);
+                double l2 = __ddiv_rn(orient3(v0, v1, x, v3), D);
+                double l3 = __ddiv_rn(orient3(v0, v1, v2, x), D);
+                double m = l0;
+                if (l1 < m) m = l1;
+                if (l2 < m) m = l2;
+                if (l3 < m) m = l3;
+                if (m >= 0.0) {
+                    found = tt;
+                    break;
+                }
+                if (m > best_m) {
+                    best_m = m;
+                    best = tt;
+                }
+            }
+            if (found < 0 && best >= 0 && best_m >= -1e-10) found = best;
+        }
+        cell[i] = found;
+        if (found < 0)
+            ++n_out;
+        else if (counts)
+            atomicAdd(&counts[found], 1u);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_out += __shfl_down_sync(0xffffffffu, n_out, o);
+        n_nonfinite += __shfl_down_sync(0xffffffffu, n_nonfinite, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_out) atomicAdd(&bad[0], n_out);
+        if (n_nonfinite) atomicAdd(&bad[1], n_nonfinite);
+    }
+}
+
+// ============================================================================ solver kernels
+template <class TS> __device__ __forceinline__ float ldf(const TS *p, int64_t i);
+template <> __device__ __forceinline__ float ldf<float>(const float *p, int64_t i) { return p[i]; }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t i) {
+    return __bfloat162float(p[i]);
+}
+template <class TS> __device__ __forceinline__ void stf(TS *p, int64_t i, float v);
+template <> __device__ __forceinline__ void stf<float>(float *p, int64_t i, float v) { p[i] = v; }
+template <> __device__ __forceinline__ void stf<__nv_bfloat16>(__nv_bfloat16 *p, int64_t i, float v) {
+    p[i] = __float2bfloat16_rn(v);
+}
+
+struct Op {          // the operator seen by the kernels
+    int n;
+    const double *vc, *diagL, *offv;
+    const float *offv32;
+    const int32_t *offc;
+    double dte;      // theta * dtau (the coefficient of L in A = M - dte L)
+    double dtau;     // full dtau (for the residual of the first pass)
+};
+
+// (L u)_k with u given by load(l)
+template <class T, class Load>
+__device__ __forceinline__ T lap_row(const Op &o, int k, T uk, Load load) {
+    T s = (T)o.diagL[k] * uk;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const size_t e = (size_t)q * o.n + k;
+        s += (T)o.offv[e] * load(o.offc[e]);
+    }
+    return s;
+}
+
+struct TScal {
+    double rr, bb, rz, alpha, beta, rr0;
+    int done, iters;
+    unsigned int ticket;
+    int breakdown;
+};
+
+// FP64 PCG, initial pass: x = u^n, r = b - A x = dtau L x, b = M x (+ dtau/2 L x for CN),
+// z = r / diag(A), p = z.
+__global__ void k_tcg_init(Op o, int scheme, const double *__restrict__ xall,
+                           double *__restrict__ rall, double *__restrict__ zall,
+                           double *__restrict__ pall, double *__restrict__ partials_all,
+                           TScal *__restrict__ sc, double tol2) {
+    const int f = blockIdx.y;
+    const size_t off = (size_t)f * o.n;
+    const double *x = xall + off;
+    double rr = 0, bb = 0, rz = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        double xk = x[k];
+        double lx = lap_row<double>(o, k, xk, [&](int l) { return x[l]; });
+        double rk = o.dtau * lx;
+        double bk = o.vc[k] * xk;
+        if (scheme == 1) bk += 0.5 * o.dtau * lx;
+        double ad = o.vc[k] - o.dte * o.diagL[k];
+        double zk = rk / ad;
+        rall[off + k] = rk;
+        zall[off + k] = zk;
+        pall[off + k] = zk;
+        rr += rk * rk;
+        bb += bk * bk;
+        rz += rk * zk;
+    }
+    double v[3] = {block_sum(rr), block_sum(bb), block_sum(rz)};
+    double *partials = partials_all + (size_t)f * 3 * gridDim.x;
+    if (arrive(partials, 3, v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
+        double RR = finish_sum(partials, 0, gridDim.x);
+        double BB = finish_sum(partials, 1, gridDim.x);
+        double RZ = finish_sum(partials, 2, gridDim.x);
+        if (is_thread0()) {
+            TScal &S = sc[f];
+            S.rr = RR;
+            S.bb = BB;
+            S.rz = RZ;
+            S.beta = 0;
+            S.iters = 0;
+            S.breakdown = 0;
+            S.done = (RR <= tol2 * BB) ? 1 : 0;
+            S.ticket = 0;
+        }
+    }
+}
+
+// pass 1: p_new = z + beta p (formed on the fly at the neighbours too), q = A p_new,
+// accumulate p_new . q; alpha = rz / (p.q).
+__global__ void k_tcg_pass1(Op o, const double *__restrict__ zall, const double *__restrict__ pin_all,
+                            double *__restrict__ pout_all, double *__restrict__ qall,
+                            double *__restrict__ partials_all, TScal *__restrict__ sc) {
+    const int f = blockIdx.y;
+    if (sc[f].done) return;
+    const double beta = sc[f].beta;
+    const size_t off = (size_t)f * o.n;
+    const double *z = zall + off;
+    const double *pin = pin_all + off;
+    double pq = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        double pk = z[k] + beta * pin[k];
+        double lp = lap_row<double>(o, k, pk, [&](int l) { return z[l] + beta * pin[l]; });
+        double qk = o.vc[k] * pk - o.dte * lp;
+        pout_all[off + k] = pk;
+        qall[off + k] = qk;
+        pq += pk * qk;
+    }
+    double v = block_sum(pq);
+    double *partials = partials_all + (size_t)f * 3 * gridDim.x;
+    if (arrive(partials, 1, &v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
+        double PQ = finish_sum(partials, 0, gridDim.x);
+        if (is_thread0()) {
+            TScal &S = sc[f];
+            if (PQ > 0) {
+                S.alpha = S.rz / PQ;
+            } else {
+                S.alpha = 0;
+                S.breakdown = 1;
+                S.done = 1;
+            }
+            S.ticket = 0;
+        }
+    }
+}
+
+// pass 2: x += alpha p, r -= alpha q, z = r / diag(A); beta = r.z_new / r.z_old.
+__global__ void k_tcg_pass2(Op o, const double *__restrict__ pall, const double *__restrict__ qall,
+                            double *__restrict__ xall, double *__restrict__ rall,
+                            double *__restrict__ zall, double *__restrict__ partials_all,
+                            TScal *__restrict__ sc, double tol2) {
+    const int f = blockIdx.y;
+    if (sc[f].done) return;
+    const double alpha = sc[f].alpha;
+    const size_t off = (size_t)f * o.n;
+    double rr = 0, rz = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        size_t i = off + k;
+        xall[i] += alpha * pall[i];
+        double rk = rall[i] - alpha * qall[i];
+        double zk = rk / (o.vc[k] - o.dte * o.diagL[k]);
+        rall[i] = rk;
+        zall[i] = zk;
+        rr += rk * rk;
+        rz += rk * zk;
+    }
+    double v[2] = {block_sum(rr), block_sum(rz)};
+    double *partials = partials_all + (size_t)f * 3 * gridDim.x;
+    if (arrive(partials, 2, v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
+        double RR = finish_sum(partials, 0, gridDim.x);
+        double RZ = finish_sum(partials, 1, gridDim.x);
+        if (is_thread0()) {
+            TScal &S = sc[f];
+            S.beta = RZ / S.rz;
+            S.rz = RZ;
+            S.rr = RR;
+            S.iters += 1;
+            S.done = (RR <= tol2 * S.bb) ? 1 : 0;
+            S.ticket = 0;
+        }
+    }
+}
+
+// explicit Euler: x_out = x + dtau L x / V_c
+__global__ void k_texplicit(Op o, const double *__restrict__ xin, double *__restrict__ xout) {
+    const size_t off = (size_t)blockIdx.y * o.n;
+    const double *x = xin + off;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        double xk = x[k];
+        double lx = lap_row<double>(o, k, xk, [&](int l) { return x[l]; });
+        xout[off + k] = xk + o.dtau * lx / o.vc[k];
+    }
+}
+
+// ---------------------------------------------------------------- mixed precision
+// One FP64 refinement pass, fused with the initialisation of the next inner solve.
+// kFirst: x = u^n, r = dtau L x, b = M x (CN: + dtau/2 L x, stored in bout).
+// Otherwise x = x_in + d (at the cell and its neighbours), x_out = x, r = b - A x
+// with b = M u^n (IE, from ub) or the stored CN right-hand side (bptr).
+// Then the inner PCG starts from d = 0 (zeroed by the host after this pass):
+// rin = r, z = r / diag(A), p = z.
+template <class TS, bool kFirst>
+__global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
+                          const TS *__restrict__ d_all, const double *__restrict__ ub_all,
+                          const double *__restrict__ bcn_all, double *__restrict__ xout_all,
+                          double *__restrict__ bout_all, TS *__restrict__ rin_all,
+                          TS *__restrict__ z_all, TS *__restrict__ p_all,
+                          double *__restrict__ partials_all, TScal *__restrict__ sc) {
+    const int f = blockIdx.y;
+    const size_t off = (size_t)f * o.n;
+    const double *xin = xin_all + off;
+    const TS *d = kFirst ? nullptr : d_all + off;
+    double rr = 0, bb = 0, rz = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        double rk;
+        if (kFirst) {
+            double xk = xin[k];
+            double lx = lap_row<double>(o, k, xk, [&](int l) { return xin[l]; });
+            rk = o.dtau * lx;
+            double bk = o.vc[k] * xk;
+            if (scheme == 1) {
+                bk += 0.5 * o.dtau * lx;
+                bout_all[off + k] = bk;
+            }
+            bb += bk * bk;
+        } else {
+            double xk = xin[k] + (double)ldf(d, k);
+            double lx = lap_row<double>(o, k, xk, [&](int l) { return xin[l] + (double)ldf(d, l); });
+            double bk = scheme == 1 ? bcn_all[off + k] : o.vc[k] * ub_all[off + k];
+            rk = bk - (o.vc[k] * xk - o.dte * lx);
+            xout_all[off + k] = xk;
+        }
+        float rf = (float)rk;
+        float zf = rf / (float)(o.vc[k] - o.dte * o.diagL[k]);
+        stf(rin_all, off + k, rf);
+        stf(z_all, off + k, zf);
+        stf(p_all, off + k, zf);
+        rr += rk * rk;
+        rz += (double)rf * (double)zf;
+    }
+    double v[3] = {block_sum(rr), block_sum(rz), kFirst ? block_sum(bb) : 0.0};
+    double *partials = partials_all + (size_t)f * 3 * gridDim.x;
+    if (arrive(partials, kFirst ? 3 : 2, v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
+        double RR = finish_sum(partials, 0, gridDim.x);
+        double RZ = finish_sum(partials, 1, gridDim.x);
+        double BB = kFirst ? finish_sum(partials, 2, gridDim.x) : 0.0;
+        if (is_thread0()) {
+            TScal &S = sc[f];
+            S.rr = RR;       // the FP64 residual of the outer iteration
+            S.rr0 = RR;      // reference for the inner stopping test
+            S.rz = RZ;
+            S.beta = 0;
+            S.iters = 0;
+            S.breakdown = 0;
+            if (kFirst) S.bb = BB;
+            S.done = 0;
+            S.ticket = 0;
+        }
+    }
+}
+
+// inner PCG pass 1 (FP32 arithmetic, TS storage): p_new = z + beta p, q = A p_new
+template <class TS>
+__global__ void k_tin_pass1(Op o, const TS *__restrict__ z_all, const TS *__restrict__ pin_all,
+                            TS *__restrict__ pout_all, TS *__restrict__ q_all,
+                            double *__restrict__ partials_all, TScal *__restrict__ sc) {
+    const int f = blockIdx.y;
+    if (sc[f].done) return;
+    const float beta = (float)sc[f].beta;
+    const float dte = (float)o.dte;
+    const size_t off = (size_t)f * o.n;
+    const TS *z = z_all + off;
+    const TS *pin = pin_all + off;
+    double pq = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        float pk = ldf(z, k) + beta * ldf(pin, k);
+        float lp = (float)o.diagL[k] * pk;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const size_t e = (size_t)q * o.n + k;
+            const int l = o.offc[e];
+            lp += o.offv32[e] * (ldf(z, l) + beta * ldf(pin, l));
+        }
+        float qk = (float)o.vc[k] * pk - dte * lp;
+        stf(pout_all, off + k, pk);
+        stf(q_all, off + k, qk);
+        pq += (double)(pk * qk);
+    }
+    double v = block_sum(pq);
+    double *partials = partials_all + (size_t)f * 3 * gridDim.x;
+    if (arrive(partials, 1, &v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
+        double PQ = finish_sum(partials, 0, gridDim.x);
+        if (is_thread0()) {
+            TScal &S = sc[f];
+            if (PQ > 0) {
+                S.alpha = S.rz / PQ;
+            } else {
+                S.alpha = 0;
+                S.breakdown = 1;
+                S.done = 1;
+            }
+            S.ticket = 0;
+        }
+    }
+}
+
+// inner PCG pass 2: d += alpha p, rin -= alpha q, z = rin / diag(A); stop when
+// ||rin|| <= eps_in * ||r||
+template <class TS>
+__global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__restrict__ q_all,
+                            TS *__restrict__ d_all, TS *__restrict__ rin_all, TS *__restrict__ z_all,
+                            double *__restrict__ partials_all, TScal *__restrict__ sc,
+                            double eps2) {
+    const int f = blockIdx.y;
+    if (sc[f].done) return;
+    const float alpha = (float)sc[f].alpha;
+    const size_t off = (size_t)f * o.n;
+    double rr = 0, rz = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        size_t i = off + k;
+        float pk = ldf(p_all, i);
+        stf(d_all, i, ldf(d_all, i) + alpha * pk);
+        float rk = ldf(rin_all, i) - alpha * ldf(q_all, i);
+        float zk = rk / (float)(o.vc[k] - o.dte * o.diagL[k]);
+        stf(rin_all, i, rk);
+        stf(z_all, i, zk);
+        rr += (double)(rk * rk);
+        rz += (double)(rk * zk);
+    }
+    double v[2] = {block_sum(rr), block_sum(rz)};
+    double *partials = partials_all + (size_t)f * 3 * gridDim.x;
+    if (arrive(partials, 2, v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
+        double RR = finish_sum(partials, 0, gridDim.x);
+        double RZ = finish_sum(partials, 1, gridDim.x);
+        if (is_thread0()) {
+            TScal &S = sc[f];
+            S.beta = RZ / S.rz;
+            S.rz = RZ;
+            S.iters += 1;
+            S.done = (RR <= eps2 * S.rr0) ? 1 : 0;
+            S.ticket = 0;
+        }
+    }
+}
+
+}  // namespace
+
+// ============================================================================ host: build
+void tet_release(cg_mesh *m) {
+    TetDevice &t = m->tet;
+    void *ptrs[] = {t.vc, t.diagL, t.offc, t.offv, t.offv32, t.xyz, t.tv, t.box, t.bucket_start,
+                    t.bucket_tets};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    t = TetDevice();
+}
+
+cg_status tet_build(cg_mesh *m, int64_t nv, const double *xyz, int64_t nt, const int32_t *tv) {
+    for (int64_t i = 0; i < 4 * nt; ++i)
+        if (tv[i] < 0 || tv[i] >= nv)
+            return fail(CG_EINVAL, "cg_create_mesh_tet: vertex id %d out of range", tv[i]);
+    // centroids (vertex means) and volumes |det| / 6
+    std::vector<double> cent(3 * (size_t)nt), vc((size_t)nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        const double *p[4];
+        for (int j = 0; j < 4; ++j) p[j] = xyz + 3 * (size_t)tv[4 * t + j];
+        for (int a = 0; a < 3; ++a) {
+            volatile double s = p[0][a] + p[1][a];
+            s = s + p[2][a];
+            s = s + p[3][a];
+            cent[3 * t + a] = s * 0.25;
+        }
+        double e[3][3];
+        for (int j = 0; j < 3; ++j)
+            for (int a = 0; a < 3; ++a) e[j][a] = p[j + 1][a] - p[0][a];
+        double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                     e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        vc[t] = std::fabs(det) / 6.0;
+        if (!(vc[t] > 0.0)) return fail(CG_EINVAL, "cg_create_mesh_tet: tet %lld has zero volume", (long long)t);
+    }
+    // faces: bucket the 4 nt faces by their smallest vertex id, then match inside a bucket
+    struct Face { int32_t b, c, tet, slot; };
+    std::vector<int64_t> start((size_t)nv + 1, 0);
+    auto face_verts = [&](int64_t t, int j, int32_t *v) {
+        int q = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != j) v[q++] = tv[4 * t + i];
+        std::sort(v, v + 3);
+    };
+    for (int64_t t = 0; t < nt; ++t)
+        for (int j = 0; j < 4; ++j) {
+            int32_t v[3];
+            face_verts(t, j, v);
+            start[(size_t)v[0] + 1]++;
+        }
+    for (int64_t i = 0; i < nv; ++i) start[i + 1] += start[i];
+    std::vector<Face> faces((size_t)(4 * nt));
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int j = 0; j < 4; ++j) {
+            int32_t v[3];
+            face_verts(t, j, v);
+            faces[(size_t)fill[v[0]]++] = Face{v[1], v[2], (int32_t)t, j};
+        }
+    std::vector<int32_t> offc(4 * (size_t)nt);
+    std::vector<double> offv(4 * (size_t)nt, 0.0), diag((size_t)nt, 0.0);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int j = 0; j < 4; ++j) offc[(size_t)j * nt + t] = (int32_t)t;
+    for (int64_t a = 0; a < nv; ++a) {
+        Face *f0 = faces.data() + start[a], *f1 = faces.data() + start[a + 1];
+        std::sort(f0, f1, [](const Face &x, const Face &y) {
+            return x.b != y.b ? x.b < y.b : (x.c != y.c ? x.c < y.c : x.tet < y.tet);
+        });
+        for (Face *f = f0; f < f1;) {
+            Face *g = f + 1;
+            while (g < f1 && g->b == f->b && g->c == f->c) ++g;
+            if (g - f > 2)
+                return fail(CG_EINVAL, "cg_create_mesh_tet: a face is shared by more than two tets");
+            if (g - f == 2) {
+                const int32_t k = f[0].tet, l = f[1].tet;
+                const double *A = xyz + 3 * (size_t)a, *B = xyz + 3 * (size_t)f->b,
+                             *C = xyz + 3 * (size_t)f->c;
+                double ab[3], ac[3], S[3], d[3];
+                for (int q = 0; q < 3; ++q) {
+                    ab[q] = B[q] - A[q];
+                    ac[q] = C[q] - A[q];
+                }
+                S[0] = 0.5 * (ab[1] * ac[2] - ab[2] * ac[1]);
+                S[1] = 0.5 * (ab[2] * ac[0] - ab[0] * ac[2]);
+                S[2] = 0.5 * (ab[0] * ac[1] - ab[1] * ac[0]);
+                double out = 0.0;   // S . (face centroid - c_k) > 0 for S pointing out of k
+                for (int q = 0; q < 3; ++q)
+                    out += S[q] * ((A[q] + B[q] + C[q]) / 3.0 - cent[3 * (size_t)k + q]);
+                if (out < 0.0)
+                    for (int q = 0; q < 3; ++q) S[q] = -S[q];
+                double ss = 0.0, sd = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                    d[q] = cent[3 * (size_t)l + q] - cent[3 * (size_t)k + q];
+                    ss += S[q] * S[q];
+                    sd += S[q] * d[q];
+                }
+                double T = ss / sd;
+                if (!(T > 0.0) || !std::isfinite(T))
+                    return fail(CG_EINVAL, "cg_create_mesh_tet: non-positive transmissibility "
+                                           "between tets %d and %d", k, l);
+                offc[(size_t)f[0].slot * nt + k] = l;
+                offv[(size_t)f[0].slot * nt + k] = T;
+                offc[(size_t)f[1].slot * nt + l] = k;
+                offv[(size_t)f[1].slot * nt + l] = T;
+                diag[k] -= T;
+                diag[l] -= T;
+            }
+            f = g;
+        }
+    }
+    faces.clear();
+    faces.shrink_to_fit();
+    // host CSR (diagonal included, ascending columns) for cg_mesh_tet_operator
+    m->h_rowptr.assign((size_t)nt + 1, 0);
+    m->h_col.clear();
+    m->h_val.clear();
+    m->h_col.reserve(5 * (size_t)nt);
+    m->h_val.reserve(5 * (size_t)nt);
+    double max_rate = 0.0;
+    for (int64_t t = 0; t < nt; ++t) {
+        std::pair<int32_t, double> e[5];
+        int q = 0;
+        e[q++] = {(int32_t)t, diag[t]};
+        for (int j = 0; j < 4; ++j)
+            if (offc[(size_t)j * nt + t] != t) e[q++] = {offc[(size_t)j * nt + t], offv[(size_t)j * nt + t]};
+        std::sort(e, e + q);
+        for (int i = 0; i < q; ++i) {
+            m->h_col.push_back(e[i].first);
+            m->h_val.push_back(e[i].second);
+        }
+        m->h_rowptr[t + 1] = (int32_t)m->h_col.size();
+        max_rate = std::max(max_rate, -diag[t] / vc[t]);
+    }
+    m->h_vc = vc;
+    // point-location buckets: a uniform grid over the vertex bounding box, cell size
+    // about the edge of the average hex (6 tets), each tet listed in every bucket its
+    // bounding box overlaps
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], xyz[3 * i + a]);
+            hi[a] = std::max(hi[a], xyz[3 * i + a]);
+        }
+    TetDevice &td = m->tet;
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) vol *= std::max(hi[a] - lo[a], 1e-300);
+    double h = std::cbrt(6.0 * vol / (double)nt);
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+        double ext = std::max(hi[a] - lo[a], 1e-300);
+        int nba = (int)std::ceil(ext / h);
+        nba = std::max(1, std::min(nba, 1024));
+        td.nb[a] = nba;
+        td.blo[a] = lo[a];
+        td.binv[a] = (double)nba / ext;
+        total *= nba;
+    }
+    std::vector<double> box(6 * (size_t)nt);
+    std::vector<int32_t> bstart((size_t)total + 1, 0);
+    auto bucket_range = [&](int64_t t, int *b0, int *b1) {
+        for (int a = 0; a < 3; ++a) {
+            double mn = xyz[3 * (size_t)tv[4 * t] + a], mx = mn;
+            for (int j = 1; j < 4; ++j) {
+                double c = xyz[3 * (size_t)tv[4 * t + j] + a];
+                mn = std::min(mn, c);
+                mx = std::max(mx, c);
+            }
+            box[6 * t + a] = mn;
+            box[6 * t + 3 + a] = mx;
+            volatile double qa = (mn - td.blo[a]);
+            volatile double qb = (mx - td.blo[a]);
+            double fa = std::floor(qa * td.binv[a]), fb = std::floor(qb * td.binv[a]);
+            b0[a] = fa < 0 ? 0 : (fa > td.nb[a] - 1 ? td.nb[a] - 1 : (int)fa);
+            b1[a] = fb < 0 ? 0 : (fb > td.nb[a] - 1 ? td.nb[a] - 1 : (int)fb);
+        }
+    };
+    for (int64_t t = 0; t < nt; ++t) {
+        int b0[3], b1[3];
+        bucket_range(t, b0, b1);
+        for (int z = b0[2]; z <= b1[2]; ++z)
+            for (int y = b0[1]; y <= b1[1]; ++y)
+                for (int x = b0[0]; x <= b1[0]; ++x) bstart[((size_t)z * td.nb[1] + y) * td.nb[0] + x + 1]++;
+    }
+    for (int64_t i = 0; i < total; ++i) bstart[i + 1] += bstart[i];
+    std::vector<int32_t> btets((size_t)bstart[total]);
+    std::vector<int32_t> bfill(bstart.begin(), bstart.end() - 1);
+    for (int64_t t = 0; t < nt; ++t) {
+        int b0[3], b1[3];
+        bucket_range(t, b0, b1);
+        for (int z = b0[2]; z <= b1[2]; ++z)
+            for (int y = b0[1]; y <= b1[1]; ++y)
+                for (int x = b0[0]; x <= b1[0]; ++x)
+                    btets[(size_t)bfill[((size_t)z * td.nb[1] + y) * td.nb[0] + x]++] = (int32_t)t;
+    }
+    std::vector<float> offv32(offv.size());
+    for (size_t i = 0; i < offv.size(); ++i) offv32[i] = (float)offv[i];
+    td.max_rate = max_rate;
+    CGK_TRY(upload(&td.vc, vc.data(), vc.size()));
+    CGK_TRY(upload(&td.diagL, diag.data(), diag.size()));
+    CGK_TRY(upload(&td.offc, offc.data(), offc.size()));
+    CGK_TRY(upload(&td.offv, offv.data(), offv.size()));
+    CGK_TRY(upload(&td.offv32, offv32.data(), offv32.size()));
+    CGK_TRY(upload(&td.xyz, xyz, 3 * (size_t)nv));
+    CGK_TRY(upload(&td.tv, tv, 4 * (size_t)nt));
+    CGK_TRY(upload(&td.box, box.data(), box.size()));
+    CGK_TRY(upload(&td.bucket_start, bstart.data(), bstart.size()));
+    CGK_TRY(upload(&td.bucket_tets, btets.data(), btets.size()));
+    return CG_OK;
+}
+
+cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                            int32_t *cell_out, uint32_t *counts, unsigned long long *bad,
+                            cudaStream_t st) {
+    CGK_LAUNCH("tet_locate", (double)n * (24 + 8 * nf + 4), st,
+               k_tet_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
+                                                            counts, bad));
+    CGK_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+// ============================================================================ host: diffuse
+static Op make_op(cg_mesh *m, double dte, double dtau) {
+    Op o;
+    o.n = (int)m->ncells;
+    o.vc = m->tet.vc;
+    o.diagL = m->tet.diagL;
+    o.offv = m->tet.offv;
+    o.offv32 = m->tet.offv32;
+    o.offc = m->tet.offc;
+    o.dte = dte;
+    o.dtau = dtau;
+    return o;
+}
+
+// bytes of one operator row: 4 ids + 4 T + diag + V_c, plus the gathered values
+static double row_bytes(int s) { return 4 * 4 + 4 * (s == 4 ? 4 : 8) + 16; }
+
+static cg_status tet_fp64(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
+                          cg_report *rep, cudaStream_t st) {
+    const int n = (int)m->ncells;
+    const double dtau = T / p->nsteps;
+    const Op o = make_op(m, p->scheme == CG_SCHEME_CRANK_NICOLSON ? 0.5 * dtau : dtau, dtau);
+    const double tol2 = p->tol * p->tol;
+    const int G = grid1d(n);
+    const dim3 grid(G, nf);
+    const size_t vec = align_up((size_t)n * nf * 8);
+    CGK_TRY(m->ws_diffuse.ensure(5 * vec));
+    char *wb = m->ws_diffuse.as<char>();
+    double *r = (double *)wb, *z = (double *)(wb + vec), *q = (double *)(wb + 2 * vec);
+    double *P[2] = {(double *)(wb + 3 * vec), (double *)(wb + 4 * vec)};
+    CGK_TRY(m->ws_small.ensure(4096 + align_up((size_t)nf * 3 * G * 8) + 64 * sizeof(TScal)));
+    double *partials = (double *)(m->ws_small.as<char>() + 4096);
+    TScal *sc = (TScal *)(m->ws_small.as<char>() + 4096 + align_up((size_t)nf * 3 * G * 8));
+    CGK_CUDA(cudaMemsetAsync(sc, 0, nf * sizeof(TScal), st));
+    CGK_TRY(m->h_small.ensure(4096 + 64 * sizeof(TScal)));
+    TScal *hsc = (TScal *)(m->h_small.as<char>() + 4096);
+    long long total = 0;
+    double worst = 0;
+    const double rb = row_bytes(8);
+    for (int s = 0; s < p->nsteps; ++s) {
+        CGK_LAUNCH("tcg64_init", (double)n * nf * (rb + 8 + 24), st,
+                   k_tcg_init<<<grid, kThreads, 0, st>>>(o, p->scheme, cells, r, z, P[0], partials,
+                                                         sc, tol2));
+        int it = 0;
+        bool all_done = false;
+        while (true) {
+            for (int c = 0; c < 8; ++c, ++it) {
+                CGK_LAUNCH("tcg64_pass1", (double)n * nf * (rb + 16 + 16), st,
+                           k_tcg_pass1<<<grid, kThreads, 0, st>>>(o, z, P[it & 1], P[(it + 1) & 1],
+                                                                  q, partials, sc));
+                CGK_LAUNCH("tcg64_pass2", (double)n * nf * (16 + 40 + 16), st,
+                           k_tcg_pass2<<<grid, kThreads, 0, st>>>(o, P[(it + 1) & 1], q, cells, r,
+                                                                  z, partials, sc, tol2));
+            }
+            CGK_CUDA(cudaGetLastError());
+            CGK_CUDA(cudaMemcpyAsync(hsc, sc, nf * sizeof(TScal), cudaMemcpyDeviceToHost, st));
+            CGK_CUDA(cudaStreamSynchronize(st));
+            all_done = true;
+            for (int f = 0; f < nf; ++f) all_done = all_done && hsc[f].done;
+            if (all_done || it >= p->max_iter) break;
+        }
+        for (int f = 0; f < nf; ++f) {
+            total += hsc[f].iters + 1;
+            double rel = hsc[f].bb > 0 ? std::sqrt(hsc[f].rr / hsc[f].bb) : 0.0;
+            worst = std::max(worst, rel);
+            if (hsc[f].breakdown && hsc[f].rr > tol2 * hsc[f].bb) all_done = false;
+        }
+        if (!all_done) {
+            if (rep) {
+                rep->iters = total;
+                rep->cell_updates = total * (long long)n;
+                rep->final_rel_residual = worst;
+            }
+            return fail(CG_ENOCONV, "cg_diffuse: FP64 PCG did not reach tol in step %d", s);
+        }
+    }
+    if (rep) {
+        rep->iters = total;
+        rep->cell_updates = total * (long long)n;
+        rep->final_rel_residual = worst;
+    }
+    return CG_OK;
+}
+
+static cg_status tet_explicit(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
+                              cg_report *rep, cudaStream_t st) {
+    const int n = (int)m->ncells;
+    const double dtau = T / p->nsteps;
+    if (dtau * m->tet.max_rate > 1.0 + 1e-12)
+        return fail(CG_EINVAL, "cg_diffuse: explicit Euler needs dtau <= %g on this mesh",
+                    1.0 / m->tet.max_rate);
+    const Op o = make_op(m, dtau, dtau);
+    const size_t vec = align_up((size_t)n * nf * 8);
+    CGK_TRY(m->ws_diffuse.ensure(vec));
+    double *a = cells, *b = m->ws_diffuse.as<double>();
+    for (int s = 0; s < p->nsteps; ++s) {
+        CGK_LAUNCH("texplicit64", (double)n * nf * (row_bytes(8) + 16), st,
+                   k_texplicit<<<dim3(grid1d(n), nf), kThreads, 0, st>>>(o, a, b));
+        std::swap(a, b);
+    }
+    CGK_CUDA(cudaGetLastError());
+    if (a != cells)
+        CGK_CUDA(cudaMemcpyAsync(cells, a, (size_t)n * nf * 8, cudaMemcpyDeviceToDevice, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    if (rep) {
+        rep->iters = (long long)p->nsteps * nf;
+        rep->cell_updates = rep->iters * n;
+    }
+    return CG_OK;
+}
+
+template <class TS>
+static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
+                           cg_report *rep, cudaStream_t st) {
+    const int n = (int)m->ncells;
+    const bool cn = p->scheme == CG_SCHEME_CRANK_NICOLSON;
+    const double dtau = T / p->nsteps;
+    const Op o = make_op(m, cn ? 0.5 * dtau : dtau, dtau);
+    const double tol2 = p->tol * p->tol;
+    const double eps_in = sizeof(TS) == 2 ? 3e-3 : 1e-6;
+    const int G = grid1d(n);
+    const dim3 grid(G, nf);
+    const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
+    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts));
+    char *wb = m->ws_diffuse.as<char>();
+    double *X1 = (double *)wb, *X2 = (double *)(wb + v64), *B = (double *)(wb + 2 * v64);
+    TS *Rin = (TS *)(wb + 3 * v64), *Z = (TS *)(wb + 3 * v64 + vts), *Q = (TS *)(wb + 3 * v64 + 2 * vts);
+    TS *Pp[2] = {(TS *)(wb + 3 * v64 + 3 * vts), (TS *)(wb + 3 * v64 + 4 * vts)};
+    TS *D = (TS *)(wb + 3 * v64 + 5 * vts);
+    CGK_TRY(m->ws_small.ensure(4096 + align_up((size_t)nf * 3 * G * 8) + 64 * sizeof(TScal)));
+    double *partials = (double *)(m->ws_small.as<char>() + 4096);
+    TScal *sc = (TScal *)(m->ws_small.as<char>() + 4096 + align_up((size_t)nf * 3 * G * 8));
+    CGK_CUDA(cudaMemsetAsync(sc, 0, nf * sizeof(TScal), st));
+    CGK_TRY(m->h_small.ensure(4096 + 64 * sizeof(TScal)));
+    TScal *hsc = (TScal *)(m->h_small.as<char>() + 4096);
+    const int max_rounds = p->max_rounds > 0 ? p->max_rounds : 12;
+    const int max_inner = p->max_iter;
+    const double rb32 = row_bytes(4);
+    long long applications = 0, rounds_total = 0;
+    double worst = 0;
+    double *ubuf = cells, *F1 = X1, *F2 = X2;
+    bool converged = true;
+    int s = 0;
+    for (; s < p->nsteps; ++s) {
+        CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 4 * sizeof(TS)), st,
+                   (k_trefine<TS, true><<<grid, kThreads, 0, st>>>(
+                       o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin, Z, Pp[0],
+                       partials, sc)));
+        CGK_CUDA(cudaMemsetAsync(D, 0, (size_t)n * nf * sizeof(TS), st));
+        applications += 1;
+        double *xcur = ubuf;
+        int rounds = 0;
+        converged = false;
+        while (rounds < max_rounds) {
+            // inner Jacobi-PCG on A d = r in FP32 (TS storage), from d = 0
+            int it = 0;
+            bool inner_done = false;
+            while (!inner_done && it < max_inner) {
+                for (int c = 0; c < 8; ++c, ++it) {
+                    CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass1_bf16" : "tin_pass1_fp32",
+                               (double)n * nf * (rb32 + 4.0 * sizeof(TS)), st,
+                               k_tin_pass1<TS><<<grid, kThreads, 0, st>>>(
+                                   o, Z, Pp[it & 1], Pp[(it + 1) & 1], Q, partials, sc));
+                    CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass2_bf16" : "tin_pass2_fp32",
+                               (double)n * nf * (16 + 7.0 * sizeof(TS)), st,
+                               k_tin_pass2<TS><<<grid, kThreads, 0, st>>>(
+                                   o, Pp[(it + 1) & 1], Q, D, Rin, Z, partials, sc, eps_in * eps_in));
+                }
+                CGK_CUDA(cudaGetLastError());
+                CGK_CUDA(cudaMemcpyAsync(hsc, sc, nf * sizeof(TScal), cudaMemcpyDeviceToHost, st));
+                CGK_CUDA(cudaStreamSynchronize(st));
+                inner_done = true;
+                for (int f = 0; f < nf; ++f) inner_done = inner_done && hsc[f].done;
+            }
+            int used = 0;
+            for (int f = 0; f < nf; ++f) used = std::max(used, hsc[f].iters);
+            applications += used;
+            // x += d, new FP64 residual, start of the next inner solve
+            double *xnext = (xcur == F1) ? F2 : F1;
+            CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) * 5 + 16), st,
+                       (k_trefine<TS, false><<<grid, kThreads, 0, st>>>(
+                           o, p->scheme, xcur, D, ubuf, B, xnext, nullptr, Rin, Z, Pp[0], partials,
+                           sc)));
+            CGK_CUDA(cudaGetLastError());
+            CGK_CUDA(cudaMemsetAsync(D, 0, (size_t)n * nf * sizeof(TS), st));
+            applications += 1;
+            ++rounds;
+            xcur = xnext;
+            CGK_CUDA(cudaMemcpyAsync(hsc, sc, nf * sizeof(TScal), cudaMemcpyDeviceToHost, st));
+            CGK_CUDA(cudaStreamSynchronize(st));
+            converged = true;
+            for (int f = 0; f < nf; ++f) converged = converged && (hsc[f].rr <= tol2 * hsc[f].bb);
+            if (converged) break;
+        }
+        rounds_total += rounds;
+        for (int f = 0; f < nf; ++f)
+            worst = std::max(worst, hsc[f].bb > 0 ? std::sqrt(hsc[f].rr / hsc[f].bb) : 0.0);
+        double *old_u = ubuf, *other = (xcur == F1) ? F2 : F1;
+        ubuf = xcur;
+        F1 = old_u;
+        F2 = other;
+        if (!converged) break;
+    }
+    if (ubuf != cells)
+        CGK_CUDA(cudaMemcpyAsync(cells, ubuf, (size_t)n * nf * 8, cudaMemcpyDeviceToDevice, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    if (rep) {
+        rep->iters = applications * nf;
+        rep->refine_rounds = rounds_total;
+        rep->cell_updates = applications * nf * (long long)n;
+        rep->final_rel_residual = worst;
+    }
+    if (!converged)
+        return fail(CG_ENOCONV, "cg_diffuse: refinement did not reach tol in step %d", s);
+    return CG_OK;
+}
+
+cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p, cg_report *rep,
+                          cudaStream_t st) {
+    double T = p->bandwidth > 0.0 ? p->bandwidth * p->bandwidth / 4.0 : p->T;
+    if (p->scheme == CG_SCHEME_EXPLICIT_EULER) return tet_explicit(m, nf, cells, p, T, rep, st);
+    if (p->precision == CG_PREC_FP64) return tet_fp64(m, nf, cells, p, T, rep, st);
+    if (p->precision == CG_PREC_FP32_REFINE) return tet_mixed<float>(m, nf, cells, p, T, rep, st);
+    return tet_mixed<__nv_bfloat16>(m, nf, cells, p, T, rep, st);
 }
 
 }  // namespace cgk

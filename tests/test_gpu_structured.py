@@ -228,3 +228,25 @@ def test_coarse_grain_clustered_128_full_size(cg, orc, precision):
                                report=True)
     assert maxrel(got.cpu().numpy(), ref) <= (FP64_TOL if precision == 0 else MIXED_TOL)
     assert abs(rep["mass_out"][0] - rep["mass_in"][0]) <= 1e-12 * rep["mass_in"][0]
+
+
+def test_barrier_timeout_reports_etimeout_and_context_survives(cg):
+    """The persistent inner solve's grid barrier has a bounded wait: with a budget of
+    one clock cycle it gives up, every block leaves, and the call returns CG_ETIMEOUT.
+    The next call on the same mesh works."""
+    dims = (40, 40, 40)
+    rng = np.random.default_rng(13)
+    u0 = rng.random((1, 40 ** 3))
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), 0.025)
+    u = dev(u0)
+    with pytest.raises(cg.CGError) as e:
+        cg.diffuse(mesh, u, cg.Params(bandwidth=0.2, nsteps=2, precision=1,
+                                      barrier_budget=1))
+    assert e.value.code == "CG_ETIMEOUT"
+    # the same mesh afterwards: persistent (ample budget) and per-launch inner solves agree
+    outs = []
+    for budget in (2_000_000_000, 0):
+        u = dev(u0)
+        cg.diffuse(mesh, u, cg.Params(bandwidth=0.2, nsteps=2, precision=1, barrier_budget=budget))
+        outs.append(bits(u.cpu().numpy()))
+    assert np.array_equal(outs[0], outs[1])
