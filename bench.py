@@ -4,8 +4,10 @@
 One step = the whole method (locate + ordered deposition + implicit-Euler diffusion
 to T = b^2/4, 10 pseudo-steps) on the 128^3 clustered unit-cube workload
 (2,000,000 spheres of d = 0.004 in 20 Gaussian clusters), once for each bandwidth
-b/dx in {1, 2, 4, 8}, in the mixed path (FP32 Chebyshev inner solves with FP64
-iterative refinement to ||r|| <= 1e-13 ||b|| per pseudo-step).
+b/dx in {1, 2, 4, 8}, in the mixed path (FP32 Chebyshev inner solves with
+double-float iterative refinement to ||r|| <= 1e-13 ||b|| per pseudo-step).  The
+other precision modes (FP64 CG, FP32 + IEEE-FP64 refinement, BF16 + double-float
+refinement) are timed on the same workload and reported beside it.
 
 Metric: diffusion cell-updates/s (one cell-update = one application of the implicit
 operator at one cell for one field), whole job over all ranks.  The same line carries
@@ -245,9 +247,10 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
+    MAIN = cg.PREC_FP32_DF_REFINE
     # ---------------- warm-up
     for _ in range(a.warmup):
-        one_step(cg.PREC_FP32_REFINE, [])
+        one_step(MAIN, [])
     barrier()
 
     # ---------------- timed region (clean: no per-kernel events)
@@ -257,7 +260,7 @@ def main():
     lib.cg_launch_count_reset()
     reps = []
     barrier()
-    ms = timed(lambda: one_step(cg.PREC_FP32_REFINE, reps), a.steps)
+    ms = timed(lambda: one_step(MAIN, reps), a.steps)
     barrier()
     launches = int(lib.cg_launch_count())
     clocks = sampler.stop()
@@ -274,20 +277,33 @@ def main():
     cg.profile_reset()
     cg.profile_enable(True)
     prof_reps = []
-    ms_prof = timed(lambda: one_step(cg.PREC_FP32_REFINE, prof_reps), a.steps)
+    ms_prof = timed(lambda: one_step(MAIN, prof_reps), a.steps)
     cg.profile_enable(False)
     kern = cg.profile_read()
 
-    # ---------------- FP64 GPU path, same workload
-    fp64_reps = []
-    ms64 = timed(lambda: one_step(cg.PREC_FP64, fp64_reps), max(a.fp64_steps, 1))
-    ms64 = max_over_ranks(ms64) / max(a.fp64_steps, 1)
-    one_step(cg.PREC_FP32_REFINE, [])
-    mixed_out = [o.clone() for o in outs]
-    one_step(cg.PREC_FP64, [])
-    fp64_out = [o.clone() for o in outs]
-    mixed_vs_fp64 = max(float((m - f).abs().max() / f.abs().max())
-                        for m, f in zip(mixed_out, fp64_out))
+    # ---------------- the other precision modes, same workload
+    main_out = [o.clone() for o in outs]
+    modes = {}
+    mode_out = {}
+    for name, prec in (("fp64_cg", cg.PREC_FP64), ("fp32_fp64refine", cg.PREC_FP32_REFINE),
+                       ("bf16_dfrefine", cg.PREC_BF16_DF_REFINE)):
+        one_step(prec, [])                      # warm the mode
+        mreps = []
+        msm = timed(lambda: one_step(prec, mreps), max(a.fp64_steps, 1)) / max(a.fp64_steps, 1)
+        msm = max_over_ranks(msm)
+        mode_out[name] = [o.clone() for o in outs]
+        modes[name] = {"ms_per_step": msm,
+                       "cell_updates_per_s": sum(r["cell_updates"] for r in mreps)
+                       / max(a.fp64_steps, 1) / (msm * 1e-3),
+                       "cell_pseudo_steps_per_s": len(B_OVER_DX) * NSTEPS * c.ncells / (msm * 1e-3)}
+    fp64_out = mode_out["fp64_cg"]
+    for name in modes:
+        modes[name]["maxrel_vs_fp64_gpu"] = max(float((m - f).abs().max() / f.abs().max())
+                                                for m, f in zip(mode_out[name], fp64_out))
+    modes["fp32_dfrefine"] = {"ms_per_step": ms / a.steps,
+                              "maxrel_vs_fp64_gpu": max(float((m - f).abs().max() / f.abs().max())
+                                                        for m, f in zip(main_out, fp64_out))}
+    outs = main_out
 
     # ---------------- end to end through the host-pointer entry point
     pos_h = torch.from_numpy(c.pos).pin_memory()
@@ -296,7 +312,7 @@ def main():
 
     def e2e_step(reps_e):
         for i, bdx in enumerate(B_OVER_DX):
-            _, r = cg.coarse_grain_host(mesh, pos_h, w_h, params(bdx, cg.PREC_FP32_REFINE),
+            _, r = cg.coarse_grain_host(mesh, pos_h, w_h, params(bdx, MAIN),
                                         out=out_h[i], report=True)
             reps_e.append(r)
 
@@ -337,8 +353,10 @@ def main():
             "metric": "diffusion cell-updates/s", "value": value, "unit": "cell-updates/s",
             "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "precision": "fp32 Chebyshev + fp64 refinement",
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a),
+                       "precision": "fp32 Chebyshev inner solves + double-float (fp32 hi/lo) "
+                                    "refinement of the implicit-step residual",
                        "l2": "flushed before every step (256 MB write, outside the timed events)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": {"value": e2e_updates / e2e_s, "unit": "cell-updates/s",
@@ -354,10 +372,8 @@ def main():
             "refine_rounds_per_solve": rounds,
             "worst_rel_residual": worst_res,
             "worst_rel_mass_error": mass_err,
-            "fp64_gpu": {"ms_per_step": ms64,
-                         "cell_pseudo_steps_per_s": len(B_OVER_DX) * NSTEPS * ncells / (ms64 * 1e-3),
-                         "mixed_speedup": ms64 / (ms / a.steps),
-                         "mixed_vs_fp64_maxrel": mixed_vs_fp64},
+            "modes": modes,
+            "mixed_speedup_vs_fp64_gpu": modes["fp64_cg"]["ms_per_step"] / (ms / a.steps),
             "profiled_ms_per_step": ms_prof / a.steps,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                             "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}

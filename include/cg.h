@@ -93,7 +93,15 @@ cg_status cg_mesh_tet_operator(const cg_mesh *mesh, int64_t *rowptr_host, int32_
 /* ------------------------------------------------------------------------ parameters */
 
 enum { CG_SCHEME_IMPLICIT_EULER = 0, CG_SCHEME_CRANK_NICOLSON = 1, CG_SCHEME_EXPLICIT_EULER = 2 };
-enum { CG_PREC_FP64 = 0, CG_PREC_FP32_REFINE = 1, CG_PREC_BF16_REFINE = 2 };
+enum {
+    CG_PREC_FP64 = 0,           /* FP64 conjugate gradients */
+    CG_PREC_FP32_REFINE = 1,    /* FP32 inner solves, IEEE-FP64 iterative refinement */
+    CG_PREC_BF16_REFINE = 2,    /* BF16-stored inner solves, IEEE-FP64 refinement */
+    CG_PREC_FP32_DF_REFINE = 3, /* FP32 inner solves, double-float refinement (the iterate
+                                   and residual as FP32 hi+lo pairs, ~48-bit significand;
+                                   hex meshes; field values must lie in FP32 range) */
+    CG_PREC_BF16_DF_REFINE = 4  /* BF16-stored inner solves, double-float refinement */
+};
 enum { CG_DEPOSIT_ORDERED = 0, CG_DEPOSIT_FIXED_POINT = 1 };
 
 typedef struct {
@@ -103,7 +111,8 @@ typedef struct {
     int scheme;         /* CG_SCHEME_*: implicit Euler (default), Crank-Nicolson (the
                            paper's choice, Section 5.1), explicit Euler */
     int precision;      /* CG_PREC_*: FP64 conjugate gradients; FP32 (or BF16-stored)
-                           inner solves with FP64 iterative refinement */
+                           inner solves with FP64 or double-float iterative refinement
+                           (tet meshes run modes 3 and 4 as 1 and 2) */
     int deposit_mode;   /* CG_DEPOSIT_ORDERED: FP64 sum per cell in ascending particle
                            index; CG_DEPOSIT_FIXED_POINT: exact 64-bit integer sum of
                            w * 2^F (F per field, see cg_report.fixed_point_bits) */

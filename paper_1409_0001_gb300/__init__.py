@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = _build.LIB_PATH
 
 SCHEME_IMPLICIT_EULER, SCHEME_CRANK_NICOLSON, SCHEME_EXPLICIT_EULER = 0, 1, 2
-PREC_FP64, PREC_FP32_REFINE, PREC_BF16_REFINE = 0, 1, 2
+PREC_FP64, PREC_FP32_REFINE, PREC_BF16_REFINE, PREC_FP32_DF_REFINE, PREC_BF16_DF_REFINE = 0, 1, 2, 3, 4
 DEPOSIT_ORDERED, DEPOSIT_FIXED_POINT = 0, 1
 MAX_REPORT_FIELDS = 8
 

@@ -40,6 +40,7 @@ cg_status DevBuf::ensure(size_t n) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaFree", __FILE__, __LINE__);
     }
     size_t want = n + n / 8;
+    ++gen;
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -122,20 +123,73 @@ cudaEvent_t pool_get() {
 }  // namespace
 
 std::atomic<long long> g_launches{0};
+thread_local std::vector<ProfRecord> *t_sink = nullptr;
+thread_local long long *t_sink_kernels = nullptr;
+
+int prof_entry(const char *name) {
+    for (size_t i = 0; i < g_prof.size(); ++i)
+        if (g_prof[i].name == name) return (int)i;
+    g_prof.push_back(ProfEntry{name});
+    return (int)g_prof.size() - 1;
+}
 
 bool prof_on() { return g_prof_enabled.load(std::memory_order_relaxed); }
 
+void prof_capture_begin(std::vector<ProfRecord> *sink, long long *kernels) {
+    t_sink = sink;
+    t_sink_kernels = kernels;
+}
+
+void prof_capture_end() {
+    t_sink = nullptr;
+    t_sink_kernels = nullptr;
+}
+
+void prof_account_replay(const GraphEntry &e) {
+    g_launches.fetch_add(e.kernels, std::memory_order_relaxed);
+    if (!e.profiled) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const ProfRecord &r : e.records) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        ProfEntry &pe = g_prof[prof_entry(r.name)];
+        pe.launches += 1;
+        pe.ms += ms;
+        pe.bytes += r.bytes;
+    }
+}
+
+void graph_release(GraphEntry &e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    e.exec = nullptr;
+    for (ProfRecord &r : e.records) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    e.records.clear();
+}
+
 ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : st(s) {
+    if (t_sink_kernels) {
+        ++*t_sink_kernels;
+        if (t_sink && prof_on()) {
+            ProfRecord r{name, bytes, nullptr, nullptr};
+            cudaEventCreate(&r.a);
+            cudaEventCreate(&r.b);
+            // inside a capture only an "external" record becomes a timing node
+            cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
+            t_sink->push_back(r);
+            slot = -2;   // end event recorded by the destructor
+        }
+        return;
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!prof_on()) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    int entry = -1;
-    for (size_t i = 0; i < g_prof.size(); ++i)
-        if (g_prof[i].name == name) entry = (int)i;
-    if (entry < 0) {
-        g_prof.push_back(ProfEntry{name});
-        entry = (int)g_prof.size() - 1;
-    }
+    int entry = prof_entry(name);
     Pending pe{pool_get(), pool_get(), entry, bytes};
     cudaEventRecord(pe.a, st);
     g_pending.push_back(pe);
@@ -143,6 +197,11 @@ ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : st(s) {
 }
 
 ProfScope::~ProfScope() {
+    if (slot == -2) {
+        if (t_sink && !t_sink->empty())
+            cudaEventRecordWithFlags(t_sink->back().b, st, cudaEventRecordExternal);
+        return;
+    }
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEventRecord(g_pending[slot].b, st);
@@ -179,7 +238,7 @@ static cg_status check_params(const cg_params *p) {
     if (!p) return fail(CG_EINVAL, "params is NULL");
     if (p->nsteps < 1) return fail(CG_EINVAL, "nsteps must be >= 1 (got %d)", p->nsteps);
     if (p->scheme < 0 || p->scheme > 2) return fail(CG_EINVAL, "unknown scheme %d", p->scheme);
-    if (p->precision < 0 || p->precision > 2)
+    if (p->precision < 0 || p->precision > 4)
         return fail(CG_EINVAL, "unknown precision %d", p->precision);
     if (p->deposit_mode < 0 || p->deposit_mode > 1)
         return fail(CG_EINVAL, "unknown deposit_mode %d", p->deposit_mode);
@@ -318,6 +377,9 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     m->ws_small.release();
     m->ws_stage.release();
     m->h_small.release();
+    for (auto &e : m->graphs) graph_release(e);
+    m->graphs.clear();
+    if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
     if (m->kind == MESH_TET) tet_release(m);
     delete m;
     return CG_OK;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <utility>
 #include <vector>
 
 #include "cg.h"
@@ -33,6 +34,7 @@ cg_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    unsigned gen = 0;        // bumped on every reallocation (invalidates captured graphs)
     cg_status ensure(size_t n);
     void release();
     template <class T> T *as() const { return static_cast<T *>(p); }
@@ -45,6 +47,37 @@ struct HostBuf {
     cg_status ensure(size_t n);
     void release();
     template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ----------------------------------------------------------------------------- graphs
+// Launch records of a captured graph: when profiling was on during capture, each
+// launch got its own event pair (recorded inside the graph); after every replay the
+// elapsed times are added to the profile.
+struct ProfRecord {
+    const char *name;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+// A captured diffusion (one entry per distinct call signature and buffer set).
+struct GraphEntry {
+    int nf = 0, precision = 0, scheme = 0, nsteps = 0, rounds = 0;
+    double T = 0, tol = 0;
+    const void *cells = nullptr;
+    unsigned gen_diffuse = 0, gen_small = 0;
+    bool profiled = false;
+    cudaGraphExec_t exec = nullptr;
+    const void *result = nullptr;   // workspace buffer holding the final iterate
+    long long kernels = 0;
+    std::vector<ProfRecord> records;
+};
+
+// Refinement rounds per step that sufficed for a call signature (learned on the first
+// call, used to capture a fixed schedule afterwards).
+struct RoundsEntry {
+    int nf, precision, scheme, nsteps;
+    double T, tol;
+    int rounds;
 };
 
 // ----------------------------------------------------------------------------- meshes
@@ -92,6 +125,10 @@ struct cg_mesh {
     cgk::DevBuf ws_small;    // scalars, partials, counters
     cgk::DevBuf ws_stage;    // device staging for the host-pointer entry point
     cgk::HostBuf h_small;    // pinned readback
+    std::vector<std::pair<int, int>> tuned;   // autotuned sweep z-chunk per (fields, type)
+    std::vector<cgk::GraphEntry> graphs;      // captured diffusions
+    std::vector<cgk::RoundsEntry> rounds;     // learned refinement schedules
+    cudaStream_t capture_stream = nullptr;    // private stream used only for capture
 };
 
 namespace cgk {
@@ -112,6 +149,14 @@ struct ProfScope {
     cudaStream_t st = nullptr;
 };
 void prof_collect();
+// While a sink is set (graph capture), profiling scopes give each launch its own event
+// pair and append it to the sink, and launches are counted into *kernels instead of the
+// process-wide counter.
+void prof_capture_begin(std::vector<ProfRecord> *sink, long long *kernels);
+void prof_capture_end();
+// After a replay of a graph: add its records' elapsed times and launch count.
+void prof_account_replay(const GraphEntry &e);
+void graph_release(GraphEntry &e);
 
 // Launch with an optional profiling scope: CGK_LAUNCH("name", algorithmic_bytes, stream,
 // kernel<<<grid, block, smem, stream>>>(args...));

@@ -901,7 +901,8 @@ cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
     double T = p->bandwidth > 0.0 ? p->bandwidth * p->bandwidth / 4.0 : p->T;
     if (p->scheme == CG_SCHEME_EXPLICIT_EULER) return tet_explicit(m, nf, cells, p, T, rep, st);
     if (p->precision == CG_PREC_FP64) return tet_fp64(m, nf, cells, p, T, rep, st);
-    if (p->precision == CG_PREC_FP32_REFINE) return tet_mixed<float>(m, nf, cells, p, T, rep, st);
+    if (p->precision == CG_PREC_FP32_REFINE || p->precision == CG_PREC_FP32_DF_REFINE)
+        return tet_mixed<float>(m, nf, cells, p, T, rep, st);
     return tet_mixed<__nv_bfloat16>(m, nf, cells, p, T, rep, st);
 }
 

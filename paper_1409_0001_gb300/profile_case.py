@@ -1,0 +1,65 @@
+"""Run one diffusion-smoothing case for a profiler (ncu) or a quick timing.
+
+    python -m paper_1409_0001_gb300.profile_case --n 256 --precision 3 --reps 2
+
+Builds a seeded random field on an n^3 (or --dims) unit-spaced hex mesh and smooths
+it --reps times with the chosen precision mode (see include/cg.h), b = --b-over-dx
+cells, --nsteps implicit-Euler steps.  Prints the device time of each call.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--dims", type=int, nargs=3, default=None)
+    ap.add_argument("--precision", type=int, default=3)
+    ap.add_argument("--b-over-dx", type=float, default=2.0)
+    ap.add_argument("--nsteps", type=int, default=10)
+    ap.add_argument("--nfields", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--tet", action="store_true", help="Kuhn tet mesh of n^3 hexes instead")
+    a = ap.parse_args(argv)
+
+    import numpy as np
+    import torch
+
+    import paper_1409_0001_gb300 as cg
+    from paper_1409_0001_gb300 import build
+    import workloads as W
+
+    build.build()
+    dims = tuple(a.dims) if a.dims else (a.n, a.n, a.n)
+    dx = 1.0 / dims[0]
+    if a.tet:
+        xyz, tets = W.kuhn_tet_mesh(a.n)
+        mesh = cg.TetMesh(xyz, tets)
+    else:
+        mesh = cg.StructuredMesh(dims, (0.0, 0.0, 0.0), dx)
+    rng = np.random.default_rng(0)
+    u0 = torch.from_numpy(rng.random((a.nfields, mesh.ncells))).cuda()
+    p = cg.Params(bandwidth=a.b_over_dx * dx, nsteps=a.nsteps, precision=a.precision)
+    for r in range(a.reps):
+        u = u0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = cg.diffuse(mesh, u, p, report=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        print("rep %d: %.3f ms, %d cell-updates, %.3e cell-updates/s, residual %.2e"
+              % (r, dt * 1e3, rep["cell_updates"], rep["cell_updates"] / dt,
+                 rep["final_rel_residual"]))
+    mesh.close()
+
+
+if __name__ == "__main__":
+    main()

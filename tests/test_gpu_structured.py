@@ -140,7 +140,8 @@ def _diffuse_case(orc, cg, dims, dx, u0, T, nsteps, scheme, precision, tol=1e-13
     return u.cpu().numpy(), np.atleast_2d(ref), rep
 
 
-@pytest.mark.parametrize("precision,bar", [(0, FP64_TOL), (1, MIXED_TOL), (2, MIXED_TOL)])
+@pytest.mark.parametrize("precision,bar", [(0, FP64_TOL), (1, MIXED_TOL), (2, MIXED_TOL),
+                                           (3, MIXED_TOL), (4, MIXED_TOL)])
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("dims", [(32, 32, 32), (13, 7, 5), (257, 3, 2)])
 def test_diffuse_parity(cg, orc, dims, scheme, precision, bar):
@@ -177,7 +178,7 @@ def test_diffuse_bandwidth_sweep_mixed_vs_fp64(cg, orc, b_over_dx):
     cell, _ = orc.locate_structured(c.dims, c.origin, c.dx, c.pos)
     u0, _ = orc.deposit(cell, c.w, c.ncells, vc_uniform=c.dx ** 3)
     T = (b_over_dx * c.dx) ** 2 / 4
-    for precision, bar in ((0, FP64_TOL), (1, MIXED_TOL)):
+    for precision, bar in ((0, FP64_TOL), (1, MIXED_TOL), (3, MIXED_TOL), (4, MIXED_TOL)):
         got, ref, _ = _diffuse_case(orc, cg, c.dims, c.dx, u0, T, 10, 0, precision)
         assert maxrel(got, ref) <= bar
 
@@ -188,12 +189,12 @@ def test_diffuse_is_deterministic(cg):
     u0 = rng.random((3, int(np.prod(dims))))
     mesh = cg.StructuredMesh(dims, (0, 0, 0), 0.02)
     outs = []
-    for precision in (0, 1, 0, 1):
+    for precision in (0, 1, 3, 0, 1, 3):
         u = dev(u0)
         cg.diffuse(mesh, u, cg.Params(bandwidth=0.08, nsteps=5, precision=precision))
         outs.append(bits(u.cpu().numpy()))
-    assert np.array_equal(outs[0], outs[2])
-    assert np.array_equal(outs[1], outs[3])
+    for i in range(3):
+        assert np.array_equal(outs[i], outs[i + 3])
 
 
 # ----------------------------------------------------------------------------- whole method
@@ -211,7 +212,7 @@ def test_coarse_grain_uniform_cube_fp64(cg, orc):
     assert np.array_equal(bits(host), bits(got.cpu().numpy()))
 
 
-@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("precision", [1, 3, 0])
 def test_coarse_grain_clustered_128_full_size(cg, orc, precision):
     """Full-size 128^3 case, 2,000,000 clustered spheres, b = 2 dx: deposition bit-exact,
     diffusion within the bar of its precision."""
