@@ -195,6 +195,32 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
                                const double *w_host, double *cells_host, const cg_params *params,
                                cg_report *report, void *stream);
 
+/* ------------------------------------------------------------------------ batches */
+
+/* Many independent snapshots (Section 3.2.1: every field and component is an
+ * independent diffusion problem) smoothed together.  meshes[nsnap] are structured
+ * meshes of any sizes; cells[s] is device [nfields][ncells_s] FP64 (in/out);
+ * bandwidths (host, may be NULL) gives b per snapshot, else params->bandwidth/T.
+ * Precision modes 3 and 4 with implicit Euler or Crank-Nicolson run every snapshot,
+ * step, refinement round and inner iteration in ONE persistent cooperative launch
+ * (grid barriers bounded by params->barrier_budget, default ~1 s of clock cycles;
+ * CG_ETIMEOUT if one gives up), with per-step residuals verified afterwards; other
+ * modes and schemes run the snapshots one after another.  The batch's descriptors
+ * and work lists are kept with meshes[0].  report (may be NULL) aggregates all
+ * snapshots.  Errors: CG_EINVAL (a tet mesh, sizes, pointers), CG_ENOCONV,
+ * CG_ETIMEOUT, CG_ENOMEM, CG_ECUDA. */
+cg_status cg_diffuse_batched(int nsnap, cg_mesh *const *meshes, int nfields,
+                             double *const *cells, const cg_params *params,
+                             const double *bandwidths, cg_report *report, void *stream);
+
+/* The whole method for a batch: cg_deposit of snapshot s (n[s] particles, pos[s]
+ * device [3][n[s]], w[s] device [nfields][n[s]]) into cells[s], then
+ * cg_diffuse_batched. */
+cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64_t *n,
+                                  const double *const *pos, int nfields, const double *const *w,
+                                  double *const *cells, const cg_params *params,
+                                  const double *bandwidths, cg_report *report, void *stream);
+
 /* ------------------------------------------------------------------------ no allocation */
 
 /* Limits of cg_deposit_fixed_noalloc's static scratch. */

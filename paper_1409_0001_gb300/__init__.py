@@ -101,6 +101,9 @@ def load_library(path: str | None = None):
         "cg_profile_count": (i32, []),
         "cg_profile_get": (i32, [i32, ctypes.c_char_p, i32, P(ctypes.c_longlong), P(dbl), P(dbl)]),
         "cg_launch_count": (ctypes.c_longlong, []),
+        "cg_diffuse_batched": (i32, [i32, vp, i32, vp, P(CgParams), vp, P(CgReport), vp]),
+        "cg_coarse_grain_batched": (i32, [i32, vp, vp, vp, i32, vp, vp, P(CgParams), vp,
+                                          P(CgReport), vp]),
         "cg_deposit_fixed_noalloc": (i32, [i32, i32, i32, P(dbl), dbl, i64, vp, i32, vp, vp,
                                            P(ctypes.c_int), vp]),
         "cg_launch_count_reset": (None, []),
@@ -120,7 +123,7 @@ def exported_symbols():
             "cg_mesh_tet_operator", "cg_locate", "cg_deposit", "cg_diffuse", "cg_coarse_grain",
             "cg_coarse_grain_host", "cg_profile_enable", "cg_profile_reset", "cg_profile_count",
             "cg_profile_get", "cg_launch_count", "cg_launch_count_reset",
-            "cg_deposit_fixed_noalloc"]
+            "cg_deposit_fixed_noalloc", "cg_diffuse_batched", "cg_coarse_grain_batched"]
 
 
 def _check(status: int, where: str):
@@ -360,3 +363,57 @@ def deposit_fixed_noalloc(dims, origin, dx, pos, w, out=None, stream=None):
                                                    out.data_ptr(), bits, _stream_handle(stream)),
            "cg_deposit_fixed_noalloc")
     return out, list(bits)[:nf]
+
+
+def _ptr_array(ptrs, ctype=ctypes.c_void_p):
+    arr = (ctype * len(ptrs))()
+    for i, v in enumerate(ptrs):
+        arr[i] = v
+    return arr
+
+
+def diffuse_batched(meshes, cells, params: Params, bandwidths=None, stream=None, report=False):
+    """Batched diffusion (cg_diffuse_batched): cells[s] is a CUDA f64 [nf, ncells_s] tensor."""
+    import numpy as np
+    for c in cells:
+        _dev_f64(c, "cells")
+    nf = cells[0].shape[0]
+    ms = _ptr_array([m.handle.value for m in meshes])
+    cs = _ptr_array([c.data_ptr() for c in cells])
+    bw = None
+    if bandwidths is not None:
+        bw = np.ascontiguousarray(bandwidths, dtype=np.float64)
+    rep = CgReport()
+    cp = params.to_c()
+    _check(load_library().cg_diffuse_batched(len(meshes), ms, nf, cs, ctypes.byref(cp),
+                                             None if bw is None else bw.ctypes.data,
+                                             ctypes.byref(rep), _stream_handle(stream)),
+           "cg_diffuse_batched")
+    return (cells, rep.as_dict()) if report else cells
+
+
+def coarse_grain_batched(meshes, pos, w, params: Params, bandwidths=None, out=None, stream=None,
+                         report=False):
+    """The whole method for a batch (cg_coarse_grain_batched).  pos[s] [3, n_s] and w[s]
+    [nf, n_s] CUDA f64 tensors; returns the list of cell tensors."""
+    import numpy as np
+    import torch
+    nf = w[0].shape[0]
+    for t in list(pos) + list(w):
+        _dev_f64(t, "pos/w")
+    if out is None:
+        out = [torch.empty((nf, m.ncells), dtype=torch.float64, device=w[0].device) for m in meshes]
+    ms = _ptr_array([m.handle.value for m in meshes])
+    ns = _ptr_array([int(p_.shape[1]) for p_ in pos], ctypes.c_int64)
+    ps = _ptr_array([p_.data_ptr() for p_ in pos])
+    ws = _ptr_array([w_.data_ptr() for w_ in w])
+    cs = _ptr_array([c.data_ptr() for c in out])
+    bw = None if bandwidths is None else np.ascontiguousarray(bandwidths, dtype=np.float64)
+    rep = CgReport()
+    cp = params.to_c()
+    _check(load_library().cg_coarse_grain_batched(len(meshes), ms, ns, ps, nf, ws, cs,
+                                                  ctypes.byref(cp),
+                                                  None if bw is None else bw.ctypes.data,
+                                                  ctypes.byref(rep), _stream_handle(stream)),
+           "cg_coarse_grain_batched")
+    return (out, rep.as_dict()) if report else out

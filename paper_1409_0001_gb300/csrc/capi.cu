@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -376,6 +377,7 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     m->ws_diffuse.release();
     m->ws_small.release();
     m->ws_stage.release();
+    m->ws_batch.release();
     m->h_small.release();
     for (auto &e : m->graphs) graph_release(e);
     m->graphs.clear();
@@ -511,6 +513,130 @@ cg_status cg_coarse_grain(cg_mesh *m, int64_t n, const double *pos, int nfields,
     cudaStream_t st = (cudaStream_t)stream;
     cg_status s = deposit_run(m, n, pos, nfields, w, cells_out, p, rep, st);
     if (s == CG_OK) s = diffuse_impl(m, nfields, cells_out, p, rep, st);
+    prof_collect();
+    return s;
+}
+
+static cg_status batched_diffuse_impl(int nsnap, cg_mesh *const *meshes, int nfields,
+                                     double *const *cells, const cg_params *p,
+                                     const double *bandwidths, cg_report *rep, cudaStream_t st) {
+    const bool fused = (p->precision == CG_PREC_FP32_DF_REFINE || p->precision == CG_PREC_BF16_DF_REFINE) &&
+                       p->scheme != CG_SCHEME_EXPLICIT_EULER;
+    double mass_in[CG_REPORT_MAX_FIELDS] = {0}, mass_out[CG_REPORT_MAX_FIELDS] = {0};
+    const int nrep = nfields < CG_REPORT_MAX_FIELDS ? nfields : CG_REPORT_MAX_FIELDS;
+    if (rep)
+        for (int s = 0; s < nsnap; ++s) {
+            double mm[CG_REPORT_MAX_FIELDS];
+            CGK_TRY(field_mass(meshes[s], nrep, cells[s], mm, st));
+            for (int f = 0; f < nrep; ++f) mass_in[f] += mm[f];
+        }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rep) {
+        CGK_CUDA(cudaEventCreate(&e0));
+        CGK_CUDA(cudaEventCreate(&e1));
+        CGK_CUDA(cudaEventRecord(e0, st));
+    }
+    cg_status s = CG_OK;
+    if (fused) {
+        s = diffuse_batched_run(nsnap, meshes, nfields, cells, p, bandwidths, rep, st);
+    } else {
+        cg_report one;
+        long long upd = 0, it = 0, rounds = 0;
+        double worst = 0;
+        for (int q = 0; q < nsnap && s == CG_OK; ++q) {
+            cg_params pq = *p;
+            if (bandwidths) pq.bandwidth = bandwidths[q];
+            std::memset(&one, 0, sizeof(one));
+            s = diffuse_structured_run(meshes[q], nfields, cells[q], &pq, &one, st);
+            upd += one.cell_updates;
+            it += one.iters;
+            rounds += one.refine_rounds;
+            worst = std::max(worst, one.final_rel_residual);
+        }
+        if (rep) {
+            rep->cell_updates = upd;
+            rep->iters = it;
+            rep->refine_rounds = rounds;
+            rep->final_rel_residual = worst;
+        }
+    }
+    if (rep) {
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        rep->ms_diffuse = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (s == CG_OK || s == CG_ENOCONV)
+            for (int q = 0; q < nsnap; ++q) {
+                double mm[CG_REPORT_MAX_FIELDS];
+                cg_status s2 = field_mass(meshes[q], nrep, cells[q], mm, st);
+                if (s2 != CG_OK) return s2;
+                for (int f = 0; f < nrep; ++f) mass_out[f] += mm[f];
+            }
+        for (int f = 0; f < nrep; ++f) {
+            rep->mass_in[f] = mass_in[f];
+            rep->mass_out[f] = mass_out[f];
+        }
+    }
+    return s;
+}
+
+static cg_status check_batch(int nsnap, cg_mesh *const *meshes, int nfields, double *const *cells,
+                             const cg_params *p, const double *bandwidths) {
+    CGK_TRY(check_params(p));
+    if (nsnap < 1 || !meshes || !cells) return fail(CG_EINVAL, "empty batch or NULL arrays");
+    if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
+    for (int s = 0; s < nsnap; ++s) {
+        if (!meshes[s] || meshes[s]->kind != MESH_STRUCTURED)
+            return fail(CG_EINVAL, "batch snapshot %d: not a structured mesh", s);
+        if (!is_device_ptr(cells[s])) return fail(CG_EINVAL, "batch snapshot %d: cells not on the device", s);
+        if (bandwidths && !(bandwidths[s] > 0.0 && std::isfinite(bandwidths[s])))
+            return fail(CG_EINVAL, "batch snapshot %d: bandwidth must be finite and > 0", s);
+        for (int q = 0; q < s; ++q)
+            if (meshes[q] == meshes[s])
+                return fail(CG_EINVAL, "batch snapshots %d and %d share a mesh (workspaces would collide)", q, s);
+    }
+    return CG_OK;
+}
+
+cg_status cg_diffuse_batched(int nsnap, cg_mesh *const *meshes, int nfields, double *const *cells,
+                             const cg_params *p, const double *bandwidths, cg_report *rep,
+                             void *stream) {
+    CGK_TRY(check_batch(nsnap, meshes, nfields, cells, p, bandwidths));
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    cg_status s = batched_diffuse_impl(nsnap, meshes, nfields, cells, p, bandwidths, rep,
+                                       (cudaStream_t)stream);
+    prof_collect();
+    return s;
+}
+
+cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64_t *n,
+                                  const double *const *pos, int nfields, const double *const *w,
+                                  double *const *cells, const cg_params *p,
+                                  const double *bandwidths, cg_report *rep, void *stream) {
+    CGK_TRY(check_batch(nsnap, meshes, nfields, cells, p, bandwidths));
+    if (!n || !pos || !w) return fail(CG_EINVAL, "NULL particle arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    for (int s = 0; s < nsnap; ++s) {
+        CGK_TRY(check_deposit_args(meshes[s], n[s], pos[s], nfields, w[s], cells[s], p));
+        cg_report one;
+        std::memset(&one, 0, sizeof(one));
+        CGK_TRY(deposit_run(meshes[s], n[s], pos[s], nfields, w[s], cells[s], p, rep ? &one : nullptr, st));
+        if (rep) {
+            rep->ms_locate += one.ms_locate;
+            rep->ms_deposit += one.ms_deposit;
+            rep->n_out_of_domain += one.n_out_of_domain;
+        }
+    }
+    double keep_loc = rep ? rep->ms_locate : 0, keep_dep = rep ? rep->ms_deposit : 0;
+    cg_status s = batched_diffuse_impl(nsnap, meshes, nfields, cells, p, bandwidths, rep, st);
+    if (rep) {
+        rep->ms_locate = keep_loc;
+        rep->ms_deposit = keep_dep;
+    }
     prof_collect();
     return s;
 }

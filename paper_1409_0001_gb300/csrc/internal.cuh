@@ -124,6 +124,7 @@ struct cg_mesh {
     cgk::DevBuf ws_diffuse;  // solver vectors
     cgk::DevBuf ws_small;    // scalars, partials, counters
     cgk::DevBuf ws_stage;    // device staging for the host-pointer entry point
+    cgk::DevBuf ws_batch;    // batched calls: descriptors, work items, partials (first mesh)
     cgk::HostBuf h_small;    // pinned readback
     std::vector<std::pair<int, int>> tuned;   // autotuned sweep z-chunk per (fields, type)
     std::vector<cgk::GraphEntry> graphs;      // captured diffusions
@@ -181,6 +182,12 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
 // Diffusion on a structured mesh (in place).
 cg_status diffuse_structured_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
                                  cg_report *rep, cudaStream_t st);
+
+// Batched diffusion of many structured snapshots in one persistent launch (double-float
+// modes 3 and 4, implicit Euler or Crank-Nicolson).
+cg_status diffuse_batched_run(int nsnap, cg_mesh *const *meshes, int nf, double *const *cells,
+                              const cg_params *p, const double *bandwidths, cg_report *rep,
+                              cudaStream_t st);
 
 // Diffusion on a tet mesh (in place).
 cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p,

@@ -889,29 +889,38 @@ template <> struct Vec4<__nv_bfloat16> {
 
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-template <class TS>
-__global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, Coef32 cf,
-                                                      float gamma, float omega,
-                                                      const TS *__restrict__ y_all,
-                                                      const TS *yprev_all,
-                                                      const TS *__restrict__ r_all, TS *ynext_all) {
-    chain_wait();
-    chain_release();
+// L2-coherent variants of the vector loads, for data written by other blocks of the
+// same (persistent) launch.
+template <class TS> struct Vec4cg;
+template <> struct Vec4cg<float> {
+    static __device__ __forceinline__ float4 load(const float *p, size_t i) {
+        return __ldcg(reinterpret_cast<const float4 *>(p + i));
+    }
+};
+template <> struct Vec4cg<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load(const __nv_bfloat16 *p, size_t i) {
+        uint2 u = __ldcg(reinterpret_cast<const uint2 *>(p + i));
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
+        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+};
+
+// One tile (128 x-cells x TY rows x planes [z0, z1)) of the vectorised Chebyshev
+// iteration; L is the load policy (Vec4 or Vec4cg), sdg the diagonal table in shared
+// memory.  Every thread of the block must call it (barriers and shuffles inside).
+template <class TS, template <class> class L>
+__device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z0, int z1,
+                                             const Coef32 &cf, const float *sdg, float gamma,
+                                             float omega, const TS *yv, const TS *ypv,
+                                             const TS *rv, TS *ynv) {
     using V = Vec4<TS>;
-    const int f = blockIdx.z / nzc;
-    const int z0 = (blockIdx.z - f * nzc) * zlen;
-    const int z1 = min(g.nz, z0 + zlen);
-    const size_t off = (size_t)f * g.n;
-    const TS *yv = y_all + off;
-    const TS *rv = r_all + off;
-    const TS *ypv = yprev_all ? yprev_all + off : nullptr;
-    TS *ynv = ynext_all + off;
+    using LD = L<TS>;
     __shared__ float4 pl[TY + 2][TX];
-    __shared__ float sdg[8];
-    stage_table(sdg, cf.dg);
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * (4 * TX);
-    const int x = x0 + 4 * tx, y = blockIdx.y * TY + ty;
+    const int x0 = bx * (4 * TX);
+    const int x = x0 + 4 * tx, y = by * TY + ty;
     const bool own = (x < g.nx) && (y < g.ny);
     const bool rowlo = (ty == 0) && (y > 0) && (x < g.nx);            // loads row y-1
     const bool rowhi = (ty == TY - 1) && (y + 1 < g.ny) && (x < g.nx);  // loads row y+1
@@ -922,9 +931,6 @@ __global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, 
     const int nyb = (y > 0) + (y + 1 < g.ny);
     const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx);
     const int n12 = nyb + 2;
-    if (!own) {
-        // still take part in the block barriers and shuffles below
-    }
     const int kxy = y * g.nx + x;
     float4 vdn = f4zero(), vc = f4zero(), vup = f4zero(), ypc = f4zero(), rc = f4zero();
     float4 hlo = f4zero(), hhi = f4zero();
@@ -932,16 +938,16 @@ __global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, 
     if (z0 < z1) {
         const size_t k0 = (size_t)kxy + (size_t)z0 * g.nxy;
         if (own) {
-            if (z0 > 0) vdn = V::load(yv, k0 - g.nxy);
-            vc = V::load(yv, k0);
-            if (z0 + 1 < g.nz) vup = V::load(yv, k0 + g.nxy);
-            if (ypv) ypc = V::load(ypv, k0);
-            rc = V::load(rv, k0);
+            if (z0 > 0) vdn = LD::load(yv, k0 - g.nxy);
+            vc = LD::load(yv, k0);
+            if (z0 + 1 < g.nz) vup = LD::load(yv, k0 + g.nxy);
+            if (ypv) ypc = LD::load(ypv, k0);
+            rc = LD::load(rv, k0);
         }
-        if (rowlo) hlo = V::load(yv, k0 - g.nx);
-        if (rowhi) hhi = V::load(yv, k0 + g.nx);
-        if (xl) hl = ld(yv, (int)(k0 - 1));
-        if (xr) hr = ld(yv, (int)(k0 + 4));
+        if (rowlo) hlo = LD::load(yv, k0 - g.nx);
+        if (rowhi) hhi = LD::load(yv, k0 + g.nx);
+        if (xl) hl = ldcg(yv, (int)(k0 - 1));
+        if (xr) hr = ldcg(yv, (int)(k0 + 4));
     }
     for (int z = z0; z < z1; ++z) {
         const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
@@ -951,14 +957,14 @@ __global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, 
         if (z + 1 < z1) {
             const size_t kn = kz + g.nxy;
             if (own) {
-                if (z + 2 < g.nz) nup = V::load(yv, kn + g.nxy);
-                if (ypv) nyp = V::load(ypv, kn);
-                nr = V::load(rv, kn);
+                if (z + 2 < g.nz) nup = LD::load(yv, kn + g.nxy);
+                if (ypv) nyp = LD::load(ypv, kn);
+                nr = LD::load(rv, kn);
             }
-            if (rowlo) nlo = V::load(yv, kn - g.nx);
-            if (rowhi) nhi = V::load(yv, kn + g.nx);
-            if (xl) nl = ld(yv, (int)(kn - 1));
-            if (xr) nrr = ld(yv, (int)(kn + 4));
+            if (rowlo) nlo = LD::load(yv, kn - g.nx);
+            if (rowhi) nhi = LD::load(yv, kn + g.nx);
+            if (xl) nl = ldcg(yv, (int)(kn - 1));
+            if (xr) nrr = ldcg(yv, (int)(kn + 4));
         }
         pl[ty + 1][tx] = vc;
         if (ty == 0) pl[0][tx] = hlo;
@@ -994,6 +1000,223 @@ __global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, 
         hhi = nhi;
         hl = nl;
         hr = nrr;
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, Coef32 cf,
+                                                      float gamma, float omega,
+                                                      const TS *__restrict__ y_all,
+                                                      const TS *yprev_all,
+                                                      const TS *__restrict__ r_all, TS *ynext_all) {
+    chain_wait();
+    chain_release();
+    const int f = blockIdx.z / nzc;
+    const int z0 = (blockIdx.z - f * nzc) * zlen;
+    const int z1 = min(g.nz, z0 + zlen);
+    const size_t off = (size_t)f * g.n;
+    __shared__ float sdg[8];
+    stage_table(sdg, cf.dg);
+    __syncthreads();
+    cheb_v4_tile<TS, Vec4>(g, blockIdx.x, blockIdx.y, z0, z1, cf, sdg, gamma, omega, y_all + off,
+                           yprev_all ? yprev_all + off : nullptr, r_all + off, ynext_all + off);
+}
+
+// ---------------------------------------------------------------- batched snapshots
+// Many independent snapshots (each its own hex mesh, bandwidth and Chebyshev count) are
+// smoothed by one persistent cooperative launch in the double-float modes.  Phases:
+// u^0 -> double-float; then per pseudo-step the first refinement pass, R rounds of
+// (m_s - 1 Chebyshev iterations, one refinement pass), with a bounded grid barrier
+// after every phase.  Work items (tile x z-chunk x field of one snapshot) are dealt to
+// blocks round-robin; a snapshot whose m_s is smaller than the longest idles in the
+// remaining Chebyshev phases.  Buffer roles are fixed: the first Chebyshev iterate is
+// in Ya and, m_s being even, the correction always ends in Yb; round 1 writes X1, later
+// rounds alternate X2/X1, and the last round (R >= 2) writes u^{n+1} over u^n in U
+// (read there only at the cell itself).  Per-item residual partials of each step's
+// last pass (and ||b||^2 partials of its first pass) are stored and reduced afterwards.
+template <class TS>
+struct SnapDesc {
+    Geo g;
+    int gx, gy, zlen, nzc;   // refinement items (scalar engine)
+    int v4, gx4, zlen4, nzc4;// Chebyshev items (vectorised if v4)
+    int m;                   // Chebyshev iterations per round (even)
+    int scheme;
+    float gamma;
+    Coef32 cf32;
+    CoefDF cfdf;
+    const double *cells;     // u^0, field-major FP64
+    DF *U, *X1, *X2, *B;
+    TS *R, *Ya, *Yb;
+    const float *omega;      // omega[k], k = 1 .. m-1
+};
+
+struct BItem {
+    int snap, bx, by, zf;    // zf = field * nzc + z-chunk
+};
+
+__device__ __forceinline__ DF ldcg_df(const DF *p, int i) {
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p + i));
+    return DF{v.x, v.y};
+}
+
+template <class TS>
+__device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BItem &it, bool first,
+                                               int round, int R, double *part) {
+    const Geo &g = d.g;
+    const int f = it.zf / d.nzc;
+    const int zc = it.zf - f * d.nzc;
+    const int z0 = zc * d.zlen, z1 = min(g.nz, z0 + d.zlen);
+    const size_t off = (size_t)f * g.n;
+    __shared__ DF sdg[8];
+    stage_table(sdg, d.cfdf.dg);
+    __syncthreads();
+    float acc = 0.0f;
+    const float gamma = d.gamma;
+    TS *r = d.R + off;
+    TS *y1 = d.Ya + off;
+    if (first) {
+        const DF *u = d.U + off;
+        DF *bo = d.B + off;
+        sweep25_at<DF>(
+            g, it.bx, it.by, z0, z1, [&](int k) { return ldcg_df(u, k); }, [](int) { return NoPre{}; },
+            [&](int k, DF v, DF sm, int nn, NoPre) {
+                DF lx = sm - df_mulf(v, (float)nn);
+                DF rk = df_mul(d.cfdf.c, lx);
+                DF bk = v;
+                if (d.scheme == 1) {
+                    bk = v + df_mul(d.cfdf.half_c, lx);
+                    bo[k] = bk;
+                }
+                float bf = df_f(bk);
+                acc = fmaf(bf, bf, acc);
+                float rf = df_f(rk);
+                st(r, k, rf);
+                st(y1, k, gamma * rf);
+            });
+    } else {
+        const DF *xin = (round == 1 ? d.U : ((round & 1) ? d.X2 : d.X1)) + off;
+        DF *xout = (round == R ? d.U : ((round & 1) ? d.X1 : d.X2)) + off;
+        const DF *b = (d.scheme == 1 ? d.B : d.U) + off;
+        const TS *dd = d.Yb + off;
+        sweep25_at<DF>(
+            g, it.bx, it.by, z0, z1, [&](int k) { return df_add_f(ldcg_df(xin, k), ldcg(dd, k)); },
+            [&](int k) { return ldcg_df(b, k); },
+            [&](int k, DF v, DF sm, int nn, DF bk) {
+                xout[k] = v;
+                DF rk = bk - (df_mul(sdg[nn], v) - df_mul(d.cfdf.ce, sm));
+                float rf = df_f(rk);
+                st(r, k, rf);
+                st(y1, k, gamma * rf);
+                acc = fmaf(rf, rf, acc);
+            });
+    }
+    double tot = block_sum((double)acc);
+    if (is_thread0() && part) *part = tot;
+}
+
+template <class TS>
+__device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem &it, int k) {
+    const Geo &g = d.g;
+    const int nzc = d.v4 ? d.nzc4 : d.nzc, zlen = d.v4 ? d.zlen4 : d.zlen;
+    const int f = it.zf / nzc;
+    const int zc = it.zf - f * nzc;
+    const int z0 = zc * zlen, z1 = min(g.nz, z0 + zlen);
+    const size_t off = (size_t)f * g.n;
+    // y_k lives in Ya for odd k, in Yb for even k; y_{k+1} overwrites y_{k-1}
+    const TS *yc = ((k & 1) ? d.Ya : d.Yb) + off;
+    TS *yo = ((k & 1) ? d.Yb : d.Ya) + off;
+    const TS *yp = k == 1 ? nullptr : yo;
+    const TS *r = d.R + off;
+    const float omega = d.omega[k];
+    __shared__ float sdg[8];
+    stage_table(sdg, d.cf32.dg);
+    __syncthreads();
+    if (d.v4) {
+        cheb_v4_tile<TS, Vec4cg>(g, it.bx, it.by, z0, z1, d.cf32, sdg, d.gamma, omega, yc, yp, r, yo);
+    } else {
+        sweep25_at<float>(
+            g, it.bx, it.by, z0, z1, [&](int q) { return ldcg(yc, q); },
+            [&](int q) { return float2{yp ? ldcg(yp, q) : 0.0f, ldcg(r, q)}; },
+            [&](int q, float v, float sm, int nn, float2 pt) {
+                float ay = fmaf(sdg[nn], v, -d.cf32.ce * sm);
+                st(yo, q, fmaf(omega, v - pt.x + d.gamma * (pt.y - ay), pt.x));
+            });
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kThreads) k_batched(const SnapDesc<TS> *__restrict__ sd, int nsnap,
+                                                      int nf, const BItem *__restrict__ ritems,
+                                                      int nr, const BItem *__restrict__ citems,
+                                                      int nc, int nsteps, int R, int mmax,
+                                                      double *__restrict__ part_rr,
+                                                      double *__restrict__ part_bb, GridBar *gb,
+                                                      long long budget) {
+    // phase 0: u^0 -> double-float
+    const size_t tid = (size_t)blockIdx.x * kThreads + threadIdx.y * TX + threadIdx.x;
+    const size_t nthr = (size_t)gridDim.x * kThreads;
+    for (int s = 0; s < nsnap; ++s) {
+        const size_t cnt = (size_t)sd[s].g.n * nf;
+        const double *u = sd[s].cells;
+        DF *U = sd[s].U;
+        for (size_t i = tid; i < cnt; i += nthr) {
+            double v = u[i];
+            float hi = __double2float_rn(v);
+            U[i] = DF{hi, __double2float_rn(v - (double)hi)};
+        }
+    }
+    if (!grid_sync(gb, gridDim.x, budget)) return;
+    for (int step = 0; step < nsteps; ++step) {
+        for (int i = blockIdx.x; i < nr; i += gridDim.x) {
+            const BItem it = ritems[i];
+            batched_refine<TS>(sd[it.snap], it, true, 0, R, part_bb + (size_t)step * nr + i);
+        }
+        if (!grid_sync(gb, gridDim.x, budget)) return;
+        for (int round = 1; round <= R; ++round) {
+            for (int k = 1; k < mmax; ++k) {
+                for (int i = blockIdx.x; i < nc; i += gridDim.x) {
+                    const BItem it = citems[i];
+                    if (k < sd[it.snap].m) batched_cheb<TS>(sd[it.snap], it, k);
+                }
+                if (!grid_sync(gb, gridDim.x, budget)) return;
+            }
+            for (int i = blockIdx.x; i < nr; i += gridDim.x) {
+                const BItem it = ritems[i];
+                batched_refine<TS>(sd[it.snap], it, false, round, R,
+                                   round == R ? part_rr + (size_t)step * nr + i : nullptr);
+            }
+            if (step + 1 < nsteps || round < R)
+                if (!grid_sync(gb, gridDim.x, budget)) return;
+        }
+    }
+}
+
+// hist[(step * nsnap + s) * nf + f] = (sum of ||r||^2 partials, sum of ||b||^2 partials)
+// over the snapshot-field's items, in item order.  One block per (step, s, f).
+__global__ void k_batched_hist(const int *__restrict__ first_item, int nsnap, int nf, int nr,
+                               const double *__restrict__ part_rr,
+                               const double *__restrict__ part_bb, double2 *__restrict__ hist) {
+    const int sf = blockIdx.x % (nsnap * nf);
+    const int step = blockIdx.x / (nsnap * nf);
+    const int i0 = first_item[sf], i1 = first_item[sf + 1];
+    double a = 0.0, b = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kThreads) {
+        a += part_rr[(size_t)step * nr + i];
+        b += part_bb[(size_t)step * nr + i];
+    }
+    double A = block_sum(a), B = block_sum(b);
+    if (threadIdx.x == 0) hist[blockIdx.x] = make_double2(A, B);
+}
+
+template <class TS>
+__global__ void k_batched_final(const SnapDesc<TS> *__restrict__ sd, int nf, double *const *cells) {
+    const SnapDesc<TS> &d = sd[blockIdx.y];
+    const size_t cnt = (size_t)d.g.n * nf;
+    double *out = cells[blockIdx.y];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (size_t)gridDim.x * blockDim.x) {
+        DF v = d.U[i];
+        out[i] = (double)v.hi + (double)v.lo;
     }
 }
 
@@ -1692,6 +1915,201 @@ cg_status diffuse_structured_run(cg_mesh *m, int nf, double *cells, const cg_par
         case CG_PREC_FP32_DF_REFINE: return diffuse_mixed<float, DF>(m, nf, cells, p, T, rep, st);
         default: return diffuse_mixed<__nv_bfloat16, DF>(m, nf, cells, p, T, rep, st);
     }
+}
+
+
+// ============================================================================ batched host
+template <class TS>
+static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
+                                    double *const *cells, const cg_params *p,
+                                    const double *bandwidths, cg_report *rep, cudaStream_t st) {
+    const bool cn = p->scheme == CG_SCHEME_CRANK_NICOLSON;
+    const double eps_inner = sizeof(TS) == 2 ? 2e-3 : 1e-6;
+    const double tol2 = p->tol * p->tol;
+    std::vector<SnapDesc<TS>> descs((size_t)nsnap);
+    std::vector<float> omegas;
+    std::vector<size_t> omega_off((size_t)nsnap);
+    std::vector<BItem> ritems, citems;
+    std::vector<int> first_item;   // per (snapshot, field), into ritems
+    int mmax = 2;
+    long long cells_total = 0;
+    for (int s = 0; s < nsnap; ++s) {
+        cg_mesh *m = meshes[s];
+        SnapDesc<TS> &d = descs[s];
+        const int n = (int)m->ncells;
+        d.g = Geo{m->nx, m->ny, m->nz, m->nx * m->ny, n};
+        const double b = bandwidths ? bandwidths[s] : p->bandwidth;
+        const double T = b > 0.0 ? b * b / 4.0 : p->T;
+        const double c = (T / p->nsteps) / (m->dx * m->dx);
+        const double ce = cn ? 0.5 * c : c;
+        const int dims[3] = {m->nx, m->ny, m->nz};
+        double lmax = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            double sv = std::sin(M_PI * (dims[a] - 1) / (2.0 * dims[a]));
+            lmax += 4.0 * ce * sv * sv;
+        }
+        const double theta = 0.5 * (lmax + 1.0), delta = 0.5 * (lmax - 1.0);
+        int mi = cheb_iters(lmax, eps_inner);
+        if (mi < 2) mi = 2;
+        if (mi & 1) ++mi;
+        d.m = mi;
+        mmax = std::max(mmax, mi);
+        d.gamma = (float)(1.0 / theta);
+        d.cf32 = coef32(ce);
+        d.cfdf = coefdf(c, ce);
+        d.scheme = p->scheme;
+        omega_off[s] = omegas.size();
+        double sigma = delta > 0.0 ? theta / delta : 0.0, om = 1.0;
+        omegas.push_back(1.0f);
+        for (int k = 1; k < mi; ++k) {
+            if (sigma > 0.0)
+                om = (k == 1) ? 1.0 / (1.0 - 1.0 / (2.0 * sigma * sigma))
+                              : 1.0 / (1.0 - om / (4.0 * sigma * sigma));
+            omegas.push_back((float)om);
+        }
+        d.gx = (m->nx + TX - 1) / TX;
+        d.gy = (m->ny + TY - 1) / TY;
+        d.zlen = std::min(8, m->nz);
+        d.nzc = (m->nz + d.zlen - 1) / d.zlen;
+        d.v4 = (m->nx % 4 == 0) ? 1 : 0;
+        d.gx4 = (m->nx + 4 * TX - 1) / (4 * TX);
+        d.zlen4 = std::min(8, m->nz);
+        d.nzc4 = (m->nz + d.zlen4 - 1) / d.zlen4;
+        // per-snapshot solver vectors, owned by the snapshot's mesh
+        const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
+        CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 3 * vts));
+        char *wb = m->ws_diffuse.as<char>();
+        d.U = (DF *)wb;
+        d.X1 = (DF *)(wb + v64);
+        d.X2 = (DF *)(wb + 2 * v64);
+        d.B = (DF *)(wb + 3 * v64);
+        d.R = (TS *)(wb + 4 * v64);
+        d.Ya = (TS *)(wb + 4 * v64 + vts);
+        d.Yb = (TS *)(wb + 4 * v64 + 2 * vts);
+        d.cells = cells[s];
+        for (int f = 0; f < nf; ++f) {
+            first_item.push_back((int)ritems.size());
+            for (int zc = 0; zc < d.nzc; ++zc)
+                for (int by = 0; by < d.gy; ++by)
+                    for (int bx = 0; bx < d.gx; ++bx) ritems.push_back(BItem{s, bx, by, f * d.nzc + zc});
+            const int cz = d.v4 ? d.nzc4 : d.nzc, cx = d.v4 ? d.gx4 : d.gx;
+            for (int zc = 0; zc < cz; ++zc)
+                for (int by = 0; by < d.gy; ++by)
+                    for (int bx = 0; bx < cx; ++bx) citems.push_back(BItem{s, bx, by, f * cz + zc});
+        }
+        cells_total += (long long)n;
+    }
+    first_item.push_back((int)ritems.size());
+    const int nr = (int)ritems.size(), nc = (int)citems.size();
+    // batch arena on the first mesh: descriptors | omega | items | partials | hist | barrier | out ptrs
+    const size_t o_desc = 0;
+    const size_t o_om = align_up(o_desc + descs.size() * sizeof(SnapDesc<TS>));
+    const size_t o_ri = align_up(o_om + omegas.size() * sizeof(float));
+    const size_t o_ci = align_up(o_ri + ritems.size() * sizeof(BItem));
+    const size_t o_fi = align_up(o_ci + citems.size() * sizeof(BItem));
+    const size_t o_prr = align_up(o_fi + first_item.size() * sizeof(int));
+    const size_t o_pbb = align_up(o_prr + (size_t)p->nsteps * nr * 8);
+    const size_t o_hist = align_up(o_pbb + (size_t)p->nsteps * nr * 8);
+    const size_t nh = (size_t)p->nsteps * nsnap * nf;
+    const size_t o_gb = align_up(o_hist + nh * sizeof(double2));
+    const size_t o_out = align_up(o_gb + sizeof(GridBar));
+    const size_t total = align_up(o_out + (size_t)nsnap * sizeof(double *));
+    cg_mesh *m0 = meshes[0];
+    CGK_TRY(m0->ws_batch.ensure(total));
+    char *ab = m0->ws_batch.as<char>();
+    for (int s = 0; s < nsnap; ++s) descs[s].omega = (const float *)(ab + o_om) + omega_off[s];
+    CGK_CUDA(cudaMemcpyAsync(ab + o_desc, descs.data(), descs.size() * sizeof(SnapDesc<TS>),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + o_om, omegas.data(), omegas.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + o_ri, ritems.data(), ritems.size() * sizeof(BItem),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + o_ci, citems.data(), citems.size() * sizeof(BItem),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + o_fi, first_item.data(), first_item.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + o_out, cells, (size_t)nsnap * sizeof(double *),
+                             cudaMemcpyHostToDevice, st));
+    // the host vectors above must outlive the copies
+    CGK_CUDA(cudaStreamSynchronize(st));
+    const SnapDesc<TS> *dsd = (const SnapDesc<TS> *)(ab + o_desc);
+    const BItem *dri = (const BItem *)(ab + o_ri), *dci = (const BItem *)(ab + o_ci);
+    double *prr = (double *)(ab + o_prr), *pbb = (double *)(ab + o_pbb);
+    double2 *hist = (double2 *)(ab + o_hist);
+    GridBar *gb = (GridBar *)(ab + o_gb);
+
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<TS>, kThreads, 0) != cudaSuccess)
+        per_sm = 1;
+    per_sm = std::max(1, std::min(per_sm, 4));
+    const int G = per_sm * num_sms();
+    const long long budget = p->barrier_budget > 0 ? p->barrier_budget : 2000000000LL;
+    const int max_r = p->max_rounds > 0 ? p->max_rounds : 12;
+    CGK_TRY(m0->h_small.ensure(4096 + nh * sizeof(double2) + 64));
+    double2 *hh = (double2 *)(m0->h_small.as<char>() + 4096);
+    GridBar *hgb = (GridBar *)(hh + nh);
+    int R = sizeof(TS) == 2 ? 5 : 2;
+    for (; R <= max_r; ++R) {
+        CGK_CUDA(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+        int a_ns = nsnap, a_nf = nf, a_nr = nr, a_nc = nc, a_steps = p->nsteps, a_R = R, a_mm = mmax;
+        long long a_budget = budget;
+        void *args[] = {&dsd, &a_ns, &a_nf, &dri, &a_nr, &dci, &a_nc, &a_steps, &a_R, &a_mm,
+                        &prr, &pbb, &gb, &a_budget};
+        double bytes = 0.0;
+        for (const auto &d : descs)
+            bytes += (double)d.g.n * nf *
+                     (16.0 + p->nsteps * ((8 + 2 * sizeof(TS)) +
+                                          R * ((24 + 3 * sizeof(TS)) + (d.m - 1) * 4.0 * sizeof(TS))));
+        CGK_LAUNCH(sizeof(TS) == 2 ? "batched_bf16" : "batched_fp32", bytes, st,
+                   CGK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batched<TS>, dim3(G),
+                                                        dim3(TX, TY), args, 0, st)));
+        CGK_LAUNCH("batched_hist", 16.0 * p->nsteps * nr, st,
+                   k_batched_hist<<<(unsigned)nh, kThreads, 0, st>>>(
+                       (const int *)(ab + o_fi), nsnap, nf, nr, prr, pbb, hist));
+        CGK_CUDA(cudaGetLastError());
+        CGK_CUDA(cudaMemcpyAsync(hh, hist, nh * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CGK_CUDA(cudaMemcpyAsync(hgb, gb, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+        CGK_CUDA(cudaStreamSynchronize(st));
+        if (hgb->err)
+            return fail(CG_ETIMEOUT, "cg_diffuse_batched: a grid barrier of the persistent kernel gave up");
+        bool ok = true;
+        double worst = 0.0;
+        for (size_t i = 0; i < nh; ++i) {
+            ok = ok && (hh[i].x <= tol2 * hh[i].y);
+            worst = std::max(worst, hh[i].y > 0 ? std::sqrt(hh[i].x / hh[i].y) : 0.0);
+        }
+        if (ok || R == max_r) {
+            CGK_LAUNCH("batched_final", 16.0 * cells_total * nf, st,
+                       k_batched_final<TS><<<dim3(num_sms() * 2, nsnap), kThreads, 0, st>>>(
+                           dsd, nf, (double *const *)(ab + o_out)));
+            CGK_CUDA(cudaGetLastError());
+            CGK_CUDA(cudaStreamSynchronize(st));
+            if (rep) {
+                long long apps = 0, upd = 0;
+                for (const auto &d : descs) {
+                    long long a = (long long)p->nsteps * (1 + (long long)R * d.m);
+                    apps += a;
+                    upd += a * d.g.n;
+                }
+                rep->iters = apps * nf;
+                rep->refine_rounds = (long long)p->nsteps * R * nsnap;
+                rep->cell_updates = upd * nf;
+                rep->final_rel_residual = worst;
+                rep->inner_iters_per_round = mmax;
+            }
+            if (!ok) return fail(CG_ENOCONV, "cg_diffuse_batched: refinement did not reach tol");
+            return CG_OK;
+        }
+    }
+    return fail(CG_ENOCONV, "cg_diffuse_batched: refinement did not reach tol");
+}
+
+cg_status diffuse_batched_run(int nsnap, cg_mesh *const *meshes, int nf, double *const *cells,
+                              const cg_params *p, const double *bandwidths, cg_report *rep,
+                              cudaStream_t st) {
+    if (p->precision == CG_PREC_FP32_DF_REFINE)
+        return diffuse_batched_df<float>(nsnap, meshes, nf, cells, p, bandwidths, rep, st);
+    return diffuse_batched_df<__nv_bfloat16>(nsnap, meshes, nf, cells, p, bandwidths, rep, st);
 }
 
 }  // namespace cgk

@@ -1,0 +1,126 @@
+"""GPU parity of batched snapshots (one persistent launch for all snapshots, steps and
+fields) against the FP64 oracle and against the single-mesh path, through the C ABI.
+
+Bars: mixed modes <= 1e-6 max-relative error per snapshot and field against the oracle;
+mass conserved to 1e-12 of sum |w| per field; the persistent kernel's grid barrier gives
+up with CG_ETIMEOUT when its wait budget runs out.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1409_0001_gb300 as cg
+    from paper_1409_0001_gb300 import build
+    build.build()
+    cg.load_library()
+    return cg
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def maxrel(u, ref):
+    u, ref = np.atleast_2d(u), np.atleast_2d(ref)
+    return max(np.max(np.abs(u[f] - ref[f])) / max(np.max(np.abs(ref[f])), 1e-300)
+               for f in range(ref.shape[0]))
+
+
+def small_batch():
+    cases = W.batched_snapshots(n_snap=6, side_lo=13, side_hi=40, logn_lo=3.0, logn_hi=4.3, seed=31)
+    cases[0].dims = (24, 24, 24)          # sides that are multiples of 4 (vectorised sweeps)
+    cases[0].dx = 1.0 / 24
+    cases[0].b = 3.0 / 24
+    cases[1].dims = (40, 40, 40)
+    cases[1].dx = 1.0 / 40
+    cases[1].b = 3.0 / 40
+    return cases
+
+
+@pytest.mark.parametrize("precision,scheme", [(3, 0), (4, 0), (3, 1)])
+def test_batched_matches_oracle_per_snapshot(cg, orc, precision, scheme):
+    cases = small_batch()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    bws = [c.b for c in cases]
+    out, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=precision,
+                                                                 scheme=scheme),
+                                       bandwidths=bws, report=True)
+    for c, o in zip(cases, out):
+        _, ref, nout, _ = orc.coarse_grain_structured(c.dims, c.origin, c.dx, c.pos, c.w, c.b,
+                                                      c.nsteps, scheme=scheme)
+        assert nout == 0
+        assert maxrel(o.cpu().numpy(), ref) <= MIXED_TOL
+    scale = np.array([sum(np.abs(c.w[f]).sum() for c in cases) for f in range(5)])
+    m_in, m_out = np.array(rep["mass_in"][:5]), np.array(rep["mass_out"][:5])
+    assert np.all(np.abs(m_out - m_in) <= 1e-12 * scale)
+    assert rep["final_rel_residual"] <= 1e-13
+
+
+def test_batched_agrees_with_single_mesh_path(cg):
+    cases = small_batch()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    bws = [c.b for c in cases]
+    out = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3), bandwidths=bws)
+    for m, p_, w_, b, o in zip(meshes, pos, w, bws, out):
+        single = cg.coarse_grain(m, p_, w_, cg.Params(bandwidth=b, nsteps=10, precision=0))
+        assert maxrel(o.cpu().numpy(), single.cpu().numpy()) <= 1e-10
+
+
+def test_batched_full_size_64_snapshots(cg, orc):
+    """64 snapshots, cube sides 32..96, 10^4..10^6 particles, 5 fields, b = 3 dx, one
+    persistent launch; three snapshots checked against the oracle."""
+    cases = W.batched_snapshots()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    out, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3),
+                                       bandwidths=[c.b for c in cases], report=True)
+    scale = np.array([sum(np.abs(c.w[f]).sum() for c in cases) for f in range(5)])
+    assert np.all(np.abs(np.array(rep["mass_out"][:5]) - np.array(rep["mass_in"][:5])) <= 1e-12 * scale)
+    assert rep["final_rel_residual"] <= 1e-13
+    for s in (0, 17, 63):
+        c = cases[s]
+        _, ref, _, _ = orc.coarse_grain_structured(c.dims, c.origin, c.dx, c.pos, c.w, c.b, c.nsteps)
+        assert maxrel(out[s].cpu().numpy(), ref) <= MIXED_TOL
+
+
+def test_batched_barrier_timeout(cg):
+    cases = small_batch()[:3]
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    with pytest.raises(cg.CGError) as e:
+        cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=2, precision=3, barrier_budget=1),
+                                bandwidths=[c.b for c in cases])
+    assert e.value.code == "CG_ETIMEOUT"
+    out = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=2, precision=3),
+                                  bandwidths=[c.b for c in cases])
+    assert all(np.isfinite(o.cpu().numpy()).all() for o in out)
+
+
+def test_batched_rejects_shared_meshes_and_tets(cg):
+    m = cg.StructuredMesh((8, 8, 8), (0, 0, 0), 0.125)
+    cells = [dev(np.zeros((1, 512))), dev(np.zeros((1, 512)))]
+    with pytest.raises(cg.CGError) as e:
+        cg.diffuse_batched([m, m], cells, cg.Params(bandwidth=0.2, precision=3))
+    assert e.value.code == "CG_EINVAL"
+    xyz, tets = W.kuhn_tet_mesh(2)
+    t = cg.TetMesh(xyz, tets)
+    with pytest.raises(cg.CGError):
+        cg.diffuse_batched([t], [dev(np.zeros((1, t.ncells)))], cg.Params(bandwidth=0.2, precision=3))
