@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n-particles", type=int, default=2_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the tet, batched and channel workloads")
     return ap.parse_args()
 
 
@@ -343,6 +345,9 @@ def main():
                 "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kern.values())}
 
     line = None
+    ext = None
+    if rank == 0 and not a.no_extras:
+        ext = extras()
     if rank == 0:
         cpu = None
         if not a.no_cpu_baseline and ws == 1:
@@ -375,6 +380,7 @@ def main():
             "modes": modes,
             "mixed_speedup_vs_fp64_gpu": modes["fp64_cg"]["ms_per_step"] / (ms / a.steps),
             "profiled_ms_per_step": ms_prof / a.steps,
+            "other_workloads": ext,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                             "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                         for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])},
@@ -383,6 +389,113 @@ def main():
     mesh.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _timed_call(fn, reps=2, warm=1):
+    """Device time (CUDA events on the current stream) of fn(), best of reps."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    best = None
+    out = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best, out
+
+
+def extras():
+    """The other workloads of the method, each measured the same way (whole method per
+    call, CUDA events, best of 2 after a warm-up call), mixed vs FP64 GPU."""
+    import torch
+    import paper_1409_0001_gb300 as cg
+    import workloads as W
+
+    def maxrel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+
+    res = {}
+    # unstructured: 100^3 hexes -> 6,000,000 jittered Kuhn tets, 5,000,000 layered spheres
+    xyz, tets = W.kuhn_tet_mesh(100)
+    mesh = cg.TetMesh(xyz, tets)
+    pos, w, _ = W.layered_cube()
+    dp, dw = torch.from_numpy(pos).cuda(), torch.from_numpy(w).cuda()
+    out = {}
+    for name, prec in (("fp32_fp64refine", cg.PREC_FP32_REFINE), ("fp64_pcg", cg.PREC_FP64)):
+        ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
+            bandwidth=0.03, nsteps=10, precision=prec), report=True))
+        out[name] = (ms, u.clone(), rep)
+    res["tet_layered_6M"] = {
+        "workload": "100^3 hexes -> 6,000,000 jittered Kuhn tets (two-point-flux FV), 5,000,000 "
+                    "spheres d=0.003 with a dense bottom layer, b=0.03, 10 IE steps",
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
+                      "cell_pseudo_steps_per_s": 10 * 6e6 / (v[0] * 1e-3)} for k, v in out.items()},
+        "particles_per_s": 5e6 / (out["fp32_fp64refine"][0] * 1e-3),
+        "mixed_speedup_vs_fp64_gpu": out["fp64_pcg"][0] / out["fp32_fp64refine"][0],
+        "mixed_vs_fp64_maxrel": maxrel(out["fp32_fp64refine"][1], out["fp64_pcg"][1])}
+    mesh.close()
+    del dp, dw
+    # batched: 64 snapshots, 32^3..96^3, 10^4..10^6 particles, 5 fields, one persistent launch
+    cases = W.batched_snapshots()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    bp = [torch.from_numpy(c.pos).cuda() for c in cases]
+    bw = [torch.from_numpy(c.w).cuda() for c in cases]
+    bands = [c.b for c in cases]
+    ms_b, (ub, rep_b) = _timed_call(lambda: cg.coarse_grain_batched(
+        meshes, bp, bw, cg.Params(nsteps=10, precision=cg.PREC_FP32_DF_REFINE),
+        bandwidths=bands, report=True))
+    ub = [u.clone() for u in ub]
+
+    def loop64():
+        outs, upd = [], 0
+        for m, p_, w_, b in zip(meshes, bp, bw, bands):
+            u, r = cg.coarse_grain(m, p_, w_, cg.Params(bandwidth=b, nsteps=10,
+                                                         precision=cg.PREC_FP64), report=True)
+            outs.append(u)
+            upd += r["cell_updates"]
+        return outs, upd
+    ms_f, (uf, upd_f) = _timed_call(loop64, reps=1)
+    ncell = sum(c.ncells for c in cases)
+    res["batched_64"] = {
+        "workload": "64 snapshots, cube sides U{32..96} (%d cells), round(10^U(4,6)) particles "
+                    "(%d), 5 fields, b=3dx, 10 IE steps" % (ncell, sum(c.n for c in cases)),
+        "ms": ms_b, "cell_updates_per_s": rep_b["cell_updates"] / (ms_b * 1e-3),
+        "cell_pseudo_steps_per_s": 5 * 10 * ncell / (ms_b * 1e-3),
+        "particles_per_s": sum(c.n for c in cases) / (ms_b * 1e-3),
+        "fp64_cg_loop_ms": ms_f, "fp64_cg_loop_cell_updates_per_s": upd_f / (ms_f * 1e-3),
+        "speedup_vs_fp64_gpu_loop": ms_f / ms_b,
+        "maxrel_vs_fp64_gpu": max(maxrel(a, b) for a, b in zip(ub, uf))}
+    for m in meshes:
+        m.close()
+    del bp, bw, ub, uf
+    # channel: 512x256x256 over 4x2x2, 50,000,000 spheres, b = 4 dx, 40 IE steps
+    ch = W.channel()
+    mesh = cg.StructuredMesh(ch.dims, ch.origin, ch.dx)
+    dp, dw = torch.from_numpy(ch.pos).cuda(), torch.from_numpy(ch.w).cuda()
+    out = {}
+    for name, prec, reps in (("bf16_dfrefine", cg.PREC_BF16_DF_REFINE, 2),
+                             ("fp32_dfrefine", cg.PREC_FP32_DF_REFINE, 2),
+                             ("fp64_cg", cg.PREC_FP64, 1)):
+        ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
+            bandwidth=ch.b, nsteps=ch.nsteps, precision=prec), report=True), reps=reps)
+        out[name] = (ms, u.clone(), rep)
+    res["channel_512x256x256"] = {
+        "workload": "512x256x256 over 4x2x2, 50,000,000 spheres d=0.004, density 1+0.5 sin(2 pi x), "
+                    "b=4dx, 40 IE steps",
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
+                      "cell_pseudo_steps_per_s": 40 * ch.ncells / (v[0] * 1e-3),
+                      "maxrel_vs_fp64_gpu": maxrel(v[1], out["fp64_cg"][1])}
+                  for k, v in out.items()},
+        "particles_per_s": ch.n / (out["bf16_dfrefine"][0] * 1e-3)}
+    mesh.close()
+    return res
 
 
 def cpu_baseline(c, outs, fp64_out):

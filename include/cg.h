@@ -120,8 +120,11 @@ typedef struct {
                            (FP64 residual); default 1e-13 */
     int max_iter;       /* FP64 CG: iteration cap per step; mixed: inner iteration cap */
     int max_rounds;     /* mixed: refinement-round cap per step (default 12) */
-    int fused_k;        /* mixed, structured: inner iterations fused per sweep (0 = auto) */
-    int reserved0;
+    int fused_k;        /* reserved (0) */
+    int sweep_shape;    /* hex Chebyshev sweep shape: 0 = autotuned per mesh (default);
+                           100 + z = vectorised, 4 x-cells per thread, z planes per block
+                           (needs nx % 4 == 0); 2, 4, 8 = register-blocked planes per
+                           block; -z = z-marching, z planes per block */
     long long barrier_budget; /* > 0: run each structured inner solve as one persistent
                                  cooperative launch whose grid barriers give up after this
                                  many clock cycles of waiting (then CG_ETIMEOUT); 0: one

@@ -36,7 +36,7 @@ class CgParams(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("precision", ctypes.c_int),
                 ("deposit_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("max_rounds", ctypes.c_int),
-                ("fused_k", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("fused_k", ctypes.c_int), ("sweep_shape", ctypes.c_int),
                 ("barrier_budget", ctypes.c_longlong)]
 
 
@@ -145,13 +145,14 @@ class Params:
     max_iter: int = 10000
     max_rounds: int = 12
     fused_k: int = 0
+    sweep_shape: int = 0
     barrier_budget: int = 0
 
     def to_c(self) -> CgParams:
         p = CgParams()
         load_library().cg_params_default(ctypes.byref(p))
         for k in ("bandwidth", "T", "nsteps", "scheme", "precision", "deposit_mode", "tol",
-                  "max_iter", "max_rounds", "fused_k", "barrier_budget"):
+                  "max_iter", "max_rounds", "fused_k", "sweep_shape", "barrier_budget"):
             setattr(p, k, getattr(self, k))
         return p
 

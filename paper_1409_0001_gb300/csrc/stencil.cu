@@ -22,6 +22,7 @@
 //    eigenvalues).  Chebyshev needs no inner products, only stencil sweeps.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -656,18 +657,22 @@ __global__ void k_from_df(size_t n, const DF *__restrict__ x, double *__restrict
 }
 
 // The refinement pass of k_refine in double-float arithmetic (same roles of the
-// arguments; x, b are double-float vectors).
-template <class TS, bool kFirst>
+// arguments; x, b are double-float vectors).  kMode 0: the first pass of a step; 1: a
+// refinement pass; 2: a step's last refinement pass, which also starts the next step:
+// with x = u^{n+1} it has A x at hand, so the next step's first residual is
+// c L x = (x - A x) / theta (theta = 1 implicit Euler, 1/2 Crank-Nicolson), written to
+// r and y1 (and the next Crank-Nicolson right-hand side x + c/2 L x to bout).  Its
+// ||b||^2 goes to sc_next, the finished step's ||r||^2 to sc.
+template <class TS, int kMode>
 __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc, CoefDF cf,
                                                         int scheme, const DF *__restrict__ xin_all,
                                                         const TS *__restrict__ d_all,
-                                                        const DF *__restrict__ b_all,
-                                                        DF *__restrict__ xout_all,
-                                                        DF *__restrict__ bout_all,
-                                                        TS *__restrict__ r_all,
+                                                        const DF *b_all, DF *__restrict__ xout_all,
+                                                        DF *bout_all, TS *__restrict__ r_all,
                                                         TS *__restrict__ y1_all, float gamma,
                                                         double *__restrict__ partials_all,
-                                                        RefScal *__restrict__ sc) {
+                                                        RefScal *__restrict__ sc,
+                                                        RefScal *__restrict__ sc_next) {
     chain_wait();
     chain_release();
     const BlockPos bp = block_pos(g, zlen, nzc);
@@ -678,7 +683,7 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
     float rr = 0.0f, bb = 0.0f;
     __shared__ DF sdg[8];
     stage_table(sdg, cf.dg);
-    if (kFirst) {
+    if (kMode == 0) {
         sweep25<DF>(
             g, bp.z0, bp.z1, [&](int k) { return xin[k]; },
             [&](int k, DF v, DF s, int nn) {
@@ -705,21 +710,37 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
             [&](int k) { return b[k]; },
             [&](int k, DF v, DF s, int nn, DF bk) {
                 xout[k] = v;
-                DF rk = bk - (df_mul(sdg[nn], v) - df_mul(cf.ce, s));
-                float rf = df_f(rk);
-                st(r, k, rf);
-                st(y1, k, gamma * rf);
+                DF ax = df_mul(sdg[nn], v) - df_mul(cf.ce, s);
+                float rf = df_f(bk - ax);
                 rr = fmaf(rf, rf, rr);
+                if (kMode == 1) {
+                    st(r, k, rf);
+                    st(y1, k, gamma * rf);
+                } else {
+                    DF cl = v - ax;                    // = theta c L v
+                    DF bn = v;
+                    if (scheme == 1) {
+                        bn = v + cl;                  // v + c/2 L v
+                        cl = cl + cl;                 // c L v
+                        bout_all[off + k] = bn;
+                    }
+                    float bf = df_f(bn);
+                    bb = fmaf(bf, bf, bb);
+                    float nf_ = df_f(cl);
+                    st(r, k, nf_);
+                    st(y1, k, gamma * nf_);
+                }
             });
     }
-    double vals[2] = {block_sum((double)rr), kFirst ? block_sum((double)bb) : 0.0};
+    double vals[2] = {block_sum((double)rr), kMode != 1 ? block_sum((double)bb) : 0.0};
     double *partials = partials_all + (size_t)bp.f * 2 * bp.nb;
-    if (arrive(partials, kFirst ? 2 : 1, vals, bp.bid, bp.nb, &sc[bp.f].ticket)) {
+    if (arrive(partials, kMode != 1 ? 2 : 1, vals, bp.bid, bp.nb, &sc[bp.f].ticket)) {
         double RR = finish_sum(partials, 0, bp.nb);
-        double BB = kFirst ? finish_sum(partials, 1, bp.nb) : 0.0;
+        double BB = kMode != 1 ? finish_sum(partials, 1, bp.nb) : 0.0;
         if (is_thread0()) {
             sc[bp.f].rr = RR;
-            if (kFirst) sc[bp.f].bb = BB;
+            if (kMode == 0) sc[bp.f].bb = BB;
+            if (kMode == 2) sc_next[bp.f].bb = BB;
             sc[bp.f].ticket = 0;
         }
     }
@@ -1375,23 +1396,34 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_code = v4 ? 102 : 8;
+    // median of 8 timed launches per shape (after 2 warm-up launches); the vectorised
+    // shape is kept unless another is more than 3 % faster
+    std::vector<std::pair<float, int>> timing;
     for (int code : cands) {
-        float tot = 0.f;
-        for (int rep = 0; rep < 4; ++rep) {
+        std::vector<float> t;
+        for (int rep = 0; rep < 10; ++rep) {
             cudaEventRecord(e0, st);
             launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, st);
             cudaEventRecord(e1, st);
             CGK_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;   // the first launch warms up
+            if (rep >= 2) t.push_back(ms);
         }
-        if (tot < best) {
-            best = tot;
-            best_code = code;
-        }
+        std::sort(t.begin(), t.end());
+        timing.push_back({0.5f * (t[3] + t[4]), code});
+    }
+    std::sort(timing.begin(), timing.end());
+    int best_code = timing[0].second;
+    if (v4) {
+        float best_v4 = 1e30f;
+        int code_v4 = 0;
+        for (auto &tc : timing)
+            if (tc.second >= 100 && tc.first < best_v4) {
+                best_v4 = tc.first;
+                code_v4 = tc.second;
+            }
+        if (code_v4 && best_v4 <= 1.03f * timing[0].first) best_code = code_v4;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1595,8 +1627,13 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     RefScal *hsc = (RefScal *)(m->h_small.as<char>() + 4096);
     GridBar *hgb = (GridBar *)((char *)hsc + 64 * sizeof(RefScal));
 
-    int cheb_code = 0;
-    CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, R, st, &cheb_code));
+    int cheb_code = p->sweep_shape;
+    if (cheb_code >= 100 && (m->nx % 4 != 0 || cheb_code - 100 < 1))
+        return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0 and at least one plane", cheb_code);
+    if (cheb_code != 0 && cheb_code != 2 && cheb_code != 4 && cheb_code != 8 && cheb_code > -1 &&
+        cheb_code < 100)
+        return fail(CG_EINVAL, "unknown sweep_shape %d", cheb_code);
+    if (cheb_code == 0) CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, R, st, &cheb_code));
 
     // ---- double-float modes: a fixed schedule captured as a CUDA graph.  The whole call
     // (conversion, every step's passes and inner iterations, R refinement rounds per
@@ -1663,16 +1700,20 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                k_to_df<<<stencil_grid(n * nf), kThreads, 0, cs>>>(
                                    (size_t)n * nf, cells, (DF *)X0));
                     XT *u = X0, *f1 = X1, *f2 = X2;
+                    TS *y1_start = Ya;
                     for (int s2 = 0; s2 < p->nsteps; ++s2) {
                         RefScal *slot = hist + (size_t)s2 * nf;
                         const XT *bp_ = cn ? B : u;
-                        TS *y1 = Ya;
-                        CGK_LAUNCH("refine_df_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), cs,
-                                   launch_chain(k_refine_df<TS, true>, sw.grid, blk, cs, g, sw.zlen,
-                                                sw.nzc, cfdf, p->scheme, (const DF *)u,
-                                                (const TS *)nullptr, (const DF *)nullptr,
-                                                (DF *)nullptr, (DF *)B, R_, y1, (float)gamma,
-                                                partials, slot));
+                        TS *y1 = y1_start;
+                        // the first step starts with its own pass; later steps were started
+                        // by the previous step's last pass
+                        if (s2 == 0)
+                            CGK_LAUNCH("refine_df_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), cs,
+                                       launch_chain(k_refine_df<TS, 0>, sw.grid, blk, cs, g, sw.zlen,
+                                                    sw.nzc, cfdf, p->scheme, (const DF *)u,
+                                                    (const TS *)nullptr, (const DF *)nullptr,
+                                                    (DF *)nullptr, (DF *)B, R_, y1, (float)gamma,
+                                                    partials, slot, slot));
                         XT *xc = u;
                         for (int r = 0; r < R; ++r) {
                             TS *yc = y1, *yp = nullptr, *yo = (y1 == Ya) ? Yb : Ya;
@@ -1690,13 +1731,25 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                 yc = yn;
                             }
                             XT *xn = (xc == f1) ? f2 : f1;
+                            // the next step's first Chebyshev iterate goes to Ya: it must not
+                            // be the buffer holding this round's correction
+                            const bool emit = (r == R - 1) && (s2 + 1 < p->nsteps);
                             y1 = (yc == Ya) ? Yb : Ya;
-                            CGK_LAUNCH("refine_df", (double)n * nf * (24 + 3 * sizeof(TS)), cs,
-                                       launch_chain(k_refine_df<TS, false>, sw.grid, blk, cs, g,
-                                                    sw.zlen, sw.nzc, cfdf, p->scheme,
-                                                    (const DF *)xc, (const TS *)yc,
-                                                    (const DF *)bp_, (DF *)xn, (DF *)nullptr, R_,
-                                                    y1, (float)gamma, partials, slot));
+                            if (emit) y1_start = y1;    // where the next step's y1 is
+                            if (emit)
+                                CGK_LAUNCH("refine_df_last", (double)n * nf * (24 + 3 * sizeof(TS) + (cn ? 8 : 0)), cs,
+                                           launch_chain(k_refine_df<TS, 2>, sw.grid, blk, cs, g,
+                                                        sw.zlen, sw.nzc, cfdf, p->scheme,
+                                                        (const DF *)xc, (const TS *)yc,
+                                                        (const DF *)bp_, (DF *)xn, (DF *)B, R_, y1,
+                                                        (float)gamma, partials, slot, slot + nf));
+                            else
+                                CGK_LAUNCH("refine_df", (double)n * nf * (24 + 3 * sizeof(TS)), cs,
+                                           launch_chain(k_refine_df<TS, 1>, sw.grid, blk, cs, g,
+                                                        sw.zlen, sw.nzc, cfdf, p->scheme,
+                                                        (const DF *)xc, (const TS *)yc,
+                                                        (const DF *)bp_, (DF *)xn, (DF *)nullptr,
+                                                        R_, y1, (float)gamma, partials, slot, slot));
                             xc = xn;
                         }
                         XT *old_u = u, *other = (xc == f1) ? f2 : f1;
@@ -1740,7 +1793,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                 CGK_CUDA(cudaGetLastError());
                 CGK_CUDA(cudaStreamSynchronize(st));
                 if (rep) {
-                    long long apps = (long long)p->nsteps * (1 + (long long)R * m_it);
+                    long long apps = 1 + (long long)p->nsteps * R * m_it;
                     rep->iters = apps * nf;
                     rep->refine_rounds = (long long)p->nsteps * R;
                     rep->cell_updates = apps * nf * (long long)n;
@@ -1784,9 +1837,9 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
         TS *y1buf = Ya;
         if constexpr (kDF)
             CGK_LAUNCH("refine_df_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), st,
-                       (k_refine_df<TS, true><<<sw.grid, blk, 0, st>>>(
+                       (k_refine_df<TS, 0><<<sw.grid, blk, 0, st>>>(
                            g, sw.zlen, sw.nzc, cfdf, p->scheme, ubuf, nullptr, nullptr, nullptr, B,
-                           R, y1buf, (float)gamma, partials, sc)));
+                           R, y1buf, (float)gamma, partials, sc, sc)));
         else
             CGK_LAUNCH("refine64_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), st,
                        (k_refine<TS, true><<<sw.grid, blk, 0, st>>>(
@@ -1842,9 +1895,9 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             y1buf = (ycur == Ya) ? Yb : Ya;
             if constexpr (kDF)
                 CGK_LAUNCH("refine_df", (double)n * nf * (24 + 3 * sizeof(TS)), st,
-                           (k_refine_df<TS, false><<<sw.grid, blk, 0, st>>>(
+                           (k_refine_df<TS, 1><<<sw.grid, blk, 0, st>>>(
                                g, sw.zlen, sw.nzc, cfdf, p->scheme, xcur, ycur, bptr, xnext,
-                               nullptr, R, y1buf, (float)gamma, partials, sc)));
+                               nullptr, R, y1buf, (float)gamma, partials, sc, sc)));
             else
                 CGK_LAUNCH("refine64", (double)n * nf * (24 + 3 * sizeof(TS)), st,
                            (k_refine<TS, false><<<sw.grid, blk, 0, st>>>(

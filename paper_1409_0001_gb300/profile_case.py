@@ -28,6 +28,7 @@ def main(argv=None):
     ap.add_argument("--nfields", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tet", action="store_true", help="Kuhn tet mesh of n^3 hexes instead")
+    ap.add_argument("--shape", type=int, default=0, help="sweep_shape (0 = autotuned)")
     a = ap.parse_args(argv)
 
     import numpy as np
@@ -47,7 +48,8 @@ def main(argv=None):
         mesh = cg.StructuredMesh(dims, (0.0, 0.0, 0.0), dx)
     rng = np.random.default_rng(0)
     u0 = torch.from_numpy(rng.random((a.nfields, mesh.ncells))).cuda()
-    p = cg.Params(bandwidth=a.b_over_dx * dx, nsteps=a.nsteps, precision=a.precision)
+    p = cg.Params(bandwidth=a.b_over_dx * dx, nsteps=a.nsteps, precision=a.precision,
+                  sweep_shape=a.shape)
     for r in range(a.reps):
         u = u0.clone()
         torch.cuda.synchronize()
