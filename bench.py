@@ -125,6 +125,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def ncu_traffic(kernel_entry):
+    """DRAM bytes per launch of a kernel from the committed ncu capture, or None when the
+    kernel's source changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f).get(kernel_entry)
+        if not rec:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        return rec["dram_bytes_per_launch"] if sha == rec["source_sha256"] else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -339,7 +355,8 @@ def main():
         achieved = k["bytes"] / (k["ms"] * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(name),
+                "algorithmic_bytes_per_launch": k["bytes"] / k["launches"],
                 "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
                 "avg_launch_us": k["ms"] * 1e3 / k["launches"],
                 "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kern.values())}

@@ -104,6 +104,7 @@ struct Pending {
     cudaEvent_t a, b;
     int entry;
     double bytes;
+    int count;
 };
 std::mutex g_prof_mu;
 std::atomic<bool> g_prof_enabled{false};
@@ -157,7 +158,7 @@ void prof_account_replay(const GraphEntry &e) {
             continue;
         }
         ProfEntry &pe = g_prof[prof_entry(r.name)];
-        pe.launches += 1;
+        pe.launches += r.count;
         pe.ms += ms;
         pe.bytes += r.bytes;
     }
@@ -173,34 +174,38 @@ void graph_release(GraphEntry &e) {
     e.records.clear();
 }
 
-ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : st(s) {
+ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s, int count,
+                     bool counts_launch)
+    : st(s) {
     if (t_sink_kernels) {
-        ++*t_sink_kernels;
-        if (t_sink && prof_on()) {
-            ProfRecord r{name, bytes, nullptr, nullptr};
+        if (counts_launch) ++*t_sink_kernels;
+        if (name && t_sink && prof_on()) {
+            ProfRecord r{name, bytes, nullptr, nullptr, count};
             cudaEventCreate(&r.a);
             cudaEventCreate(&r.b);
             // inside a capture only an "external" record becomes a timing node
             cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
             t_sink->push_back(r);
-            slot = -2;   // end event recorded by the destructor
+            slot = (int)t_sink->size() - 1;
+            slot = -2 - slot;   // records in the sink are addressed as -2 - index
         }
         return;
     }
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!prof_on()) return;
+    if (counts_launch) g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!name || !prof_on()) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     int entry = prof_entry(name);
-    Pending pe{pool_get(), pool_get(), entry, bytes};
+    Pending pe{pool_get(), pool_get(), entry, bytes, count};
     cudaEventRecord(pe.a, st);
     g_pending.push_back(pe);
     slot = (int)g_pending.size() - 1;
 }
 
 ProfScope::~ProfScope() {
-    if (slot == -2) {
-        if (t_sink && !t_sink->empty())
-            cudaEventRecordWithFlags(t_sink->back().b, st, cudaEventRecordExternal);
+    if (slot <= -2) {
+        const size_t i = (size_t)(-2 - slot);
+        if (t_sink && i < t_sink->size())
+            cudaEventRecordWithFlags((*t_sink)[i].b, st, cudaEventRecordExternal);
         return;
     }
     if (slot < 0) return;
@@ -216,7 +221,7 @@ void prof_collect() {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, pe.a, pe.b);
         ProfEntry &e = g_prof[pe.entry];
-        e.launches += 1;
+        e.launches += pe.count;
         e.ms += ms;
         e.bytes += pe.bytes;
         g_event_pool.push_back(pe.a);

@@ -4,9 +4,9 @@
 //
 // Ordered mode reproduces a sequential loop over particles bit for bit: the
 // (cell, particle) pairs are put in cell order by a stable LSD radix sort on the
-// cell id (particle order is kept inside a cell), and one thread per cell adds its
-// segment's weights in that order, in FP64 starting from +0.0, then divides by V_c
-// with an IEEE division.  Fixed-point mode quantises w * 2^F to int64 (round half to
+// cell id (particle order is kept inside a cell), and the first position of each
+// cell's segment adds the segment's weights in that order, in FP64 starting from
+// +0.0, then divides by V_c with an IEEE division.  Fixed-point mode quantises w * 2^F to int64 (round half to
 // even) and adds with 64-bit integer atomics, which is exact and order-free.
 #include <cuda_runtime.h>
 #include <cmath>
@@ -248,22 +248,26 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(
 }
 
 // --------------------------------------------------------------------------- sums
-// One thread per cell: S = +0.0; S += w[f][idx] over the cell's segment in ascending
-// particle index; eps = S / V_c.
-__global__ void k_segment_sum(int64_t ncells, const uint32_t *__restrict__ start,
-                              const uint32_t *__restrict__ counts,
-                              const uint32_t *__restrict__ sorted_idx, int nf,
-                              const double *__restrict__ w, int64_t n,
-                              const double *__restrict__ vc, double vc_uniform,
-                              double *__restrict__ out) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t s = start[c], e = s + counts[c];
-        double v = vc ? vc[c] : vc_uniform;
+// One thread per position p of the cell-sorted particle list; the first position of
+// each cell's segment sums the segment's weights in ascending particle index (FP64,
+// from +0.0) and writes eps = S / V_c.  Cells without particles keep the +0.0 the
+// output was cleared to (0.0 / V_c = +0.0).
+__global__ void k_segment_heads(int64_t n, const uint32_t *__restrict__ keys,
+                                const uint32_t *__restrict__ sorted_idx, int nf,
+                                const double *__restrict__ w, int64_t ncells,
+                                const double *__restrict__ vc, double vc_uniform,
+                                double *__restrict__ out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = keys[p];
+        if (p > 0 && keys[p - 1] == c) continue;
+        int64_t e = p + 1;
+        while (e < n && keys[e] == c) ++e;
+        const double v = vc ? vc[c] : vc_uniform;
         for (int f = 0; f < nf; ++f) {
             const double *wf = w + (int64_t)f * n;
             double acc = 0.0;
-            for (uint32_t p = s; p < e; ++p) acc = __dadd_rn(acc, wf[sorted_idx[p]]);
+            for (int64_t q = p; q < e; ++q) acc = __dadd_rn(acc, wf[sorted_idx[q]]);
             out[(int64_t)f * ncells + c] = __ddiv_rn(acc, v);
         }
     }
@@ -398,28 +402,17 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
     const double *vc = m->kind == MESH_TET ? m->tet.vc : nullptr;
     const double vcu = m->kind == MESH_TET ? 0.0 : (m->dx * m->dx) * m->dx;
 
-    // workspace: cell[n] (int32) | counts[ncells] | start[ncells] | scan tmp
-    size_t off_cell = 0;
-    size_t off_counts = align_up(off_cell + (size_t)n * 4);
-    size_t off_start = align_up(off_counts + (size_t)ncells * 4);
-    size_t off_tmp = align_up(off_start + (size_t)ncells * 4);
-    size_t need = align_up(off_tmp + scan_tmp_words(ncells) * 4);
-    CGK_TRY(m->ws_locate.ensure(need));
-    char *base = m->ws_locate.as<char>();
-    int32_t *cell = (int32_t *)(base + off_cell);
-    uint32_t *counts = (uint32_t *)(base + off_counts);
-    uint32_t *start = (uint32_t *)(base + off_start);
-    uint32_t *tmp = (uint32_t *)(base + off_tmp);
+    // workspace: cell[n] (int32)
+    CGK_TRY(m->ws_locate.ensure(align_up((size_t)(n > 0 ? n : 1) * 4)));
+    int32_t *cell = m->ws_locate.as<int32_t>();
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (rep) {
         for (auto &e : ev) CGK_CUDA(cudaEventCreate(&e));
         CGK_CUDA(cudaEventRecord(ev[0], st));
     }
-    if (mode == CG_DEPOSIT_ORDERED) CGK_CUDA(cudaMemsetAsync(counts, 0, (size_t)ncells * 4, st));
     int64_t n_out = 0, n_bad = 0;
-    CGK_TRY(locate_run(m, n, pos, nf, w, cell, mode == CG_DEPOSIT_ORDERED ? counts : nullptr,
-                       &n_out, &n_bad, st));
+    CGK_TRY(locate_run(m, n, pos, nf, w, cell, nullptr, &n_out, &n_bad, st));
     if (rep) {
         CGK_CUDA(cudaEventRecord(ev[1], st));
         rep->n_out_of_domain = n_out;
@@ -465,11 +458,13 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
                 vout = (vout == va) ? vb : va;
             }
         }
-        CGK_TRY(exclusive_scan_u32(counts, start, ncells, tmp, st));
-        CGK_LAUNCH("segment_sum", (double)n * (4 + 8 * nf) + (double)ncells * (8 + 8 * nf), st,
-                   k_segment_sum<<<grid_for(ncells), kThreads, 0, st>>>(
-                       ncells, start, counts, vin, nf, w, n, vc, vcu, out));
-        CGK_CUDA(cudaGetLastError());
+        CGK_CUDA(cudaMemsetAsync(out, 0, (size_t)ncells * nf * 8, st));
+        if (n > 0) {
+            CGK_LAUNCH("segment_heads", (double)n * (8 + 8 * nf) + (double)ncells * 8 * nf, st,
+                       k_segment_heads<<<grid_for(n), kThreads, 0, st>>>(
+                           n, kin, vin, nf, w, ncells, vc, vcu, out));
+            CGK_CUDA(cudaGetLastError());
+        }
         if (rep)
             for (int f = 0; f < nf && f < CG_REPORT_MAX_FIELDS; ++f) rep->fixed_point_bits[f] = 0;
     } else {

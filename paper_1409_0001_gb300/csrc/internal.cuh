@@ -57,6 +57,7 @@ struct ProfRecord {
     const char *name;
     double bytes;
     cudaEvent_t a, b;
+    int count;               // launches between the two events
 };
 
 // A captured diffusion (one entry per distinct call signature and buffer set).
@@ -144,7 +145,11 @@ int num_sms();
 // accumulates the elapsed times per kernel name.
 bool prof_on();
 struct ProfScope {
-    ProfScope(const char *name, double bytes, cudaStream_t st);
+    // name == nullptr: count the launch only.  count: launches the scope covers (their
+    // device time is the interval between the scope's two events).  counts_launch:
+    // the scope itself is one launch for the launch counter.
+    ProfScope(const char *name, double bytes, cudaStream_t st, int count = 1,
+              bool counts_launch = true);
     ~ProfScope();
     int slot = -1;
     cudaStream_t st = nullptr;
@@ -166,6 +171,16 @@ void graph_release(GraphEntry &e);
         ::cgk::ProfScope ps_(name, (double)(bytes), st);                        \
         __VA_ARGS__;                                                            \
     } while (0)
+
+// A launch counted but not timed on its own (it is inside a CGK_TIMED scope).
+#define CGK_LAUNCH_UNTIMED(st, ...)                                             \
+    do {                                                                        \
+        ::cgk::ProfScope ps_(nullptr, 0.0, st);                                 \
+        __VA_ARGS__;                                                            \
+    } while (0)
+
+// A timed scope over `count` launches made with CGK_LAUNCH_UNTIMED: one event pair.
+#define CGK_TIMED(var, name, bytes, st, count) ::cgk::ProfScope var(name, (double)(bytes), st, count, false)
 
 // ----------------------------------------------------------------------------- phases
 // Locate (structured or tet).  Writes cell ids (int32, -1 outside) to cell_out and the

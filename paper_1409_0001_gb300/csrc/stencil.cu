@@ -1718,17 +1718,21 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                         for (int r = 0; r < R; ++r) {
                             TS *yc = y1, *yp = nullptr, *yo = (y1 == Ya) ? Yb : Ya;
                             double om = 1.0;
-                            for (int k = 1; k < m_it; ++k) {
-                                if (sigma_d > 0.0)
-                                    om = (k == 1) ? 1.0 / (1.0 - 1.0 / (2.0 * sigma_d * sigma_d))
-                                                  : 1.0 / (1.0 - om / (4.0 * sigma_d * sigma_d));
-                                TS *yn = yp ? yp : yo;
-                                CGK_LAUNCH(sizeof(TS) == 2 ? "cheb_bf16" : "cheb_fp32",
-                                           (double)n * nf * sizeof(TS) * (yp ? 4 : 3), cs,
-                                           launch_cheb<TS>(cheb_code, g, nf, cf32, (float)gamma,
-                                                           (float)om, yc, yp, R_, yn, cs));
-                                yp = yc;
-                                yc = yn;
+                            if (m_it > 1) {
+                                CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb_bf16" : "cheb_fp32",
+                                          (double)n * nf * sizeof(TS) * (3.0 + 4.0 * (m_it - 2)),
+                                          cs, m_it - 1);
+                                for (int k = 1; k < m_it; ++k) {
+                                    if (sigma_d > 0.0)
+                                        om = (k == 1) ? 1.0 / (1.0 - 1.0 / (2.0 * sigma_d * sigma_d))
+                                                      : 1.0 / (1.0 - om / (4.0 * sigma_d * sigma_d));
+                                    TS *yn = yp ? yp : yo;
+                                    CGK_LAUNCH_UNTIMED(cs, launch_cheb<TS>(cheb_code, g, nf, cf32,
+                                                                           (float)gamma, (float)om,
+                                                                           yc, yp, R_, yn, cs));
+                                    yp = yc;
+                                    yc = yn;
+                                }
                             }
                             XT *xn = (xc == f1) ? f2 : f1;
                             // the next step's first Chebyshev iterate goes to Ya: it must not
