@@ -32,6 +32,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1409_0001_gb300.ranks import dist_env, reduce_scalar  # noqa: E402
+
 B_OVER_DX = (1.0, 2.0, 4.0, 8.0)
 NSTEPS = 10
 TOL = 1e-13
@@ -57,13 +59,6 @@ def workload_name(a):
     return ("clustered_cube_%d: %d^3 unit cube, %d spheres d=0.004 in 20 Gaussian clusters "
             "(sigma 0.05, <=8 per cell), b/dx in {1,2,4,8}, %d implicit-Euler pseudo-steps, "
             "tol 1e-13" % (a.n_side, a.n_side, a.n_particles, NSTEPS))
-
-
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
 
 
 class ClockSampler:
@@ -252,18 +247,10 @@ def main():
         return tot
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_scalar(x, "max", device="cuda")
 
     def sum_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_scalar(x, "sum", device="cuda")
 
     MAIN = cg.PREC_FP32_DF_REFINE
     # ---------------- warm-up
