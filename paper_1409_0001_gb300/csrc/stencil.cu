@@ -746,6 +746,211 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
     }
 }
 
+// The refinement pass of k_refine_df with two x-cells per thread (nx even): a float4
+// holds the two cells' double-float values, a warp row covers 64 cells; x neighbours
+// by shuffle (and two scalar loads at the tile edges), y neighbours from a shared plane,
+// z neighbours from a register queue with one-plane-ahead prefetch.  Same modes,
+// arguments and results as k_refine_df.
+template <class TS> struct Pair;
+template <> struct Pair<float> {
+    static __device__ __forceinline__ float2 load(const float *p, size_t i) {
+        return *reinterpret_cast<const float2 *>(p + i);
+    }
+    static __device__ __forceinline__ void store(float *p, size_t i, float a, float b) {
+        *reinterpret_cast<float2 *>(p + i) = make_float2(a, b);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 load(const __nv_bfloat16 *p, size_t i) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + i));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, size_t i, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162 *>(p + i) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+__device__ __forceinline__ DF lo_df(float4 v) { return DF{v.x, v.y}; }
+__device__ __forceinline__ DF hi_df(float4 v) { return DF{v.z, v.w}; }
+__device__ __forceinline__ float4 pack_df(DF a, DF b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
+__device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+template <class TS, int kMode>
+__global__ void __launch_bounds__(kThreads) k_refine_df2(Geo g, int zlen, int nzc, CoefDF cf,
+                                                         int scheme, const DF *__restrict__ xin_all,
+                                                         const TS *__restrict__ d_all,
+                                                         const DF *b_all, DF *__restrict__ xout_all,
+                                                         DF *bout_all, TS *__restrict__ r_all,
+                                                         TS *__restrict__ y1_all, float gamma,
+                                                         double *__restrict__ partials_all,
+                                                         RefScal *__restrict__ sc,
+                                                         RefScal *__restrict__ sc_next) {
+    chain_wait();
+    chain_release();
+    using PR = Pair<TS>;
+    const int f = blockIdx.z / nzc;
+    const int zc = blockIdx.z - f * nzc;
+    const int z0 = zc * zlen, z1 = min(g.nz, z0 + zlen);
+    const int bid = (zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int nb = gridDim.x * gridDim.y * nzc;
+    const size_t off = (size_t)f * g.n;
+    const float4 *X = reinterpret_cast<const float4 *>(xin_all + off);   // cell pairs
+    const TS *D = kMode == 0 ? nullptr : d_all + off;
+    const float4 *Bv = reinterpret_cast<const float4 *>((kMode == 0 ? xin_all : b_all) + off);
+    float4 *XO = reinterpret_cast<float4 *>(xout_all + off);
+    float4 *BO = reinterpret_cast<float4 *>(bout_all ? bout_all + off : nullptr);
+    TS *r = r_all + off;
+    TS *y1 = y1_all + off;
+    __shared__ float4 pl[TY + 2][TX];
+    __shared__ DF sdg[8];
+    stage_table(sdg, cf.dg);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * (2 * TX);
+    const int x = x0 + 2 * tx, y = blockIdx.y * TY + ty;
+    const bool own = (x < g.nx) && (y < g.ny);
+    const bool rowlo = (ty == 0) && (y > 0) && (x < g.nx);
+    const bool rowhi = (ty == TY - 1) && (y + 1 < g.ny) && (x < g.nx);
+    const bool xl = (tx == 0) && (x > 0) && (y < g.ny);
+    const int xlast = min(g.nx, x0 + 2 * TX) - 2;
+    const bool xr = (x == xlast) && (x + 2 < g.nx) && (y < g.ny);
+    const int nyb = (y > 0) + (y + 1 < g.ny);
+    const int n0 = nyb + (x > 0) + 1, n1 = nyb + 1 + (x + 2 < g.nx);
+    const int kxy = y * g.nx + x;
+    // stencil value of a cell pair / of one cell
+    auto val2 = [&](size_t k) -> float4 {
+        float4 xv = X[k >> 1];
+        if (kMode == 0) return xv;
+        float2 dv = PR::load(D, k);
+        return pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
+    };
+    auto val1 = [&](size_t k) -> DF {
+        DF xv = xin_all[off + k];
+        if (kMode == 0) return xv;
+        return df_add_f(xv, ld(D, (int)k));
+    };
+    float4 vdn = f4z(), vc = f4z(), vup = f4z(), bc = f4z(), hlo = f4z(), hhi = f4z();
+    DF hl = DF{0.f, 0.f}, hr = DF{0.f, 0.f};
+    float rr = 0.0f, bb = 0.0f;
+    if (z0 < z1) {
+        const size_t k0 = (size_t)kxy + (size_t)z0 * g.nxy;
+        if (own) {
+            if (z0 > 0) vdn = val2(k0 - g.nxy);
+            vc = val2(k0);
+            if (z0 + 1 < g.nz) vup = val2(k0 + g.nxy);
+            if (kMode != 0) bc = Bv[k0 >> 1];
+        }
+        if (rowlo) hlo = val2(k0 - g.nx);
+        if (rowhi) hhi = val2(k0 + g.nx);
+        if (xl) hl = val1(k0 - 1);
+        if (xr) hr = val1(k0 + 2);
+    }
+    for (int z = z0; z < z1; ++z) {
+        const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
+        float4 nup = f4z(), nb_ = f4z(), nlo = f4z(), nhi = f4z();
+        DF nl = DF{0.f, 0.f}, nr = DF{0.f, 0.f};
+        if (z + 1 < z1) {
+            const size_t kn = kz + g.nxy;
+            if (own) {
+                if (z + 2 < g.nz) nup = val2(kn + g.nxy);
+                if (kMode != 0) nb_ = Bv[kn >> 1];
+            }
+            if (rowlo) nlo = val2(kn - g.nx);
+            if (rowhi) nhi = val2(kn + g.nx);
+            if (xl) nl = val1(kn - 1);
+            if (xr) nr = val1(kn + 2);
+        }
+        pl[ty + 1][tx] = vc;
+        if (ty == 0) pl[0][tx] = hlo;
+        if (ty == TY - 1) pl[TY + 1][tx] = hhi;
+        DF left{__shfl_up_sync(0xffffffffu, vc.z, 1), __shfl_up_sync(0xffffffffu, vc.w, 1)};
+        DF right{__shfl_down_sync(0xffffffffu, vc.x, 1), __shfl_down_sync(0xffffffffu, vc.y, 1)};
+        if (tx == 0) left = hl;
+        if (x == xlast) right = hr;
+        __syncthreads();
+        if (own) {
+            const float4 up = pl[ty][tx], dn = pl[ty + 2][tx];
+            const int nz_ = (z > 0) + (z + 1 < g.nz);
+            const DF v0 = lo_df(vc), v1 = hi_df(vc);
+            DF s0 = left;
+            s0 += v1;
+            s0 += lo_df(up);
+            s0 += lo_df(dn);
+            s0 += lo_df(vdn);
+            s0 += lo_df(vup);
+            DF s1 = v0;
+            s1 += right;
+            s1 += hi_df(up);
+            s1 += hi_df(dn);
+            s1 += hi_df(vdn);
+            s1 += hi_df(vup);
+            float rf0, rf1;
+            if (kMode == 0) {
+                const DF l0 = s0 - df_mulf(v0, (float)(n0 + nz_));
+                const DF l1 = s1 - df_mulf(v1, (float)(n1 + nz_));
+                rf0 = df_f(df_mul(cf.c, l0));
+                rf1 = df_f(df_mul(cf.c, l1));
+                DF b0 = v0, b1 = v1;
+                if (scheme == 1) {
+                    b0 = v0 + df_mul(cf.half_c, l0);
+                    b1 = v1 + df_mul(cf.half_c, l1);
+                    BO[kz >> 1] = pack_df(b0, b1);
+                }
+                const float f0 = df_f(b0), f1 = df_f(b1);
+                bb = fmaf(f0, f0, fmaf(f1, f1, bb));
+                rr = fmaf(rf0, rf0, fmaf(rf1, rf1, rr));
+                PR::store(r, kz, rf0, rf1);
+                PR::store(y1, kz, gamma * rf0, gamma * rf1);
+            } else {
+                XO[kz >> 1] = vc;
+                const DF ax0 = df_mul(sdg[n0 + nz_], v0) - df_mul(cf.ce, s0);
+                const DF ax1 = df_mul(sdg[n1 + nz_], v1) - df_mul(cf.ce, s1);
+                rf0 = df_f(lo_df(bc) - ax0);
+                rf1 = df_f(hi_df(bc) - ax1);
+                rr = fmaf(rf0, rf0, fmaf(rf1, rf1, rr));
+                if (kMode == 1) {
+                    PR::store(r, kz, rf0, rf1);
+                    PR::store(y1, kz, gamma * rf0, gamma * rf1);
+                } else {
+                    DF c0 = v0 - ax0, c1 = v1 - ax1;       // theta c L v
+                    DF bn0 = v0, bn1 = v1;
+                    if (scheme == 1) {
+                        bn0 = v0 + c0;
+                        bn1 = v1 + c1;
+                        c0 = c0 + c0;
+                        c1 = c1 + c1;
+                        BO[kz >> 1] = pack_df(bn0, bn1);
+                    }
+                    const float f0 = df_f(bn0), f1 = df_f(bn1);
+                    bb = fmaf(f0, f0, fmaf(f1, f1, bb));
+                    const float q0 = df_f(c0), q1 = df_f(c1);
+                    PR::store(r, kz, q0, q1);
+                    PR::store(y1, kz, gamma * q0, gamma * q1);
+                }
+            }
+        }
+        __syncthreads();
+        vdn = vc;
+        vc = vup;
+        vup = nup;
+        bc = nb_;
+        hlo = nlo;
+        hhi = nhi;
+        hl = nl;
+        hr = nr;
+    }
+    double vals[2] = {block_sum((double)rr), kMode != 1 ? block_sum((double)bb) : 0.0};
+    double *partials = partials_all + (size_t)f * 2 * nb;
+    if (arrive(partials, kMode != 1 ? 2 : 1, vals, bid, nb, &sc[f].ticket)) {
+        double RR = finish_sum(partials, 0, nb);
+        double BB = kMode != 1 ? finish_sum(partials, 1, nb) : 0.0;
+        if (is_thread0()) {
+            sc[f].rr = RR;
+            if (kMode == 0) sc[f].bb = BB;
+            if (kMode == 2) sc_next[f].bb = BB;
+            sc[f].ticket = 0;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- grid barrier
 // A barrier over all blocks of a cooperative launch (all blocks co-resident).  The
 // wait is bounded: a block that spins longer than `budget` clock cycles raises err and
@@ -1025,7 +1230,7 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
 }
 
 template <class TS>
-__global__ void __launch_bounds__(kThreads) k_cheb_v4(Geo g, int zlen, int nzc, Coef32 cf,
+__global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nzc, Coef32 cf,
                                                       float gamma, float omega,
                                                       const TS *__restrict__ y_all,
                                                       const TS *yprev_all,
@@ -1374,6 +1579,24 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
     }
 }
 
+// A double-float refinement pass of mode kMode: the two-cells-per-thread kernel when nx
+// is even, the scalar one otherwise; both use the z-chunks of sw (same partial slots).
+template <class TS, int kMode>
+void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, int scheme,
+                      const DF *xin, const TS *d, const DF *b, DF *xout, DF *bout, TS *r, TS *y1,
+                      float gamma, double *partials, RefScal *sc, RefScal *sc_next,
+                      cudaStream_t st) {
+    const dim3 blk(TX, TY);
+    if (g.nx % 2 == 0) {
+        const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
+        launch_chain(k_refine_df2<TS, kMode>, grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
+                     d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
+    } else {
+        launch_chain(k_refine_df<TS, kMode>, sw.grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
+                     d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
+    }
+}
+
 // Autotuner of the Chebyshev sweep's shape (register-blocked with 2, 4 or 8 planes per
 // block, or z-marching with 1..32 planes per block): times a few launches of each
 // candidate on the caller's buffers (y_next is scratch at this point) and keeps the
@@ -1396,22 +1619,24 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
-    // median of 8 timed launches per shape (after 2 warm-up launches); the vectorised
-    // shape is kept unless another is more than 3 % faster
+    // per shape: 2 warm-up launches, then 3 bursts of 10 back-to-back launches timed by
+    // one event pair each, the fastest burst counts; the vectorised shape is kept
+    // unless another is more than 3 % faster
     std::vector<std::pair<float, int>> timing;
     for (int code : cands) {
-        std::vector<float> t;
-        for (int rep = 0; rep < 10; ++rep) {
+        for (int w = 0; w < 2; ++w) launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, st);
+        float best_burst = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, st);
-            launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, st);
+            for (int q = 0; q < 10; ++q)
+                launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, st);
             cudaEventRecord(e1, st);
             CGK_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep >= 2) t.push_back(ms);
+            best_burst = std::min(best_burst, ms);
         }
-        std::sort(t.begin(), t.end());
-        timing.push_back({0.5f * (t[3] + t[4]), code});
+        timing.push_back({best_burst, code});
     }
     std::sort(timing.begin(), timing.end());
     int best_code = timing[0].second;
@@ -1709,11 +1934,11 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                         // by the previous step's last pass
                         if (s2 == 0)
                             CGK_LAUNCH("refine_df_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), cs,
-                                       launch_chain(k_refine_df<TS, 0>, sw.grid, blk, cs, g, sw.zlen,
-                                                    sw.nzc, cfdf, p->scheme, (const DF *)u,
-                                                    (const TS *)nullptr, (const DF *)nullptr,
-                                                    (DF *)nullptr, (DF *)B, R_, y1, (float)gamma,
-                                                    partials, slot, slot));
+                                       launch_refine_df<TS, 0>(g, sw, nf, cfdf, p->scheme,
+                                                               (const DF *)u, (const TS *)nullptr,
+                                                               (const DF *)nullptr, (DF *)nullptr,
+                                                               (DF *)B, R_, y1, (float)gamma,
+                                                               partials, slot, slot, cs));
                         XT *xc = u;
                         for (int r = 0; r < R; ++r) {
                             TS *yc = y1, *yp = nullptr, *yo = (y1 == Ya) ? Yb : Ya;
@@ -1742,18 +1967,19 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                             if (emit) y1_start = y1;    // where the next step's y1 is
                             if (emit)
                                 CGK_LAUNCH("refine_df_last", (double)n * nf * (24 + 3 * sizeof(TS) + (cn ? 8 : 0)), cs,
-                                           launch_chain(k_refine_df<TS, 2>, sw.grid, blk, cs, g,
-                                                        sw.zlen, sw.nzc, cfdf, p->scheme,
-                                                        (const DF *)xc, (const TS *)yc,
-                                                        (const DF *)bp_, (DF *)xn, (DF *)B, R_, y1,
-                                                        (float)gamma, partials, slot, slot + nf));
+                                           launch_refine_df<TS, 2>(g, sw, nf, cfdf, p->scheme,
+                                                                   (const DF *)xc, (const TS *)yc,
+                                                                   (const DF *)bp_, (DF *)xn,
+                                                                   (DF *)B, R_, y1, (float)gamma,
+                                                                   partials, slot, slot + nf, cs));
                             else
                                 CGK_LAUNCH("refine_df", (double)n * nf * (24 + 3 * sizeof(TS)), cs,
-                                           launch_chain(k_refine_df<TS, 1>, sw.grid, blk, cs, g,
-                                                        sw.zlen, sw.nzc, cfdf, p->scheme,
-                                                        (const DF *)xc, (const TS *)yc,
-                                                        (const DF *)bp_, (DF *)xn, (DF *)nullptr,
-                                                        R_, y1, (float)gamma, partials, slot, slot));
+                                           launch_refine_df<TS, 1>(g, sw, nf, cfdf, p->scheme,
+                                                                   (const DF *)xc, (const TS *)yc,
+                                                                   (const DF *)bp_, (DF *)xn,
+                                                                   (DF *)nullptr, R_, y1,
+                                                                   (float)gamma, partials, slot,
+                                                                   slot, cs));
                             xc = xn;
                         }
                         XT *old_u = u, *other = (xc == f1) ? f2 : f1;
@@ -1841,9 +2067,10 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
         TS *y1buf = Ya;
         if constexpr (kDF)
             CGK_LAUNCH("refine_df_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), st,
-                       (k_refine_df<TS, 0><<<sw.grid, blk, 0, st>>>(
-                           g, sw.zlen, sw.nzc, cfdf, p->scheme, ubuf, nullptr, nullptr, nullptr, B,
-                           R, y1buf, (float)gamma, partials, sc, sc)));
+                       (launch_refine_df<TS, 0>(g, sw, nf, cfdf, p->scheme, (const DF *)ubuf,
+                                                (const TS *)nullptr, (const DF *)nullptr,
+                                                (DF *)nullptr, (DF *)B, R, y1buf, (float)gamma,
+                                                partials, sc, sc, st)));
         else
             CGK_LAUNCH("refine64_first", (double)n * nf * (8 + (cn ? 8 : 0) + 2 * sizeof(TS)), st,
                        (k_refine<TS, true><<<sw.grid, blk, 0, st>>>(
@@ -1899,9 +2126,10 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             y1buf = (ycur == Ya) ? Yb : Ya;
             if constexpr (kDF)
                 CGK_LAUNCH("refine_df", (double)n * nf * (24 + 3 * sizeof(TS)), st,
-                           (k_refine_df<TS, 1><<<sw.grid, blk, 0, st>>>(
-                               g, sw.zlen, sw.nzc, cfdf, p->scheme, xcur, ycur, bptr, xnext,
-                               nullptr, R, y1buf, (float)gamma, partials, sc, sc)));
+                           (launch_refine_df<TS, 1>(g, sw, nf, cfdf, p->scheme, (const DF *)xcur,
+                                                    (const TS *)ycur, (const DF *)bptr,
+                                                    (DF *)xnext, (DF *)nullptr, R, y1buf,
+                                                    (float)gamma, partials, sc, sc, st)));
             else
                 CGK_LAUNCH("refine64", (double)n * nf * (24 + 3 * sizeof(TS)), st,
                            (k_refine<TS, false><<<sw.grid, blk, 0, st>>>(
