@@ -473,6 +473,8 @@ def extras():
         "ms": ms_b, "cell_updates_per_s": rep_b["cell_updates"] / (ms_b * 1e-3),
         "cell_pseudo_steps_per_s": 5 * 10 * ncell / (ms_b * 1e-3),
         "particles_per_s": sum(c.n for c in cases) / (ms_b * 1e-3),
+        "ms_per_phase": {k: rep_b[k] for k in ("ms_locate", "ms_deposit", "ms_diffuse")},
+        "z_planes_per_item": rep_b["sweep_shape_used"],
         "fp64_cg_loop_ms": ms_f, "fp64_cg_loop_cell_updates_per_s": upd_f / (ms_f * 1e-3),
         "speedup_vs_fp64_gpu_loop": ms_f / ms_b,
         "maxrel_vs_fp64_gpu": max(maxrel(a, b) for a, b in zip(ub, uf))}

@@ -124,7 +124,8 @@ typedef struct {
     int sweep_shape;    /* hex Chebyshev sweep shape: 0 = autotuned per mesh (default);
                            100 + z = vectorised, 4 x-cells per thread, z planes per block
                            (needs nx % 4 == 0); 2, 4, 8 = register-blocked planes per
-                           block; -z = z-marching, z planes per block */
+                           block; -z = z-marching, z planes per block.  Batched calls:
+                           z planes per work item (0 = autotuned per batch shape) */
     long long barrier_budget; /* > 0: run each structured inner solve as one persistent
                                  cooperative launch whose grid barriers give up after this
                                  many clock cycles of waiting (then CG_ETIMEOUT); 0: one
@@ -148,7 +149,7 @@ typedef struct {
     long long n_out_of_domain;
     int fixed_point_bits[CG_REPORT_MAX_FIELDS];
     int inner_iters_per_round;/* mixed: Chebyshev iterations per refinement round */
-    int reserved;
+    int sweep_shape_used;     /* mixed hex: the sweep shape (or batched z planes) that ran */
 } cg_report;
 
 /* ------------------------------------------------------------------------ the path */

@@ -49,7 +49,7 @@ class CgReport(ctypes.Structure):
                 ("mass_out", ctypes.c_double * MAX_REPORT_FIELDS),
                 ("n_out_of_domain", ctypes.c_longlong),
                 ("fixed_point_bits", ctypes.c_int * MAX_REPORT_FIELDS),
-                ("inner_iters_per_round", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("inner_iters_per_round", ctypes.c_int), ("sweep_shape_used", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         out = {}

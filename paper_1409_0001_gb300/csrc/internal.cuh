@@ -61,7 +61,27 @@ struct ProfRecord {
 };
 
 // A captured diffusion (one entry per distinct call signature and buffer set).
+// Shape of a captured batched schedule: the arena its kernels read (descriptors and
+// work items are re-uploaded before every replay), the readback buffer, and the scalars
+// baked into its launches.
+struct BatchKey {
+    const void *arena = nullptr;
+    unsigned gen = 0;
+    int nsnap = 0, nf = 0, nsteps = 0, R = 0, mmax = 0, nr = 0, nc = 0, grid = 0, zlen = 0,
+        tsize = 0, scheme = 0;
+    long long budget = 0;
+    double tol2 = 0.0;
+    bool operator==(const BatchKey &o) const {
+        return arena == o.arena && gen == o.gen && nsnap == o.nsnap && nf == o.nf &&
+               nsteps == o.nsteps && R == o.R && mmax == o.mmax && nr == o.nr && nc == o.nc &&
+               grid == o.grid && zlen == o.zlen && tsize == o.tsize && scheme == o.scheme &&
+               budget == o.budget && tol2 == o.tol2;
+    }
+};
+
 struct GraphEntry {
+    bool batched = false;           // a batched schedule (matched by bkey only)
+    BatchKey bkey;
     int nf = 0, precision = 0, scheme = 0, nsteps = 0, rounds = 0;
     double T = 0, tol = 0;
     const void *cells = nullptr;
@@ -128,6 +148,8 @@ struct cg_mesh {
     cgk::DevBuf ws_batch;    // batched calls: descriptors, work items, partials (first mesh)
     cgk::HostBuf h_small;    // pinned readback
     std::vector<std::pair<int, int>> tuned;   // autotuned sweep z-chunk per (fields, type)
+    std::vector<std::pair<std::vector<int>, int>> btuned;   // batched z-chunk per batch shape
+    std::vector<std::pair<std::vector<double>, int>> brounds;  // batched rounds per call signature
     std::vector<cgk::GraphEntry> graphs;      // captured diffusions
     std::vector<cgk::RoundsEntry> rounds;     // learned refinement schedules
     cudaStream_t capture_stream = nullptr;    // private stream used only for capture

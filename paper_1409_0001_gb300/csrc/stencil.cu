@@ -775,7 +775,7 @@ __device__ __forceinline__ float4 pack_df(DF a, DF b) { return make_float4(a.hi,
 __device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 template <class TS, int kMode>
-__global__ void __launch_bounds__(kThreads) k_refine_df2(Geo g, int zlen, int nzc, CoefDF cf,
+__global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int nzc, CoefDF cf,
                                                          int scheme, const DF *__restrict__ xin_all,
                                                          const TS *__restrict__ d_all,
                                                          const DF *b_all, DF *__restrict__ xout_all,
@@ -1371,7 +1371,7 @@ __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem 
 }
 
 template <class TS>
-__global__ void __launch_bounds__(kThreads) k_batched(const SnapDesc<TS> *__restrict__ sd, int nsnap,
+__global__ void __launch_bounds__(kThreads, 4) k_batched(const SnapDesc<TS> *__restrict__ sd, int nsnap,
                                                       int nf, const BItem *__restrict__ ritems,
                                                       int nr, const BItem *__restrict__ citems,
                                                       int nc, int nsteps, int R, int mmax,
@@ -1418,10 +1418,12 @@ __global__ void __launch_bounds__(kThreads) k_batched(const SnapDesc<TS> *__rest
 }
 
 // hist[(step * nsnap + s) * nf + f] = (sum of ||r||^2 partials, sum of ||b||^2 partials)
-// over the snapshot-field's items, in item order.  One block per (step, s, f).
+// over the snapshot-field's items, in item order.  One block per (step, s, f).  A step
+// whose ||r||^2 exceeds tol2 ||b||^2 (or is not a number) increments *bad.
 __global__ void k_batched_hist(const int *__restrict__ first_item, int nsnap, int nf, int nr,
                                const double *__restrict__ part_rr,
-                               const double *__restrict__ part_bb, double2 *__restrict__ hist) {
+                               const double *__restrict__ part_bb, double2 *__restrict__ hist,
+                               double tol2, unsigned int *bad) {
     const int sf = blockIdx.x % (nsnap * nf);
     const int step = blockIdx.x / (nsnap * nf);
     const int i0 = first_item[sf], i1 = first_item[sf + 1];
@@ -1431,11 +1433,18 @@ __global__ void k_batched_hist(const int *__restrict__ first_item, int nsnap, in
         b += part_bb[(size_t)step * nr + i];
     }
     double A = block_sum(a), B = block_sum(b);
-    if (threadIdx.x == 0) hist[blockIdx.x] = make_double2(A, B);
+    if (threadIdx.x == 0) {
+        hist[blockIdx.x] = make_double2(A, B);
+        if (!(A <= tol2 * B)) atomicAdd(bad, 1u);
+    }
 }
 
+// u^{n} -> the caller's FP64 arrays, only when every step of every snapshot-field met
+// the tolerance (otherwise the inputs stay intact for a run with more rounds).
 template <class TS>
-__global__ void k_batched_final(const SnapDesc<TS> *__restrict__ sd, int nf, double *const *cells) {
+__global__ void k_batched_final(const SnapDesc<TS> *__restrict__ sd, int nf, double *const *cells,
+                                const unsigned int *__restrict__ bad) {
+    if (*bad != 0u) return;
     const SnapDesc<TS> &d = sd[blockIdx.y];
     const size_t cnt = (size_t)d.g.n * nf;
     double *out = cells[blockIdx.y];
@@ -1889,6 +1898,10 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             const bool prof = prof_on();
             GraphEntry *ge = nullptr;
             for (auto it = m->graphs.begin(); it != m->graphs.end();) {
+                if (it->batched) {
+                    ++it;
+                    continue;
+                }
                 if (it->gen_diffuse != m->ws_diffuse.gen || it->gen_small != m->ws_small.gen) {
                     graph_release(*it);
                     it = m->graphs.erase(it);
@@ -2029,6 +2042,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                     rep->cell_updates = apps * nf * (long long)n;
                     rep->final_rel_residual = worst_g;
                     rep->inner_iters_per_round = m_it;
+                    rep->sweep_shape_used = cheb_code;
                 }
                 return CG_OK;
             }
@@ -2181,6 +2195,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
         rep->cell_updates = applications * nf * (long long)n;
         rep->final_rel_residual = worst;
         rep->inner_iters_per_round = m_it;
+        rep->sweep_shape_used = persistent ? 0 : cheb_code;
     }
     if (timed_out)
         return fail(CG_ETIMEOUT, "cg_diffuse: a grid barrier of the inner solve gave up (step %d)", s);
@@ -2204,23 +2219,31 @@ cg_status diffuse_structured_run(cg_mesh *m, int nf, double *cells, const cg_par
 
 
 // ============================================================================ batched host
+// Host-side plan of a batched call for one z-chunk length: per-snapshot descriptors,
+// Chebyshev weights, and the work items of the refinement and Chebyshev phases.
 template <class TS>
-static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
-                                    double *const *cells, const cg_params *p,
-                                    const double *bandwidths, cg_report *rep, cudaStream_t st) {
-    const bool cn = p->scheme == CG_SCHEME_CRANK_NICOLSON;
-    const double eps_inner = sizeof(TS) == 2 ? 2e-3 : 1e-6;
-    const double tol2 = p->tol * p->tol;
-    std::vector<SnapDesc<TS>> descs((size_t)nsnap);
+struct BatchPlan {
+    std::vector<SnapDesc<TS>> descs;
     std::vector<float> omegas;
-    std::vector<size_t> omega_off((size_t)nsnap);
+    std::vector<size_t> omega_off;
     std::vector<BItem> ritems, citems;
     std::vector<int> first_item;   // per (snapshot, field), into ritems
     int mmax = 2;
     long long cells_total = 0;
+};
+
+template <class TS>
+static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *const *cells,
+                            const cg_params *p, const double *bandwidths, int zlen,
+                            BatchPlan<TS> &P) {
+    const bool cn = p->scheme == CG_SCHEME_CRANK_NICOLSON;
+    const double eps_inner = sizeof(TS) == 2 ? 2e-3 : 1e-6;
+    P = BatchPlan<TS>();
+    P.descs.resize((size_t)nsnap);
+    P.omega_off.resize((size_t)nsnap);
     for (int s = 0; s < nsnap; ++s) {
         cg_mesh *m = meshes[s];
-        SnapDesc<TS> &d = descs[s];
+        SnapDesc<TS> &d = P.descs[s];
         const int n = (int)m->ncells;
         d.g = Geo{m->nx, m->ny, m->nz, m->nx * m->ny, n};
         const double b = bandwidths ? bandwidths[s] : p->bandwidth;
@@ -2238,28 +2261,28 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
         if (mi < 2) mi = 2;
         if (mi & 1) ++mi;
         d.m = mi;
-        mmax = std::max(mmax, mi);
+        P.mmax = std::max(P.mmax, mi);
         d.gamma = (float)(1.0 / theta);
         d.cf32 = coef32(ce);
         d.cfdf = coefdf(c, ce);
         d.scheme = p->scheme;
-        omega_off[s] = omegas.size();
+        P.omega_off[s] = P.omegas.size();
         double sigma = delta > 0.0 ? theta / delta : 0.0, om = 1.0;
-        omegas.push_back(1.0f);
+        P.omegas.push_back(1.0f);
         for (int k = 1; k < mi; ++k) {
             if (sigma > 0.0)
                 om = (k == 1) ? 1.0 / (1.0 - 1.0 / (2.0 * sigma * sigma))
                               : 1.0 / (1.0 - om / (4.0 * sigma * sigma));
-            omegas.push_back((float)om);
+            P.omegas.push_back((float)om);
         }
         d.gx = (m->nx + TX - 1) / TX;
         d.gy = (m->ny + TY - 1) / TY;
-        d.zlen = std::min(8, m->nz);
+        d.zlen = std::min(zlen, m->nz);
         d.nzc = (m->nz + d.zlen - 1) / d.zlen;
         d.v4 = (m->nx % 4 == 0) ? 1 : 0;
         d.gx4 = (m->nx + 4 * TX - 1) / (4 * TX);
-        d.zlen4 = std::min(8, m->nz);
-        d.nzc4 = (m->nz + d.zlen4 - 1) / d.zlen4;
+        d.zlen4 = d.zlen;
+        d.nzc4 = d.nzc;
         // per-snapshot solver vectors, owned by the snapshot's mesh
         const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
         CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 3 * vts));
@@ -2273,88 +2296,286 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
         d.Yb = (TS *)(wb + 4 * v64 + 2 * vts);
         d.cells = cells[s];
         for (int f = 0; f < nf; ++f) {
-            first_item.push_back((int)ritems.size());
+            P.first_item.push_back((int)P.ritems.size());
             for (int zc = 0; zc < d.nzc; ++zc)
                 for (int by = 0; by < d.gy; ++by)
-                    for (int bx = 0; bx < d.gx; ++bx) ritems.push_back(BItem{s, bx, by, f * d.nzc + zc});
-            const int cz = d.v4 ? d.nzc4 : d.nzc, cx = d.v4 ? d.gx4 : d.gx;
-            for (int zc = 0; zc < cz; ++zc)
+                    for (int bx = 0; bx < d.gx; ++bx) P.ritems.push_back(BItem{s, bx, by, f * d.nzc + zc});
+            const int cx = d.v4 ? d.gx4 : d.gx;
+            for (int zc = 0; zc < d.nzc4; ++zc)
                 for (int by = 0; by < d.gy; ++by)
-                    for (int bx = 0; bx < cx; ++bx) citems.push_back(BItem{s, bx, by, f * cz + zc});
+                    for (int bx = 0; bx < cx; ++bx) P.citems.push_back(BItem{s, bx, by, f * d.nzc4 + zc});
         }
-        cells_total += (long long)n;
+        P.cells_total += (long long)n;
     }
-    first_item.push_back((int)ritems.size());
-    const int nr = (int)ritems.size(), nc = (int)citems.size();
-    // batch arena on the first mesh: descriptors | omega | items | partials | hist | barrier | out ptrs
-    const size_t o_desc = 0;
-    const size_t o_om = align_up(o_desc + descs.size() * sizeof(SnapDesc<TS>));
-    const size_t o_ri = align_up(o_om + omegas.size() * sizeof(float));
-    const size_t o_ci = align_up(o_ri + ritems.size() * sizeof(BItem));
-    const size_t o_fi = align_up(o_ci + citems.size() * sizeof(BItem));
-    const size_t o_prr = align_up(o_fi + first_item.size() * sizeof(int));
-    const size_t o_pbb = align_up(o_prr + (size_t)p->nsteps * nr * 8);
-    const size_t o_hist = align_up(o_pbb + (size_t)p->nsteps * nr * 8);
-    const size_t nh = (size_t)p->nsteps * nsnap * nf;
-    const size_t o_gb = align_up(o_hist + nh * sizeof(double2));
-    const size_t o_out = align_up(o_gb + sizeof(GridBar));
-    const size_t total = align_up(o_out + (size_t)nsnap * sizeof(double *));
-    cg_mesh *m0 = meshes[0];
-    CGK_TRY(m0->ws_batch.ensure(total));
-    char *ab = m0->ws_batch.as<char>();
-    for (int s = 0; s < nsnap; ++s) descs[s].omega = (const float *)(ab + o_om) + omega_off[s];
-    CGK_CUDA(cudaMemcpyAsync(ab + o_desc, descs.data(), descs.size() * sizeof(SnapDesc<TS>),
-                             cudaMemcpyHostToDevice, st));
-    CGK_CUDA(cudaMemcpyAsync(ab + o_om, omegas.data(), omegas.size() * sizeof(float),
-                             cudaMemcpyHostToDevice, st));
-    CGK_CUDA(cudaMemcpyAsync(ab + o_ri, ritems.data(), ritems.size() * sizeof(BItem),
-                             cudaMemcpyHostToDevice, st));
-    CGK_CUDA(cudaMemcpyAsync(ab + o_ci, citems.data(), citems.size() * sizeof(BItem),
-                             cudaMemcpyHostToDevice, st));
-    CGK_CUDA(cudaMemcpyAsync(ab + o_fi, first_item.data(), first_item.size() * sizeof(int),
-                             cudaMemcpyHostToDevice, st));
-    CGK_CUDA(cudaMemcpyAsync(ab + o_out, cells, (size_t)nsnap * sizeof(double *),
-                             cudaMemcpyHostToDevice, st));
-    // the host vectors above must outlive the copies
-    CGK_CUDA(cudaStreamSynchronize(st));
-    const SnapDesc<TS> *dsd = (const SnapDesc<TS> *)(ab + o_desc);
-    const BItem *dri = (const BItem *)(ab + o_ri), *dci = (const BItem *)(ab + o_ci);
-    double *prr = (double *)(ab + o_prr), *pbb = (double *)(ab + o_pbb);
-    double2 *hist = (double2 *)(ab + o_hist);
-    GridBar *gb = (GridBar *)(ab + o_gb);
+    P.first_item.push_back((int)P.ritems.size());
+    return CG_OK;
+}
 
+// The batch arena on the first mesh: descriptors | weights | items | partials | hist |
+// barrier | failure count | output pointers.
+struct BatchArena {
+    char *ab = nullptr;
+    size_t o_desc = 0, o_om = 0, o_ri = 0, o_ci = 0, o_fi = 0, o_prr = 0, o_pbb = 0, o_hist = 0,
+           o_gb = 0, o_bad = 0, o_out = 0, total = 0;
+    size_t nh = 0;
+};
+
+template <class TS>
+static BatchArena batch_layout(const BatchPlan<TS> &P, int nsnap, int nf, int nsteps) {
+    BatchArena A;
+    const size_t nr = P.ritems.size();
+    A.o_desc = 0;
+    A.o_om = align_up(A.o_desc + P.descs.size() * sizeof(SnapDesc<TS>));
+    A.o_ri = align_up(A.o_om + P.omegas.size() * sizeof(float));
+    A.o_ci = align_up(A.o_ri + P.ritems.size() * sizeof(BItem));
+    A.o_fi = align_up(A.o_ci + P.citems.size() * sizeof(BItem));
+    A.o_prr = align_up(A.o_fi + P.first_item.size() * sizeof(int));
+    A.o_pbb = align_up(A.o_prr + (size_t)nsteps * nr * 8);
+    A.o_hist = align_up(A.o_pbb + (size_t)nsteps * nr * 8);
+    A.nh = (size_t)nsteps * nsnap * nf;
+    A.o_gb = align_up(A.o_hist + A.nh * sizeof(double2));
+    A.o_bad = align_up(A.o_gb + sizeof(GridBar));
+    A.o_out = align_up(A.o_bad + sizeof(unsigned int));
+    A.total = align_up(A.o_out + (size_t)nsnap * sizeof(double *));
+    return A;
+}
+
+// Uploads the plan into the arena (ensured large enough by the caller).  The host
+// vectors are read by the copies, so the stream is synchronised before returning.
+template <class TS>
+static cg_status batch_upload(BatchPlan<TS> &P, BatchArena &A, char *ab, int nsnap,
+                              double *const *cells, cudaStream_t st) {
+    A.ab = ab;
+    for (int s = 0; s < nsnap; ++s) P.descs[s].omega = (const float *)(ab + A.o_om) + P.omega_off[s];
+    CGK_CUDA(cudaMemcpyAsync(ab + A.o_desc, P.descs.data(), P.descs.size() * sizeof(SnapDesc<TS>),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + A.o_om, P.omegas.data(), P.omegas.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + A.o_ri, P.ritems.data(), P.ritems.size() * sizeof(BItem),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + A.o_ci, P.citems.data(), P.citems.size() * sizeof(BItem),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + A.o_fi, P.first_item.data(), P.first_item.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaMemcpyAsync(ab + A.o_out, cells, (size_t)nsnap * sizeof(double *),
+                             cudaMemcpyHostToDevice, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    return CG_OK;
+}
+
+// One batched schedule on stream st: reset the barrier and the failure count, the
+// persistent launch (nsteps pseudo-steps of R rounds), the residual history and, if
+// `final`, the write-back (skipped on the device when a step missed the tolerance).
+template <class TS>
+static cg_status batch_issue(const BatchPlan<TS> &P, const BatchArena &A, int nsnap, int nf,
+                             int nsteps, int R, int G, long long budget, double tol2, bool final,
+                             cudaStream_t st) {
+    char *ab = A.ab;
+    const SnapDesc<TS> *dsd = (const SnapDesc<TS> *)(ab + A.o_desc);
+    const BItem *dri = (const BItem *)(ab + A.o_ri), *dci = (const BItem *)(ab + A.o_ci);
+    double *prr = (double *)(ab + A.o_prr), *pbb = (double *)(ab + A.o_pbb);
+    double2 *hist = (double2 *)(ab + A.o_hist);
+    GridBar *gb = (GridBar *)(ab + A.o_gb);
+    unsigned int *bad = (unsigned int *)(ab + A.o_bad);
+    const int nr = (int)P.ritems.size(), nc = (int)P.citems.size();
+    CGK_CUDA(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+    CGK_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
+    int a_ns = nsnap, a_nf = nf, a_nr = nr, a_nc = nc, a_steps = nsteps, a_R = R, a_mm = P.mmax;
+    long long a_budget = budget;
+    void *args[] = {&dsd, &a_ns, &a_nf, &dri, &a_nr, &dci, &a_nc, &a_steps, &a_R, &a_mm,
+                    &prr, &pbb, &gb, &a_budget};
+    double bytes = 0.0;
+    for (const auto &d : P.descs)
+        bytes += (double)d.g.n * nf *
+                 (16.0 + nsteps * ((8 + 2 * sizeof(TS)) +
+                                   R * ((24 + 3 * sizeof(TS)) + (d.m - 1) * 4.0 * sizeof(TS))));
+    CGK_LAUNCH(sizeof(TS) == 2 ? "batched_bf16" : "batched_fp32", bytes, st,
+               CGK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batched<TS>, dim3(G),
+                                                    dim3(TX, TY), args, 0, st)));
+    CGK_LAUNCH("batched_hist", 16.0 * nsteps * nr, st,
+               k_batched_hist<<<(unsigned)A.nh, kThreads, 0, st>>>(
+                   (const int *)(ab + A.o_fi), nsnap, nf, nr, prr, pbb, hist, tol2, bad));
+    CGK_CUDA(cudaGetLastError());
+    if (final) {
+        CGK_LAUNCH("batched_final", 16.0 * P.cells_total * nf, st,
+                   k_batched_final<TS><<<dim3(num_sms() * 2, nsnap), kThreads, 0, st>>>(
+                       dsd, nf, (double *const *)(ab + A.o_out), bad));
+        CGK_CUDA(cudaGetLastError());
+    }
+    return CG_OK;
+}
+
+// Autotuner of the batched z-chunk length: one pseudo-step of two rounds per candidate
+// (the caller's arrays are not written), timed with events; the fastest is kept per
+// batch shape (the snapshots' dimensions, the field count and the inner type).
+template <class TS>
+static cg_status batch_tune(int nsnap, cg_mesh *const *meshes, int nf, double *const *cells,
+                            const cg_params *p, const double *bandwidths, int G, long long budget,
+                            cudaStream_t st, int *zbest) {
+    std::vector<int> key;
+    key.reserve((size_t)nsnap * 3 + 2);
+    key.push_back(nf);
+    key.push_back((int)sizeof(TS));
+    for (int s = 0; s < nsnap; ++s) {
+        key.push_back(meshes[s]->nx);
+        key.push_back(meshes[s]->ny);
+        key.push_back(meshes[s]->nz);
+    }
+    cg_mesh *m0 = meshes[0];
+    for (const auto &e : m0->btuned)
+        if (e.first == key) {
+            *zbest = e.second;
+            return CG_OK;
+        }
+    static const int cand[] = {4, 8, 16};
+    float best = 0.f;
+    *zbest = 8;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CGK_CUDA(cudaEventCreate(&e0));
+    CGK_CUDA(cudaEventCreate(&e1));
+    cg_status rc = CG_OK;
+    for (int z : cand) {
+        BatchPlan<TS> P;
+        rc = batch_plan<TS>(nsnap, meshes, nf, cells, p, bandwidths, z, P);
+        if (rc != CG_OK) break;
+        BatchArena A = batch_layout(P, nsnap, nf, 1);
+        rc = m0->ws_batch.ensure(A.total);
+        if (rc != CG_OK) break;
+        rc = batch_upload(P, A, m0->ws_batch.as<char>(), nsnap, cells, st);
+        if (rc != CG_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && rc == CG_OK; ++rep) {   // the first run warms up
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = fail(CG_ECUDA, "event");
+            if (rc == CG_OK) rc = batch_issue(P, A, nsnap, nf, 1, 2, G, budget, 0.0, false, st);
+            if (rc == CG_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = fail(CG_ECUDA, "event");
+            if (rc == CG_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(CG_ECUDA, "sync");
+            if (rc == CG_OK) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (rc != CG_OK) break;
+        GridBar hgb;
+        if (cudaMemcpy(&hgb, A.ab + A.o_gb, sizeof(GridBar), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = fail(CG_ECUDA, "readback");
+            break;
+        }
+        if (hgb.err) {
+            rc = fail(CG_ETIMEOUT, "cg_diffuse_batched: a grid barrier of the persistent kernel gave up");
+            break;
+        }
+        if (best == 0.f || ms < best) {
+            best = ms;
+            *zbest = z;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CG_OK) return rc;
+    m0->btuned.push_back({key, *zbest});
+    return CG_OK;
+}
+
+template <class TS>
+static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
+                                    double *const *cells, const cg_params *p,
+                                    const double *bandwidths, cg_report *rep, cudaStream_t st) {
+    const double tol2 = p->tol * p->tol;
+    cg_mesh *m0 = meshes[0];
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<TS>, kThreads, 0) != cudaSuccess)
         per_sm = 1;
+    cudaGetLastError();
     per_sm = std::max(1, std::min(per_sm, 4));
     const int G = per_sm * num_sms();
     const long long budget = p->barrier_budget > 0 ? p->barrier_budget : 2000000000LL;
     const int max_r = p->max_rounds > 0 ? p->max_rounds : 12;
+    int zlen = p->sweep_shape > 0 ? p->sweep_shape : 0;
+    if (zlen == 0) CGK_TRY(batch_tune<TS>(nsnap, meshes, nf, cells, p, bandwidths, G, budget, st, &zlen));
+    BatchPlan<TS> P;
+    CGK_TRY(batch_plan<TS>(nsnap, meshes, nf, cells, p, bandwidths, zlen, P));
+    BatchArena A = batch_layout(P, nsnap, nf, p->nsteps);
+    CGK_TRY(m0->ws_batch.ensure(A.total));
+    CGK_TRY(batch_upload(P, A, m0->ws_batch.as<char>(), nsnap, cells, st));
+    const size_t nh = A.nh;
     CGK_TRY(m0->h_small.ensure(4096 + nh * sizeof(double2) + 64));
     double2 *hh = (double2 *)(m0->h_small.as<char>() + 4096);
     GridBar *hgb = (GridBar *)(hh + nh);
+    // rounds learned by an earlier call with the same signature
+    std::vector<double> sig = {(double)nf, (double)p->precision, (double)p->scheme,
+                               (double)p->nsteps, p->tol, p->T};
+    for (int s = 0; s < nsnap; ++s) {
+        sig.push_back(meshes[s]->nx);
+        sig.push_back(meshes[s]->ny);
+        sig.push_back(meshes[s]->nz);
+        sig.push_back(meshes[s]->dx);
+        sig.push_back(bandwidths ? bandwidths[s] : p->bandwidth);
+    }
     int R = sizeof(TS) == 2 ? 5 : 2;
+    int *learned = nullptr;
+    for (auto &e : m0->brounds)
+        if (e.first == sig) learned = &e.second;
+    if (learned) R = std::max(R, *learned);
     for (; R <= max_r; ++R) {
-        CGK_CUDA(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
-        int a_ns = nsnap, a_nf = nf, a_nr = nr, a_nc = nc, a_steps = p->nsteps, a_R = R, a_mm = mmax;
-        long long a_budget = budget;
-        void *args[] = {&dsd, &a_ns, &a_nf, &dri, &a_nr, &dci, &a_nc, &a_steps, &a_R, &a_mm,
-                        &prr, &pbb, &gb, &a_budget};
-        double bytes = 0.0;
-        for (const auto &d : descs)
-            bytes += (double)d.g.n * nf *
-                     (16.0 + p->nsteps * ((8 + 2 * sizeof(TS)) +
-                                          R * ((24 + 3 * sizeof(TS)) + (d.m - 1) * 4.0 * sizeof(TS))));
-        CGK_LAUNCH(sizeof(TS) == 2 ? "batched_bf16" : "batched_fp32", bytes, st,
-                   CGK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batched<TS>, dim3(G),
-                                                        dim3(TX, TY), args, 0, st)));
-        CGK_LAUNCH("batched_hist", 16.0 * p->nsteps * nr, st,
-                   k_batched_hist<<<(unsigned)nh, kThreads, 0, st>>>(
-                       (const int *)(ab + o_fi), nsnap, nf, nr, prr, pbb, hist));
-        CGK_CUDA(cudaGetLastError());
-        CGK_CUDA(cudaMemcpyAsync(hh, hist, nh * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        CGK_CUDA(cudaMemcpyAsync(hgb, gb, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+        // the schedule is replayed from a CUDA graph captured once per shape
+        BatchKey key;
+        key.arena = A.ab;
+        key.gen = m0->ws_batch.gen;
+        key.nsnap = nsnap;
+        key.nf = nf;
+        key.nsteps = p->nsteps;
+        key.R = R;
+        key.mmax = P.mmax;
+        key.nr = (int)P.ritems.size();
+        key.nc = (int)P.citems.size();
+        key.grid = G;
+        key.zlen = zlen;
+        key.tsize = (int)sizeof(TS);
+        key.scheme = p->scheme;
+        key.budget = budget;
+        key.tol2 = tol2;
+        const bool prof = prof_on();
+        GraphEntry *ge = nullptr;
+        for (auto it = m0->graphs.begin(); it != m0->graphs.end();) {
+            if (it->batched && it->bkey.arena == A.ab && it->bkey.gen != m0->ws_batch.gen) {
+                graph_release(*it);
+                it = m0->graphs.erase(it);
+                continue;
+            }
+            if (it->batched && it->bkey == key && it->profiled == prof) ge = &*it;
+            ++it;
+        }
+        if (!ge) {
+            if (!m0->capture_stream)
+                CGK_CUDA(cudaStreamCreateWithFlags(&m0->capture_stream, cudaStreamNonBlocking));
+            cudaStream_t cs = m0->capture_stream;
+            GraphEntry e;
+            e.batched = true;
+            e.bkey = key;
+            e.profiled = prof;
+            prof_capture_begin(&e.records, &e.kernels);
+            cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            cg_status is = CG_OK;
+            if (ce == cudaSuccess) {
+                is = batch_issue(P, A, nsnap, nf, p->nsteps, R, G, budget, tol2, true, cs);
+                cudaGraph_t graph = nullptr;
+                ce = cudaStreamEndCapture(cs, &graph);
+                if (ce == cudaSuccess && is == CG_OK) ce = cudaGraphInstantiate(&e.exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+            }
+            prof_capture_end();
+            if (is != CG_OK || ce != cudaSuccess || !e.exec) {
+                graph_release(e);
+                cudaGetLastError();
+                if (is != CG_OK) return is;
+                return cuda_fail(ce == cudaSuccess ? cudaErrorUnknown : ce, "batched graph capture",
+                                 __FILE__, __LINE__);
+            }
+            m0->graphs.push_back(e);
+            ge = &m0->graphs.back();
+        }
+        CGK_CUDA(cudaGraphLaunch(ge->exec, st));
+        CGK_CUDA(cudaMemcpyAsync(hh, A.ab + A.o_hist, nh * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CGK_CUDA(cudaMemcpyAsync(hgb, A.ab + A.o_gb, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
         CGK_CUDA(cudaStreamSynchronize(st));
+        prof_account_replay(*ge);
         if (hgb->err)
             return fail(CG_ETIMEOUT, "cg_diffuse_batched: a grid barrier of the persistent kernel gave up");
         bool ok = true;
@@ -2363,15 +2584,14 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
             ok = ok && (hh[i].x <= tol2 * hh[i].y);
             worst = std::max(worst, hh[i].y > 0 ? std::sqrt(hh[i].x / hh[i].y) : 0.0);
         }
-        if (ok || R == max_r) {
-            CGK_LAUNCH("batched_final", 16.0 * cells_total * nf, st,
-                       k_batched_final<TS><<<dim3(num_sms() * 2, nsnap), kThreads, 0, st>>>(
-                           dsd, nf, (double *const *)(ab + o_out)));
-            CGK_CUDA(cudaGetLastError());
-            CGK_CUDA(cudaStreamSynchronize(st));
+        if (ok) {
+            if (learned)
+                *learned = R;
+            else
+                m0->brounds.push_back({sig, R});
             if (rep) {
                 long long apps = 0, upd = 0;
-                for (const auto &d : descs) {
+                for (const auto &d : P.descs) {
                     long long a = (long long)p->nsteps * (1 + (long long)R * d.m);
                     apps += a;
                     upd += a * d.g.n;
@@ -2380,10 +2600,22 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
                 rep->refine_rounds = (long long)p->nsteps * R * nsnap;
                 rep->cell_updates = upd * nf;
                 rep->final_rel_residual = worst;
-                rep->inner_iters_per_round = mmax;
+                rep->inner_iters_per_round = P.mmax;
+                rep->sweep_shape_used = zlen;
             }
-            if (!ok) return fail(CG_ENOCONV, "cg_diffuse_batched: refinement did not reach tol");
             return CG_OK;
+        }
+        if (R == max_r) {   // the last iterate is left in place
+            unsigned int *bad = (unsigned int *)(A.ab + A.o_bad);
+            CGK_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
+            CGK_LAUNCH("batched_final", 16.0 * P.cells_total * nf, st,
+                       k_batched_final<TS><<<dim3(num_sms() * 2, nsnap), kThreads, 0, st>>>(
+                           (const SnapDesc<TS> *)(A.ab + A.o_desc), nf,
+                           (double *const *)(A.ab + A.o_out), bad));
+            CGK_CUDA(cudaGetLastError());
+            CGK_CUDA(cudaStreamSynchronize(st));
+            if (rep) rep->final_rel_residual = worst;
+            break;
         }
     }
     return fail(CG_ENOCONV, "cg_diffuse_batched: refinement did not reach tol");

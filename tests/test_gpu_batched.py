@@ -124,3 +124,56 @@ def test_batched_rejects_shared_meshes_and_tets(cg):
     t = cg.TetMesh(xyz, tets)
     with pytest.raises(cg.CGError):
         cg.diffuse_batched([t], [dev(np.zeros((1, t.ncells)))], cg.Params(bandwidth=0.2, precision=3))
+
+
+@pytest.mark.parametrize("zlen", [4, 16])
+def test_batched_tile_override_matches_oracle(cg, orc, zlen):
+    """Work items of 4 or 16 z-planes (the autotuner's other candidates) give the same
+    answers as the oracle; the report names the z-chunk that ran."""
+    cases = small_batch()[:4]
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    out, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3,
+                                                                 sweep_shape=zlen),
+                                       bandwidths=[c.b for c in cases], report=True)
+    assert rep["sweep_shape_used"] == zlen
+    for c, o in zip(cases, out):
+        _, ref, _, _ = orc.coarse_grain_structured(c.dims, c.origin, c.dx, c.pos, c.w, c.b, c.nsteps)
+        assert maxrel(o.cpu().numpy(), ref) <= MIXED_TOL
+
+
+def test_batched_graph_replay_is_deterministic(cg):
+    """The first call tunes the z-chunk and captures the schedule; later calls replay the
+    captured graph and must reproduce the first call's bits."""
+    cases = small_batch()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    bws = [c.b for c in cases]
+    runs = []
+    for _ in range(3):
+        out, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3),
+                                           bandwidths=bws, report=True)
+        assert rep["sweep_shape_used"] in (4, 8, 16)
+        runs.append([o.cpu().numpy().view(np.int64) for o in out])
+    for r in runs[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
+
+
+def test_batched_unreachable_tol_leaves_last_iterate(cg, orc):
+    """A tolerance below double-float resolution cannot be met: CG_ENOCONV, with the last
+    iterate (still within the mixed bar of the oracle) written to the caller's arrays."""
+    cases = small_batch()[:2]
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    cells = [dev(orc.deposit(orc.locate_structured(c.dims, c.origin, c.dx, c.pos)[0], c.w,
+                             int(np.prod(c.dims)), vc_uniform=c.dx * c.dx * c.dx)[0])
+             for c in cases]
+    with pytest.raises(cg.CGError) as e:
+        cg.diffuse_batched(meshes, cells, cg.Params(nsteps=10, precision=3, tol=1e-17,
+                                                    max_rounds=3),
+                           bandwidths=[c.b for c in cases])
+    assert e.value.code == "CG_ENOCONV"
+    for c, u in zip(cases, cells):
+        _, ref, _, _ = orc.coarse_grain_structured(c.dims, c.origin, c.dx, c.pos, c.w, c.b, c.nsteps)
+        assert maxrel(u.cpu().numpy(), ref) <= MIXED_TOL
