@@ -124,12 +124,17 @@ typedef struct {
     int sweep_shape;    /* hex Chebyshev sweep shape: 0 = autotuned per mesh (default);
                            100 + z = vectorised, 4 x-cells per thread, z planes per block
                            (needs nx % 4 == 0); 2, 4, 8 = register-blocked planes per
-                           block; -z = z-marching, z planes per block.  Batched calls:
+                           block; -z = z-marching, z planes per block; 300 = resident:
+                           each round's inner solve in one cooperative launch that keeps
+                           the mesh in the SMs' shared memory (one field, nx % 4 == 0, a
+                           mesh that fits; the autotuner also weighs it).  Batched calls:
                            z planes per work item (0 = autotuned per batch shape) */
     long long barrier_budget; /* > 0: run each structured inner solve as one persistent
                                  cooperative launch whose grid barriers give up after this
-                                 many clock cycles of waiting (then CG_ETIMEOUT); 0: one
-                                 launch per inner iteration (default) */
+                                 many clock cycles of waiting (then CG_ETIMEOUT); with
+                                 sweep_shape 300 it bounds the resident solve's waits
+                                 instead (default about one second); 0: one launch per
+                                 inner iteration (default) */
 } cg_params;
 
 /* Fills the defaults: bandwidth 0, T 0, nsteps 10, implicit Euler, FP64, ordered

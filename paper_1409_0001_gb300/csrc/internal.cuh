@@ -83,6 +83,8 @@ struct GraphEntry {
     bool batched = false;           // a batched schedule (matched by bkey only)
     BatchKey bkey;
     int nf = 0, precision = 0, scheme = 0, nsteps = 0, rounds = 0;
+    int code = 0;                   // inner-solve shape (sweep_shape code) captured
+    long long wait_budget = 0;      // resident waits' clock-cycle budget captured
     double T = 0, tol = 0;
     const void *cells = nullptr;
     unsigned gen_diffuse = 0, gen_small = 0;

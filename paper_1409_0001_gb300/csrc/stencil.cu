@@ -1248,6 +1248,256 @@ __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nz
                            yprev_all ? yprev_all + off : nullptr, r_all + off, ynext_all + off);
 }
 
+// ---------------------------------------------------------------- on-chip resident sweep
+constexpr int kResidentThreads = 1024;
+constexpr int kResidentMaxIters = 128;
+constexpr int kResidentCode = 300;   // sweep_shape of the resident inner solve
+
+// The m-1 Chebyshev iterations of one refinement round with the iterates held in shared
+// memory, for a mesh whose two iterates fit in the SMs' shared memory (one field,
+// nx % 4 == 0).  The mesh is cut into bricks of whole x-rows (by rows x bz planes), one
+// brick per block, every block resident (cooperative launch, one block per SM).  Each
+// shared array holds a brick with a one-row / one-plane halo in y and z and four zero
+// cells of padding at both ends of every row (the x walls).  Per iteration a block
+// computes y_{k+1} over its brick from y_k (neighbours from shared memory) and y_{k-1}
+// (same cell, overwritten), r from global memory: first the brick's surface rows, whose
+// four faces (y and z) it then publishes to global memory (two parities) before raising
+// its flag to k+1 (a release store), then the inner rows while the faces travel; then it
+// waits -- bounded -- until its up to four neighbours have raised theirs and copies their
+// faces into its halo.  A neighbour cannot overwrite a face parity before this block has read it: it
+// would first need this block's next face.  Halos on walls stay zero.  Arithmetic and
+// its order are those of k_cheb_v4, so the iterates are bit-identical.
+struct Brick {
+    int by, bz, nby, nbz;   // rows / planes per brick, bricks along y / z
+    int pitch;              // shared row pitch in floats (nx + 8)
+    int fmax;               // floats per face slot (nx * max(by, bz))
+};
+
+struct ChebWeights {
+    float w[kResidentMaxIters];   // omega_k, k = 1 .. m-1
+};
+
+// floor(n / d) as a multiply-high by ceil(2^32 / d): exact whenever n * d < 2^32, which
+// holds for every index divided below (at most a few thousand times at most 1024).  d = 1
+// (whose multiplier would not fit in 32 bits) divides trivially.
+struct FastDiv {
+    unsigned int m;
+    int d;
+    __device__ explicit FastDiv(int d_)
+        : m(d_ > 1 ? (unsigned int)((0x100000000ull + d_ - 1) / d_) : 0u), d(d_) {}
+    __device__ __forceinline__ int div(int n) const {
+        return d > 1 ? (int)__umulhi((unsigned int)n, m) : n;
+    }
+};
+
+// One Chebyshev update (y_{k+1} into Ynext) of a brick's surface rows (boundary = true)
+// or of its inner rows, for k_cheb_resident; a warp always covers whole rows, so it
+// skips a row together.
+template <class TS>
+__device__ __forceinline__ void resident_rows(const Geo &g, const float *__restrict__ sdg, float ce,
+                                              float gam, float omega, const TS *__restrict__ r,
+                                              const float *Ycur, float *Ynext, int tid, int nthr,
+                                              int nq, int bys, int bzs, int y0, int z0, int RW,
+                                              int P, int PL, bool warp_rows, bool boundary,
+                                              FastDiv dq, FastDiv dy) {
+    const int nrow_b = bys * bzs;
+    for (int it = tid; it < nrow_b * nq; it += nthr) {
+        const int row = dq.div(it), q = it - row * nq;
+        const int zz = dy.div(row), yy = row - zz * bys;
+        const bool surf = yy == 0 || yy == bys - 1 || zz == 0 || zz == bzs - 1;
+        if (surf != boundary) continue;
+        const int gy = y0 + yy, gz = z0 + zz, x = 4 * q;
+        const int si = ((zz + 1) * RW + (yy + 1)) * P + 4 + x;
+        const float4 vc = *reinterpret_cast<const float4 *>(Ycur + si);
+        const float4 up = *reinterpret_cast<const float4 *>(Ycur + si - P);
+        const float4 dn = *reinterpret_cast<const float4 *>(Ycur + si + P);
+        const float4 vdn = *reinterpret_cast<const float4 *>(Ycur + si - PL);
+        const float4 vup = *reinterpret_cast<const float4 *>(Ycur + si + PL);
+        float left, right;
+        if (warp_rows) {   // a warp covers 128 consecutive cells of one row
+            const int lane = tid & 31;
+            left = __shfl_up_sync(0xffffffffu, vc.w, 1);
+            right = __shfl_down_sync(0xffffffffu, vc.x, 1);
+            if (lane == 0) left = Ycur[si - 1];
+            if (lane == 31) right = Ycur[si + 4];
+        } else {
+            left = Ycur[si - 1];
+            right = Ycur[si + 4];
+        }
+        const float4 ypc = *reinterpret_cast<const float4 *>(Ynext + si);
+        const float4 rc = Vec4<TS>::load(r, ((size_t)gz * g.ny + gy) * g.nx + x);
+        const int nyb = (gy > 0) + (gy + 1 < g.ny);
+        const int nz_ = (gz > 0) + (gz + 1 < g.nz);
+        const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx), n12 = nyb + 2;
+        float4 s;
+        s.x = left + vc.y + up.x + dn.x + vdn.x + vup.x;
+        s.y = vc.x + vc.z + up.y + dn.y + vdn.y + vup.y;
+        s.z = vc.y + vc.w + up.z + dn.z + vdn.z + vup.z;
+        s.w = vc.z + right + up.w + dn.w + vdn.w + vup.w;
+        float4 o;
+        o.x = fmaf(omega, vc.x - ypc.x + gam * (rc.x - fmaf(sdg[n0 + nz_], vc.x, -ce * s.x)), ypc.x);
+        o.y = fmaf(omega, vc.y - ypc.y + gam * (rc.y - fmaf(sdg[n12 + nz_], vc.y, -ce * s.y)), ypc.y);
+        o.z = fmaf(omega, vc.z - ypc.z + gam * (rc.z - fmaf(sdg[n12 + nz_], vc.z, -ce * s.z)), ypc.z);
+        o.w = fmaf(omega, vc.w - ypc.w + gam * (rc.w - fmaf(sdg[n3 + nz_], vc.w, -ce * s.w)), ypc.w);
+        *reinterpret_cast<float4 *>(Ynext + si) = o;
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kResidentThreads, 1)
+    k_cheb_resident(Geo g, Brick bk, Coef32 cf, float gamma, ChebWeights om, int m,
+                    const TS *__restrict__ y1, const TS *__restrict__ r, TS *__restrict__ yout,
+                    float *__restrict__ faces, unsigned int *flags, int *err, long long budget) {
+    extern __shared__ float4 smem4[];
+    __shared__ float sdg[8];
+    __shared__ float somega[kResidentMaxIters];
+    __shared__ int s_stop;
+    float *sm = reinterpret_cast<float *>(smem4);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int b = blockIdx.x;
+    const int iy = b % bk.nby, iz = b / bk.nby;
+    const int y0 = iy * bk.by, z0 = iz * bk.bz;
+    const int bys = min(bk.by, g.ny - y0), bzs = min(bk.bz, g.nz - z0);
+    const int P = bk.pitch, RW = bk.by + 2, PL = RW * P;
+    const int arr = PL * (bk.bz + 2);
+    float *A0 = sm, *A1 = sm + arr;
+    const int nq = g.nx >> 2;
+    const FastDiv dq(nq), dy(bys);
+#pragma unroll
+    for (int i = 0; i < 7; ++i)   // constant indices: the parameter is not copied to memory
+        if (tid == i) sdg[i] = cf.dg[i];
+    if (tid == 7) sdg[7] = 0.f;
+#pragma unroll
+    for (int i = 0; i < kResidentMaxIters; i += 32)
+        if (tid < 32) somega[i + tid] = om.w[i + tid];
+    if (tid == 0) s_stop = 0;
+    // zero both arrays (walls, padding), then y1 over the brick and its halo
+    for (int i = tid; i < 2 * arr / 4; i += nthr) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    {
+        const int ylo = max(y0 - 1, 0), yhi = min(y0 + bys + 1, g.ny);
+        const int zlo = max(z0 - 1, 0), zhi = min(z0 + bzs + 1, g.nz);
+        const int ny_ = yhi - ylo, nrows = ny_ * (zhi - zlo);
+        const FastDiv dny(ny_);
+        for (int it = tid; it < nrows * nq; it += nthr) {
+            const int row = dq.div(it), q = it - row * nq;
+            const int rz = dny.div(row);
+            const int gy = ylo + (row - rz * ny_), gz = zlo + rz;
+            const bool iny = gy >= y0 && gy < y0 + bys, inz = gz >= z0 && gz < z0 + bzs;
+            if (!iny && !inz) continue;   // halo edges and corners are never read
+            const size_t k = ((size_t)gz * g.ny + gy) * g.nx + 4 * q;
+            const int si = ((gz - z0 + 1) * RW + (gy - y0 + 1)) * P + 4 + 4 * q;
+            *reinterpret_cast<float4 *>(A0 + si) = Vec4<TS>::load(y1, k);
+        }
+    }
+    __syncthreads();
+    float *Yc = A0, *Yp = A1;
+    const int nrow_b = bys * bzs;
+    const size_t fslot = (size_t)bk.fmax;
+    const bool warp_rows = (nq % 32 == 0) && (nthr % 32 == 0);
+    const float ce = cf.ce, gam = gamma;
+    for (int k = 1; k < m; ++k) {
+        const bool last = k + 1 == m;
+        const int par = (k + 1) & 1;
+        // surface rows first, so that their faces travel while the inner rows are computed
+        resident_rows<TS>(g, sdg, ce, gam, somega[k], r, Yc, Yp, tid, nthr, nq, bys, bzs, y0, z0,
+                          RW, P, PL, warp_rows, true, dq, dy);
+        __syncthreads();
+        if (!last) {
+            // faces of y_{k+1}: slot (b, parity, face), face 0/1 = rows y0 / y0+bys-1 (all
+            // planes), 2/3 = planes z0 / z0+bzs-1 (all rows)
+            float *fb = faces + ((size_t)b * 2 + par) * 4 * fslot;
+            for (int it = tid; it < 2 * (bzs + bys) * nq; it += nthr) {
+                int rr = dq.div(it), face, si;
+                const int q = it - rr * nq;
+                if (rr < 2 * bzs) {
+                    face = rr >= bzs ? 1 : 0;
+                    rr -= face * bzs;
+                    si = ((rr + 1) * RW + (face == 0 ? 1 : bys)) * P + 4 + 4 * q;
+                } else {
+                    rr -= 2 * bzs;
+                    face = rr >= bys ? 3 : 2;
+                    rr -= (face - 2) * bys;
+                    si = ((face == 2 ? 1 : bzs) * RW + rr + 1) * P + 4 + 4 * q;
+                }
+                __stcg(reinterpret_cast<float4 *>(fb + face * fslot + (size_t)rr * g.nx + 4 * q),
+                       *reinterpret_cast<const float4 *>(Yp + si));
+            }
+            __syncthreads();
+            if (tid == 0)   // release: the block's face stores above happen before the flag
+                asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(flags + b), "r"((unsigned int)(k + 1))
+                             : "memory");
+        }
+        resident_rows<TS>(g, sdg, ce, gam, somega[k], r, Yc, Yp, tid, nthr, nq, bys, bzs, y0, z0,
+                          RW, P, PL, warp_rows, false, dq, dy);
+        __syncthreads();
+        float *t = Yc;
+        Yc = Yp;
+        Yp = t;
+        if (last) break;
+        // wait for the neighbours' faces of y_{k+1}
+        if (tid < 4) {
+            const int nb = tid == 0 ? (iy > 0 ? b - 1 : -1)
+                         : tid == 1 ? (iy + 1 < bk.nby ? b + 1 : -1)
+                         : tid == 2 ? (iz > 0 ? b - bk.nby : -1)
+                                    : (iz + 1 < bk.nbz ? b + bk.nby : -1);
+            if (nb >= 0) {
+                const long long t0 = clock64();
+                while (true) {
+                    unsigned int f;
+                    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(f) : "l"(flags + nb) : "memory");
+                    if (f >= (unsigned int)(k + 1)) break;
+                    if (*(volatile int *)err) {
+                        s_stop = 1;
+                        break;
+                    }
+                    if (clock64() - t0 > budget) {
+                        atomicExch(err, 1);
+                        s_stop = 1;
+                        break;
+                    }
+                    __nanosleep(20);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) return;
+        // halo rows / planes from the neighbours' opposite faces
+        for (int it = tid; it < 2 * (bzs + bys) * nq; it += nthr) {
+            int rr = dq.div(it), side, si, nb, face;
+            const int q = it - rr * nq;
+            if (rr < 2 * bzs) {
+                side = rr >= bzs ? 1 : 0;   // 0: row y0-1 from the lower neighbour's top face
+                rr -= side * bzs;
+                if (side == 0 ? iy == 0 : iy + 1 == bk.nby) continue;
+                nb = side == 0 ? b - 1 : b + 1;
+                face = side == 0 ? 1 : 0;
+                si = ((rr + 1) * RW + (side == 0 ? 0 : bys + 1)) * P + 4 + 4 * q;
+            } else {
+                rr -= 2 * bzs;
+                side = rr >= bys ? 1 : 0;
+                rr -= side * bys;
+                if (side == 0 ? iz == 0 : iz + 1 == bk.nbz) continue;
+                nb = side == 0 ? b - bk.nby : b + bk.nby;
+                face = side == 0 ? 3 : 2;
+                si = ((side == 0 ? 0 : bzs + 1) * RW + rr + 1) * P + 4 + 4 * q;
+            }
+            const float *src = faces + ((size_t)nb * 2 + par) * 4 * fslot + face * fslot;
+            *reinterpret_cast<float4 *>(Yc + si) =
+                __ldcg(reinterpret_cast<const float4 *>(src + (size_t)rr * g.nx + 4 * q));
+        }
+        __syncthreads();
+    }
+    // y_m over the brick
+    for (int it = tid; it < nrow_b * nq; it += nthr) {
+        const int row = dq.div(it), q = it - row * nq;
+        const int zz = dy.div(row), yy = row - zz * bys;
+        const int si = ((zz + 1) * RW + (yy + 1)) * P + 4 + 4 * q;
+        Vec4<TS>::store(yout, ((size_t)(z0 + zz) * g.ny + (y0 + yy)) * g.nx + 4 * q,
+                        *reinterpret_cast<const float4 *>(Yc + si));
+    }
+}
+
 // ---------------------------------------------------------------- batched snapshots
 // Many independent snapshots (each its own hex mesh, bandwidth and Chebyshev count) are
 // smoothed by one persistent cooperative launch in the double-float modes.  Phases:
@@ -1606,6 +1856,164 @@ void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, i
     }
 }
 
+// Brick decomposition for k_cheb_resident: the smallest brick (rows x planes) such that
+// the bricks fit on the SMs one per SM and two padded brick arrays fit in one block's
+// shared memory.  Not available (ok = false) for several fields, nx % 4 != 0, more
+// iterations than the weight table holds, or a mesh too large for the SMs.
+struct ResidentPlan {
+    bool ok = false;
+    Brick bk{};
+    int nblocks = 0;
+    size_t smem = 0;       // dynamic shared memory per block
+    size_t ws_bytes = 0;   // flags | error word | faces
+};
+
+template <class TS>
+ResidentPlan plan_resident(const Geo &g, int nf, int m_it) {
+    ResidentPlan rp;
+    if (nf != 1 || g.nx % 4 != 0 || m_it < 2 || m_it > kResidentMaxIters) return rp;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return rp;
+    }
+    const int nsm = num_sms();
+    const size_t limit = (size_t)optin > 2048 ? (size_t)optin - 2048 : 0;   // static shared
+    const int P = g.nx + 8;
+    long long best_rows = -1;
+    int best_halo = 0;
+    for (int by = 1; by <= std::min(g.ny, 64); ++by)
+        for (int bz = 1; bz <= std::min(g.nz, 64); ++bz) {
+            const int nby = (g.ny + by - 1) / by, nbz = (g.nz + bz - 1) / bz;
+            if ((long long)nby * nbz > nsm) continue;
+            const size_t smem = 2ull * P * (by + 2) * (bz + 2) * 4;
+            if (smem > limit) continue;
+            const long long rows = (long long)by * bz;
+            if (best_rows < 0 || rows < best_rows || (rows == best_rows && by + bz < best_halo)) {
+                best_rows = rows;
+                best_halo = by + bz;
+                rp.bk = Brick{by, bz, nby, nbz, P, g.nx * std::max(by, bz)};
+                rp.smem = smem;
+                rp.nblocks = nby * nbz;
+            }
+        }
+    if (best_rows < 0) return rp;
+    // the attribute is raised to the device limit once for all meshes (a captured launch
+    // of another mesh may need more than this one)
+    if (cudaFuncSetAttribute(k_cheb_resident<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)limit) != cudaSuccess) {
+        cudaGetLastError();
+        return rp;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_resident<TS>, kResidentThreads,
+                                                      rp.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return rp;
+    }
+    if (per_sm < 1 || rp.nblocks > per_sm * nsm) return rp;
+    rp.ws_bytes = align_up((size_t)(rp.nblocks + 1) * 4) + (size_t)rp.nblocks * 8 * rp.bk.fmax * 4;
+    rp.ok = true;
+    return rp;
+}
+
+// One round's m-1 Chebyshev iterations as one resident launch; the flags are cleared
+// first (ws: flags | error word | faces, ws_bytes of plan_resident).  The error word is
+// left alone so that it collects every launch since the caller cleared it.
+template <class TS>
+cudaError_t launch_resident(const Geo &g, const ResidentPlan &rp, const Coef32 &cf, float gamma,
+                            double sigma, int m, const TS *y1, const TS *r, TS *yout, char *ws,
+                            long long budget, cudaStream_t st) {
+    unsigned int *flags = (unsigned int *)ws;
+    int *err = (int *)(ws + (size_t)rp.nblocks * 4);
+    float *faces = (float *)(ws + align_up((size_t)(rp.nblocks + 1) * 4));
+    ChebWeights om{};
+    double o = 1.0;
+    om.w[0] = 1.0f;
+    for (int k = 1; k < m; ++k) {
+        if (sigma > 0.0)
+            o = (k == 1) ? 1.0 / (1.0 - 1.0 / (2.0 * sigma * sigma))
+                         : 1.0 / (1.0 - o / (4.0 * sigma * sigma));
+        om.w[k] = (float)o;
+    }
+    cudaError_t e = cudaMemsetAsync(ws, 0, (size_t)rp.nblocks * 4, st);
+    if (e != cudaSuccess) return e;
+    Geo ga = g;
+    Brick bk = rp.bk;
+    Coef32 cfa = cf;
+    float ga_ = gamma;
+    int ma = m;
+    const TS *y1a = y1, *ra = r;
+    TS *ya = yout;
+    long long bu = budget;
+    void *args[] = {&ga, &bk, &cfa, &ga_, &om, &ma, &y1a, &ra, &ya, &faces, &flags, &err, &bu};
+    return cudaLaunchCooperativeKernel((const void *)k_cheb_resident<TS>, dim3(rp.nblocks),
+                                       dim3(kResidentThreads), args, rp.smem, st);
+}
+
+// Where the last of the m-1 streamed Chebyshev iterates lands (y_{k+1} over y_{k-1},
+// the first over `other`).
+template <class TS>
+TS *cheb_final_buffer(TS *y1, TS *other, int m) {
+    TS *yc = y1, *yp = nullptr;
+    for (int k = 1; k < m; ++k) {
+        TS *yn = yp ? yp : other;
+        yp = yc;
+        yc = yn;
+    }
+    return yc;
+}
+
+// Resident or streamed inner solve for m iterations: both are timed on the caller's
+// buffers (the round's whole Chebyshev loop, best of three after a warm-up) and the
+// faster is kept per mesh, field count, storage type and m.
+template <class TS>
+cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int code, int m_it,
+                        const Coef32 &cf, TS *ya, TS *yb, const TS *r, char *ws, cudaStream_t st,
+                        bool *use) {
+    const int key = -((m_it * 64 + 1) * 4 + (int)sizeof(TS));
+    for (auto &e : m->tuned)
+        if (e.first == key) {
+            *use = e.second != 0;
+            return CG_OK;
+        }
+    cudaEvent_t e0, e1;
+    CGK_CUDA(cudaEventCreate(&e0));
+    CGK_CUDA(cudaEventCreate(&e1));
+    float t[2] = {1e30f, 1e30f};
+    CGK_CUDA(cudaMemsetAsync(ws + (size_t)rp.nblocks * 4, 0, 4, st));
+    for (int variant = 0; variant < 2; ++variant)
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, st);
+            if (variant == 0) {
+                TS *yc = ya, *yp = nullptr;
+                for (int k = 1; k < m_it; ++k) {
+                    TS *yn = yp ? yp : yb;
+                    launch_cheb<TS>(code, g, 1, cf, 0.5f, 1.0f, yc, yp, r, yn, st);
+                    yp = yc;
+                    yc = yn;
+                }
+            } else {
+                CGK_CUDA(launch_resident<TS>(g, rp, cf, 0.5f, 0.0, m_it, ya, r, yb, ws, 2000000000LL, st));
+            }
+            cudaEventRecord(e1, st);
+            CGK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t[variant] = std::min(t[variant], ms);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CGK_CUDA(cudaGetLastError());
+    int errh = 0;
+    CGK_CUDA(cudaMemcpy(&errh, ws + (size_t)rp.nblocks * 4, 4, cudaMemcpyDeviceToHost));
+    if (errh) return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the resident inner solve gave up");
+    *use = t[1] < t[0];
+    m->tuned.push_back({key, *use ? 1 : 0});
+    return CG_OK;
+}
+
 // Autotuner of the Chebyshev sweep's shape (register-blocked with 2, 4 or 8 planes per
 // block, or z-marching with 1..32 planes per block): times a few launches of each
 // candidate on the caller's buffers (y_next is scratch at this point) and keeps the
@@ -1836,13 +2244,18 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     const Items items = make_items(g, nf, coopG);
     // barrier_budget > 0: the whole inner solve as one cooperative launch with bounded
     // grid barriers between iterations; otherwise one launch per iteration.
-    const bool persistent = p->barrier_budget > 0;
+    // (with sweep_shape = the resident code, barrier_budget bounds the resident waits)
+    const bool persistent = p->barrier_budget > 0 && p->sweep_shape != kResidentCode;
     const long long budget = persistent ? p->barrier_budget : 0;
 
     // buffers: X0 (double-float copy of u^0), X1, X2, B (XT); R, Ya, Yb (TS)
     const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
-    CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 3 * vts));
+    // the resident inner solve (whole mesh in shared memory) where it fits; its flags and
+    // faces follow the vectors
+    const ResidentPlan rp = persistent ? ResidentPlan{} : plan_resident<TS>(g, nf, m_it);
+    CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 3 * vts + (rp.ok ? rp.ws_bytes : 0)));
     char *wb = m->ws_diffuse.as<char>();
+    char *rws = wb + 4 * v64 + 3 * vts;
     XT *X1 = (XT *)wb, *X2 = (XT *)(wb + v64), *B = (XT *)(wb + 2 * v64), *X0 = (XT *)(wb + 3 * v64);
     TS *R = (TS *)(wb + 4 * v64), *Ya = (TS *)(wb + 4 * v64 + vts), *Yb = (TS *)(wb + 4 * v64 + 2 * vts);
     TS *const R_ = R;
@@ -1862,12 +2275,27 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     GridBar *hgb = (GridBar *)((char *)hsc + 64 * sizeof(RefScal));
 
     int cheb_code = p->sweep_shape;
-    if (cheb_code >= 100 && (m->nx % 4 != 0 || cheb_code - 100 < 1))
-        return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0 and at least one plane", cheb_code);
-    if (cheb_code != 0 && cheb_code != 2 && cheb_code != 4 && cheb_code != 8 && cheb_code > -1 &&
-        cheb_code < 100)
-        return fail(CG_EINVAL, "unknown sweep_shape %d", cheb_code);
-    if (cheb_code == 0) CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, R, st, &cheb_code));
+    bool resident = false;
+    if (cheb_code == kResidentCode) {
+        if (!rp.ok)
+            return fail(CG_EINVAL, "sweep_shape %d needs one field, nx %% 4 == 0, at most %d inner "
+                        "iterations, one-launch solves and a mesh that fits in shared memory",
+                        kResidentCode, kResidentMaxIters);
+        resident = true;
+    } else {
+        if (cheb_code >= 100 && (m->nx % 4 != 0 || cheb_code - 100 < 1 || cheb_code >= 200))
+            return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0 and 1..99 planes", cheb_code);
+        if (cheb_code != 0 && cheb_code != 2 && cheb_code != 4 && cheb_code != 8 && cheb_code > -1 &&
+            cheb_code < 100)
+            return fail(CG_EINVAL, "unknown sweep_shape %d", cheb_code);
+        const bool auto_shape = cheb_code == 0;
+        if (auto_shape) CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, R, st, &cheb_code));
+        if (auto_shape && rp.ok)
+            CGK_TRY(tune_resident<TS>(m, g, rp, cheb_code, m_it, cf32, Ya, Yb, R, rws, st, &resident));
+    }
+    const int shape_used = resident ? kResidentCode : cheb_code;
+    // clock cycles a resident wait may take (about one second by default)
+    const long long rbudget = (resident && p->barrier_budget > 0) ? p->barrier_budget : 2000000000LL;
 
     // ---- double-float modes: a fixed schedule captured as a CUDA graph.  The whole call
     // (conversion, every step's passes and inner iterations, R refinement rounds per
@@ -1909,7 +2337,8 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                 }
                 if (it->nf == nf && it->precision == p->precision && it->scheme == p->scheme &&
                     it->nsteps == p->nsteps && it->rounds == R && it->T == T && it->tol == p->tol &&
-                    it->cells == cells && it->profiled == prof)
+                    it->cells == cells && it->profiled == prof && it->code == shape_used &&
+                    it->wait_budget == rbudget)
                     ge = &*it;
                 ++it;
             }
@@ -1930,10 +2359,14 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                 e.gen_diffuse = m->ws_diffuse.gen;
                 e.gen_small = m->ws_small.gen;
                 e.profiled = prof;
+                e.code = shape_used;
+                e.wait_budget = rbudget;
                 prof_capture_begin(&e.records, &e.kernels);
+                cudaError_t cap_err = cudaSuccess;   // a launch refused while capturing
                 cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
                 if (ce == cudaSuccess) {
                     cudaMemsetAsync(hist, 0, hist_n * sizeof(RefScal), cs);
+                    if (resident) cudaMemsetAsync(rws + (size_t)rp.nblocks * 4, 0, 4, cs);
                     CGK_LAUNCH("to_double_float", (double)n * nf * 16, cs,
                                k_to_df<<<stencil_grid(n * nf), kThreads, 0, cs>>>(
                                    (size_t)n * nf, cells, (DF *)X0));
@@ -1956,7 +2389,18 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                         for (int r = 0; r < R; ++r) {
                             TS *yc = y1, *yp = nullptr, *yo = (y1 == Ya) ? Yb : Ya;
                             double om = 1.0;
-                            if (m_it > 1) {
+                            if (m_it > 1 && resident) {
+                                TS *yf = cheb_final_buffer(yc, yo, m_it);
+                                CGK_LAUNCH(sizeof(TS) == 2 ? "cheb_resident_bf16" : "cheb_resident_fp32",
+                                           (double)n * nf * sizeof(TS) * (3.0 + 4.0 * (m_it - 2)), cs,
+                                           {
+                                               cudaError_t le = launch_resident<TS>(
+                                                   g, rp, cf32, (float)gamma, sigma_d, m_it, yc, R_,
+                                                   yf, rws, rbudget, cs);
+                                               if (cap_err == cudaSuccess) cap_err = le;
+                                           });
+                                yc = yf;
+                            } else if (m_it > 1) {
                                 CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb_bf16" : "cheb_fp32",
                                           (double)n * nf * sizeof(TS) * (3.0 + 4.0 * (m_it - 2)),
                                           cs, m_it - 1);
@@ -2003,6 +2447,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                     result = u;
                     cudaGraph_t graph = nullptr;
                     ce = cudaStreamEndCapture(cs, &graph);
+                    if (ce == cudaSuccess) ce = cap_err;
                     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e.exec, graph, 0);
                     if (graph) cudaGraphDestroy(graph);
                 }
@@ -2021,8 +2466,14 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             CGK_CUDA(cudaGraphLaunch(ge->exec, st));
             RefScal *hh = (RefScal *)(m->h_small.as<char>() + 4096);
             CGK_CUDA(cudaMemcpyAsync(hh, hist, hist_n * sizeof(RefScal), cudaMemcpyDeviceToHost, st));
+            int *herr = (int *)(m->h_small.as<char>() + 1024);
+            *herr = 0;
+            if (resident)
+                CGK_CUDA(cudaMemcpyAsync(herr, rws + (size_t)rp.nblocks * 4, 4, cudaMemcpyDeviceToHost, st));
             CGK_CUDA(cudaStreamSynchronize(st));
             prof_account_replay(*ge);
+            if (*herr)
+                return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the resident inner solve gave up");
             bool ok = true;
             double worst_g = 0.0;
             for (size_t i = 0; i < hist_n; ++i) {
@@ -2042,7 +2493,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                     rep->cell_updates = apps * nf * (long long)n;
                     rep->final_rel_residual = worst_g;
                     rep->inner_iters_per_round = m_it;
-                    rep->sweep_shape_used = cheb_code;
+                    rep->sweep_shape_used = shape_used;
                 }
                 return CG_OK;
             }
@@ -2074,6 +2525,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
         ubuf = X0;
     }
     XT *F1 = X1, *F2 = X2;                   // the two buffers not holding u^n
+    if (resident) CGK_CUDA(cudaMemsetAsync(rws + (size_t)rp.nblocks * 4, 0, 4, st));
     bool converged = true, timed_out = false;
     int s = 0;
     for (; s < p->nsteps; ++s) {
@@ -2117,7 +2569,14 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                                                 dim3(coopG), dim3(TX, TY), args, 0,
                                                                 st)));
             }
-            {
+            if (m_it > 1 && resident) {
+                TS *yf = cheb_final_buffer(ycur, yother, m_it);
+                CGK_LAUNCH(sizeof(TS) == 2 ? "cheb_resident_bf16" : "cheb_resident_fp32",
+                           (double)n * nf * sizeof(TS) * (3.0 + 4.0 * (m_it - 2)), st,
+                           CGK_CUDA(launch_resident<TS>(g, rp, cf32, (float)gamma, sigma_d, m_it,
+                                                        ycur, R, yf, rws, rbudget, st)));
+                ycur = yf;
+            } else {
                 double om = 1.0;
                 for (int k = 1; k < m_it; ++k) {
                     if (sigma_d > 0.0)
@@ -2157,8 +2616,11 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                 CGK_CUDA(cudaMemcpyAsync(hsc, sc, nf * sizeof(RefScal), cudaMemcpyDeviceToHost, st));
                 if (persistent)
                     CGK_CUDA(cudaMemcpyAsync(hgb, gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+                if (resident)   // the resident error word, in the barrier's err slot
+                    CGK_CUDA(cudaMemcpyAsync(&hgb->err, rws + (size_t)rp.nblocks * 4, 4,
+                                             cudaMemcpyDeviceToHost, st));
                 CGK_CUDA(cudaStreamSynchronize(st));
-                if (persistent && hgb->err) {
+                if ((persistent || resident) && hgb->err) {
                     timed_out = true;
                     break;
                 }
@@ -2195,10 +2657,11 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
         rep->cell_updates = applications * nf * (long long)n;
         rep->final_rel_residual = worst;
         rep->inner_iters_per_round = m_it;
-        rep->sweep_shape_used = persistent ? 0 : cheb_code;
+        rep->sweep_shape_used = persistent ? 0 : shape_used;
     }
     if (timed_out)
-        return fail(CG_ETIMEOUT, "cg_diffuse: a grid barrier of the inner solve gave up (step %d)", s);
+        return fail(CG_ETIMEOUT, "cg_diffuse: a %s of the inner solve gave up (step %d)",
+                    resident ? "neighbour wait" : "grid barrier", s);
     if (!converged)
         return fail(CG_ENOCONV, "cg_diffuse: refinement did not reach tol in step %d", s);
     return CG_OK;
