@@ -30,27 +30,75 @@ inline int grid_for(int64_t n, int per_block = kThreads, int max_blocks_per_sm =
 }
 
 // --------------------------------------------------------------------------- locate
-// Host cell per axis: i = floor((x - x0) * inv_dx) clamped into [0, n-1]; outside
-// unless x0 <= x <= hi on every axis (NaN is outside).  Every FP64 operation is an
-// explicitly rounded intrinsic so that no multiply-add is contracted.
+// Host cell per axis: i = floor(fl(fl(x - x0) * inv_dx)) clamped into [0, n-1]; outside
+// unless x0 <= x <= hi on every axis (NaN is outside).  FP64 arithmetic is slow on this
+// GPU, so the result is first taken from an FP32 estimate with a rigorous error bound,
+// and the FP64 definition (explicitly rounded intrinsics, no contraction) is evaluated
+// only when the bound does not keep the estimate away from an integer -- the answer is
+// the FP64 definition's either way.  The domain test compares doubles exactly as
+// ordered integer keys.
+
+// A double as a 64-bit key in the order of the doubles (-0 as +0; a NaN sorts above +inf
+// or below -inf by its sign, so it fails one side of a range test).
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (b == 0x8000000000000000ull) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// A float carrying the sign, exponent and top 20 fraction bits of v (relative error
+// below 2^-20); ok is cleared outside float's normal range.  Zero maps to zero.
+__device__ __forceinline__ float approx20(double v, bool &ok) {
+    const int hi = __double2hiint(v);
+    const unsigned int lo = (unsigned int)__double2loint(v);
+    const int e = (hi >> 20) & 0x7ff;
+    const unsigned int frac = (unsigned int)hi & 0xfffffu;
+    if (e == 0 && frac == 0 && lo == 0) return 0.0f;
+    const int e32 = e - 1023 + 127;
+    if (e32 < 1 || e32 > 254) {
+        ok = false;
+        return 0.0f;
+    }
+    return __int_as_float((int)(((unsigned int)hi & 0x80000000u) | ((unsigned int)e32 << 23) | (frac << 3)));
+}
+
+// floor(fl(fl(x - o) * inv)) for x >= o.  With xf = approx20(x), of and invf the FP32
+// roundings of o and inv, rf = (xf - of) * invf differs from the FP64 value by less than
+// (|xf| + |of|) invf 2^-20 (1 + 2^-20) + 3 |rf| 2^-24 + 2 |rf| 2^-53; the bound used is
+// four times the first term plus 2^-18 |rf|.  If rf's fraction clears it on both sides,
+// both values have the same floor.
+__device__ __forceinline__ int cell_index(double x, double o, double inv, float of, float invf) {
+    bool ok = true;
+    const float xf = approx20(x, ok);
+    const float rf = (xf - of) * invf;
+    const float bound = (fabsf(xf) + fabsf(of)) * invf * 0x1p-18f + fabsf(rf) * 0x1p-18f;
+    const float fl = floorf(rf);
+    const float fr = rf - fl;   // exact (Sterbenz)
+    if (ok && rf >= 0.0f && rf < 4194304.0f && fr > bound && fr < 1.0f - bound) return (int)fl;
+    return (int)floor(__dmul_rn(__dsub_rn(x, o), inv));
+}
+
 __global__ void k_locate_structured(int64_t n, const double *__restrict__ pos, int nx, int ny,
                                     int nz, double ox, double oy, double oz, double inv_dx,
-                                    double hx, double hy, double hz, int nf,
-                                    const double *__restrict__ w, int32_t *__restrict__ cell,
-                                    uint32_t *__restrict__ counts,
+                                    double hx, double hy, double hz, float oxf, float oyf,
+                                    float ozf, float invf, int nf, const double *__restrict__ w,
+                                    int32_t *__restrict__ cell, uint32_t *__restrict__ counts,
                                     unsigned long long *__restrict__ bad) {
     unsigned long long n_out = 0, n_nonfinite = 0;
+    const unsigned long long kox = dkey(ox), koy = dkey(oy), koz = dkey(oz);
+    const unsigned long long khx = dkey(hx), khy = dkey(hy), khz = dkey(hz);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
+        const double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
         for (int f = 0; f < nf; ++f)
-            if (!isfinite(w[(int64_t)f * n + i])) ++n_nonfinite;
-        bool inside = (x >= ox) && (x <= hx) && (y >= oy) && (y <= hy) && (z >= oz) && (z <= hz);
+            if (((__double2hiint(w[(int64_t)f * n + i]) >> 20) & 0x7ff) == 0x7ff) ++n_nonfinite;
+        const unsigned long long kx = dkey(x), ky = dkey(y), kz = dkey(z);
+        const bool inside = kx >= kox && kx <= khx && ky >= koy && ky <= khy && kz >= koz && kz <= khz;
         int32_t c = -1;
         if (inside) {
-            int ix = (int)floor(__dmul_rn(__dsub_rn(x, ox), inv_dx));
-            int iy = (int)floor(__dmul_rn(__dsub_rn(y, oy), inv_dx));
-            int iz = (int)floor(__dmul_rn(__dsub_rn(z, oz), inv_dx));
+            int ix = cell_index(x, ox, inv_dx, oxf, invf);
+            int iy = cell_index(y, oy, inv_dx, oyf, invf);
+            int iz = cell_index(z, oz, inv_dx, ozf, invf);
             ix = min(max(ix, 0), nx - 1);
             iy = min(max(iy, 0), ny - 1);
             iz = min(max(iz, 0), nz - 1);
@@ -70,6 +118,16 @@ __global__ void k_locate_structured(int64_t n, const double *__restrict__ pos, i
         if (n_out) atomicAdd(&bad[0], n_out);
         if (n_nonfinite) atomicAdd(&bad[1], n_nonfinite);
     }
+}
+
+// largest per-cell count (into *mx)
+__global__ void k_max_u32(int64_t n, const uint32_t *__restrict__ v, unsigned long long *mx) {
+    uint32_t m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, (unsigned long long)m);
 }
 
 // --------------------------------------------------------------------------- scan
@@ -273,6 +331,57 @@ __global__ void k_segment_heads(int64_t n, const uint32_t *__restrict__ keys,
     }
 }
 
+// Counting path of the ordered sums (cells holding at most kSegMax particles): each
+// particle goes to a slot of its cell's segment, found by decrementing the cell's count
+// (the order inside a segment is arbitrary), then one thread per cell sorts its
+// segment's particle ids and adds the weights in ascending particle index.
+constexpr int kSegMax = 64;
+
+__global__ void k_scatter_cells(int64_t n, const int32_t *__restrict__ cell,
+                                const uint32_t *__restrict__ off, uint32_t *__restrict__ cnt,
+                                uint32_t *__restrict__ idx) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cell[i];
+        idx[off[c] + atomicSub(&cnt[c], 1u) - 1u] = (uint32_t)i;
+    }
+}
+
+// eps_c = (sum of the cell's weights in ascending particle index, FP64 from +0.0) / V_c;
+// an empty cell gets +0.0.
+__global__ void k_cell_sums(int64_t ncells, const uint32_t *__restrict__ off,
+                            const uint32_t *__restrict__ idx, int nf,
+                            const double *__restrict__ w, int64_t n,
+                            const double *__restrict__ vc, double vc_uniform,
+                            double *__restrict__ out) {
+    uint32_t s[kSegMax];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t beg = off[c];
+        const int k = (int)(off[c + 1] - beg);
+        if (k == 0) {
+            for (int f = 0; f < nf; ++f) out[(int64_t)f * ncells + c] = 0.0;
+            continue;
+        }
+        for (int j = 0; j < k; ++j) {   // insertion sort of the segment's ids
+            const uint32_t v = idx[beg + j];
+            int q = j;
+            while (q > 0 && s[q - 1] > v) {
+                s[q] = s[q - 1];
+                --q;
+            }
+            s[q] = v;
+        }
+        const double v = vc ? vc[c] : vc_uniform;
+        for (int f = 0; f < nf; ++f) {
+            const double *wf = w + (int64_t)f * n;
+            double acc = 0.0;
+            for (int j = 0; j < k; ++j) acc = __dadd_rn(acc, wf[s[j]]);
+            out[(int64_t)f * ncells + c] = __ddiv_rn(acc, v);
+        }
+    }
+}
+
 // max |w| per field as the bit pattern of a non-negative double (orders like uint64)
 __global__ void k_absmax(int64_t n, int nf, const double *__restrict__ w,
                          unsigned long long *__restrict__ out) {
@@ -351,11 +460,11 @@ cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, co
 
 cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                      int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
-                     cudaStream_t st) {
+                     cudaStream_t st, uint32_t *max_count) {
     CGK_TRY(m->ws_small.ensure(4096));
     CGK_TRY(m->h_small.ensure(4096));
     unsigned long long *bad = m->ws_small.as<unsigned long long>();
-    CGK_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), st));
+    CGK_CUDA(cudaMemsetAsync(bad, 0, 3 * sizeof(unsigned long long), st));
     if (n > 0) {
         if (m->kind == MESH_STRUCTURED) {
             double hi[3];
@@ -368,18 +477,26 @@ cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const dou
             CGK_LAUNCH("locate_structured", (double)n * (24 + 8 * nf + 4), st,
                        k_locate_structured<<<grid_for(n), kThreads, 0, st>>>(
                            n, pos, m->nx, m->ny, m->nz, m->origin[0], m->origin[1],
-                           m->origin[2], inv_dx, hi[0], hi[1], hi[2], nf, w, cell_out, counts,
-                           bad));
+                           m->origin[2], inv_dx, hi[0], hi[1], hi[2], (float)m->origin[0],
+                           (float)m->origin[1], (float)m->origin[2], (float)inv_dx, nf, w,
+                           cell_out, counts, bad));
             CGK_CUDA(cudaGetLastError());
         } else {
             CGK_TRY(tet_locate_launch(m, n, pos, nf, w, cell_out, counts, bad, st));
         }
+        if (counts && max_count) {
+            CGK_LAUNCH("count_max", (double)m->ncells * 4, st,
+                       k_max_u32<<<grid_for(m->ncells), kThreads, 0, st>>>(m->ncells, counts,
+                                                                          bad + 2));
+            CGK_CUDA(cudaGetLastError());
+        }
     }
     unsigned long long *hb = m->h_small.as<unsigned long long>();
-    CGK_CUDA(cudaMemcpyAsync(hb, bad, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CGK_CUDA(cudaMemcpyAsync(hb, bad, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CGK_CUDA(cudaStreamSynchronize(st));
     if (n_out) *n_out = (int64_t)hb[0];
     if (n_nonfinite) *n_nonfinite = (int64_t)hb[1];
+    if (max_count) *max_count = (uint32_t)hb[2];
     return CG_OK;
 }
 
@@ -402,9 +519,15 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
     const double *vc = m->kind == MESH_TET ? m->tet.vc : nullptr;
     const double vcu = m->kind == MESH_TET ? 0.0 : (m->dx * m->dx) * m->dx;
 
-    // workspace: cell[n] (int32)
-    CGK_TRY(m->ws_locate.ensure(align_up((size_t)(n > 0 ? n : 1) * 4)));
+    // workspace: cell[n] (int32); the ordered mode also counts particles per cell
+    // (ncells + 1 counters, the last one staying 0 for the exclusive scan)
+    const bool ordered = mode == CG_DEPOSIT_ORDERED;
+    const size_t s_cell = align_up((size_t)(n > 0 ? n : 1) * 4);
+    const size_t s_cnt = align_up((size_t)(ncells + 1) * 4);
+    CGK_TRY(m->ws_locate.ensure(s_cell + (ordered ? s_cnt : 0)));
     int32_t *cell = m->ws_locate.as<int32_t>();
+    uint32_t *counts = ordered ? (uint32_t *)(m->ws_locate.as<char>() + s_cell) : nullptr;
+    if (counts) CGK_CUDA(cudaMemsetAsync(counts, 0, (size_t)(ncells + 1) * 4, st));
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (rep) {
@@ -412,7 +535,9 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         CGK_CUDA(cudaEventRecord(ev[0], st));
     }
     int64_t n_out = 0, n_bad = 0;
-    CGK_TRY(locate_run(m, n, pos, nf, w, cell, nullptr, &n_out, &n_bad, st));
+    uint32_t max_count = 0;
+    CGK_TRY(locate_run(m, n, pos, nf, w, cell, counts, &n_out, &n_bad, st,
+                       counts ? &max_count : nullptr));
     if (rep) {
         CGK_CUDA(cudaEventRecord(ev[1], st));
         rep->n_out_of_domain = n_out;
@@ -421,8 +546,30 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
     if (n_out)
         return fail(CG_EDOMAIN, "cg_deposit: %lld particles outside the mesh", (long long)n_out);
 
-    if (mode == CG_DEPOSIT_ORDERED) {
-        // stable sort of (cell, particle) by cell
+    if (ordered && max_count <= (uint32_t)kSegMax) {
+        // counting sort by cell: offsets = exclusive scan of the counts, a scatter into the
+        // segments, then per cell the segment's ids in ascending order and the ordered sum
+        const size_t s_off = s_cnt;
+        const size_t s_idx = align_up((size_t)(n > 0 ? n : 1) * 4);
+        const size_t s_tmp = align_up(scan_tmp_words(ncells + 1) * 4);
+        CGK_TRY(m->ws_sort.ensure(s_off + s_idx + s_tmp));
+        char *sb = m->ws_sort.as<char>();
+        uint32_t *off = (uint32_t *)sb, *idx = (uint32_t *)(sb + s_off);
+        uint32_t *tmp = (uint32_t *)(sb + s_off + s_idx);
+        CGK_TRY(exclusive_scan_u32(counts, off, ncells + 1, tmp, st));
+        if (n > 0) {
+            CGK_LAUNCH("scatter_cells", (double)n * 16, st,
+                       k_scatter_cells<<<grid_for(n), kThreads, 0, st>>>(n, cell, off, counts, idx));
+            CGK_CUDA(cudaGetLastError());
+        }
+        CGK_LAUNCH("cell_sums", (double)n * (4 + 8 * nf) + (double)ncells * (4 + 8 * nf), st,
+                   k_cell_sums<<<grid_for(ncells), kThreads, 0, st>>>(ncells, off, idx, nf, w, n,
+                                                                      vc, vcu, out));
+        CGK_CUDA(cudaGetLastError());
+        if (rep)
+            for (int f = 0; f < nf && f < CG_REPORT_MAX_FIELDS; ++f) rep->fixed_point_bits[f] = 0;
+    } else if (ordered) {
+        // a crowded cell: stable sort of (cell, particle) by cell
         int bits = 1;
         while (bits < 32 && ((int64_t)1 << bits) < ncells) ++bits;
         int passes = (bits + kRadixBits - 1) / kRadixBits;

@@ -66,6 +66,33 @@ def test_locate_bit_exact(cg, orc, dims, origin, dx):
     assert np.array_equal(got.cpu().numpy(), ref)
 
 
+def test_locate_near_faces_bit_exact(cg, orc):
+    """Positions a few ulps either side of every face plane, on an offset origin with an
+    inexact spacing (and -0.0 on a wall at 0): the estimate-then-confirm locate must give
+    the FP64 definition's cell everywhere."""
+    dims, dx = (29, 17, 13), 1.0 / 7.0
+    for origin in ((-3.7, 0.0, 1e-3), (0.0, 123.456, -0.5)):
+        rng = np.random.default_rng(11)
+        o = np.array(origin)
+        faces = [o[a] + np.arange(dims[a] + 1) * dx for a in range(3)]
+        cols = []
+        for a in range(3):
+            f = np.repeat(faces[a], 9)
+            ulps = np.tile(np.arange(-4, 5), dims[a] + 1)
+            cols.append(f + ulps * np.spacing(np.abs(f) + 1e-300))
+        n = max(len(c) for c in cols)
+        pos = np.empty((3, n))
+        for a in range(3):
+            pos[a] = np.resize(cols[a], n)
+            rng.shuffle(pos[a])
+        pos[:, 0] = [-0.0 if origin[0] == 0.0 else origin[0], pos[1, 0], pos[2, 0]]
+        ref, nref = orc.locate_structured(dims, origin, dx, pos)
+        mesh = cg.StructuredMesh(dims, origin, dx)
+        got, nout = cg.locate(mesh, dev(pos))
+        assert nout == nref
+        assert np.array_equal(got.cpu().numpy(), ref)
+
+
 # ----------------------------------------------------------------------------- deposit
 def _deposit_case(orc, cg, dims, origin, dx, pos, w, mode):
     cell, nout = orc.locate_structured(dims, origin, dx, pos)
@@ -107,6 +134,20 @@ def test_deposit_degenerate_inputs(cg, orc, mode):
     # a single particle; particles exactly on the upper walls
     _deposit_case(orc, cg, dims, origin, dx, np.array([[1.125], [0.625], [0.375]]),
                   np.array([[2.0]]), mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("crowd", [64, 65])
+def test_deposit_crowded_cell_both_paths(cg, orc, mode, crowd):
+    """One cell holding 64 particles (the largest the per-cell sort takes) or 65 (the
+    stable radix sort takes over), among scattered others: bit-exact either way."""
+    dims, origin, dx = (16, 16, 16), (0.0, 0.0, 0.0), 1.0 / 16
+    rng = np.random.default_rng(12)
+    pos = rng.random((3, 5000))
+    idx = rng.choice(5000, crowd, replace=False)
+    pos[:, idx] = 0.51
+    w = rng.standard_normal((2, 5000)) * 10.0 ** rng.integers(-6, 6, (2, 5000))
+    _deposit_case(orc, cg, dims, origin, dx, pos, w, mode)
 
 
 def test_deposit_empty_and_errors(cg, orc):
