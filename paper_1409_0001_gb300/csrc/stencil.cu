@@ -1248,6 +1248,144 @@ __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nz
                            yprev_all ? yprev_all + off : nullptr, r_all + off, ynext_all + off);
 }
 
+// ---------------------------------------------------------------- two iterations per sweep
+// Iterations k and k+1 of the Chebyshev recurrence in one launch (temporal blocking), for
+// rows of at most 128 cells (nx <= 128, nx % 4 == 0: a warp holds a whole row, four cells
+// per lane, so x needs no halo).  A block owns TY2 rows and a z-chunk; it also computes
+// y_{k+1} on the row above and the row below (from y_k on two rows either side), which
+// y_{k+2} needs.  It marches q over the chunk's planes plus one either side: y_{k+1} on
+// plane q from y_k (register queue over q-1, q, q+1; rows from a shared plane), then
+// y_{k+2} on plane q-1 from y_{k+1} (register queue, rows from a second shared plane).
+// y_{k+1} and y_{k+2} go to two buffers that nothing in the launch reads, so the rows a
+// block recomputes never race with their owners' writes (four buffers rotate across
+// launches).  Arithmetic and its order per cell are those of k_cheb_v4.
+constexpr int TY2 = 8;
+constexpr int kCheb2Threads = 32 * (TY2 + 2);
+
+// A value as the storage type holds it (y_{k+1} is used by iteration k+1 exactly as the
+// one-iteration sweep would read it back from memory).
+template <class TS> __device__ __forceinline__ float4 as_stored(float4 v) { return v; }
+template <> __device__ __forceinline__ float4 as_stored<__nv_bfloat16>(float4 v) {
+    return make_float4(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)),
+                       __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
+}
+constexpr int kPairCode = 200;   // sweep_shape 200 + z: two iterations per launch, z planes
+
+template <class TS>
+__global__ void __launch_bounds__(kCheb2Threads, 2)
+    k_cheb2_v4(Geo g, int zlen, int nzc, Coef32 cf, float gamma, float om1, float om2,
+               const TS *__restrict__ yk_all, const TS *__restrict__ ykm_all,
+               const TS *__restrict__ r_all, TS *__restrict__ c_all, TS *__restrict__ d_all) {
+    chain_wait();
+    chain_release();
+    using V = Vec4<TS>;
+    __shared__ float4 Sk[TY2 + 4][32];   // y_k on plane q, rows y0-2 .. y0+TY2+1
+    __shared__ float4 Su[TY2 + 2][32];   // y_{k+1} on plane q-1, rows y0-1 .. y0+TY2
+    __shared__ float sdg[8];
+    stage_table(sdg, cf.dg);
+    const int f = blockIdx.z / nzc;
+    const int z0 = (blockIdx.z - f * nzc) * zlen, z1 = min(g.nz, z0 + zlen);
+    const size_t off = (size_t)f * g.n;
+    const TS *yk = yk_all + off;
+    const TS *ykm = ykm_all ? ykm_all + off : nullptr;
+    const TS *r = r_all + off;
+    TS *yc = c_all + off;
+    TS *yd = d_all + off;
+    const int tx = threadIdx.x, t = threadIdx.y;
+    const int x = 4 * tx;
+    const int y0 = blockIdx.y * TY2, y = y0 - 1 + t;
+    const bool ownx = x < g.nx;
+    const bool rowin = y >= 0 && y < g.ny && ownx;
+    const bool inner = t >= 1 && t <= TY2 && y < g.ny && ownx;   // rows this block writes
+    const bool hlo = t == 0 && y0 - 2 >= 0 && ownx;                // also loads row y0-2
+    const bool hhi = t == TY2 + 1 && y0 + TY2 + 1 < g.ny && ownx;  // also loads row y0+TY2+1
+    const int nyb = (y > 0) + (y + 1 < g.ny);
+    const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx), n12 = nyb + 2;
+    auto at = [&](int q, int yy) -> size_t { return ((size_t)q * g.ny + yy) * g.nx + x; };
+    const int qs = max(z0 - 1, 0);
+    // queues at q = qs
+    float4 vkm = f4zero(), vk0 = f4zero(), vkp = f4zero(), hk = f4zero();
+    float4 ypq = f4zero(), rq = f4zero(), rprev = f4zero();
+    if (rowin) {
+        if (qs > 0) vkm = V::load(yk, at(qs - 1, y));
+        vk0 = V::load(yk, at(qs, y));
+        if (qs + 1 < g.nz) vkp = V::load(yk, at(qs + 1, y));
+        if (ykm) ypq = V::load(ykm, at(qs, y));
+        rq = V::load(r, at(qs, y));
+    }
+    if (hlo) hk = V::load(yk, at(qs, y0 - 2));
+    if (hhi) hk = V::load(yk, at(qs, y0 + TY2 + 1));
+    float4 um = f4zero(), u0 = f4zero();
+    for (int q = qs; q <= z1; ++q) {
+        // loads for plane q+1 (y_k two planes ahead)
+        float4 nvkp = f4zero(), nhk = f4zero(), nyp = f4zero(), nr = f4zero();
+        if (q + 1 < g.nz) {
+            if (rowin) {
+                if (q + 2 < g.nz) nvkp = V::load(yk, at(q + 2, y));
+                if (ykm) nyp = V::load(ykm, at(q + 1, y));
+                nr = V::load(r, at(q + 1, y));
+            }
+            if (hlo) nhk = V::load(yk, at(q + 1, y0 - 2));
+            if (hhi) nhk = V::load(yk, at(q + 1, y0 + TY2 + 1));
+        }
+        Sk[t + 1][tx] = vk0;
+        if (t == 0) Sk[0][tx] = hk;
+        if (t == TY2 + 1) Sk[TY2 + 3][tx] = hk;
+        Su[t][tx] = u0;
+        // x neighbours of y_k (plane q) and of y_{k+1} (plane q-1) across lanes
+        const float kl = __shfl_up_sync(0xffffffffu, vk0.w, 1);
+        const float kr = __shfl_down_sync(0xffffffffu, vk0.x, 1);
+        const float ul = __shfl_up_sync(0xffffffffu, u0.w, 1);
+        const float ur = __shfl_down_sync(0xffffffffu, u0.x, 1);
+        __syncthreads();
+        // y_{k+1} on plane q
+        float4 un = f4zero();
+        if (q < g.nz && rowin) {
+            const float4 up = Sk[t][tx], dn = Sk[t + 2][tx];
+            const float left = tx == 0 ? 0.f : kl, right = x + 4 < g.nx ? kr : 0.f;
+            const int nz_ = (q > 0) + (q + 1 < g.nz);
+            float4 s;
+            s.x = left + vk0.y + up.x + dn.x + vkm.x + vkp.x;
+            s.y = vk0.x + vk0.z + up.y + dn.y + vkm.y + vkp.y;
+            s.z = vk0.y + vk0.w + up.z + dn.z + vkm.z + vkp.z;
+            s.w = vk0.z + right + up.w + dn.w + vkm.w + vkp.w;
+            un.x = fmaf(om1, vk0.x - ypq.x + gamma * (rq.x - fmaf(sdg[n0 + nz_], vk0.x, -cf.ce * s.x)), ypq.x);
+            un.y = fmaf(om1, vk0.y - ypq.y + gamma * (rq.y - fmaf(sdg[n12 + nz_], vk0.y, -cf.ce * s.y)), ypq.y);
+            un.z = fmaf(om1, vk0.z - ypq.z + gamma * (rq.z - fmaf(sdg[n12 + nz_], vk0.z, -cf.ce * s.z)), ypq.z);
+            un.w = fmaf(om1, vk0.w - ypq.w + gamma * (rq.w - fmaf(sdg[n3 + nz_], vk0.w, -cf.ce * s.w)), ypq.w);
+            un = as_stored<TS>(un);
+            if (inner && q >= z0 && q < z1) V::store(yc, at(q, y), un);
+        }
+        // y_{k+2} on plane z = q-1
+        const int z = q - 1;
+        if (inner && z >= z0 && z < z1) {
+            const float4 up = Su[t - 1][tx], dn = Su[t + 1][tx];
+            const float left = tx == 0 ? 0.f : ul, right = x + 4 < g.nx ? ur : 0.f;
+            const int nz_ = (z > 0) + (z + 1 < g.nz);
+            float4 s, o;
+            s.x = left + u0.y + up.x + dn.x + um.x + un.x;
+            s.y = u0.x + u0.z + up.y + dn.y + um.y + un.y;
+            s.z = u0.y + u0.w + up.z + dn.z + um.z + un.z;
+            s.w = u0.z + right + up.w + dn.w + um.w + un.w;
+            o.x = fmaf(om2, u0.x - vkm.x + gamma * (rprev.x - fmaf(sdg[n0 + nz_], u0.x, -cf.ce * s.x)), vkm.x);
+            o.y = fmaf(om2, u0.y - vkm.y + gamma * (rprev.y - fmaf(sdg[n12 + nz_], u0.y, -cf.ce * s.y)), vkm.y);
+            o.z = fmaf(om2, u0.z - vkm.z + gamma * (rprev.z - fmaf(sdg[n12 + nz_], u0.z, -cf.ce * s.z)), vkm.z);
+            o.w = fmaf(om2, u0.w - vkm.w + gamma * (rprev.w - fmaf(sdg[n3 + nz_], u0.w, -cf.ce * s.w)), vkm.w);
+            V::store(yd, at(z, y), o);
+        }
+        __syncthreads();
+        um = u0;
+        u0 = un;
+        vkm = vk0;
+        vk0 = vkp;
+        vkp = nvkp;
+        hk = nhk;
+        ypq = nyp;
+        rprev = rq;
+        rq = nr;
+    }
+}
+
 // ---------------------------------------------------------------- on-chip resident sweep
 constexpr int kResidentThreads = 1024;
 constexpr int kResidentMaxIters = 128;
@@ -1838,6 +1976,66 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
     }
 }
 
+// Chebyshev iterations k and k+1 in one launch (k_cheb2_v4): zlen planes per block.
+inline bool cheb2_fits(const Geo &g) { return g.nx % 4 == 0 && g.nx <= 128; }
+
+template <class TS>
+void launch_cheb2(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, float om1,
+                  float om2, const TS *yk, const TS *ykm, const TS *r, TS *yc, TS *yd,
+                  cudaStream_t st) {
+    zlen = std::max(1, std::min(zlen, g.nz));
+    const int nzc = (g.nz + zlen - 1) / zlen;
+    const dim3 grid(1, (g.ny + TY2 - 1) / TY2, nzc * nf);
+    launch_chain(k_cheb2_v4<TS>, grid, dim3(32, TY2 + 2), st, g, zlen, nzc, cf, gamma, om1, om2,
+                 yk, ykm, r, yc, yd);
+}
+
+// The m-1 Chebyshev iterations of a round from y1 (y_0 = 0), two per launch; a last odd
+// iteration runs alone in the vectorised sweep (code 100 + zlen).  Four buffers rotate:
+// each pair launch writes its two iterates to the two buffers it does not read.
+// `pool` holds y1's buffer first and three spares; returns the buffer holding y_m.
+template <class TS>
+TS *cheb_pairs(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, double sigma, int m,
+               TS *const pool[4], const TS *r, cudaStream_t st) {
+    TS *cur = pool[0], *prev = nullptr;
+    double om = 1.0;
+    auto omega_next = [&](int k) {
+        if (sigma > 0.0)
+            om = (k == 1) ? 1.0 / (1.0 - 1.0 / (2.0 * sigma * sigma))
+                          : 1.0 / (1.0 - om / (4.0 * sigma * sigma));
+        return (float)om;
+    };
+    int k = 1;
+    while (k < m) {
+        if (k + 1 < m) {
+            const float o1 = omega_next(k), o2 = omega_next(k + 1);
+            TS *n1 = nullptr, *n2 = nullptr;
+            for (int i = 0; i < 4; ++i) {
+                if (pool[i] == cur || pool[i] == prev) continue;
+                if (!n1) n1 = pool[i];
+                else if (!n2) n2 = pool[i];
+            }
+            CGK_LAUNCH_UNTIMED(st, launch_cheb2<TS>(zlen, g, nf, cf, gamma, o1, o2, cur, prev, r,
+                                                    n1, n2, st));
+            prev = n1;
+            cur = n2;
+            k += 2;
+        } else {
+            const float o1 = omega_next(k);
+            TS *yn = prev;
+            if (!yn)
+                for (int i = 0; i < 4 && !yn; ++i)
+                    if (pool[i] != cur) yn = pool[i];
+            CGK_LAUNCH_UNTIMED(st, launch_cheb<TS>(100 + zlen, g, nf, cf, gamma, o1, cur, prev, r,
+                                                   yn, st));
+            prev = cur;
+            cur = yn;
+            k += 1;
+        }
+    }
+    return cur;
+}
+
 // A double-float refinement pass of mode kMode: the two-cells-per-thread kernel when nx
 // is even, the scalar one otherwise; both use the z-chunks of sw (same partial slots).
 template <class TS, int kMode>
@@ -1970,8 +2168,8 @@ TS *cheb_final_buffer(TS *y1, TS *other, int m) {
 // faster is kept per mesh, field count, storage type and m.
 template <class TS>
 cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int code, int m_it,
-                        const Coef32 &cf, TS *ya, TS *yb, const TS *r, char *ws, cudaStream_t st,
-                        bool *use) {
+                        const Coef32 &cf, TS *ya, TS *yb, TS *yc4, TS *yd4, const TS *r, char *ws,
+                        cudaStream_t st, bool *use) {
     const int key = -((m_it * 64 + 1) * 4 + (int)sizeof(TS));
     for (auto &e : m->tuned)
         if (e.first == key) {
@@ -1986,7 +2184,10 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
     for (int variant = 0; variant < 2; ++variant)
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, st);
-            if (variant == 0) {
+            if (variant == 0 && code >= kPairCode && code < kResidentCode) {
+                TS *const pool[4] = {ya, yb, yc4, yd4};
+                cheb_pairs<TS>(code - kPairCode, g, 1, cf, 0.5f, 0.0, m_it, pool, r, st);
+            } else if (variant == 0) {
                 TS *yc = ya, *yp = nullptr;
                 for (int k = 1; k < m_it; ++k) {
                     TS *yn = yp ? yp : yb;
@@ -2014,13 +2215,14 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
     return CG_OK;
 }
 
-// Autotuner of the Chebyshev sweep's shape (register-blocked with 2, 4 or 8 planes per
-// block, or z-marching with 1..32 planes per block): times a few launches of each
-// candidate on the caller's buffers (y_next is scratch at this point) and keeps the
-// fastest.  The choice is cached per mesh, field count and storage type.
+// Autotuner of the Chebyshev sweep's shape (vectorised, register-blocked with 2, 4 or 8
+// planes per block, z-marching with 1..16 planes per block, or two iterations per launch
+// with 1..16 planes per block where rows fit a warp): times a few launches of each
+// candidate on the caller's buffers (all scratch at this point) and keeps the fastest
+// per iteration.  The choice is cached per mesh, field count and storage type.
 template <class TS>
-cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, TS *yb,
-                    const TS *r, cudaStream_t st, int *code_out) {
+cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, TS *yb, TS *yc,
+                    TS *yd, const TS *r, cudaStream_t st, int *code_out) {
     const int key = nf * 4 + (int)sizeof(TS);
     for (auto &e : m->tuned)
         if (e.first == key) {
@@ -2057,6 +2259,7 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     }
     std::sort(timing.begin(), timing.end());
     int best_code = timing[0].second;
+    float best_time = timing[0].first;
     if (v4) {
         float best_v4 = 1e30f;
         int code_v4 = 0;
@@ -2065,7 +2268,32 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
                 best_v4 = tc.first;
                 code_v4 = tc.second;
             }
-        if (code_v4 && best_v4 <= 1.03f * timing[0].first) best_code = code_v4;
+        if (code_v4 && best_v4 <= 1.03f * timing[0].first) {
+            best_code = code_v4;
+            best_time = best_v4;
+        }
+    }
+    // two iterations per launch: bursts of 5 launches (10 iterations)
+    if (cheb2_fits(g)) {
+        for (int z : {1, 2, 4, 8, 16}) {
+            for (int w = 0; w < 2; ++w)
+                launch_cheb2<TS>(z, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc, yd, st);
+            float best_burst = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                for (int q = 0; q < 5; ++q)
+                    launch_cheb2<TS>(z, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc, yd, st);
+                cudaEventRecord(e1, st);
+                CGK_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best_burst = std::min(best_burst, ms);
+            }
+            if (best_burst < best_time) {
+                best_time = best_burst;
+                best_code = kPairCode + z;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2253,11 +2481,13 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     // the resident inner solve (whole mesh in shared memory) where it fits; its flags and
     // faces follow the vectors
     const ResidentPlan rp = persistent ? ResidentPlan{} : plan_resident<TS>(g, nf, m_it);
-    CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 3 * vts + (rp.ok ? rp.ws_bytes : 0)));
+    CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 5 * vts + (rp.ok ? rp.ws_bytes : 0)));
     char *wb = m->ws_diffuse.as<char>();
-    char *rws = wb + 4 * v64 + 3 * vts;
+    char *rws = wb + 4 * v64 + 5 * vts;
     XT *X1 = (XT *)wb, *X2 = (XT *)(wb + v64), *B = (XT *)(wb + 2 * v64), *X0 = (XT *)(wb + 3 * v64);
     TS *R = (TS *)(wb + 4 * v64), *Ya = (TS *)(wb + 4 * v64 + vts), *Yb = (TS *)(wb + 4 * v64 + 2 * vts);
+    // two more iterate buffers for two-iterations-per-launch sweeps
+    TS *Yc = (TS *)(wb + 4 * v64 + 3 * vts), *Yd = (TS *)(wb + 4 * v64 + 4 * vts);
     TS *const R_ = R;
     // small workspace: partials | scalars | barrier | per-step residual history
     const size_t hist_off = 4096 + align_up((size_t)nf * 2 * G * 8) + 64 * sizeof(RefScal) + 256;
@@ -2283,15 +2513,19 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                         kResidentCode, kResidentMaxIters);
         resident = true;
     } else {
-        if (cheb_code >= 100 && (m->nx % 4 != 0 || cheb_code - 100 < 1 || cheb_code >= 200))
+        if (cheb_code >= kPairCode && (!cheb2_fits(g) || cheb_code - kPairCode < 1))
+            return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0, nx <= 128 and 1..99 planes",
+                        cheb_code);
+        if (cheb_code >= 100 && cheb_code < kPairCode && (m->nx % 4 != 0 || cheb_code - 100 < 1))
             return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0 and 1..99 planes", cheb_code);
         if (cheb_code != 0 && cheb_code != 2 && cheb_code != 4 && cheb_code != 8 && cheb_code > -1 &&
             cheb_code < 100)
             return fail(CG_EINVAL, "unknown sweep_shape %d", cheb_code);
         const bool auto_shape = cheb_code == 0;
-        if (auto_shape) CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, R, st, &cheb_code));
+        if (auto_shape) CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, Yc, Yd, R, st, &cheb_code));
         if (auto_shape && rp.ok)
-            CGK_TRY(tune_resident<TS>(m, g, rp, cheb_code, m_it, cf32, Ya, Yb, R, rws, st, &resident));
+            CGK_TRY(tune_resident<TS>(m, g, rp, cheb_code, m_it, cf32, Ya, Yb, Yc, Yd, R, rws, st,
+                                      &resident));
     }
     const int shape_used = resident ? kResidentCode : cheb_code;
     // clock cycles a resident wait may take (about one second by default)
@@ -2400,6 +2634,16 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                                if (cap_err == cudaSuccess) cap_err = le;
                                            });
                                 yc = yf;
+                            } else if (m_it > 1 && cheb_code >= kPairCode) {
+                                const int np = (m_it - 1) / 2, ns = (m_it - 1) % 2;
+                                CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb2_bf16" : "cheb2_fp32",
+                                          (double)n * nf * sizeof(TS) *
+                                              (np > 0 ? 4.0 + 5.0 * (np - 1) : 0.0) +
+                                              (double)n * nf * sizeof(TS) * 4.0 * ns,
+                                          cs, np + ns);
+                                TS *const pool[4] = {yc, yo, Yc, Yd};   // y1 is Ya or Yb
+                                yc = cheb_pairs<TS>(cheb_code - kPairCode, g, nf, cf32, (float)gamma,
+                                                    sigma_d, m_it, pool, R_, cs);
                             } else if (m_it > 1) {
                                 CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb_bf16" : "cheb_fp32",
                                           (double)n * nf * sizeof(TS) * (3.0 + 4.0 * (m_it - 2)),
@@ -2569,7 +2813,15 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                                                 dim3(coopG), dim3(TX, TY), args, 0,
                                                                 st)));
             }
-            if (m_it > 1 && resident) {
+            if (m_it > 1 && !persistent && !resident && cheb_code >= kPairCode) {
+                const int np = (m_it - 1) / 2, ns = (m_it - 1) % 2;
+                CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb2_bf16" : "cheb2_fp32",
+                          (double)n * nf * sizeof(TS) * ((np > 0 ? 4.0 + 5.0 * (np - 1) : 0.0) + 4.0 * ns),
+                          st, np + ns);
+                TS *const pool[4] = {ycur, yother, Yc, Yd};   // y1 is Ya or Yb
+                ycur = cheb_pairs<TS>(cheb_code - kPairCode, g, nf, cf32, (float)gamma, sigma_d,
+                                      m_it, pool, R, st);
+            } else if (m_it > 1 && resident) {
                 TS *yf = cheb_final_buffer(ycur, yother, m_it);
                 CGK_LAUNCH(sizeof(TS) == 2 ? "cheb_resident_bf16" : "cheb_resident_fp32",
                            (double)n * nf * sizeof(TS) * (3.0 + 4.0 * (m_it - 2)), st,

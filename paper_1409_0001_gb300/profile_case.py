@@ -29,6 +29,9 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tet", action="store_true", help="Kuhn tet mesh of n^3 hexes instead")
     ap.add_argument("--shape", type=int, default=0, help="sweep_shape (0 = autotuned)")
+    ap.add_argument("--deposit", action="store_true",
+                    help="ordered deposition of the clustered n^3 workload (2,000,000 spheres "
+                         "at n = 128) instead of a diffusion")
     a = ap.parse_args(argv)
 
     import numpy as np
@@ -39,6 +42,20 @@ def main(argv=None):
     import workloads as W
 
     build.build()
+    if a.deposit:
+        c = W.clustered_cube(n_side=a.n, n_particles=2_000_000 * (a.n // 128) ** 3 or 2_000_000)
+        mesh = cg.StructuredMesh(c.dims, c.origin, c.dx)
+        pos, w = torch.from_numpy(c.pos).cuda(), torch.from_numpy(c.w).cuda()
+        for r in range(a.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rep = cg.deposit(mesh, pos, w, cg.Params(), report=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            print("rep %d: %.3f ms (locate %.3f, deposit %.3f), %.3e particles/s"
+                  % (r, dt * 1e3, rep["ms_locate"], rep["ms_deposit"], c.n / dt))
+        mesh.close()
+        return
     dims = tuple(a.dims) if a.dims else (a.n, a.n, a.n)
     dx = 1.0 / dims[0]
     if a.tet:

@@ -1,0 +1,120 @@
+"""GPU parity of the two-iterations-per-launch Chebyshev sweep (sweep_shape 200 + z:
+iterations k and k+1 in one launch, rows of at most 128 cells, z planes per block).
+
+Per cell it evaluates the same expression, in the same order, as the one-iteration
+vectorised sweep (sweep_shape 100 + z), so with the same z the two must agree bit for
+bit, whatever the parity of the iteration count; both must meet the mixed-precision bar
+(1e-6 max-relative) against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1409_0001_gb300 as cg
+    from paper_1409_0001_gb300 import build
+    build.build()
+    cg.load_library()
+    return cg
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.int64)
+
+
+def maxrel(u, ref):
+    u, ref = np.atleast_2d(u), np.atleast_2d(ref)
+    return max(np.max(np.abs(u[f] - ref[f])) / np.max(np.abs(ref[f])) for f in range(ref.shape[0]))
+
+
+def field(shape, seed):
+    rng = np.random.default_rng(seed)
+    u0 = rng.random(shape) * 0.2
+    n = u0.shape[-1]
+    idx = rng.integers(0, n, max(n // 40, 3))
+    u0[..., idx] += 10.0
+    return u0
+
+
+# rows of 128 (a full warp), 36 (a partial warp), 4; ragged last row tile (ny % 8 != 0);
+# b/dx 1 and 3 give odd and even iteration counts per round
+@pytest.mark.parametrize("dims", [(128, 20, 13), (36, 17, 9), (4, 9, 30), (64, 64, 64)])
+@pytest.mark.parametrize("z", [1, 4, 16])
+@pytest.mark.parametrize("b_over_dx", [1, 3])
+def test_pairs_bit_identical_to_single_sweep(cg, orc, dims, z, b_over_dx):
+    dx = 1.0 / dims[0]
+    u0 = field((2, int(np.prod(dims))), 50)
+    T = (b_over_dx * dx) ** 2 / 4
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx)
+    outs = {}
+    for shape in (200 + z, 100 + z):
+        u = dev(u0)
+        _, rep = cg.diffuse(mesh, u, cg.Params(T=T, nsteps=10, precision=3, sweep_shape=shape),
+                            report=True)
+        assert rep["sweep_shape_used"] == shape
+        assert rep["final_rel_residual"] <= 1e-13
+        outs[shape] = u.cpu().numpy()
+    assert np.array_equal(bits(outs[200 + z]), bits(outs[100 + z]))
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 10, tol=1e-15)
+    assert maxrel(outs[200 + z], ref) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,scheme", [(1, 0), (4, 0), (3, 1)])
+def test_pairs_other_modes_bit_identical(cg, orc, precision, scheme):
+    """IEEE-FP64 refinement (adaptive schedule), BF16 storage, Crank-Nicolson."""
+    dims = (96, 40, 24)
+    dx = 1.0 / 96
+    u0 = field((1, int(np.prod(dims))), 51)
+    T = (4 * dx) ** 2 / 4
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx)
+    outs = {}
+    for shape in (204, 104):
+        u = dev(u0)
+        cg.diffuse(mesh, u, cg.Params(T=T, nsteps=10, precision=precision, scheme=scheme,
+                                      sweep_shape=shape))
+        outs[shape] = u.cpu().numpy()
+    assert np.array_equal(bits(outs[204]), bits(outs[104]))
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 10, scheme=scheme, tol=1e-15)
+    assert maxrel(outs[204], ref) <= MIXED_TOL
+
+
+def test_pairs_full_size_clustered_128(cg, orc):
+    """The 128^3 clustered case (2,000,000 spheres), b = 2 dx, whole method: two
+    iterations per launch reproduce the one-iteration sweep bit for bit."""
+    c = W.clustered_cube()
+    cell, _ = orc.locate_structured(c.dims, c.origin, c.dx, c.pos)
+    eps0, _ = orc.deposit(cell, c.w, c.ncells, vc_uniform=(c.dx * c.dx) * c.dx)
+    ref, _ = orc.diffuse_structured(eps0, c.dims, c.dx, c.b ** 2 / 4, c.nsteps, tol=1e-14)
+    mesh = cg.StructuredMesh(c.dims, c.origin, c.dx)
+    pos, w = dev(c.pos), dev(c.w)
+    outs = {}
+    for shape in (208, 108):
+        got = cg.coarse_grain(mesh, pos, w, cg.Params(bandwidth=c.b, nsteps=c.nsteps, precision=3,
+                                                      sweep_shape=shape))
+        outs[shape] = got.cpu().numpy()
+    assert np.array_equal(bits(outs[208]), bits(outs[108]))
+    assert maxrel(outs[208], ref) <= MIXED_TOL
+
+
+def test_pairs_reject_long_rows(cg):
+    for dims in ((132, 8, 8), (30, 8, 8)):
+        mesh = cg.StructuredMesh(dims, (0, 0, 0), 1.0 / dims[0])
+        with pytest.raises(cg.CGError) as e:
+            cg.diffuse(mesh, dev(np.zeros((1, int(np.prod(dims))))),
+                       cg.Params(bandwidth=0.1, precision=3, sweep_shape=204))
+        assert e.value.code == "CG_EINVAL"
