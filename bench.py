@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the tet, batched and channel workloads")
+    ap.add_argument("--sweep-shape", type=int, default=0,
+                    help="inner-solve sweep shape for the mixed modes (include/cg.h "
+                         "sweep_shape; 0 = autotuned)")
     return ap.parse_args()
 
 
@@ -120,20 +123,41 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def source_section(path, start, end):
+    """The text of a source file from the line that begins with `start` up to (not
+    including) the line that begins with `end`."""
+    with open(os.path.join(ROOT, path)) as f:
+        text = f.read()
+    i = text.index(start)
+    return text[i:text.index(end, i + len(start))]
+
+
 def ncu_traffic(kernel_entry):
     """DRAM bytes per launch of a kernel from the committed ncu capture, or None when the
-    kernel's source changed since the counters were taken."""
+    kernel's source section changed since the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f).get(kernel_entry)
         if not rec:
             return None
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        return rec["dram_bytes_per_launch"] if sha == rec["source_sha256"] else None
+        sec = source_section(rec["source"], rec["section_start"], rec["section_end"])
+        sha = hashlib.sha256(sec.encode()).hexdigest()
+        return rec["dram_bytes_per_launch"] if sha == rec["section_sha256"] else None
     except (OSError, ValueError, KeyError):
         return None
+
+
+def nvtx(push, name):
+    """Open (push) or close an NVTX range, where torch's NVTX binding is present."""
+    try:
+        import torch
+        if push:
+            torch.cuda.nvtx.range_push(name)
+        else:
+            torch.cuda.nvtx.range_pop()
+    except (RuntimeError, AttributeError):
+        pass
 
 
 def measured_peaks():
@@ -218,7 +242,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def params(bdx, precision):
-        return cg.Params(bandwidth=bdx * c.dx, nsteps=NSTEPS, precision=precision, tol=TOL)
+        return cg.Params(bandwidth=bdx * c.dx, nsteps=NSTEPS, precision=precision, tol=TOL,
+                         sweep_shape=a.sweep_shape if precision != cg.PREC_FP64 else 0)
 
     def one_step(precision, reps):
         for i, bdx in enumerate(B_OVER_DX):
@@ -231,18 +256,24 @@ def main():
             dist.barrier()
             torch.cuda.synchronize()
 
-    def timed(fn, steps):
-        """Per-step CUDA-event time (L2 flushed before every step, outside the events)."""
+    def timed(fn, steps, label=None):
+        """Per-step CUDA-event time (L2 flushed before every step, outside the events).
+        With a label, each step is an NVTX range of that name (a profiler can select the
+        step's kernels by it)."""
         stream = torch.cuda.current_stream()
         tot = 0.0
         for _ in range(steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            if label:
+                nvtx(True, label)
             e0.record(stream)
             fn()
             e1.record(stream)
             e1.synchronize()
+            if label:
+                nvtx(False, label)
             tot += e0.elapsed_time(e1)
         return tot
 
@@ -262,10 +293,11 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
+    launches_before = int(lib.cg_launch_count())
     lib.cg_launch_count_reset()
     reps = []
     barrier()
-    ms = timed(lambda: one_step(MAIN, reps), a.steps)
+    ms = timed(lambda: one_step(MAIN, reps), a.steps, label="timed_step")
     barrier()
     launches = int(lib.cg_launch_count())
     clocks = sampler.stop()
@@ -372,6 +404,8 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "entry_point": "cg_coarse_grain_host (pinned host buffers)"},
             "gpu_launches": launches,
+            "gpu_launches_before_timed": launches_before,
+            "sweep_shape_used": sorted({r["sweep_shape_used"] for r in reps}),
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,

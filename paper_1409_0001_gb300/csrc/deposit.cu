@@ -62,6 +62,12 @@ __device__ __forceinline__ float approx20(double v, bool &ok) {
     return __int_as_float((int)(((unsigned int)hi & 0x80000000u) | ((unsigned int)e32 << 23) | (frac << 3)));
 }
 
+// The FP64 definition itself, out of line so that it is not evaluated speculatively for
+// every particle.
+__device__ __noinline__ int cell_index_exact(double x, double o, double inv) {
+    return (int)floor(__dmul_rn(__dsub_rn(x, o), inv));
+}
+
 // floor(fl(fl(x - o) * inv)) for x >= o.  With xf = approx20(x), of and invf the FP32
 // roundings of o and inv, rf = (xf - of) * invf differs from the FP64 value by less than
 // (|xf| + |of|) invf 2^-20 (1 + 2^-20) + 3 |rf| 2^-24 + 2 |rf| 2^-53; the bound used is
@@ -75,7 +81,7 @@ __device__ __forceinline__ int cell_index(double x, double o, double inv, float 
     const float fl = floorf(rf);
     const float fr = rf - fl;   // exact (Sterbenz)
     if (ok && rf >= 0.0f && rf < 4194304.0f && fr > bound && fr < 1.0f - bound) return (int)fl;
-    return (int)floor(__dmul_rn(__dsub_rn(x, o), inv));
+    return cell_index_exact(x, o, inv);
 }
 
 __global__ void k_locate_structured(int64_t n, const double *__restrict__ pos, int nx, int ny,
@@ -83,8 +89,10 @@ __global__ void k_locate_structured(int64_t n, const double *__restrict__ pos, i
                                     double hx, double hy, double hz, float oxf, float oyf,
                                     float ozf, float invf, int nf, const double *__restrict__ w,
                                     int32_t *__restrict__ cell, uint32_t *__restrict__ counts,
+                                    uint32_t *__restrict__ ranks,
                                     unsigned long long *__restrict__ bad) {
     unsigned long long n_out = 0, n_nonfinite = 0;
+    uint32_t most = 0;   // largest per-cell count seen (counts != nullptr)
     const unsigned long long kox = dkey(ox), koy = dkey(oy), koz = dkey(oz);
     const unsigned long long khx = dkey(hx), khy = dkey(hy), khz = dkey(hz);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -103,31 +111,27 @@ __global__ void k_locate_structured(int64_t n, const double *__restrict__ pos, i
             iy = min(max(iy, 0), ny - 1);
             iz = min(max(iz, 0), nz - 1);
             c = (int32_t)(((int64_t)iz * ny + iy) * nx + ix);
-            if (counts) atomicAdd(&counts[c], 1u);
+            if (counts) {   // the arrival rank orders nothing: it only picks a free slot
+                const uint32_t r = atomicAdd(&counts[c], 1u);
+                if (ranks) ranks[i] = r;
+                most = max(most, r + 1u);
+            }
         } else {
             ++n_out;
         }
         cell[i] = c;
     }
-    // warp-aggregate the rare error counters
+    // warp-aggregate the rare error counters and the largest count
     for (int o = 16; o > 0; o >>= 1) {
         n_out += __shfl_down_sync(0xffffffffu, n_out, o);
         n_nonfinite += __shfl_down_sync(0xffffffffu, n_nonfinite, o);
+        most = max(most, __shfl_down_sync(0xffffffffu, most, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (n_out) atomicAdd(&bad[0], n_out);
         if (n_nonfinite) atomicAdd(&bad[1], n_nonfinite);
+        if (most) atomicMax(&bad[2], (unsigned long long)most);
     }
-}
-
-// largest per-cell count (into *mx)
-__global__ void k_max_u32(int64_t n, const uint32_t *__restrict__ v, unsigned long long *mx) {
-    uint32_t m = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m = max(m, v[i]);
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, (unsigned long long)m);
 }
 
 // --------------------------------------------------------------------------- scan
@@ -332,19 +336,17 @@ __global__ void k_segment_heads(int64_t n, const uint32_t *__restrict__ keys,
 }
 
 // Counting path of the ordered sums (cells holding at most kSegMax particles): each
-// particle goes to a slot of its cell's segment, found by decrementing the cell's count
-// (the order inside a segment is arbitrary), then one thread per cell sorts its
-// segment's particle ids and adds the weights in ascending particle index.
+// particle goes to the slot of its cell's segment given by its arrival rank at the
+// cell's counter (so the order inside a segment is arbitrary), then one thread per cell
+// sorts its segment's particle ids and adds the weights in ascending particle index.
 constexpr int kSegMax = 64;
 
 __global__ void k_scatter_cells(int64_t n, const int32_t *__restrict__ cell,
-                                const uint32_t *__restrict__ off, uint32_t *__restrict__ cnt,
+                                const uint32_t *__restrict__ off, const uint32_t *__restrict__ ranks,
                                 uint32_t *__restrict__ idx) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = cell[i];
-        idx[off[c] + atomicSub(&cnt[c], 1u) - 1u] = (uint32_t)i;
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        idx[off[cell[i]] + ranks[i]] = (uint32_t)i;
 }
 
 // eps_c = (sum of the cell's weights in ascending particle index, FP64 from +0.0) / V_c;
@@ -455,12 +457,12 @@ cg_status exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint3
 
 // Forward declaration of the tet locate launcher (tet.cu).
 cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
-                            int32_t *cell_out, uint32_t *counts, unsigned long long *bad,
-                            cudaStream_t st);
+                            int32_t *cell_out, uint32_t *counts, uint32_t *ranks,
+                            unsigned long long *bad, cudaStream_t st);
 
 cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                      int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
-                     cudaStream_t st, uint32_t *max_count) {
+                     cudaStream_t st, uint32_t *max_count, uint32_t *ranks) {
     CGK_TRY(m->ws_small.ensure(4096));
     CGK_TRY(m->h_small.ensure(4096));
     unsigned long long *bad = m->ws_small.as<unsigned long long>();
@@ -479,16 +481,10 @@ cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const dou
                            n, pos, m->nx, m->ny, m->nz, m->origin[0], m->origin[1],
                            m->origin[2], inv_dx, hi[0], hi[1], hi[2], (float)m->origin[0],
                            (float)m->origin[1], (float)m->origin[2], (float)inv_dx, nf, w,
-                           cell_out, counts, bad));
+                           cell_out, counts, ranks, bad));
             CGK_CUDA(cudaGetLastError());
         } else {
-            CGK_TRY(tet_locate_launch(m, n, pos, nf, w, cell_out, counts, bad, st));
-        }
-        if (counts && max_count) {
-            CGK_LAUNCH("count_max", (double)m->ncells * 4, st,
-                       k_max_u32<<<grid_for(m->ncells), kThreads, 0, st>>>(m->ncells, counts,
-                                                                          bad + 2));
-            CGK_CUDA(cudaGetLastError());
+            CGK_TRY(tet_locate_launch(m, n, pos, nf, w, cell_out, counts, ranks, bad, st));
         }
     }
     unsigned long long *hb = m->h_small.as<unsigned long long>();
@@ -521,12 +517,14 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
 
     // workspace: cell[n] (int32); the ordered mode also counts particles per cell
     // (ncells + 1 counters, the last one staying 0 for the exclusive scan)
+    // and keeps each particle's arrival rank at its cell's counter
     const bool ordered = mode == CG_DEPOSIT_ORDERED;
     const size_t s_cell = align_up((size_t)(n > 0 ? n : 1) * 4);
     const size_t s_cnt = align_up((size_t)(ncells + 1) * 4);
-    CGK_TRY(m->ws_locate.ensure(s_cell + (ordered ? s_cnt : 0)));
+    CGK_TRY(m->ws_locate.ensure(s_cell + (ordered ? s_cnt + s_cell : 0)));
     int32_t *cell = m->ws_locate.as<int32_t>();
     uint32_t *counts = ordered ? (uint32_t *)(m->ws_locate.as<char>() + s_cell) : nullptr;
+    uint32_t *ranks = ordered ? (uint32_t *)(m->ws_locate.as<char>() + s_cell + s_cnt) : nullptr;
     if (counts) CGK_CUDA(cudaMemsetAsync(counts, 0, (size_t)(ncells + 1) * 4, st));
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -537,7 +535,7 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
     int64_t n_out = 0, n_bad = 0;
     uint32_t max_count = 0;
     CGK_TRY(locate_run(m, n, pos, nf, w, cell, counts, &n_out, &n_bad, st,
-                       counts ? &max_count : nullptr));
+                       counts ? &max_count : nullptr, ranks));
     if (rep) {
         CGK_CUDA(cudaEventRecord(ev[1], st));
         rep->n_out_of_domain = n_out;
@@ -559,7 +557,7 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         CGK_TRY(exclusive_scan_u32(counts, off, ncells + 1, tmp, st));
         if (n > 0) {
             CGK_LAUNCH("scatter_cells", (double)n * 16, st,
-                       k_scatter_cells<<<grid_for(n), kThreads, 0, st>>>(n, cell, off, counts, idx));
+                       k_scatter_cells<<<grid_for(n), kThreads, 0, st>>>(n, cell, off, ranks, idx));
             CGK_CUDA(cudaGetLastError());
         }
         CGK_LAUNCH("cell_sums", (double)n * (4 + 8 * nf) + (double)ncells * (4 + 8 * nf), st,

@@ -209,11 +209,12 @@ void graph_release(GraphEntry &e);
 // ----------------------------------------------------------------------------- phases
 // Locate (structured or tet).  Writes cell ids (int32, -1 outside) to cell_out and the
 // number outside / number of non-finite weights to the host.  If counts != nullptr
-// also accumulates per-cell particle counts (must be zeroed by the caller) and, if
-// max_count != nullptr, returns the largest of them.
+// also accumulates per-cell particle counts (must be zeroed by the caller), writes each
+// particle's arrival rank at its cell's counter to ranks (if not nullptr) and returns
+// the largest count in max_count (if not nullptr).
 cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                      int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
-                     cudaStream_t st, uint32_t *max_count = nullptr);
+                     cudaStream_t st, uint32_t *max_count = nullptr, uint32_t *ranks = nullptr);
 
 // Deposition (Eq. (pcm-k)) given particles; validates and writes out[nf][ncells].
 cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,

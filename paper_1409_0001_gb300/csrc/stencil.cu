@@ -2163,9 +2163,10 @@ TS *cheb_final_buffer(TS *y1, TS *other, int m) {
     return yc;
 }
 
-// Resident or streamed inner solve for m iterations: both are timed on the caller's
-// buffers (the round's whole Chebyshev loop, best of three after a warm-up) and the
-// faster is kept per mesh, field count, storage type and m.
+// Resident or streamed inner solve for m iterations: both are captured as CUDA graphs on
+// the caller's buffers (the round's whole Chebyshev loop, as the solver runs it), and
+// the faster replay (best of three after a warm-up) is kept per mesh, field count,
+// storage type and m.
 template <class TS>
 cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int code, int m_it,
                         const Coef32 &cf, TS *ya, TS *yb, TS *yc4, TS *yd4, const TS *r, char *ws,
@@ -2176,37 +2177,54 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
             *use = e.second != 0;
             return CG_OK;
         }
+    if (!m->capture_stream)
+        CGK_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
     float t[2] = {1e30f, 1e30f};
     CGK_CUDA(cudaMemsetAsync(ws + (size_t)rp.nblocks * 4, 0, 4, st));
-    for (int variant = 0; variant < 2; ++variant)
-        for (int rep = 0; rep < 4; ++rep) {
-            cudaEventRecord(e0, st);
+    cudaError_t ce = cudaSuccess;
+    for (int variant = 0; variant < 2 && ce == cudaSuccess; ++variant) {
+        cudaStream_t cs = m->capture_stream;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t le = cudaSuccess;
+        ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
             if (variant == 0 && code >= kPairCode && code < kResidentCode) {
                 TS *const pool[4] = {ya, yb, yc4, yd4};
-                cheb_pairs<TS>(code - kPairCode, g, 1, cf, 0.5f, 0.0, m_it, pool, r, st);
+                cheb_pairs<TS>(code - kPairCode, g, 1, cf, 0.5f, 0.0, m_it, pool, r, cs);
             } else if (variant == 0) {
                 TS *yc = ya, *yp = nullptr;
                 for (int k = 1; k < m_it; ++k) {
                     TS *yn = yp ? yp : yb;
-                    launch_cheb<TS>(code, g, 1, cf, 0.5f, 1.0f, yc, yp, r, yn, st);
+                    launch_cheb<TS>(code, g, 1, cf, 0.5f, 1.0f, yc, yp, r, yn, cs);
                     yp = yc;
                     yc = yn;
                 }
             } else {
-                CGK_CUDA(launch_resident<TS>(g, rp, cf, 0.5f, 0.0, m_it, ya, r, yb, ws, 2000000000LL, st));
+                le = launch_resident<TS>(g, rp, cf, 0.5f, 0.0, m_it, ya, r, yb, ws, 2000000000LL, cs);
             }
+            ce = cudaStreamEndCapture(cs, &graph);
+            if (ce == cudaSuccess) ce = le;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        for (int rep = 0; rep < 4 && ce == cudaSuccess; ++rep) {
+            cudaEventRecord(e0, st);
+            ce = cudaGraphLaunch(exec, st);
             cudaEventRecord(e1, st);
-            CGK_CUDA(cudaEventSynchronize(e1));
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0) t[variant] = std::min(t[variant], ms);
         }
+        if (exec) cudaGraphExecDestroy(exec);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    CGK_CUDA(cudaGetLastError());
+    if (ce != cudaSuccess) return cuda_fail(ce, "resident autotuner", __FILE__, __LINE__);
     int errh = 0;
     CGK_CUDA(cudaMemcpy(&errh, ws + (size_t)rp.nblocks * 4, 4, cudaMemcpyDeviceToHost));
     if (errh) return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the resident inner solve gave up");
@@ -2229,75 +2247,73 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
             *code_out = e.second;
             return CG_OK;
         }
-    // vectorised shapes need whole 4-cell vectors per row
-    const bool v4 = g.nx % 4 == 0;
-    const int all[] = {101, 102, 104, 108, 116, 2, 4, 8, -1, -4, -16};
-    std::vector<int> cands;
-    for (int c : all)
-        if (c < 100 || v4) cands.push_back(c);
+    if (!m->capture_stream)
+        CGK_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+    // candidates: code, and how many launches make 10 iterations
+    std::vector<std::pair<int, int>> cands;
+    const bool v4 = g.nx % 4 == 0;   // vectorised shapes need whole 4-cell vectors per row
+    for (int c : {101, 102, 104, 108, 116, 2, 4, 8, -1, -4, -16})
+        if (c < 100 || v4) cands.push_back({c, 10});
+    if (cheb2_fits(g))
+        for (int z : {1, 2, 4, 8, 16}) cands.push_back({kPairCode + z, 5});
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
-    // per shape: 2 warm-up launches, then 3 bursts of 10 back-to-back launches timed by
-    // one event pair each, the fastest burst counts; the vectorised shape is kept
-    // unless another is more than 3 % faster
+    // per shape: 10 iterations captured as a CUDA graph (as the solver runs them), one
+    // warm-up replay, then the fastest of three timed replays; the vectorised shape is
+    // kept unless another is more than 3 % faster
     std::vector<std::pair<float, int>> timing;
-    for (int code : cands) {
-        for (int w = 0; w < 2; ++w) launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, st);
+    cg_status rc = CG_OK;
+    for (auto &cand : cands) {
+        const int code = cand.first;
+        cudaStream_t cs = m->capture_stream;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int q = 0; q < cand.second; ++q) {
+                if (code >= kPairCode)
+                    launch_cheb2<TS>(code - kPairCode, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc,
+                                     yd, cs);
+                else
+                    launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, cs);
+            }
+            ce = cudaStreamEndCapture(cs, &graph);
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
         float best_burst = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 4 && ce == cudaSuccess; ++rep) {
             cudaEventRecord(e0, st);
-            for (int q = 0; q < 10; ++q)
-                launch_cheb<TS>(code, g, nf, cf, 0.5f, 1.0f, ya, yb, r, yb, st);
+            ce = cudaGraphLaunch(exec, st);
             cudaEventRecord(e1, st);
-            CGK_CUDA(cudaEventSynchronize(e1));
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            best_burst = std::min(best_burst, ms);
+            if (rep > 0) best_burst = std::min(best_burst, ms);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "sweep autotuner", __FILE__, __LINE__);
+            break;
         }
         timing.push_back({best_burst, code});
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CG_OK) return rc;
     std::sort(timing.begin(), timing.end());
     int best_code = timing[0].second;
-    float best_time = timing[0].first;
     if (v4) {
         float best_v4 = 1e30f;
         int code_v4 = 0;
         for (auto &tc : timing)
-            if (tc.second >= 100 && tc.first < best_v4) {
+            if (tc.second >= 100 && tc.second < kPairCode && tc.first < best_v4) {
                 best_v4 = tc.first;
                 code_v4 = tc.second;
             }
-        if (code_v4 && best_v4 <= 1.03f * timing[0].first) {
-            best_code = code_v4;
-            best_time = best_v4;
-        }
+        if (code_v4 && best_v4 <= 1.03f * timing[0].first) best_code = code_v4;
     }
-    // two iterations per launch: bursts of 5 launches (10 iterations)
-    if (cheb2_fits(g)) {
-        for (int z : {1, 2, 4, 8, 16}) {
-            for (int w = 0; w < 2; ++w)
-                launch_cheb2<TS>(z, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc, yd, st);
-            float best_burst = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, st);
-                for (int q = 0; q < 5; ++q)
-                    launch_cheb2<TS>(z, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc, yd, st);
-                cudaEventRecord(e1, st);
-                CGK_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                best_burst = std::min(best_burst, ms);
-            }
-            if (best_burst < best_time) {
-                best_time = best_burst;
-                best_code = kPairCode + z;
-            }
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    CGK_CUDA(cudaGetLastError());
     m->tuned.push_back({key, best_code});
     *code_out = best_code;
     return CG_OK;

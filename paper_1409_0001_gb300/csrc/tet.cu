@@ -71,8 +71,10 @@ __device__ __forceinline__ double orient3(const double *p0, const double *p1, co
 // the bucket of x, which holds every tet whose box overlaps it, in ascending order.
 __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevice t, int nf,
                              const double *__restrict__ w, int32_t *__restrict__ cell,
-                             uint32_t *__restrict__ counts, unsigned long long *__restrict__ bad) {
+                             uint32_t *__restrict__ counts, uint32_t *__restrict__ ranks,
+                             unsigned long long *__restrict__ bad) {
     unsigned long long n_out = 0, n_nonfinite = 0;
+    uint32_t most = 0;   // largest per-cell count seen (counts != nullptr)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         for (int f = 0; f < nf; ++f)
@@ -121,18 +123,23 @@ __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevic
             if (found < 0 && best >= 0 && best_m >= -1e-10) found = best;
         }
         cell[i] = found;
-        if (found < 0)
+        if (found < 0) {
             ++n_out;
-        else if (counts)
-            atomicAdd(&counts[found], 1u);
+        } else if (counts) {
+            const uint32_t r = atomicAdd(&counts[found], 1u);
+            if (ranks) ranks[i] = r;
+            most = max(most, r + 1u);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         n_out += __shfl_down_sync(0xffffffffu, n_out, o);
         n_nonfinite += __shfl_down_sync(0xffffffffu, n_nonfinite, o);
+        most = max(most, __shfl_down_sync(0xffffffffu, most, o));
     }
     if ((threadIdx.x & 31) == 0) {
         if (n_out) atomicAdd(&bad[0], n_out);
         if (n_nonfinite) atomicAdd(&bad[1], n_nonfinite);
+        if (most) atomicMax(&bad[2], (unsigned long long)most);
     }
 }
 
@@ -670,11 +677,11 @@ cg_status tet_build(cg_mesh *m, int64_t nv, const double *xyz, int64_t nt, const
 }
 
 cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
-                            int32_t *cell_out, uint32_t *counts, unsigned long long *bad,
-                            cudaStream_t st) {
+                            int32_t *cell_out, uint32_t *counts, uint32_t *ranks,
+                            unsigned long long *bad, cudaStream_t st) {
     CGK_LAUNCH("tet_locate", (double)n * (24 + 8 * nf + 4), st,
                k_tet_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
-                                                            counts, bad));
+                                                            counts, ranks, bad));
     CGK_CUDA(cudaGetLastError());
     return CG_OK;
 }
