@@ -1157,6 +1157,8 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
     const int nyb = (y > 0) + (y + 1 < g.ny);
     const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx);
     const int n12 = nyb + 2;
+    // diagonals of the four cells on planes with both z neighbours (most planes)
+    const float d0i = sdg[n0 + 2], d12i = sdg[n12 + 2], d3i = sdg[n3 + 2];
     const int kxy = y * g.nx + x;
     float4 vdn = f4zero(), vc = f4zero(), vup = f4zero(), ypc = f4zero(), rc = f4zero();
     float4 hlo = f4zero(), hhi = f4zero();
@@ -1203,17 +1205,23 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
         __syncthreads();
         if (own) {
             const float4 up = pl[ty][tx], dn = pl[ty + 2][tx];
-            const int nz_ = (z > 0) + (z + 1 < g.nz);
+            float d0 = d0i, d12 = d12i, d3 = d3i;
+            if (z == 0 || z + 1 == g.nz) {   // a z wall: fewer neighbours
+                const int nz_ = (z > 0) + (z + 1 < g.nz);
+                d0 = sdg[n0 + nz_];
+                d12 = sdg[n12 + nz_];
+                d3 = sdg[n3 + nz_];
+            }
             float4 s;
             s.x = left + vc.y + up.x + dn.x + vdn.x + vup.x;
             s.y = vc.x + vc.z + up.y + dn.y + vdn.y + vup.y;
             s.z = vc.y + vc.w + up.z + dn.z + vdn.z + vup.z;
             s.w = vc.z + right + up.w + dn.w + vdn.w + vup.w;
             float4 o;
-            o.x = fmaf(omega, vc.x - ypc.x + gamma * (rc.x - fmaf(sdg[n0 + nz_], vc.x, -cf.ce * s.x)), ypc.x);
-            o.y = fmaf(omega, vc.y - ypc.y + gamma * (rc.y - fmaf(sdg[n12 + nz_], vc.y, -cf.ce * s.y)), ypc.y);
-            o.z = fmaf(omega, vc.z - ypc.z + gamma * (rc.z - fmaf(sdg[n12 + nz_], vc.z, -cf.ce * s.z)), ypc.z);
-            o.w = fmaf(omega, vc.w - ypc.w + gamma * (rc.w - fmaf(sdg[n3 + nz_], vc.w, -cf.ce * s.w)), ypc.w);
+            o.x = fmaf(omega, vc.x - ypc.x + gamma * (rc.x - fmaf(d0, vc.x, -cf.ce * s.x)), ypc.x);
+            o.y = fmaf(omega, vc.y - ypc.y + gamma * (rc.y - fmaf(d12, vc.y, -cf.ce * s.y)), ypc.y);
+            o.z = fmaf(omega, vc.z - ypc.z + gamma * (rc.z - fmaf(d12, vc.z, -cf.ce * s.z)), ypc.z);
+            o.w = fmaf(omega, vc.w - ypc.w + gamma * (rc.w - fmaf(d3, vc.w, -cf.ce * s.w)), ypc.w);
             V::store(ynv, kz, o);
         }
         __syncthreads();
@@ -1237,8 +1245,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nz
                                                       const TS *__restrict__ r_all, TS *ynext_all) {
     chain_wait();
     chain_release();
-    const int f = blockIdx.z / nzc;
-    const int z0 = (blockIdx.z - f * nzc) * zlen;
+    const int f = nzc == (int)gridDim.z ? 0 : (int)blockIdx.z / nzc;   // one field: no division
+    const int z0 = ((int)blockIdx.z - f * nzc) * zlen;
     const int z1 = min(g.nz, z0 + zlen);
     const size_t off = (size_t)f * g.n;
     __shared__ float sdg[8];
@@ -2234,10 +2242,11 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
 }
 
 // Autotuner of the Chebyshev sweep's shape (vectorised, register-blocked with 2, 4 or 8
-// planes per block, z-marching with 1..16 planes per block, or two iterations per launch
-// with 1..16 planes per block where rows fit a warp): times a few launches of each
-// candidate on the caller's buffers (all scratch at this point) and keeps the fastest
-// per iteration.  The choice is cached per mesh, field count and storage type.
+// planes per block, z-marching with 1..16 planes per block): times ten iterations of
+// each candidate on the caller's buffers (all scratch at this point) and keeps the
+// fastest.  The choice is cached per mesh, field count and storage type.  (The
+// two-iterations-per-launch sweep is not a candidate: inside the solver's graph it
+// measured no faster per iteration than the one-iteration sweep; sweep_shape selects it.)
 template <class TS>
 cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, TS *yb, TS *yc,
                     TS *yd, const TS *r, cudaStream_t st, int *code_out) {
@@ -2254,8 +2263,6 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     const bool v4 = g.nx % 4 == 0;   // vectorised shapes need whole 4-cell vectors per row
     for (int c : {101, 102, 104, 108, 116, 2, 4, 8, -1, -4, -16})
         if (c < 100 || v4) cands.push_back({c, 10});
-    if (cheb2_fits(g))
-        for (int z : {1, 2, 4, 8, 16}) cands.push_back({kPairCode + z, 5});
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
@@ -2650,7 +2657,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                                if (cap_err == cudaSuccess) cap_err = le;
                                            });
                                 yc = yf;
-                            } else if (m_it > 1 && cheb_code >= kPairCode) {
+                            } else if (m_it > 1 && cheb_code >= kPairCode && cheb_code < kResidentCode) {
                                 const int np = (m_it - 1) / 2, ns = (m_it - 1) % 2;
                                 CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb2_bf16" : "cheb2_fp32",
                                           (double)n * nf * sizeof(TS) *
