@@ -433,3 +433,37 @@ def test_image_kernel_is_normalised_over_the_box(orc):
     vals = orc.kernel_sum(src, np.array([2.0]), ev, L, b, mmax=2)
     integral = vals.sum() * (L[0] * L[1] * L[2]) / n ** 3
     assert abs(integral - 2.0) <= 1e-6
+
+
+def test_golden_close_packed_layer_solid_fraction(orc):
+    """The paper's 0.606 (Section 4.3, tests/golden/close_packed_layer.json): a triangular
+    close-packed layer of spheres (diameter d, spacing d, one diameter thick) deposited by
+    the particle centroid method onto cells of side d carries a mean solid fraction over the
+    layer equal to pi/(3 sqrt 3) = 0.6046 -- a check of V_p, V_c and the per-cell division.
+    Single cells see 1 or 2 centroids (0.52 or 1.05: PCM exceeds the packing limit, as the
+    paper remarks); the smoothed field keeps the layer's mean."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "close_packed_layer.json")) as f:
+        gold = json.load(f)
+    d = 1.0 / 64
+    cols, rows = 64, 74
+    i, j = np.meshgrid(np.arange(cols), np.arange(rows))
+    pos = np.vstack([(i * d + 0.25 * d + (j % 2) * 0.5 * d).ravel(),
+                     ((j + 0.5) * np.sqrt(3) / 2 * d).ravel(),
+                     np.full(cols * rows, d / 2)])
+    vp = np.pi * d ** 3 / 6
+    w = np.full((1, cols * rows), vp)
+    dims = (64, 65, 1)
+    cell, nout = orc.locate_structured(dims, (0, 0, 0), d, pos)
+    assert nout == 0
+    eps, _ = orc.deposit(cell, w, int(np.prod(dims)), vc_uniform=d * d * d)
+    layer_volume = (cols * d) * (rows * np.sqrt(3) / 2 * d) * d
+    mean = eps.sum() * d ** 3 / layer_volume
+    assert abs(mean - np.pi / (3 * np.sqrt(3))) <= 1e-12
+    assert abs(mean - gold["value"]) <= gold["tolerance_abs"]
+    assert eps.max() > gold["value"]                     # PCM overshoots the packing limit
+    u, _ = orc.diffuse_structured(eps, dims, d, (3 * d) ** 2 / 4, 10)
+    assert abs(u.sum() * d ** 3 / layer_volume - mean) <= 1e-12
+    inner = u.reshape(65, 64)[10:54, 10:54]
+    assert abs(inner.mean() - mean) <= 2e-3
