@@ -64,11 +64,104 @@ __device__ __forceinline__ double orient3(const double *p0, const double *p1, co
     return __dadd_rn(__dsub_rn(__dmul_rn(a0, m0), __dmul_rn(a1, m1)), __dmul_rn(a2, m2));
 }
 
+// A double as a 64-bit key in the order of the doubles (-0 as +0; a NaN sorts above +inf
+// or below -inf by its sign, so it fails one side of a range test).
+__device__ __forceinline__ unsigned long long tkey(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (b == 0x8000000000000000ull) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// The FP64 barycentric coordinates of x in tet tt by the defining expressions.
+__device__ __noinline__ void tet_lambdas(const TetDevice &t, int32_t tt, const double *x, double *lam) {
+    const double *v0 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 0];
+    const double *v1 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 1];
+    const double *v2 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 2];
+    const double *v3 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 3];
+    const double D = orient3(v0, v1, v2, v3);
+    lam[0] = __ddiv_rn(orient3(x, v1, v2, v3), D);
+    lam[1] = __ddiv_rn(orient3(v0, x, v2, v3), D);
+    lam[2] = __ddiv_rn(orient3(v0, v1, x, v3), D);
+    lam[3] = __ddiv_rn(orient3(v0, v1, v2, x), D);
+}
+
+// det[a; b; c] in FP32 and a bound on its distance from the exact determinant of the
+// vectors a, b, c stand for (each component within 2^-24 (1 + 2^-28) relative of the
+// exact value): input error 3.0001 u + evaluation error 6 u (u = 2^-24) times the
+// permanent of |a|, |b|, |c|, with a factor of more than 1.5 to spare.
+__device__ __forceinline__ float det3f(const float *a, const float *b, const float *c, float *bound) {
+    const float d = a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                    a[2] * (b[0] * c[1] - b[1] * c[0]);
+    const float p = fabsf(a[0]) * (fabsf(b[1] * c[2]) + fabsf(b[2] * c[1])) +
+                    fabsf(a[1]) * (fabsf(b[0] * c[2]) + fabsf(b[2] * c[0])) +
+                    fabsf(a[2]) * (fabsf(b[0] * c[1]) + fabsf(b[1] * c[0]));
+    *bound = p * 0x1p-20f;
+    return d;
+}
+
+// Whether x is in tet tt by the FP64 definition (all four lambda >= 0), decided from
+// FP32 determinants when their signs are certain: 1 inside, 0 outside, -1 undecided.
+// With e_i = v_i - v0 and q = x - v0 (FP64 differences, then FP32), the coordinates'
+// numerators are det(q,e2,e3), det(e1,q,e3), det(e1,e2,q) and D minus those three (the
+// four sum to D exactly); the FP64 definition evaluates the same determinants with errors
+// below 2^-50 of their permanents, far inside the bounds used here.
+__device__ __forceinline__ int tet_inside_f(const TetDevice &t, int32_t tt, const double *x) {
+    const double *v0 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 0];
+    const double *v1 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 1];
+    const double *v2 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 2];
+    const double *v3 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 3];
+    float e1[3], e2[3], e3[3], q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = __double2float_rn(__dsub_rn(v1[k], v0[k]));
+        e2[k] = __double2float_rn(__dsub_rn(v2[k], v0[k]));
+        e3[k] = __double2float_rn(__dsub_rn(v3[k], v0[k]));
+        q[k] = __double2float_rn(__dsub_rn(x[k], v0[k]));
+    }
+    float bD, b1, b2, b3;
+    const float D = det3f(e1, e2, e3, &bD);
+    const float o1 = det3f(q, e2, e3, &b1);
+    const float o2 = det3f(e1, q, e3, &b2);
+    const float o3 = det3f(e1, e2, q, &b3);
+    const float o0 = ((D - o1) - o2) - o3;
+    // o0's bound: the four bounds, the three subtractions' rounding (3 u of the terms),
+    // and the FP64 definition's error on det(v1-x, v2-x, v3-x) (below 6 2^-50 of the
+    // product of the vectors' max-norms, each at most |e_i| + |q|)
+    float n1 = 0.f, n2 = 0.f, n3 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        n1 = fmaxf(n1, fabsf(e1[k]) + fabsf(q[k]));
+        n2 = fmaxf(n2, fabsf(e2[k]) + fabsf(q[k]));
+        n3 = fmaxf(n3, fabsf(e3[k]) + fabsf(q[k]));
+    }
+    const float b0 = 1.001f * (bD + b1 + b2 + b3) +
+                     (fabsf(D) + fabsf(o1) + fabsf(o2) + fabsf(o3)) * 0x1p-22f +
+                     n1 * n2 * n3 * 0x1p-44f;
+    if (!(fabsf(D) > bD)) return -1;   // a flat tet: leave it to FP64
+    const bool pos = D > 0.f;
+    const float o[4] = {o0, o1, o2, o3}, bb[4] = {b0, b1, b2, b3};
+    bool undecided = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (o[j] > bb[j]) {
+            if (!pos) return 0;
+        } else if (o[j] < -bb[j]) {
+            if (pos) return 0;
+        } else {
+            undecided = true;
+        }
+    }
+    return undecided ? -1 : 1;
+}
+
 // Host tet of each particle: the lowest-index tet whose axis-aligned box holds x and
 // whose four barycentric coordinates lambda_j = orient(tet with v_j -> x) / orient(tet)
 // are all >= 0; else the tet (box holding x) with the largest min_j lambda_j, lowest
 // index on ties, if that value is >= -1e-10; else outside (-1).  Candidates come from
-// the bucket of x, which holds every tet whose box overlaps it, in ascending order.
+// the bucket of x, which holds every tet whose box overlaps it, in ascending order.  The
+// box tests compare doubles exactly as integer keys; a candidate is settled from FP32
+// determinants when their signs are certain and from the FP64 coordinates otherwise,
+// and the largest-minimum search (no tet holds x) runs on FP64 coordinates only.
 __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevice t, int nf,
                              const double *__restrict__ w, int32_t *__restrict__ cell,
                              uint32_t *__restrict__ counts, uint32_t *__restrict__ ranks,
@@ -78,10 +171,12 @@ __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevic
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         for (int f = 0; f < nf; ++f)
-            if (!isfinite(w[(int64_t)f * n + i])) ++n_nonfinite;
+            if (((__double2hiint(w[(int64_t)f * n + i]) >> 20) & 0x7ff) == 0x7ff) ++n_nonfinite;
         double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
         int32_t found = -1;
-        bool ok = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ok = ok && (((__double2hiint(x[a]) >> 20) & 0x7ff) != 0x7ff);
         if (ok) {
             int bi[3];
             for (int a = 0; a < 3; ++a) {
@@ -89,38 +184,47 @@ __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevic
                 int v = q < 0.0 ? 0 : (q > (double)(t.nb[a] - 1) ? t.nb[a] - 1 : (int)q);
                 bi[a] = v;
             }
-            int b = (bi[2] * t.nb[1] + bi[1]) * t.nb[0] + bi[0];
-            int32_t best = -1;
-            double best_m = -INFINITY;
-            for (int c = t.bucket_start[b]; c < t.bucket_start[b + 1]; ++c) {
-                int32_t tt = t.bucket_tets[c];
+            const int b = (bi[2] * t.nb[1] + bi[1]) * t.nb[0] + bi[0];
+            const unsigned long long kx0 = tkey(x[0]), kx1 = tkey(x[1]), kx2 = tkey(x[2]);
+            const int c0 = t.bucket_start[b], c1 = t.bucket_start[b + 1];
+            bool any_box = false;
+            for (int c = c0; c < c1 && found < 0; ++c) {
+                const int32_t tt = t.bucket_tets[c];
                 const double *bx = t.box + 6 * (size_t)tt;
-                if (!(x[0] >= bx[0] && x[0] <= bx[3] && x[1] >= bx[1] && x[1] <= bx[4] &&
-                      x[2] >= bx[2] && x[2] <= bx[5]))
+                if (!(kx0 >= tkey(bx[0]) && kx0 <= tkey(bx[3]) && kx1 >= tkey(bx[1]) &&
+                      kx1 <= tkey(bx[4]) && kx2 >= tkey(bx[2]) && kx2 <= tkey(bx[5])))
                     continue;
-                const double *v0 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 0];
-                const double *v1 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 1];
-                const double *v2 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 2];
-                const double *v3 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 3];
-                double D = orient3(v0, v1, v2, v3);
-                double l0 = __ddiv_rn(orient3(x, v1, v2, v3), D);
-                double l1 = __ddiv_rn(orient3(v0, x, v2, v3), D);
-                double l2 = __ddiv_rn(orient3(v0, v1, x, v3), D);
-                double l3 = __ddiv_rn(orient3(v0, v1, v2, x), D);
-                double m = l0;
-                if (l1 < m) m = l1;
-                if (l2 < m) m = l2;
-                if (l3 < m) m = l3;
-                if (m >= 0.0) {
-                    found = tt;
-                    break;
+                any_box = true;
+                int in = tet_inside_f(t, tt, x);
+                if (in < 0) {
+                    double lam[4];
+                    tet_lambdas(t, tt, x, lam);
+                    in = (lam[0] >= 0.0 && lam[1] >= 0.0 && lam[2] >= 0.0 && lam[3] >= 0.0) ? 1 : 0;
                 }
-                if (m > best_m) {
-                    best_m = m;
-                    best = tt;
-                }
+                if (in) found = tt;
             }
-            if (found < 0 && best >= 0 && best_m >= -1e-10) found = best;
+            if (found < 0 && any_box) {   // no tet holds x: the largest minimum coordinate
+                int32_t best = -1;
+                double best_m = -INFINITY;
+                for (int c = c0; c < c1; ++c) {
+                    const int32_t tt = t.bucket_tets[c];
+                    const double *bx = t.box + 6 * (size_t)tt;
+                    if (!(kx0 >= tkey(bx[0]) && kx0 <= tkey(bx[3]) && kx1 >= tkey(bx[1]) &&
+                          kx1 <= tkey(bx[4]) && kx2 >= tkey(bx[2]) && kx2 <= tkey(bx[5])))
+                        continue;
+                    double lam[4];
+                    tet_lambdas(t, tt, x, lam);
+                    double m = lam[0];
+                    if (lam[1] < m) m = lam[1];
+                    if (lam[2] < m) m = lam[2];
+                    if (lam[3] < m) m = lam[3];
+                    if (m > best_m) {
+                        best_m = m;
+                        best = tt;
+                    }
+                }
+                if (best >= 0 && best_m >= -1e-10) found = best;
+            }
         }
         cell[i] = found;
         if (found < 0) {
