@@ -266,7 +266,19 @@ struct Op {          // the operator seen by the kernels
     const int32_t *offc;
     double dte;      // theta * dtau (the coefficient of L in A = M - dte L)
     double dtau;     // full dtau (for the residual of the first pass)
+    const float *adiag32 = nullptr;    // FP32 diagonal of A, V_c - dte L_kk (inner solves)
+    const float *iadiag32 = nullptr;   // its reciprocal (the Jacobi preconditioner)
 };
+
+// The FP32 diagonal of A = M - dte L and its reciprocal, for the inner solves.
+__global__ void k_tdiag32(int n, const double *__restrict__ vc, const double *__restrict__ diagL,
+                          double dte, float *__restrict__ ad, float *__restrict__ iad) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double a = vc[k] - dte * diagL[k];
+        ad[k] = (float)a;
+        iad[k] = (float)(1.0 / a);
+    }
+}
 
 // (L u)_k with u given by load(l)
 template <class T, class Load>
@@ -457,7 +469,7 @@ __global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
             xout_all[off + k] = xk;
         }
         float rf = (float)rk;
-        float zf = rf / (float)(o.vc[k] - o.dte * o.diagL[k]);
+        float zf = rf * o.iadiag32[k];
         stf(rin_all, off + k, rf);
         stf(z_all, off + k, zf);
         stf(p_all, off + k, zf);
@@ -497,22 +509,22 @@ __global__ void k_tin_pass1(Op o, const TS *__restrict__ z_all, const TS *__rest
     const size_t off = (size_t)f * o.n;
     const TS *z = z_all + off;
     const TS *pin = pin_all + off;
-    double pq = 0;
+    float pq = 0.f;   // a thread's partial sum stays short: FP32, then FP64 across threads
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
         float pk = ldf(z, k) + beta * ldf(pin, k);
-        float lp = (float)o.diagL[k] * pk;
+        float off_sum = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const size_t e = (size_t)q * o.n + k;
             const int l = o.offc[e];
-            lp += o.offv32[e] * (ldf(z, l) + beta * ldf(pin, l));
+            off_sum += o.offv32[e] * (ldf(z, l) + beta * ldf(pin, l));
         }
-        float qk = (float)o.vc[k] * pk - dte * lp;
+        float qk = o.adiag32[k] * pk - dte * off_sum;
         stf(pout_all, off + k, pk);
         stf(q_all, off + k, qk);
-        pq += (double)(pk * qk);
+        pq = fmaf(pk, qk, pq);
     }
-    double v = block_sum(pq);
+    double v = block_sum((double)pq);
     double *partials = partials_all + (size_t)f * 3 * gridDim.x;
     if (arrive(partials, 1, &v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
         double PQ = finish_sum(partials, 0, gridDim.x);
@@ -541,19 +553,19 @@ __global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__rest
     if (sc[f].done) return;
     const float alpha = (float)sc[f].alpha;
     const size_t off = (size_t)f * o.n;
-    double rr = 0, rz = 0;
+    float rr = 0.f, rz = 0.f;   // per-thread partial sums in FP32, FP64 across threads
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
         size_t i = off + k;
         float pk = ldf(p_all, i);
         stf(d_all, i, ldf(d_all, i) + alpha * pk);
         float rk = ldf(rin_all, i) - alpha * ldf(q_all, i);
-        float zk = rk / (float)(o.vc[k] - o.dte * o.diagL[k]);
+        float zk = rk * o.iadiag32[k];
         stf(rin_all, i, rk);
         stf(z_all, i, zk);
-        rr += (double)(rk * rk);
-        rz += (double)(rk * zk);
+        rr = fmaf(rk, rk, rr);
+        rz = fmaf(rk, zk, rz);
     }
-    double v[2] = {block_sum(rr), block_sum(rz)};
+    double v[2] = {block_sum((double)rr), block_sum((double)rz)};
     double *partials = partials_all + (size_t)f * 3 * gridDim.x;
     if (arrive(partials, 2, v, blockIdx.x, gridDim.x, &sc[f].ticket)) {
         double RR = finish_sum(partials, 0, gridDim.x);
@@ -907,14 +919,23 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     const int n = (int)m->ncells;
     const bool cn = p->scheme == CG_SCHEME_CRANK_NICOLSON;
     const double dtau = T / p->nsteps;
-    const Op o = make_op(m, cn ? 0.5 * dtau : dtau, dtau);
+    Op o = make_op(m, cn ? 0.5 * dtau : dtau, dtau);
     const double tol2 = p->tol * p->tol;
     const double eps_in = sizeof(TS) == 2 ? 3e-3 : 1e-6;
     const int G = grid1d(n);
     const dim3 grid(G, nf);
     const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
-    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts));
+    const size_t v32 = align_up((size_t)n * 4);
+    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts + 2 * v32));
     char *wb = m->ws_diffuse.as<char>();
+    {   // FP32 diagonal of A and its reciprocal for this call's dtau
+        float *ad = (float *)(wb + 3 * v64 + 7 * vts), *iad = (float *)(wb + 3 * v64 + 7 * vts + v32);
+        CGK_LAUNCH("tdiag32", (double)n * 24, st,
+                   k_tdiag32<<<G, kThreads, 0, st>>>(n, o.vc, o.diagL, o.dte, ad, iad));
+        CGK_CUDA(cudaGetLastError());
+        o.adiag32 = ad;
+        o.iadiag32 = iad;
+    }
     double *X1 = (double *)wb, *X2 = (double *)(wb + v64), *B = (double *)(wb + 2 * v64);
     TS *Rin = (TS *)(wb + 3 * v64), *Z = (TS *)(wb + 3 * v64 + vts), *Q = (TS *)(wb + 3 * v64 + 2 * vts);
     TS *Pp[2] = {(TS *)(wb + 3 * v64 + 3 * vts), (TS *)(wb + 3 * v64 + 4 * vts)};
