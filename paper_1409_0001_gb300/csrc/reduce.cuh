@@ -25,6 +25,24 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;
 }
 
+// The same block reduction in FP32, for the residual norms of the mixed-precision
+// passes (their values are FP32 already and the convergence test needs them to far less
+// than FP32 accuracy; GB300 runs FP64 arithmetic at a small fraction of its FP32 rate,
+// so even a block reduction in FP64 shows in these short passes).  The result is
+// promoted to FP64 for the grid-wide sum.
+__device__ __forceinline__ double block_sum_f(float v) {
+    __shared__ float wsf[kThreads / 32];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) wsf[t >> 5] = v;
+    __syncthreads();
+    float r = 0.0f;
+    if (t == 0)
+        for (int w = 0; w < kThreads / 32; ++w) r += wsf[w];
+    __syncthreads();
+    return (double)r;
+}
+
 // Stores this block's partial(s) at partials[q * nb + bid]; true in the last block.
 __device__ __forceinline__ bool arrive(double *partials, int nparts, const double *vals, int bid,
                                        int nb, unsigned int *ticket) {

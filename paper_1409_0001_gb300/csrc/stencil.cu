@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
                 }
             });
     }
-    double vals[2] = {block_sum((double)rr), kMode != 1 ? block_sum((double)bb) : 0.0};
+    double vals[2] = {block_sum_f(rr), kMode != 1 ? block_sum_f(bb) : 0.0};
     double *partials = partials_all + (size_t)bp.f * 2 * bp.nb;
     if (arrive(partials, kMode != 1 ? 2 : 1, vals, bp.bid, bp.nb, &sc[bp.f].ticket)) {
         double RR = finish_sum(partials, 0, bp.nb);
@@ -937,7 +937,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         hl = nl;
         hr = nr;
     }
-    double vals[2] = {block_sum((double)rr), kMode != 1 ? block_sum((double)bb) : 0.0};
+    double vals[2] = {block_sum_f(rr), kMode != 1 ? block_sum_f(bb) : 0.0};
     double *partials = partials_all + (size_t)f * 2 * nb;
     if (arrive(partials, kMode != 1 ? 2 : 1, vals, bid, nb, &sc[f].ticket)) {
         double RR = finish_sum(partials, 0, nb);
@@ -1732,7 +1732,7 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
                 acc = fmaf(rf, rf, acc);
             });
     }
-    double tot = block_sum((double)acc);
+    double tot = block_sum_f(acc);
     if (is_thread0() && part) *part = tot;
 }
 
