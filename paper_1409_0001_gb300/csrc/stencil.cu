@@ -1136,7 +1136,9 @@ template <> struct Vec4cg<__nv_bfloat16> {
 // One tile (128 x-cells x TY rows x planes [z0, z1)) of the vectorised Chebyshev
 // iteration; L is the load policy (Vec4 or Vec4cg), sdg the diagonal table in shared
 // memory.  Every thread of the block must call it (barriers and shuffles inside).
-template <class TS, template <class> class L>
+// ZFIX > 0: the caller guarantees at most ZFIX planes per block, so the march is
+// unrolled (the register queue rotates without copies).
+template <class TS, template <class> class L, int ZFIX = 0>
 __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z0, int z1,
                                              const Coef32 &cf, const float *sdg, float gamma,
                                              float omega, const TS *yv, const TS *ypv,
@@ -1177,7 +1179,10 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
         if (xl) hl = ldcg(yv, (int)(k0 - 1));
         if (xr) hr = ldcg(yv, (int)(k0 + 4));
     }
-    for (int z = z0; z < z1; ++z) {
+#pragma unroll
+    for (int zi = 0; zi < (ZFIX > 0 ? ZFIX : z1 - z0); ++zi) {
+        const int z = z0 + zi;
+        if (ZFIX > 0 && z >= z1) break;
         const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
         // loads for the next plane
         float4 nup = f4zero(), nyp = f4zero(), nr = f4zero(), nlo = f4zero(), nhi = f4zero();
@@ -1237,7 +1242,7 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
     }
 }
 
-template <class TS>
+template <class TS, int ZFIX = 0>
 __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nzc, Coef32 cf,
                                                       float gamma, float omega,
                                                       const TS *__restrict__ y_all,
@@ -1252,7 +1257,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nz
     __shared__ float sdg[8];
     stage_table(sdg, cf.dg);
     __syncthreads();
-    cheb_v4_tile<TS, Vec4>(g, blockIdx.x, blockIdx.y, z0, z1, cf, sdg, gamma, omega, y_all + off,
+    cheb_v4_tile<TS, Vec4, ZFIX>(g, blockIdx.x, blockIdx.y, z0, z1, cf, sdg, gamma, omega, y_all + off,
                            yprev_all ? yprev_all + off : nullptr, r_all + off, ynext_all + off);
 }
 
@@ -1971,7 +1976,12 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
         const int zlen = code - 100;
         const int nzc = (g.nz + zlen - 1) / zlen;
         const dim3 grid((g.nx + 4 * TX - 1) / (4 * TX), gy, nzc * nf);
-        launch_chain(k_cheb_v4<TS>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
+        if (zlen == 1)
+            launch_chain(k_cheb_v4<TS, 1>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
+        else if (zlen == 2)
+            launch_chain(k_cheb_v4<TS, 2>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
+        else
+            launch_chain(k_cheb_v4<TS>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
     } else if (code > 0) {
         const int nzb = (g.nz + code - 1) / code;
         const dim3 grid(gx, gy, nzb * nf);
