@@ -526,6 +526,19 @@ def extras():
         ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
             bandwidth=ch.b, nsteps=ch.nsteps, precision=prec), report=True), reps=reps)
         out[name] = (ms, u.clone(), rep)
+    # the explicit reading of the same case: 40 explicit Euler steps (dtau/dx^2 = 0.1)
+    ex = {}
+    for name, prec in (("explicit_df", cg.PREC_FP32_DF_REFINE), ("explicit_fp64", cg.PREC_FP64)):
+        ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
+            bandwidth=ch.b, nsteps=ch.nsteps, scheme=2, precision=prec), report=True))
+        ex[name] = (ms, u.clone(), rep)
+    res["channel_512x256x256_explicit"] = {
+        "workload": "the channel case with 40 explicit Euler steps (dtau/dx^2 = 0.1)",
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3)}
+                  for k, v in ex.items()},
+        "df_vs_fp64_maxrel": maxrel(ex["explicit_df"][1], ex["explicit_fp64"][1]),
+        "explicit_vs_implicit_fp64_maxrel": maxrel(ex["explicit_fp64"][1], out["fp64_cg"][1])}
+    del ex
     res["channel_512x256x256"] = {
         "workload": "512x256x256 over 4x2x2, 50,000,000 spheres d=0.004, density 1+0.5 sin(2 pi x), "
                     "b=4dx, 40 IE steps",

@@ -185,7 +185,9 @@ cg_status cg_deposit(cg_mesh *mesh, int64_t n, const double *pos, int nfields, c
  * params->nsteps steps of the chosen scheme of Eq. (diffusion) to T, zero-flux walls.
  * Implicit Euler solves (M - dtau L) u^{n+1} = M u^n per step, Crank-Nicolson
  * (M - dtau/2 L) u^{n+1} = (M + dtau/2 L) u^n, explicit Euler u += dtau M^{-1} L u
- * (requires dtau <= dx^2/6 on hex meshes).  cells: device [nfields][ncells] FP64.
+ * (requires dtau <= dx^2/6 on hex meshes; with precision 3 or 4 on a hex mesh of even
+ * nx its steps run in double-float arithmetic, else in FP64).  cells: device
+ * [nfields][ncells] FP64.
  * Errors: CG_EINVAL, CG_ENOCONV (report->final_rel_residual says how far it got),
  * CG_ENOMEM, CG_ECUDA. */
 cg_status cg_diffuse(cg_mesh *mesh, int nfields, double *cells, const cg_params *params,

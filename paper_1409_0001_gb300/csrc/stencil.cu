@@ -749,8 +749,9 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
 // The refinement pass of k_refine_df with two x-cells per thread (nx even): a float4
 // holds the two cells' double-float values, a warp row covers 64 cells; x neighbours
 // by shuffle (and two scalar loads at the tile edges), y neighbours from a shared plane,
-// z neighbours from a register queue with one-plane-ahead prefetch.  Same modes,
-// arguments and results as k_refine_df.
+// z neighbours from a register queue with one-plane-ahead prefetch.  Modes 0-2 as in
+// k_refine_df; mode 3 is one explicit Euler step in double-float arithmetic,
+// xout = xin + c L xin (cf.c = dtau / dx^2), with no reduction.
 template <class TS> struct Pair;
 template <> struct Pair<float> {
     static __device__ __forceinline__ float2 load(const float *p, size_t i) {
@@ -794,8 +795,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     const int nb = gridDim.x * gridDim.y * nzc;
     const size_t off = (size_t)f * g.n;
     const float4 *X = reinterpret_cast<const float4 *>(xin_all + off);   // cell pairs
-    const TS *D = kMode == 0 ? nullptr : d_all + off;
-    const float4 *Bv = reinterpret_cast<const float4 *>((kMode == 0 ? xin_all : b_all) + off);
+    constexpr bool kPlain = kMode == 0 || kMode == 3;   // the stencil of x itself (no d)
+    const TS *D = kPlain ? nullptr : d_all + off;
+    const float4 *Bv = reinterpret_cast<const float4 *>((kPlain ? xin_all : b_all) + off);
     float4 *XO = reinterpret_cast<float4 *>(xout_all + off);
     float4 *BO = reinterpret_cast<float4 *>(bout_all ? bout_all + off : nullptr);
     TS *r = r_all + off;
@@ -818,13 +820,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     // stencil value of a cell pair / of one cell
     auto val2 = [&](size_t k) -> float4 {
         float4 xv = X[k >> 1];
-        if (kMode == 0) return xv;
+        if (kPlain) return xv;
         float2 dv = PR::load(D, k);
         return pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
     };
     auto val1 = [&](size_t k) -> DF {
         DF xv = xin_all[off + k];
-        if (kMode == 0) return xv;
+        if (kPlain) return xv;
         return df_add_f(xv, ld(D, (int)k));
     };
     float4 vdn = f4z(), vc = f4z(), vup = f4z(), bc = f4z(), hlo = f4z(), hhi = f4z();
@@ -836,7 +838,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
             if (z0 > 0) vdn = val2(k0 - g.nxy);
             vc = val2(k0);
             if (z0 + 1 < g.nz) vup = val2(k0 + g.nxy);
-            if (kMode != 0) bc = Bv[k0 >> 1];
+            if (!kPlain) bc = Bv[k0 >> 1];
         }
         if (rowlo) hlo = val2(k0 - g.nx);
         if (rowhi) hhi = val2(k0 + g.nx);
@@ -851,7 +853,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
             const size_t kn = kz + g.nxy;
             if (own) {
                 if (z + 2 < g.nz) nup = val2(kn + g.nxy);
-                if (kMode != 0) nb_ = Bv[kn >> 1];
+                if (!kPlain) nb_ = Bv[kn >> 1];
             }
             if (rowlo) nlo = val2(kn - g.nx);
             if (rowhi) nhi = val2(kn + g.nx);
@@ -883,7 +885,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
             s1 += hi_df(vdn);
             s1 += hi_df(vup);
             float rf0, rf1;
-            if (kMode == 0) {
+            if (kMode == 3) {   // one explicit Euler step: x + c L x
+                const DF l0 = s0 - df_mulf(v0, (float)(n0 + nz_));
+                const DF l1 = s1 - df_mulf(v1, (float)(n1 + nz_));
+                XO[kz >> 1] = pack_df(v0 + df_mul(cf.c, l0), v1 + df_mul(cf.c, l1));
+            } else if (kMode == 0) {
                 const DF l0 = s0 - df_mulf(v0, (float)(n0 + nz_));
                 const DF l1 = s1 - df_mulf(v1, (float)(n1 + nz_));
                 rf0 = df_f(df_mul(cf.c, l0));
@@ -937,6 +943,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         hl = nl;
         hr = nr;
     }
+    if (kMode == 3) return;   // the explicit step reduces nothing
     double vals[2] = {block_sum_f(rr), kMode != 1 ? block_sum_f(bb) : 0.0};
     double *partials = partials_all + (size_t)f * 2 * nb;
     if (arrive(partials, kMode != 1 ? 2 : 1, vals, bid, nb, &sc[f].ticket)) {
@@ -2444,10 +2451,40 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
     if (c > 1.0 / 6.0 + 1e-15)
         return fail(CG_EINVAL, "cg_diffuse: explicit Euler needs dtau <= dx^2/6 (dtau/dx^2 = %g)", c);
     const size_t vec = align_up((size_t)n * nf * 8);
-    CGK_TRY(m->ws_diffuse.ensure(vec));
-    double *tmp = m->ws_diffuse.as<double>();
     const Sweep sw = make_sweep(g, nf);
     const dim3 blk(TX, TY);
+    const bool df = (p->precision == CG_PREC_FP32_DF_REFINE || p->precision == CG_PREC_BF16_DF_REFINE) &&
+                    m->nx % 2 == 0;
+    if (df) {
+        // double-float steps (FP64-class accuracy on the FP32 units), two cells per thread
+        CGK_TRY(m->ws_diffuse.ensure(2 * vec));
+        DF *A = m->ws_diffuse.as<DF>(), *Bf = (DF *)(m->ws_diffuse.as<char>() + vec);
+        const CoefDF cfdf = coefdf(c, c);
+        const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
+        CGK_LAUNCH("to_double_float", (double)n * nf * 16, st,
+                   k_to_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, cells, A));
+        for (int s = 0; s < p->nsteps; ++s) {
+            CGK_LAUNCH("explicit_df", (double)n * nf * 16, st,
+                       launch_chain(k_refine_df2<float, 3>, grid, blk, st, g, sw.zlen, sw.nzc, cfdf,
+                                    p->scheme, (const DF *)A, (const float *)nullptr,
+                                    (const DF *)nullptr, Bf, (DF *)nullptr, (float *)nullptr,
+                                    (float *)nullptr, 0.0f, (double *)nullptr, (RefScal *)nullptr,
+                                    (RefScal *)nullptr));
+            std::swap(A, Bf);
+        }
+        CGK_LAUNCH("from_double_float", (double)n * nf * 16, st,
+                   k_from_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, A, cells));
+        CGK_CUDA(cudaGetLastError());
+        CGK_CUDA(cudaStreamSynchronize(st));
+        if (rep) {
+            rep->iters = (long long)p->nsteps * nf;
+            rep->cell_updates = rep->iters * (long long)n;
+            rep->final_rel_residual = 0.0;
+        }
+        return CG_OK;
+    }
+    CGK_TRY(m->ws_diffuse.ensure(vec));
+    double *tmp = m->ws_diffuse.as<double>();
     double *a = cells, *b = tmp;
     for (int s = 0; s < p->nsteps; ++s) {
         CGK_LAUNCH("explicit64", (double)n * nf * 16, st,

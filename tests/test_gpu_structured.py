@@ -292,3 +292,29 @@ def test_barrier_timeout_reports_etimeout_and_context_survives(cg):
         cg.diffuse(mesh, u, cg.Params(bandwidth=0.2, nsteps=2, precision=1, barrier_budget=budget))
         outs.append(bits(u.cpu().numpy()))
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("dims", [(40, 30, 20), (130, 9, 7)])
+def test_diffuse_explicit_double_float_parity(cg, orc, dims):
+    """Explicit Euler steps in double-float arithmetic (precision 3, even nx): within
+    the FP64 bar of the oracle after 40 steps, deterministic, and matching the FP64 GPU
+    steps; beyond the stability limit the call is refused."""
+    dx = 1.0 / dims[0]
+    rng = np.random.default_rng(17)
+    u0 = rng.random((2, int(np.prod(dims))))
+    u0[1] -= 0.5
+    T = 0.15 * dx * dx * 40          # dtau/dx^2 = 0.15 <= 1/6
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 40, scheme=2)
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx)
+    outs = []
+    for _ in range(2):
+        u = dev(u0)
+        cg.diffuse(mesh, u, cg.Params(T=T, nsteps=40, scheme=2, precision=3))
+        outs.append(u.cpu().numpy())
+    assert np.array_equal(bits(outs[0]), bits(outs[1]))
+    assert maxrel(outs[0], ref) <= 1e-12
+    u64 = dev(u0)
+    cg.diffuse(mesh, u64, cg.Params(T=T, nsteps=40, scheme=2, precision=0))
+    assert maxrel(outs[0], u64.cpu().numpy()) <= 1e-12
+    with pytest.raises(cg.CGError):
+        cg.diffuse(mesh, dev(u0), cg.Params(T=0.2 * dx * dx * 40, nsteps=40, scheme=2, precision=3))
