@@ -71,6 +71,15 @@ def _load():
                                                ctypes.c_double, ctypes.c_int, _f64p,
                                                ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_int, _i64p]
+        lib.orc_diffuse_structured_p.restype = ctypes.c_int
+        lib.orc_diffuse_structured_p.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                 _f64p, ctypes.c_double, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                 _i64p]
+        lib.orc_solid_velocity.restype = None
+        lib.orc_solid_velocity.argtypes = [ctypes.c_int64, ctypes.c_int, _f64p, _f64p,
+                                           ctypes.c_double, _f64p]
         lib.orc_tet_build.restype = ctypes.c_int64
         lib.orc_tet_build.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p,
                                       _i64p, _i32p, _f64p]
@@ -171,16 +180,20 @@ def deposit(cell, w, ncells, vc=None, vc_uniform=1.0, mode=0):
 
 
 # ----------------------------------------------------------------------------- diffuse
-def diffuse_structured(u, dims, dx, T, nsteps, scheme=0, tol=1e-14, max_iter=100000):
-    """Pseudo-time integration of Eq. (diffusion) on a uniform mesh with zero-flux walls.
-    u is [nf, ncells] (or [ncells]); returns (u(T), total CG iterations)."""
+def diffuse_structured(u, dims, dx, T, nsteps, scheme=0, tol=1e-14, max_iter=100000,
+                       periodic=(False, False, False)):
+    """Pseudo-time integration of Eq. (diffusion) on a uniform mesh with zero-flux walls
+    (or periodic axes where periodic[a] is set, Section 3.2.2).  u is [nf, ncells] (or
+    [ncells]); returns (u(T), total CG iterations)."""
     nx, ny, nz = (int(d) for d in dims)
+    per = sum(1 << a for a in range(3) if periodic[a])
     squeeze = np.ndim(u) == 1
     u = np.array(np.atleast_2d(u), dtype=np.float64, order="C", copy=True)
     iters = ctypes.c_int64(0)
-    st = _load().orc_diffuse_structured(nx, ny, nz, float(dx), u.shape[0], _p(u, ctypes.c_double),
-                                        float(T), int(nsteps), int(scheme), float(tol),
-                                        int(max_iter), ctypes.byref(iters))
+    st = _load().orc_diffuse_structured_p(nx, ny, nz, per, float(dx), u.shape[0],
+                                          _p(u, ctypes.c_double), float(T), int(nsteps),
+                                          int(scheme), float(tol), int(max_iter),
+                                          ctypes.byref(iters))
     if st != 0:
         raise RuntimeError("oracle CG did not converge")
     return (u[0] if squeeze else u), int(iters.value)
@@ -246,3 +259,15 @@ def coarse_grain_structured(dims, origin, dx, pos, w, b, nsteps, scheme=0, mode=
     eps0, _ = deposit(cell, w, nx * ny * nz, vc_uniform=vcu, mode=mode)
     epsT, iters = diffuse_structured(eps0, dims, dx, bandwidth_to_time(b), nsteps, scheme, tol)
     return eps0, epsT, nout, iters
+
+
+def solid_velocity(eps, mom, eps_min=0.0):
+    """Solid velocity as diffused momentum over diffused solid fraction (conclusions of
+    the paper: momentum, not velocity, is diffused); 0 where eps <= eps_min.  eps is
+    [ncells], mom [ncomp, ncells]."""
+    eps = _f64(eps)
+    mom = np.array(np.atleast_2d(mom), dtype=np.float64, order="C")
+    out = np.empty_like(mom)
+    _load().orc_solid_velocity(eps.shape[0], mom.shape[0], _p(eps, ctypes.c_double),
+                               _p(mom, ctypes.c_double), float(eps_min), _p(out, ctypes.c_double))
+    return out

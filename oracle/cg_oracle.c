@@ -154,30 +154,38 @@ void orc_deposit(int64_t n, const int32_t *cell, int nf, const double *w,
 /* The physical operator is L / dx^2.                                           */
 /* ------------------------------------------------------------------------- */
 
-static void lap7(int nx, int ny, int nz, const double *u, double *out)
+/* An axis may instead be periodic (Section 3.2.2: periodic boundaries keep periodic
+ * conditions): bit a of per set means the neighbour beyond the last cell along axis a
+ * is the first one and the other way round (on an axis of one cell that is the cell
+ * itself). */
+static int64_t wrap(int64_t i, int64_t n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+static void lap7p(int nx, int ny, int nz, int per, const double *u, double *out)
 {
+    const int px = per & 1, py = (per >> 1) & 1, pz = (per >> 2) & 1;
     for (int iz = 0; iz < nz; ++iz)
         for (int iy = 0; iy < ny; ++iy)
             for (int ix = 0; ix < nx; ++ix) {
                 int64_t k = ((int64_t)iz * ny + iy) * nx + ix;
                 double s = 0.0;
-                if (ix > 0) s += u[k - 1] - u[k];
-                if (ix < nx - 1) s += u[k + 1] - u[k];
-                if (iy > 0) s += u[k - nx] - u[k];
-                if (iy < ny - 1) s += u[k + nx] - u[k];
-                if (iz > 0) s += u[k - (int64_t)nx * ny] - u[k];
-                if (iz < nz - 1) s += u[k + (int64_t)nx * ny] - u[k];
+                if (ix > 0 || px) s += u[((int64_t)iz * ny + iy) * nx + wrap(ix - 1, nx)] - u[k];
+                if (ix < nx - 1 || px) s += u[((int64_t)iz * ny + iy) * nx + wrap(ix + 1, nx)] - u[k];
+                if (iy > 0 || py) s += u[((int64_t)iz * ny + wrap(iy - 1, ny)) * nx + ix] - u[k];
+                if (iy < ny - 1 || py) s += u[((int64_t)iz * ny + wrap(iy + 1, ny)) * nx + ix] - u[k];
+                if (iz > 0 || pz) s += u[(wrap(iz - 1, nz) * ny + iy) * nx + ix] - u[k];
+                if (iz < nz - 1 || pz) s += u[(wrap(iz + 1, nz) * ny + iy) * nx + ix] - u[k];
                 out[k] = s;
             }
 }
 
+
 /* A u = u - theta * c * L u, with c = dtau / dx^2 and theta = 1 (implicit Euler)
  * or 1/2 (Crank-Nicolson). */
-static void apply_implicit(int nx, int ny, int nz, double cth, const double *u,
+static void apply_implicit(int nx, int ny, int nz, int per, double cth, const double *u,
                            double *tmp, double *out)
 {
     int64_t N = (int64_t)nx * ny * nz;
-    lap7(nx, ny, nz, u, tmp);
+    lap7p(nx, ny, nz, per, u, tmp);
     for (int64_t k = 0; k < N; ++k) out[k] = u[k] - cth * tmp[k];
 }
 
@@ -228,7 +236,7 @@ static int cg_solve(int64_t n, orc_apply_fn apply, const void *ctx, const double
 }
 
 typedef struct {
-    int nx, ny, nz;
+    int nx, ny, nz, per;
     double cth;
     double *tmp;
 } struct_ctx;
@@ -236,7 +244,7 @@ typedef struct {
 static void struct_apply(const void *vctx, const double *in, double *out)
 {
     const struct_ctx *c = (const struct_ctx *)vctx;
-    apply_implicit(c->nx, c->ny, c->nz, c->cth, in, c->tmp, out);
+    apply_implicit(c->nx, c->ny, c->nz, c->per, c->cth, in, c->tmp, out);
 }
 
 /* u is [nf][nx*ny*nz] (intensive field eps, in/out).  T is the pseudo-time,
@@ -247,9 +255,9 @@ static void struct_apply(const void *vctx, const double *in, double *out)
  * (all divided through by the uniform cell volume).  Each implicit step starts CG
  * from u^n.  iters_out (may be NULL) receives the total CG iteration count.
  * Returns 0, or -1 if some solve did not converge. */
-int orc_diffuse_structured(int nx, int ny, int nz, double dx, int nf, double *u,
-                           double T, int nsteps, int scheme, double tol, int max_iter,
-                           int64_t *iters_out)
+int orc_diffuse_structured_p(int nx, int ny, int nz, int per, double dx, int nf, double *u,
+                             double T, int nsteps, int scheme, double tol, int max_iter,
+                             int64_t *iters_out)
 {
     int64_t N = (int64_t)nx * ny * nz;
     double dtau = T / (double)nsteps;
@@ -257,19 +265,19 @@ int orc_diffuse_structured(int nx, int ny, int nz, double dx, int nf, double *u,
     double *tmp = (double *)malloc((size_t)N * sizeof(double));
     double *rhs = (double *)malloc((size_t)N * sizeof(double));
     double *lu = (double *)malloc((size_t)N * sizeof(double));
-    struct_ctx ctx = {nx, ny, nz, scheme == 1 ? 0.5 * c : c, tmp};
+    struct_ctx ctx = {nx, ny, nz, per, scheme == 1 ? 0.5 * c : c, tmp};
     int64_t iters = 0;
     int status = 0;
     for (int f = 0; f < nf; ++f) {
         double *uf = u + (int64_t)f * N;
         for (int s = 0; s < nsteps; ++s) {
             if (scheme == 2) {
-                lap7(nx, ny, nz, uf, lu);
+                lap7p(nx, ny, nz, per, uf, lu);
                 for (int64_t k = 0; k < N; ++k) uf[k] = uf[k] + c * lu[k];
                 continue;
             }
             if (scheme == 1) {
-                lap7(nx, ny, nz, uf, lu);
+                lap7p(nx, ny, nz, per, uf, lu);
                 for (int64_t k = 0; k < N; ++k) rhs[k] = uf[k] + 0.5 * c * lu[k];
             } else {
                 for (int64_t k = 0; k < N; ++k) rhs[k] = uf[k];
@@ -287,6 +295,27 @@ int orc_diffuse_structured(int nx, int ny, int nz, double dx, int nf, double *u,
     free(lu);
     if (iters_out) *iters_out = iters;
     return status;
+}
+
+/* The zero-flux case (no periodic axis). */
+int orc_diffuse_structured(int nx, int ny, int nz, double dx, int nf, double *u,
+                           double T, int nsteps, int scheme, double tol, int max_iter,
+                           int64_t *iters_out)
+{
+    return orc_diffuse_structured_p(nx, ny, nz, 0, dx, nf, u, T, nsteps, scheme, tol, max_iter,
+                                    iters_out);
+}
+
+/* The solid velocity of a cell as the ratio of two smoothed fields: the diffused
+ * momentum sum_i V_p,i u_i / V_c and the diffused solid fraction (the momentum, not
+ * the velocity, is what is diffused).  Cells whose solid fraction is not above eps_min
+ * get 0.  mom is [ncomp][n], out the same. */
+void orc_solid_velocity(int64_t n, int ncomp, const double *eps, const double *mom,
+                        double eps_min, double *out)
+{
+    for (int c = 0; c < ncomp; ++c)
+        for (int64_t k = 0; k < n; ++k)
+            out[(int64_t)c * n + k] = eps[k] > eps_min ? mom[(int64_t)c * n + k] / eps[k] : 0.0;
 }
 
 /* ------------------------------------------------------------------------- */

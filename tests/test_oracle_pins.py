@@ -467,3 +467,73 @@ def test_golden_close_packed_layer_solid_fraction(orc):
     assert abs(u.sum() * d ** 3 / layer_volume - mean) <= 1e-12
     inner = u.reshape(65, 64)[10:54, 10:54]
     assert abs(inner.mean() - mean) <= 2e-3
+
+
+def _closed_form_mixed(u0, dims, c, nsteps, periodic, scheme=0):
+    """The exact discrete solution with per-axis eigenbases: the DFT on a periodic axis
+    (eigenvalues -4 sin^2(pi j / n)), the orthonormal DCT-II on a zero-flux axis
+    (-4 sin^2(pi j / (2 n)))."""
+    import scipy.fft as sf
+    nx, ny, nz = dims
+    a = np.asarray(u0, dtype=np.float64).reshape(nz, ny, nx).astype(complex)
+    lam = np.zeros((nz, ny, nx))
+    for ax, (n, per) in enumerate(zip((nz, ny, nx), (periodic[2], periodic[1], periodic[0]))):
+        j = np.arange(n)
+        lj = -4.0 * np.sin(np.pi * j / n) ** 2 if per else -4.0 * np.sin(np.pi * j / (2 * n)) ** 2
+        shape = [1, 1, 1]
+        shape[ax] = n
+        lam = lam + lj.reshape(shape)
+        a = np.fft.fft(a, axis=ax) if per else sf.dct(a.real, type=2, norm="ortho", axis=ax) + 1j * sf.dct(a.imag, type=2, norm="ortho", axis=ax)
+    g = {0: 1.0 / (1.0 - c * lam), 1: (1.0 + 0.5 * c * lam) / (1.0 - 0.5 * c * lam),
+         2: 1.0 + c * lam}[scheme]
+    a = a * g ** nsteps
+    for ax, (n, per) in reversed(list(enumerate(zip((nz, ny, nx), (periodic[2], periodic[1], periodic[0]))))):
+        a = np.fft.ifft(a, axis=ax) if per else sf.idct(a.real, type=2, norm="ortho", axis=ax) + 1j * sf.idct(a.imag, type=2, norm="ortho", axis=ax)
+    return a.real.ravel()
+
+
+@pytest.mark.parametrize("periodic", [(True, True, True), (True, False, False), (False, True, True)])
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_periodic_diffusion_matches_closed_form(orc, periodic, scheme):
+    """Periodic axes (Section 3.2.2): the oracle against the exact DFT/DCT solution."""
+    dims = (9, 6, 5)
+    rng = np.random.default_rng(60)
+    u0 = rng.random(int(np.prod(dims)))
+    dx = 0.1
+    c = 0.15 if scheme == 2 else 0.8
+    T = c * dx * dx * 7
+    got, _ = orc.diffuse_structured(u0, dims, dx, T, 7, scheme=scheme, tol=1e-15, periodic=periodic)
+    ref = _closed_form_mixed(u0, dims, c, 7, periodic, scheme)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert abs(got.sum() - u0.sum()) <= 1e-12 * u0.sum()
+
+
+def test_periodic_shift_invariance(orc):
+    """On an all-periodic mesh the smoothing commutes with a cyclic shift of the cells."""
+    dims = (8, 7, 6)
+    rng = np.random.default_rng(61)
+    u0 = rng.random(dims[::-1])
+    shifted = np.roll(u0, (2, -3, 5), axis=(0, 1, 2))
+    a, _ = orc.diffuse_structured(u0.ravel(), dims, 0.1, 0.02, 5, tol=1e-15, periodic=(True,) * 3)
+    b, _ = orc.diffuse_structured(shifted.ravel(), dims, 0.1, 0.02, 5, tol=1e-15, periodic=(True,) * 3)
+    assert np.max(np.abs(np.roll(a.reshape(dims[::-1]), (2, -3, 5), axis=(0, 1, 2)) - b.reshape(dims[::-1]))) <= 1e-13
+
+
+def test_solid_velocity_of_uniform_motion(orc):
+    """Every particle moving with the same velocity U0: the diffused momentum is U0 times
+    the diffused solid fraction (linearity), so the solid velocity is U0 in every cell
+    with solid, and 0 where there is none."""
+    c = W.uniform_cube(n_side=16, n_particles=2000, seed=62)
+    U0 = np.array([0.3, -1.25, 2.0])
+    w = np.vstack([c.w[0], np.outer(U0, c.w[0])])
+    cell, _ = orc.locate_structured(c.dims, c.origin, c.dx, c.pos)
+    eps, _ = orc.deposit(cell, w, c.ncells, vc_uniform=c.dx ** 3)
+    u, _ = orc.diffuse_structured(eps, c.dims, c.dx, (2 * c.dx) ** 2 / 4, 10, tol=1e-15)
+    us = orc.solid_velocity(u[0], u[1:], eps_min=1e-12 * u[0].max())
+    inside = u[0] > 1e-12 * u[0].max()
+    assert inside.any()
+    assert np.max(np.abs(us[:, inside] - U0[:, None])) <= 1e-12 * np.abs(U0).max()
+    assert np.all(us[:, ~inside] == 0.0)
+    raw = orc.solid_velocity(eps[0], eps[1:], 0.0)      # before smoothing: per particle cell
+    occ = eps[0] > 0
+    assert np.max(np.abs(raw[:, occ] - U0[:, None])) <= 1e-14 * np.abs(U0).max()
