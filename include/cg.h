@@ -84,6 +84,16 @@ int64_t cg_mesh_num_cells(const cg_mesh *mesh);
 /* Copies the cell volumes V_c into out_host[ncells] (FP64). */
 cg_status cg_mesh_cell_volumes(const cg_mesh *mesh, double *out_host);
 
+/* Periodic axes of a structured mesh (Section 3.2.2: a periodic boundary keeps a
+ * periodic condition instead of zero flux).  px, py, pz nonzero make the faces at the
+ * two ends of the mesh along x, y, z neighbours of each other (on an axis of one cell,
+ * of the cell itself); all zero restores the walls.  Deposition is unchanged.  With a
+ * periodic axis the diffusion uses the z-marching sweeps and the one-cell-per-thread
+ * refinement (params->sweep_shape must be 0 or negative), and batched calls reject the
+ * mesh.  Drops the mesh's captured schedules and tuned shapes.  Errors: CG_EINVAL (NULL
+ * or a tet mesh). */
+cg_status cg_mesh_set_periodic(cg_mesh *mesh, int px, int py, int pz);
+
 /* Copies the tet mesh's Laplacian in CSR form to host arrays: rowptr_host[ncells+1],
  * col_host[nnz], val_host[nnz]; *nnz_out receives nnz.  Pass NULL arrays to query
  * nnz only.  CG_EINVAL for a structured mesh. */
@@ -205,6 +215,16 @@ cg_status cg_coarse_grain(cg_mesh *mesh, int64_t n, const double *pos, int nfiel
 cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host, int nfields,
                                const double *w_host, double *cells_host, const cg_params *params,
                                cg_report *report, void *stream);
+
+/* The solid velocity (the paper's conclusions: the momentum, not the velocity, is
+ * diffused): U_s = smoothed momentum / smoothed solid fraction per cell and component,
+ * the two smoothed fields taken from one multi-field cg_coarse_grain or cg_diffuse call
+ * (weights V_p and V_p u).  eps: device [ncells] FP64; mom: device [ncomp][ncells];
+ * u_out: device [ncomp][ncells], not overlapping the inputs.  A cell whose solid
+ * fraction is not above eps_min (>= 0) gets 0; the division is IEEE FP64.  Synchronises
+ * the stream.  Errors: CG_EINVAL (NULL, host pointers, overlap, ncomp outside [1, 64]). */
+cg_status cg_solid_velocity(const cg_mesh *mesh, int ncomp, const double *eps,
+                            const double *mom, double eps_min, double *u_out, void *stream);
 
 /* ------------------------------------------------------------------------ batches */
 

@@ -107,6 +107,8 @@ def load_library(path: str | None = None):
         "cg_deposit_fixed_noalloc": (i32, [i32, i32, i32, P(dbl), dbl, i64, vp, i32, vp, vp,
                                            P(ctypes.c_int), vp]),
         "cg_launch_count_reset": (None, []),
+        "cg_mesh_set_periodic": (i32, [vp, i32, i32, i32]),
+        "cg_solid_velocity": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -123,7 +125,8 @@ def exported_symbols():
             "cg_mesh_tet_operator", "cg_locate", "cg_deposit", "cg_diffuse", "cg_coarse_grain",
             "cg_coarse_grain_host", "cg_profile_enable", "cg_profile_reset", "cg_profile_count",
             "cg_profile_get", "cg_launch_count", "cg_launch_count_reset",
-            "cg_deposit_fixed_noalloc", "cg_diffuse_batched", "cg_coarse_grain_batched"]
+            "cg_deposit_fixed_noalloc", "cg_diffuse_batched", "cg_coarse_grain_batched",
+            "cg_mesh_set_periodic", "cg_solid_velocity"]
 
 
 def _check(status: int, where: str):
@@ -202,9 +205,10 @@ class _MeshBase:
 
 
 class StructuredMesh(_MeshBase):
-    """Uniform Cartesian hex mesh (cg_create_mesh_structured)."""
+    """Uniform Cartesian hex mesh (cg_create_mesh_structured); periodic = (px, py, pz)
+    marks periodic axes (cg_mesh_set_periodic)."""
 
-    def __init__(self, dims, origin, dx):
+    def __init__(self, dims, origin, dx, periodic=(False, False, False)):
         lib = load_library()
         self.dims = tuple(int(d) for d in dims)
         self.origin = tuple(float(o) for o in origin)
@@ -214,6 +218,12 @@ class StructuredMesh(_MeshBase):
         _check(lib.cg_create_mesh_structured(self.dims[0], self.dims[1], self.dims[2], org, self.dx,
                                              ctypes.byref(h)), "cg_create_mesh_structured")
         self._h = h
+        if any(periodic):
+            self.set_periodic(*periodic)
+
+    def set_periodic(self, px, py, pz):
+        _check(load_library().cg_mesh_set_periodic(self.handle, int(bool(px)), int(bool(py)),
+                                                   int(bool(pz))), "cg_mesh_set_periodic")
 
 
 class TetMesh(_MeshBase):
@@ -297,6 +307,20 @@ def coarse_grain(mesh, pos, w, params: Params, out=None, stream=None, report=Fal
                                           out.data_ptr(), ctypes.byref(cp), ctypes.byref(rep),
                                           _stream_handle(stream)), "cg_coarse_grain")
     return (out, rep.as_dict()) if report else out
+
+
+def solid_velocity(mesh, eps, mom, eps_min=0.0, out=None, stream=None):
+    """Solid velocity (cg_solid_velocity): mom / eps per cell where eps > eps_min, else 0.
+    eps: CUDA f64 [ncells]; mom: CUDA f64 [ncomp, ncells]; returns [ncomp, ncells]."""
+    import torch
+    _dev_f64(eps, "eps")
+    _dev_f64(mom, "mom")
+    if out is None:
+        out = torch.empty_like(mom)
+    _check(load_library().cg_solid_velocity(mesh.handle, mom.shape[0], eps.data_ptr(),
+                                            mom.data_ptr(), float(eps_min), out.data_ptr(),
+                                            _stream_handle(stream)), "cg_solid_velocity")
+    return out
 
 
 def coarse_grain_host(mesh, pos, w, params: Params, out=None, stream=None, report=False):

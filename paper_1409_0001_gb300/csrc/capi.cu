@@ -394,6 +394,35 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
 
 int64_t cg_mesh_num_cells(const cg_mesh *m) { return m ? m->ncells : -1; }
 
+cg_status cg_mesh_set_periodic(cg_mesh *m, int px, int py, int pz) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    if (m->kind != MESH_STRUCTURED) return fail(CG_EINVAL, "periodic axes need a structured mesh");
+    const int per = (px ? 1 : 0) | (py ? 2 : 0) | (pz ? 4 : 0);
+    if (per != m->per) {   // captured schedules and tuned shapes assumed the old walls
+        for (auto &e : m->graphs) graph_release(e);
+        m->graphs.clear();
+        m->tuned.clear();
+        m->rounds.clear();
+        m->per = per;
+    }
+    return CG_OK;
+}
+
+cg_status cg_solid_velocity(const cg_mesh *m, int ncomp, const double *eps, const double *mom,
+                            double eps_min, double *u_out, void *stream) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    if (ncomp < 1 || ncomp > 64) return fail(CG_EINVAL, "ncomp must be in [1, 64]");
+    if (!is_device_ptr(eps) || !is_device_ptr(mom) || !is_device_ptr(u_out))
+        return fail(CG_EINVAL, "eps, mom and u_out must be device pointers");
+    if (!(eps_min >= 0.0) || !std::isfinite(eps_min)) return fail(CG_EINVAL, "eps_min must be >= 0");
+    const int64_t n = m->ncells;
+    const char *a = (const char *)u_out, *b = (const char *)mom, *c = (const char *)eps;
+    const size_t bytes = (size_t)ncomp * n * 8;
+    if ((a < b + bytes && b < a + bytes) || (a < c + (size_t)n * 8 && c < a + bytes))
+        return fail(CG_EINVAL, "u_out overlaps eps or mom");
+    return solid_velocity_run(n, ncomp, eps, mom, eps_min, u_out, (cudaStream_t)stream);
+}
+
 cg_status cg_mesh_cell_volumes(const cg_mesh *m, double *out_host) {
     if (!m || !out_host) return fail(CG_EINVAL, "NULL argument");
     if (m->kind == MESH_STRUCTURED) {
@@ -596,6 +625,8 @@ static cg_status check_batch(int nsnap, cg_mesh *const *meshes, int nfields, dou
     for (int s = 0; s < nsnap; ++s) {
         if (!meshes[s] || meshes[s]->kind != MESH_STRUCTURED)
             return fail(CG_EINVAL, "batch snapshot %d: not a structured mesh", s);
+        if (meshes[s]->per)
+            return fail(CG_EINVAL, "batch snapshot %d: periodic meshes are not batched", s);
         if (!is_device_ptr(cells[s])) return fail(CG_EINVAL, "batch snapshot %d: cells not on the device", s);
         if (bandwidths && !(bandwidths[s] > 0.0 && std::isfinite(bandwidths[s])))
             return fail(CG_EINVAL, "batch snapshot %d: bandwidth must be finite and > 0", s);

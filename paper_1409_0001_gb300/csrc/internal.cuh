@@ -131,6 +131,7 @@ struct TetDevice {
 struct cg_mesh {
     int kind = cgk::MESH_STRUCTURED;
     int nx = 0, ny = 0, nz = 0;
+    int per = 0;   // periodic axes of a structured mesh (bit 0 x, 1 y, 2 z)
     double origin[3] = {0, 0, 0};
     double dx = 0;
     int64_t ncells = 0;
@@ -212,6 +213,10 @@ void graph_release(GraphEntry &e);
 // also accumulates per-cell particle counts (must be zeroed by the caller), writes each
 // particle's arrival rank at its cell's counter to ranks (if not nullptr) and returns
 // the largest count in max_count (if not nullptr).
+// u_out[c][k] = mom[c][k] / eps[k] where eps[k] > eps_min, else 0 (IEEE division).
+cg_status solid_velocity_run(int64_t n, int ncomp, const double *eps, const double *mom,
+                             double eps_min, double *u_out, cudaStream_t st);
+
 cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                      int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
                      cudaStream_t st, uint32_t *max_count = nullptr, uint32_t *ranks = nullptr);

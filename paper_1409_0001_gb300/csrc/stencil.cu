@@ -41,6 +41,7 @@ struct Geo {
     int nx, ny, nz;
     int nxy;
     int n;
+    int per = 0;   // periodic axes: bit 0 x, bit 1 y, bit 2 z (scalar engines only)
 };
 
 // Programmatic dependent launch: a kernel of the solver chain is launched while its
@@ -123,12 +124,21 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
     const int x = bx * TX + tx, y = by * TY + ty;
     const bool own = (x < g.nx) && (y < g.ny);
     const int kxy = y * g.nx + x;
-    // halo roles: which neighbour column (if any) this thread also loads
-    const bool hxl = (tx == 0) && (x > 0) && (y < g.ny);
-    const bool hxh = (tx == TX - 1) && (x + 1 < g.nx) && (y < g.ny);
-    const bool hyl = (ty == 0) && (y > 0) && (x < g.nx);
-    const bool hyh = (ty == TY - 1) && (y + 1 < g.ny) && (x < g.nx);
-    const int nnxy = (x > 0) + (x + 1 < g.nx) + (y > 0) + (y + 1 < g.ny);
+    const bool px = g.per & 1, py = (g.per >> 1) & 1, pz = (g.per >> 2) & 1;
+    // halo roles: which neighbour column (if any) this thread also loads -- the first
+    // and the last column / row of the tile inside the mesh; across a periodic axis the
+    // neighbour of the mesh's first (last) cell is its last (first)
+    const int xe = min(bx * TX + TX, g.nx) - 1, ye = min(by * TY + TY, g.ny) - 1;
+    const bool hxl = (tx == 0) && (x > 0 || px) && (y < g.ny) && (x < g.nx);
+    const bool hxh = (x == xe) && (x + 1 < g.nx || px) && (y < g.ny);
+    const bool hyl = (ty == 0) && (y > 0 || py) && (x < g.nx) && (y < g.ny);
+    const bool hyh = (y == ye) && (y + 1 < g.ny || py) && (x < g.nx);
+    const int dxl = x > 0 ? -1 : g.nx - 1, dxh = x + 1 < g.nx ? 1 : 1 - g.nx;
+    const int dyl = y > 0 ? -g.nx : (g.ny - 1) * g.nx, dyh = y + 1 < g.ny ? g.nx : (1 - g.ny) * g.nx;
+    const int nnxy = (px ? 2 : (x > 0) + (x + 1 < g.nx)) + (py ? 2 : (y > 0) + (y + 1 < g.ny));
+    // plane offsets of the z neighbours (periodic z wraps)
+    auto zdn = [&](int z) { return z > 0 ? -g.nxy : (g.nz - 1) * g.nxy; };
+    auto zup = [&](int z) { return z + 1 < g.nz ? g.nxy : (1 - g.nz) * g.nxy; };
     // zero the plane once: wall slots and the slots of columns outside the mesh are
     // never written again
     for (int i = ty * TX + tx; i < (TY + 2) * (TX + 2); i += TX * TY) (&pl[0][0])[i] = T();
@@ -141,15 +151,15 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
     if (z0 < z1) {
         const int k0 = kxy + z0 * g.nxy;
         if (own) {
-            if (z0 > 0) vdn = produce(k0 - g.nxy);
+            if (z0 > 0 || pz) vdn = produce(k0 + zdn(z0));
             vc = produce(k0);
-            if (z0 + 1 < g.nz) vup = produce(k0 + g.nxy);
+            if (z0 + 1 < g.nz || pz) vup = produce(k0 + zup(z0));
             pt = pre(k0);
         }
-        if (hxl) hxa = produce(k0 - 1);
-        if (hxh) hxb = produce(k0 + 1);
-        if (hyl) hya = produce(k0 - g.nx);
-        if (hyh) hyb = produce(k0 + g.nx);
+        if (hxl) hxa = produce(k0 + dxl);
+        if (hxh) hxb = produce(k0 + dxh);
+        if (hyl) hya = produce(k0 + dyl);
+        if (hyh) hyb = produce(k0 + dyh);
     }
     for (int z = z0; z < z1; ++z) {
         const int kz = kxy + z * g.nxy;
@@ -159,20 +169,20 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
         if (z + 1 < z1) {
             const int kn = kz + g.nxy;
             if (own) {
-                if (z + 2 < g.nz) nup = produce(kn + g.nxy);
+                if (z + 2 < g.nz || pz) nup = produce(kn + zup(z + 1));
                 npt = pre(kn);
             }
-            if (hxl) nxa = produce(kn - 1);
-            if (hxh) nxb = produce(kn + 1);
-            if (hyl) nya = produce(kn - g.nx);
-            if (hyh) nyb = produce(kn + g.nx);
+            if (hxl) nxa = produce(kn + dxl);
+            if (hxh) nxb = produce(kn + dxh);
+            if (hyl) nya = produce(kn + dyl);
+            if (hyh) nyb = produce(kn + dyh);
         }
         // publish plane z and update its cells
         if (own) pl[ty + 1][tx + 1] = vc;
         if (hxl) pl[ty + 1][0] = hxa;
-        if (hxh) pl[ty + 1][TX + 1] = hxb;
+        if (hxh) pl[ty + 1][tx + 2] = hxb;
         if (hyl) pl[0][tx + 1] = hya;
-        if (hyh) pl[TY + 1][tx + 1] = hyb;
+        if (hyh) pl[ty + 2][tx + 1] = hyb;
         __syncthreads();
         if (own) {
             T s = pl[ty + 1][tx];
@@ -181,7 +191,7 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
             s += pl[ty + 2][tx + 1];
             s += vdn;
             s += vup;
-            const int nn = nnxy + (z > 0) + (z + 1 < g.nz);
+            const int nn = nnxy + (pz ? 2 : (z > 0) + (z + 1 < g.nz));
             consume(kz, vc, s, nn, pt);
         }
         __syncthreads();
@@ -2062,14 +2072,15 @@ TS *cheb_pairs(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, do
 }
 
 // A double-float refinement pass of mode kMode: the two-cells-per-thread kernel when nx
-// is even, the scalar one otherwise; both use the z-chunks of sw (same partial slots).
+// is even (and no axis is periodic), the scalar one otherwise; both use the z-chunks of
+// sw (same partial slots).
 template <class TS, int kMode>
 void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, int scheme,
                       const DF *xin, const TS *d, const DF *b, DF *xout, DF *bout, TS *r, TS *y1,
                       float gamma, double *partials, RefScal *sc, RefScal *sc_next,
                       cudaStream_t st) {
     const dim3 blk(TX, TY);
-    if (g.nx % 2 == 0) {
+    if (g.nx % 2 == 0 && g.per == 0) {
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
         launch_chain(k_refine_df2<TS, kMode>, grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
                      d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
@@ -2267,7 +2278,7 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
 template <class TS>
 cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, TS *yb, TS *yc,
                     TS *yd, const TS *r, cudaStream_t st, int *code_out) {
-    const int key = nf * 4 + (int)sizeof(TS);
+    const int key = (nf * 4 + (int)sizeof(TS)) * 8 + g.per;
     for (auto &e : m->tuned)
         if (e.first == key) {
             *code_out = e.second;
@@ -2279,7 +2290,8 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     std::vector<std::pair<int, int>> cands;
     const bool v4 = g.nx % 4 == 0;   // vectorised shapes need whole 4-cell vectors per row
     for (int c : {101, 102, 104, 108, 116, 2, 4, 8, -1, -4, -16})
-        if (c < 100 || v4) cands.push_back({c, 10});
+        if ((c < 100 || v4) && (g.per == 0 || c < 0))   // periodic axes: z-marching only
+            cands.push_back({c, 10});
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
@@ -2343,9 +2355,34 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     return CG_OK;
 }
 
+// ---------------------------------------------------------------- solid velocity
+__global__ void k_solid_velocity(int64_t n, int ncomp, const double *__restrict__ eps,
+                                 const double *__restrict__ mom, double eps_min,
+                                 double *__restrict__ out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double e = eps[k];
+        const bool solid = e > eps_min;
+        for (int c = 0; c < ncomp; ++c)
+            out[(int64_t)c * n + k] = solid ? __ddiv_rn(mom[(int64_t)c * n + k], e) : 0.0;
+    }
+}
+
 }  // namespace
 
 // ============================================================================ host side
+cg_status solid_velocity_run(int64_t n, int ncomp, const double *eps, const double *mom,
+                             double eps_min, double *u_out, cudaStream_t st) {
+    if (n > 0) {
+        CGK_LAUNCH("solid_velocity", (double)n * (8 + 16.0 * ncomp), st,
+                   k_solid_velocity<<<stencil_grid(n), kThreads, 0, st>>>(n, ncomp, eps, mom,
+                                                                         eps_min, u_out));
+        CGK_CUDA(cudaGetLastError());
+    }
+    CGK_CUDA(cudaStreamSynchronize(st));
+    return CG_OK;
+}
+
 cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host, cudaStream_t st) {
     int n = (int)m->ncells;
     int G = stencil_grid(n);
@@ -2371,7 +2408,7 @@ cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host,
 static cg_status diffuse_fp64(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
                               cg_report *rep, cudaStream_t st) {
     const int n = (int)m->ncells;
-    Geo g{m->nx, m->ny, m->nz, m->nx * m->ny, n};
+    Geo g{m->nx, m->ny, m->nz, m->nx * m->ny, n, m->per};
     const double dtau = T / p->nsteps;
     const double c = dtau / (m->dx * m->dx);
     const double ce = p->scheme == CG_SCHEME_CRANK_NICOLSON ? 0.5 * c : c;
@@ -2445,7 +2482,7 @@ static cg_status diffuse_fp64(cg_mesh *m, int nf, double *cells, const cg_params
 static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
                                   cg_report *rep, cudaStream_t st) {
     const int n = (int)m->ncells;
-    Geo g{m->nx, m->ny, m->nz, m->nx * m->ny, n};
+    Geo g{m->nx, m->ny, m->nz, m->nx * m->ny, n, m->per};
     const double dtau = T / p->nsteps;
     const double c = dtau / (m->dx * m->dx);
     if (c > 1.0 / 6.0 + 1e-15)
@@ -2454,7 +2491,7 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
     const Sweep sw = make_sweep(g, nf);
     const dim3 blk(TX, TY);
     const bool df = (p->precision == CG_PREC_FP32_DF_REFINE || p->precision == CG_PREC_BF16_DF_REFINE) &&
-                    m->nx % 2 == 0;
+                    m->nx % 2 == 0 && m->per == 0;
     if (df) {
         // double-float steps (FP64-class accuracy on the FP32 units), two cells per thread
         CGK_TRY(m->ws_diffuse.ensure(2 * vec));
@@ -2512,7 +2549,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     constexpr bool kDF = std::is_same<XT, DF>::value;
     static_assert(sizeof(XT) == 8, "iterate types are 8 bytes");
     const int n = (int)m->ncells;
-    Geo g{m->nx, m->ny, m->nz, m->nx * m->ny, n};
+    Geo g{m->nx, m->ny, m->nz, m->nx * m->ny, n, m->per};
     const bool cn = p->scheme == CG_SCHEME_CRANK_NICOLSON;
     const double dtau = T / p->nsteps;
     const double c = dtau / (m->dx * m->dx);
@@ -2525,11 +2562,12 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     const Coef32 cf32 = coef32(ce);
     const CoefDF cfdf = coefdf(c, ce);
 
-    // spectrum of A = I - ce L: [1, lmax]
+    // spectrum of A = I - ce L: [1, lmax] (a periodic axis of even length reaches 4 ce)
     const int dims[3] = {m->nx, m->ny, m->nz};
     double lmax = 1.0;
     for (int a = 0; a < 3; ++a) {
         double sv = std::sin(M_PI * (dims[a] - 1) / (2.0 * dims[a]));
+        if (((m->per >> a) & 1) && dims[a] % 2 == 0) sv = 1.0;
         lmax += 4.0 * ce * sv * sv;
     }
     const double theta = 0.5 * (lmax + 1.0), delta = 0.5 * (lmax - 1.0);
@@ -2550,7 +2588,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
     // the resident inner solve (whole mesh in shared memory) where it fits; its flags and
     // faces follow the vectors
-    const ResidentPlan rp = persistent ? ResidentPlan{} : plan_resident<TS>(g, nf, m_it);
+    const ResidentPlan rp = (persistent || m->per) ? ResidentPlan{} : plan_resident<TS>(g, nf, m_it);
     CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 5 * vts + (rp.ok ? rp.ws_bytes : 0)));
     char *wb = m->ws_diffuse.as<char>();
     char *rws = wb + 4 * v64 + 5 * vts;
@@ -2576,6 +2614,9 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
 
     int cheb_code = p->sweep_shape;
     bool resident = false;
+    if (m->per && cheb_code > 0)
+        return fail(CG_EINVAL, "sweep_shape %d: with periodic axes only the z-marching sweeps "
+                    "(sweep_shape < 0, or 0 for autotuning) apply", cheb_code);
     if (cheb_code == kResidentCode) {
         if (!rp.ok)
             return fail(CG_EINVAL, "sweep_shape %d needs one field, nx %% 4 == 0, at most %d inner "
