@@ -80,6 +80,12 @@ def _load():
         lib.orc_solid_velocity.restype = None
         lib.orc_solid_velocity.argtypes = [ctypes.c_int64, ctypes.c_int, _f64p, _f64p,
                                            ctypes.c_double, _f64p]
+        lib.orc_hex_build.restype = ctypes.c_int64
+        lib.orc_hex_build.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _f64p,
+                                      _f64p, _f64p, _f64p, _i64p, _i32p, _f64p]
+        lib.orc_locate_hex.restype = ctypes.c_int64
+        lib.orc_locate_hex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _f64p,
+                                       _f64p, ctypes.c_int64, _f64p, _i32p]
         lib.orc_tet_build.restype = ctypes.c_int64
         lib.orc_tet_build.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p, _f64p, _f64p,
                                       _i64p, _i32p, _f64p]
@@ -271,3 +277,35 @@ def solid_velocity(eps, mom, eps_min=0.0):
     _load().orc_solid_velocity(eps.shape[0], mom.shape[0], _p(eps, ctypes.c_double),
                                _p(mom, ctypes.c_double), float(eps_min), _p(out, ctypes.c_double))
     return out
+
+
+def hex_build(xf, yf, zf, D=None):
+    """Cell volumes and the CSR two-point-flux Laplacian of a stretched Cartesian mesh
+    with face coordinates xf, yf, zf and a cell diffusion constant D (default 1; the face
+    value is the harmonic mean).  Returns (vc, rowptr, col, val)."""
+    xf, yf, zf = _f64(xf), _f64(yf), _f64(zf)
+    nx, ny, nz = len(xf) - 1, len(yf) - 1, len(zf) - 1
+    n = nx * ny * nz
+    d = None if D is None else _f64(D)
+    vc = np.empty(n)
+    rowptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(7 * n, dtype=np.int32)
+    val = np.empty(7 * n)
+    nnz = _load().orc_hex_build(nx, ny, nz, _p(xf, ctypes.c_double), _p(yf, ctypes.c_double),
+                                _p(zf, ctypes.c_double),
+                                None if d is None else _p(d, ctypes.c_double),
+                                _p(vc, ctypes.c_double), _p(rowptr, ctypes.c_int64),
+                                _p(col, ctypes.c_int32), _p(val, ctypes.c_double))
+    return vc, rowptr, col[:nnz].copy(), val[:nnz].copy()
+
+
+def locate_hex(xf, yf, zf, pos):
+    """Cell of each point on a stretched Cartesian mesh (-1 outside); returns (cell, nout)."""
+    xf, yf, zf = _f64(xf), _f64(yf), _f64(zf)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = pos.shape[1]
+    cell = np.empty(n, dtype=np.int32)
+    nout = _load().orc_locate_hex(len(xf) - 1, len(yf) - 1, len(zf) - 1, _p(xf, ctypes.c_double),
+                                  _p(yf, ctypes.c_double), _p(zf, ctypes.c_double), n,
+                                  _p(pos, ctypes.c_double), _p(cell, ctypes.c_int32))
+    return cell, int(nout)

@@ -677,3 +677,96 @@ void orc_kernel_sum(int64_t ns, const double *src /*[ns][3]*/, const double *w, 
         out[k] = s;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* A stretched Cartesian mesh with a spatially varying diffusion constant      */
+/* (stretched meshes: Section 4.4; a local diffusion constant that can fall    */
+/* to zero to degenerate to PCM there, with conservation kept: Section 5.2).   */
+/* Cell (ix, iy, iz), k = (iz ny + iy) nx + ix, spans [xf[ix], xf[ix+1]] x ... */
+/* Finite volumes with a two-point flux: across the face between cells a and b  */
+/* T_f = D_f |A_f| / d_f, |A_f| the face area, d_f the distance between the     */
+/* two cell centres, D_f = 2 D_a D_b / (D_a + D_b) (harmonic mean, 0 if either  */
+/* is 0); walls carry no flux.  (L u)_k = sum_f T_f (u_l - u_k), M = diag(V_c),  */
+/* the same CSR layout as orc_tet_build (diagonal entry first in each row).     */
+/* ------------------------------------------------------------------------- */
+
+static double face_d(double da, double db)
+{
+    return (da > 0.0 && db > 0.0) ? 2.0 * da * db / (da + db) : 0.0;
+}
+
+int64_t orc_hex_build(int nx, int ny, int nz, const double *xf, const double *yf,
+                      const double *zf, const double *D, double *vc, int64_t *rowptr,
+                      int32_t *col, double *val)
+{
+    const int n3[3] = {nx, ny, nz};
+    const double *f[3] = {xf, yf, zf};
+    int64_t nnz = 0;
+    rowptr[0] = 0;
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                const int64_t k = ((int64_t)iz * ny + iy) * nx + ix;
+                const int id[3] = {ix, iy, iz};
+                double w[3], c[3];
+                for (int a = 0; a < 3; ++a) {
+                    w[a] = f[a][id[a] + 1] - f[a][id[a]];
+                    c[a] = 0.5 * (f[a][id[a]] + f[a][id[a] + 1]);
+                }
+                vc[k] = w[0] * w[1] * w[2];
+                const double dk = D ? D[k] : 1.0;
+                const int64_t dstart = nnz++;   /* diagonal first */
+                col[dstart] = (int32_t)k;
+                double diag = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int s = -1; s <= 1; s += 2) {
+                        const int j = id[a] + s;
+                        if (j < 0 || j >= n3[a]) continue;
+                        int nid[3] = {ix, iy, iz};
+                        nid[a] = j;
+                        const int64_t l = ((int64_t)nid[2] * ny + nid[1]) * nx + nid[0];
+                        const double cl = 0.5 * (f[a][j] + f[a][j + 1]);
+                        const double area = w[(a + 1) % 3] * w[(a + 2) % 3];
+                        const double t = face_d(dk, D ? D[l] : 1.0) * area / fabs(cl - c[a]);
+                        col[nnz] = (int32_t)l;
+                        val[nnz] = t;
+                        ++nnz;
+                        diag -= t;
+                    }
+                val[dstart] = diag;
+                rowptr[k + 1] = nnz;
+            }
+    return nnz;
+}
+
+/* Cell of each point on the stretched mesh: per axis the i with f[i] <= x < f[i+1]
+ * (x = f[n] is in the last cell); outside the closed box or NaN gives -1.  Returns
+ * the number outside. */
+int64_t orc_locate_hex(int nx, int ny, int nz, const double *xf, const double *yf,
+                       const double *zf, int64_t n, const double *pos, int32_t *cell)
+{
+    const int n3[3] = {nx, ny, nz};
+    const double *f[3] = {xf, yf, zf};
+    int64_t nout = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        int id[3];
+        int ok = 1;
+        for (int a = 0; a < 3 && ok; ++a) {
+            const double x = pos[(int64_t)a * n + p];
+            if (!(x >= f[a][0] && x <= f[a][n3[a]])) {
+                ok = 0;
+                break;
+            }
+            int i = 0;   /* the last face not above x, by a linear scan */
+            while (i + 1 < n3[a] && f[a][i + 1] <= x) ++i;
+            id[a] = i;
+        }
+        if (!ok) {
+            cell[p] = -1;
+            ++nout;
+        } else {
+            cell[p] = (int32_t)(((int64_t)id[2] * ny + id[1]) * nx + id[0]);
+        }
+    }
+    return nout;
+}

@@ -537,3 +537,75 @@ def test_solid_velocity_of_uniform_motion(orc):
     raw = orc.solid_velocity(eps[0], eps[1:], 0.0)      # before smoothing: per particle cell
     occ = eps[0] > 0
     assert np.max(np.abs(raw[:, occ] - U0[:, None])) <= 1e-14 * np.abs(U0).max()
+
+
+def _stretched_faces(n, ratio, length=1.0):
+    w = ratio ** np.arange(n)
+    f = np.concatenate([[0.0], np.cumsum(w)])
+    return f * (length / f[-1])
+
+
+def test_hex_operator_uniform_equals_structured(orc):
+    """A stretched mesh with equal spacing and D = 1 is the uniform mesh: the CSR oracle
+    on it reproduces the structured oracle (both implicit schemes and explicit)."""
+    dims = (7, 5, 4)
+    dx = 0.125
+    xf, yf, zf = (np.arange(n + 1) * dx for n in dims)
+    vc, rp, col, val = orc.hex_build(xf, yf, zf)
+    assert np.allclose(vc, dx ** 3, rtol=0, atol=1e-18)
+    rng = np.random.default_rng(80)
+    u0 = rng.random(int(np.prod(dims)))
+    for scheme, T in ((0, 0.01), (1, 0.01), (2, 0.1 * dx * dx * 6)):
+        a, _ = orc.diffuse_structured(u0, dims, dx, T, 6, scheme=scheme, tol=1e-15)
+        b, _ = orc.diffuse_csr(u0, vc, rp, col, val, T, 6, scheme=scheme, tol=1e-15)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_hex_operator_varying_diffusivity(orc):
+    """Stretched spacing (ratio 1.04, as the paper's stretched mesh) and a region with
+    D = 0: the operator is symmetric with L 1 = 0 and total volume equal to the box; the
+    D = 0 cells keep their deposited values exactly (PCM there), and mass is conserved."""
+    xf, yf, zf = _stretched_faces(20, 1.04), _stretched_faces(12, 1 / 1.04, 0.6), _stretched_faces(6, 1.0, 0.3)
+    nx, ny, nz = 20, 12, 6
+    D = np.ones(nx * ny * nz)
+    frozen = np.zeros((nz, ny, nx), bool)
+    frozen[:, 3:7, 5:11] = True
+    D[frozen.ravel()] = 0.0
+    D[~frozen.ravel()] = 0.5 + np.random.default_rng(81).random((~frozen).sum())
+    vc, rp, col, val = orc.hex_build(xf, yf, zf, D)
+    assert abs(vc.sum() - 1.0 * 0.6 * 0.3) <= 1e-14
+    n = nx * ny * nz
+    A = scipy.sparse.csr_matrix((val, col, rp), shape=(n, n))
+    assert abs(A - A.T).max() <= 1e-15 * abs(A).max()
+    assert np.max(np.abs(A @ np.ones(n))) <= 1e-12 * abs(A).max()
+    u0 = np.random.default_rng(82).random(n)
+    u, _ = orc.diffuse_csr(u0, vc, rp, col, val, 0.002, 10, tol=1e-15)
+    assert np.array_equal(u[frozen.ravel()], u0[frozen.ravel()])
+    assert abs((vc * u).sum() - (vc * u0).sum()) <= 1e-13 * (vc * u0).sum()
+    assert u.min() >= 0.0
+
+
+def test_locate_hex_against_searchsorted(orc):
+    xf, yf, zf = _stretched_faces(17, 1.05), _stretched_faces(9, 0.97), _stretched_faces(5, 1.0)
+    rng = np.random.default_rng(83)
+    pos = rng.random((3, 5000)) * np.array([[1.0], [1.0], [1.0]])
+    pos[0, :100] = xf[rng.integers(0, 18, 100)]        # exactly on faces
+    pos[1, 100:200] = yf[rng.integers(0, 10, 100)]
+    pos[:, 200] = (1.5, 0.5, 0.5)
+    pos[:, 201] = (0.5, np.nan, 0.5)
+    cell, nout = orc.locate_hex(xf, yf, zf, pos)
+    ids = []
+    for a, f in enumerate((xf, yf, zf)):
+        i = np.searchsorted(f, pos[a], side="right") - 1
+        ids.append(np.clip(i, 0, len(f) - 2))
+    inside = np.all([(pos[a] >= f[0]) & (pos[a] <= f[-1]) for a, f in enumerate((xf, yf, zf))], axis=0)
+    ref = np.where(inside, (ids[2] * 9 + ids[1]) * 17 + ids[0], -1)
+    assert nout == 2
+    assert np.array_equal(cell, ref)
+    # power-of-two spacing: the same cells as the uniform-mesh locate
+    dx = 1.0 / 16
+    f = np.arange(17) * dx
+    p2 = rng.random((3, 2000))
+    a, _ = orc.locate_hex(f, f, f, p2)
+    b, _ = orc.locate_structured((16, 16, 16), (0, 0, 0), dx, p2)
+    assert np.array_equal(a, b)
