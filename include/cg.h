@@ -94,9 +94,27 @@ cg_status cg_mesh_cell_volumes(const cg_mesh *mesh, double *out_host);
  * or a tet mesh). */
 cg_status cg_mesh_set_periodic(cg_mesh *mesh, int px, int py, int pz);
 
-/* Copies the tet mesh's Laplacian in CSR form to host arrays: rowptr_host[ncells+1],
- * col_host[nnz], val_host[nnz]; *nnz_out receives nnz.  Pass NULL arrays to query
- * nnz only.  CG_EINVAL for a structured mesh. */
+/* Stretched Cartesian mesh with a spatially varying diffusion constant (stretched
+ * meshes: Section 4.4; a local diffusion constant that may be set very small, down to
+ * 0, to degenerate to PCM there with conservation kept: Section 5.2).  Cell
+ * (ix, iy, iz), k = (iz ny + iy) nx + ix, spans [xf[ix], xf[ix+1]] x [yf[iy], yf[iy+1]]
+ * x [zf[iz], zf[iz+1]] (host arrays of nx+1, ny+1, nz+1 strictly increasing face
+ * coordinates); diffusivity (host [ncells], may be NULL for 1) is the cell's D >= 0.
+ * The operator is the two-point-flux finite-volume Laplacian T_f = D_f |A_f| / d_f
+ * between face neighbours (|A_f| the face area, d_f the distance between the cell
+ * centres, D_f the harmonic mean of the two cells' D, 0 if either is 0), M = diag(V_c),
+ * zero-flux walls; it is solved like the tet operator (cg_diffuse on this mesh uses
+ * the same solvers and precision modes).  A point is in the cell whose half-open face
+ * interval holds it on every axis (the upper boundary face belongs to the last cell).
+ * Errors: CG_EINVAL (NULL, dimensions, non-increasing or non-finite faces, a negative
+ * or non-finite D), CG_ENOMEM, CG_ECUDA. */
+cg_status cg_create_mesh_hex(int nx, int ny, int nz, const double *xf, const double *yf,
+                             const double *zf, const double *diffusivity, cg_mesh **out);
+
+/* Copies the mesh's Laplacian (tet or stretched hex mesh) in CSR form to host arrays:
+ * rowptr_host[ncells+1], col_host[nnz], val_host[nnz] (ascending columns, diagonal
+ * included); *nnz_out receives nnz.  Pass NULL arrays to query nnz only.  CG_EINVAL
+ * for a uniform structured mesh. */
 cg_status cg_mesh_tet_operator(const cg_mesh *mesh, int64_t *rowptr_host, int32_t *col_host,
                                double *val_host, int64_t *nnz_out);
 

@@ -108,6 +108,7 @@ def load_library(path: str | None = None):
                                            P(ctypes.c_int), vp]),
         "cg_launch_count_reset": (None, []),
         "cg_mesh_set_periodic": (i32, [vp, i32, i32, i32]),
+        "cg_create_mesh_hex": (i32, [i32, i32, i32, vp, vp, vp, vp, P(vp)]),
         "cg_solid_velocity": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
     }
     for name, (res, args) in sigs.items():
@@ -126,7 +127,7 @@ def exported_symbols():
             "cg_coarse_grain_host", "cg_profile_enable", "cg_profile_reset", "cg_profile_count",
             "cg_profile_get", "cg_launch_count", "cg_launch_count_reset",
             "cg_deposit_fixed_noalloc", "cg_diffuse_batched", "cg_coarse_grain_batched",
-            "cg_mesh_set_periodic", "cg_solid_velocity"]
+            "cg_mesh_set_periodic", "cg_solid_velocity", "cg_create_mesh_hex"]
 
 
 def _check(status: int, where: str):
@@ -224,6 +225,29 @@ class StructuredMesh(_MeshBase):
     def set_periodic(self, px, py, pz):
         _check(load_library().cg_mesh_set_periodic(self.handle, int(bool(px)), int(bool(py)),
                                                    int(bool(pz))), "cg_mesh_set_periodic")
+
+
+class HexMesh(_MeshBase):
+    """Stretched Cartesian mesh with a cell diffusion constant (cg_create_mesh_hex):
+    face coordinates xf, yf, zf (strictly increasing), diffusivity [ncells] or None."""
+
+    def __init__(self, xf, yf, zf, diffusivity=None):
+        import numpy as np
+        lib = load_library()
+        self.faces = tuple(np.ascontiguousarray(f, dtype=np.float64) for f in (xf, yf, zf))
+        self.dims = tuple(len(f) - 1 for f in self.faces)
+        self.diffusivity = None if diffusivity is None else np.ascontiguousarray(diffusivity,
+                                                                                 dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.cg_create_mesh_hex(self.dims[0], self.dims[1], self.dims[2],
+                                      self.faces[0].ctypes.data, self.faces[1].ctypes.data,
+                                      self.faces[2].ctypes.data,
+                                      None if self.diffusivity is None else self.diffusivity.ctypes.data,
+                                      ctypes.byref(h)), "cg_create_mesh_hex")
+        self._h = h
+
+    def operator(self):
+        return TetMesh.operator(self)
 
 
 class TetMesh(_MeshBase):

@@ -375,6 +375,44 @@ cg_status cg_create_mesh_tet(int64_t nverts, const double *xyz_host, int64_t nte
     return CG_OK;
 }
 
+cg_status cg_create_mesh_hex(int nx, int ny, int nz, const double *xf, const double *yf,
+                             const double *zf, const double *diffusivity, cg_mesh **out) {
+    if (!out) return fail(CG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!xf || !yf || !zf) return fail(CG_EINVAL, "face coordinate arrays are NULL");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(CG_EINVAL, "mesh dimensions must be >= 1");
+    if ((int64_t)nx * ny * nz >= ((int64_t)1 << 31) / 7)
+        return fail(CG_EINVAL, "mesh too large: nx*ny*nz must be < 2^31 / 7");
+    const int n3[3] = {nx, ny, nz};
+    const double *f[3] = {xf, yf, zf};
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i <= n3[a]; ++i) {
+            if (!std::isfinite(f[a][i])) return fail(CG_EINVAL, "face coordinates must be finite");
+            if (i > 0 && !(f[a][i] > f[a][i - 1]))
+                return fail(CG_EINVAL, "face coordinates must increase strictly (axis %d, face %d)", a, i);
+        }
+    const int64_t n = (int64_t)nx * ny * nz;
+    if (diffusivity)
+        for (int64_t k = 0; k < n; ++k)
+            if (!(diffusivity[k] >= 0.0) || !std::isfinite(diffusivity[k]))
+                return fail(CG_EINVAL, "diffusivity must be finite and >= 0 (cell %lld)", (long long)k);
+    cg_mesh *m = new (std::nothrow) cg_mesh();
+    if (!m) return fail(CG_ENOMEM, "host allocation failed");
+    m->kind = MESH_HEX;
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    m->ncells = n;
+    cg_status s = hex_build(m, nx, ny, nz, xf, yf, zf, diffusivity);
+    if (s != CG_OK) {
+        tet_release(m);
+        delete m;
+        return s;
+    }
+    *out = m;
+    return CG_OK;
+}
+
 cg_status cg_destroy_mesh(cg_mesh *m) {
     if (!m) return CG_OK;
     m->ws_locate.release();
@@ -387,7 +425,7 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     for (auto &e : m->graphs) graph_release(e);
     m->graphs.clear();
     if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
-    if (m->kind == MESH_TET) tet_release(m);
+    if (m->kind != MESH_STRUCTURED) tet_release(m);
     delete m;
     return CG_OK;
 }
@@ -437,7 +475,7 @@ cg_status cg_mesh_cell_volumes(const cg_mesh *m, double *out_host) {
 cg_status cg_mesh_tet_operator(const cg_mesh *m, int64_t *rowptr_host, int32_t *col_host,
                                double *val_host, int64_t *nnz_out) {
     if (!m) return fail(CG_EINVAL, "mesh is NULL");
-    if (m->kind != MESH_TET) return fail(CG_EINVAL, "not a tet mesh");
+    if (m->kind == MESH_STRUCTURED) return fail(CG_EINVAL, "a uniform mesh has no stored operator");
     if (nnz_out) *nnz_out = (int64_t)m->h_col.size();
     if (rowptr_host)
         for (int64_t k = 0; k <= m->ncells; ++k) rowptr_host[k] = m->h_rowptr[k];

@@ -512,8 +512,8 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
                       double *out, const cg_params *p, cg_report *rep, cudaStream_t st) {
     const int64_t ncells = m->ncells;
     const int mode = p->deposit_mode;
-    const double *vc = m->kind == MESH_TET ? m->tet.vc : nullptr;
-    const double vcu = m->kind == MESH_TET ? 0.0 : (m->dx * m->dx) * m->dx;
+    const double *vc = m->kind != MESH_STRUCTURED ? m->tet.vc : nullptr;
+    const double vcu = m->kind != MESH_STRUCTURED ? 0.0 : (m->dx * m->dx) * m->dx;
 
     // workspace: cell[n] (int32); the ordered mode also counts particles per cell
     // (ncells + 1 counters, the last one staying 0 for the exclusive scan)

@@ -104,7 +104,7 @@ struct RoundsEntry {
 };
 
 // ----------------------------------------------------------------------------- meshes
-enum MeshKind { MESH_STRUCTURED = 0, MESH_TET = 1 };
+enum MeshKind { MESH_STRUCTURED = 0, MESH_TET = 1, MESH_HEX = 2 };   // HEX: stretched Cartesian
 
 struct TetDevice {
     // operator in ELL-4 form (slot s = the face opposite local vertex s); a boundary
@@ -115,6 +115,10 @@ struct TetDevice {
     double *offv = nullptr;      // [4][ncells] T_f across face s (FP64)
     float *offv32 = nullptr;     // [4][ncells] the same in FP32
     double max_rate = 0.0;       // max_k (-L_kk / V_k): explicit Euler needs dtau <= 1/max_rate
+    int ns = 4;                  // neighbour slots per cell: 4 (tets) or 6 (stretched hex)
+    // point location on a stretched Cartesian mesh: face coordinates x | y | z
+    double *faces = nullptr;
+    int hn[3] = {0, 0, 0};
     // point location
     double *xyz = nullptr;       // [nverts][3]
     int32_t *tv = nullptr;       // [ntets][4]
@@ -246,6 +250,11 @@ cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host,
 // Tet mesh construction (host C++), fills m->tet and the host copies.
 cg_status tet_build(cg_mesh *m, int64_t nverts, const double *xyz, int64_t ntets,
                     const int32_t *tv);
+// A stretched Cartesian mesh (host C++): face coordinates xf[nx+1], yf[ny+1], zf[nz+1]
+// (strictly increasing) and a cell diffusion constant D[ncells] (NULL: 1), as the same
+// finite-volume operator with six neighbour slots; fills m->tet and the host copies.
+cg_status hex_build(cg_mesh *m, int nx, int ny, int nz, const double *xf, const double *yf,
+                    const double *zf, const double *D);
 void tet_release(cg_mesh *m);
 
 // Exclusive scan of n uint32 values (in and out may alias).  tmp needs

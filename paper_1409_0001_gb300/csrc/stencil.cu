@@ -2393,7 +2393,7 @@ cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host,
     double *out = (double *)(base + align_up((size_t)nf * G * 8));
     unsigned int *tickets = (unsigned int *)(out + 64);
     CGK_CUDA(cudaMemsetAsync(tickets, 0, 64 * 4, st));
-    const double *vc = m->kind == MESH_TET ? m->tet.vc : nullptr;
+    const double *vc = m->kind != MESH_STRUCTURED ? m->tet.vc : nullptr;
     double vcu = (m->dx * m->dx) * m->dx;
     CGK_LAUNCH("mass", (double)n * nf * 8, st,
                k_mass<<<dim3(G, nf), kThreads, 0, st>>>(n, cells, vc, vcu, partials, tickets, out));

@@ -247,6 +247,63 @@ __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevic
     }
 }
 
+// Host cell of each particle on a stretched Cartesian mesh: per axis the largest i with
+// f[i] <= x by bisection over the face coordinates (x = f[n] is in the last cell);
+// outside the closed box, or NaN, is -1.  Doubles are compared exactly as integer keys.
+__global__ void k_hex_locate(int64_t n, const double *__restrict__ pos, TetDevice t, int nf,
+                             const double *__restrict__ w, int32_t *__restrict__ cell,
+                             uint32_t *__restrict__ counts, uint32_t *__restrict__ ranks,
+                             unsigned long long *__restrict__ bad) {
+    unsigned long long n_out = 0, n_nonfinite = 0;
+    uint32_t most = 0;
+    const double *fa[3] = {t.faces, t.faces + t.hn[0] + 1, t.faces + t.hn[0] + t.hn[1] + 2};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int f = 0; f < nf; ++f)
+            if (((__double2hiint(w[(int64_t)f * n + i]) >> 20) & 0x7ff) == 0x7ff) ++n_nonfinite;
+        int id[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const unsigned long long kx = tkey(pos[(int64_t)a * n + i]);
+            const double *f = fa[a];
+            const int na = t.hn[a];
+            if (!(kx >= tkey(f[0]) && kx <= tkey(f[na]))) {
+                ok = false;
+                id[a] = 0;
+                continue;
+            }
+            int lo = 0, hi = na - 1;   // invariant: f[lo] <= x, answer in [lo, hi]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tkey(f[mid]) <= kx) lo = mid;
+                else hi = mid - 1;
+            }
+            id[a] = lo;
+        }
+        int32_t found = -1;
+        if (ok) found = (int32_t)(((int64_t)id[2] * t.hn[1] + id[1]) * t.hn[0] + id[0]);
+        cell[i] = found;
+        if (found < 0) {
+            ++n_out;
+        } else if (counts) {
+            const uint32_t r = atomicAdd(&counts[found], 1u);
+            if (ranks) ranks[i] = r;
+            most = max(most, r + 1u);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_out += __shfl_down_sync(0xffffffffu, n_out, o);
+        n_nonfinite += __shfl_down_sync(0xffffffffu, n_nonfinite, o);
+        most = max(most, __shfl_down_sync(0xffffffffu, most, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_out) atomicAdd(&bad[0], n_out);
+        if (n_nonfinite) atomicAdd(&bad[1], n_nonfinite);
+        if (most) atomicMax(&bad[2], (unsigned long long)most);
+    }
+}
+
 // ============================================================================ solver kernels
 template <class TS> __device__ __forceinline__ float ldf(const TS *p, int64_t i);
 template <> __device__ __forceinline__ float ldf<float>(const float *p, int64_t i) { return p[i]; }
@@ -268,7 +325,9 @@ struct Op {          // the operator seen by the kernels
     double dtau;     // full dtau (for the residual of the first pass)
     const float *adiag32 = nullptr;    // FP32 diagonal of A, V_c - dte L_kk (inner solves)
     const float *iadiag32 = nullptr;   // its reciprocal (the Jacobi preconditioner)
+    int ns = 4;                        // neighbour slots per cell (4 tets, 6 stretched hex)
 };
+constexpr int kMaxSlots = 6;
 
 // The FP32 diagonal of A = M - dte L and its reciprocal, for the inner solves.
 __global__ void k_tdiag32(int n, const double *__restrict__ vc, const double *__restrict__ diagL,
@@ -285,7 +344,8 @@ template <class T, class Load>
 __device__ __forceinline__ T lap_row(const Op &o, int k, T uk, Load load) {
     T s = (T)o.diagL[k] * uk;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kMaxSlots; ++q) {
+        if (q >= o.ns) break;
         const size_t e = (size_t)q * o.n + k;
         s += (T)o.offv[e] * load(o.offc[e]);
     }
@@ -514,7 +574,8 @@ __global__ void k_tin_pass1(Op o, const TS *__restrict__ z_all, const TS *__rest
         float pk = ldf(z, k) + beta * ldf(pin, k);
         float off_sum = 0.f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kMaxSlots; ++q) {
+            if (q >= o.ns) break;
             const size_t e = (size_t)q * o.n + k;
             const int l = o.offc[e];
             off_sum += o.offv32[e] * (ldf(z, l) + beta * ldf(pin, l));
@@ -587,7 +648,7 @@ __global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__rest
 void tet_release(cg_mesh *m) {
     TetDevice &t = m->tet;
     void *ptrs[] = {t.vc, t.diagL, t.offc, t.offv, t.offv32, t.xyz, t.tv, t.box, t.bucket_start,
-                    t.bucket_tets};
+                    t.bucket_tets, t.faces};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     t = TetDevice();
@@ -792,12 +853,96 @@ cg_status tet_build(cg_mesh *m, int64_t nv, const double *xyz, int64_t nt, const
     return CG_OK;
 }
 
+// ============================================================================ host: stretched hex
+// The operator of a stretched Cartesian mesh with the same arithmetic, in the same order,
+// as its finite-volume definition: cell widths w = f[i+1] - f[i], centres (f[i] + f[i+1])/2,
+// T_f = D_f |A_f| / |c_l - c_k| with D_f the harmonic mean of the two cells' D (0 if either
+// is 0).  Slots 0..5 = x-, x+, y-, y+, z-, z+; a wall slot points at the cell itself with
+// a zero transmissibility.
+static double hex_face_d(double a, double b) { return (a > 0.0 && b > 0.0) ? 2.0 * a * b / (a + b) : 0.0; }
+
+cg_status hex_build(cg_mesh *m, int nx, int ny, int nz, const double *xf, const double *yf,
+                    const double *zf, const double *D) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int n3[3] = {nx, ny, nz};
+    const double *f[3] = {xf, yf, zf};
+    std::vector<double> vc((size_t)n), diag((size_t)n, 0.0), offv(6 * (size_t)n, 0.0);
+    std::vector<int32_t> offc(6 * (size_t)n);
+    m->h_rowptr.assign((size_t)n + 1, 0);
+    m->h_col.clear();
+    m->h_val.clear();
+    m->h_col.reserve(7 * (size_t)n);
+    m->h_val.reserve(7 * (size_t)n);
+    double max_rate = 0.0;
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                const int64_t k = ((int64_t)iz * ny + iy) * nx + ix;
+                const int id[3] = {ix, iy, iz};
+                double w[3], c[3];
+                for (int a = 0; a < 3; ++a) {
+                    w[a] = f[a][id[a] + 1] - f[a][id[a]];
+                    c[a] = 0.5 * (f[a][id[a]] + f[a][id[a] + 1]);
+                }
+                vc[k] = w[0] * w[1] * w[2];
+                const double dk = D ? D[k] : 1.0;
+                std::pair<int32_t, double> e[7];
+                int ne = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int sgn = 0; sgn < 2; ++sgn) {
+                        const int slot = 2 * a + sgn;
+                        const int j = id[a] + (sgn ? 1 : -1);
+                        offc[(size_t)slot * n + k] = (int32_t)k;
+                        if (j < 0 || j >= n3[a]) continue;
+                        int nid[3] = {ix, iy, iz};
+                        nid[a] = j;
+                        const int64_t l = ((int64_t)nid[2] * ny + nid[1]) * nx + nid[0];
+                        const double cl = 0.5 * (f[a][j] + f[a][j + 1]);
+                        const double area = w[(a + 1) % 3] * w[(a + 2) % 3];
+                        const double t = hex_face_d(dk, D ? D[l] : 1.0) * area / std::fabs(cl - c[a]);
+                        offc[(size_t)slot * n + k] = (int32_t)l;
+                        offv[(size_t)slot * n + k] = t;
+                        diag[k] -= t;
+                        e[ne++] = {(int32_t)l, t};
+                    }
+                e[ne++] = {(int32_t)k, diag[k]};
+                std::sort(e, e + ne);
+                for (int q = 0; q < ne; ++q) {
+                    m->h_col.push_back(e[q].first);
+                    m->h_val.push_back(e[q].second);
+                }
+                m->h_rowptr[k + 1] = (int32_t)m->h_col.size();
+                max_rate = std::max(max_rate, -diag[k] / vc[k]);
+            }
+    m->h_vc = vc;
+    std::vector<float> offv32(offv.size());
+    for (size_t i = 0; i < offv.size(); ++i) offv32[i] = (float)offv[i];
+    std::vector<double> faces;
+    for (int a = 0; a < 3; ++a) faces.insert(faces.end(), f[a], f[a] + n3[a] + 1);
+    TetDevice &td = m->tet;
+    td.ns = 6;
+    td.max_rate = max_rate;
+    for (int a = 0; a < 3; ++a) td.hn[a] = n3[a];
+    CGK_TRY(upload(&td.vc, vc.data(), vc.size()));
+    CGK_TRY(upload(&td.diagL, diag.data(), diag.size()));
+    CGK_TRY(upload(&td.offc, offc.data(), offc.size()));
+    CGK_TRY(upload(&td.offv, offv.data(), offv.size()));
+    CGK_TRY(upload(&td.offv32, offv32.data(), offv32.size()));
+    CGK_TRY(upload(&td.faces, faces.data(), faces.size()));
+    return CG_OK;
+}
+
 cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                             int32_t *cell_out, uint32_t *counts, uint32_t *ranks,
                             unsigned long long *bad, cudaStream_t st) {
-    CGK_LAUNCH("tet_locate", (double)n * (24 + 8 * nf + 4), st,
-               k_tet_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
-                                                            counts, ranks, bad));
+    if (m->kind == MESH_HEX)
+        CGK_LAUNCH("hex_locate", (double)n * (24 + 8 * nf + 4), st,
+                   k_hex_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
+                                                                counts, ranks, bad));
+    else
+        CGK_LAUNCH("tet_locate", (double)n * (24 + 8 * nf + 4), st,
+                   k_tet_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
+                                                                counts, ranks, bad));
     CGK_CUDA(cudaGetLastError());
     return CG_OK;
 }
@@ -813,11 +958,13 @@ static Op make_op(cg_mesh *m, double dte, double dtau) {
     o.offc = m->tet.offc;
     o.dte = dte;
     o.dtau = dtau;
+    o.ns = m->tet.ns;
     return o;
 }
 
-// bytes of one operator row: 4 ids + 4 T + diag + V_c, plus the gathered values
-static double row_bytes(int s) { return 4 * 4 + 4 * (s == 4 ? 4 : 8) + 16; }
+// bytes of one operator row: ns ids + ns T + diag + V_c, plus the gathered values
+static int g_row_slots = 4;   // set per call from the mesh (profiling byte counts only)
+static double row_bytes(int s) { return g_row_slots * 4 + g_row_slots * (s == 4 ? 4 : 8) + 16; }
 
 static cg_status tet_fp64(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
                           cg_report *rep, cudaStream_t st) {
@@ -1030,6 +1177,7 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
 
 cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p, cg_report *rep,
                           cudaStream_t st) {
+    g_row_slots = m->tet.ns;
     double T = p->bandwidth > 0.0 ? p->bandwidth * p->bandwidth / 4.0 : p->T;
     if (p->scheme == CG_SCHEME_EXPLICIT_EULER) return tet_explicit(m, nf, cells, p, T, rep, st);
     if (p->precision == CG_PREC_FP64) return tet_fp64(m, nf, cells, p, T, rep, st);
