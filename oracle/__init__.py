@@ -189,7 +189,7 @@ def deposit(cell, w, ncells, vc=None, vc_uniform=1.0, mode=0):
 def diffuse_structured(u, dims, dx, T, nsteps, scheme=0, tol=1e-14, max_iter=100000,
                        periodic=(False, False, False)):
     """Pseudo-time integration of Eq. (diffusion) on a uniform mesh with zero-flux walls
-    (or periodic axes where periodic[a] is set, Section 3.2.2).  u is [nf, ncells] (or
+    (or periodic axes where periodic[a] is set, Section 3.1).  u is [nf, ncells] (or
     [ncells]); returns (u(T), total CG iterations)."""
     nx, ny, nz = (int(d) for d in dims)
     per = sum(1 << a for a in range(3) if periodic[a])

@@ -154,7 +154,7 @@ void orc_deposit(int64_t n, const int32_t *cell, int nf, const double *w,
 /* The physical operator is L / dx^2.                                           */
 /* ------------------------------------------------------------------------- */
 
-/* An axis may instead be periodic (Section 3.2.2: periodic boundaries keep periodic
+/* An axis may instead be periodic (Section 3.1: periodic boundaries keep periodic
  * conditions): bit a of per set means the neighbour beyond the last cell along axis a
  * is the first one and the other way round (on an axis of one cell that is the cell
  * itself). */

@@ -1,4 +1,4 @@
-"""GPU parity of periodic axes (Section 3.2.2: periodic boundaries keep periodic
+"""GPU parity of periodic axes (Section 3.1: periodic boundaries keep periodic
 conditions) and of the solid velocity (diffused momentum over diffused solid fraction),
 against the FP64 oracle.
 

@@ -495,7 +495,7 @@ def _closed_form_mixed(u0, dims, c, nsteps, periodic, scheme=0):
 @pytest.mark.parametrize("periodic", [(True, True, True), (True, False, False), (False, True, True)])
 @pytest.mark.parametrize("scheme", [0, 1, 2])
 def test_periodic_diffusion_matches_closed_form(orc, periodic, scheme):
-    """Periodic axes (Section 3.2.2): the oracle against the exact DFT/DCT solution."""
+    """Periodic axes (Section 3.1): the oracle against the exact DFT/DCT solution."""
     dims = (9, 6, 5)
     rng = np.random.default_rng(60)
     u0 = rng.random(int(np.prod(dims)))
@@ -609,3 +609,30 @@ def test_locate_hex_against_searchsorted(orc):
     a, _ = orc.locate_hex(f, f, f, p2)
     b, _ = orc.locate_structured((16, 16, 16), (0, 0, 0), dx, p2)
     assert np.array_equal(a, b)
+
+
+def test_hex_operator_is_exact_on_linear_fields(orc):
+    """Two-point flux on a Cartesian stretched mesh with uniform D is consistent: for a
+    linear field u = a.x the flux through a face is D |A_f| a_axis, equal on both faces of
+    an interior cell along each axis, so (L u)_k = 0 in every interior cell; a wall cell
+    loses exactly the flux of its missing face (D |A_f| a_axis).  A wrong centre distance,
+    area or neighbour index breaks this at stretched spacing."""
+    xf, yf, zf = _stretched_faces(11, 1.07), _stretched_faces(8, 0.93, 0.7), _stretched_faces(6, 1.12, 0.4)
+    n3 = (11, 8, 6)
+    D0 = 2.5
+    vc, rp, col, val = orc.hex_build(xf, yf, zf, np.full(int(np.prod(n3)), D0))
+    n = len(vc)
+    A = scipy.sparse.csr_matrix((val, col, rp), shape=(n, n))
+    cen = [0.5 * (f[1:] + f[:-1]) for f in (xf, yf, zf)]
+    wid = [np.diff(f) for f in (xf, yf, zf)]
+    Z, Y, X = np.meshgrid(cen[2], cen[1], cen[0], indexing="ij")
+    WZ, WY, WX = np.meshgrid(wid[2], wid[1], wid[0], indexing="ij")
+    grid_ix = np.meshgrid(np.arange(n3[2]), np.arange(n3[1]), np.arange(n3[0]), indexing="ij")
+    a = (0.7, -1.3, 2.1)
+    Lu = (A @ (a[0] * X + a[1] * Y + a[2] * Z).ravel()).reshape(n3[::-1])
+    expect = np.zeros(n3[::-1])
+    areas = (WY * WZ, WX * WZ, WX * WY)
+    for ax, idx in enumerate((grid_ix[2], grid_ix[1], grid_ix[0])):
+        expect -= np.where(idx == n3[ax] - 1, D0 * areas[ax] * a[ax], 0.0)   # no face above
+        expect += np.where(idx == 0, D0 * areas[ax] * a[ax], 0.0)            # no face below
+    assert np.max(np.abs(Lu - expect)) <= 1e-12 * np.max(np.abs(expect))
