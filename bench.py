@@ -528,14 +528,30 @@ def extras():
         out[name] = (ms, u.clone(), rep)
     # the explicit reading of the same case: 40 explicit Euler steps (dtau/dx^2 = 0.1)
     ex = {}
-    for name, prec in (("explicit_df", cg.PREC_FP32_DF_REFINE), ("explicit_fp64", cg.PREC_FP64)):
+    for name, prec, k in (("explicit_df", cg.PREC_FP32_DF_REFINE, 0), ("explicit_fp64", cg.PREC_FP64, 0),
+                          ("explicit_fp32_k1", 0, 1), ("explicit_fp32_blocked_k2", 0, 2),
+                          ("explicit_fp32_blocked_k3", 0, 3), ("explicit_fp32_blocked_k4", 0, 4)):
         ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
-            bandwidth=ch.b, nsteps=ch.nsteps, scheme=2, precision=prec), report=True))
+            bandwidth=ch.b, nsteps=ch.nsteps, scheme=2, precision=prec, fused_k=k), report=True))
         ex[name] = (ms, u.clone(), rep)
+    # the diffusion phase alone for the FP32 modes: cell-steps per second and the
+    # algorithmic bytes of one launch (read and write one FP32 value per cell) per time
+    e0 = cg.deposit(mesh, dp, dw)
+    fp32_diffusion = {}
+    for k in (1, 2, 3, 4):
+        u = e0.clone()
+        ms, _ = _timed_call(lambda: cg.diffuse(mesh, u, cg.Params(
+            bandwidth=ch.b, nsteps=ch.nsteps, scheme=2, fused_k=k)), reps=3)
+        fp32_diffusion["k%d" % k] = {
+            "ms": ms, "cell_steps_per_s": ch.nsteps * ch.ncells / (ms * 1e-3),
+            "algorithmic_GBps": (ch.ncells * 8 * -(-ch.nsteps // k)) / (ms * 1e-3) / 1e9}
+    del e0
     res["channel_512x256x256_explicit"] = {
         "workload": "the channel case with 40 explicit Euler steps (dtau/dx^2 = 0.1)",
-        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3)}
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
+                      "maxrel_vs_fp64_gpu": maxrel(v[1], ex["explicit_fp64"][1])}
                   for k, v in ex.items()},
+        "fp32_diffusion_only": fp32_diffusion,
         "df_vs_fp64_maxrel": maxrel(ex["explicit_df"][1], ex["explicit_fp64"][1]),
         "explicit_vs_implicit_fp64_maxrel": maxrel(ex["explicit_fp64"][1], out["fp64_cg"][1])}
     del ex
@@ -547,6 +563,64 @@ def extras():
                       "maxrel_vs_fp64_gpu": maxrel(v[1], out["fp64_cg"][1])}
                   for k, v in out.items()},
         "particles_per_s": ch.n / (out["bf16_dfrefine"][0] * 1e-3)}
+    mesh.close()
+    del out
+    # the same channel periodic in x (Section 3.1) with the particles' momentum as three
+    # more fields, then the solid velocity (diffused momentum / diffused solid fraction)
+    dw4 = torch.from_numpy(np.vstack([ch.w, ch.w * W.channel_velocities(ch.pos)])).cuda()
+    mesh = cg.StructuredMesh(ch.dims, ch.origin, ch.dx, periodic=(True, False, False))
+    per = {}
+    for name, prec, reps in (("fp32_dfrefine", cg.PREC_FP32_DF_REFINE, 2), ("fp64_cg", cg.PREC_FP64, 1)):
+        ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw4, cg.Params(
+            bandwidth=ch.b, nsteps=ch.nsteps, precision=prec), report=True), reps=reps)
+        per[name] = (ms, u.clone(), rep)
+    um = per["fp32_dfrefine"][1]
+    ms_us, us = _timed_call(lambda: cg.solid_velocity(mesh, um[0], um[1:], eps_min=1e-6), reps=3)
+    res["channel_periodic_x_solid_velocity"] = {
+        "workload": "the channel case periodic in x, 4 fields (V_p and V_p u, u = 1 + 0.5 sin(2 pi x) "
+                    "streamwise + N(0, 0.1)), b=4dx, 40 IE steps, then U_s = diffused momentum / "
+                    "diffused solid fraction",
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
+                      "maxrel_vs_fp64_gpu": maxrel(v[1], per["fp64_cg"][1]),
+                      "sweep_shape_used": v[2]["sweep_shape_used"]} for k, v in per.items()},
+        "solid_velocity_ms": ms_us, "solid_velocity_cells_per_s": ch.ncells / (ms_us * 1e-3),
+        "solid_velocity_GBps": ch.ncells * (4 + 3) * 8 / (ms_us * 1e-3) / 1e9,
+        "mean_streamwise_velocity": float(us[0].mean())}
+    mesh.close()
+    del dp, dw, dw4, per, um, us
+    # Crank-Nicolson (the paper's scheme, Section 5.1) on the 128^3 clustered case, b = 4 dx
+    c = W.clustered_cube()
+    mesh = cg.StructuredMesh(c.dims, c.origin, c.dx)
+    dp, dw = torch.from_numpy(c.pos).cuda(), torch.from_numpy(c.w).cuda()
+    cn = {}
+    for name, prec in (("fp32_dfrefine", cg.PREC_FP32_DF_REFINE), ("fp64_cg", cg.PREC_FP64)):
+        ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
+            bandwidth=4 * c.dx, nsteps=10, scheme=1, precision=prec), report=True))
+        cn[name] = (ms, u.clone(), rep)
+    res["clustered_128_crank_nicolson"] = {
+        "workload": "the 128^3 clustered case, b = 4 dx, 10 Crank-Nicolson steps",
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
+                      "maxrel_vs_fp64_gpu": maxrel(v[1], cn["fp64_cg"][1])} for k, v in cn.items()}}
+    mesh.close()
+    del dp, dw, cn
+    # stretched 128^3 mesh with a cell diffusion constant (0 in one block, 4 in another)
+    xf, yf, zf, D, pos, w = W.stretched_box()
+    mesh = cg.HexMesh(xf, yf, zf, D)
+    dp, dw = torch.from_numpy(pos).cuda(), torch.from_numpy(w).cuda()
+    eps0 = cg.deposit(mesh, dp, dw)
+    frozen = torch.from_numpy(D == 0.0).cuda()
+    hx = {}
+    for name, prec in (("fp32_fp64refine", cg.PREC_FP32_REFINE), ("fp64_pcg", cg.PREC_FP64)):
+        ms, (u, rep) = _timed_call(lambda: cg.coarse_grain(mesh, dp, dw, cg.Params(
+            bandwidth=2.0 / 128, nsteps=10, precision=prec), report=True))
+        hx[name] = (ms, u.clone(), rep)
+    res["stretched_hex_128"] = {
+        "workload": "128^3 stretched mesh (z faces geometric, ratio 1.02), D = 1 with a D = 0 block "
+                    "and a D = 4 block, 5,000,000 layered spheres with 4 fields, b = 2/128, 10 IE steps",
+        "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
+                      "maxrel_vs_fp64_gpu": maxrel(v[1], hx["fp64_pcg"][1])} for k, v in hx.items()},
+        "frozen_cells_bit_identical_to_pcm": all(
+            bool(torch.equal(v[1][:, frozen], eps0[:, frozen])) for v in hx.values())}
     mesh.close()
     return res
 

@@ -84,7 +84,7 @@ int64_t cg_mesh_num_cells(const cg_mesh *mesh);
 /* Copies the cell volumes V_c into out_host[ncells] (FP64). */
 cg_status cg_mesh_cell_volumes(const cg_mesh *mesh, double *out_host);
 
-/* Periodic axes of a structured mesh (Section 3.2.2: a periodic boundary keeps a
+/* Periodic axes of a structured mesh (Section 3.1: a periodic boundary keeps a
  * periodic condition instead of zero flux).  px, py, pz nonzero make the faces at the
  * two ends of the mesh along x, y, z neighbours of each other (on an axis of one cell,
  * of the cell itself); all zero restores the walls.  Deposition is unchanged.  With a
@@ -148,7 +148,13 @@ typedef struct {
                            (FP64 residual); default 1e-13 */
     int max_iter;       /* FP64 CG: iteration cap per step; mixed: inner iteration cap */
     int max_rounds;     /* mixed: refinement-round cap per step (default 12) */
-    int fused_k;        /* reserved (0) */
+    int fused_k;        /* explicit Euler on a uniform structured mesh only: 1..4 runs
+                           the steps in FP32 storage and arithmetic, fused_k steps per
+                           launch (temporal blocking; the precision field is then not
+                           used; results do not depend on fused_k); rounding grows with
+                           the step count (about 2-7e-7 max-relative after 40 steps).
+                           0 (default): FP64 or double-float steps per precision.  Other
+                           schemes need 0 (else CG_EINVAL) */
     int sweep_shape;    /* hex Chebyshev sweep shape: 0 = autotuned per mesh (default);
                            100 + z = vectorised, 4 x-cells per thread, z planes per block
                            (needs nx % 4 == 0); 2, 4, 8 = register-blocked planes per

@@ -252,6 +252,9 @@ static cg_status check_params(const cg_params *p) {
     if (!(T >= 0.0) || !std::isfinite(T)) return fail(CG_EINVAL, "pseudo-time T must be finite and >= 0");
     if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(CG_EINVAL, "tol must be in (0, 1)");
     if (p->max_iter < 1) return fail(CG_EINVAL, "max_iter must be >= 1");
+    if (p->fused_k < 0 || p->fused_k > 4) return fail(CG_EINVAL, "fused_k must be in [0, 4] (got %d)", p->fused_k);
+    if (p->fused_k > 0 && p->scheme != CG_SCHEME_EXPLICIT_EULER)
+        return fail(CG_EINVAL, "fused_k > 0 selects blocked explicit Euler steps (scheme 2)");
     return CG_OK;
 }
 

@@ -468,6 +468,200 @@ __global__ void __launch_bounds__(kThreads) k_explicit(Geo g, int zlen, int nzc,
         [&](int k, double v, double s, int nn) { y[k] = v + c * (s - nn * v); });
 }
 
+// ---------------------------------------------------------------- explicit Euler, temporally blocked
+// K explicit Euler steps per launch in FP32 storage and arithmetic (3.5D blocking).  A
+// block holds a tile of kEW x kEH columns (32 lanes x two x-cells, 16 warps x two rows)
+// and marches in z.  At iteration p it loads plane p of the input (level 0) and computes
+// level t at plane p - t for t = 1..K, so a level's z neighbours are the last three
+// planes of the level below, kept per thread in registers, and its x and y neighbours
+// are the level below at the same plane: lane shuffles in x, the thread's own second row
+// or a shared plane per level in y.  That shared plane was written one iteration earlier
+// into the other of two buffers, so one barrier per iteration orders every exchange.
+// The valid region shrinks by one column and row per level on each side; the block
+// writes level K on its inner (kEW - 2K) x (kEH - 2K) columns.  Cells outside the mesh
+// (and planes outside it) hold zero and are not counted as neighbours (zero-flux walls);
+// on a periodic axis coordinates wrap and every cell has both neighbours.  Every cell
+// update is the same expression in the same order whatever K, so the result does not
+// depend on K.
+constexpr int kEW = 64, kEH = 32;
+constexpr dim3 kEBlock(32, 16);
+constexpr int kEStages = 4;   // input planes staged ahead by cp.async (three in flight)
+
+__host__ __device__ constexpr size_t explicit_tb_smem(int K) {
+    return (size_t)(kEStages + 2 * K) * kEH * kEW * sizeof(float);
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int wrap_coord(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+__global__ void k_to_f32(size_t n, const double *__restrict__ u, float *__restrict__ v) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v[i] = __double2float_rn(u[i]);
+}
+
+__global__ void k_from_f32(size_t n, const float *__restrict__ v, double *__restrict__ u) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = (double)v[i];
+}
+
+template <int K>
+__global__ void __launch_bounds__(512, 2) k_explicit_tb(Geo g, int zlen, int nzc, float c,
+                                                        const float *__restrict__ uin_all,
+                                                        float *__restrict__ uout_all) {
+    extern __shared__ float4 tb_smem[];
+    // stage[slot][row][column]: input planes in flight; buf[level][parity][row][column],
+    // levels 0..K-1
+    float(*stage)[kEH][kEW] = reinterpret_cast<float(*)[kEH][kEW]>(tb_smem);
+    float(*buf)[2][kEH][kEW] = reinterpret_cast<float(*)[2][kEH][kEW]>(&stage[kEStages][0][0]);
+    constexpr int OX = kEW - 2 * K, OY = kEH - 2 * K;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int f = blockIdx.z / nzc, zc = blockIdx.z - f * nzc;
+    const int z0 = zc * zlen, z1 = min(g.nz, z0 + zlen);
+    const bool px = g.per & 1, py = (g.per >> 1) & 1, pz = (g.per >> 2) & 1;
+    const float *uin = uin_all + (size_t)f * g.n;
+    float *uout = uout_all + (size_t)f * g.n;
+
+    // per cell (row h, column i of the thread's 2 x 2): its offset in a plane, whether it
+    // is in the mesh (as a 0/1 factor and as a copy size), its x-y face count, and
+    // whether the block writes it
+    int off[2][2], csz[2][2];
+    float msk[2][2], nxy[2][2];
+    bool wr[2][2];
+    {
+        int gx[2], gy[2];
+        bool ex[2], ey[2], wx[2], wy[2];
+        float cx[2], cy[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int j = 2 * lane + i, x = blockIdx.x * OX - K + j;
+            ex[i] = px || (x >= 0 && x < g.nx);
+            gx[i] = px ? wrap_coord(x, g.nx) : min(max(x, 0), g.nx - 1);
+            cx[i] = px ? 2.f : (float)((x > 0) + (x < g.nx - 1));
+            wx[i] = j >= K && j < kEW - K && x >= 0 && x < g.nx;
+            const int r = 2 * w + i, y = blockIdx.y * OY - K + r;
+            ey[i] = py || (y >= 0 && y < g.ny);
+            gy[i] = py ? wrap_coord(y, g.ny) : min(max(y, 0), g.ny - 1);
+            cy[i] = py ? 2.f : (float)((y > 0) + (y < g.ny - 1));
+            wy[i] = r >= K && r < kEH - K && y >= 0 && y < g.ny;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                off[h][i] = gy[h] * g.nx + gx[i];
+                csz[h][i] = (ex[i] && ey[h]) ? 4 : 0;
+                msk[h][i] = (ex[i] && ey[h]) ? 1.f : 0.f;
+                nxy[h][i] = cx[i] + cy[h];
+                wr[h][i] = wx[i] && wy[h];
+            }
+    }
+    // the level buffers start at zero, so every value a cell ever reads is finite
+    for (int k = threadIdx.y * 32 + threadIdx.x; k < K * 2 * kEH * kEW; k += 512) (&buf[0][0][0][0])[k] = 0.f;
+    __syncthreads();
+    // queue of each level below K: planes q-1 (qa) and q (qb) of this thread's 2 x 2 cells
+    float qa[K][2][2], qb[K][2][2];
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) qa[t][h][i] = qb[t][h][i] = 0.f;
+
+    const int p_begin = pz ? z0 - K : max(z0 - K, 0);
+    const int p_end = pz ? z1 + K : min(z1 + K, g.nz + K);
+    // each thread stages its own four cells of a plane (zero outside the mesh), so
+    // reading them back needs only its own wait, no barrier
+    const unsigned stage0 = (unsigned)__cvta_generic_to_shared(&stage[0][2 * w][2 * lane]);
+    auto stage_plane = [&](int p) {
+        const bool zok = p < p_end && (pz || (p >= 0 && p < g.nz));
+        const float *src = uin + (size_t)(pz ? wrap_coord(p, g.nz) : min(max(p, 0), g.nz - 1)) * g.nxy;
+        const unsigned dst = stage0 + (unsigned)(((p - p_begin) & (kEStages - 1)) * kEH * kEW * 4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + (h * kEW + i) * 4),
+                             "l"(src + off[h][i]), "r"(zok ? csz[h][i] : 0)
+                             : "memory");
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int d = 0; d < kEStages - 1; ++d) stage_plane(p_begin + d);
+    for (int p = p_begin; p < p_end; ++p) {
+        stage_plane(p + kEStages - 1);   // past the end: an empty (zero-filled) group
+        cp_async_wait<kEStages - 1>();     // plane p has landed
+        float nw[2][2];   // the newest plane of the level below: level 0 at plane p
+        {
+            const float(*src)[kEW] = stage[(p - p_begin) & (kEStages - 1)];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 v = *reinterpret_cast<const float2 *>(&src[2 * w + h][2 * lane]);
+                nw[h][0] = v.x;
+                nw[h][1] = v.y;
+            }
+        }
+        const int par = p & 1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            *reinterpret_cast<float2 *>(&buf[0][par][2 * w + h][2 * lane]) = make_float2(nw[h][0], nw[h][1]);
+#pragma unroll
+        for (int t = 1; t <= K; ++t) {
+            const int q = p - t;
+            float v[2][2];
+            if (q >= z0 - (K - t) && q < z1 + (K - t) && (pz || (q >= 0 && q < g.nz))) {   // uniform
+                const float cz = pz ? 2.f : (float)((q > 0) + (q < g.nz - 1));
+                // y neighbours outside the thread's two rows (row 2w-1 above, 2w+2 below)
+                const float2 up = *reinterpret_cast<const float2 *>(&buf[t - 1][par ^ 1][max(2 * w - 1, 0)][2 * lane]);
+                const float2 dn = *reinterpret_cast<const float2 *>(&buf[t - 1][par ^ 1][min(2 * w + 2, kEH - 1)][2 * lane]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float b0 = qb[t - 1][h][0], b1 = qb[t - 1][h][1];
+                    const float xl = __shfl_up_sync(0xffffffffu, b1, 1);
+                    const float xr = __shfl_down_sync(0xffffffffu, b0, 1);
+                    const float yu0 = h ? qb[t - 1][0][0] : up.x, yu1 = h ? qb[t - 1][0][1] : up.y;
+                    const float yd0 = h ? dn.x : qb[t - 1][1][0], yd1 = h ? dn.y : qb[t - 1][1][1];
+                    const float s0 = ((xl + b1) + (yu0 + yd0)) + (qa[t - 1][h][0] + nw[h][0]);
+                    const float s1 = ((b0 + xr) + (yu1 + yd1)) + (qa[t - 1][h][1] + nw[h][1]);
+                    v[h][0] = msk[h][0] * fmaf(c, fmaf(-(nxy[h][0] + cz), b0, s0), b0);
+                    v[h][1] = msk[h][1] * fmaf(c, fmaf(-(nxy[h][1] + cz), b1, s1), b1);
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) v[h][0] = v[h][1] = 0.f;
+            }
+            if (t < K) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    *reinterpret_cast<float2 *>(&buf[t][par][2 * w + h][2 * lane]) = make_float2(v[h][0], v[h][1]);
+            } else if (q >= z0 && q < z1) {   // uniform
+                float *dst = uout + (size_t)q * g.nxy;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+                        if (wr[h][i]) dst[off[h][i]] = v[h][i];
+            }
+            // shift the queue of level t-1; level t's new plane feeds level t+1
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    qa[t - 1][h][i] = qb[t - 1][h][i];
+                    qb[t - 1][h][i] = nw[h][i];
+                    nw[h][i] = v[h][i];
+                }
+        }
+        __syncthreads();
+    }
+}
+
 // ================================================================ mixed precision
 template <class TS> __device__ __forceinline__ float ld(const TS *p, int i);
 template <> __device__ __forceinline__ float ld<float>(const float *p, int i) { return p[i]; }
@@ -2479,6 +2673,89 @@ static cg_status diffuse_fp64(cg_mesh *m, int nf, double *cells, const cg_params
     return CG_OK;
 }
 
+// One launch of k_explicit_tb<K>: kt explicit steps (1 <= kt <= 4) from a to b.
+template <int K> static int explicit_tb_blocks_per_sm(size_t smem) {
+    static int cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(k_explicit_tb<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_explicit_tb<K>, kEBlock.x * kEBlock.y, smem) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+static cg_status launch_explicit_tb(const Geo &g, int nf, int kt, float c, const float *a, float *b,
+                                    cudaStream_t st) {
+    const int OX = kEW - 2 * kt, OY = kEH - 2 * kt;
+    const int gx = (g.nx + OX - 1) / OX, gy = (g.ny + OY - 1) / OY;
+    const size_t smem = explicit_tb_smem(kt);
+    const int per_sm = kt == 1 ? explicit_tb_blocks_per_sm<1>(smem)
+                     : kt == 2 ? explicit_tb_blocks_per_sm<2>(smem)
+                     : kt == 3 ? explicit_tb_blocks_per_sm<3>(smem) : explicit_tb_blocks_per_sm<4>(smem);
+    // z chunks: a block of a chunk of zlen planes runs zlen + 2K pipeline iterations, and
+    // the launch takes ceil(blocks / resident blocks) waves; pick the chunk length that
+    // minimises waves x (zlen + 2K)
+    const long long cols = (long long)gx * gy * nf, slots = (long long)num_sms() * per_sm;
+    int zlen = g.nz;
+    long long best = -1;
+    for (int zl = 1; zl <= g.nz; ++zl) {
+        const long long nzc = (g.nz + zl - 1) / zl;
+        if (zl > 1 && (g.nz + zl - 2) / (zl - 1) == nzc) continue;   // same chunk count, shorter zl wins
+        const long long waves = (cols * nzc + slots - 1) / slots;
+        const long long cost = waves * (zl + 2 * kt);
+        if (best < 0 || cost < best) best = cost, zlen = zl;
+    }
+    const int nzc = (g.nz + zlen - 1) / zlen;
+    const dim3 grid(gx, gy, nzc * nf);
+    const double bytes = (double)g.n * nf * 8;
+    switch (kt) {
+    case 1:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb<1><<<grid, kEBlock, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    case 2:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb<2><<<grid, kEBlock, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    case 3:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb<3><<<grid, kEBlock, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    default:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb<4><<<grid, kEBlock, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    }
+    CGK_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
+// Explicit Euler in FP32 with K = fused_k steps per launch (the last launch takes the
+// remainder).
+static cg_status explicit_blocked(const Geo &g, int nf, double *cells, int nsteps, int K, float c,
+                                  cg_mesh *m, cg_report *rep, cudaStream_t st) {
+    if (K > 4) return fail(CG_EINVAL, "cg_diffuse: fused_k must be 0..4 (got %d)", K);
+    const size_t cnt = (size_t)g.n * nf;
+    const size_t vec = align_up(cnt * 4);
+    CGK_TRY(m->ws_diffuse.ensure(2 * vec));
+    float *a = m->ws_diffuse.as<float>(), *b = (float *)(m->ws_diffuse.as<char>() + vec);
+    CGK_LAUNCH("to_f32", (double)cnt * 12, st, k_to_f32<<<stencil_grid(cnt), kThreads, 0, st>>>(cnt, cells, a));
+    for (int s = 0; s < nsteps;) {
+        const int kt = std::min(K, nsteps - s);
+        CGK_TRY(launch_explicit_tb(g, nf, kt, c, a, b, st));
+        std::swap(a, b);
+        s += kt;
+    }
+    CGK_LAUNCH("from_f32", (double)cnt * 12, st, k_from_f32<<<stencil_grid(cnt), kThreads, 0, st>>>(cnt, a, cells));
+    CGK_CUDA(cudaGetLastError());
+    CGK_CUDA(cudaStreamSynchronize(st));
+    if (rep) {
+        rep->iters = (long long)nsteps * nf;
+        rep->cell_updates = rep->iters * (long long)g.n;
+        rep->final_rel_residual = 0.0;
+    }
+    return CG_OK;
+}
+
 static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
                                   cg_report *rep, cudaStream_t st) {
     const int n = (int)m->ncells;
@@ -2488,6 +2765,7 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
     if (c > 1.0 / 6.0 + 1e-15)
         return fail(CG_EINVAL, "cg_diffuse: explicit Euler needs dtau <= dx^2/6 (dtau/dx^2 = %g)", c);
     const size_t vec = align_up((size_t)n * nf * 8);
+    if (p->fused_k > 0) return explicit_blocked(g, nf, cells, p->nsteps, p->fused_k, (float)c, m, rep, st);
     const Sweep sw = make_sweep(g, nf);
     const dim3 blk(TX, TY);
     const bool df = (p->precision == CG_PREC_FP32_DF_REFINE || p->precision == CG_PREC_BF16_DF_REFINE) &&

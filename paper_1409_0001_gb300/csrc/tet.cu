@@ -1179,7 +1179,11 @@ cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
                           cudaStream_t st) {
     g_row_slots = m->tet.ns;
     double T = p->bandwidth > 0.0 ? p->bandwidth * p->bandwidth / 4.0 : p->T;
-    if (p->scheme == CG_SCHEME_EXPLICIT_EULER) return tet_explicit(m, nf, cells, p, T, rep, st);
+    if (p->scheme == CG_SCHEME_EXPLICIT_EULER) {
+        if (p->fused_k > 0)
+            return fail(CG_EINVAL, "cg_diffuse: fused_k (blocked explicit steps) needs a uniform structured mesh");
+        return tet_explicit(m, nf, cells, p, T, rep, st);
+    }
     if (p->precision == CG_PREC_FP64) return tet_fp64(m, nf, cells, p, T, rep, st);
     if (p->precision == CG_PREC_FP32_REFINE || p->precision == CG_PREC_FP32_DF_REFINE)
         return tet_mixed<float>(m, nf, cells, p, T, rep, st);

@@ -24,6 +24,13 @@ order is the generation order, which matters for ordered deposition):
   d = 0.004, 5 fields: V_p, V_p u (u ~ N(0, 0.1) per component), drag ~ LogNormal(0,1).
 * ``channel``: a 512x256x256 mesh over a 4x2x2 box, 50,000,000 spheres of d = 0.004,
   density proportional to 1 + 0.5 sin(2 pi x) (x in box units), by rejection.
+* ``stretched_box``: a 128^3 stretched Cartesian mesh of the unit cube, uniform in x and
+  y, z faces growing geometrically (ratio 1.02) away from the bottom wall, a cell
+  diffusion constant of 1 except a block with D = 0 (where the smoothed field stays the
+  PCM field) and a block with D = 4; the particles of ``layered_cube`` with their
+  velocities as three more fields (u ~ N(0, 0.1)).
+* ``channel_velocities``: per-particle velocities for the channel, a mean streamwise
+  flow of 1 + 0.5 sin(2 pi x) plus N(0, 0.1) per component.
 """
 from __future__ import annotations
 
@@ -207,6 +214,36 @@ def channel(n_particles=50_000_000, dims=(512, 256, 256), lengths=(4.0, 2.0, 2.0
     dx = lengths[0] / dims[0]
     return StructuredCase("channel_%dx%dx%d" % dims, tuple(dims), (0.0, 0.0, 0.0), dx, out, w,
                           b_over_dx * dx, nsteps)
+
+
+def stretched_box(n=128, ratio=1.02, n_particles=5_000_000, d=0.003, seed=0):
+    """Face coordinates (xf, yf, zf), cell diffusion constants D [ncells] (cell k =
+    (iz n + iy) n + ix), particle centroids [3, n_p] and weights [4, n_p] (V_p and V_p u)."""
+    rng = np.random.default_rng(seed)
+    xf = np.linspace(0.0, 1.0, n + 1)
+    wz = ratio ** np.arange(n)
+    zf = np.concatenate([[0.0], np.cumsum(wz)])
+    zf /= zf[-1]
+    zf[-1] = 1.0
+    D = np.ones((n, n, n))
+    D[n // 8:n // 4, 3 * n // 8:5 * n // 8, 3 * n // 8:5 * n // 8] = 0.0
+    D[n // 2:3 * n // 4, n // 8:n // 4, :] = 4.0
+    pos, _ = layered_positions(rng, n_particles, d=d)
+    u = 0.1 * rng.standard_normal((3, n_particles))
+    vp = sphere_volume(d)
+    w = np.empty((4, n_particles))
+    w[0] = vp
+    w[1:] = vp * u
+    return xf, xf.copy(), zf, D.ravel(), pos, w
+
+
+def channel_velocities(pos, seed=1):
+    """Particle velocities [3, n] for the channel: 1 + 0.5 sin(2 pi x) streamwise plus
+    N(0, 0.1) per component."""
+    rng = np.random.default_rng(seed)
+    v = 0.1 * rng.standard_normal((3, pos.shape[1]))
+    v[0] += 1.0 + 0.5 * np.sin(2.0 * np.pi * pos[0])
+    return v
 
 
 def random_field(rng, nf, ncells, positive=True):
