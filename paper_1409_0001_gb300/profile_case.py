@@ -4,7 +4,8 @@
 
 Builds a seeded random field on an n^3 (or --dims) unit-spaced hex mesh and smooths
 it --reps times with the chosen precision mode (see include/cg.h), b = --b-over-dx
-cells, --nsteps implicit-Euler steps.  Prints the device time of each call.
+cells, --nsteps implicit-Euler steps (or, with --explicit-k K, --nsteps explicit steps
+in FP32 with K steps per launch).  Prints the device time of each call.
 """
 from __future__ import annotations
 
@@ -29,6 +30,9 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tet", action="store_true", help="Kuhn tet mesh of n^3 hexes instead")
     ap.add_argument("--shape", type=int, default=0, help="sweep_shape (0 = autotuned)")
+    ap.add_argument("--explicit-k", type=int, default=0,
+                    help="explicit Euler instead: fused_k steps per launch (FP32, temporal "
+                         "blocking), --nsteps steps at dtau/dx^2 = 0.1")
     ap.add_argument("--deposit", action="store_true",
                     help="ordered deposition of the clustered n^3 workload (2,000,000 spheres "
                          "at n = 128) instead of a diffusion")
@@ -65,8 +69,11 @@ def main(argv=None):
         mesh = cg.StructuredMesh(dims, (0.0, 0.0, 0.0), dx)
     rng = np.random.default_rng(0)
     u0 = torch.from_numpy(rng.random((a.nfields, mesh.ncells))).cuda()
-    p = cg.Params(bandwidth=a.b_over_dx * dx, nsteps=a.nsteps, precision=a.precision,
-                  sweep_shape=a.shape)
+    if a.explicit_k:
+        p = cg.Params(T=0.1 * dx * dx * a.nsteps, nsteps=a.nsteps, scheme=2, fused_k=a.explicit_k)
+    else:
+        p = cg.Params(bandwidth=a.b_over_dx * dx, nsteps=a.nsteps, precision=a.precision,
+                      sweep_shape=a.shape)
     for r in range(a.reps):
         u = u0.clone()
         torch.cuda.synchronize()
