@@ -240,6 +240,23 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
                                const double *w_host, double *cells_host, const cg_params *params,
                                cg_report *report, void *stream);
 
+/* Independent coarse-grainings run concurrently: problem i is exactly
+ * cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
+ * reports ? &reports[i] : NULL, streams[i]) -- same results, bit for bit -- and up to
+ * max_concurrent problems run at a time, each on a host thread of the library (the
+ * calling thread is one of them), so their kernels overlap on the device where their
+ * streams allow it.  The meshes must be distinct (each problem uses its mesh's
+ * workspaces); give each problem its own non-default stream for overlap.  A mesh's
+ * first call of a configuration autotunes its sweep shape by timing candidates, which
+ * other running problems would disturb: make that first call through cg_coarse_grain.
+ * Returns when every problem has finished: CG_OK, or the status of the lowest-index
+ * failing problem (cg_last_error names it).  CG_EINVAL also for NULL arrays, a shared
+ * mesh, max_concurrent < 1, or kernel profiling switched on (cg_profile_enable). */
+cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const int64_t *n,
+                                     const double *const *pos, int nfields, const double *const *w,
+                                     double *const *cells, const cg_params *params, cg_report *reports,
+                                     void *const *streams, int max_concurrent);
+
 /* The solid velocity (the paper's conclusions: the momentum, not the velocity, is
  * diffused): U_s = smoothed momentum / smoothed solid fraction per cell and component,
  * the two smoothed fields taken from one multi-field cg_coarse_grain or cg_diffuse call

@@ -110,6 +110,7 @@ def load_library(path: str | None = None):
         "cg_mesh_set_periodic": (i32, [vp, i32, i32, i32]),
         "cg_create_mesh_hex": (i32, [i32, i32, i32, vp, vp, vp, vp, P(vp)]),
         "cg_solid_velocity": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
+        "cg_coarse_grain_concurrent": (i32, [i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -127,7 +128,8 @@ def exported_symbols():
             "cg_coarse_grain_host", "cg_profile_enable", "cg_profile_reset", "cg_profile_count",
             "cg_profile_get", "cg_launch_count", "cg_launch_count_reset",
             "cg_deposit_fixed_noalloc", "cg_diffuse_batched", "cg_coarse_grain_batched",
-            "cg_mesh_set_periodic", "cg_solid_velocity", "cg_create_mesh_hex"]
+            "cg_mesh_set_periodic", "cg_solid_velocity", "cg_create_mesh_hex",
+            "cg_coarse_grain_concurrent"]
 
 
 def _check(status: int, where: str):
@@ -466,3 +468,40 @@ def coarse_grain_batched(meshes, pos, w, params: Params, bandwidths=None, out=No
                                                   ctypes.byref(rep), _stream_handle(stream)),
            "cg_coarse_grain_batched")
     return (out, rep.as_dict()) if report else out
+
+
+def coarse_grain_concurrent(meshes, pos, w, params, out=None, streams=None, max_concurrent=2,
+                            report=False):
+    """Independent coarse-grainings run concurrently (cg_coarse_grain_concurrent): problem
+    i is coarse_grain(meshes[i], pos[i], w[i], params[i]) on streams[i] (one new stream per
+    problem by default).  pos[i] [3, n_i] and w[i] [nf, n_i] are CUDA f64 tensors (they
+    may be shared between problems); params is one Params or a list.  Returns the list of
+    [nf, ncells_i] cell tensors (and the reports)."""
+    import torch
+    k = len(meshes)
+    params = list(params) if isinstance(params, (list, tuple)) else [params] * k
+    nf = w[0].shape[0]
+    for t in list(pos) + list(w):
+        _dev_f64(t, "pos/w")
+    if out is None:
+        out = [torch.empty((nf, m.ncells), dtype=torch.float64, device=w[0].device) for m in meshes]
+    if streams is None:
+        streams = [torch.cuda.Stream(device=w[0].device) for _ in range(k)]
+    # the problems' streams start after the work already queued on the current stream
+    cur = torch.cuda.current_stream(w[0].device)
+    for s_ in streams:
+        s_.wait_stream(cur)
+    ms = _ptr_array([m.handle.value for m in meshes])
+    ns = _ptr_array([int(p_.shape[1]) for p_ in pos], ctypes.c_int64)
+    ps = _ptr_array([p_.data_ptr() for p_ in pos])
+    ws = _ptr_array([w_.data_ptr() for w_ in w])
+    cs = _ptr_array([c.data_ptr() for c in out])
+    ss = _ptr_array([s_.cuda_stream for s_ in streams])
+    cps = (CgParams * k)(*[p_.to_c() for p_ in params])
+    reps = (CgReport * k)()
+    _check(load_library().cg_coarse_grain_concurrent(k, ms, ns, ps, nf, ws, cs, cps, reps, ss,
+                                                     int(max_concurrent)),
+           "cg_coarse_grain_concurrent")
+    for s_ in streams:   # later work on the current stream sees the results
+        cur.wait_stream(s_)
+    return (out, [r.as_dict() for r in reps]) if report else out

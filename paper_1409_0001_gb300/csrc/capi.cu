@@ -11,6 +11,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -716,6 +718,52 @@ cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64
     }
     prof_collect();
     return s;
+}
+
+cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const int64_t *n,
+                                     const double *const *pos, int nfields, const double *const *w,
+                                     double *const *cells, const cg_params *params, cg_report *reports,
+                                     void *const *streams, int max_concurrent) {
+    if (nprob < 1 || !meshes || !n || !pos || !w || !cells || !params || !streams)
+        return fail(CG_EINVAL, "cg_coarse_grain_concurrent: no problems or a NULL array");
+    if (max_concurrent < 1) return fail(CG_EINVAL, "max_concurrent must be >= 1");
+    if (prof_on())
+        return fail(CG_EINVAL, "kernel profiling is on: concurrent problems would share its event timing");
+    for (int i = 0; i < nprob; ++i) {
+        if (!meshes[i]) return fail(CG_EINVAL, "problem %d: mesh is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (meshes[j] == meshes[i])
+                return fail(CG_EINVAL, "problems %d and %d share a mesh (workspaces would collide)", j, i);
+    }
+    int dev = 0;
+    CGK_CUDA(cudaGetDevice(&dev));
+    std::vector<cg_status> status(nprob, CG_OK);
+    std::vector<std::string> detail(nprob);
+    std::atomic<int> next{0};
+    auto worker = [&](bool own_thread) {
+        if (own_thread && cudaSetDevice(dev) != cudaSuccess) return;
+        for (int i; (i = next.fetch_add(1)) < nprob;) {
+            status[i] = cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
+                                        reports ? &reports[i] : nullptr, streams[i]);
+            if (status[i] != CG_OK) detail[i] = g_last_error;   // this thread's message
+        }
+    };
+    std::vector<std::thread> pool;
+    const int nthreads = std::min(max_concurrent, nprob);
+    for (int t = 1; t < nthreads; ++t) {
+        try {
+            pool.emplace_back(worker, true);
+        } catch (...) {
+            break;   // fewer workers: the remaining problems run on the threads there are
+        }
+    }
+    worker(false);
+    for (std::thread &t : pool) t.join();
+    if (next.load() < nprob)   // a worker could not select the device: finish here
+        worker(false);
+    for (int i = 0; i < nprob; ++i)
+        if (status[i] != CG_OK) return fail(status[i], "problem %d: %s", i, detail[i].c_str());
+    return CG_OK;
 }
 
 cg_status cg_coarse_grain_host(cg_mesh *m, int64_t n, const double *pos_host, int nfields,

@@ -1,0 +1,86 @@
+"""Concurrent independent coarse-grainings (cg_coarse_grain_concurrent): every problem's
+result and report equal those of cg_coarse_grain on the same arguments, bit for bit, for
+any concurrency; failures name the lowest failing problem; misuse is refused."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1409_0001_gb300 as cg
+    from paper_1409_0001_gb300 import build
+    build.build()
+    cg.load_library()
+    return cg
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+@pytest.fixture(scope="module")
+def problems(cg):
+    """Four bandwidths of one clustered case, a second structured case and a tet mesh."""
+    c = W.clustered_cube(n_side=48, n_particles=200_000, seed=11)
+    u = W.uniform_cube(n_side=40, n_particles=50_000, seed=12)
+    xyz, tets = W.kuhn_tet_mesh(12, jitter=0.2, seed=13)
+    rng = np.random.default_rng(14)
+    tp = rng.random((3, 30_000))
+    tw = np.vstack([np.full(30_000, 1e-6), rng.standard_normal(30_000)])
+    probs = []
+    for bdx in (1.0, 2.0, 4.0, 8.0):
+        probs.append((cg.StructuredMesh(c.dims, c.origin, c.dx), dev(c.pos), dev(np.vstack([c.w, c.w])),
+                      cg.Params(bandwidth=bdx * c.dx, nsteps=10, precision=3)))
+    probs.append((cg.StructuredMesh(u.dims, u.origin, u.dx), dev(u.pos), dev(np.vstack([u.w, -u.w])),
+                  cg.Params(bandwidth=u.b, nsteps=10, precision=0)))
+    probs.append((cg.TetMesh(xyz, tets), dev(tp), dev(tw), cg.Params(bandwidth=0.1, nsteps=5, precision=1)))
+    # sequential results first (this also autotunes every mesh in isolation)
+    ref = [cg.coarse_grain(m, p, w, prm, report=True) for m, p, w, prm in probs]
+    return probs, [(u_.clone(), r) for u_, r in ref]
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 6])
+def test_concurrent_equals_sequential(cg, problems, k):
+    import torch
+    probs, ref = problems
+    out, reps = cg.coarse_grain_concurrent([p[0] for p in probs], [p[1] for p in probs],
+                                           [p[2] for p in probs], [p[3] for p in probs],
+                                           max_concurrent=k, report=True)
+    for (u_ref, r_ref), u, r in zip(ref, out, reps):
+        assert torch.equal(u, u_ref)
+        for key in ("cell_updates", "refine_rounds", "iters", "final_rel_residual", "n_out_of_domain"):
+            assert r[key] == r_ref[key], key
+        assert r["mass_out"] == r_ref["mass_out"]
+
+
+def test_concurrent_failure_and_misuse(cg, problems):
+    probs, _ = problems
+    meshes = [p[0] for p in probs[:3]]
+    pos = [p[1] for p in probs[:3]]
+    bad = pos[1].clone()
+    bad[0, 5] = 7.0                      # outside the unit cube: problem 1 fails
+    w = [p[2] for p in probs[:3]]
+    prm = [p[3] for p in probs[:3]]
+    with pytest.raises(cg.CGError) as e:
+        cg.coarse_grain_concurrent(meshes, [pos[0], bad, pos[2]], w, prm, max_concurrent=3)
+    assert e.value.code == "CG_EDOMAIN" and "problem 1" in str(e.value)
+    with pytest.raises(cg.CGError) as e:                      # a mesh used twice
+        cg.coarse_grain_concurrent([meshes[0], meshes[0]], pos[:2], w[:2], prm[:2])
+    assert e.value.code == "CG_EINVAL"
+    with pytest.raises(cg.CGError):
+        cg.coarse_grain_concurrent(meshes, pos, w, prm, max_concurrent=0)
+    cg.profile_enable(True)
+    try:
+        with pytest.raises(cg.CGError) as e:
+            cg.coarse_grain_concurrent(meshes, pos, w, prm)
+        assert "profiling" in str(e.value)
+    finally:
+        cg.profile_enable(False)
