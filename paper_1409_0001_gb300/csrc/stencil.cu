@@ -2674,8 +2674,10 @@ static cg_status diffuse_fp64(cg_mesh *m, int nf, double *cells, const cg_params
 }
 
 // One launch of k_explicit_tb<K>: kt explicit steps (1 <= kt <= 4) from a to b.
+// Resident blocks per SM of k_explicit_tb<K> (queried once per thread: the library's
+// calls may run on several host threads at a time).
 template <int K> static int explicit_tb_blocks_per_sm(size_t smem) {
-    static int cached = 0;
+    static thread_local int cached = 0;
     if (!cached) {
         cudaFuncSetAttribute(k_explicit_tb<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int nb = 0;

@@ -963,7 +963,7 @@ static Op make_op(cg_mesh *m, double dte, double dtau) {
 }
 
 // bytes of one operator row: ns ids + ns T + diag + V_c, plus the gathered values
-static int g_row_slots = 4;   // set per call from the mesh (profiling byte counts only)
+static thread_local int g_row_slots = 4;   // set per call from the mesh (profiling byte counts only)
 static double row_bytes(int s) { return g_row_slots * 4 + g_row_slots * (s == 4 ? 4 : 8) + 16; }
 
 static cg_status tet_fp64(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
