@@ -558,10 +558,15 @@ __global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
 }
 
 // inner PCG pass 1 (FP32 arithmetic, TS storage): p_new = z + beta p, q = A p_new
+// hist (may be null): per field, alpha_j at [f * 2H + j] and beta_j at [f * 2H + H + j]
+// for the first H iterations (the Lanczos coefficients of the solve)
+constexpr int kHist = 64;
+
 template <class TS>
 __global__ void k_tin_pass1(Op o, const TS *__restrict__ z_all, const TS *__restrict__ pin_all,
                             TS *__restrict__ pout_all, TS *__restrict__ q_all,
-                            double *__restrict__ partials_all, TScal *__restrict__ sc) {
+                            double *__restrict__ partials_all, TScal *__restrict__ sc,
+                            double *__restrict__ hist) {
     const int f = blockIdx.y;
     if (sc[f].done) return;
     const float beta = (float)sc[f].beta;
@@ -593,6 +598,7 @@ __global__ void k_tin_pass1(Op o, const TS *__restrict__ z_all, const TS *__rest
             TScal &S = sc[f];
             if (PQ > 0) {
                 S.alpha = S.rz / PQ;
+                if (hist && S.iters < kHist) hist[(size_t)f * 2 * kHist + S.iters] = S.alpha;
             } else {
                 S.alpha = 0;
                 S.breakdown = 1;
@@ -609,7 +615,7 @@ template <class TS>
 __global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__restrict__ q_all,
                             TS *__restrict__ d_all, TS *__restrict__ rin_all, TS *__restrict__ z_all,
                             double *__restrict__ partials_all, TScal *__restrict__ sc,
-                            double eps2) {
+                            double eps2, double *__restrict__ hist) {
     const int f = blockIdx.y;
     if (sc[f].done) return;
     const float alpha = (float)sc[f].alpha;
@@ -634,11 +640,44 @@ __global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__rest
         if (is_thread0()) {
             TScal &S = sc[f];
             S.beta = RZ / S.rz;
+            if (hist && S.iters < kHist) hist[(size_t)f * 2 * kHist + kHist + S.iters] = S.beta;
             S.rz = RZ;
             S.iters += 1;
             S.done = (RR <= eps2 * S.rr0) ? 1 : 0;
             S.ticket = 0;
         }
+    }
+}
+
+// Inner Chebyshev iteration on the Jacobi-scaled system D^-1 A d = D^-1 r (FP32
+// arithmetic, TS storage), spectrum enclosed in [theta - delta, theta + delta]: from
+// d_0 = 0, d_1 = c0 D^-1 r; then d_{k+1} = d_k + c1 (d_k - d_{k-1}) + c2 D^-1 (r - A d_k)
+// (dkm1 null: d_0 = 0).  No inner products, one pass per iteration.
+template <class TS, bool kFirst>
+__global__ void k_tcheb(Op o, const TS *__restrict__ r_all, const TS *__restrict__ dk_all,
+                        const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all, float c1, float c2) {
+    const size_t off = (size_t)blockIdx.y * o.n;
+    const TS *r = r_all + off;
+    const float dte = (float)o.dte;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        float dn;
+        if (kFirst) {
+            dn = c1 * (o.iadiag32[k] * ldf(r, k));
+        } else {
+            const TS *dk = dk_all + off;
+            const float dkk = ldf(dk, k);
+            float off_sum = 0.f;
+#pragma unroll
+            for (int q = 0; q < kMaxSlots; ++q) {
+                if (q >= o.ns) break;
+                const size_t e = (size_t)q * o.n + k;
+                off_sum += o.offv32[e] * ldf(dk, o.offc[e]);
+            }
+            const float res = ldf(r, k) - (o.adiag32[k] * dkk - dte * off_sum);
+            const float dm = dkm1_all ? ldf(dkm1_all + off, k) : 0.f;
+            dn = dkk + c1 * (dkk - dm) + c2 * (o.iadiag32[k] * res);
+        }
+        stf(dn_all, off + k, dn);
     }
 }
 
@@ -1060,6 +1099,62 @@ static cg_status tet_explicit(cg_mesh *m, int nf, double *cells, const cg_params
     return CG_OK;
 }
 
+// The smallest eigenvalue of the Lanczos tridiagonal that m conjugate-gradient steps
+// (coefficients alpha_j, beta_j) build for the preconditioned operator:
+// T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1}^2 = beta_j / alpha_j^2 (Saad,
+// Iterative Methods for Sparse Linear Systems, Section 6.7.3).  Its eigenvalues (Ritz
+// values) lie inside the operator's spectrum, here within (0, 2); bisection on the
+// Sturm count of the LDL^T pivots below x.
+static double lanczos_min(const double *alpha, const double *beta, int m) {
+    std::vector<double> a(m), b2(m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        a[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+        if (j + 1 < m) b2[j] = beta[j] / (alpha[j] * alpha[j]);
+    }
+    auto below = [&](double x) {
+        int c = 0;
+        double q = a[0] - x;
+        c += q < 0;
+        for (int j = 1; j < m; ++j) {
+            if (q == 0.0) q = 1e-300;
+            q = a[j] - x - b2[j - 1] / q;
+            c += q < 0;
+        }
+        return c;
+    };
+    double lo = 0.0, hi = 2.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        (below(mid) >= 1 ? hi : lo) = mid;
+    }
+    return hi;
+}
+
+// Chebyshev schedule on [a, b] for a residual reduction eps: c0 and, per later
+// iteration k, (c1_k, c2_k) of k_tcheb.
+struct ChebSchedule {
+    float c0 = 1.f;
+    std::vector<float> c1, c2;
+    int iterations() const { return 1 + (int)c1.size(); }
+};
+static ChebSchedule cheb_schedule(double a, double b, double eps) {
+    ChebSchedule cs;
+    const double theta = 0.5 * (a + b), delta = 0.5 * (b - a);
+    cs.c0 = (float)(1.0 / theta);
+    if (!(delta > 1e-12 * theta)) return cs;   // one point: D^-1 A = theta I
+    const double kappa = b / a, sg = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
+    const int m = std::max(1, (int)std::ceil(std::log(2.0 / eps) / -std::log(sg)));
+    const double s1 = theta / delta;
+    double rho = 1.0 / s1;
+    for (int k = 1; k < m; ++k) {
+        const double rn = 1.0 / (2.0 * s1 - rho);
+        cs.c1.push_back((float)(rn * rho));
+        cs.c2.push_back((float)(2.0 * rn / delta));
+        rho = rn;
+    }
+    return cs;
+}
+
 template <class TS>
 static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p, double T,
                            cg_report *rep, cudaStream_t st) {
@@ -1087,12 +1182,27 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     TS *Rin = (TS *)(wb + 3 * v64), *Z = (TS *)(wb + 3 * v64 + vts), *Q = (TS *)(wb + 3 * v64 + 2 * vts);
     TS *Pp[2] = {(TS *)(wb + 3 * v64 + 3 * vts), (TS *)(wb + 3 * v64 + 4 * vts)};
     TS *D = (TS *)(wb + 3 * v64 + 5 * vts);
-    CGK_TRY(m->ws_small.ensure(4096 + align_up((size_t)nf * 3 * G * 8) + 64 * sizeof(TScal)));
+    TS *Cb[3] = {Q, Pp[1], D};   // the Chebyshev iterates rotate through these
+    const size_t hist_bytes = align_up((size_t)nf * 2 * kHist * 8);
+    CGK_TRY(m->ws_small.ensure(4096 + align_up((size_t)nf * 3 * G * 8) + 64 * sizeof(TScal) + hist_bytes));
     double *partials = (double *)(m->ws_small.as<char>() + 4096);
     TScal *sc = (TScal *)(m->ws_small.as<char>() + 4096 + align_up((size_t)nf * 3 * G * 8));
+    double *hist = (double *)(m->ws_small.as<char>() + 4096 + align_up((size_t)nf * 3 * G * 8) +
+                              64 * sizeof(TScal));
     CGK_CUDA(cudaMemsetAsync(sc, 0, nf * sizeof(TScal), st));
-    CGK_TRY(m->h_small.ensure(4096 + 64 * sizeof(TScal)));
+    CGK_TRY(m->h_small.ensure(4096 + 64 * sizeof(TScal) + hist_bytes));
     TScal *hsc = (TScal *)(m->h_small.as<char>() + 4096);
+    double *hhist = (double *)(m->h_small.as<char>() + 4096 + 64 * sizeof(TScal));
+    // Inner solver: Jacobi-PCG for the first inner solve of the call, whose coefficients
+    // give a Lanczos estimate of the smallest eigenvalue of D^-1 A; then Chebyshev on
+    // [0.95 estimate, 1 + rho], 1 + rho the Gershgorin bound (rho = dte R / (1 + dte R),
+    // R the largest sum of a cell's transmissibilities over its volume).  sweep_shape 1
+    // keeps PCG throughout, and so does BF16 storage: the three-term recurrence stored
+    // with an 8-bit significand stalls above the inner tolerance.
+    const bool want_cheb = p->sweep_shape != 1 && sizeof(TS) == 4;
+    const double rho_g = o.dte * m->tet.max_rate / (1.0 + o.dte * m->tet.max_rate);
+    ChebSchedule cheb;
+    bool have_cheb = false, tried_cheb = false;
     const int max_rounds = p->max_rounds > 0 ? p->max_rounds : 12;
     const int max_inner = p->max_iter;
     const double rb32 = row_bytes(4);
@@ -1112,7 +1222,24 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
         int rounds = 0;
         converged = false;
         while (rounds < max_rounds) {
+            TS *dsol = D;
+            if (have_cheb) {
+            // inner Chebyshev on A d = r, from d = 0: d_1, then one pass per iteration
+            CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * nf * (8 + 2.0 * sizeof(TS)), st,
+                       (k_tcheb<TS, true><<<grid, kThreads, 0, st>>>(o, Rin, nullptr, nullptr, Cb[1], cheb.c0, 0.f)));
+            const int mi = cheb.iterations();
+            for (int k = 1; k < mi; ++k)
+                CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * nf * (rb32 + 4.0 * sizeof(TS)),
+                           st, (k_tcheb<TS, false><<<grid, kThreads, 0, st>>>(
+                                   o, Rin, Cb[k % 3], k == 1 ? nullptr : Cb[(k - 1) % 3], Cb[(k + 1) % 3],
+                                   cheb.c1[k - 1], cheb.c2[k - 1])));
+            CGK_CUDA(cudaGetLastError());
+            dsol = Cb[mi % 3];
+            applications += mi - 1;
+            } else {
             // inner Jacobi-PCG on A d = r in FP32 (TS storage), from d = 0
+            double *hst = (want_cheb && !tried_cheb) ? hist : nullptr;
+            tried_cheb = tried_cheb || hst;
             int it = 0;
             bool inner_done = false;
             while (!inner_done && it < max_inner) {
@@ -1120,11 +1247,11 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass1_bf16" : "tin_pass1_fp32",
                                (double)n * nf * (rb32 + 4.0 * sizeof(TS)), st,
                                k_tin_pass1<TS><<<grid, kThreads, 0, st>>>(
-                                   o, Z, Pp[it & 1], Pp[(it + 1) & 1], Q, partials, sc));
+                                   o, Z, Pp[it & 1], Pp[(it + 1) & 1], Q, partials, sc, hst));
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass2_bf16" : "tin_pass2_fp32",
                                (double)n * nf * (16 + 7.0 * sizeof(TS)), st,
                                k_tin_pass2<TS><<<grid, kThreads, 0, st>>>(
-                                   o, Pp[(it + 1) & 1], Q, D, Rin, Z, partials, sc, eps_in * eps_in));
+                                   o, Pp[(it + 1) & 1], Q, D, Rin, Z, partials, sc, eps_in * eps_in, hst));
                 }
                 CGK_CUDA(cudaGetLastError());
                 CGK_CUDA(cudaMemcpyAsync(hsc, sc, nf * sizeof(TScal), cudaMemcpyDeviceToHost, st));
@@ -1135,14 +1262,30 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             int used = 0;
             for (int f = 0; f < nf; ++f) used = std::max(used, hsc[f].iters);
             applications += used;
+            if (hst) {   // the spectrum estimate from this solve's coefficients
+                CGK_CUDA(cudaMemcpyAsync(hhist, hist, (size_t)nf * 2 * kHist * 8, cudaMemcpyDeviceToHost, st));
+                CGK_CUDA(cudaStreamSynchronize(st));
+                double est = 2.0;
+                bool ok = true;
+                for (int f = 0; f < nf && ok; ++f) {
+                    const int mf = std::min(hsc[f].iters, kHist);
+                    if (hsc[f].breakdown || mf < 4) ok = false;
+                    else est = std::min(est, lanczos_min(hhist + (size_t)f * 2 * kHist,
+                                                         hhist + (size_t)f * 2 * kHist + kHist, mf));
+                }
+                const double a = ok ? std::max(0.95 * est, 1.0 - rho_g) : 1.0 - rho_g;
+                cheb = cheb_schedule(a, 1.0 + rho_g, eps_in);
+                have_cheb = cheb.iterations() <= max_inner;   // else PCG stays cheaper
+            }
+            }
             // x += d, new FP64 residual, start of the next inner solve
             double *xnext = (xcur == F1) ? F2 : F1;
             CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) * 5 + 16), st,
                        (k_trefine<TS, false><<<grid, kThreads, 0, st>>>(
-                           o, p->scheme, xcur, D, ubuf, B, xnext, nullptr, Rin, Z, Pp[0], partials,
+                           o, p->scheme, xcur, dsol, ubuf, B, xnext, nullptr, Rin, Z, Pp[0], partials,
                            sc)));
             CGK_CUDA(cudaGetLastError());
-            CGK_CUDA(cudaMemsetAsync(D, 0, (size_t)n * nf * sizeof(TS), st));
+            if (!have_cheb) CGK_CUDA(cudaMemsetAsync(D, 0, (size_t)n * nf * sizeof(TS), st));
             applications += 1;
             ++rounds;
             xcur = xnext;

@@ -97,9 +97,9 @@ def test_hex_locate_and_deposit_bit_exact(cg, orc, case):
         assert np.array_equal(bits(d), bits(eps))
 
 
-@pytest.mark.parametrize("precision,bar", [(0, 1e-10), (1, 1e-6), (3, 1e-6)])
+@pytest.mark.parametrize("precision,bar,shape", [(0, 1e-10, 0), (1, 1e-6, 0), (3, 1e-6, 0), (1, 1e-6, 1)])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_hex_diffuse_parity_and_frozen_cells(cg, orc, case, precision, scheme, bar):
+def test_hex_diffuse_parity_and_frozen_cells(cg, orc, case, precision, scheme, bar, shape):
     xf, yf, zf, D, frozen, mesh = case
     vc, rp, col, val = orc.hex_build(xf, yf, zf, D)
     rng = np.random.default_rng(92)
@@ -108,8 +108,8 @@ def test_hex_diffuse_parity_and_frozen_cells(cg, orc, case, precision, scheme, b
     T = 0.004
     ref, _ = orc.diffuse_csr(u0, vc, rp, col, val, T, 10, scheme=scheme, tol=1e-15)
     u = dev(u0)
-    _, rep = cg.diffuse(mesh, u, cg.Params(T=T, nsteps=10, scheme=scheme, precision=precision),
-                        report=True)
+    _, rep = cg.diffuse(mesh, u, cg.Params(T=T, nsteps=10, scheme=scheme, precision=precision,
+                                           sweep_shape=shape), report=True)
     got = u.cpu().numpy()
     assert maxrel(got, ref) <= bar
     assert np.array_equal(bits(got[:, frozen]), bits(u0[:, frozen]))     # D = 0: PCM kept

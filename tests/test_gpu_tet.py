@@ -85,9 +85,11 @@ def test_tet_deposit_bit_exact(cg, orc, small_mesh, mode):
     assert np.array_equal(bits(got), bits(ref))
 
 
-@pytest.mark.parametrize("precision,bar", [(0, 1e-10), (1, 1e-6), (2, 1e-6)])
+# inner solver of the mixed modes: 0 = Chebyshev after a PCG spectrum estimate, 1 = PCG
+@pytest.mark.parametrize("precision,bar,shape", [(0, 1e-10, 0), (1, 1e-6, 0), (2, 1e-6, 0),
+                                                 (1, 1e-6, 1), (2, 1e-6, 1)])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_tet_diffuse_parity(cg, orc, small_mesh, scheme, precision, bar):
+def test_tet_diffuse_parity(cg, orc, small_mesh, scheme, precision, bar, shape):
     xyz, tets, mesh = small_mesh
     vc, cent, rp, col, val = orc.tet_build(xyz, tets)
     nt = len(vc)
@@ -100,7 +102,7 @@ def test_tet_diffuse_parity(cg, orc, small_mesh, scheme, precision, bar):
     ref, _ = orc.diffuse_csr(u0, vc, rp, col, val, T, 10, scheme=scheme, tol=1e-15)
     u = dev(u0)
     _, rep = cg.diffuse(mesh, u, cg.Params(bandwidth=b, nsteps=10, scheme=scheme,
-                                           precision=precision), report=True)
+                                           precision=precision, sweep_shape=shape), report=True)
     got = u.cpu().numpy()
     assert maxrel(got, ref) <= bar
     assert rep["final_rel_residual"] <= 1e-13
@@ -148,3 +150,6 @@ def test_tet_full_size_layered(cg, orc):
     assert m.min() >= -1e-12 * m.max()
     f64 = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=0.03, nsteps=10, precision=0))
     assert maxrel(m, f64.cpu().numpy()) <= 1e-6
+    pcg = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=0.03, nsteps=10, precision=1,
+                                                    sweep_shape=1))    # PCG inner solves
+    assert maxrel(pcg.cpu().numpy(), f64.cpu().numpy()) <= 1e-6
