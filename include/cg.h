@@ -162,7 +162,10 @@ typedef struct {
                            each round's inner solve in one cooperative launch that keeps
                            the mesh in the SMs' shared memory (one field, nx % 4 == 0, a
                            mesh that fits; the autotuner also weighs it).  Batched calls:
-                           z planes per work item (0 = autotuned per batch shape) */
+                           z planes per work item (0 = autotuned per batch shape).  Tet
+                           and stretched meshes, FP32 storage: 0 = Chebyshev inner
+                           solves on a spectrum estimated from the call's first PCG
+                           solve, 1 = Jacobi-PCG throughout (BF16 storage: always PCG) */
     long long barrier_budget; /* > 0: run each structured inner solve as one persistent
                                  cooperative launch whose grid barriers give up after this
                                  many clock cycles of waiting (then CG_ETIMEOUT); with
