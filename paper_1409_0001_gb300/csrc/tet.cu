@@ -652,31 +652,45 @@ __global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__rest
 // Inner Chebyshev iteration on the Jacobi-scaled system D^-1 A d = D^-1 r (FP32
 // arithmetic, TS storage), spectrum enclosed in [theta - delta, theta + delta]: from
 // d_0 = 0, d_1 = c0 D^-1 r; then d_{k+1} = d_k + c1 (d_k - d_{k-1}) + c2 D^-1 (r - A d_k)
-// (dkm1 null: d_0 = 0).  No inner products, one pass per iteration.  A thread reads a
-// cell's operator row once and applies it to all nf fields.
-template <class TS, bool kFirst, bool kOneField>
-__global__ void __launch_bounds__(kThreads, kOneField ? 8 : 4) k_tcheb(Op o, int nf,
-                        const TS *__restrict__ r_all, const TS *__restrict__ dk_all,
-                        const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all, float c1, float c2) {
+// (dkm1 null: d_0 = 0).  No inner products, one pass per iteration.  This form handles
+// one field (the launch's y index picks it); k_tcheb below handles several.
+template <class TS>
+__global__ void k_tcheb1(Op o, const TS *__restrict__ r_all, const TS *__restrict__ dk_all,
+                         const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all, float c1, float c2) {
+    const size_t off = (size_t)blockIdx.y * o.n;
+    const TS *r = r_all + off;
+    const float dte = (float)o.dte;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        const TS *dk = dk_all + off;
+        const float dkk = ldf(dk, k);
+        float off_sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < kMaxSlots; ++q) {
+            if (q >= o.ns) break;
+            const size_t e = (size_t)q * o.n + k;
+            off_sum += o.offv32[e] * ldf(dk, o.offc[e]);
+        }
+        const float res = ldf(r, k) - (o.adiag32[k] * dkk - dte * off_sum);
+        const float dm = dkm1_all ? ldf(dkm1_all + off, k) : 0.f;   // d_0 = 0
+        stf(dn_all, off + k, dkk + c1 * (dkk - dm) + c2 * (o.iadiag32[k] * res));
+    }
+}
+
+// The same iteration for nf fields (and the first step, d_1 = c1 D^-1 r, for any nf): a
+// thread reads a cell's operator row once and applies it to every field.  The
+// one-field loop above keeps more gathers in flight when there is only one.
+template <class TS, bool kFirst>
+__global__ void __launch_bounds__(kThreads, 4) k_tcheb(Op o, int nf, const TS *__restrict__ r_all,
+                                                        const TS *__restrict__ dk_all,
+                                                        const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all,
+                                                        float c1, float c2) {
     const float dte = (float)o.dte;
     const size_t n = (size_t)o.n;
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
         if constexpr (kFirst) {
             const float iad = o.iadiag32[k];
             for (int f = 0; f < nf; ++f) stf(dn_all, f * n + k, c1 * (iad * ldf(r_all, f * n + k)));
-        } else if constexpr (kOneField) {   // one field: fewer registers, more loads in flight
-            const float dkk = ldf(dk_all, k);
-            float off_sum = 0.f;
-#pragma unroll
-            for (int q = 0; q < kMaxSlots; ++q) {
-                if (q >= o.ns) break;
-                const size_t e = (size_t)q * n + k;
-                off_sum += o.offv32[e] * ldf(dk_all, o.offc[e]);
-            }
-            const float res = ldf(r_all, k) - (o.adiag32[k] * dkk - dte * off_sum);
-            const float dm = dkm1_all ? ldf(dkm1_all, k) : 0.f;   // d_0 = 0
-            stf(dn_all, k, dkk + c1 * (dkk - dm) + c2 * (o.iadiag32[k] * res));
-        } else {   // several fields: the cell's operator row is read once for all of them
+        } else {   // the cell's operator row is read once for all fields
             int nb[kMaxSlots];
             float wv[kMaxSlots];
 #pragma unroll
@@ -696,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, kOneField ? 8 : 4) k_tcheb(Op o, int
                     off_sum += wv[q] * ldf(dk, nb[q]);
                 }
                 const float res = ldf(r_all, f * n + k) - (ad * dkk - dte * off_sum);
-                const float dm = dkm1_all ? ldf(dkm1_all, f * n + k) : 0.f;
+                const float dm = dkm1_all ? ldf(dkm1_all, f * n + k) : 0.f;   // d_0 = 0
                 stf(dn_all, f * n + k, dkk + c1 * (dkk - dm) + c2 * (iad * res));
             }
         }
@@ -1250,19 +1264,19 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             // bytes: the operator row (slots, diagonal, its reciprocal) once per cell, then
             // per field r, d_k, d_{k-1} and d_{k+1}
             CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (4 + nf * 2.0 * sizeof(TS)), st,
-                       (k_tcheb<TS, true, false><<<G, kThreads, 0, st>>>(o, nf, Rin, nullptr, nullptr, Cb[1],
+                       (k_tcheb<TS, true><<<G, kThreads, 0, st>>>(o, nf, Rin, nullptr, nullptr, Cb[1],
                                                                               cheb.c0, 0.f)));
             const int mi = cheb.iterations();
             for (int k = 1; k < mi; ++k) {
                 const TS *dm = k == 1 ? nullptr : Cb[(k - 1) % 3];
                 if (nf == 1)
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (rb32 - 8 + 4.0 * sizeof(TS)),
-                               st, (k_tcheb<TS, false, true><<<G, kThreads, 0, st>>>(
-                                       o, nf, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1])));
+                               st, (k_tcheb1<TS><<<G, kThreads, 0, st>>>(
+                                       o, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1])));
                 else
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32",
                                (double)n * (rb32 - 8 + nf * 4.0 * sizeof(TS)), st,
-                               (k_tcheb<TS, false, false><<<G, kThreads, 0, st>>>(
+                               (k_tcheb<TS, false><<<G, kThreads, 0, st>>>(
                                    o, nf, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1])));
             }
             CGK_CUDA(cudaGetLastError());
