@@ -159,6 +159,8 @@ struct cg_mesh {
     std::vector<std::pair<std::vector<double>, int>> brounds;  // batched rounds per call signature
     std::vector<cgk::GraphEntry> graphs;      // captured diffusions
     std::vector<cgk::RoundsEntry> rounds;     // learned refinement schedules
+    std::vector<std::pair<double, double>> spectrum;   // unstructured: lower end of the
+                                                       // Chebyshev interval per dte
     cudaStream_t capture_stream = nullptr;    // private stream used only for capture
 };
 

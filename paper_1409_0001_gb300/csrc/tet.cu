@@ -649,6 +649,50 @@ __global__ void k_tin_pass2(Op o, const TS *__restrict__ p_all, const TS *__rest
     }
 }
 
+// Start of the spectrum probe: an inner PCG solve (field 0) on a fixed right-hand side,
+// r_k uniform in [-1/2, 1/2) from the 32-bit finaliser of MurmurHash3 (Appleby) applied
+// to k, so the estimate depends on the operator alone.  Sets r, z = D^-1 r, p = z, d = 0
+// and the solve's scalars as k_trefine does for a real solve (bb untouched).
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+template <class TS>
+__global__ void k_tprobe_init(Op o, TS *__restrict__ rin, TS *__restrict__ z, TS *__restrict__ p,
+                              TS *__restrict__ d, double *__restrict__ partials, TScal *__restrict__ sc) {
+    double rr = 0, rz = 0;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
+        const float rf = (float)(mix32((uint32_t)k) >> 8) * 0x1p-24f - 0.5f;
+        const float zf = rf * o.iadiag32[k];
+        stf(rin, k, rf);
+        stf(z, k, zf);
+        stf(p, k, zf);
+        stf(d, k, 0.f);
+        rr += (double)rf * rf;
+        rz += (double)rf * zf;
+    }
+    double v[2] = {block_sum(rr), block_sum(rz)};
+    if (arrive(partials, 2, v, blockIdx.x, gridDim.x, &sc[0].ticket)) {
+        const double RR = finish_sum(partials, 0, gridDim.x), RZ = finish_sum(partials, 1, gridDim.x);
+        if (is_thread0()) {
+            TScal &S = sc[0];
+            S.rr = RR;
+            S.rr0 = RR;
+            S.rz = RZ;
+            S.beta = 0;
+            S.iters = 0;
+            S.breakdown = 0;
+            S.done = 0;
+            S.ticket = 0;
+        }
+    }
+}
+
 // Inner Chebyshev iteration on the Jacobi-scaled system D^-1 A d = D^-1 r (FP32
 // arithmetic, TS storage), spectrum enclosed in [theta - delta, theta + delta]: from
 // d_0 = 0, d_1 = c0 D^-1 r; then d_{k+1} = d_k + c1 (d_k - d_{k-1}) + c2 D^-1 (r - A d_k)
@@ -1229,16 +1273,16 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     CGK_TRY(m->h_small.ensure(4096 + 64 * sizeof(TScal) + hist_bytes));
     TScal *hsc = (TScal *)(m->h_small.as<char>() + 4096);
     double *hhist = (double *)(m->h_small.as<char>() + 4096 + 64 * sizeof(TScal));
-    // Inner solver: Jacobi-PCG for the first inner solve of the call, whose coefficients
-    // give a Lanczos estimate of the smallest eigenvalue of D^-1 A; then Chebyshev on
-    // [0.95 estimate, 1 + rho], 1 + rho the Gershgorin bound (rho = dte R / (1 + dte R),
-    // R the largest sum of a cell's transmissibilities over its volume).  sweep_shape 1
-    // keeps PCG throughout, and so does BF16 storage: the three-term recurrence stored
-    // with an 8-bit significand stalls above the inner tolerance.
+    // Inner solver: Chebyshev on [a, 1 + rho], 1 + rho the Gershgorin bound (rho =
+    // dte R / (1 + dte R), R the largest sum of a cell's transmissibilities over its
+    // volume) and a from a probe (below), so every inner solve of every call is the same
+    // fixed polynomial for this mesh and dte.  sweep_shape 1 keeps Jacobi-PCG throughout,
+    // and so does BF16 storage: the three-term recurrence stored with an 8-bit
+    // significand stalls above the inner tolerance.
     const bool want_cheb = p->sweep_shape != 1 && sizeof(TS) == 4;
     const double rho_g = o.dte * m->tet.max_rate / (1.0 + o.dte * m->tet.max_rate);
     ChebSchedule cheb;
-    bool have_cheb = false, tried_cheb = false;
+    bool have_cheb = false;
     const int max_rounds = p->max_rounds > 0 ? p->max_rounds : 12;
     const int max_inner = p->max_iter;
     const double rb32 = row_bytes(4);
@@ -1246,6 +1290,43 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     double worst = 0;
     double *ubuf = cells, *F1 = X1, *F2 = X2;
     bool converged = true;
+    if (want_cheb) {
+        // the lower end of the Chebyshev interval for this dte: remembered per mesh, else
+        // from a PCG probe solve on a fixed right-hand side (Lanczos estimate of the
+        // smallest eigenvalue of D^-1 A, taken 5 % lower; never below Gershgorin's)
+        double a = -1.0;
+        for (const auto &e : m->spectrum)
+            if (e.first == o.dte) a = e.second;
+        if (a < 0) {
+            CGK_LAUNCH("tprobe_init", (double)n * (8 + 4.0 * sizeof(TS)), st,
+                       k_tprobe_init<TS><<<G, kThreads, 0, st>>>(o, Rin, Z, Pp[0], D, partials, sc));
+            int it = 0;
+            bool done = false;
+            while (!done && it < std::min(max_inner, kHist)) {
+                for (int c = 0; c < 8; ++c, ++it) {
+                    CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass1_bf16" : "tin_pass1_fp32", (double)n * (rb32 + 4.0 * sizeof(TS)),
+                               st, k_tin_pass1<TS><<<G, kThreads, 0, st>>>(o, Z, Pp[it & 1], Pp[(it + 1) & 1], Q,
+                                                                            partials, sc, hist));
+                    CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass2_bf16" : "tin_pass2_fp32", (double)n * (16 + 7.0 * sizeof(TS)),
+                               st, k_tin_pass2<TS><<<G, kThreads, 0, st>>>(o, Pp[(it + 1) & 1], Q, D, Rin, Z, partials,
+                                                                            sc, eps_in * eps_in, hist));
+                }
+                CGK_CUDA(cudaGetLastError());
+                CGK_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(TScal), cudaMemcpyDeviceToHost, st));
+                CGK_CUDA(cudaStreamSynchronize(st));
+                done = hsc[0].done;
+            }
+            // (setup of the inner solver: not counted as cell-updates of the fields)
+            CGK_CUDA(cudaMemcpyAsync(hhist, hist, 2 * kHist * 8, cudaMemcpyDeviceToHost, st));
+            CGK_CUDA(cudaStreamSynchronize(st));
+            const int mh = std::min(hsc[0].iters, kHist);
+            a = 1.0 - rho_g;
+            if (!hsc[0].breakdown && mh >= 4) a = std::max(0.95 * lanczos_min(hhist, hhist + kHist, mh), a);
+            if (m->spectrum.size() < 64) m->spectrum.emplace_back(o.dte, a);
+        }
+        cheb = cheb_schedule(a, 1.0 + rho_g, eps_in);
+        have_cheb = cheb.iterations() <= max_inner;   // else PCG stays cheaper
+    }
     int s = 0;
     for (; s < p->nsteps; ++s) {
         CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 4 * sizeof(TS)), st,
@@ -1284,8 +1365,6 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             applications += mi - 1;
             } else {
             // inner Jacobi-PCG on A d = r in FP32 (TS storage), from d = 0
-            double *hst = (want_cheb && !tried_cheb) ? hist : nullptr;
-            tried_cheb = tried_cheb || hst;
             int it = 0;
             bool inner_done = false;
             while (!inner_done && it < max_inner) {
@@ -1293,11 +1372,11 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass1_bf16" : "tin_pass1_fp32",
                                (double)n * nf * (rb32 + 4.0 * sizeof(TS)), st,
                                k_tin_pass1<TS><<<grid, kThreads, 0, st>>>(
-                                   o, Z, Pp[it & 1], Pp[(it + 1) & 1], Q, partials, sc, hst));
+                                   o, Z, Pp[it & 1], Pp[(it + 1) & 1], Q, partials, sc, nullptr));
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tin_pass2_bf16" : "tin_pass2_fp32",
                                (double)n * nf * (16 + 7.0 * sizeof(TS)), st,
                                k_tin_pass2<TS><<<grid, kThreads, 0, st>>>(
-                                   o, Pp[(it + 1) & 1], Q, D, Rin, Z, partials, sc, eps_in * eps_in, hst));
+                                   o, Pp[(it + 1) & 1], Q, D, Rin, Z, partials, sc, eps_in * eps_in, nullptr));
                 }
                 CGK_CUDA(cudaGetLastError());
                 CGK_CUDA(cudaMemcpyAsync(hsc, sc, nf * sizeof(TScal), cudaMemcpyDeviceToHost, st));
@@ -1308,21 +1387,6 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             int used = 0;
             for (int f = 0; f < nf; ++f) used = std::max(used, hsc[f].iters);
             applications += used;
-            if (hst) {   // the spectrum estimate from this solve's coefficients
-                CGK_CUDA(cudaMemcpyAsync(hhist, hist, (size_t)nf * 2 * kHist * 8, cudaMemcpyDeviceToHost, st));
-                CGK_CUDA(cudaStreamSynchronize(st));
-                double est = 2.0;
-                bool ok = true;
-                for (int f = 0; f < nf && ok; ++f) {
-                    const int mf = std::min(hsc[f].iters, kHist);
-                    if (hsc[f].breakdown || mf < 4) ok = false;
-                    else est = std::min(est, lanczos_min(hhist + (size_t)f * 2 * kHist,
-                                                         hhist + (size_t)f * 2 * kHist + kHist, mf));
-                }
-                const double a = ok ? std::max(0.95 * est, 1.0 - rho_g) : 1.0 - rho_g;
-                cheb = cheb_schedule(a, 1.0 + rho_g, eps_in);
-                have_cheb = cheb.iterations() <= max_inner;   // else PCG stays cheaper
-            }
             }
             // x += d, new FP64 residual, start of the next inner solve
             double *xnext = (xcur == F1) ? F2 : F1;

@@ -153,3 +153,23 @@ def test_tet_full_size_layered(cg, orc):
     pcg = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=0.03, nsteps=10, precision=1,
                                                     sweep_shape=1))    # PCG inner solves
     assert maxrel(pcg.cpu().numpy(), f64.cpu().numpy()) <= 1e-6
+
+
+def test_tet_mixed_results_do_not_depend_on_call_history(cg, small_mesh):
+    """The Chebyshev interval comes from a probe on a fixed right-hand side and is
+    remembered per mesh and dtau, so a call gives the same bits on a fresh mesh and on a
+    mesh that has already smoothed other fields with other step sizes."""
+    import torch
+    xyz, tets, _ = small_mesh
+    a, b = cg.TetMesh(xyz, tets), cg.TetMesh(xyz, tets)
+    rng = np.random.default_rng(26)
+    x = dev(rng.random((1, a.ncells)))
+    y = dev(rng.random((2, a.ncells)) - 0.3)
+    p = cg.Params(bandwidth=0.3, nsteps=10, precision=1)
+    cg.diffuse(a, x.clone(), cg.Params(bandwidth=0.2, nsteps=5, precision=1))
+    cg.diffuse(a, x.clone(), p)
+    ya, yb, yc = y.clone(), y.clone(), y.clone()
+    cg.diffuse(a, ya, p)
+    cg.diffuse(b, yb, p)
+    cg.diffuse(b, yc, p)
+    assert torch.equal(ya, yb) and torch.equal(yb, yc)
