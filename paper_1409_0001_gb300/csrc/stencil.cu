@@ -20,6 +20,7 @@
 //    iteration, whose spectrum bounds are known in closed form on this mesh:
 //    lambda(A) lies in [1, 1 + 4 c sum_axes sin^2(pi (n-1) / (2n))] (DCT-II
 //    eigenvalues).  Chebyshev needs no inner products, only stencil sweeps.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -1614,6 +1615,7 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
 constexpr int kResidentThreads = 1024;
 constexpr int kResidentMaxIters = 128;
 constexpr int kResidentCode = 300;   // sweep_shape of the resident inner solve
+constexpr int kTmaCode = 400;        // sweep_shape 400 + z: TMA-staged sweep, z planes per block
 
 // The m-1 Chebyshev iterations of one refinement round with the iterates held in shared
 // memory, for a mesh whose two iterates fit in the SMs' shared memory (one field,
@@ -2149,6 +2151,190 @@ Coef32 coef32(double ce) {
     return c;
 }
 
+// ---------------------------------------------------------------- TMA-staged sweep
+// The vectorised Chebyshev iteration with its planes staged by the Tensor Memory
+// Accelerator: one thread issues, per plane, 2D tile copies (cp.async.bulk.tensor) of
+// y_k with a one-row and four-column halo (136 x 10 floats), y_{k-1} and r (128 x 8
+// each) into a ring of kTmaStages shared-memory stages, each completing on its own
+// mbarrier; the block reads planes z-1, z and z+1 of y_k from the ring, so no thread
+// spends registers or address arithmetic on prefetching.  Cells outside the mesh come
+// back as zeros from the copy (zero flux: they add nothing and are not counted).  The
+// arithmetic is the vectorised tile's, term for term, so the results are the same bits.
+// Waits are bounded by `budget` clock cycles; a wait that gives up sets *err and the
+// block finishes without its copies in flight.
+constexpr int kTmaStages = 4;
+constexpr int kTmaW = 4 * TX + 8;                              // 136 floats per halo row
+constexpr int kTmaYBytes = (TY + 2) * kTmaW * 4;               // 5440
+constexpr int kTmaYSlot = (kTmaYBytes + 127) / 128 * 128;      // 5504
+constexpr int kTmaTBytes = TY * 4 * TX * 4;                    // 4096 (y_{k-1}, r)
+constexpr int kTmaStageBytes = kTmaYSlot + 2 * kTmaTBytes;     // 13696
+constexpr int kTmaSmem = kTmaStages * kTmaStageBytes;          // 54784
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                          int c3, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long budget) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_cheb_tma(Geo g, int zlen, int nzc, Coef32 cf, float gamma,
+                                                       float omega, const __grid_constant__ CUtensorMap ty_map,
+                                                       const __grid_constant__ CUtensorMap tp_map,
+                                                       const __grid_constant__ CUtensorMap tr_map, int has_yp,
+                                                       float *ynext_all, int *err, long long budget) {
+    chain_wait();
+    chain_release();
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    __shared__ __align__(8) unsigned long long bar[kTmaStages];
+    __shared__ float sdg[8];
+    __shared__ int abort_flag;
+    const int f = nzc == (int)gridDim.z ? 0 : (int)blockIdx.z / nzc;
+    const int z0 = ((int)blockIdx.z - f * nzc) * zlen;
+    const int z1 = min(g.nz, z0 + zlen);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool leader = tx == 0 && ty == 0;
+    const int x0 = blockIdx.x * (4 * TX), yb0 = blockIdx.y * TY;
+    const int x = x0 + 4 * tx, y = yb0 + ty;
+    const bool own = (x < g.nx) && (y < g.ny);
+    const int nyb = (y > 0) + (y + 1 < g.ny);
+    const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx), n12 = nyb + 2;
+    const unsigned sbase = smem_u32(tma_smem), bbase = smem_u32(bar);
+    const int nload = (z1 - z0) + 2;   // planes z0-1 .. z1 (outside the mesh: zeros)
+    const unsigned tbytes = kTmaYBytes + (has_yp ? 2 : 1) * kTmaTBytes;
+    if (leader) {
+        for (int s = 0; s < kTmaStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bbase + 8 * s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    stage_table(sdg, cf.dg);
+    __syncthreads();
+    // plane z0 - 1 + j into stage j % kTmaStages (leader only)
+    auto issue = [&](int j) {
+        const int st = j % kTmaStages, p = z0 - 1 + j;
+        const unsigned b = bbase + 8 * st, d = sbase + st * kTmaStageBytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(tbytes) : "memory");
+        tma_load4(d, &ty_map, x0 - 4, yb0 - 1, p, f, b);
+        if (has_yp) tma_load4(d + kTmaYSlot, &tp_map, x0, yb0, p, f, b);
+        tma_load4(d + kTmaYSlot + kTmaTBytes, &tr_map, x0, yb0, p, f, b);
+    };
+    int issued = 0;
+    if (leader)
+        for (; issued < min(kTmaStages, nload); ++issued) issue(issued);
+    int waited = 0;   // stages this thread has waited for
+    bool ok = true;
+    auto wait_upto = [&](int j) {   // planes up to j have landed
+        for (; waited <= j; ++waited)
+            if (ok && !mbar_wait(bbase + 8 * (waited % kTmaStages), (waited / kTmaStages) & 1, budget)) {
+                ok = false;
+                atomicExch(err, 1);
+                abort_flag = 1;
+            }
+    };
+    for (int i = 0; i < z1 - z0; ++i) {
+        const int z = z0 + i;
+        wait_upto(i + 2);
+        const float *ym = reinterpret_cast<const float *>(tma_smem + (i % kTmaStages) * kTmaStageBytes);
+        const unsigned char *cur = tma_smem + ((i + 1) % kTmaStages) * kTmaStageBytes;
+        const float *yc = reinterpret_cast<const float *>(cur);
+        const float *yq = reinterpret_cast<const float *>(tma_smem + ((i + 2) % kTmaStages) * kTmaStageBytes);
+        const float *tp = reinterpret_cast<const float *>(cur + kTmaYSlot);
+        const float *tr = reinterpret_cast<const float *>(cur + kTmaYSlot + kTmaTBytes);
+        const int c = 4 + 4 * tx;   // this thread's first cell in a halo row
+        const float4 vc = *reinterpret_cast<const float4 *>(yc + (ty + 1) * kTmaW + c);
+        const float4 vdn = *reinterpret_cast<const float4 *>(ym + (ty + 1) * kTmaW + c);
+        const float4 vup = *reinterpret_cast<const float4 *>(yq + (ty + 1) * kTmaW + c);
+        const float4 up = *reinterpret_cast<const float4 *>(yc + ty * kTmaW + c);
+        const float4 dn = *reinterpret_cast<const float4 *>(yc + (ty + 2) * kTmaW + c);
+        const float4 ypc = has_yp ? *reinterpret_cast<const float4 *>(tp + ty * 4 * TX + 4 * tx) : f4zero();
+        const float4 rc = *reinterpret_cast<const float4 *>(tr + ty * 4 * TX + 4 * tx);
+        float left = __shfl_up_sync(0xffffffffu, vc.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, vc.x, 1);
+        if (tx == 0) left = yc[(ty + 1) * kTmaW + 3];
+        if (tx == TX - 1) right = yc[(ty + 1) * kTmaW + c + 4];
+        if (own && ok) {
+            const int nz_ = (z > 0) + (z + 1 < g.nz);
+            const float d0 = sdg[n0 + nz_], d12 = sdg[n12 + nz_], d3 = sdg[n3 + nz_];
+            float4 s4;
+            s4.x = left + vc.y + up.x + dn.x + vdn.x + vup.x;
+            s4.y = vc.x + vc.z + up.y + dn.y + vdn.y + vup.y;
+            s4.z = vc.y + vc.w + up.z + dn.z + vdn.z + vup.z;
+            s4.w = vc.z + right + up.w + dn.w + vdn.w + vup.w;
+            float4 o;
+            o.x = fmaf(omega, vc.x - ypc.x + gamma * (rc.x - fmaf(d0, vc.x, -cf.ce * s4.x)), ypc.x);
+            o.y = fmaf(omega, vc.y - ypc.y + gamma * (rc.y - fmaf(d12, vc.y, -cf.ce * s4.y)), ypc.y);
+            o.z = fmaf(omega, vc.z - ypc.z + gamma * (rc.z - fmaf(d12, vc.z, -cf.ce * s4.z)), ypc.z);
+            o.w = fmaf(omega, vc.w - ypc.w + gamma * (rc.w - fmaf(d3, vc.w, -cf.ce * s4.w)), ypc.w);
+            *reinterpret_cast<float4 *>(ynext_all + (size_t)f * g.n + (size_t)y * g.nx + x +
+                                        (size_t)z * g.nxy) = o;
+        }
+        __syncthreads();   // stage i is no longer read: refill it with plane i + kTmaStages
+        if (abort_flag) break;
+        if (leader && issued < nload) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(issued++);
+        }
+    }
+    if (abort_flag && leader)   // let the copies still in flight land before the block ends
+        for (int j = max(0, issued - kTmaStages); j < issued; ++j)
+            mbar_wait(bbase + 8 * (j % kTmaStages), (j / kTmaStages) & 1, budget);
+}
+
+// Tensor maps of the TMA-staged sweep: a field-major [nf][nz][ny][nx] FP32 array as a 4D
+// tensor (x fastest), box 136 x 10 (halo) or 128 x 8 (tile), zeros outside.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tma_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+        tried = true;
+    }
+    return fn;
+}
+
+bool tma_sweep_fits(const Geo &g) { return g.nx % 4 == 0 && g.per == 0 && tma_encoder() != nullptr; }
+
+bool tma_map(CUtensorMap *map, const Geo &g, int nf, const float *base, bool halo) {
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nf};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nxy * 4, (cuuint64_t)g.n * 4};
+    const cuuint32_t box[4] = {halo ? (cuuint32_t)kTmaW : (cuuint32_t)(4 * TX), halo ? (cuuint32_t)(TY + 2) : (cuuint32_t)TY,
+                               1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return tma_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+__device__ int g_tma_err;   // set by a TMA-staged sweep whose wait gave up
+constexpr long long kTmaBudget = 4000000000LL;   // clock cycles (about two seconds)
+
 // Chebyshev iteration count for a residual reduction eps on spectrum [1, lmax].
 int cheb_iters(double lmax, double eps) {
     if (lmax <= 1.0 + 1e-12) return 1;
@@ -2175,6 +2361,67 @@ void launch_chain(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t 
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// One launch of the TMA-staged sweep (FP32 storage): zlen planes per block.  The tensor
+// maps are encoded for this launch's buffers (inside a captured graph they are part of
+// the recorded parameters).  A map that cannot be encoded runs the vectorised kernel,
+// which computes the same bits.
+// Per host thread: the device address of the error word, once the kernel's shared
+// memory limit is raised (tma_prepare, called before any stream capture).
+static thread_local int *t_tma_errp = nullptr;
+void tma_prepare() {
+    if (t_tma_errp) return;
+    int *p = nullptr;
+    if (cudaFuncSetAttribute(k_cheb_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem) == cudaSuccess &&
+        cudaGetSymbolAddress((void **)&p, g_tma_err) == cudaSuccess)
+        t_tma_errp = p;
+    else
+        cudaGetLastError();
+}
+
+template <class TS>
+void launch_cheb_tma(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, float omega,
+                     const TS *y, const TS *yp, const TS *r, TS *yn, cudaStream_t st) {
+    const int nzc = (g.nz + zlen - 1) / zlen;
+    const dim3 grid((g.nx + 4 * TX - 1) / (4 * TX), (g.ny + TY - 1) / TY, nzc * nf);
+    if constexpr (std::is_same<TS, float>::value) {
+        int *errp = t_tma_errp;
+        CUtensorMap my, mp, mr;
+        if (errp && tma_sweep_fits(g) && tma_map(&my, g, nf, y, true) && tma_map(&mr, g, nf, r, false) &&
+            tma_map(&mp, g, nf, yp ? yp : r, false)) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = dim3(TX, TY);
+            cfg.dynamicSmemBytes = kTmaSmem;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, k_cheb_tma, g, zlen, nzc, cf, gamma, omega, my, mp, mr, yp ? 1 : 0,
+                               (float *)yn, errp, kTmaBudget);
+            return;
+        }
+    }
+    launch_chain(k_cheb_v4<TS>, grid, dim3(TX, TY), st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
+}
+
+// The TMA wait error word: returns (and clears) whether a TMA-staged sweep gave up a wait.
+bool tma_wait_failed(cudaStream_t st) {
+    int h = 0;
+    if (cudaMemcpyFromSymbolAsync(&h, g_tma_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (h) {
+        const int zero = 0;
+        cudaMemcpyToSymbolAsync(g_tma_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    return h != 0;
+}
+
 // One Chebyshev iteration launch in a tuned shape: code > 0 = register-blocked engine
 // with ZB = code planes per block, code < 0 = z-marching engine with -code planes per
 // block.
@@ -2183,7 +2430,9 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
                  const TS *y, const TS *yp, const TS *r, TS *yn, cudaStream_t st) {
     const dim3 blk(TX, TY);
     const int gx = (g.nx + TX - 1) / TX, gy = (g.ny + TY - 1) / TY;
-    if (code >= 100) {
+    if (code >= kTmaCode) {
+        launch_cheb_tma<TS>(code - kTmaCode, g, nf, cf, gamma, omega, y, yp, r, yn, st);
+    } else if (code >= 100) {
         const int zlen = code - 100;
         const int nzc = (g.nz + zlen - 1) / zlen;
         const dim3 grid((g.nx + 4 * TX - 1) / (4 * TX), gy, nzc * nf);
@@ -2486,6 +2735,10 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     for (int c : {101, 102, 104, 108, 116, 2, 4, 8, -1, -4, -16})
         if ((c < 100 || v4) && (g.per == 0 || c < 0))   // periodic axes: z-marching only
             cands.push_back({c, 10});
+    if (sizeof(TS) == 4 && tma_sweep_fits(g)) {        // TMA-staged sweep: FP32 storage
+        tma_prepare();
+        for (int c : {401, 402, 404, 408}) cands.push_back({c, 10});
+    }
     cudaEvent_t e0, e1;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
@@ -2502,7 +2755,7 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int q = 0; q < cand.second; ++q) {
-                if (code >= kPairCode)
+                if (code >= kPairCode && code < kResidentCode)
                     launch_cheb2<TS>(code - kPairCode, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc,
                                      yd, cs);
                 else
@@ -2532,6 +2785,7 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != CG_OK) return rc;
+    if (tma_wait_failed(st)) return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the TMA-staged sweep gave up");
     std::sort(timing.begin(), timing.end());
     int best_code = timing[0].second;
     if (v4) {
@@ -2904,7 +3158,13 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                         kResidentCode, kResidentMaxIters);
         resident = true;
     } else {
-        if (cheb_code >= kPairCode && (!cheb2_fits(g) || cheb_code - kPairCode < 1))
+        if ((cheb_code > kResidentCode && cheb_code < kTmaCode) || cheb_code >= kTmaCode + 100)
+            return fail(CG_EINVAL, "unknown sweep_shape %d", cheb_code);
+        if (cheb_code >= kTmaCode &&
+            (sizeof(TS) != 4 || !tma_sweep_fits(g) || cheb_code - kTmaCode < 1))
+            return fail(CG_EINVAL, "sweep_shape %d needs FP32 inner storage, nx %% 4 == 0, no periodic axis and "
+                        "1..99 planes", cheb_code);
+        if (cheb_code >= kPairCode && cheb_code < kResidentCode && (!cheb2_fits(g) || cheb_code - kPairCode < 1))
             return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0, nx <= 128 and 1..99 planes",
                         cheb_code);
         if (cheb_code >= 100 && cheb_code < kPairCode && (m->nx % 4 != 0 || cheb_code - 100 < 1))
@@ -2919,6 +3179,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                       &resident));
     }
     const int shape_used = resident ? kResidentCode : cheb_code;
+    if (cheb_code >= kTmaCode) tma_prepare();
     // clock cycles a resident wait may take (about one second by default)
     const long long rbudget = (resident && p->barrier_budget > 0) ? p->barrier_budget : 2000000000LL;
 
@@ -3109,6 +3370,8 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             prof_account_replay(*ge);
             if (*herr)
                 return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the resident inner solve gave up");
+            if (cheb_code >= kTmaCode && tma_wait_failed(st))
+                return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the TMA-staged sweep gave up");
             bool ok = true;
             double worst_g = 0.0;
             for (size_t i = 0; i < hist_n; ++i) {
@@ -3204,7 +3467,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                                                                 dim3(coopG), dim3(TX, TY), args, 0,
                                                                 st)));
             }
-            if (m_it > 1 && !persistent && !resident && cheb_code >= kPairCode) {
+            if (m_it > 1 && !persistent && !resident && cheb_code >= kPairCode && cheb_code < kResidentCode) {
                 const int np = (m_it - 1) / 2, ns = (m_it - 1) % 2;
                 CGK_TIMED(loop_, sizeof(TS) == 2 ? "cheb2_bf16" : "cheb2_fp32",
                           (double)n * nf * sizeof(TS) * ((np > 0 ? 4.0 + 5.0 * (np - 1) : 0.0) + 4.0 * ns),
@@ -3305,6 +3568,8 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     if (timed_out)
         return fail(CG_ETIMEOUT, "cg_diffuse: a %s of the inner solve gave up (step %d)",
                     resident ? "neighbour wait" : "grid barrier", s);
+    if (!persistent && !resident && cheb_code >= kTmaCode && tma_wait_failed(st))
+        return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the TMA-staged sweep gave up");
     if (!converged)
         return fail(CG_ENOCONV, "cg_diffuse: refinement did not reach tol in step %d", s);
     return CG_OK;
