@@ -161,7 +161,10 @@ typedef struct {
                            block; -z = z-marching, z planes per block; 300 = resident:
                            each round's inner solve in one cooperative launch that keeps
                            the mesh in the SMs' shared memory (one field, nx % 4 == 0, a
-                           mesh that fits; the autotuner also weighs it).  Batched calls:
+                           mesh that fits; the autotuner also weighs it); 400 + z =
+                           TMA-staged vectorised sweep, z planes per block (FP32 inner
+                           storage, nx % 4 == 0, no periodic axis; same results as
+                           100 + z).  Batched calls:
                            z planes per work item (0 = autotuned per batch shape).  Tet
                            and stretched meshes, FP32 storage: 0 = Chebyshev inner
                            solves on a spectrum estimated from the call's first PCG
