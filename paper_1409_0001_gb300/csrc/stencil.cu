@@ -1870,7 +1870,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
 // after every phase.  Work items (tile x z-chunk x field of one snapshot) are dealt to
 // blocks round-robin; a snapshot whose m_s is smaller than the longest idles in the
 // remaining Chebyshev phases.  Buffer roles are fixed: the first Chebyshev iterate is
-// in Ya and, m_s being even, the correction always ends in Yb; round 1 writes X1, later
+// in Ya and, m_s being even, the correction always ends in Yb; the first round writes X1, later
 // rounds alternate X2/X1, and the last round (R >= 2) writes u^{n+1} over u^n in U
 // (read there only at the cell itself).  Per-item residual partials of each step's
 // last pass (and ||b||^2 partials of its first pass) are stored and reduced afterwards.
