@@ -363,21 +363,27 @@ def main():
                                                         for m, f in zip(main_out, fp64_out))}
     outs = main_out
 
-    # ---------------- end to end: pinned host particles in, the four fields out
+    # ---------------- end to end through the C ABI with host buffers: each of the step's
+    # coarse-grainings copies the pinned host particles in and its field out
+    # (cg_coarse_grain_host, several at a time through cg_coarse_grain_concurrent)
     main_ref = [o.cpu() for o in main_out]
     pos_h = torch.from_numpy(c.pos).pin_memory()
     w_h = torch.from_numpy(c.w).pin_memory()
     out_h = [torch.empty((1, c.ncells), dtype=torch.float64).pin_memory() for _ in B_OVER_DX]
-    pos_d = torch.empty_like(pos_h, device="cuda")
-    w_d = torch.empty_like(w_h, device="cuda")
 
     def e2e_step(reps_e):
-        pos_d.copy_(pos_h, non_blocking=True)
-        w_d.copy_(w_h, non_blocking=True)
-        one_step(MAIN, reps_e, pos_d, w_d)
-        for i in range(len(B_OVER_DX)):
-            out_h[i].copy_(outs[i], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        if a.concurrency > 1:
+            k = len(B_OVER_DX)
+            _, r = cg.coarse_grain_concurrent(meshes, [pos_h] * k, [w_h] * k,
+                                              [params(bdx, MAIN) for bdx in B_OVER_DX], out=out_h,
+                                              streams=streams, max_concurrent=a.concurrency,
+                                              report=True)
+            reps_e.extend(r)
+        else:
+            for i, bdx in enumerate(B_OVER_DX):
+                _, r = cg.coarse_grain_host(meshes[i], pos_h, w_h, params(bdx, MAIN), out=out_h[i],
+                                            report=True)
+                reps_e.append(r)
 
     e2e_step([])
     reps_e = []
@@ -388,7 +394,7 @@ def main():
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_updates = sum_over_ranks(float(sum(r["cell_updates"] for r in reps_e)))
-    h2d = (pos_h.numel() + w_h.numel()) * 8
+    h2d = len(B_OVER_DX) * (pos_h.numel() + w_h.numel()) * 8
     d2h = len(B_OVER_DX) * c.ncells * 8
     e2e_ok = all(bool(torch.equal(o, h)) for o, h in zip(main_ref, out_h))
 
@@ -432,8 +438,10 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": {"value": e2e_updates / e2e_s, "unit": "cell-updates/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "entry_point": "pinned host particles copied in once per step, the step's "
-                                   "coarse-grainings, the four fields copied out",
+                    "entry_point": "cg_coarse_grain_host per bandwidth (pinned host buffers, copies "
+                                   "inside), %s" % ("%d at a time through cg_coarse_grain_concurrent"
+                                                    % a.concurrency if a.concurrency > 1
+                                                    else "one after another"),
                     "result_identical_to_device_run": e2e_ok},
             "gpu_launches": launches,
             "gpu_launches_before_timed": launches_before,

@@ -248,7 +248,9 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
 
 /* Independent coarse-grainings run concurrently: problem i is exactly
  * cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
- * reports ? &reports[i] : NULL, streams[i]) -- same results, bit for bit -- and up to
+ * reports ? &reports[i] : NULL, streams[i]) -- same results, bit for bit -- or, when
+ * cells[i] is host memory, cg_coarse_grain_host with the same arguments (pos[i], w[i]
+ * host memory too: the problem copies its inputs in and its result out), and up to
  * max_concurrent problems run at a time, each on a host thread of the library (the
  * calling thread is one of them), so their kernels overlap on the device where their
  * streams allow it.  The meshes must be distinct (each problem uses its mesh's

@@ -474,21 +474,29 @@ def coarse_grain_concurrent(meshes, pos, w, params, out=None, streams=None, max_
                             report=False):
     """Independent coarse-grainings run concurrently (cg_coarse_grain_concurrent): problem
     i is coarse_grain(meshes[i], pos[i], w[i], params[i]) on streams[i] (one new stream per
-    problem by default).  pos[i] [3, n_i] and w[i] [nf, n_i] are CUDA f64 tensors (they
-    may be shared between problems); params is one Params or a list.  Returns the list of
+    problem by default).  pos[i] [3, n_i] and w[i] [nf, n_i] are f64 tensors (they may be
+    shared between problems): all CUDA tensors, or all host tensors (pinned for fast
+    copies), in which case every problem copies its inputs in and its result out as
+    coarse_grain_host does.  params is one Params or a list.  Returns the list of
     [nf, ncells_i] cell tensors (and the reports)."""
     import torch
     k = len(meshes)
     params = list(params) if isinstance(params, (list, tuple)) else [params] * k
     nf = w[0].shape[0]
+    on_host = not w[0].is_cuda
     for t in list(pos) + list(w):
-        _dev_f64(t, "pos/w")
+        if on_host:
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("pos/w: contiguous float64 host tensors expected")
+        else:
+            _dev_f64(t, "pos/w")
     if out is None:
-        out = [torch.empty((nf, m.ncells), dtype=torch.float64, device=w[0].device) for m in meshes]
+        out = [torch.empty((nf, m.ncells), dtype=torch.float64, device=w[0].device,
+                           pin_memory=on_host) for m in meshes]
     if streams is None:
-        streams = [torch.cuda.Stream(device=w[0].device) for _ in range(k)]
+        streams = [torch.cuda.Stream() for _ in range(k)]
     # the problems' streams start after the work already queued on the current stream
-    cur = torch.cuda.current_stream(w[0].device)
+    cur = torch.cuda.current_stream()
     for s_ in streams:
         s_.wait_stream(cur)
     ms = _ptr_array([m.handle.value for m in meshes])

@@ -740,11 +740,18 @@ cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const in
     std::vector<cg_status> status(nprob, CG_OK);
     std::vector<std::string> detail(nprob);
     std::atomic<int> next{0};
+    // a problem whose output is host memory runs as cg_coarse_grain_host (its inputs are
+    // host memory too), otherwise as cg_coarse_grain
+    std::vector<char> host(nprob);
+    for (int i = 0; i < nprob; ++i) host[i] = !is_device_ptr(cells[i]);
     auto worker = [&](bool own_thread) {
         if (own_thread && cudaSetDevice(dev) != cudaSuccess) return;
         for (int i; (i = next.fetch_add(1)) < nprob;) {
-            status[i] = cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
-                                        reports ? &reports[i] : nullptr, streams[i]);
+            cg_report *ri = reports ? &reports[i] : nullptr;
+            status[i] = host[i] ? cg_coarse_grain_host(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
+                                                       ri, streams[i])
+                                : cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i], ri,
+                                                  streams[i]);
             if (status[i] != CG_OK) detail[i] = g_last_error;   // this thread's message
         }
     };

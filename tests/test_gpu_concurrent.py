@@ -84,3 +84,18 @@ def test_concurrent_failure_and_misuse(cg, problems):
         assert "profiling" in str(e.value)
     finally:
         cg.profile_enable(False)
+
+
+def test_concurrent_host_buffers_equal_device_run(cg, problems):
+    """Host inputs and outputs: each problem runs as cg_coarse_grain_host (copies in and
+    out) and gives the device run's bits."""
+    import torch
+    probs, ref = problems
+    pos = [p[1].cpu().pin_memory() for p in probs]
+    w = [p[2].cpu().pin_memory() for p in probs]
+    out, reps = cg.coarse_grain_concurrent([p[0] for p in probs], pos, w, [p[3] for p in probs],
+                                           max_concurrent=3, report=True)
+    for (u_ref, r_ref), u, r in zip(ref, out, reps):
+        assert not u.is_cuda
+        assert torch.equal(u, u_ref.cpu())
+        assert r["cell_updates"] == r_ref["cell_updates"]
