@@ -512,6 +512,115 @@ __global__ void k_from_f32(size_t n, const float *__restrict__ v, double *__rest
         u[i] = (double)v[i];
 }
 
+// The same K-step explicit march with four consecutive x-cells per thread (nx % 4 == 0):
+// a block of 32 lanes x 32 rows holds a tile of 128 columns x 32 rows.  x neighbours
+// inside a thread's four cells are in registers, across lanes they come by shuffle; y
+// neighbours come from the per-level shared plane as 128-bit loads; each thread stages
+// its own four input cells of a plane with one 16-byte cp.async.  The tile keeps a fixed
+// halo of four columns on each side (so every tile starts 16-byte aligned, whatever K)
+// and K rows above and below; it writes the inner 120 x (32 - 2K) columns.  Every cell
+// update is k_explicit_tb's expression in the same order, so the two kernels agree bit
+// for bit.
+constexpr int kE4W = 128, kE4H = 32, kE4OX = kE4W - 8;
+constexpr dim3 kE4Block(32, kE4H);
+
+__host__ __device__ constexpr size_t explicit_tb4_smem(int K) {
+    return (size_t)(kEStages + 2 * K) * kE4H * kE4W * sizeof(float);
+}
+
+template <int K>
+__global__ void __launch_bounds__(1024, 1) k_explicit_tb4(Geo g, int zlen, int nzc, float c,
+                                                          const float *__restrict__ uin_all,
+                                                          float *__restrict__ uout_all) {
+    extern __shared__ float4 tb4_smem[];
+    // stage[slot][row][128]; buf[level][parity][row][128], levels 0..K-1
+    float(*stage)[kE4H][kE4W] = reinterpret_cast<float(*)[kE4H][kE4W]>(tb4_smem);
+    float(*buf)[2][kE4H][kE4W] = reinterpret_cast<float(*)[2][kE4H][kE4W]>(&stage[kEStages][0][0]);
+    constexpr int OY = kE4H - 2 * K;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int f = blockIdx.z / nzc, zc = blockIdx.z - f * nzc;
+    const int z0 = zc * zlen, z1 = min(g.nz, z0 + zlen);
+    const bool px = g.per & 1, py = (g.per >> 1) & 1, pz = (g.per >> 2) & 1;
+    const float *uin = uin_all + (size_t)f * g.n;
+    float *uout = uout_all + (size_t)f * g.n;
+
+    // this thread's four cells: columns 4 lane .. 4 lane + 3 of row w
+    const int xa = blockIdx.x * kE4OX - 4 + 4 * lane;   // first column (a multiple of 4)
+    const int y = blockIdx.y * OY - K + w;
+    const bool ey = py || (y >= 0 && y < g.ny);
+    const bool ex = px || (xa >= 0 && xa < g.nx);        // the four cells share it (nx % 4 == 0)
+    const int gx = px ? wrap_coord(xa, g.nx) : min(max(xa, 0), g.nx - 4);
+    const int rowoff = (py ? wrap_coord(y, g.ny) : min(max(y, 0), g.ny - 1)) * g.nx + gx;
+    const float cy = py ? 2.f : (float)((y > 0) + (y < g.ny - 1));
+    float nxy[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        nxy[i] = (px ? 2.f : (float)((xa + i > 0) + (xa + i < g.nx - 1))) + cy;
+    const float msk = (ex && ey) ? 1.f : 0.f;
+    const bool wr = lane >= 1 && lane <= 30 && xa >= 0 && xa < g.nx && w >= K && w < kE4H - K && y >= 0 &&
+                    y < g.ny;   // columns 4 .. 123 of the tile, rows K .. 31 - K
+    // the level buffers start at zero, so every value a cell ever reads is finite
+    for (int k = threadIdx.y * 32 + threadIdx.x; k < K * 2 * kE4H * kE4W; k += 1024)
+        (&buf[0][0][0][0])[k] = 0.f;
+    __syncthreads();
+    float4 qa[K], qb[K];   // planes q-1 and q of the level below K
+#pragma unroll
+    for (int t = 0; t < K; ++t) qa[t] = qb[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    const int p_begin = pz ? z0 - K : max(z0 - K, 0);
+    const int p_end = pz ? z1 + K : min(z1 + K, g.nz + K);
+    const unsigned stage0 = (unsigned)__cvta_generic_to_shared(&stage[0][w][4 * lane]);
+    auto stage_plane = [&](int p) {
+        const bool zok = p < p_end && (pz || (p >= 0 && p < g.nz));
+        const float *src = uin + (size_t)(pz ? wrap_coord(p, g.nz) : min(max(p, 0), g.nz - 1)) * g.nxy + rowoff;
+        const unsigned dst = stage0 + (unsigned)(((p - p_begin) & (kEStages - 1)) * kE4H * kE4W * 4);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                     "r"((zok && ex && ey) ? 16 : 0)
+                     : "memory");
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int d = 0; d < kEStages - 1; ++d) stage_plane(p_begin + d);
+    for (int p = p_begin; p < p_end; ++p) {
+        stage_plane(p + kEStages - 1);   // past the end: an empty (zero-filled) group
+        cp_async_wait<kEStages - 1>();     // plane p has landed
+        float4 nw = *reinterpret_cast<const float4 *>(&stage[(p - p_begin) & (kEStages - 1)][w][4 * lane]);
+        const int par = p & 1;
+        *reinterpret_cast<float4 *>(&buf[0][par][w][4 * lane]) = nw;
+#pragma unroll
+        for (int t = 1; t <= K; ++t) {
+            const int q = p - t;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q >= z0 - (K - t) && q < z1 + (K - t) && (pz || (q >= 0 && q < g.nz))) {   // uniform
+                const float cz = pz ? 2.f : (float)((q > 0) + (q < g.nz - 1));
+                const float4 b = qb[t - 1], za = qa[t - 1];
+                const float4 up = *reinterpret_cast<const float4 *>(&buf[t - 1][par ^ 1][max(w - 1, 0)][4 * lane]);
+                const float4 dn =
+                    *reinterpret_cast<const float4 *>(&buf[t - 1][par ^ 1][min(w + 1, kE4H - 1)][4 * lane]);
+                const float xl = __shfl_up_sync(0xffffffffu, b.w, 1);
+                const float xr = __shfl_down_sync(0xffffffffu, b.x, 1);
+                const float s0 = ((xl + b.y) + (up.x + dn.x)) + (za.x + nw.x);
+                const float s1 = ((b.x + b.z) + (up.y + dn.y)) + (za.y + nw.y);
+                const float s2 = ((b.y + b.w) + (up.z + dn.z)) + (za.z + nw.z);
+                const float s3 = ((b.z + xr) + (up.w + dn.w)) + (za.w + nw.w);
+                v.x = msk * fmaf(c, fmaf(-(nxy[0] + cz), b.x, s0), b.x);
+                v.y = msk * fmaf(c, fmaf(-(nxy[1] + cz), b.y, s1), b.y);
+                v.z = msk * fmaf(c, fmaf(-(nxy[2] + cz), b.z, s2), b.z);
+                v.w = msk * fmaf(c, fmaf(-(nxy[3] + cz), b.w, s3), b.w);
+            }
+            if (t < K) {
+                *reinterpret_cast<float4 *>(&buf[t][par][w][4 * lane]) = v;
+            } else if (q >= z0 && q < z1 && wr) {
+                *reinterpret_cast<float4 *>(uout + (size_t)q * g.nxy + rowoff) = v;
+            }
+            qa[t - 1] = qb[t - 1];
+            qb[t - 1] = nw;
+            nw = v;
+        }
+        __syncthreads();
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(512, 2) k_explicit_tb(Geo g, int zlen, int nzc, float c,
                                                         const float *__restrict__ uin_all,
@@ -2943,8 +3052,70 @@ template <int K> static int explicit_tb_blocks_per_sm(size_t smem) {
     return cached;
 }
 
+template <int K> static int explicit_tb4_blocks_per_sm(size_t smem) {
+    static thread_local int cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(k_explicit_tb4<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_explicit_tb4<K>, 1024, smem) != cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+// z-chunk length of a blocked explicit launch: a block of a chunk of zlen planes runs
+// zlen + 2K pipeline iterations and the launch takes ceil(blocks / resident blocks)
+// waves; the chunk length that minimises waves x (zlen + 2K).
+static int explicit_zlen(const Geo &g, long long cols, long long slots, int kt) {
+    int zlen = g.nz;
+    long long best = -1;
+    for (int zl = 1; zl <= g.nz; ++zl) {
+        const long long nzc = (g.nz + zl - 1) / zl;
+        if (zl > 1 && (g.nz + zl - 2) / (zl - 1) == nzc) continue;   // same chunk count, shorter zl wins
+        const long long waves = (cols * nzc + slots - 1) / slots;
+        const long long cost = waves * (zl + 2 * kt);
+        if (best < 0 || cost < best) best = cost, zlen = zl;
+    }
+    return zlen;
+}
+
+// One launch of the four-cells-per-thread kernel k_explicit_tb4<K> (nx % 4 == 0).
+static cg_status launch_explicit_tb4(const Geo &g, int nf, int kt, float c, const float *a, float *b,
+                                     cudaStream_t st) {
+    const int OY = kE4H - 2 * kt;
+    const int gx = (g.nx + kE4OX - 1) / kE4OX, gy = (g.ny + OY - 1) / OY;
+    const size_t smem = explicit_tb4_smem(kt);
+    const int per_sm = kt == 1 ? explicit_tb4_blocks_per_sm<1>(smem)
+                     : kt == 2 ? explicit_tb4_blocks_per_sm<2>(smem)
+                     : kt == 3 ? explicit_tb4_blocks_per_sm<3>(smem) : explicit_tb4_blocks_per_sm<4>(smem);
+    const long long cols = (long long)gx * gy * nf;
+    const int zlen = explicit_zlen(g, cols, (long long)num_sms() * per_sm, kt);
+    const int nzc = (g.nz + zlen - 1) / zlen;
+    const dim3 grid(gx, gy, nzc * nf);
+    const double bytes = (double)g.n * nf * 8;
+    switch (kt) {
+    case 1:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb4<1><<<grid, kE4Block, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    case 2:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb4<2><<<grid, kE4Block, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    case 3:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb4<3><<<grid, kE4Block, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    default:
+        CGK_LAUNCH("explicit_tb", bytes, st, k_explicit_tb4<4><<<grid, kE4Block, smem, st>>>(g, zlen, nzc, c, a, b));
+        break;
+    }
+    CGK_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
 static cg_status launch_explicit_tb(const Geo &g, int nf, int kt, float c, const float *a, float *b,
                                     cudaStream_t st) {
+    if (g.nx % 4 == 0) return launch_explicit_tb4(g, nf, kt, c, a, b, st);
     const int OX = kEW - 2 * kt, OY = kEH - 2 * kt;
     const int gx = (g.nx + OX - 1) / OX, gy = (g.ny + OY - 1) / OY;
     const size_t smem = explicit_tb_smem(kt);

@@ -49,7 +49,7 @@ def run(cg, mesh, u0, T, nsteps, k, report=False):
 
 
 # ragged tiles in x and y (the output tile is (64 - 2K) x (32 - 2K)), short z chunks
-@pytest.mark.parametrize("dims", [(70, 45, 19), (128, 24, 9), (13, 70, 33)])
+@pytest.mark.parametrize("dims", [(70, 45, 19), (128, 24, 9), (13, 70, 33), (244, 61, 12)])
 @pytest.mark.parametrize("ratio", [0.1, 1 / 6])
 def test_blocked_explicit_parity_and_k_independence(cg, orc, dims, ratio):
     rng = np.random.default_rng(100)
@@ -83,7 +83,9 @@ def test_blocked_explicit_forty_steps_on_a_pcm_field(cg, orc):
     assert maxrel(got, df.cpu().numpy()) <= BAR
 
 
-@pytest.mark.parametrize("dims", [(37, 13, 11), (6, 1, 9), (2, 9, 5), (1, 3, 4)])
+# nx % 4 == 0 runs the four-cells-per-thread kernel, other nx the two-cells one
+@pytest.mark.parametrize("dims", [(37, 13, 11), (6, 1, 9), (2, 9, 5), (1, 3, 4), (36, 13, 11), (4, 3, 4),
+                                  (248, 7, 5)])
 @pytest.mark.parametrize("periodic", [(True, True, True), (True, False, False), (False, True, True)])
 def test_blocked_explicit_periodic(cg, orc, dims, periodic):
     rng = np.random.default_rng(101)
