@@ -3122,19 +3122,8 @@ static cg_status launch_explicit_tb(const Geo &g, int nf, int kt, float c, const
     const int per_sm = kt == 1 ? explicit_tb_blocks_per_sm<1>(smem)
                      : kt == 2 ? explicit_tb_blocks_per_sm<2>(smem)
                      : kt == 3 ? explicit_tb_blocks_per_sm<3>(smem) : explicit_tb_blocks_per_sm<4>(smem);
-    // z chunks: a block of a chunk of zlen planes runs zlen + 2K pipeline iterations, and
-    // the launch takes ceil(blocks / resident blocks) waves; pick the chunk length that
-    // minimises waves x (zlen + 2K)
-    const long long cols = (long long)gx * gy * nf, slots = (long long)num_sms() * per_sm;
-    int zlen = g.nz;
-    long long best = -1;
-    for (int zl = 1; zl <= g.nz; ++zl) {
-        const long long nzc = (g.nz + zl - 1) / zl;
-        if (zl > 1 && (g.nz + zl - 2) / (zl - 1) == nzc) continue;   // same chunk count, shorter zl wins
-        const long long waves = (cols * nzc + slots - 1) / slots;
-        const long long cost = waves * (zl + 2 * kt);
-        if (best < 0 || cost < best) best = cost, zlen = zl;
-    }
+    const long long cols = (long long)gx * gy * nf;
+    const int zlen = explicit_zlen(g, cols, (long long)num_sms() * per_sm, kt);
     const int nzc = (g.nz + zlen - 1) / zlen;
     const dim3 grid(gx, gy, nzc * nf);
     const double bytes = (double)g.n * nf * 8;
