@@ -99,3 +99,17 @@ def test_concurrent_host_buffers_equal_device_run(cg, problems):
         assert not u.is_cuda
         assert torch.equal(u, u_ref.cpu())
         assert r["cell_updates"] == r_ref["cell_updates"]
+
+
+def test_concurrent_full_size_benchmark_configuration(cg):
+    """The benchmark's step as it times it: the 128^3 clustered case (2,000,000 spheres)
+    at b/dx = 1, 2, 4, 8, two problems at a time -- the same bits as four calls in a row."""
+    import torch
+    c = W.clustered_cube()
+    pos, w = dev(c.pos), dev(c.w)
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for _ in range(4)]
+    prm = [cg.Params(bandwidth=b * c.dx, nsteps=10, precision=3, tol=1e-13) for b in (1.0, 2.0, 4.0, 8.0)]
+    seq = [cg.coarse_grain(m, pos, w, p) for m, p in zip(meshes, prm)]
+    out = cg.coarse_grain_concurrent(meshes, [pos] * 4, [w] * 4, prm, max_concurrent=2)
+    for a, b in zip(out, seq):
+        assert torch.equal(a, b)
