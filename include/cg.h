@@ -43,7 +43,8 @@ typedef enum {
     CG_ENOMEM = 2,    /* device or host allocation failed */
     CG_ECUDA = 3,     /* a CUDA runtime call failed (see cg_last_error) */
     CG_ENOCONV = 4,   /* an implicit step did not reach params.tol within the limits */
-    CG_ETIMEOUT = 5,  /* a bounded device-side wait gave up (persistent kernels) */
+    CG_ETIMEOUT = 5,  /* a bounded device-side wait gave up (persistent, resident or
+                         TMA-staged kernels) */
     CG_EDOMAIN = 6    /* particles outside the mesh; report->n_out_of_domain has the count */
 } cg_status;
 
@@ -64,8 +65,8 @@ typedef struct cg_mesh cg_mesh; /* opaque, library-owned */
 cg_status cg_create_mesh_structured(int nx, int ny, int nz, const double origin[3], double dx,
                                     cg_mesh **out);
 
-/* Unstructured tetrahedral mesh (Section 4.3 uses unstructured cells; the build
- * uses tets).  xyz_host is [nverts][3] FP64, tv_host is [ntets][4] int32 vertex ids
+/* Unstructured tetrahedral mesh (Section 4.3 uses unstructured cells; this library
+ * takes tetrahedra).  xyz_host is [nverts][3] FP64, tv_host is [ntets][4] int32 vertex ids
  * (either orientation).  The library derives cell volumes V_c, centroids (vertex
  * means), faces, and the two-point-flux finite-volume Laplacian
  * T_f = |S_f|^2 / (S_f . d_f) between face neighbours (S_f the face area vector out
