@@ -33,6 +33,9 @@ def main(argv=None):
     ap.add_argument("--explicit-k", type=int, default=0,
                     help="explicit Euler instead: fused_k steps per launch (FP32, temporal "
                          "blocking), --nsteps steps at dtau/dx^2 = 0.1")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="the first N snapshots of the 64-snapshot batch (cube sides 32..96, "
+                         "5 fields, b = 3 dx) through one batched call instead")
     ap.add_argument("--deposit", action="store_true",
                     help="ordered deposition of the clustered n^3 workload (2,000,000 spheres "
                          "at n = 128) instead of a diffusion")
@@ -46,6 +49,21 @@ def main(argv=None):
     import workloads as W
 
     build.build()
+    if a.batched:
+        cases = W.batched_snapshots()[:a.batched]
+        meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+        pos = [torch.from_numpy(c.pos).cuda() for c in cases]
+        w = [torch.from_numpy(c.w).cuda() for c in cases]
+        for r in range(a.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=a.nsteps, precision=a.precision),
+                                             bandwidths=[c.b for c in cases], report=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            print("rep %d: %.3f ms, %d cell-updates, %.3e cell-updates/s"
+                  % (r, dt * 1e3, rep["cell_updates"], rep["cell_updates"] / dt))
+        return
     if a.deposit:
         c = W.clustered_cube(n_side=a.n, n_particles=2_000_000 * (a.n // 128) ** 3 or 2_000_000)
         mesh = cg.StructuredMesh(c.dims, c.origin, c.dx)
