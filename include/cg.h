@@ -254,7 +254,8 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
  * host memory too: the problem copies its inputs in and its result out), and up to
  * max_concurrent problems run at a time, each on a host thread of the library (the
  * calling thread is one of them), so their kernels overlap on the device where their
- * streams allow it.  The meshes must be distinct (each problem uses its mesh's
+ * streams allow it.  Problems start longest first (estimated from cells, steps and
+ * dtau over the squared cell size).  The meshes must be distinct (each problem uses its mesh's
  * workspaces); give each problem its own non-default stream for overlap.  A mesh's
  * first call of a configuration autotunes its sweep shape by timing candidates, which
  * other running problems would disturb: make that first call through cg_coarse_grain.

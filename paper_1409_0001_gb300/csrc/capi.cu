@@ -744,9 +744,31 @@ cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const in
     // host memory too), otherwise as cg_coarse_grain
     std::vector<char> host(nprob);
     for (int i = 0; i < nprob; ++i) host[i] = !is_device_ptr(cells[i]);
+    // longest first (fewer idle workers at the end): the cost estimate is cells x steps x
+    // sqrt(1 + 12 dtau / h^2), which follows the Chebyshev iteration count, with h the
+    // cell edge (structured) or the edge of a cube of the mean cell volume
+    std::vector<int> order(nprob);
+    std::vector<double> cost(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const cg_mesh *m = meshes[i];
+        const cg_params &q = params[i];
+        const double T = q.bandwidth > 0.0 ? q.bandwidth * q.bandwidth / 4.0 : q.T;
+        double h = m->dx;
+        if (m->kind != MESH_STRUCTURED) {
+            double v = 0;
+            for (double x : m->h_vc) v += x;
+            h = std::cbrt(v / std::max<int64_t>(m->ncells, 1));
+        }
+        const int ns = std::max(q.nsteps, 1);
+        const double c = (h > 0 && std::isfinite(T)) ? T / ns / (h * h) : 0.0;
+        cost[i] = (double)m->ncells * ns * std::sqrt(1.0 + 12.0 * std::max(c, 0.0));
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     auto worker = [&](bool own_thread) {
         if (own_thread && cudaSetDevice(dev) != cudaSuccess) return;
-        for (int i; (i = next.fetch_add(1)) < nprob;) {
+        for (int j; (j = next.fetch_add(1)) < nprob;) {
+            const int i = order[j];
             cg_report *ri = reports ? &reports[i] : nullptr;
             status[i] = host[i] ? cg_coarse_grain_host(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
                                                        ri, streams[i])
