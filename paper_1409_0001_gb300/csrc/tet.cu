@@ -698,25 +698,43 @@ __global__ void k_tprobe_init(Op o, TS *__restrict__ rin, TS *__restrict__ z, TS
 // d_0 = 0, d_1 = c0 D^-1 r; then d_{k+1} = d_k + c1 (d_k - d_{k-1}) + c2 D^-1 (r - A d_k)
 // (dkm1 null: d_0 = 0).  No inner products, one pass per iteration.  This form handles
 // one field (the launch's y index picks it); k_tcheb below handles several.
-template <class TS>
-__global__ void k_tcheb1(Op o, const TS *__restrict__ r_all, const TS *__restrict__ dk_all,
-                         const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all, float c1, float c2) {
+template <class TS, int NS>
+__global__ void __launch_bounds__(kThreads, 6) k_tcheb1(Op o, const TS *__restrict__ r_all,
+                                                        const TS *__restrict__ dk_all,
+                                                        const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all,
+                                                        float c1, float c2) {
     const size_t off = (size_t)blockIdx.y * o.n;
     const TS *r = r_all + off;
+    const TS *dk = dk_all + off;
     const float dte = (float)o.dte;
-    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
-        const TS *dk = dk_all + off;
-        const float dkk = ldf(dk, k);
-        float off_sum = 0.f;
+    const int stride = gridDim.x * kThreads;
+    // two cells per pass (k and k + stride): both cells' NS neighbour indices and
+    // transmissibilities are loaded before either cell's gathers, so twice the dependent
+    // loads are in flight per thread
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += 2 * stride) {
+        const int k2 = k + stride;
+        const bool two = k2 < o.n;
+        const int kb = two ? k2 : k;
+        int nb[2][NS];
+        float wv[2][NS];
 #pragma unroll
-        for (int q = 0; q < kMaxSlots; ++q) {
-            if (q >= o.ns) break;
-            const size_t e = (size_t)q * o.n + k;
-            off_sum += o.offv32[e] * ldf(dk, o.offc[e]);
+        for (int q = 0; q < NS; ++q) {
+            nb[0][q] = o.offc[(size_t)q * o.n + k];
+            wv[0][q] = o.offv32[(size_t)q * o.n + k];
+            nb[1][q] = o.offc[(size_t)q * o.n + kb];
+            wv[1][q] = o.offv32[(size_t)q * o.n + kb];
         }
-        const float res = ldf(r, k) - (o.adiag32[k] * dkk - dte * off_sum);
-        const float dm = dkm1_all ? ldf(dkm1_all + off, k) : 0.f;   // d_0 = 0
-        stf(dn_all, off + k, dkk + c1 * (dkk - dm) + c2 * (o.iadiag32[k] * res));
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int kc = c ? kb : k;
+            float off_sum = 0.f;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) off_sum += wv[c][q] * ldf(dk, nb[c][q]);
+            const float dkk = ldf(dk, kc);
+            const float res = ldf(r, kc) - (o.adiag32[kc] * dkk - dte * off_sum);
+            const float dm = dkm1_all ? ldf(dkm1_all + off, kc) : 0.f;   // d_0 = 0
+            if (c == 0 || two) stf(dn_all, off + kc, dkk + c1 * (dkk - dm) + c2 * (o.iadiag32[kc] * res));
+        }
     }
 }
 
@@ -1352,8 +1370,8 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                 const TS *dm = k == 1 ? nullptr : Cb[(k - 1) % 3];
                 if (nf == 1)
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (rb32 - 8 + 4.0 * sizeof(TS)),
-                               st, (k_tcheb1<TS><<<G, kThreads, 0, st>>>(
-                                       o, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1])));
+                               st, (o.ns == 4 ? k_tcheb1<TS, 4> : k_tcheb1<TS, 6>)<<<G, kThreads, 0, st>>>(
+                                       o, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1]));
                 else
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32",
                                (double)n * (rb32 - 8 + nf * 4.0 * sizeof(TS)), st,
