@@ -2412,19 +2412,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn tma_encoder() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
+    // looked up once per process (a function-local static is initialised exactly once,
+    // also when several library threads get here together)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-        else
-            cudaGetLastError();
-        tried = true;
-    }
+            return (EncodeTiledFn)p;
+        cudaGetLastError();
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -2441,7 +2440,8 @@ bool tma_map(CUtensorMap *map, const Geo &g, int nf, const float *base, bool hal
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-__device__ int g_tma_err;   // set by a TMA-staged sweep whose wait gave up
+__device__ int g_tma_err;   // set by a TMA-staged sweep whose wait gave up (one word per device:
+                            // concurrent problems share it, so any of them may report it)
 constexpr long long kTmaBudget = 4000000000LL;   // clock cycles (about two seconds)
 
 // Chebyshev iteration count for a residual reduction eps on spectrum [1, lmax].
