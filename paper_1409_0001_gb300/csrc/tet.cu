@@ -326,6 +326,7 @@ struct Op {          // the operator seen by the kernels
     const float *adiag32 = nullptr;    // FP32 diagonal of A, V_c - dte L_kk (inner solves)
     const float *iadiag32 = nullptr;   // its reciprocal (the Jacobi preconditioner)
     int ns = 4;                        // neighbour slots per cell (4 tets, 6 stretched hex)
+    int hx = 0, hy = 0, hz = 0;        // stretched hex mesh: cells per axis (0 for tets)
 };
 constexpr int kMaxSlots = 6;
 
@@ -779,6 +780,43 @@ __global__ void __launch_bounds__(kThreads, 4) k_tcheb(Op o, int nf, const TS *_
     }
 }
 
+// The Chebyshev iteration of k_tcheb on a stretched Cartesian mesh, whose neighbours are
+// implicit: slots 0..5 are the cells at k-1, k+1, k-nx, k+nx, k-nx ny, k+nx ny (a wall
+// slot has T = 0 and reads the cell itself), so the neighbour values load without first
+// loading their indices.  The sum runs over the slots in k_tcheb's order, so the result
+// is the same.  A block is blockDim.x cells of a row by blockDim.y rows (256 threads).
+template <class TS>
+__global__ void __launch_bounds__(kThreads) k_hcheb(Op o, int nf, const TS *__restrict__ r_all,
+                                                     const TS *__restrict__ dk_all,
+                                                     const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all,
+                                                     float c1, float c2) {
+    const float dte = (float)o.dte;
+    const size_t n = (size_t)o.n;
+    const int nx = o.hx, nxy = o.hx * o.hy, rows = o.hy * o.hz;
+    for (int row = blockIdx.y * blockDim.y + threadIdx.y; row < rows; row += gridDim.y * blockDim.y) {
+        const int iy = row % o.hy, iz = row / o.hy;
+        for (int ix = blockIdx.x * blockDim.x + threadIdx.x; ix < nx; ix += gridDim.x * blockDim.x) {
+            const int k = row * nx + ix;
+            const int nb[6] = {ix > 0 ? k - 1 : k, ix + 1 < nx ? k + 1 : k, iy > 0 ? k - nx : k,
+                               iy + 1 < o.hy ? k + nx : k, iz > 0 ? k - nxy : k, iz + 1 < o.hz ? k + nxy : k};
+            float wv[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) wv[q] = o.offv32[(size_t)q * n + k];
+            const float ad = o.adiag32[k], iad = o.iadiag32[k];
+            for (int f = 0; f < nf; ++f) {
+                const TS *dk = dk_all + f * n;
+                const float dkk = ldf(dk, k);
+                float off_sum = 0.f;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) off_sum += wv[q] * ldf(dk, nb[q]);
+                const float res = ldf(r_all, f * n + k) - (ad * dkk - dte * off_sum);
+                const float dm = dkm1_all ? ldf(dkm1_all, f * n + k) : 0.f;   // d_0 = 0
+                stf(dn_all, f * n + k, dkk + c1 * (dkk - dm) + c2 * (iad * res));
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ============================================================================ host: build
@@ -1096,6 +1134,11 @@ static Op make_op(cg_mesh *m, double dte, double dtau) {
     o.dte = dte;
     o.dtau = dtau;
     o.ns = m->tet.ns;
+    if (m->kind == MESH_HEX) {
+        o.hx = m->tet.hn[0];
+        o.hy = m->tet.hn[1];
+        o.hz = m->tet.hn[2];
+    }
     return o;
 }
 
@@ -1366,9 +1409,19 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                        (k_tcheb<TS, true><<<G, kThreads, 0, st>>>(o, nf, Rin, nullptr, nullptr, Cb[1],
                                                                               cheb.c0, 0.f)));
             const int mi = cheb.iterations();
+            // blocks of (row width rounded to a warp, at most 256) x (256 / that) rows
+            const int hbx = std::min(kThreads, (o.hx + 31) / 32 * 32);
+            const dim3 hblk((unsigned)hbx, (unsigned)(kThreads / hbx));
+            const dim3 hgrid((unsigned)((o.hx + hbx - 1) / hbx),
+                             (unsigned)std::min((o.hy * o.hz + (int)hblk.y - 1) / (int)hblk.y, 65535));
             for (int k = 1; k < mi; ++k) {
                 const TS *dm = k == 1 ? nullptr : Cb[(k - 1) % 3];
-                if (nf == 1)
+                if (o.hx > 0)   // stretched hex mesh: implicit neighbours
+                    CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32",
+                               (double)n * (6 * 4 + 8 + nf * 4.0 * sizeof(TS)), st,
+                               k_hcheb<TS><<<hgrid, hblk, 0, st>>>(o, nf, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3],
+                                                                       cheb.c1[k - 1], cheb.c2[k - 1]));
+                else if (nf == 1)
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (rb32 - 8 + 4.0 * sizeof(TS)),
                                st, (o.ns == 4 ? k_tcheb1<TS, 4> : k_tcheb1<TS, 6>)<<<G, kThreads, 0, st>>>(
                                        o, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1]));
