@@ -416,7 +416,12 @@ def main():
     line = None
     ext = None
     if rank == 0 and not a.no_extras:
-        ext = extras()
+        try:
+            ext = extras()
+        except Exception as e:   # the main line is printed whatever an extra workload does
+            import traceback
+            traceback.print_exc()
+            ext = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         cpu = None
         if not a.no_cpu_baseline and ws == 1:
