@@ -425,7 +425,12 @@ def main():
     if rank == 0:
         cpu = None
         if not a.no_cpu_baseline and ws == 1:
-            cpu = cpu_baseline(c, outs, fp64_out)
+            try:
+                cpu = cpu_baseline(c, outs, fp64_out)
+            except Exception as e:
+                import traceback
+                traceback.print_exc()
+                cpu = {"error": "%s: %s" % (type(e).__name__, e), "kind": "oracle"}
         ncells = c.ncells
         cps = ws * a.steps * len(B_OVER_DX) * NSTEPS * ncells / (ms * 1e-3)
         line = {
