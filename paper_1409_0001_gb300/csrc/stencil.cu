@@ -1458,8 +1458,10 @@ template <> struct Vec4cg<__nv_bfloat16> {
 // iteration; L is the load policy (Vec4 or Vec4cg), sdg the diagonal table in shared
 // memory.  Every thread of the block must call it (barriers and shuffles inside).
 // ZFIX > 0: the caller guarantees at most ZFIX planes per block, so the march is
-// unrolled (the register queue rotates without copies).
-template <class TS, template <class> class L, int ZFIX = 0>
+// unrolled (the register queue rotates without copies).  PER: periodic axes (g.per):
+// halo rows, columns and planes wrap, every cell has both neighbours on a periodic
+// axis, and the tile's rows beyond ny hold the wrapped rows (y mod ny) as neighbours.
+template <class TS, template <class> class L, int ZFIX = 0, bool PER = false>
 __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z0, int z1,
                                              const Coef32 &cf, const float *sdg, float gamma,
                                              float omega, const TS *yv, const TS *ypv,
@@ -1470,55 +1472,67 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = bx * (4 * TX);
     const int x = x0 + 4 * tx, y = by * TY + ty;
+    const bool px = PER && (g.per & 1), py = PER && (g.per & 2), pz = PER && (g.per & 4);
     const bool own = (x < g.nx) && (y < g.ny);
-    const bool rowlo = (ty == 0) && (y > 0) && (x < g.nx);            // loads row y-1
-    const bool rowhi = (ty == TY - 1) && (y + 1 < g.ny) && (x < g.nx);  // loads row y+1
-    const bool xl = (tx == 0) && (x > 0) && (y < g.ny);                 // cell x-1
+    const int yw = py ? y % g.ny : y;                                    // the row this thread holds
+    const bool hold = (x < g.nx) && (yw < g.ny);                         // holds a mesh row (own or wrapped)
+    const bool rowlo = (ty == 0) && (y > 0 || py) && (x < g.nx);         // loads row y-1
+    const bool rowhi = (ty == TY - 1) && (y + 1 < g.ny || py) && (x < g.nx);  // loads row y+1
+    const bool xl = (tx == 0) && (x > 0 || px) && (yw < g.ny);           // cell x-1
     const int xlast = min(g.nx, x0 + 4 * TX) - 4;                       // first cell of the last owned vector
-    const bool xr = (x == xlast) && (x + 4 < g.nx) && (y < g.ny);      // cell x+4
+    const bool xr = (x == xlast) && (x + 4 < g.nx || px) && (yw < g.ny);  // cell x+4
     // neighbour counts in x and y of the four cells (z added per plane)
-    const int nyb = (y > 0) + (y + 1 < g.ny);
-    const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx);
+    const int nyb = py ? 2 : (y > 0) + (y + 1 < g.ny);
+    const int n0 = nyb + (px ? 1 : (x > 0)) + 1, n3 = nyb + 1 + (px ? 1 : (x + 4 < g.nx));
     const int n12 = nyb + 2;
     // diagonals of the four cells on planes with both z neighbours (most planes)
     const float d0i = sdg[n0 + 2], d12i = sdg[n12 + 2], d3i = sdg[n3 + 2];
-    const int kxy = y * g.nx + x;
+    const int kxy = yw * g.nx + x;
+    // neighbour offsets within a plane (wrapped across a periodic face)
+    const int dlo = (PER && yw == 0) ? (g.ny - 1) * g.nx : -g.nx;
+    const int dhi = (PER && yw == g.ny - 1) ? -(g.ny - 1) * g.nx : g.nx;
+    const int dxl = (PER && x == 0) ? g.nx - 1 : -1;
+    const int dxr = (PER && x + 4 >= g.nx) ? 4 - g.nx : 4;
+    // plane index of plane q of the z march (wrapped on a periodic z axis)
+    auto zp = [&](int q) -> size_t { return (size_t)(pz ? (q + g.nz) % g.nz : q) * g.nxy; };
     float4 vdn = f4zero(), vc = f4zero(), vup = f4zero(), ypc = f4zero(), rc = f4zero();
     float4 hlo = f4zero(), hhi = f4zero();
     float hl = 0.f, hr = 0.f;
     if (z0 < z1) {
-        const size_t k0 = (size_t)kxy + (size_t)z0 * g.nxy;
-        if (own) {
-            if (z0 > 0) vdn = LD::load(yv, k0 - g.nxy);
+        const size_t k0 = (size_t)kxy + zp(z0);
+        if (hold) {
+            if (z0 > 0 || pz) vdn = LD::load(yv, (size_t)kxy + zp(z0 - 1));
             vc = LD::load(yv, k0);
-            if (z0 + 1 < g.nz) vup = LD::load(yv, k0 + g.nxy);
+            if (z0 + 1 < g.nz || pz) vup = LD::load(yv, (size_t)kxy + zp(z0 + 1));
+        }
+        if (own) {
             if (ypv) ypc = LD::load(ypv, k0);
             rc = LD::load(rv, k0);
         }
-        if (rowlo) hlo = LD::load(yv, k0 - g.nx);
-        if (rowhi) hhi = LD::load(yv, k0 + g.nx);
-        if (xl) hl = ldcg(yv, (int)(k0 - 1));
-        if (xr) hr = ldcg(yv, (int)(k0 + 4));
+        if (rowlo) hlo = LD::load(yv, (size_t)((long long)k0 + dlo));
+        if (rowhi) hhi = LD::load(yv, (size_t)((long long)k0 + dhi));
+        if (xl) hl = ldcg(yv, (int)((long long)k0 + dxl));
+        if (xr) hr = ldcg(yv, (int)((long long)k0 + dxr));
     }
 #pragma unroll
     for (int zi = 0; zi < (ZFIX > 0 ? ZFIX : z1 - z0); ++zi) {
         const int z = z0 + zi;
         if (ZFIX > 0 && z >= z1) break;
-        const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
+        const size_t kz = (size_t)kxy + (PER ? zp(z) : (size_t)z * g.nxy);
         // loads for the next plane
         float4 nup = f4zero(), nyp = f4zero(), nr = f4zero(), nlo = f4zero(), nhi = f4zero();
         float nl = 0.f, nrr = 0.f;
         if (z + 1 < z1) {
-            const size_t kn = kz + g.nxy;
+            const size_t kn = PER ? (size_t)kxy + zp(z + 1) : kz + g.nxy;
+            if (hold && (z + 2 < g.nz || pz)) nup = LD::load(yv, PER ? (size_t)kxy + zp(z + 2) : kn + g.nxy);
             if (own) {
-                if (z + 2 < g.nz) nup = LD::load(yv, kn + g.nxy);
                 if (ypv) nyp = LD::load(ypv, kn);
                 nr = LD::load(rv, kn);
             }
-            if (rowlo) nlo = LD::load(yv, kn - g.nx);
-            if (rowhi) nhi = LD::load(yv, kn + g.nx);
-            if (xl) nl = ldcg(yv, (int)(kn - 1));
-            if (xr) nrr = ldcg(yv, (int)(kn + 4));
+            if (rowlo) nlo = LD::load(yv, (size_t)((long long)kn + dlo));
+            if (rowhi) nhi = LD::load(yv, (size_t)((long long)kn + dhi));
+            if (xl) nl = ldcg(yv, (int)((long long)kn + dxl));
+            if (xr) nrr = ldcg(yv, (int)((long long)kn + dxr));
         }
         pl[ty + 1][tx] = vc;
         if (ty == 0) pl[0][tx] = hlo;
@@ -1532,7 +1546,7 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
         if (own) {
             const float4 up = pl[ty][tx], dn = pl[ty + 2][tx];
             float d0 = d0i, d12 = d12i, d3 = d3i;
-            if (z == 0 || z + 1 == g.nz) {   // a z wall: fewer neighbours
+            if (!pz && (z == 0 || z + 1 == g.nz)) {   // a z wall: fewer neighbours
                 const int nz_ = (z > 0) + (z + 1 < g.nz);
                 d0 = sdg[n0 + nz_];
                 d12 = sdg[n12 + nz_];
@@ -1563,7 +1577,7 @@ __device__ __forceinline__ void cheb_v4_tile(const Geo &g, int bx, int by, int z
     }
 }
 
-template <class TS, int ZFIX = 0>
+template <class TS, int ZFIX = 0, bool PER = false>
 __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nzc, Coef32 cf,
                                                       float gamma, float omega,
                                                       const TS *__restrict__ y_all,
@@ -1578,7 +1592,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cheb_v4(Geo g, int zlen, int nz
     __shared__ float sdg[8];
     stage_table(sdg, cf.dg);
     __syncthreads();
-    cheb_v4_tile<TS, Vec4, ZFIX>(g, blockIdx.x, blockIdx.y, z0, z1, cf, sdg, gamma, omega, y_all + off,
+    cheb_v4_tile<TS, Vec4, ZFIX, PER>(g, blockIdx.x, blockIdx.y, z0, z1, cf, sdg, gamma, omega, y_all + off,
                            yprev_all ? yprev_all + off : nullptr, r_all + off, ynext_all + off);
 }
 
@@ -2545,7 +2559,9 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
         const int zlen = code - 100;
         const int nzc = (g.nz + zlen - 1) / zlen;
         const dim3 grid((g.nx + 4 * TX - 1) / (4 * TX), gy, nzc * nf);
-        if (zlen == 1)
+        if (g.per)   // periodic axes: the wrapping variant
+            launch_chain(k_cheb_v4<TS, 0, true>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
+        else if (zlen == 1)
             launch_chain(k_cheb_v4<TS, 1>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
         else if (zlen == 2)
             launch_chain(k_cheb_v4<TS, 2>, grid, blk, st, g, zlen, nzc, cf, gamma, omega, y, yp, r, yn);
@@ -2842,7 +2858,7 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     std::vector<std::pair<int, int>> cands;
     const bool v4 = g.nx % 4 == 0;   // vectorised shapes need whole 4-cell vectors per row
     for (int c : {101, 102, 104, 108, 116, 2, 4, 8, -1, -4, -16})
-        if ((c < 100 || v4) && (g.per == 0 || c < 0))   // periodic axes: z-marching only
+        if ((c < 100 || v4) && (g.per == 0 || c < 0 || c >= 100))   // periodic: z-marching or vectorised
             cands.push_back({c, 10});
     if (sizeof(TS) == 4 && tma_sweep_fits(g)) {        // TMA-staged sweep: FP32 storage
         tma_prepare();
@@ -3308,9 +3324,9 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
 
     int cheb_code = p->sweep_shape;
     bool resident = false;
-    if (m->per && cheb_code > 0)
-        return fail(CG_EINVAL, "sweep_shape %d: with periodic axes only the z-marching sweeps "
-                    "(sweep_shape < 0, or 0 for autotuning) apply", cheb_code);
+    if (m->per && cheb_code > 0 && !(cheb_code >= 100 && cheb_code < kPairCode))
+        return fail(CG_EINVAL, "sweep_shape %d: with periodic axes only the z-marching and vectorised "
+                    "sweeps (sweep_shape < 0 or 100 + z, or 0 for autotuning) apply", cheb_code);
     if (cheb_code == kResidentCode) {
         if (!rp.ok)
             return fail(CG_EINVAL, "sweep_shape %d needs one field, nx %% 4 == 0, at most %d inner "

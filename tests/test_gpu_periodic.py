@@ -80,8 +80,9 @@ def test_periodic_other_schemes(cg, orc, scheme):
 
 
 def test_periodic_shapes_and_reset(cg):
-    """Shapes outside the scalar engine are refused on a periodic mesh; clearing the
-    periodic axes restores the wall results bit for bit (cached schedules are dropped)."""
+    """Shapes other than the z-marching and vectorised sweeps are refused on a periodic
+    mesh; clearing the periodic axes restores the wall results bit for bit (cached
+    schedules are dropped)."""
     dims = (32, 24, 16)
     rng = np.random.default_rng(72)
     u0 = rng.random((1, int(np.prod(dims))))
@@ -91,7 +92,7 @@ def test_periodic_shapes_and_reset(cg):
     cg.diffuse(mesh, u, p)
     walls = u.cpu().numpy()
     mesh.set_periodic(True, True, False)
-    for shape in (104, 4, 300, 204):
+    for shape in (4, 300, 204, 404):
         with pytest.raises(cg.CGError) as e:
             cg.diffuse(mesh, dev(u0), cg.Params(bandwidth=3 / 32, nsteps=5, precision=3,
                                                 sweep_shape=shape))
@@ -137,3 +138,27 @@ def test_solid_velocity_parity(cg, orc):
     assert maxrel(g, ref) <= MIXED_TOL
     with pytest.raises(cg.CGError):   # the output may not alias an input
         cg.solid_velocity(mesh, got[0].contiguous(), got[1:].contiguous(), out=got[1:])
+
+
+# nx % 4 == 0: the vectorised sweep with wrapping halos (partial row tiles, one-cell and
+# four-cell axes); against the oracle and against the z-marching sweep
+@pytest.mark.parametrize("dims", [(36, 13, 11), (4, 3, 5), (128, 1, 6), (8, 9, 1), (260, 17, 4)])
+@pytest.mark.parametrize("periodic", [(True, True, True), (True, False, False), (False, True, False),
+                                      (False, False, True)])
+@pytest.mark.parametrize("shape", [101, 104])
+def test_periodic_vectorised_sweep(cg, orc, dims, periodic, shape):
+    rng = np.random.default_rng(75)
+    n = int(np.prod(dims))
+    u0 = np.vstack([rng.random(n), rng.random(n) - 0.4])
+    dx = 1.0 / max(dims)
+    T = (2.5 * dx) ** 2 / 4
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 8, tol=1e-15, periodic=periodic)
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx, periodic=periodic)
+    out = {}
+    for sh in (shape, -4):
+        u = dev(u0)
+        _, rep = cg.diffuse(mesh, u, cg.Params(T=T, nsteps=8, precision=3, sweep_shape=sh), report=True)
+        assert rep["sweep_shape_used"] == sh
+        out[sh] = u.cpu().numpy()
+    assert maxrel(out[shape], ref) <= MIXED_TOL
+    assert maxrel(out[shape], out[-4]) <= 1e-12
