@@ -89,9 +89,9 @@ cg_status cg_mesh_cell_volumes(const cg_mesh *mesh, double *out_host);
  * periodic condition instead of zero flux).  px, py, pz nonzero make the faces at the
  * two ends of the mesh along x, y, z neighbours of each other (on an axis of one cell,
  * of the cell itself); all zero restores the walls.  Deposition is unchanged.  With a
- * periodic axis the diffusion uses the z-marching sweeps and the one-cell-per-thread
- * refinement (params->sweep_shape must be 0 or negative), and batched calls reject the
- * mesh.  Drops the mesh's captured schedules and tuned shapes.  Errors: CG_EINVAL (NULL
+ * periodic axis the diffusion uses the z-marching or the vectorised sweeps and the
+ * one-cell-per-thread refinement (params->sweep_shape must be 0, negative or 100 + z),
+ * and batched calls reject the mesh.  Drops the mesh's captured schedules and tuned shapes.  Errors: CG_EINVAL (NULL
  * or a tet mesh). */
 cg_status cg_mesh_set_periodic(cg_mesh *mesh, int px, int py, int pz);
 
@@ -168,8 +168,10 @@ typedef struct {
                            100 + z).  Batched calls:
                            z planes per work item (0 = autotuned per batch shape).  Tet
                            and stretched meshes, FP32 storage: 0 = Chebyshev inner
-                           solves on a spectrum estimated from the call's first PCG
-                           solve, 1 = Jacobi-PCG throughout (BF16 storage: always PCG) */
+                           solves on an interval from a probe PCG solve on a fixed
+                           right-hand side (kept per mesh and pseudo-step, so results do
+                           not depend on earlier calls), 1 = Jacobi-PCG throughout (BF16
+                           storage: always PCG) */
     long long barrier_budget; /* > 0: run each structured inner solve as one persistent
                                  cooperative launch whose grid barriers give up after this
                                  many clock cycles of waiting (then CG_ETIMEOUT); with
