@@ -71,3 +71,24 @@ def test_bad_arguments_fail_without_a_gpu(lib):
     p.nsteps = 0
     assert L.cg_diffuse(h, 1, None, ctypes.byref(p), None, None) == 1
     assert L.cg_destroy_mesh(h) == 0
+
+
+def test_size_limits_refused_before_any_device_work(lib):
+    """Particle counts outside [0, 2^31) and field counts outside [1, 64] are refused by
+    the argument checks, which run before any pointer is inspected or any device call."""
+    import paper_1409_0001_gb300 as cg
+    L = cg.load_library()
+    h = ctypes.c_void_p()
+    org = (ctypes.c_double * 3)(0, 0, 0)
+    assert L.cg_create_mesh_structured(4, 4, 4, org, 0.25, ctypes.byref(h)) == 0
+    p = cg.CgParams()
+    L.cg_params_default(ctypes.byref(p))
+    for n, nf, what in (((1 << 31), 1, b"n must be"), (-1, 1, b"n must be"),
+                        (10, 0, b"nfields"), (10, 65, b"nfields")):
+        assert L.cg_deposit(h, n, None, nf, None, None, ctypes.byref(p), None, None) == 1
+        assert what in L.cg_last_error()
+        assert L.cg_coarse_grain(h, n, None, nf, None, None, ctypes.byref(p), None, None) == 1
+        assert what in L.cg_last_error()
+    assert L.cg_diffuse(h, 65, None, ctypes.byref(p), None, None) == 1
+    assert b"nfields" in L.cg_last_error()
+    assert L.cg_destroy_mesh(h) == 0

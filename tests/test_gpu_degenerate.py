@@ -103,3 +103,24 @@ def test_single_step_matches_oracle(cg, orc, kind, precision, bar):
     got = u.cpu().numpy()
     ref = np.atleast_2d(ref)
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= bar
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("kind", ["structured", "tet", "hex"])
+def test_empty_particle_set(cg, kind, mode):
+    """No particles: the deposited fields are zero in both deposition modes, and so is
+    the coarse-grained result (zero is a fixed point of the diffusion), with zero mass in
+    and out and nothing out of the domain."""
+    import torch
+    m = meshes(cg)[kind]
+    pos, w = dev(np.zeros((3, 0))), dev(np.zeros((2, 0)))
+    sentinel = torch.full((2, m.ncells), 7.0, dtype=torch.float64, device="cuda")
+    out = cg.deposit(m, pos, w, cg.Params(deposit_mode=mode), out=sentinel)
+    assert torch.count_nonzero(out).item() == 0
+    for precision in (0, 3):
+        u, rep = cg.coarse_grain(m, pos, w, cg.Params(bandwidth=0.2, nsteps=3, precision=precision,
+                                                      deposit_mode=mode), report=True)
+        assert u.shape == (2, m.ncells)
+        assert torch.count_nonzero(u).item() == 0
+        assert rep["n_out_of_domain"] == 0
+        assert rep["mass_in"][:2] == [0.0, 0.0] and rep["mass_out"][:2] == [0.0, 0.0]
