@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -211,7 +212,7 @@ def run_reference(a):
             "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                              "sample": "per step: locate+deposit all %d particles, 2 of 10 "
                                        "implicit-Euler steps at b/dx=2, FP64 CG to 1e-13"
-                                       % a.n_particles},
+                                       % a.n_particles, "host": host_cpu()},
             "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -697,6 +698,7 @@ def cpu_baseline(c, outs, fp64_out):
     t0 = time.perf_counter()
     cell, _ = oracle.locate_structured(c.dims, c.origin, c.dx, c.pos)
     eps0, _ = oracle.deposit(cell, c.w, c.ncells, vc_uniform=(c.dx * c.dx) * c.dx)
+    t1 = time.perf_counter()
     b = 2.0 * c.dx
     ref, iters = oracle.diffuse_structured(eps0, c.dims, c.dx, b * b / 4, NSTEPS, tol=TOL)
     dt = time.perf_counter() - t0
@@ -708,8 +710,34 @@ def cpu_baseline(c, outs, fp64_out):
     return {"value": updates / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
             "sample": "locate+deposit all %d particles and 10 implicit-Euler steps at b/dx=2 "
                       "(FP64 CG to 1e-13), %.1f s" % (c.n, dt),
+            "particles_per_s": c.n / (t1 - t0),
+            "diffusion_cell_updates_per_s": updates / (dt - (t1 - t0)),
+            "host": host_cpu(),
             "mixed_maxrel_vs_oracle": float(np.max(np.abs(mixed - ref)) / scale),
             "fp64_maxrel_vs_oracle": float(np.max(np.abs(f64 - ref)) / scale)}
+
+
+def host_cpu():
+    """The host's logical CPU count and model name (/proc/cpuinfo, else lscpu)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
 
 
 if __name__ == "__main__":
