@@ -351,11 +351,15 @@ def main():
         msm = timed(lambda: one_step(prec, mreps), max(a.fp64_steps, 1)) / max(a.fp64_steps, 1)
         msm = max_over_ranks(msm)
         mode_out[name] = [o.clone() for o in outs]
+        if name == "fp64_cg":
+            fp64_reps = mreps
         modes[name] = {"ms_per_step": msm,
                        "cell_updates_per_s": sum(r["cell_updates"] for r in mreps)
                        / max(a.fp64_steps, 1) / (msm * 1e-3),
                        "cell_pseudo_steps_per_s": len(B_OVER_DX) * NSTEPS * c.ncells / (msm * 1e-3)}
     fp64_out = mode_out["fp64_cg"]
+    modes["fp64_cg"]["roofline"] = fp64_roofline(fp64_reps, outs[0].shape[0], modes["fp64_cg"]["ms_per_step"],
+                                                 max(a.fp64_steps, 1), measured_peaks()[0])
     for name in modes:
         modes[name]["maxrel_vs_fp64_gpu"] = max(float((m - f).abs().max() / f.abs().max())
                                                 for m, f in zip(mode_out[name], fp64_out))
@@ -687,6 +691,35 @@ def extras():
             bool(torch.equal(v[1][:, frozen], eps0[:, frozen])) for v in hx.values())}
     mesh.close()
     return res
+
+
+# FP64 operations of the FP64 conjugate-gradient path per cell (a fused multiply-add
+# counts two): an iteration's first pass forms p = r + beta p (2), the six-neighbour sum
+# (5), A p = dg p - ce s (3) and p.Ap (2); its second pass the sum and A p again (8),
+# x += alpha p, r -= alpha Ap and r.r (6): 26.  A step's initial residual c L x with
+# r.r and b.b: 12.  Bytes per cell and iteration: 24 (pass 1) + 40 (pass 2).
+FP64_FLOPS_PER_ITER, FP64_FLOPS_PER_INIT, FP64_BYTES_PER_ITER = 26, 12, 64
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def fp64_roofline(reps, nf, ms_per_step, steps, peaks):
+    """The FP64 path against GB300's FP64 units and against HBM, from the library's
+    operation counts (iters includes one initial residual per step and field)."""
+    flops = 0.0
+    by = 0.0
+    for r in reps:
+        n = r["cell_updates"] / max(r["iters"], 1)
+        inits = NSTEPS * nf
+        cg_it = r["iters"] - inits
+        flops += n * (FP64_FLOPS_PER_ITER * cg_it + FP64_FLOPS_PER_INIT * inits)
+        by += n * (FP64_BYTES_PER_ITER * cg_it + 24 * inits)
+    sec = ms_per_step * 1e-3 * steps
+    tf = flops / sec / 1e12
+    gbs = by / sec / 1e9
+    return {"bound": "fp64", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": tf / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 FP64 (no measured FP64 peak)",
+            "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+            "flops_per_cell_iteration": FP64_FLOPS_PER_ITER, "bytes_per_cell_iteration": FP64_BYTES_PER_ITER}
 
 
 def cpu_baseline(c, outs, fp64_out):
