@@ -253,7 +253,9 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
  * cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
  * reports ? &reports[i] : NULL, streams[i]) -- same results, bit for bit -- or, when
  * cells[i] is host memory, cg_coarse_grain_host with the same arguments (pos[i], w[i]
- * host memory too: the problem copies its inputs in and its result out), and up to
+ * host memory too: the problem copies its inputs in and its result out; host problems
+ * given the same pos, w and n share one copy of those inputs, made before any problem
+ * starts, in the mesh of the first of them to start), and up to
  * max_concurrent problems run at a time, each on a host thread of the library (the
  * calling thread is one of them), so their kernels overlap on the device where their
  * streams allow it.  Problems start longest first (estimated from cells, steps and

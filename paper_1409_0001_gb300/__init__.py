@@ -477,7 +477,7 @@ def coarse_grain_concurrent(meshes, pos, w, params, out=None, streams=None, max_
     problem by default).  pos[i] [3, n_i] and w[i] [nf, n_i] are f64 tensors (they may be
     shared between problems): all CUDA tensors, or all host tensors (pinned for fast
     copies), in which case every problem copies its inputs in and its result out as
-    coarse_grain_host does.  params is one Params or a list.  Returns the list of
+    coarse_grain_host does (problems given the same host tensors share one copy).  params is one Params or a list.  Returns the list of
     [nf, ncells_i] cell tensors (and the reports)."""
     import torch
     k = len(meshes)

@@ -425,6 +425,7 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     m->ws_diffuse.release();
     m->ws_small.release();
     m->ws_stage.release();
+    m->ws_shared_in.release();
     m->ws_batch.release();
     m->h_small.release();
     for (auto &e : m->graphs) graph_release(e);
@@ -720,6 +721,46 @@ cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64
     return s;
 }
 
+// The host-memory form of the method (cg_coarse_grain_host).  dpos/dw non-NULL: the
+// inputs are already on the device (a copy shared with other problems, complete once
+// `ready` has fired), else pos_host/w_host are copied into this mesh's staging buffer.
+// The result is staged in this mesh's buffer and copied to cells_host.
+static cg_status coarse_grain_host_impl(cg_mesh *m, int64_t n, const double *pos_host, int nfields,
+                                        const double *w_host, double *cells_host, const cg_params *p,
+                                        cg_report *rep, cudaStream_t st, const double *dpos_in,
+                                        const double *dw_in, cudaEvent_t ready) {
+    if (!m) return fail(CG_EINVAL, "mesh is NULL");
+    CGK_TRY(check_params(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
+    if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
+    if (!cells_host || (n > 0 && (!pos_host || !w_host)))
+        return fail(CG_EINVAL, "NULL host array");
+    const bool shared = dpos_in != nullptr;
+    const size_t b_pos = ((size_t)3 * n * 8 + 255) / 256 * 256;
+    const size_t b_w = ((size_t)nfields * n * 8 + 255) / 256 * 256;
+    const size_t b_c = (size_t)nfields * m->ncells * 8;
+    const size_t b_in = shared ? 0 : b_pos + b_w;
+    CGK_TRY(m->ws_stage.ensure(b_in + b_c + 256));
+    char *base = m->ws_stage.as<char>();
+    const double *dpos = shared ? dpos_in : (const double *)base;
+    const double *dw = shared ? dw_in : (const double *)(base + b_pos);
+    double *dc = (double *)(base + b_in);
+    if (shared) {
+        CGK_CUDA(cudaStreamWaitEvent(st, ready, 0));
+    } else if (n > 0) {
+        CGK_CUDA(cudaMemcpyAsync(base, pos_host, (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
+        CGK_CUDA(cudaMemcpyAsync(base + b_pos, w_host, (size_t)nfields * n * 8, cudaMemcpyHostToDevice, st));
+    }
+    if (rep) std::memset(rep, 0, sizeof(*rep));
+    CGK_TRY(deposit_run(m, n, dpos, nfields, dw, dc, p, rep, st));
+    cg_status s = diffuse_impl(m, nfields, dc, p, rep, st);
+    if (s != CG_OK && s != CG_ENOCONV) return s;
+    CGK_CUDA(cudaMemcpyAsync(cells_host, dc, b_c, cudaMemcpyDeviceToHost, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    prof_collect();
+    return s;
+}
+
 cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const int64_t *n,
                                      const double *const *pos, int nfields, const double *const *w,
                                      double *const *cells, const cg_params *params, cg_report *reports,
@@ -765,13 +806,55 @@ cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const in
         order[i] = i;
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // host problems given the same input arrays (pos, w and n) share one host-to-device
+    // copy, made here before any problem starts, into the shared-input buffer of the
+    // group's first problem in start order; the others wait for it on their streams.  A
+    // group whose copy cannot be set up runs unshared (each problem copies its own).
+    std::vector<const double *> sh_pos(nprob, nullptr), sh_w(nprob, nullptr);
+    std::vector<cudaEvent_t> sh_ev(nprob, nullptr);
+    std::vector<cudaEvent_t> events;
+    const bool nf_ok = nfields >= 1 && nfields <= 64;
+    for (int a = 0; a < nprob && nf_ok; ++a) {
+        const int i = order[a];
+        if (!host[i] || sh_pos[i] || n[i] <= 0 || n[i] >= ((int64_t)1 << 31) || !pos[i] || !w[i]) continue;
+        std::vector<int> members{i};
+        for (int b = a + 1; b < nprob; ++b) {
+            const int k = order[b];
+            if (host[k] && !sh_pos[k] && pos[k] == pos[i] && w[k] == w[i] && n[k] == n[i]) members.push_back(k);
+        }
+        if (members.size() < 2) continue;
+        const size_t b_pos = ((size_t)3 * n[i] * 8 + 255) / 256 * 256;
+        const size_t b_w = (size_t)nfields * n[i] * 8;
+        if (meshes[i]->ws_shared_in.ensure(b_pos + b_w) != CG_OK) continue;
+        char *base = meshes[i]->ws_shared_in.as<char>();
+        cudaStream_t st = (cudaStream_t)streams[i];
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaMemcpyAsync(base, pos[i], (size_t)3 * n[i] * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(base + b_pos, w[i], b_w, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaEventRecord(ev, st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(ev);
+            continue;
+        }
+        events.push_back(ev);
+        for (int k : members) {
+            sh_pos[k] = (const double *)base;
+            sh_w[k] = (const double *)(base + b_pos);
+            sh_ev[k] = ev;
+        }
+    }
     auto worker = [&](bool own_thread) {
         if (own_thread && cudaSetDevice(dev) != cudaSuccess) return;
         for (int j; (j = next.fetch_add(1)) < nprob;) {
             const int i = order[j];
             cg_report *ri = reports ? &reports[i] : nullptr;
-            status[i] = host[i] ? cg_coarse_grain_host(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
-                                                       ri, streams[i])
+            status[i] = host[i] ? coarse_grain_host_impl(meshes[i], n[i], pos[i], nfields, w[i], cells[i],
+                                                         &params[i], ri, (cudaStream_t)streams[i], sh_pos[i],
+                                                         sh_w[i], sh_ev[i])
                                 : cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i], ri,
                                                   streams[i]);
             if (status[i] != CG_OK) detail[i] = g_last_error;   // this thread's message
@@ -790,6 +873,7 @@ cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const in
     for (std::thread &t : pool) t.join();
     if (next.load() < nprob)   // a worker could not select the device: finish here
         worker(false);
+    for (cudaEvent_t ev : events) cudaEventDestroy(ev);
     for (int i = 0; i < nprob; ++i)
         if (status[i] != CG_OK) return fail(status[i], "problem %d: %s", i, detail[i].c_str());
     return CG_OK;
@@ -798,31 +882,8 @@ cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const in
 cg_status cg_coarse_grain_host(cg_mesh *m, int64_t n, const double *pos_host, int nfields,
                                const double *w_host, double *cells_host, const cg_params *p,
                                cg_report *rep, void *stream) {
-    if (!m) return fail(CG_EINVAL, "mesh is NULL");
-    CGK_TRY(check_params(p));
-    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
-    if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
-    if (!cells_host || (n > 0 && (!pos_host || !w_host)))
-        return fail(CG_EINVAL, "NULL host array");
-    cudaStream_t st = (cudaStream_t)stream;
-    size_t b_pos = ((size_t)3 * n * 8 + 255) / 256 * 256;
-    size_t b_w = ((size_t)nfields * n * 8 + 255) / 256 * 256;
-    size_t b_c = (size_t)nfields * m->ncells * 8;
-    CGK_TRY(m->ws_stage.ensure(b_pos + b_w + b_c + 256));
-    char *base = m->ws_stage.as<char>();
-    double *dpos = (double *)base, *dw = (double *)(base + b_pos), *dc = (double *)(base + b_pos + b_w);
-    if (n > 0) {
-        CGK_CUDA(cudaMemcpyAsync(dpos, pos_host, (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
-        CGK_CUDA(cudaMemcpyAsync(dw, w_host, (size_t)nfields * n * 8, cudaMemcpyHostToDevice, st));
-    }
-    if (rep) std::memset(rep, 0, sizeof(*rep));
-    CGK_TRY(deposit_run(m, n, dpos, nfields, dw, dc, p, rep, st));
-    cg_status s = diffuse_impl(m, nfields, dc, p, rep, st);
-    if (s != CG_OK && s != CG_ENOCONV) return s;
-    CGK_CUDA(cudaMemcpyAsync(cells_host, dc, b_c, cudaMemcpyDeviceToHost, st));
-    CGK_CUDA(cudaStreamSynchronize(st));
-    prof_collect();
-    return s;
+    return coarse_grain_host_impl(m, n, pos_host, nfields, w_host, cells_host, p, rep,
+                                  (cudaStream_t)stream, nullptr, nullptr, nullptr);
 }
 
 }  // extern "C"

@@ -101,6 +101,30 @@ def test_concurrent_host_buffers_equal_device_run(cg, problems):
         assert r["cell_updates"] == r_ref["cell_updates"]
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_concurrent_shared_host_inputs(cg, problems, k):
+    """The four bandwidths of one particle set given the same host arrays share one copy
+    of them (made before any problem starts); the other problems copy their own.  Every
+    result equals the device run's bits, whichever problems run together."""
+    import torch
+    probs, ref = problems
+    pos0, w0 = probs[0][1].cpu().pin_memory(), probs[0][2].cpu().pin_memory()
+    for p in probs[1:4]:
+        assert torch.equal(p[1].cpu(), pos0) and torch.equal(p[2].cpu(), w0)
+    pos = [pos0] * 4 + [p[1].cpu().pin_memory() for p in probs[4:]]
+    w = [w0] * 4 + [p[2].cpu().pin_memory() for p in probs[4:]]
+    out, reps = cg.coarse_grain_concurrent([p[0] for p in probs], pos, w, [p[3] for p in probs],
+                                           max_concurrent=k, report=True)
+    for (u_ref, r_ref), u, r in zip(ref, out, reps):
+        assert torch.equal(u, u_ref.cpu())
+        assert r["cell_updates"] == r_ref["cell_updates"]
+    # the inputs are untouched and a second call (buffers reused) gives the same bits
+    assert torch.equal(pos0, probs[0][1].cpu())
+    out2 = cg.coarse_grain_concurrent([p[0] for p in probs], pos, w, [p[3] for p in probs], max_concurrent=k)
+    for a, b in zip(out, out2):
+        assert torch.equal(a, b)
+
+
 def test_concurrent_full_size_benchmark_configuration(cg):
     """The benchmark's step as it times it: the 128^3 clustered case (2,000,000 spheres)
     at b/dx = 1, 2, 4, 8, two problems at a time -- the same bits as four calls in a row."""
