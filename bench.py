@@ -534,6 +534,7 @@ def extras():
         "modes": {k: {"ms": v[0], "cell_updates_per_s": v[2]["cell_updates"] / (v[0] * 1e-3),
                       "cell_pseudo_steps_per_s": 10 * 6e6 / (v[0] * 1e-3)} for k, v in out.items()},
         "particles_per_s": 5e6 / (out["fp32_fp64refine"][0] * 1e-3),
+        "ms_per_phase": {k: out["fp32_fp64refine"][2][k] for k in ("ms_locate", "ms_deposit", "ms_diffuse")},
         "mixed_speedup_vs_fp64_gpu": out["fp64_pcg"][0] / out["fp32_fp64refine"][0],
         "mixed_vs_fp64_maxrel": maxrel(out["fp32_fp64refine"][1], out["fp64_pcg"][1])}
     mesh.close()

@@ -426,6 +426,7 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     m->ws_small.release();
     m->ws_stage.release();
     m->ws_shared_in.release();
+    m->ws_order.release();
     m->ws_batch.release();
     m->h_small.release();
     for (auto &e : m->graphs) graph_release(e);

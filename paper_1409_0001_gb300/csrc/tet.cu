@@ -162,29 +162,61 @@ __device__ __forceinline__ int tet_inside_f(const TetDevice &t, int32_t tt, cons
 // box tests compare doubles exactly as integer keys; a candidate is settled from FP32
 // determinants when their signs are certain and from the FP64 coordinates otherwise,
 // and the largest-minimum search (no tet holds x) runs on FP64 coordinates only.
+// The point-location bucket of x (clamped into the bucket grid), or nbuckets if a
+// coordinate is not finite.
+__device__ __forceinline__ int tet_bucket(const TetDevice &t, const double *x) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ok = ok && (((__double2hiint(x[a]) >> 20) & 0x7ff) != 0x7ff);
+    if (!ok) return t.nb[0] * t.nb[1] * t.nb[2];
+    int bi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double q = floor(__dmul_rn(__dsub_rn(x[a], t.blo[a]), t.binv[a]));
+        bi[a] = q < 0.0 ? 0 : (q > (double)(t.nb[a] - 1) ? t.nb[a] - 1 : (int)q);
+    }
+    return (bi[2] * t.nb[1] + bi[1]) * t.nb[0] + bi[0];
+}
+
+// Particles grouped by bucket (a counting sort; the order within a bucket is arbitrary),
+// so that the lanes of a warp in k_tet_locate scan the same candidate list: bucket and
+// arrival rank per particle, then order[offset[bucket] + rank] = particle.
+__global__ void k_tet_bucket_count(int64_t n, const double *__restrict__ pos, TetDevice t,
+                                   int32_t *__restrict__ key, uint32_t *__restrict__ rank,
+                                   uint32_t *__restrict__ count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+        const int b = tet_bucket(t, x);
+        key[i] = b;
+        rank[i] = atomicAdd(&count[b], 1u);
+    }
+}
+
+__global__ void k_tet_bucket_scatter(int64_t n, const int32_t *__restrict__ key,
+                                     const uint32_t *__restrict__ rank,
+                                     const uint32_t *__restrict__ offset, int32_t *__restrict__ order) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        order[offset[key[i]] + rank[i]] = (int32_t)i;
+}
+
 __global__ void k_tet_locate(int64_t n, const double *__restrict__ pos, TetDevice t, int nf,
                              const double *__restrict__ w, int32_t *__restrict__ cell,
                              uint32_t *__restrict__ counts, uint32_t *__restrict__ ranks,
-                             unsigned long long *__restrict__ bad) {
+                             unsigned long long *__restrict__ bad, const int32_t *__restrict__ order) {
     unsigned long long n_out = 0, n_nonfinite = 0;
     uint32_t most = 0;   // largest per-cell count seen (counts != nullptr)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int nbk = t.nb[0] * t.nb[1] * t.nb[2];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = order ? (int64_t)order[j] : j;
         for (int f = 0; f < nf; ++f)
             if (((__double2hiint(w[(int64_t)f * n + i]) >> 20) & 0x7ff) == 0x7ff) ++n_nonfinite;
         double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
         int32_t found = -1;
-        bool ok = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ok = ok && (((__double2hiint(x[a]) >> 20) & 0x7ff) != 0x7ff);
-        if (ok) {
-            int bi[3];
-            for (int a = 0; a < 3; ++a) {
-                double q = floor(__dmul_rn(__dsub_rn(x[a], t.blo[a]), t.binv[a]));
-                int v = q < 0.0 ? 0 : (q > (double)(t.nb[a] - 1) ? t.nb[a] - 1 : (int)q);
-                bi[a] = v;
-            }
-            const int b = (bi[2] * t.nb[1] + bi[1]) * t.nb[0] + bi[0];
+        const int b = tet_bucket(t, x);
+        if (b < nbk) {
             const unsigned long long kx0 = tkey(x[0]), kx1 = tkey(x[1]), kx2 = tkey(x[2]);
             const int c0 = t.bucket_start[b], c1 = t.bucket_start[b + 1];
             bool any_box = false;
@@ -1107,6 +1139,10 @@ cg_status hex_build(cg_mesh *m, int nx, int ny, int nz, const double *xf, const 
     return CG_OK;
 }
 
+// Particle sets at least this large are grouped by point-location bucket before the
+// tet search (smaller ones are searched in their own order).
+constexpr int64_t kTetOrderMin = 1 << 16;
+
 cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                             int32_t *cell_out, uint32_t *counts, uint32_t *ranks,
                             unsigned long long *bad, cudaStream_t st) {
@@ -1114,10 +1150,38 @@ cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, co
         CGK_LAUNCH("hex_locate", (double)n * (24 + 8 * nf + 4), st,
                    k_hex_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
                                                                 counts, ranks, bad));
-    else
+    else {
+        // large sets: group the particles by bucket first (a counting sort) so that a
+        // warp's lanes share their candidate lists; the results do not depend on the order
+        const int32_t *order = nullptr;
+        const TetDevice &t = m->tet;
+        const int64_t nbk = (int64_t)t.nb[0] * t.nb[1] * t.nb[2];
+        if (n >= kTetOrderMin) {
+            const size_t s_n = ((size_t)n * 4 + 255) / 256 * 256;
+            const size_t s_b = ((size_t)(nbk + 2) * 4 + 255) / 256 * 256;
+            const size_t s_t = (scan_tmp_words(nbk + 2) * 4 + 255) / 256 * 256;
+            CGK_TRY(m->ws_order.ensure(3 * s_n + 2 * s_b + s_t));
+            char *base = m->ws_order.as<char>();
+            int32_t *key = (int32_t *)base;
+            uint32_t *rank = (uint32_t *)(base + s_n);
+            int32_t *ord = (int32_t *)(base + 2 * s_n);
+            uint32_t *cnt = (uint32_t *)(base + 3 * s_n);
+            uint32_t *off = (uint32_t *)(base + 3 * s_n + s_b);
+            uint32_t *tmp = (uint32_t *)(base + 3 * s_n + 2 * s_b);
+            CGK_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nbk + 2) * 4, st));
+            CGK_LAUNCH("tet_bucket_count", (double)n * 32, st,
+                       k_tet_bucket_count<<<grid1d(n), kThreads, 0, st>>>(n, pos, t, key, rank, cnt));
+            CGK_CUDA(cudaGetLastError());
+            CGK_TRY(exclusive_scan_u32(cnt, off, nbk + 2, tmp, st));
+            CGK_LAUNCH("tet_bucket_scatter", (double)n * 12, st,
+                       k_tet_bucket_scatter<<<grid1d(n), kThreads, 0, st>>>(n, key, rank, off, ord));
+            CGK_CUDA(cudaGetLastError());
+            order = ord;
+        }
         CGK_LAUNCH("tet_locate", (double)n * (24 + 8 * nf + 4), st,
                    k_tet_locate<<<grid1d(n), kThreads, 0, st>>>(n, pos, m->tet, nf, w, cell_out,
-                                                                counts, ranks, bad));
+                                                                counts, ranks, bad, order));
+    }
     CGK_CUDA(cudaGetLastError());
     return CG_OK;
 }

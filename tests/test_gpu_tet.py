@@ -71,6 +71,37 @@ def test_tet_locate_bit_exact(cg, orc, small_mesh):
     assert np.array_equal(got.cpu().numpy(), ref)
 
 
+def test_tet_locate_bucket_ordered_bit_exact(cg, orc, small_mesh):
+    """A set large enough to be grouped by point-location bucket before the search
+    (at least 65,536 particles): the same cells as the oracle, including points on
+    vertices and faces, outside the mesh and not finite; deposition bit-exact too."""
+    xyz, tets, mesh = small_mesh
+    rng = np.random.default_rng(23)
+    n = 90_000
+    pos = rng.random((3, n))
+    k = 3000
+    pos[:, :k] = xyz[rng.integers(0, len(xyz), k)].T
+    fc = xyz[tets[rng.integers(0, len(tets), k)][:, :3]].mean(axis=1)
+    pos[:, k:2 * k] = fc.T
+    pos[:, 2 * k] = (1.2, 0.5, 0.5)
+    pos[:, 2 * k + 1] = (0.5, np.nan, 0.5)
+    pos[:, 2 * k + 2] = (-np.inf, 0.5, 0.5)
+    perm = rng.permutation(n)
+    pos = pos[:, perm]
+    ref, nref = orc.locate_tet(xyz, tets, pos)
+    got, nout = cg.locate(mesh, dev(pos))
+    assert nout == nref == 3
+    assert np.array_equal(got.cpu().numpy(), ref)
+    inside = ref >= 0
+    p_in = pos[:, inside]
+    w = np.vstack([np.full(p_in.shape[1], 3e-7), rng.standard_normal(p_in.shape[1])])
+    vc, *_ = orc.tet_build(xyz, tets)
+    for mode in (0, 1):
+        eps, _ = orc.deposit(ref[inside], w, len(tets), vc=vc, mode=mode)
+        d = cg.deposit(mesh, dev(p_in), dev(w), cg.Params(deposit_mode=mode)).cpu().numpy()
+        assert np.array_equal(bits(d), bits(eps))
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_tet_deposit_bit_exact(cg, orc, small_mesh, mode):
     xyz, tets, mesh = small_mesh
