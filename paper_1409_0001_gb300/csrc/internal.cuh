@@ -123,6 +123,8 @@ struct TetDevice {
     double *xyz = nullptr;       // [nverts][3]
     int32_t *tv = nullptr;       // [ntets][4]
     double *box = nullptr;       // [ntets][6] lo.x lo.y lo.z hi.x hi.y hi.z
+    float *edge32 = nullptr;     // [ntets][9] v1 - v0, v2 - v0, v3 - v0: FP64 differences
+                                 // rounded to FP32 (the inside test's edge vectors)
     int32_t *bucket_start = nullptr;  // [nbuckets+1]
     int32_t *bucket_tets = nullptr;   // tet ids, ascending within a bucket
     int nb[3] = {0, 0, 0};

@@ -101,21 +101,19 @@ __device__ __forceinline__ float det3f(const float *a, const float *b, const flo
 
 // Whether x is in tet tt by the FP64 definition (all four lambda >= 0), decided from
 // FP32 determinants when their signs are certain: 1 inside, 0 outside, -1 undecided.
-// With e_i = v_i - v0 and q = x - v0 (FP64 differences, then FP32), the coordinates'
+// With e_i = v_i - v0 (kept per tet) and q = x - v0 (FP64 differences, then FP32), the coordinates'
 // numerators are det(q,e2,e3), det(e1,q,e3), det(e1,e2,q) and D minus those three (the
 // four sum to D exactly); the FP64 definition evaluates the same determinants with errors
 // below 2^-50 of their permanents, far inside the bounds used here.
 __device__ __forceinline__ int tet_inside_f(const TetDevice &t, int32_t tt, const double *x) {
     const double *v0 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 0];
-    const double *v1 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 1];
-    const double *v2 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 2];
-    const double *v3 = t.xyz + 3 * (size_t)t.tv[4 * (size_t)tt + 3];
+    const float *ev = t.edge32 + 9 * (size_t)tt;   // precomputed: same roundings as below
     float e1[3], e2[3], e3[3], q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        e1[k] = __double2float_rn(__dsub_rn(v1[k], v0[k]));
-        e2[k] = __double2float_rn(__dsub_rn(v2[k], v0[k]));
-        e3[k] = __double2float_rn(__dsub_rn(v3[k], v0[k]));
+        e1[k] = ev[k];
+        e2[k] = ev[3 + k];
+        e3[k] = ev[6 + k];
         q[k] = __double2float_rn(__dsub_rn(x[k], v0[k]));
     }
     float bD, b1, b2, b3;
@@ -854,7 +852,7 @@ __global__ void __launch_bounds__(kThreads) k_hcheb(Op o, int nf, const TS *__re
 // ============================================================================ host: build
 void tet_release(cg_mesh *m) {
     TetDevice &t = m->tet;
-    void *ptrs[] = {t.vc, t.diagL, t.offc, t.offv, t.offv32, t.xyz, t.tv, t.box, t.bucket_start,
+    void *ptrs[] = {t.vc, t.diagL, t.offc, t.offv, t.offv32, t.xyz, t.tv, t.box, t.edge32, t.bucket_start,
                     t.bucket_tets, t.faces};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1055,6 +1053,18 @@ cg_status tet_build(cg_mesh *m, int64_t nv, const double *xyz, int64_t nt, const
     CGK_TRY(upload(&td.xyz, xyz, 3 * (size_t)nv));
     CGK_TRY(upload(&td.tv, tv, 4 * (size_t)nt));
     CGK_TRY(upload(&td.box, box.data(), box.size()));
+    std::vector<float> edge((size_t)9 * nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        const double *v0 = xyz + 3 * (size_t)tv[4 * t];
+        for (int j = 1; j < 4; ++j) {
+            const double *vj = xyz + 3 * (size_t)tv[4 * t + j];
+            for (int a = 0; a < 3; ++a) {
+                volatile double dd = vj[a] - v0[a];   // one FP64 rounding, then one to FP32
+                edge[9 * (size_t)t + 3 * (j - 1) + a] = (float)dd;
+            }
+        }
+    }
+    CGK_TRY(upload(&td.edge32, edge.data(), edge.size()));
     CGK_TRY(upload(&td.bucket_start, bstart.data(), bstart.size()));
     CGK_TRY(upload(&td.bucket_tets, btets.data(), btets.size()));
     return CG_OK;
