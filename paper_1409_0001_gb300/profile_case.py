@@ -5,7 +5,8 @@
 Builds a seeded random field on an n^3 (or --dims) unit-spaced hex mesh and smooths
 it --reps times with the chosen precision mode (see include/cg.h), b = --b-over-dx
 cells, --nsteps implicit-Euler steps (or, with --explicit-k K, --nsteps explicit steps
-in FP32 with K steps per launch).  Prints the device time of each call.
+in FP32 with K steps per launch; or, with --tet --locate N, the point location of N
+particles).  Prints the device time of each call.
 """
 from __future__ import annotations
 
@@ -39,6 +40,9 @@ def main(argv=None):
     ap.add_argument("--deposit", action="store_true",
                     help="ordered deposition of the clustered n^3 workload (2,000,000 spheres "
                          "at n = 128) instead of a diffusion")
+    ap.add_argument("--locate", type=int, default=0,
+                    help="with --tet: point location of N particles of the layered workload "
+                         "(a dense bottom layer) on the Kuhn tet mesh instead of a diffusion")
     a = ap.parse_args(argv)
 
     import numpy as np
@@ -83,6 +87,17 @@ def main(argv=None):
     if a.tet:
         xyz, tets = W.kuhn_tet_mesh(a.n)
         mesh = cg.TetMesh(xyz, tets)
+        if a.locate:
+            pos = torch.from_numpy(W.layered_cube(n_particles=a.locate)[0]).cuda()
+            for r in range(a.reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, nout = cg.locate(mesh, pos)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                print("rep %d: %.3f ms, %d outside, %.3e particles/s" % (r, dt * 1e3, nout, a.locate / dt))
+            mesh.close()
+            return
     else:
         mesh = cg.StructuredMesh(dims, (0.0, 0.0, 0.0), dx)
     rng = np.random.default_rng(0)
