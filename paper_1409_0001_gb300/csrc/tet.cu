@@ -522,13 +522,26 @@ __global__ void k_texplicit(Op o, const double *__restrict__ xin, double *__rest
 }
 
 // ---------------------------------------------------------------- mixed precision
+// x_out = x_in + d (the refinement update of every field; FP64 = FP64 + FP32)
+template <class TS>
+__global__ void k_tadd(size_t n, const double *__restrict__ xin, const TS *__restrict__ d,
+                       double *__restrict__ xout) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        xout[i] = xin[i] + (double)ldf(d, i);
+}
+
 // One FP64 refinement pass, fused with the initialisation of the next inner solve.
 // kFirst: x = u^n, r = dtau L x, b = M x (CN: + dtau/2 L x, stored in bout).
 // Otherwise x = x_in + d (at the cell and its neighbours), x_out = x, r = b - A x
 // with b = M u^n (IE, from ub) or the stored CN right-hand side (bptr).
 // Then the inner PCG starts from d = 0 (zeroed by the host after this pass):
 // rin = r, z = r / diag(A), p = z.
-template <class TS, bool kFirst>
+// kPcg false (Chebyshev inner solves): only rin is started (no z, p or r.z), and a
+// non-first pass reads x_in as the updated iterate itself (d = NULL, x_out unused; the
+// update x += d ran before as k_tadd, so neighbours cost no conversions or additions on
+// the FP64 units, which bound this pass on GB300).
+template <class TS, bool kFirst, bool kPcg = true>
 __global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
                           const TS *__restrict__ d_all, const double *__restrict__ ub_all,
                           const double *__restrict__ bcn_all, double *__restrict__ xout_all,
@@ -538,7 +551,7 @@ __global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
     const int f = blockIdx.y;
     const size_t off = (size_t)f * o.n;
     const double *xin = xin_all + off;
-    const TS *d = kFirst ? nullptr : d_all + off;
+    const TS *d = (kFirst || !kPcg) ? nullptr : d_all + off;
     double rr = 0, bb = 0, rz = 0;
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
         double rk;
@@ -553,19 +566,27 @@ __global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
             }
             bb += bk * bk;
         } else {
-            double xk = xin[k] + (double)ldf(d, k);
-            double lx = lap_row<double>(o, k, xk, [&](int l) { return xin[l] + (double)ldf(d, l); });
+            double xk, lx;
+            if (kPcg) {
+                xk = xin[k] + (double)ldf(d, k);
+                lx = lap_row<double>(o, k, xk, [&](int l) { return xin[l] + (double)ldf(d, l); });
+                xout_all[off + k] = xk;
+            } else {
+                xk = xin[k];
+                lx = lap_row<double>(o, k, xk, [&](int l) { return xin[l]; });
+            }
             double bk = scheme == 1 ? bcn_all[off + k] : o.vc[k] * ub_all[off + k];
             rk = bk - (o.vc[k] * xk - o.dte * lx);
-            xout_all[off + k] = xk;
         }
         float rf = (float)rk;
-        float zf = rf * o.iadiag32[k];
         stf(rin_all, off + k, rf);
-        stf(z_all, off + k, zf);
-        stf(p_all, off + k, zf);
+        if (kPcg) {
+            float zf = rf * o.iadiag32[k];
+            stf(z_all, off + k, zf);
+            stf(p_all, off + k, zf);
+            rz += (double)rf * (double)zf;
+        }
         rr += rk * rk;
-        rz += (double)rf * (double)zf;
     }
     double v[3] = {block_sum(rr), block_sum(rz), kFirst ? block_sum(bb) : 0.0};
     double *partials = partials_all + (size_t)f * 3 * gridDim.x;
@@ -1464,10 +1485,16 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     }
     int s = 0;
     for (; s < p->nsteps; ++s) {
-        CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 4 * sizeof(TS)), st,
-                   (k_trefine<TS, true><<<grid, kThreads, 0, st>>>(
-                       o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin, Z, Pp[0],
-                       partials, sc)));
+        if (have_cheb)
+            CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 2 * sizeof(TS)), st,
+                       (k_trefine<TS, true, false><<<grid, kThreads, 0, st>>>(
+                           o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin, nullptr,
+                           nullptr, partials, sc)));
+        else
+            CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 4 * sizeof(TS)), st,
+                       (k_trefine<TS, true><<<grid, kThreads, 0, st>>>(
+                           o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin, Z, Pp[0],
+                           partials, sc)));
         CGK_CUDA(cudaMemsetAsync(D, 0, (size_t)n * nf * sizeof(TS), st));
         applications += 1;
         double *xcur = ubuf;
@@ -1535,10 +1562,20 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             }
             // x += d, new FP64 residual, start of the next inner solve
             double *xnext = (xcur == F1) ? F2 : F1;
-            CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) * 5 + 16), st,
-                       (k_trefine<TS, false><<<grid, kThreads, 0, st>>>(
-                           o, p->scheme, xcur, dsol, ubuf, B, xnext, nullptr, Rin, Z, Pp[0], partials,
-                           sc)));
+            if (have_cheb) {
+                CGK_LAUNCH("tadd", (double)n * nf * (16 + sizeof(TS)), st,
+                           k_tadd<TS><<<grid1d((int64_t)n * nf), kThreads, 0, st>>>((size_t)n * nf, xcur, dsol,
+                                                                                 xnext));
+                CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) + 8), st,
+                           (k_trefine<TS, false, false><<<grid, kThreads, 0, st>>>(
+                               o, p->scheme, xnext, nullptr, ubuf, B, nullptr, nullptr, Rin, nullptr,
+                               nullptr, partials, sc)));
+            } else {
+                CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) * 5 + 16), st,
+                           (k_trefine<TS, false><<<grid, kThreads, 0, st>>>(
+                               o, p->scheme, xcur, dsol, ubuf, B, xnext, nullptr, Rin, Z, Pp[0],
+                               partials, sc)));
+            }
             CGK_CUDA(cudaGetLastError());
             if (!have_cheb) CGK_CUDA(cudaMemsetAsync(D, 0, (size_t)n * nf * sizeof(TS), st));
             applications += 1;
