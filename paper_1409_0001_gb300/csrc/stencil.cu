@@ -1988,9 +1988,9 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
 // ---------------------------------------------------------------- batched snapshots
 // Many independent snapshots (each its own hex mesh, bandwidth and Chebyshev count) are
 // smoothed by one persistent cooperative launch in the double-float modes.  Phases:
-// u^0 -> double-float; then per pseudo-step the first refinement pass, R rounds of
-// (m_s - 1 Chebyshev iterations, one refinement pass), with a bounded grid barrier
-// after every phase.  Work items (tile x z-chunk x field of one snapshot) are dealt to
+// u^0 -> double-float; the first refinement pass of the first pseudo-step; then per
+// pseudo-step R rounds of (m_s - 1 Chebyshev iterations, one refinement pass), the last
+// of which also starts the next step; a bounded grid barrier after every phase.  Work items (tile x z-chunk x field of one snapshot) are dealt to
 // blocks round-robin; a snapshot whose m_s is smaller than the longest idles in the
 // remaining Chebyshev phases.  Buffer roles are fixed: the first Chebyshev iterate is
 // in Ya and, m_s being even, the correction always ends in Yb; the first round writes X1, later
@@ -2022,9 +2022,14 @@ __device__ __forceinline__ DF ldcg_df(const DF *p, int i) {
     return DF{v.x, v.y};
 }
 
+// part: this item's ||r||^2 partial of a step's last pass (or ||b||^2 of its first pass).
+// part_next (a step's last pass, not the call's last step): the pass also starts the next
+// step, as the single-mesh path's last refinement pass does: with x = u^{n+1} it has A x at
+// hand, so the next first residual is c L x = (x - A x) / theta (and the Crank-Nicolson
+// right-hand side x + c/2 L x), and that step's ||b||^2 partial goes to part_next.
 template <class TS>
 __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BItem &it, bool first,
-                                               int round, int R, double *part) {
+                                               int round, int R, double *part, double *part_next) {
     const Geo &g = d.g;
     const int f = it.zf / d.nzc;
     const int zc = it.zf - f * d.nzc;
@@ -2033,7 +2038,7 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     __shared__ DF sdg[8];
     stage_table(sdg, d.cfdf.dg);
     __syncthreads();
-    float acc = 0.0f;
+    float acc = 0.0f, acc_b = 0.0f;
     const float gamma = d.gamma;
     TS *r = d.R + off;
     TS *y1 = d.Ya + off;
@@ -2060,18 +2065,34 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
         const DF *xin = (round == 1 ? d.U : ((round & 1) ? d.X2 : d.X1)) + off;
         DF *xout = (round == R ? d.U : ((round & 1) ? d.X1 : d.X2)) + off;
         const DF *b = (d.scheme == 1 ? d.B : d.U) + off;
+        DF *bo = d.B + off;
         const TS *dd = d.Yb + off;
+        const bool next = part_next != nullptr;
         sweep25_at<DF>(
             g, it.bx, it.by, z0, z1, [&](int k) { return df_add_f(ldcg_df(xin, k), ldcg(dd, k)); },
             [&](int k) { return ldcg_df(b, k); },
             [&](int k, DF v, DF sm, int nn, DF bk) {
                 xout[k] = v;
-                DF rk = bk - (df_mul(sdg[nn], v) - df_mul(d.cfdf.ce, sm));
-                float rf = df_f(rk);
+                const DF ax = df_mul(sdg[nn], v) - df_mul(d.cfdf.ce, sm);
+                float rf = df_f(bk - ax);
+                acc = fmaf(rf, rf, acc);
+                if (next) {
+                    DF cl = v - ax;                    // = theta c L v
+                    DF bn = v;
+                    if (d.scheme == 1) {
+                        bn = v + cl;                  // v + c/2 L v
+                        cl = cl + cl;                 // c L v
+                        bo[k] = bn;                   // read above at this cell only
+                    }
+                    const float bf = df_f(bn);
+                    acc_b = fmaf(bf, bf, acc_b);
+                    rf = df_f(cl);
+                }
                 st(r, k, rf);
                 st(y1, k, gamma * rf);
-                acc = fmaf(rf, rf, acc);
             });
+        const double tb = block_sum_f(acc_b);
+        if (is_thread0() && next) *part_next = tb;
     }
     double tot = block_sum_f(acc);
     if (is_thread0() && part) *part = tot;
@@ -2130,11 +2151,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_batched(const SnapDesc<TS> *__r
     }
     if (!grid_sync(gb, gridDim.x, budget)) return;
     for (int step = 0; step < nsteps; ++step) {
-        for (int i = blockIdx.x; i < nr; i += gridDim.x) {
-            const BItem it = ritems[i];
-            batched_refine<TS>(sd[it.snap], it, true, 0, R, part_bb + (size_t)step * nr + i);
+        if (step == 0) {   // later steps were started by the previous step's last pass
+            for (int i = blockIdx.x; i < nr; i += gridDim.x) {
+                const BItem it = ritems[i];
+                batched_refine<TS>(sd[it.snap], it, true, 0, R, part_bb + i, nullptr);
+            }
+            if (!grid_sync(gb, gridDim.x, budget)) return;
         }
-        if (!grid_sync(gb, gridDim.x, budget)) return;
         for (int round = 1; round <= R; ++round) {
             for (int k = 1; k < mmax; ++k) {
                 for (int i = blockIdx.x; i < nc; i += gridDim.x) {
@@ -2146,7 +2169,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_batched(const SnapDesc<TS> *__r
             for (int i = blockIdx.x; i < nr; i += gridDim.x) {
                 const BItem it = ritems[i];
                 batched_refine<TS>(sd[it.snap], it, false, round, R,
-                                   round == R ? part_rr + (size_t)step * nr + i : nullptr);
+                                   round == R ? part_rr + (size_t)step * nr + i : nullptr,
+                                   round == R && step + 1 < nsteps ? part_bb + (size_t)(step + 1) * nr + i
+                                                                   : nullptr);
             }
             if (step + 1 < nsteps || round < R)
                 if (!grid_sync(gb, gridDim.x, budget)) return;
@@ -4139,7 +4164,9 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
             if (rep) {
                 long long apps = 0, upd = 0;
                 for (const auto &d : P.descs) {
-                    long long a = (long long)p->nsteps * (1 + (long long)R * d.m);
+                    // the first pass of the first step, then R rounds of m applications
+                    // per step (a step's last pass also starts the next one)
+                    long long a = 1 + (long long)p->nsteps * R * d.m;
                     apps += a;
                     upd += a * d.g.n;
                 }
