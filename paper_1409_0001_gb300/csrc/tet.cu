@@ -355,6 +355,7 @@ struct Op {          // the operator seen by the kernels
     double dtau;     // full dtau (for the residual of the first pass)
     const float *adiag32 = nullptr;    // FP32 diagonal of A, V_c - dte L_kk (inner solves)
     const float *iadiag32 = nullptr;   // its reciprocal (the Jacobi preconditioner)
+    const float *wsc32 = nullptr;      // [ns][n] dte T_f / A_kk (the Jacobi-scaled off-diagonals)
     int ns = 4;                        // neighbour slots per cell (4 tets, 6 stretched hex)
     int hx = 0, hy = 0, hz = 0;        // stretched hex mesh: cells per axis (0 for tets)
 };
@@ -367,6 +368,16 @@ __global__ void k_tdiag32(int n, const double *__restrict__ vc, const double *__
         const double a = vc[k] - dte * diagL[k];
         ad[k] = (float)a;
         iad[k] = (float)(1.0 / a);
+    }
+}
+
+// Jacobi-scaled off-diagonal weights of A for this call's dte: w[q][k] = dte T_q / A_kk,
+// from the FP64 values, rounded once to FP32
+__global__ void k_tscaled(int n, int ns, const double *__restrict__ vc, const double *__restrict__ diagL,
+                          const double *__restrict__ offv, double dte, float *__restrict__ w) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double a = vc[k] - dte * diagL[k];
+        for (int q = 0; q < ns; ++q) w[(size_t)q * n + k] = (float)(dte * offv[(size_t)q * n + k] / a);
     }
 }
 
@@ -580,6 +591,7 @@ __global__ void k_trefine(Op o, int scheme, const double *__restrict__ xin_all,
         }
         float rf = (float)rk;
         stf(rin_all, off + k, rf);
+        if (!kPcg && z_all) stf(z_all, off + k, rf * o.iadiag32[k]);   // D^-1 r for k_tcheb1
         if (kPcg) {
             float zf = rf * o.iadiag32[k];
             stf(z_all, off + k, zf);
@@ -749,20 +761,19 @@ __global__ void k_tprobe_init(Op o, TS *__restrict__ rin, TS *__restrict__ z, TS
 // arithmetic, TS storage), spectrum enclosed in [theta - delta, theta + delta]: from
 // d_0 = 0, d_1 = c0 D^-1 r; then d_{k+1} = d_k + c1 (d_k - d_{k-1}) + c2 D^-1 (r - A d_k)
 // (dkm1 null: d_0 = 0).  No inner products, one pass per iteration.  This form handles
-// one field (the launch's y index picks it); k_tcheb below handles several.
+// one field; it reads the scaled residual rs = D^-1 r (written by the refinement pass)
+// and the scaled weights w_q = dte T_q / A_kk, so that D^-1 (r - A d) = rs - d_k +
+// sum_q w_q d_nb(q): a cell's operator row is NS indices and NS weights (32 B on tets),
+// no diagonal.  k_tcheb below handles several fields.
 template <class TS, int NS>
-__global__ void __launch_bounds__(kThreads, 6) k_tcheb1(Op o, const TS *__restrict__ r_all,
-                                                        const TS *__restrict__ dk_all,
-                                                        const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all,
+__global__ void __launch_bounds__(kThreads, 6) k_tcheb1(Op o, const TS *__restrict__ rs,
+                                                        const TS *__restrict__ dk,
+                                                        const TS *__restrict__ dkm1, TS *__restrict__ dn,
                                                         float c1, float c2) {
-    const size_t off = (size_t)blockIdx.y * o.n;
-    const TS *r = r_all + off;
-    const TS *dk = dk_all + off;
-    const float dte = (float)o.dte;
     const int stride = gridDim.x * kThreads;
     // two cells per pass (k and k + stride): both cells' NS neighbour indices and
-    // transmissibilities are loaded before either cell's gathers, so twice the dependent
-    // loads are in flight per thread
+    // weights are loaded before either cell's gathers, so twice the dependent loads are
+    // in flight per thread
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += 2 * stride) {
         const int k2 = k + stride;
         const bool two = k2 < o.n;
@@ -772,9 +783,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_tcheb1(Op o, const TS *__restri
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
             nb[0][q] = o.offc[(size_t)q * o.n + k];
-            wv[0][q] = o.offv32[(size_t)q * o.n + k];
+            wv[0][q] = o.wsc32[(size_t)q * o.n + k];
             nb[1][q] = o.offc[(size_t)q * o.n + kb];
-            wv[1][q] = o.offv32[(size_t)q * o.n + kb];
+            wv[1][q] = o.wsc32[(size_t)q * o.n + kb];
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -783,9 +794,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_tcheb1(Op o, const TS *__restri
 #pragma unroll
             for (int q = 0; q < NS; ++q) off_sum += wv[c][q] * ldf(dk, nb[c][q]);
             const float dkk = ldf(dk, kc);
-            const float res = ldf(r, kc) - (o.adiag32[kc] * dkk - dte * off_sum);
-            const float dm = dkm1_all ? ldf(dkm1_all + off, kc) : 0.f;   // d_0 = 0
-            if (c == 0 || two) stf(dn_all, off + kc, dkk + c1 * (dkk - dm) + c2 * (o.iadiag32[kc] * res));
+            const float sres = (ldf(rs, kc) - dkk) + off_sum;   // D^-1 (r - A d_k)
+            const float dm = dkm1 ? ldf(dkm1, kc) : 0.f;        // d_0 = 0
+            if (c == 0 || two) stf(dn, kc, dkk + c1 * (dkk - dm) + c2 * sres);
         }
     }
 }
@@ -1404,7 +1415,9 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     const dim3 grid(G, nf);
     const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
     const size_t v32 = align_up((size_t)n * 4);
-    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts + 2 * v32));
+    // one field on a tet mesh: the Chebyshev pass uses Jacobi-scaled weights (k_tcheb1)
+    const bool scaled = nf == 1 && o.hx == 0;
+    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts + (2 + (scaled ? o.ns : 0)) * v32));
     char *wb = m->ws_diffuse.as<char>();
     {   // FP32 diagonal of A and its reciprocal for this call's dtau
         float *ad = (float *)(wb + 3 * v64 + 7 * vts), *iad = (float *)(wb + 3 * v64 + 7 * vts + v32);
@@ -1413,6 +1426,13 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
         CGK_CUDA(cudaGetLastError());
         o.adiag32 = ad;
         o.iadiag32 = iad;
+        if (scaled) {
+            float *w = (float *)(wb + 3 * v64 + 7 * vts + 2 * v32);
+            CGK_LAUNCH("tscaled", (double)n * (16 + 12.0 * o.ns), st,
+                       k_tscaled<<<G, kThreads, 0, st>>>(n, o.ns, o.vc, o.diagL, o.offv, o.dte, w));
+            CGK_CUDA(cudaGetLastError());
+            o.wsc32 = w;
+        }
     }
     double *X1 = (double *)wb, *X2 = (double *)(wb + v64), *B = (double *)(wb + 2 * v64);
     TS *Rin = (TS *)(wb + 3 * v64), *Z = (TS *)(wb + 3 * v64 + vts), *Q = (TS *)(wb + 3 * v64 + 2 * vts);
@@ -1488,8 +1508,8 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
         if (have_cheb)
             CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 2 * sizeof(TS)), st,
                        (k_trefine<TS, true, false><<<grid, kThreads, 0, st>>>(
-                           o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin, nullptr,
-                           nullptr, partials, sc)));
+                           o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin,
+                           scaled ? Z : nullptr, nullptr, partials, sc)));
         else
             CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 4 * sizeof(TS)), st,
                        (k_trefine<TS, true><<<grid, kThreads, 0, st>>>(
@@ -1522,10 +1542,10 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                                (double)n * (6 * 4 + 8 + nf * 4.0 * sizeof(TS)), st,
                                k_hcheb<TS><<<hgrid, hblk, 0, st>>>(o, nf, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3],
                                                                        cheb.c1[k - 1], cheb.c2[k - 1]));
-                else if (nf == 1)
-                    CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (rb32 - 8 + 4.0 * sizeof(TS)),
+                else if (scaled)   // bytes: the row's indices and scaled weights, rs, d_k, d_{k-1}, d_{k+1}
+                    CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (8.0 * o.ns + 4.0 * sizeof(TS)),
                                st, (o.ns == 4 ? k_tcheb1<TS, 4> : k_tcheb1<TS, 6>)<<<G, kThreads, 0, st>>>(
-                                       o, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1]));
+                                       o, Z, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1]));
                 else
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32",
                                (double)n * (rb32 - 8 + nf * 4.0 * sizeof(TS)), st,
@@ -1568,8 +1588,8 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                                                                                  xnext));
                 CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) + 8), st,
                            (k_trefine<TS, false, false><<<grid, kThreads, 0, st>>>(
-                               o, p->scheme, xnext, nullptr, ubuf, B, nullptr, nullptr, Rin, nullptr,
-                               nullptr, partials, sc)));
+                               o, p->scheme, xnext, nullptr, ubuf, B, nullptr, nullptr, Rin,
+                               scaled ? Z : nullptr, nullptr, partials, sc)));
             } else {
                 CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) * 5 + 16), st,
                            (k_trefine<TS, false><<<grid, kThreads, 0, st>>>(
