@@ -845,14 +845,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_tcheb(Op o, int nf, const TS *_
 // The Chebyshev iteration of k_tcheb on a stretched Cartesian mesh, whose neighbours are
 // implicit: slots 0..5 are the cells at k-1, k+1, k-nx, k+nx, k-nx ny, k+nx ny (a wall
 // slot has T = 0 and reads the cell itself), so the neighbour values load without first
-// loading their indices.  The sum runs over the slots in k_tcheb's order, so the result
-// is the same.  A block is blockDim.x cells of a row by blockDim.y rows (256 threads).
+// loading their indices.  Like k_tcheb1 it reads the scaled residual rs = D^-1 r and the
+// Jacobi-scaled weights dte T_q / A_kk (six per cell, no diagonal), for every field of
+// the call.  A block is blockDim.x cells of a row by blockDim.y rows (256 threads).
 template <class TS>
-__global__ void __launch_bounds__(kThreads) k_hcheb(Op o, int nf, const TS *__restrict__ r_all,
+__global__ void __launch_bounds__(kThreads) k_hcheb(Op o, int nf, const TS *__restrict__ rs_all,
                                                      const TS *__restrict__ dk_all,
                                                      const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all,
                                                      float c1, float c2) {
-    const float dte = (float)o.dte;
     const size_t n = (size_t)o.n;
     const int nx = o.hx, nxy = o.hx * o.hy, rows = o.hy * o.hz;
     for (int row = blockIdx.y * blockDim.y + threadIdx.y; row < rows; row += gridDim.y * blockDim.y) {
@@ -861,19 +861,18 @@ __global__ void __launch_bounds__(kThreads) k_hcheb(Op o, int nf, const TS *__re
             const int k = row * nx + ix;
             const int nb[6] = {ix > 0 ? k - 1 : k, ix + 1 < nx ? k + 1 : k, iy > 0 ? k - nx : k,
                                iy + 1 < o.hy ? k + nx : k, iz > 0 ? k - nxy : k, iz + 1 < o.hz ? k + nxy : k};
-            float wv[6];
+            float wv[6];   // Jacobi-scaled weights dte T_q / A_kk
 #pragma unroll
-            for (int q = 0; q < 6; ++q) wv[q] = o.offv32[(size_t)q * n + k];
-            const float ad = o.adiag32[k], iad = o.iadiag32[k];
+            for (int q = 0; q < 6; ++q) wv[q] = o.wsc32[(size_t)q * n + k];
             for (int f = 0; f < nf; ++f) {
                 const TS *dk = dk_all + f * n;
                 const float dkk = ldf(dk, k);
                 float off_sum = 0.f;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) off_sum += wv[q] * ldf(dk, nb[q]);
-                const float res = ldf(r_all, f * n + k) - (ad * dkk - dte * off_sum);
+                const float sres = (ldf(rs_all, f * n + k) - dkk) + off_sum;   // D^-1 (r - A d_k)
                 const float dm = dkm1_all ? ldf(dkm1_all, f * n + k) : 0.f;   // d_0 = 0
-                stf(dn_all, f * n + k, dkk + c1 * (dkk - dm) + c2 * (iad * res));
+                stf(dn_all, f * n + k, dkk + c1 * (dkk - dm) + c2 * sres);
             }
         }
     }
@@ -1415,8 +1414,9 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     const dim3 grid(G, nf);
     const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
     const size_t v32 = align_up((size_t)n * 4);
-    // one field on a tet mesh: the Chebyshev pass uses Jacobi-scaled weights (k_tcheb1)
-    const bool scaled = nf == 1 && o.hx == 0;
+    // one field on a tet mesh: the Chebyshev pass uses Jacobi-scaled weights (k_tcheb1),
+    // and so does a stretched hex mesh (k_hcheb, any number of fields)
+    const bool scaled = (nf == 1 && o.hx == 0) || o.hx > 0;
     CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts + (2 + (scaled ? o.ns : 0)) * v32));
     char *wb = m->ws_diffuse.as<char>();
     {   // FP32 diagonal of A and its reciprocal for this call's dtau
@@ -1539,8 +1539,8 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                 const TS *dm = k == 1 ? nullptr : Cb[(k - 1) % 3];
                 if (o.hx > 0)   // stretched hex mesh: implicit neighbours
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32",
-                               (double)n * (6 * 4 + 8 + nf * 4.0 * sizeof(TS)), st,
-                               k_hcheb<TS><<<hgrid, hblk, 0, st>>>(o, nf, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3],
+                               (double)n * (6 * 4 + nf * 4.0 * sizeof(TS)), st,
+                               k_hcheb<TS><<<hgrid, hblk, 0, st>>>(o, nf, Z, Cb[k % 3], dm, Cb[(k + 1) % 3],
                                                                        cheb.c1[k - 1], cheb.c2[k - 1]));
                 else if (scaled)   // bytes: the row's indices and scaled weights, rs, d_k, d_{k-1}, d_{k+1}
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (8.0 * o.ns + 4.0 * sizeof(TS)),
