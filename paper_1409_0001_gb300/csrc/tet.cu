@@ -801,30 +801,30 @@ __global__ void __launch_bounds__(kThreads, 6) k_tcheb1(Op o, const TS *__restri
     }
 }
 
-// The same iteration for nf fields (and the first step, d_1 = c1 D^-1 r, for any nf): a
-// thread reads a cell's operator row once and applies it to every field.  The
-// one-field loop above keeps more gathers in flight when there is only one.
+// The same iteration for nf fields: a thread reads a cell's operator row (indices and
+// scaled weights) once and applies it to every field; r_all is the scaled residual
+// rs = D^-1 r.  kFirst: the first step d_1 = c1 D^-1 r for any nf, with r_all the
+// residual r itself.  The one-field loop above keeps more gathers in flight when there
+// is only one.
 template <class TS, bool kFirst>
 __global__ void __launch_bounds__(kThreads, 4) k_tcheb(Op o, int nf, const TS *__restrict__ r_all,
                                                         const TS *__restrict__ dk_all,
                                                         const TS *__restrict__ dkm1_all, TS *__restrict__ dn_all,
                                                         float c1, float c2) {
-    const float dte = (float)o.dte;
     const size_t n = (size_t)o.n;
     for (int k = blockIdx.x * kThreads + threadIdx.x; k < o.n; k += gridDim.x * kThreads) {
         if constexpr (kFirst) {
             const float iad = o.iadiag32[k];
             for (int f = 0; f < nf; ++f) stf(dn_all, f * n + k, c1 * (iad * ldf(r_all, f * n + k)));
-        } else {   // the cell's operator row is read once for all fields
+        } else {   // the cell's operator row (indices, scaled weights) is read once for all fields
             int nb[kMaxSlots];
             float wv[kMaxSlots];
 #pragma unroll
             for (int q = 0; q < kMaxSlots; ++q) {
                 if (q >= o.ns) break;
                 nb[q] = o.offc[(size_t)q * n + k];
-                wv[q] = o.offv32[(size_t)q * n + k];
+                wv[q] = o.wsc32[(size_t)q * n + k];
             }
-            const float ad = o.adiag32[k], iad = o.iadiag32[k];
             for (int f = 0; f < nf; ++f) {
                 const TS *dk = dk_all + f * n;
                 const float dkk = ldf(dk, k);
@@ -834,9 +834,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_tcheb(Op o, int nf, const TS *_
                     if (q >= o.ns) break;
                     off_sum += wv[q] * ldf(dk, nb[q]);
                 }
-                const float res = ldf(r_all, f * n + k) - (ad * dkk - dte * off_sum);
+                const float sres = (ldf(r_all, f * n + k) - dkk) + off_sum;   // D^-1 (r - A d_k)
                 const float dm = dkm1_all ? ldf(dkm1_all, f * n + k) : 0.f;   // d_0 = 0
-                stf(dn_all, f * n + k, dkk + c1 * (dkk - dm) + c2 * (iad * res));
+                stf(dn_all, f * n + k, dkk + c1 * (dkk - dm) + c2 * sres);
             }
         }
     }
@@ -1414,10 +1414,9 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     const dim3 grid(G, nf);
     const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
     const size_t v32 = align_up((size_t)n * 4);
-    // one field on a tet mesh: the Chebyshev pass uses Jacobi-scaled weights (k_tcheb1),
-    // and so does a stretched hex mesh (k_hcheb, any number of fields)
-    const bool scaled = (nf == 1 && o.hx == 0) || o.hx > 0;
-    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts + (2 + (scaled ? o.ns : 0)) * v32));
+    // the Chebyshev passes (k_tcheb1, k_tcheb, k_hcheb) read Jacobi-scaled weights and
+    // the scaled residual D^-1 r, which the refinement passes write to Z
+    CGK_TRY(m->ws_diffuse.ensure(3 * v64 + 7 * vts + (2 + o.ns) * v32));
     char *wb = m->ws_diffuse.as<char>();
     {   // FP32 diagonal of A and its reciprocal for this call's dtau
         float *ad = (float *)(wb + 3 * v64 + 7 * vts), *iad = (float *)(wb + 3 * v64 + 7 * vts + v32);
@@ -1426,7 +1425,7 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
         CGK_CUDA(cudaGetLastError());
         o.adiag32 = ad;
         o.iadiag32 = iad;
-        if (scaled) {
+        {
             float *w = (float *)(wb + 3 * v64 + 7 * vts + 2 * v32);
             CGK_LAUNCH("tscaled", (double)n * (16 + 12.0 * o.ns), st,
                        k_tscaled<<<G, kThreads, 0, st>>>(n, o.ns, o.vc, o.diagL, o.offv, o.dte, w));
@@ -1509,7 +1508,7 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 2 * sizeof(TS)), st,
                        (k_trefine<TS, true, false><<<grid, kThreads, 0, st>>>(
                            o, p->scheme, ubuf, nullptr, nullptr, nullptr, nullptr, B, Rin,
-                           scaled ? Z : nullptr, nullptr, partials, sc)));
+                           Z, nullptr, partials, sc)));
         else
             CGK_LAUNCH("trefine64_first", (double)n * nf * (row_bytes(8) + 8 + 8 * cn + 4 * sizeof(TS)), st,
                        (k_trefine<TS, true><<<grid, kThreads, 0, st>>>(
@@ -1542,15 +1541,15 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                                (double)n * (6 * 4 + nf * 4.0 * sizeof(TS)), st,
                                k_hcheb<TS><<<hgrid, hblk, 0, st>>>(o, nf, Z, Cb[k % 3], dm, Cb[(k + 1) % 3],
                                                                        cheb.c1[k - 1], cheb.c2[k - 1]));
-                else if (scaled)   // bytes: the row's indices and scaled weights, rs, d_k, d_{k-1}, d_{k+1}
+                else if (nf == 1)   // bytes: the row's indices and scaled weights, rs, d_k, d_{k-1}, d_{k+1}
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (8.0 * o.ns + 4.0 * sizeof(TS)),
                                st, (o.ns == 4 ? k_tcheb1<TS, 4> : k_tcheb1<TS, 6>)<<<G, kThreads, 0, st>>>(
                                        o, Z, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1]));
                 else
                     CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32",
-                               (double)n * (rb32 - 8 + nf * 4.0 * sizeof(TS)), st,
+                               (double)n * (8.0 * o.ns + nf * 4.0 * sizeof(TS)), st,
                                (k_tcheb<TS, false><<<G, kThreads, 0, st>>>(
-                                   o, nf, Rin, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1])));
+                                   o, nf, Z, Cb[k % 3], dm, Cb[(k + 1) % 3], cheb.c1[k - 1], cheb.c2[k - 1])));
             }
             CGK_CUDA(cudaGetLastError());
             dsol = Cb[mi % 3];
@@ -1589,7 +1588,7 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
                 CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) + 8), st,
                            (k_trefine<TS, false, false><<<grid, kThreads, 0, st>>>(
                                o, p->scheme, xnext, nullptr, ubuf, B, nullptr, nullptr, Rin,
-                               scaled ? Z : nullptr, nullptr, partials, sc)));
+                               Z, nullptr, partials, sc)));
             } else {
                 CGK_LAUNCH("trefine64", (double)n * nf * (row_bytes(8) + 8 + sizeof(TS) * 5 + 16), st,
                            (k_trefine<TS, false><<<grid, kThreads, 0, st>>>(
