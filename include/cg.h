@@ -71,7 +71,8 @@ cg_status cg_create_mesh_structured(int nx, int ny, int nz, const double origin[
  * means), faces, and the two-point-flux finite-volume Laplacian
  * T_f = |S_f|^2 / (S_f . d_f) between face neighbours (S_f the face area vector out
  * of the first cell, d_f the centroid-to-centroid vector), M = diag(V_c); boundary
- * faces carry no flux.  Also builds the point-location buckets.
+ * faces carry no flux.  Also builds the point-location buckets and each tet's box and
+ * FP32 edge vectors for the inside test (device memory held until cg_destroy_mesh).
  * Errors: CG_EINVAL (vertex id out of range, a face shared by more than two tets, a
  * zero-volume tet, a non-positive transmissibility), CG_ENOMEM, CG_ECUDA. */
 cg_status cg_create_mesh_tet(int64_t nverts, const double *xyz_host, int64_t ntets,
@@ -209,8 +210,10 @@ typedef struct {
  * is outside).  Tet: the lowest-index tet whose bounding box holds x and whose four
  * barycentric coordinates (signed-volume ratios) are all >= 0; if none, the tet
  * with the largest minimum barycentric coordinate (lowest index on ties) when that
- * value is >= -1e-10; else outside.  *n_out_host receives the outside count.
- * Errors: CG_EINVAL, CG_ECUDA. */
+ * value is >= -1e-10; else outside.  The result does not depend on the particles'
+ * order (sets of 65,536 or more are searched grouped by location bucket, in a
+ * workspace kept with the mesh).  *n_out_host receives the outside count.
+ * Errors: CG_EINVAL, CG_ENOMEM, CG_ECUDA. */
 cg_status cg_locate(cg_mesh *mesh, int64_t n, const double *pos, int32_t *cell_out,
                     int64_t *n_out_host, void *stream);
 
