@@ -332,16 +332,22 @@ cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64
  * receives F per field.
  *
  * Scratch: a file-scope static device array of 128 + CG_NOALLOC_MAX_CELL_FIELDS
- * 64-bit words (about 16 MiB), which every GPU that loads the library holds until the
- * process exits.  The first call on a device looks up that array's device address
- * (once per device, with the device current); make that first call before any
- * stream capture.  Every call on a device shares the array and clears the part it
- * uses; calls whose work overlaps on the GPU race on it, so serialise them.  The call
- * makes no cudaMalloc, cudaFree or other allocating call; it synchronises `stream`
- * before returning, like every entry point here.
+ * 64-bit words (about 16 MiB), which every GPU that loads the library's module holds
+ * until the process exits.  Under CUDA's default lazy module loading that memory is
+ * taken when the module first loads on a device, i.e. by the first call there (or
+ * earlier with CUDA_MODULE_LOADING=EAGER): a caller that must not allocate later
+ * should make one call at start-up.  The first call on a device also looks up the
+ * array's device address (once per device, with the device current); make that
+ * first call before any stream capture.  A device reset (cudaDeviceReset)
+ * invalidates the looked-up address: make no call after one.  Every call on a device
+ * shares the array and clears the part it uses; calls whose work overlaps on the GPU
+ * race on it, so serialise them.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call; it synchronises `stream` before returning, like every entry point
+ * here.
  *
  * Errors: CG_EINVAL (nfields outside [1, CG_NOALLOC_MAX_FIELDS], nfields * ncells >
- * CG_NOALLOC_MAX_CELL_FIELDS, bad sizes or NULL pointers, non-finite weights),
+ * CG_NOALLOC_MAX_CELL_FIELDS -- checked without overflow --, a non-finite origin or
+ * box, bad sizes or NULL pointers, non-finite weights),
  * CG_EDOMAIN (particles outside the mesh; nothing written), CG_ECUDA. */
 cg_status cg_deposit_fixed_noalloc(int nx, int ny, int nz, const double origin[3], double dx,
                                    int64_t n, const double *pos, int nfields, const double *w,

@@ -95,6 +95,16 @@ int num_sms() {
     return sms;
 }
 
+bool cells_below(int nx, int ny, int nz, int64_t limit) {
+    // each factor is bounded before it multiplies, so no product overflows
+    if (nx < 1 || ny < 1 || nz < 1 || limit < 1) return false;
+    if ((int64_t)nx >= limit) return false;
+    if ((int64_t)ny > (limit - 1) / nx) return false;
+    const int64_t nxy = (int64_t)nx * ny;
+    if ((int64_t)nz > (limit - 1) / nxy) return false;
+    return nxy * nz < limit;
+}
+
 // ----------------------------------------------------------------------------- profiler
 namespace {
 struct ProfEntry {
@@ -339,7 +349,7 @@ cg_status cg_create_mesh_structured(int nx, int ny, int nz, const double origin[
     *out = nullptr;
     if (!origin) return fail(CG_EINVAL, "origin is NULL");
     if (nx < 1 || ny < 1 || nz < 1) return fail(CG_EINVAL, "mesh dimensions must be >= 1");
-    if ((int64_t)nx * ny * nz >= ((int64_t)1 << 31))
+    if (!cells_below(nx, ny, nz, (int64_t)1 << 31))
         return fail(CG_EINVAL, "mesh too large: nx*ny*nz must be < 2^31");
     if (!(dx > 0.0) || !std::isfinite(dx)) return fail(CG_EINVAL, "dx must be finite and > 0");
     for (int a = 0; a < 3; ++a)
@@ -386,7 +396,7 @@ cg_status cg_create_mesh_hex(int nx, int ny, int nz, const double *xf, const dou
     *out = nullptr;
     if (!xf || !yf || !zf) return fail(CG_EINVAL, "face coordinate arrays are NULL");
     if (nx < 1 || ny < 1 || nz < 1) return fail(CG_EINVAL, "mesh dimensions must be >= 1");
-    if ((int64_t)nx * ny * nz >= ((int64_t)1 << 31) / 7)
+    if (!cells_below(nx, ny, nz, ((int64_t)1 << 31) / 7))
         return fail(CG_EINVAL, "mesh too large: nx*ny*nz must be < 2^31 / 7");
     const int n3[3] = {nx, ny, nz};
     const double *f[3] = {xf, yf, zf};

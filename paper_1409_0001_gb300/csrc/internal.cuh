@@ -173,6 +173,9 @@ namespace cgk {
 // ----------------------------------------------------------------------------- device props
 int num_sms();
 
+// nx * ny * nz < limit for dimensions >= 1, decided without overflow.
+bool cells_below(int nx, int ny, int nz, int64_t limit);
+
 // ----------------------------------------------------------------------------- profiling
 // Opt-in per-kernel device timing (cg_profile_enable).  A scope records a CUDA event
 // pair on the launching stream around one launch and remembers the launch's

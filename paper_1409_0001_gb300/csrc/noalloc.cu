@@ -3,7 +3,8 @@
 //
 // Its scratch (error counters, per-field max |w|, and the 64-bit accumulators) lives in
 // the file-scope array below, part of this library's static device memory: every GPU
-// that loads the library holds it (CG_NOALLOC_SCRATCH_BYTES) until the process exits.
+// that loads this module holds it (8 * (128 + CG_NOALLOC_MAX_CELL_FIELDS) bytes) until the
+// process exits.
 // The array is shared by every call on a device and keeps the previous call's contents,
 // so each call clears what must start at zero; calls that overlap on the GPU race.
 #include <cuda_runtime.h>
@@ -23,7 +24,10 @@ static __device__ __align__(256) unsigned long long
     g_noalloc_scratch[kNoallocHeader + CG_NOALLOC_MAX_CELL_FIELDS];
 
 // Device address of g_noalloc_scratch per device (host code may not use the symbol's
-// name as an address: it is a host-side stand-in).
+// name as an address: it is a host-side stand-in).  Under CUDA's lazy module loading
+// (the default) the array is placed in device memory when this file's module first
+// loads on a device, i.e. by the first call there; a device reset (cudaDeviceReset)
+// invalidates the cached address, and calls after one must not follow.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
@@ -142,21 +146,20 @@ extern "C" cg_status cg_deposit_fixed_noalloc(int nx, int ny, int nz, const doub
     if (!origin || !cells_out) return fail(CG_EINVAL, "origin and cells_out must not be NULL");
     if (nx < 1 || ny < 1 || nz < 1) return fail(CG_EINVAL, "mesh dimensions must be >= 1");
     if (!(dx > 0.0) || !std::isfinite(dx)) return fail(CG_EINVAL, "dx must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin[a])) return fail(CG_EINVAL, "origin must be finite");
     if (nfields < 1 || nfields > CG_NOALLOC_MAX_FIELDS)
         return fail(CG_EINVAL, "nfields must be in [1, %d]", CG_NOALLOC_MAX_FIELDS);
-    const int64_t ncells = (int64_t)nx * ny * nz;
-    if (ncells * nfields > (int64_t)CG_NOALLOC_MAX_CELL_FIELDS)
+    // the cell count is bounded before it is formed, so that no product overflows
+    if (!cells_below(nx, ny, nz, (int64_t)CG_NOALLOC_MAX_CELL_FIELDS / nfields + 1))
         return fail(CG_EINVAL,
-                    "cg_deposit_fixed_noalloc: nfields * ncells = %lld exceeds the static "
-                    "scratch of %d accumulators",
-                    (long long)(ncells * nfields), CG_NOALLOC_MAX_CELL_FIELDS);
+                    "cg_deposit_fixed_noalloc: nfields * nx * ny * nz (%d * %d * %d * %d) "
+                    "exceeds the static scratch of %d accumulators",
+                    nfields, nx, ny, nz, CG_NOALLOC_MAX_CELL_FIELDS);
+    const int64_t ncells = (int64_t)nx * ny * nz;
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
     if (n > 0 && (!pos || !w)) return fail(CG_EINVAL, "pos and w must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
-
-    unsigned long long *scratch = nullptr;
-    CGK_TRY(scratch_for_current_device(&scratch));
-    unsigned long long *acc = scratch + kNoallocHeader;
 
     Box b;
     b.nx = nx;
@@ -167,6 +170,7 @@ extern "C" cg_status cg_deposit_fixed_noalloc(int nx, int ny, int nz, const doub
     for (int a = 0; a < 3; ++a) {
         volatile double len = (double)dims[a] * dx;   // two roundings, as cg_locate defines
         hi[a] = origin[a] + len;
+        if (!std::isfinite(hi[a])) return fail(CG_EINVAL, "origin + n * dx must be finite");
     }
     b.ox = origin[0];
     b.oy = origin[1];
@@ -175,6 +179,10 @@ extern "C" cg_status cg_deposit_fixed_noalloc(int nx, int ny, int nz, const doub
     b.hx = hi[0];
     b.hy = hi[1];
     b.hz = hi[2];
+
+    unsigned long long *scratch = nullptr;
+    CGK_TRY(scratch_for_current_device(&scratch));
+    unsigned long long *acc = scratch + kNoallocHeader;
 
     // clear the counters, the maxima and this call's accumulators
     CGK_CUDA(cudaMemsetAsync(scratch, 0, (kNoallocHeader + (size_t)ncells * nfields) * 8, st));

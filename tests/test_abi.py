@@ -92,3 +92,42 @@ def test_size_limits_refused_before_any_device_work(lib):
     assert L.cg_diffuse(h, 65, None, ctypes.byref(p), None, None) == 1
     assert b"nfields" in L.cg_last_error()
     assert L.cg_destroy_mesh(h) == 0
+
+
+def test_mesh_sizes_whose_product_overflows_are_refused(lib):
+    """nx * ny * nz is bounded factor by factor, so dimensions whose product would wrap
+    around 64 bits (2^21 * 2^21 * 2^22 = 2^64) are refused, not taken as a small mesh."""
+    import paper_1409_0001_gb300 as cg
+    L = cg.load_library()
+    h = ctypes.c_void_p()
+    org = (ctypes.c_double * 3)(0, 0, 0)
+    for dims in ((1 << 21, 1 << 21, 1 << 22), (2 ** 31 - 1, 2 ** 31 - 1, 2 ** 31 - 1),
+                 (1 << 16, 1 << 16, 1), (2, 1, 1 << 30)):
+        assert L.cg_create_mesh_structured(*dims, org, 0.1, ctypes.byref(h)) == 1
+        assert b"too large" in L.cg_last_error()
+    assert L.cg_create_mesh_structured(1 << 10, 1 << 10, (1 << 11) - 1, org, 0.1,
+                                       ctypes.byref(h)) == 0
+    assert L.cg_mesh_num_cells(h) == (1 << 20) * ((1 << 11) - 1)
+    assert L.cg_destroy_mesh(h) == 0
+
+
+def test_noalloc_deposition_refuses_bad_sizes_before_any_device_work(lib):
+    """cg_deposit_fixed_noalloc checks its sizes against the static scratch without
+    forming a product that could overflow, and refuses a non-finite origin, before it
+    touches the device."""
+    import paper_1409_0001_gb300 as cg
+    L = cg.load_library()
+    org = (ctypes.c_double * 3)(0, 0, 0)
+    dummy = ctypes.c_void_p(16)
+    for dims, nf in (((1 << 21, 1 << 21, 1 << 22), 1), ((160, 160, 160), 1),
+                     ((128, 128, 128), 2), ((2 ** 31 - 1, 2 ** 31 - 1, 2 ** 31 - 1), 8)):
+        st = L.cg_deposit_fixed_noalloc(*dims, org, 0.01, 1, dummy, nf, dummy, dummy, None, None)
+        assert st == 1
+        assert b"exceeds the static scratch" in L.cg_last_error()
+    for bad in (float("inf"), float("-inf"), float("nan")):
+        o = (ctypes.c_double * 3)(0.0, bad, 0.0)
+        st = L.cg_deposit_fixed_noalloc(8, 8, 8, o, 0.01, 1, dummy, 1, dummy, dummy, None, None)
+        assert st == 1 and b"origin" in L.cg_last_error()
+    big = (ctypes.c_double * 3)(1.7e308, 0.0, 0.0)        # origin + n dx overflows
+    st = L.cg_deposit_fixed_noalloc(8, 8, 8, big, 1e307, 1, dummy, 1, dummy, dummy, None, None)
+    assert st == 1 and b"finite" in L.cg_last_error()
