@@ -418,6 +418,115 @@ def test_tet_locate_matches_independent_barycentric(orc):
     assert nout == 1
 
 
+def _bary_solve(xyz, tet, x):
+    """Barycentric coordinates of x in a tet by a linear solve of the edge system (an
+    independent route: no orientation determinants).  Returns the 4 coordinates."""
+    v = xyz[np.asarray(tet)]
+    lam = np.linalg.solve((v[1:] - v[0]).T, np.asarray(x, dtype=np.float64) - v[0])
+    return np.concatenate([[1.0 - lam.sum()], lam])
+
+
+def test_tet_locate_fallback_takes_a_point_just_outside_a_lone_tet():
+    """The fallback branch: a point inside a tet's bounding box but 5e-11 outside one of
+    its faces qualifies for no tet, so the rule takes the tet with the largest minimum
+    coordinate when that minimum is >= -1e-10; 2e-10 outside it is out of domain."""
+    import oracle as orc
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    # the face x + y + z = 1 (opposite vertex 0): lambda_0 = 1 - x - y - z
+    pts = np.array([[0.25, 0.25, 0.5 + 5e-11], [0.25, 0.25, 0.5 - 5e-11],
+                    [0.25, 0.25, 0.5 + 2e-10], [0.5, 0.5, 0.5]]).T
+    cell, nout = orc.locate_tet(xyz, tets, pts)
+    assert list(cell) == [0, 0, -1, -1] and nout == 2
+    for i in (0, 2):                                   # both are outside the tet
+        assert _bary_solve(xyz, tets[0], pts[:, i]).min() < 0.0
+
+
+def test_tet_locate_fallback_takes_the_largest_minimum_not_the_lowest_index():
+    """Two disjoint tets whose boxes both hold the point, which lies outside both, each
+    by less than 1e-10: the rule picks the tet whose minimum coordinate is larger
+    (closer to containing it), whichever index it has; between identical minima (a tet
+    listed twice) the lower index."""
+    import oracle as orc
+    base = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    # tet A: the unit corner tet, face x + y + z = 1; tet B: A mirrored through the
+    # plane x + y + z = 1 + g, so B's matching face is x + y + z = 1 + 2g
+    g = 4e-11
+
+    def mirror(p):
+        return p + (2.0 * (1.0 + g) - 2.0 * p.sum()) / 3.0 * np.ones(3)
+    xyz = np.vstack([base, np.array([mirror(p) for p in base])])
+    A, B = [0, 1, 2, 3], [4, 5, 6, 7]
+    # 1e-11 beyond A's face, about 7e-11 short of B's
+    x = np.array([0.3, 0.3, 0.4 + 1e-11])
+    la, lb = _bary_solve(xyz, A, x).min(), _bary_solve(xyz, B, x).min()
+    assert -1e-10 < lb < la < 0.0
+    for order, want in (([A, B], 0), ([B, A], 1)):
+        cell, nout = orc.locate_tet(xyz, np.array(order, dtype=np.int32), x[:, None])
+        assert nout == 0 and cell[0] == want
+    for order, want in (([A, A, B], 0), ([B, A, A], 1), ([B, B], 0)):
+        cell, nout = orc.locate_tet(xyz, np.array(order, dtype=np.int32), x[:, None])
+        assert nout == 0 and cell[0] == want
+
+
+def test_tet_locate_takes_the_lowest_index_of_overlapping_tets():
+    """The first branch: among tets that contain the point, the lowest index."""
+    import oracle as orc
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0],
+                    [2.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 2.0]])
+    small, big = [0, 1, 2, 3], [0, 4, 5, 6]
+    x = np.array([[0.2], [0.2], [0.2]])
+    for order, want in (([small, big], 0), ([big, small], 0), ([small, small, big], 0)):
+        cell, nout = orc.locate_tet(xyz, np.array(order, dtype=np.int32), x)
+        assert nout == 0 and cell[0] == want
+    y = np.array([[0.2], [0.2], [1.2]])              # only in the big tet
+    cell, _ = orc.locate_tet(xyz, np.array([small, big], dtype=np.int32), y)
+    assert cell[0] == 1
+    # exactly on the small tet's face x + y + z = 1 (dyadic coordinates: every
+    # determinant is exact, the minimum coordinate is exactly 0) and 1e-13 inside it:
+    # the small tet qualifies and wins over the big tet, which holds the point deeply
+    for z in (0.5, 0.5 - 1e-13):
+        p = np.array([[0.25], [0.25], [z]])
+        assert 0.0 <= _bary_solve(xyz, small, p[:, 0]).min() < 1e-12
+        cell, _ = orc.locate_tet(xyz, np.array([small, big], dtype=np.int32), p)
+        assert cell[0] == 0
+
+
+def test_tet_locate_on_shared_faces_edges_and_vertices():
+    """Points placed on shared faces, edges and vertices of a jittered Kuhn mesh, where
+    the first branch or the fallback decides on rounding: the tet returned holds the
+    point to within 1e-9 (linear-solve barycentrics), no lower-index tet holds it by
+    more than 1e-9, and points 1e-6 outside the cube are out of domain."""
+    import oracle as orc
+    xyz, tets = W.kuhn_tet_mesh(3, jitter=0.2, seed=5)
+    rng = np.random.default_rng(17)
+    pts = []
+    nt = tets.shape[0]
+    for t in rng.choice(nt, 40, replace=False):
+        v = xyz[tets[t]]
+        pts.append(v[rng.integers(4)])                             # a vertex
+        a, b = rng.choice(4, 2, replace=False)
+        s = rng.random()
+        pts.append(v[a] + s * (v[b] - v[a]))                       # on an edge
+        f = rng.choice(4, 3, replace=False)
+        l = rng.dirichlet(np.ones(3))
+        pts.append(l[0] * v[f[0]] + l[1] * v[f[1]] + l[2] * v[f[2]])  # on a face
+    pts = np.array(pts).T
+    inside = np.all((pts >= 0.0) & (pts <= 1.0), axis=0)
+    pts = pts[:, inside]
+    cell, nout = orc.locate_tet(xyz, tets, pts)
+    assert nout == 0
+    for i in range(pts.shape[1]):
+        x = pts[:, i]
+        got = cell[i]
+        assert _bary_solve(xyz, tets[got], x).min() >= -1e-9
+        for t in range(got):
+            assert _bary_solve(xyz, tets[t], x).min() <= 1e-9
+    out = np.array([[-1e-6, 0.5, 0.5], [0.5, 1.0 + 1e-6, 0.5], [0.3, 0.3, 1.0 + 1e-6]]).T
+    cell, nout = orc.locate_tet(xyz, tets, out)
+    assert nout == 3 and list(cell) == [-1, -1, -1]
+
+
 def test_image_kernel_is_normalised_over_the_box(orc):
     """Eq. (normal) with Eq. (hi-bound): the image-summed kernel of a particle near a
     corner integrates to its volume over the box (midpoint quadrature, 60^3 points)."""
