@@ -98,6 +98,9 @@ def _load():
         lib.orc_locate_tet.restype = ctypes.c_int64
         lib.orc_locate_tet.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p,
                                        ctypes.c_int64, _f64p, _i32p]
+        lib.orc_locate_tet_bucketed.restype = ctypes.c_int64
+        lib.orc_locate_tet_bucketed.argtypes = [ctypes.c_int64, _f64p, ctypes.c_int64, _i32p,
+                                                ctypes.c_int64, _f64p, _i32p, ctypes.c_int]
         lib.orc_kernel_sum.restype = None
         lib.orc_kernel_sum.argtypes = [ctypes.c_int64, _f64p, _f64p, ctypes.c_int64, _f64p, _f64p,
                                        ctypes.c_double, ctypes.c_int, _f64p]
@@ -146,6 +149,23 @@ def locate_tet(xyz, tets, pos):
     out = _load().orc_locate_tet(xyz.shape[0], _p(xyz, ctypes.c_double), tets.shape[0],
                                  _p(tets, ctypes.c_int32), n, _p(pos, ctypes.c_double),
                                  _p(cell, ctypes.c_int32))
+    return cell, int(out)
+
+
+def locate_tet_bucketed(xyz, tets, pos, nb=None):
+    """The rule of locate_tet, searching only the tets listed in the point's bucket of a
+    uniform nb^3 grid over the mesh's box (every tet whose box holds the point is listed
+    there), for meshes too large for the brute force.  nb defaults to round((ntets/6)^(1/3))."""
+    xyz = _f64(xyz)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    pos = _f64(pos)
+    n = pos.shape[1]
+    if nb is None:
+        nb = max(1, int(round((tets.shape[0] / 6.0) ** (1.0 / 3.0))))
+    cell = np.empty(n, dtype=np.int32)
+    out = _load().orc_locate_tet_bucketed(xyz.shape[0], _p(xyz, ctypes.c_double), tets.shape[0],
+                                          _p(tets, ctypes.c_int32), n, _p(pos, ctypes.c_double),
+                                          _p(cell, ctypes.c_int32), int(nb))
     return cell, int(out)
 
 

@@ -641,6 +641,116 @@ int64_t orc_locate_tet(int64_t nv, const double *xyz, int64_t nt, const int32_t 
     return out;
 }
 
+/* The same rule, for large meshes: the candidates of a point are the tets whose  */
+/* axis-aligned box holds it, and only those; a uniform grid of buckets over the   */
+/* mesh's box lists each tet in every bucket its box overlaps, in ascending index. */
+/* The bucket of a coordinate, clamp(floor((c - lo) * inv), 0, nb - 1), does not   */
+/* decrease as c grows, so a tet whose box [lo_t, hi_t] holds x is listed in x's   */
+/* bucket; scanning that bucket in ascending index with the box test meets exactly */
+/* the candidates orc_locate_tet meets, in the same order, and gives the same      */
+/* result.  A point outside the mesh's box has no candidate.                       */
+static int64_t bucket_of(double c, double lo, double inv, int64_t nb)
+{
+    double f = floor((c - lo) * inv);
+    if (!(f >= 0.0)) return 0;          /* also NaN: such points fail the box test */
+    if (f >= (double)nb) return nb - 1;
+    return (int64_t)f;
+}
+
+int64_t orc_locate_tet_bucketed(int64_t nv, const double *xyz, int64_t nt, const int32_t *tv,
+                                int64_t n, const double *pos, int32_t *cell, int nb1)
+{
+    (void)nv;
+    double *lo = (double *)malloc((size_t)(3 * nt) * sizeof(double));
+    double *hi = (double *)malloc((size_t)(3 * nt) * sizeof(double));
+    double glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) {
+            double mn = xyz[3 * (int64_t)tv[4 * t] + a], mx = mn;
+            for (int j = 1; j < 4; ++j) {
+                double c = xyz[3 * (int64_t)tv[4 * t + j] + a];
+                if (c < mn) mn = c;
+                if (c > mx) mx = c;
+            }
+            lo[3 * t + a] = mn;
+            hi[3 * t + a] = mx;
+            if (mn < glo[a]) glo[a] = mn;
+            if (mx > ghi[a]) ghi[a] = mx;
+        }
+    int64_t nb = nb1 < 1 ? 1 : nb1;
+    double inv[3];
+    for (int a = 0; a < 3; ++a)
+        inv[a] = ghi[a] > glo[a] ? (double)nb / (ghi[a] - glo[a]) : 0.0;
+    int64_t nbk = nb * nb * nb;
+    /* pass 0 counts the tets each bucket lists, pass 1 writes the lists; tets are
+     * visited in ascending index, so every list is ascending */
+    int64_t *start = (int64_t *)calloc((size_t)(nbk + 1), sizeof(int64_t));
+    int64_t *fill = NULL;
+    int64_t *lists = NULL;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            for (int64_t b = 0; b < nbk; ++b) start[b + 1] += start[b];
+            lists = (int64_t *)malloc((size_t)(start[nbk] > 0 ? start[nbk] : 1) * sizeof(int64_t));
+            fill = (int64_t *)malloc((size_t)nbk * sizeof(int64_t));
+            for (int64_t b = 0; b < nbk; ++b) fill[b] = start[b];
+        }
+        for (int64_t t = 0; t < nt; ++t) {
+            int64_t b0[3], b1[3];
+            for (int a = 0; a < 3; ++a) {
+                b0[a] = bucket_of(lo[3 * t + a], glo[a], inv[a], nb);
+                b1[a] = bucket_of(hi[3 * t + a], glo[a], inv[a], nb);
+            }
+            for (int64_t k = b0[2]; k <= b1[2]; ++k)
+                for (int64_t j = b0[1]; j <= b1[1]; ++j)
+                    for (int64_t i = b0[0]; i <= b1[0]; ++i) {
+                        int64_t b = (k * nb + j) * nb + i;
+                        if (pass == 0)
+                            ++start[b + 1];
+                        else
+                            lists[fill[b]++] = t;
+                    }
+        }
+    }
+    free(fill);
+    int64_t out = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+        int64_t found = -1, best = -1;
+        double best_m = -INFINITY;
+        int inside = 1;
+        for (int a = 0; a < 3; ++a)
+            if (!(x[a] >= glo[a] && x[a] <= ghi[a])) inside = 0;
+        if (inside) {
+            int64_t b = (bucket_of(x[2], glo[2], inv[2], nb) * nb +
+                         bucket_of(x[1], glo[1], inv[1], nb)) * nb +
+                        bucket_of(x[0], glo[0], inv[0], nb);
+            for (int64_t q = start[b]; q < start[b + 1]; ++q) {
+                int64_t t = lists[q];
+                if (!(x[0] >= lo[3 * t] && x[0] <= hi[3 * t] && x[1] >= lo[3 * t + 1] &&
+                      x[1] <= hi[3 * t + 1] && x[2] >= lo[3 * t + 2] && x[2] <= hi[3 * t + 2]))
+                    continue;
+                double m = orc_tet_min_bary(xyz, tv, t, x);
+                if (m >= 0.0) {
+                    found = t;
+                    break;
+                }
+                if (m > best_m) {
+                    best_m = m;
+                    best = t;
+                }
+            }
+        }
+        if (found < 0 && best >= 0 && best_m >= -1e-10) found = best;
+        cell[i] = (int32_t)found;
+        if (found < 0) ++out;
+    }
+    free(lists);
+    free(start);
+    free(lo);
+    free(hi);
+    return out;
+}
+
 /* ------------------------------------------------------------------------- */
 /* The Gaussian kernel of Eq. (hi) with bandwidth b (equivalently the Green's  */
 /* function of Eq. (solutionGi) at T = b^2/4), summed with images about the    */

@@ -40,18 +40,20 @@ def _headers_mtime() -> float:
     return max([os.path.getmtime(h) for h in hs] + [0.0])
 
 
-def _compile(src: str, extra) -> str:
+def _compile(src: str, extra):
+    """Compile one source unless its object is newer than it and every header;
+    returns (object path, whether nvcc ran)."""
     obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
     if (os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
             and os.path.getmtime(obj) >= _headers_mtime()):
-        return obj
+        return obj, False
     cmd = [_nvcc()] + NVCC_FLAGS + ARCH + list(extra) + ["-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, res.stdout, res.stderr))
     if res.stderr.strip():
         sys.stderr.write(res.stderr)
-    return obj
+    return obj, True
 
 
 def build(force: bool = False, extra=(), verbose: bool = False) -> str:
@@ -64,9 +66,12 @@ def build(force: bool = False, extra=(), verbose: bool = False) -> str:
             if os.path.exists(o):
                 os.remove(o)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        done = list(ex.map(lambda s: _compile(s, extra), srcs))
+    objs = [o for o, _ in done]
+    compiled = [os.path.basename(s) for s, (_, ran) in zip(srcs, done) if ran]
     newest = max(os.path.getmtime(o) for o in objs)
-    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
+    linked = force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest
+    if linked:
         tmp = LIB_PATH + ".%d.tmp" % os.getpid()
         cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart"]
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -74,7 +79,9 @@ def build(force: bool = False, extra=(), verbose: bool = False) -> str:
             raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))
         os.replace(tmp, LIB_PATH)
     if verbose:
-        print("built", LIB_PATH)
+        print("built %s: compiled %s; reused %d object(s); %s" % (
+            LIB_PATH, ", ".join(compiled) if compiled else "nothing",
+            len(objs) - len(compiled), "linked" if linked else "library up to date"))
     return LIB_PATH
 
 

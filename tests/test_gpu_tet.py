@@ -3,8 +3,8 @@
 Bars as for the structured path: locate and deposition bit-exact; diffusion max-relative
 error <= 1e-10 (FP64 PCG) and <= 1e-6 (FP32/BF16 inner solves with FP64 refinement);
 mass conserved to 1e-12.  The full-size mesh (100^3 hexes -> 6,000,000 Kuhn tets,
-5,000,000 particles in a dense bottom layer) is checked on sampled particles (the
-oracle locates each one by brute force) and by properties that hold at any size.
+5,000,000 particles in a dense bottom layer) is checked against the oracle on every
+particle (its bucketed search), bit for bit in the deposition, and in the diffusion.
 """
 import numpy as np
 import pytest
@@ -156,34 +156,75 @@ def test_tet_explicit_parity(cg, orc, small_mesh):
         cg.diffuse(mesh, dev(u0[None]), cg.Params(T=3.0 / rate * 20, nsteps=20, scheme=2))
 
 
+def _near_face_points(xyz, tets, rng, k, eps=1e-12):
+    """k points within eps of a face of random tets (a random point of the face, moved
+    by at most eps along a random direction), inside the unit cube."""
+    t = tets[rng.integers(0, len(tets), k)]
+    f = np.stack([rng.permutation(4)[:3] for _ in range(k)])
+    corners = xyz[np.take_along_axis(t, f, axis=1)]             # [k, 3, 3]
+    lam = rng.dirichlet(np.ones(3), size=k)
+    p = np.einsum("kj,kja->ka", lam, corners)
+    d = rng.standard_normal((k, 3))
+    d *= (rng.random((k, 1)) * eps) / np.linalg.norm(d, axis=1, keepdims=True)
+    return np.clip(p + d, 0.0, 1.0).T
+
+
 def test_tet_full_size_layered(cg, orc):
-    """100^3 hexes -> 6,000,000 jittered Kuhn tets, 5,000,000 spheres (d = 0.003) with a
-    dense bottom layer, b = 0.03, 10 implicit-Euler steps, FP32 PCG + FP64 refinement.
-    Sampled particles are located by the oracle one by one; the smoothed field conserves
-    mass to 1e-12, stays non-negative, and agrees with FP64 PCG to 1e-6."""
+    """Configuration of the paper's unstructured case (Section 4.3) at full size: 100^3
+    hexes -> 6,000,000 jittered Kuhn tets, 5,000,000 spheres (d = 0.003) with a dense
+    bottom layer, b = 0.03, 10 implicit-Euler steps.  Against the oracle: every
+    particle's tet (the oracle's bucketed search, the same rule as its brute force),
+    plus 2,000 particles half of them within 1e-12 of a face, both alone and inside a
+    set large enough for the bucket-ordered search; the ordered deposition bit for bit;
+    the oracle's 10 FP64 CG steps against FP64 PCG (1e-10) and the mixed modes (1e-6,
+    Chebyshev and PCG inner solves); mass to 1e-12; non-negativity."""
+    import torch
     xyz, tets = W.kuhn_tet_mesh(100, jitter=0.2, seed=0)
     mesh = cg.TetMesh(xyz, tets)
     assert mesh.ncells == 6_000_000
     pos, w, h = W.layered_cube()
     dpos, dw = dev(pos), dev(w)
+    # locate: all 5,000,000 particles
+    ref_cell, nref = orc.locate_tet_bucketed(xyz, tets, pos)
+    assert nref == 0
     cell, nout = cg.locate(mesh, dpos)
     assert nout == 0
-    cell = cell.cpu().numpy()
+    assert np.array_equal(cell.cpu().numpy(), ref_cell)
+    # locate: 2,000 particles, half within 1e-12 of a face, alone and among 98,000 others
     rng = np.random.default_rng(25)
-    sample = rng.choice(pos.shape[1], 64, replace=False)
-    ref, _ = orc.locate_tet(xyz, tets, pos[:, sample])
-    assert np.array_equal(cell[sample], ref)
-    mixed, rep = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=0.03, nsteps=10,
+    special = np.hstack([pos[:, rng.choice(pos.shape[1], 1000, replace=False)],
+                         _near_face_points(xyz, tets, rng, 1000)])
+    ref_s, nref_s = orc.locate_tet_bucketed(xyz, tets, special)
+    got_s, nout_s = cg.locate(mesh, dev(special))
+    assert nout_s == nref_s
+    assert np.array_equal(got_s.cpu().numpy(), ref_s)
+    mixed_set = np.hstack([pos[:, :98_000], special])[:, rng.permutation(100_000)]
+    ref_m, _ = orc.locate_tet_bucketed(xyz, tets, mixed_set)
+    got_m, _ = cg.locate(mesh, dev(mixed_set))
+    assert np.array_equal(got_m.cpu().numpy(), ref_m)
+    # deposition, bit for bit, on the oracle's own cells and volumes
+    vc, cent, rp, col, val = orc.tet_build(xyz, tets)
+    eps0, _ = orc.deposit(ref_cell, w, len(tets), vc=vc, mode=0)
+    got0 = cg.deposit(mesh, dpos, dw).cpu().numpy()
+    assert np.array_equal(bits(got0), bits(eps0))
+    # diffusion: the oracle's FP64 CG against the GPU modes
+    b = 0.03
+    ref, _ = orc.diffuse_csr(eps0, vc, rp, col, val, b * b / 4, 10, scheme=0, tol=1e-14)
+    f64 = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=b, nsteps=10, precision=0))
+    assert maxrel(f64.cpu().numpy(), ref) <= 1e-10
+    mixed, rep = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=b, nsteps=10,
                                                            precision=1), report=True)
+    m = mixed.cpu().numpy()
+    assert maxrel(m, ref) <= 1e-6
     assert abs(rep["mass_out"][0] - w.sum()) <= 1e-12 * w.sum()
     assert abs(rep["mass_in"][0] - w.sum()) <= 1e-12 * w.sum()
-    m = mixed.cpu().numpy()
     assert m.min() >= -1e-12 * m.max()
-    f64 = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=0.03, nsteps=10, precision=0))
-    assert maxrel(m, f64.cpu().numpy()) <= 1e-6
-    pcg = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=0.03, nsteps=10, precision=1,
+    pcg = cg.coarse_grain(mesh, dpos, dw, cg.Params(bandwidth=b, nsteps=10, precision=1,
                                                     sweep_shape=1))    # PCG inner solves
-    assert maxrel(pcg.cpu().numpy(), f64.cpu().numpy()) <= 1e-6
+    assert maxrel(pcg.cpu().numpy(), ref) <= 1e-6
+    mesh.close()
+    del dpos, dw, f64, mixed, pcg
+    torch.cuda.empty_cache()
 
 
 def test_tet_mixed_results_do_not_depend_on_call_history(cg, small_mesh):

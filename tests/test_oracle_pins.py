@@ -527,6 +527,31 @@ def test_tet_locate_on_shared_faces_edges_and_vertices():
     assert nout == 3 and list(cell) == [-1, -1, -1]
 
 
+@pytest.mark.parametrize("nb", [1, 2, 3, 7])
+def test_bucketed_tet_locate_equals_the_brute_force(orc, nb):
+    """locate_tet_bucketed searches only the point's bucket; its results equal the brute
+    force over all tets bit for bit, for any bucket count, on points at vertices, on
+    faces and edges, just off faces, outside the mesh and not finite."""
+    xyz, tets = W.kuhn_tet_mesh(5, jitter=0.2, seed=6)
+    rng = np.random.default_rng(19)
+    n = 6000
+    pos = rng.random((3, n))
+    k = 1000
+    pos[:, :k] = xyz[rng.integers(0, len(xyz), k)].T
+    t = tets[rng.integers(0, len(tets), k)]
+    pos[:, k:2 * k] = xyz[t[:, :3]].mean(axis=1).T
+    pos[:, 2 * k:3 * k] = (0.5 * (xyz[t[:, 0]] + xyz[t[:, 3]])).T
+    pos[:, 3 * k:4 * k] = xyz[t[:, :3]].mean(axis=1).T + rng.standard_normal((3, k)) * 1e-12
+    pos[:, 4 * k] = (1.2, 0.5, 0.5)
+    pos[:, 4 * k + 1] = (0.5, np.nan, 0.5)
+    pos[:, 4 * k + 2] = (-np.inf, 0.5, 0.5)
+    pos[:, 4 * k + 3] = (0.5, 0.5, 1.0 + 1e-15)
+    ref, nref = orc.locate_tet(xyz, tets, pos)
+    got, nout = orc.locate_tet_bucketed(xyz, tets, pos, nb=nb)
+    assert nout == nref and nref >= 3
+    assert np.array_equal(got, ref)
+
+
 def test_image_kernel_is_normalised_over_the_box(orc):
     """Eq. (normal) with Eq. (hi-bound): the image-summed kernel of a particle near a
     corner integrates to its volume over the box (midpoint quadrature, 60^3 points)."""
