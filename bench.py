@@ -829,12 +829,14 @@ def profile_case(argv=None):
         for r in range(a.reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=a.nsteps, precision=a.precision),
+            _, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=a.nsteps, precision=a.precision,
+                                                                       sweep_shape=a.shape),
                                              bandwidths=[c.b for c in cases], report=True)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
-            print("rep %d: %.3f ms, %d cell-updates, %.3e cell-updates/s"
-                  % (r, dt * 1e3, rep["cell_updates"], rep["cell_updates"] / dt))
+            print("rep %d: %.3f ms, %d cell-updates, %.3e cell-updates/s, schedule %d"
+                  % (r, dt * 1e3, rep["cell_updates"], rep["cell_updates"] / dt,
+                     rep["sweep_shape_used"]))
         return
     if a.deposit:
         c = W.clustered_cube(n_side=a.n, n_particles=2_000_000 * (a.n // 128) ** 3 or 2_000_000)

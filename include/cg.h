@@ -166,8 +166,11 @@ typedef struct {
                            mesh that fits; the autotuner also weighs it); 400 + z =
                            TMA-staged vectorised sweep, z planes per block (FP32 inner
                            storage, nx % 4 == 0, no periodic axis; same results as
-                           100 + z).  Batched calls:
-                           z planes per work item (0 = autotuned per batch shape).  Tet
+                           100 + z).  Batched calls: z = the persistent launch with
+                           z planes per work item, 500 + z = one launch per phase with z
+                           planes per work item (same results); 0 = autotuned per batch
+                           shape (both schedules; only the persistent one when
+                           barrier_budget > 0).  Tet
                            and stretched meshes, FP32 storage: 0 = Chebyshev inner
                            solves on an interval from a probe PCG solve on a fixed
                            right-hand side (kept per mesh and pseudo-step, so results do
@@ -291,10 +294,13 @@ cg_status cg_solid_velocity(const cg_mesh *mesh, int ncomp, const double *eps,
  * meshes of any sizes; cells[s] is device [nfields][ncells_s] FP64 (in/out);
  * bandwidths (host, may be NULL) gives b per snapshot, else params->bandwidth/T.
  * Precision modes 3 and 4 with implicit Euler or Crank-Nicolson run every snapshot,
- * step, refinement round and inner iteration in ONE persistent cooperative launch
- * (grid barriers bounded by params->barrier_budget, default ~1 s of clock cycles;
- * CG_ETIMEOUT if one gives up), with per-step residuals verified afterwards; other
- * modes and schemes run the snapshots one after another.  The batch's descriptors
+ * step, refinement round and inner iteration as one CUDA graph, either as ONE persistent
+ * cooperative launch (grid barriers bounded by params->barrier_budget, default ~1 s of
+ * clock cycles; CG_ETIMEOUT if one gives up) or as one launch per phase covering every
+ * snapshot and field (no grid barrier), whichever the autotuner measures faster for the
+ * batch shape (params->sweep_shape can force either; barrier_budget > 0 forces the
+ * persistent launch), with per-step residuals verified afterwards; both give the same
+ * bits.  Other modes and schemes run the snapshots one after another.  The batch's descriptors
  * and work lists are kept with meshes[0].  report (may be NULL) aggregates all
  * snapshots.  Errors: CG_EINVAL (a tet mesh, sizes, pointers), CG_ENOCONV,
  * CG_ETIMEOUT, CG_ENOMEM, CG_ECUDA. */

@@ -676,6 +676,7 @@ static cg_status check_batch(int nsnap, cg_mesh *const *meshes, int nfields, dou
                              const cg_params *p, const double *bandwidths) {
     CGK_TRY(check_params(p));
     if (nsnap < 1 || !meshes || !cells) return fail(CG_EINVAL, "empty batch or NULL arrays");
+    if (nsnap > 65535) return fail(CG_EINVAL, "a batch holds at most 65535 snapshots");
     if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
     for (int s = 0; s < nsnap; ++s) {
         if (!meshes[s] || meshes[s]->kind != MESH_STRUCTURED)

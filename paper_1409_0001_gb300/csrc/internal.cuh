@@ -68,14 +68,14 @@ struct BatchKey {
     const void *arena = nullptr;
     unsigned gen = 0;
     int nsnap = 0, nf = 0, nsteps = 0, R = 0, mmax = 0, nr = 0, nc = 0, grid = 0, zlen = 0,
-        tsize = 0, scheme = 0;
+        tsize = 0, scheme = 0, phased = 0;
     long long budget = 0;
     double tol2 = 0.0;
     bool operator==(const BatchKey &o) const {
         return arena == o.arena && gen == o.gen && nsnap == o.nsnap && nf == o.nf &&
                nsteps == o.nsteps && R == o.R && mmax == o.mmax && nr == o.nr && nc == o.nc &&
                grid == o.grid && zlen == o.zlen && tsize == o.tsize && scheme == o.scheme &&
-               budget == o.budget && tol2 == o.tol2;
+               phased == o.phased && budget == o.budget && tol2 == o.tol2;
     }
 };
 

@@ -207,6 +207,148 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
     }
 }
 
+// A flat-plane variant of the engine for meshes of short rows (nx <= kFlatMaxNx,
+// walls only), whose cost does not depend on nx: the block covers kFlatCells consecutive
+// cells [q0, q0 + kFlatCells) of the flattened xy plane (q = y nx + x; thread t holds the
+// cells q0 + t + kThreads j, j = 0..3, so every load is coalesced whatever nx is) and
+// marches over the planes [z0, z1).  Plane z is published in a shared segment with nx
+// cells of halo either side, which holds every x and y neighbour; z neighbours come from
+// register queues; loads for plane z+1 are issued while plane z is computed.  consume()
+// receives exactly what sweep25_at gives it -- the same neighbour sum in the same order
+// (x-, x+, y-, y+, z-, z+, a wall adding a zero) -- so results are bit-identical.
+constexpr int kFlatCells = 4 * kThreads;
+constexpr int kFlatMaxNx = 512;
+
+template <class T, class Produce, class Pre, class Consume>
+__device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, int z1,
+                                              Produce produce, Pre pre, Consume consume) {
+    __shared__ T sp[kFlatCells + 2 * kFlatMaxNx];
+    const int t = threadIdx.y * TX + threadIdx.x;
+    const int nx = g.nx, nxy = g.nxy;
+    const int q0 = chunk * kFlatCells;
+    // the block's cells and their x/y neighbours (bits: x-, x+, y-, y+)
+    int nnxy[4];
+    unsigned nb[4];
+    bool own[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int q = q0 + t + kThreads * j;
+        own[j] = q < nxy;
+        const int iy = q / nx, ix = q - iy * nx;
+        nb[j] = (ix > 0 ? 1u : 0u) | (ix + 1 < nx ? 2u : 0u) | (iy > 0 ? 4u : 0u) |
+                (iy + 1 < g.ny ? 8u : 0u);
+        nnxy[j] = __popc(nb[j]);
+    }
+    // halo cells of the segment: [q0 - nx, q0) and [q0 + kFlatCells, q0 + kFlatCells + nx)
+    // inside the plane; thread t loads cells t and t + kThreads of each side
+    const int lo0 = max(q0 - nx, 0);
+    const int hi0 = q0 + kFlatCells, hi1 = min(q0 + kFlatCells + nx, nxy);
+    bool hl[2], hh[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        hl[j] = lo0 + t + kThreads * j < q0;
+        hh[j] = hi0 + t + kThreads * j < hi1;
+    }
+    using P = decltype(pre(0));
+    T vdn[4], vc[4], vup[4], ha[2], hb[2];
+    P pt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        vdn[j] = T();
+        vc[j] = T();
+        vup[j] = T();
+        pt[j] = P{};
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        ha[j] = T();
+        hb[j] = T();
+    }
+    if (z0 < z1) {
+        const int kz = z0 * nxy;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (own[j]) {
+                const int k = kz + q0 + t + kThreads * j;
+                if (z0 > 0) vdn[j] = produce(k - nxy);
+                vc[j] = produce(k);
+                if (z0 + 1 < g.nz) vup[j] = produce(k + nxy);
+                pt[j] = pre(k);
+            }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (hl[j]) ha[j] = produce(kz + lo0 + t + kThreads * j);
+            if (hh[j]) hb[j] = produce(kz + hi0 + t + kThreads * j);
+        }
+    }
+    // segment slot of cell q: q - q0 + nx
+    for (int z = z0; z < z1; ++z) {
+        const int kz = z * nxy;
+        T nup[4], na[2], nbv[2];
+        P npt[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            nup[j] = T();
+            npt[j] = P{};
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            na[j] = T();
+            nbv[j] = T();
+        }
+        if (z + 1 < z1) {
+            const int kn = kz + nxy;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (own[j]) {
+                    const int k = kn + q0 + t + kThreads * j;
+                    if (z + 2 < g.nz) nup[j] = produce(k + nxy);
+                    npt[j] = pre(k);
+                }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (hl[j]) na[j] = produce(kn + lo0 + t + kThreads * j);
+                if (hh[j]) nbv[j] = produce(kn + hi0 + t + kThreads * j);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (own[j]) sp[t + kThreads * j + nx] = vc[j];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (hl[j]) sp[lo0 + t + kThreads * j - q0 + nx] = ha[j];
+            if (hh[j]) sp[hi0 + t + kThreads * j - q0 + nx] = hb[j];
+        }
+        __syncthreads();
+        const int nnz = (z > 0) + (z + 1 < g.nz);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (own[j]) {
+                const int i = t + kThreads * j + nx;
+                T s = (nb[j] & 1u) ? sp[i - 1] : T();
+                s += (nb[j] & 2u) ? sp[i + 1] : T();
+                s += (nb[j] & 4u) ? sp[i - nx] : T();
+                s += (nb[j] & 8u) ? sp[i + nx] : T();
+                s += vdn[j];
+                s += vup[j];
+                consume(kz + q0 + t + kThreads * j, vc[j], s, nnxy[j] + nnz, pt[j]);
+            }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            vdn[j] = vc[j];
+            vc[j] = vup[j];
+            vup[j] = nup[j];
+            pt[j] = npt[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            ha[j] = na[j];
+            hb[j] = nbv[j];
+        }
+    }
+}
+
 // Without cell-local prefetch: consume(k, v, s, nn).
 template <class T, class Produce, class Consume>
 __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0, int z1,
@@ -2002,6 +2144,7 @@ struct SnapDesc {
     Geo g;
     int gx, gy, zlen, nzc;   // refinement items (scalar engine)
     int v4, gx4, zlen4, nzc4;// Chebyshev items (vectorised if v4)
+    int flat, nch;           // flat-plane items (both phases): nch plane chunks per plane
     int m;                   // Chebyshev iterations per round (even)
     int scheme;
     float gamma;
@@ -2022,12 +2165,29 @@ __device__ __forceinline__ DF ldcg_df(const DF *p, int i) {
     return DF{v.x, v.y};
 }
 
+// Loads of the batched phases: COH (the persistent launch) reads data that other blocks
+// of the same launch wrote, so it bypasses L1; one launch per phase reads plainly.
+template <bool COH> __device__ __forceinline__ DF bld_df(const DF *p, int i) {
+    if constexpr (COH) {
+        return ldcg_df(p, i);
+    } else {
+        return p[i];
+    }
+}
+template <bool COH, class TS> __device__ __forceinline__ float bld(const TS *p, int i) {
+    if constexpr (COH) {
+        return ldcg(p, i);
+    } else {
+        return ld(p, i);
+    }
+}
+
 // part: this item's ||r||^2 partial of a step's last pass (or ||b||^2 of its first pass).
 // part_next (a step's last pass, not the call's last step): the pass also starts the next
 // step, as the single-mesh path's last refinement pass does: with x = u^{n+1} it has A x at
 // hand, so the next first residual is c L x = (x - A x) / theta (and the Crank-Nicolson
 // right-hand side x + c/2 L x), and that step's ||b||^2 partial goes to part_next.
-template <class TS>
+template <class TS, bool COH>
 __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BItem &it, bool first,
                                                int round, int R, double *part, double *part_next) {
     const Geo &g = d.g;
@@ -2042,11 +2202,18 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     const float gamma = d.gamma;
     TS *r = d.R + off;
     TS *y1 = d.Ya + off;
+    // the flat-plane engine or the 2.5D tile engine (the same arithmetic per cell)
+    auto engine = [&](auto produce, auto pre, auto consume) {
+        if (d.flat)
+            sweep_flat_at<DF>(g, it.bx, z0, z1, produce, pre, consume);
+        else
+            sweep25_at<DF>(g, it.bx, it.by, z0, z1, produce, pre, consume);
+    };
     if (first) {
         const DF *u = d.U + off;
         DF *bo = d.B + off;
-        sweep25_at<DF>(
-            g, it.bx, it.by, z0, z1, [&](int k) { return ldcg_df(u, k); }, [](int) { return NoPre{}; },
+        engine(
+            [&](int k) { return bld_df<COH>(u, k); }, [](int) { return NoPre{}; },
             [&](int k, DF v, DF sm, int nn, NoPre) {
                 DF lx = sm - df_mulf(v, (float)nn);
                 DF rk = df_mul(d.cfdf.c, lx);
@@ -2068,9 +2235,9 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
         DF *bo = d.B + off;
         const TS *dd = d.Yb + off;
         const bool next = part_next != nullptr;
-        sweep25_at<DF>(
-            g, it.bx, it.by, z0, z1, [&](int k) { return df_add_f(ldcg_df(xin, k), ldcg(dd, k)); },
-            [&](int k) { return ldcg_df(b, k); },
+        engine(
+            [&](int k) { return df_add_f(bld_df<COH>(xin, k), bld<COH>(dd, k)); },
+            [&](int k) { return bld_df<COH>(b, k); },
             [&](int k, DF v, DF sm, int nn, DF bk) {
                 xout[k] = v;
                 const DF ax = df_mul(sdg[nn], v) - df_mul(d.cfdf.ce, sm);
@@ -2098,10 +2265,10 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     if (is_thread0() && part) *part = tot;
 }
 
-template <class TS>
+template <class TS, bool COH>
 __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem &it, int k) {
     const Geo &g = d.g;
-    const int nzc = d.v4 ? d.nzc4 : d.nzc, zlen = d.v4 ? d.zlen4 : d.zlen;
+    const int nzc = (d.v4 && !d.flat) ? d.nzc4 : d.nzc, zlen = (d.v4 && !d.flat) ? d.zlen4 : d.zlen;
     const int f = it.zf / nzc;
     const int zc = it.zf - f * nzc;
     const int z0 = zc * zlen, z1 = min(g.nz, z0 + zlen);
@@ -2115,12 +2282,23 @@ __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem 
     __shared__ float sdg[8];
     stage_table(sdg, d.cf32.dg);
     __syncthreads();
-    if (d.v4) {
-        cheb_v4_tile<TS, Vec4cg>(g, it.bx, it.by, z0, z1, d.cf32, sdg, d.gamma, omega, yc, yp, r, yo);
+    if (d.flat) {
+        sweep_flat_at<float>(
+            g, it.bx, z0, z1, [&](int q) { return bld<COH>(yc, q); },
+            [&](int q) { return float2{yp ? bld<COH>(yp, q) : 0.0f, bld<COH>(r, q)}; },
+            [&](int q, float v, float sm, int nn, float2 pt) {
+                float ay = fmaf(sdg[nn], v, -d.cf32.ce * sm);
+                st(yo, q, fmaf(omega, v - pt.x + d.gamma * (pt.y - ay), pt.x));
+            });
+    } else if (d.v4) {
+        if constexpr (COH)
+            cheb_v4_tile<TS, Vec4cg>(g, it.bx, it.by, z0, z1, d.cf32, sdg, d.gamma, omega, yc, yp, r, yo);
+        else
+            cheb_v4_tile<TS, Vec4>(g, it.bx, it.by, z0, z1, d.cf32, sdg, d.gamma, omega, yc, yp, r, yo);
     } else {
         sweep25_at<float>(
-            g, it.bx, it.by, z0, z1, [&](int q) { return ldcg(yc, q); },
-            [&](int q) { return float2{yp ? ldcg(yp, q) : 0.0f, ldcg(r, q)}; },
+            g, it.bx, it.by, z0, z1, [&](int q) { return bld<COH>(yc, q); },
+            [&](int q) { return float2{yp ? bld<COH>(yp, q) : 0.0f, bld<COH>(r, q)}; },
             [&](int q, float v, float sm, int nn, float2 pt) {
                 float ay = fmaf(sdg[nn], v, -d.cf32.ce * sm);
                 st(yo, q, fmaf(omega, v - pt.x + d.gamma * (pt.y - ay), pt.x));
@@ -2154,7 +2332,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_batched(const SnapDesc<TS> *__r
         if (step == 0) {   // later steps were started by the previous step's last pass
             for (int i = blockIdx.x; i < nr; i += gridDim.x) {
                 const BItem it = ritems[i];
-                batched_refine<TS>(sd[it.snap], it, true, 0, R, part_bb + i, nullptr);
+                batched_refine<TS, true>(sd[it.snap], it, true, 0, R, part_bb + i, nullptr);
             }
             if (!grid_sync(gb, gridDim.x, budget)) return;
         }
@@ -2162,13 +2340,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_batched(const SnapDesc<TS> *__r
             for (int k = 1; k < mmax; ++k) {
                 for (int i = blockIdx.x; i < nc; i += gridDim.x) {
                     const BItem it = citems[i];
-                    if (k < sd[it.snap].m) batched_cheb<TS>(sd[it.snap], it, k);
+                    if (k < sd[it.snap].m) batched_cheb<TS, true>(sd[it.snap], it, k);
                 }
                 if (!grid_sync(gb, gridDim.x, budget)) return;
             }
             for (int i = blockIdx.x; i < nr; i += gridDim.x) {
                 const BItem it = ritems[i];
-                batched_refine<TS>(sd[it.snap], it, false, round, R,
+                batched_refine<TS, true>(sd[it.snap], it, false, round, R,
                                    round == R ? part_rr + (size_t)step * nr + i : nullptr,
                                    round == R && step + 1 < nsteps ? part_bb + (size_t)(step + 1) * nr + i
                                                                    : nullptr);
@@ -2177,6 +2355,48 @@ __global__ void __launch_bounds__(kThreads, 4) k_batched(const SnapDesc<TS> *__r
                 if (!grid_sync(gb, gridDim.x, budget)) return;
         }
     }
+}
+
+// The same schedule as k_batched with one launch per phase (the phased schedule): the
+// launch boundary orders the phases, so there is no grid barrier, loads may use L1, and
+// the hardware deals the work items (block i takes item i) to the SMs as they free up.
+// A captured graph holds the whole sequence of launches.
+template <class TS>
+__global__ void __launch_bounds__(kThreads, 4) k_bconvert(const SnapDesc<TS> *__restrict__ sd, int nf) {
+    chain_wait();
+    chain_release();
+    const SnapDesc<TS> &d = sd[blockIdx.y];
+    const size_t cnt = (size_t)d.g.n * nf;
+    const size_t tid = (size_t)blockIdx.x * kThreads + threadIdx.y * TX + threadIdx.x;
+    for (size_t i = tid; i < cnt; i += (size_t)gridDim.x * kThreads) {
+        double v = d.cells[i];
+        float hi = __double2float_rn(v);
+        d.U[i] = DF{hi, __double2float_rn(v - (double)hi)};
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kThreads, 3) k_bcheb(const SnapDesc<TS> *__restrict__ sd,
+                                                    const BItem *__restrict__ citems, int k) {
+    chain_wait();
+    chain_release();
+    const BItem it = citems[blockIdx.x];
+    if (k < sd[it.snap].m) batched_cheb<TS, false>(sd[it.snap], it, k);
+}
+
+// first: a step's first pass (||b||^2 partial to part[i]); else round `round` of R
+// (||r||^2 partial to part[i] when part, the next step's ||b||^2 to part_next[i]).
+template <class TS>
+__global__ void __launch_bounds__(kThreads, 2) k_brefine(const SnapDesc<TS> *__restrict__ sd,
+                                                      const BItem *__restrict__ ritems, int first,
+                                                      int round, int R, double *part,
+                                                      double *part_next) {
+    chain_wait();
+    chain_release();
+    const int i = blockIdx.x;
+    const BItem it = ritems[i];
+    batched_refine<TS, false>(sd[it.snap], it, first != 0, round, R, part ? part + i : nullptr,
+                              part_next ? part_next + i : nullptr);
 }
 
 // hist[(step * nsnap + s) * nf + f] = (sum of ||r||^2 partials, sum of ||b||^2 partials)
@@ -3852,6 +4072,8 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
         d.zlen = std::min(zlen, m->nz);
         d.nzc = (m->nz + d.zlen - 1) / d.zlen;
         d.v4 = (m->nx % 4 == 0) ? 1 : 0;
+        d.flat = m->nx <= kFlatMaxNx ? 1 : 0;
+        d.nch = (m->nx * m->ny + kFlatCells - 1) / kFlatCells;
         d.gx4 = (m->nx + 4 * TX - 1) / (4 * TX);
         d.zlen4 = d.zlen;
         d.nzc4 = d.nzc;
@@ -3869,6 +4091,14 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
         d.cells = cells[s];
         for (int f = 0; f < nf; ++f) {
             P.first_item.push_back((int)P.ritems.size());
+            if (d.flat) {   // plane chunks x z-chunks, the same items for both phases
+                for (int zc = 0; zc < d.nzc; ++zc)
+                    for (int ch = 0; ch < d.nch; ++ch) {
+                        P.ritems.push_back(BItem{s, ch, 0, f * d.nzc + zc});
+                        P.citems.push_back(BItem{s, ch, 0, f * d.nzc + zc});
+                    }
+                continue;
+            }
             for (int zc = 0; zc < d.nzc; ++zc)
                 for (int by = 0; by < d.gy; ++by)
                     for (int bx = 0; bx < d.gx; ++bx) P.ritems.push_back(BItem{s, bx, by, f * d.nzc + zc});
@@ -3935,9 +4165,53 @@ static cg_status batch_upload(BatchPlan<TS> &P, BatchArena &A, char *ab, int nsn
     return CG_OK;
 }
 
+// The phased schedule's launches on stream st (one per phase, in k_batched's order),
+// each with its algorithmic bytes: a Chebyshev iteration reads y_k, y_{k-1} and r and
+// writes y_{k+1} of every snapshot that runs it; a refinement pass reads the double-float
+// iterate and right-hand side and the correction and writes the iterate, the residual
+// and the first Chebyshev iterate.
+template <class TS>
+static cg_status batch_issue_phased(const BatchPlan<TS> &P, const BatchArena &A, int nf,
+                                    int nsteps, int R, cudaStream_t st) {
+    char *ab = A.ab;
+    const SnapDesc<TS> *dsd = (const SnapDesc<TS> *)(ab + A.o_desc);
+    const BItem *dri = (const BItem *)(ab + A.o_ri), *dci = (const BItem *)(ab + A.o_ci);
+    double *prr = (double *)(ab + A.o_prr), *pbb = (double *)(ab + A.o_pbb);
+    const int nr = (int)P.ritems.size(), nc = (int)P.citems.size();
+    const int nsnap = (int)P.descs.size();
+    const double cells_f = (double)P.cells_total * nf;
+    const char *cname = sizeof(TS) == 2 ? "bcheb_bf16" : "bcheb_fp32";
+    const char *rname = sizeof(TS) == 2 ? "brefine_bf16" : "brefine_fp32";
+    std::vector<double> cheb_bytes((size_t)P.mmax, 0.0);
+    for (const auto &d : P.descs)
+        for (int k = 1; k < d.m; ++k) cheb_bytes[(size_t)k] += (double)d.g.n * nf * 4.0 * sizeof(TS);
+    const double ref_bytes = cells_f * (24.0 + 3.0 * sizeof(TS));
+    CGK_LAUNCH("bconvert", cells_f * 16.0, st,
+               launch_chain(k_bconvert<TS>, dim3(num_sms() * 2, nsnap), dim3(TX, TY), st, dsd, nf));
+    for (int step = 0; step < nsteps; ++step) {
+        if (step == 0)
+            CGK_LAUNCH(rname, cells_f * (8.0 + 2.0 * sizeof(TS)), st,
+                       launch_chain(k_brefine<TS>, dim3(nr), dim3(TX, TY), st, dsd, dri, 1, 0, R, pbb,
+                                    (double *)nullptr));
+        for (int round = 1; round <= R; ++round) {
+            for (int k = 1; k < P.mmax; ++k)
+                CGK_LAUNCH(cname, cheb_bytes[(size_t)k], st,
+                           launch_chain(k_bcheb<TS>, dim3(nc), dim3(TX, TY), st, dsd, dci, k));
+            double *part = round == R ? prr + (size_t)step * nr : nullptr;
+            double *next = round == R && step + 1 < nsteps ? pbb + (size_t)(step + 1) * nr : nullptr;
+            CGK_LAUNCH(rname, ref_bytes, st,
+                       launch_chain(k_brefine<TS>, dim3(nr), dim3(TX, TY), st, dsd, dri, 0, round, R,
+                                    part, next));
+        }
+    }
+    CGK_CUDA(cudaGetLastError());
+    return CG_OK;
+}
+
 // One batched schedule on stream st: reset the barrier and the failure count, the
-// persistent launch (nsteps pseudo-steps of R rounds), the residual history and, if
-// `final`, the write-back (skipped on the device when a step missed the tolerance).
+// persistent launch (G > 0: nsteps pseudo-steps of R rounds) or the phased launches
+// (G == 0), the residual history and, if `final`, the write-back (skipped on the device
+// when a step missed the tolerance).
 template <class TS>
 static cg_status batch_issue(const BatchPlan<TS> &P, const BatchArena &A, int nsnap, int nf,
                              int nsteps, int R, int G, long long budget, double tol2, bool final,
@@ -3961,9 +4235,13 @@ static cg_status batch_issue(const BatchPlan<TS> &P, const BatchArena &A, int ns
         bytes += (double)d.g.n * nf *
                  (16.0 + nsteps * ((8 + 2 * sizeof(TS)) +
                                    R * ((24 + 3 * sizeof(TS)) + (d.m - 1) * 4.0 * sizeof(TS))));
-    CGK_LAUNCH(sizeof(TS) == 2 ? "batched_bf16" : "batched_fp32", bytes, st,
-               CGK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batched<TS>, dim3(G),
-                                                    dim3(TX, TY), args, 0, st)));
+    if (G > 0) {
+        CGK_LAUNCH(sizeof(TS) == 2 ? "batched_bf16" : "batched_fp32", bytes, st,
+                   CGK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batched<TS>, dim3(G),
+                                                        dim3(TX, TY), args, 0, st)));
+    } else {
+        CGK_TRY(batch_issue_phased(P, A, nf, nsteps, R, st));
+    }
     CGK_LAUNCH("batched_hist", 16.0 * nsteps * nr, st,
                k_batched_hist<<<(unsigned)A.nh, kThreads, 0, st>>>(
                    (const int *)(ab + A.o_fi), nsnap, nf, nr, prr, pbb, hist, tol2, bad));
@@ -3977,17 +4255,23 @@ static cg_status batch_issue(const BatchPlan<TS> &P, const BatchArena &A, int ns
     return CG_OK;
 }
 
-// Autotuner of the batched z-chunk length: one pseudo-step of two rounds per candidate
-// (the caller's arrays are not written), timed with events; the fastest is kept per
-// batch shape (the snapshots' dimensions, the field count and the inner type).
+// Autotuner of the batched schedule: the z-chunk length and, unless the caller asked
+// for the persistent launch (G_only), persistent (G) against phased (one launch per
+// phase); one pseudo-step of two rounds per candidate (the caller's arrays are not
+// written), timed with events; the fastest is kept per batch shape (the snapshots'
+// dimensions, the field count, the inner type and G_only) as a code: z for the
+// persistent launch, kPhasedCode + z for the phased one.
+constexpr int kPhasedCode = 500;
+
 template <class TS>
 static cg_status batch_tune(int nsnap, cg_mesh *const *meshes, int nf, double *const *cells,
-                            const cg_params *p, const double *bandwidths, int G, long long budget,
-                            cudaStream_t st, int *zbest) {
+                            const cg_params *p, const double *bandwidths, int G, bool G_only,
+                            long long budget, cudaStream_t st, int *zbest) {
     std::vector<int> key;
-    key.reserve((size_t)nsnap * 3 + 2);
+    key.reserve((size_t)nsnap * 3 + 3);
     key.push_back(nf);
     key.push_back((int)sizeof(TS));
+    key.push_back(G_only ? 1 : 0);
     for (int s = 0; s < nsnap; ++s) {
         key.push_back(meshes[s]->nx);
         key.push_back(meshes[s]->ny);
@@ -3999,14 +4283,18 @@ static cg_status batch_tune(int nsnap, cg_mesh *const *meshes, int nf, double *c
             *zbest = e.second;
             return CG_OK;
         }
-    static const int cand[] = {4, 8, 16};
+    std::vector<int> cand = {4, 8, 16};
+    if (!G_only)
+        for (int z : {4, 8, 16}) cand.push_back(kPhasedCode + z);
     float best = 0.f;
-    *zbest = 8;
+    *zbest = G_only ? 8 : kPhasedCode + 8;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CGK_CUDA(cudaEventCreate(&e0));
     CGK_CUDA(cudaEventCreate(&e1));
     cg_status rc = CG_OK;
-    for (int z : cand) {
+    for (int code : cand) {
+        const int z = code % kPhasedCode;
+        const int g = code >= kPhasedCode ? 0 : G;
         BatchPlan<TS> P;
         rc = batch_plan<TS>(nsnap, meshes, nf, cells, p, bandwidths, z, P);
         if (rc != CG_OK) break;
@@ -4018,7 +4306,7 @@ static cg_status batch_tune(int nsnap, cg_mesh *const *meshes, int nf, double *c
         float ms = 0.f;
         for (int rep = 0; rep < 2 && rc == CG_OK; ++rep) {   // the first run warms up
             if (cudaEventRecord(e0, st) != cudaSuccess) rc = fail(CG_ECUDA, "event");
-            if (rc == CG_OK) rc = batch_issue(P, A, nsnap, nf, 1, 2, G, budget, 0.0, false, st);
+            if (rc == CG_OK) rc = batch_issue(P, A, nsnap, nf, 1, 2, g, budget, 0.0, false, st);
             if (rc == CG_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = fail(CG_ECUDA, "event");
             if (rc == CG_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(CG_ECUDA, "sync");
             if (rc == CG_OK) cudaEventElapsedTime(&ms, e0, e1);
@@ -4035,7 +4323,7 @@ static cg_status batch_tune(int nsnap, cg_mesh *const *meshes, int nf, double *c
         }
         if (best == 0.f || ms < best) {
             best = ms;
-            *zbest = z;
+            *zbest = code;
         }
     }
     cudaEventDestroy(e0);
@@ -4059,8 +4347,18 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
     const int G = per_sm * num_sms();
     const long long budget = p->barrier_budget > 0 ? p->barrier_budget : 2000000000LL;
     const int max_r = p->max_rounds > 0 ? p->max_rounds : 12;
-    int zlen = p->sweep_shape > 0 ? p->sweep_shape : 0;
-    if (zlen == 0) CGK_TRY(batch_tune<TS>(nsnap, meshes, nf, cells, p, bandwidths, G, budget, st, &zlen));
+    // schedule code: z = persistent launch with z planes per work item, kPhasedCode + z =
+    // one launch per phase; barrier_budget > 0 asks for the persistent launch
+    const bool G_only = p->barrier_budget > 0;
+    int code = p->sweep_shape > 0 ? p->sweep_shape : 0;
+    if (code >= kPhasedCode && G_only)
+        return fail(CG_EINVAL, "cg_diffuse_batched: barrier_budget > 0 needs the persistent schedule "
+                               "(sweep_shape below %d)", kPhasedCode);
+    if (code == 0)
+        CGK_TRY(batch_tune<TS>(nsnap, meshes, nf, cells, p, bandwidths, G, G_only, budget, st, &code));
+    const int zlen = code % kPhasedCode;
+    const int Gx = code >= kPhasedCode ? 0 : G;
+    if (zlen < 1) return fail(CG_EINVAL, "cg_diffuse_batched: bad sweep_shape %d", code);
     BatchPlan<TS> P;
     CGK_TRY(batch_plan<TS>(nsnap, meshes, nf, cells, p, bandwidths, zlen, P));
     BatchArena A = batch_layout(P, nsnap, nf, p->nsteps);
@@ -4097,8 +4395,9 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
         key.mmax = P.mmax;
         key.nr = (int)P.ritems.size();
         key.nc = (int)P.citems.size();
-        key.grid = G;
+        key.grid = Gx;
         key.zlen = zlen;
+        key.phased = Gx == 0 ? 1 : 0;
         key.tsize = (int)sizeof(TS);
         key.scheme = p->scheme;
         key.budget = budget;
@@ -4126,7 +4425,7 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
             cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             cg_status is = CG_OK;
             if (ce == cudaSuccess) {
-                is = batch_issue(P, A, nsnap, nf, p->nsteps, R, G, budget, tol2, true, cs);
+                is = batch_issue(P, A, nsnap, nf, p->nsteps, R, Gx, budget, tol2, true, cs);
                 cudaGraph_t graph = nullptr;
                 ce = cudaStreamEndCapture(cs, &graph);
                 if (ce == cudaSuccess && is == CG_OK) ce = cudaGraphInstantiate(&e.exec, graph, 0);
@@ -4175,7 +4474,7 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
                 rep->cell_updates = upd * nf;
                 rep->final_rel_residual = worst;
                 rep->inner_iters_per_round = P.mmax;
-                rep->sweep_shape_used = zlen;
+                rep->sweep_shape_used = code;
             }
             return CG_OK;
         }

@@ -1,5 +1,6 @@
-"""GPU parity of batched snapshots (one persistent launch for all snapshots, steps and
-fields) against the FP64 oracle and against the single-mesh path, through the C ABI.
+"""GPU parity of batched snapshots (all snapshots, steps and fields in one persistent
+launch, or in one launch per phase, captured as one graph) against the FP64 oracle and
+against the single-mesh path, through the C ABI.
 
 Bars: mixed modes <= 1e-6 max-relative error per snapshot and field against the oracle;
 mass conserved to 1e-12 of sum |w| per field; the persistent kernel's grid barrier gives
@@ -82,9 +83,31 @@ def test_batched_agrees_with_single_mesh_path(cg):
         assert maxrel(o.cpu().numpy(), single.cpu().numpy()) <= 1e-10
 
 
+def test_batched_phased_and_persistent_schedules_give_the_same_bits(cg):
+    """The phased schedule (one launch per phase) evaluates every cell's update as the
+    persistent launch does, so both give the same bits, for any work-item depth."""
+    import torch
+    cases = small_batch()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    bws = [c.b for c in cases]
+    outs = []
+    for shape in (8, 508, 4, 516):
+        out, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3,
+                                                                     sweep_shape=shape),
+                                           bandwidths=bws, report=True)
+        assert rep["sweep_shape_used"] == shape
+        outs.append([o.clone() for o in out])
+    for o in outs[1:]:
+        assert all(torch.equal(a, b) for a, b in zip(outs[0], o))
+
+
 def test_batched_full_size_64_snapshots(cg, orc):
-    """64 snapshots, cube sides 32..96, 10^4..10^6 particles, 5 fields, b = 3 dx, one
-    persistent launch; three snapshots checked against the oracle."""
+    """64 snapshots, cube sides 32..96, 10^4..10^6 particles, 5 fields, b = 3 dx, the
+    autotuned schedule (as the benchmark runs it); three snapshots checked against the
+    oracle, and the persistent launch gives the same bits."""
+    import torch
     cases = W.batched_snapshots()
     meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
     pos = [dev(c.pos) for c in cases]
@@ -98,6 +121,12 @@ def test_batched_full_size_64_snapshots(cg, orc):
         c = cases[s]
         _, ref, _, _ = orc.coarse_grain_structured(c.dims, c.origin, c.dx, c.pos, c.w, c.b, c.nsteps)
         assert maxrel(out[s].cpu().numpy(), ref) <= MIXED_TOL
+    out = [o.clone() for o in out]
+    other = 16 if rep["sweep_shape_used"] >= 500 else 516
+    out2 = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3,
+                                                             sweep_shape=other),
+                                   bandwidths=[c.b for c in cases])
+    assert all(torch.equal(a, b) for a, b in zip(out, out2))
 
 
 def test_batched_barrier_timeout(cg):
@@ -126,10 +155,11 @@ def test_batched_rejects_shared_meshes_and_tets(cg):
         cg.diffuse_batched([t], [dev(np.zeros((1, t.ncells)))], cg.Params(bandwidth=0.2, precision=3))
 
 
-@pytest.mark.parametrize("zlen", [4, 16])
+@pytest.mark.parametrize("zlen", [4, 16, 504, 516])
 def test_batched_tile_override_matches_oracle(cg, orc, zlen):
-    """Work items of 4 or 16 z-planes (the autotuner's other candidates) give the same
-    answers as the oracle; the report names the z-chunk that ran."""
+    """Work items of 4 or 16 z-planes, in the persistent launch (4, 16) or one launch per
+    phase (504, 516) -- the autotuner's other candidates -- give the same answers as the
+    oracle; the report names the schedule that ran."""
     cases = small_batch()[:4]
     meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
     pos = [dev(c.pos) for c in cases]
@@ -155,7 +185,7 @@ def test_batched_graph_replay_is_deterministic(cg):
     for _ in range(3):
         out, rep = cg.coarse_grain_batched(meshes, pos, w, cg.Params(nsteps=10, precision=3),
                                            bandwidths=bws, report=True)
-        assert rep["sweep_shape_used"] in (4, 8, 16)
+        assert rep["sweep_shape_used"] in (4, 8, 16, 504, 508, 516)
         runs.append([o.cpu().numpy().view(np.int64) for o in out])
     for r in runs[1:]:
         assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
