@@ -208,30 +208,33 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
 }
 
 // A flat-plane variant of the engine for meshes of short rows (nx <= kFlatMaxNx,
-// walls only), whose cost does not depend on nx: the block covers kFlatCells consecutive
-// cells [q0, q0 + kFlatCells) of the flattened xy plane (q = y nx + x; thread t holds the
-// cells q0 + t + kThreads j, j = 0..3, so every load is coalesced whatever nx is) and
+// walls only), whose cost does not depend on nx: the block covers CPT kThreads
+// consecutive cells [q0, q0 + CPT kThreads) of the flattened xy plane (q = y nx + x;
+// thread t holds the cells q0 + t + kThreads j, j < CPT, so every load is coalesced
+// whatever nx is) and
 // marches over the planes [z0, z1).  Plane z is published in a shared segment with nx
 // cells of halo either side, which holds every x and y neighbour; z neighbours come from
 // register queues; loads for plane z+1 are issued while plane z is computed.  consume()
 // receives exactly what sweep25_at gives it -- the same neighbour sum in the same order
 // (x-, x+, y-, y+, z-, z+, a wall adding a zero) -- so results are bit-identical.
-constexpr int kFlatCells = 4 * kThreads;
 constexpr int kFlatMaxNx = 512;
+constexpr int kFlatCpt = 4;     // cells per thread of the FP32 / BF16 sweeps
+constexpr int kFlatCptDF = 2;   // ... of the double-float refinement passes
 
-template <class T, class Produce, class Pre, class Consume>
+template <class T, int CPT, class Produce, class Pre, class Consume>
 __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, int z1,
                                               Produce produce, Pre pre, Consume consume) {
+    constexpr int kFlatCells = CPT * kThreads;
     __shared__ T sp[kFlatCells + 2 * kFlatMaxNx];
     const int t = threadIdx.y * TX + threadIdx.x;
     const int nx = g.nx, nxy = g.nxy;
     const int q0 = chunk * kFlatCells;
     // the block's cells and their x/y neighbours (bits: x-, x+, y-, y+)
-    int nnxy[4];
-    unsigned nb[4];
-    bool own[4];
+    int nnxy[CPT];
+    unsigned nb[CPT];
+    bool own[CPT];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < CPT; ++j) {
         const int q = q0 + t + kThreads * j;
         own[j] = q < nxy;
         const int iy = q / nx, ix = q - iy * nx;
@@ -250,10 +253,10 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         hh[j] = hi0 + t + kThreads * j < hi1;
     }
     using P = decltype(pre(0));
-    T vdn[4], vc[4], vup[4], ha[2], hb[2];
-    P pt[4];
+    T vdn[CPT], vc[CPT], vup[CPT], ha[2], hb[2];
+    P pt[CPT];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < CPT; ++j) {
         vdn[j] = T();
         vc[j] = T();
         vup[j] = T();
@@ -267,7 +270,7 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
     if (z0 < z1) {
         const int kz = z0 * nxy;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < CPT; ++j)
             if (own[j]) {
                 const int k = kz + q0 + t + kThreads * j;
                 if (z0 > 0) vdn[j] = produce(k - nxy);
@@ -284,10 +287,10 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
     // segment slot of cell q: q - q0 + nx
     for (int z = z0; z < z1; ++z) {
         const int kz = z * nxy;
-        T nup[4], na[2], nbv[2];
-        P npt[4];
+        T nup[CPT], na[2], nbv[2];
+        P npt[CPT];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < CPT; ++j) {
             nup[j] = T();
             npt[j] = P{};
         }
@@ -299,7 +302,7 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         if (z + 1 < z1) {
             const int kn = kz + nxy;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < CPT; ++j)
                 if (own[j]) {
                     const int k = kn + q0 + t + kThreads * j;
                     if (z + 2 < g.nz) nup[j] = produce(k + nxy);
@@ -312,7 +315,7 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
             }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < CPT; ++j)
             if (own[j]) sp[t + kThreads * j + nx] = vc[j];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -322,7 +325,7 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         __syncthreads();
         const int nnz = (z > 0) + (z + 1 < g.nz);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < CPT; ++j)
             if (own[j]) {
                 const int i = t + kThreads * j + nx;
                 T s = (nb[j] & 1u) ? sp[i - 1] : T();
@@ -335,7 +338,7 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
             }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < CPT; ++j) {
             vdn[j] = vc[j];
             vc[j] = vup[j];
             vup[j] = nup[j];
@@ -2127,6 +2130,155 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------- flat-plane Chebyshev
+// The Chebyshev iteration of k_cheb_v4 on the flat-plane layout of sweep_flat_at (a
+// block owns kFlatCpt * kThreads consecutive cells of the flattened xy plane, thread t
+// the cells q0 + t + kThreads j), written with per-thread pointers that advance one
+// plane per step, so every load and store of a cell is an immediate offset from them
+// and the index arithmetic is paid once per plane rather than once per access.  The
+// neighbour sum (x-, x+, y-, y+, z-, z+, a wall adding a zero) and the update are
+// those of the other sweeps: the same bits.  L is the load policy (Vec4-style
+// scalars: plain or L2-coherent).
+template <class TS, bool COH>
+__device__ __forceinline__ float fld(const TS *p) {
+    if constexpr (COH) {
+        return ldcg(p, 0);
+    } else {
+        return ld(p, 0);
+    }
+}
+
+template <class TS, bool COH>
+__device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, int z1, float ce,
+                                               float gamma, float omega, const float *sdg,
+                                               const TS *yv, const TS *ypv, const TS *rv,
+                                               TS *ynv) {
+    constexpr int C = kFlatCpt;
+    constexpr int S = kThreads;   // stride between a thread's cells
+    __shared__ float sp[C * S + 2 * kFlatMaxNx];
+    const int t = threadIdx.y * TX + threadIdx.x;
+    const int nx = g.nx, nxy = g.nxy, nz = g.nz;
+    const int q0 = chunk * (C * S);
+    unsigned nbits[C];
+    int nnxy[C];
+    bool own[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int q = q0 + t + S * j;
+        own[j] = q < nxy;
+        const int iy = q / nx, ix = q - iy * nx;
+        nbits[j] = (ix > 0 ? 1u : 0u) | (ix + 1 < nx ? 2u : 0u) | (iy > 0 ? 4u : 0u) |
+                   (iy + 1 < g.ny ? 8u : 0u);
+        nnxy[j] = __popc(nbits[j]);
+    }
+    const int lo0 = max(q0 - nx, 0);
+    const int hi0 = q0 + C * S, hi1 = min(hi0 + nx, nxy);
+    const bool hl0 = lo0 + t < q0, hl1 = lo0 + t + S < q0;
+    const bool hh0 = hi0 + t < hi1, hh1 = hi0 + t + S < hi1;
+    // per-thread pointers at plane z (cell j at [S * j]); shared slots likewise
+    const size_t pz0 = (size_t)z0 * nxy;
+    const TS *py = yv + pz0 + q0 + t;
+    const TS *pp = ypv ? ypv + pz0 + q0 + t : nullptr;
+    const TS *pr = rv + pz0 + q0 + t;
+    TS *po = ynv + pz0 + q0 + t;
+    const TS *plo = yv + pz0 + lo0 + t;
+    const TS *phi = yv + pz0 + hi0 + t;
+    float *so = sp + nx + t;                  // own cells
+    float *sl = sp + nx + (lo0 - q0) + t;     // low halo
+    float *sh = sp + nx + (hi0 - q0) + t;     // high halo
+    const float *sym = so - nx, *syp = so + nx;
+    float vdn[C], vc[C], vup[C], yp[C], rc[C], ha0 = 0.f, ha1 = 0.f, hb0 = 0.f, hb1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        vdn[j] = 0.f;
+        vc[j] = 0.f;
+        vup[j] = 0.f;
+        yp[j] = 0.f;
+        rc[j] = 0.f;
+    }
+    if (z0 < z1) {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (own[j]) {
+                if (z0 > 0) vdn[j] = fld<TS, COH>(py - nxy + S * j);
+                vc[j] = fld<TS, COH>(py + S * j);
+                if (z0 + 1 < nz) vup[j] = fld<TS, COH>(py + nxy + S * j);
+                if (pp) yp[j] = fld<TS, COH>(pp + S * j);
+                rc[j] = fld<TS, COH>(pr + S * j);
+            }
+        if (hl0) ha0 = fld<TS, COH>(plo);
+        if (hl1) ha1 = fld<TS, COH>(plo + S);
+        if (hh0) hb0 = fld<TS, COH>(phi);
+        if (hh1) hb1 = fld<TS, COH>(phi + S);
+    }
+    for (int z = z0; z < z1; ++z) {
+        // loads for plane z+1: y at z+2, y_prev and r at z+1, the halo at z+1
+        float nup[C], nyp[C], nrc[C], na0 = 0.f, na1 = 0.f, nb0 = 0.f, nb1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            nup[j] = 0.f;
+            nyp[j] = 0.f;
+            nrc[j] = 0.f;
+        }
+        if (z + 1 < z1) {
+            const bool up2 = z + 2 < nz;
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (own[j]) {
+                    if (up2) nup[j] = fld<TS, COH>(py + 2 * nxy + S * j);
+                    if (pp) nyp[j] = fld<TS, COH>(pp + nxy + S * j);
+                    nrc[j] = fld<TS, COH>(pr + nxy + S * j);
+                }
+            if (hl0) na0 = fld<TS, COH>(plo + nxy);
+            if (hl1) na1 = fld<TS, COH>(plo + nxy + S);
+            if (hh0) nb0 = fld<TS, COH>(phi + nxy);
+            if (hh1) nb1 = fld<TS, COH>(phi + nxy + S);
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (own[j]) so[S * j] = vc[j];
+        if (hl0) sl[0] = ha0;
+        if (hl1) sl[S] = ha1;
+        if (hh0) sh[0] = hb0;
+        if (hh1) sh[S] = hb1;
+        __syncthreads();
+        const int nnz = (z > 0) + (z + 1 < nz);
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (own[j]) {
+                const unsigned b = nbits[j];
+                float sm = (b & 1u) ? so[S * j - 1] : 0.f;
+                sm += (b & 2u) ? so[S * j + 1] : 0.f;
+                sm += (b & 4u) ? sym[S * j] : 0.f;
+                sm += (b & 8u) ? syp[S * j] : 0.f;
+                sm += vdn[j];
+                sm += vup[j];
+                const float v = vc[j];
+                const float ay = fmaf(sdg[nnxy[j] + nnz], v, -ce * sm);
+                st(po + S * j, 0, fmaf(omega, v - yp[j] + gamma * (rc[j] - ay), yp[j]));
+            }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            vdn[j] = vc[j];
+            vc[j] = vup[j];
+            vup[j] = nup[j];
+            yp[j] = nyp[j];
+            rc[j] = nrc[j];
+        }
+        ha0 = na0;
+        ha1 = na1;
+        hb0 = nb0;
+        hb1 = nb1;
+        py += nxy;
+        if (pp) pp += nxy;
+        pr += nxy;
+        po += nxy;
+        plo += nxy;
+        phi += nxy;
+    }
+}
+
 // ---------------------------------------------------------------- batched snapshots
 // Many independent snapshots (each its own hex mesh, bandwidth and Chebyshev count) are
 // smoothed by one persistent cooperative launch in the double-float modes.  Phases:
@@ -2144,7 +2296,7 @@ struct SnapDesc {
     Geo g;
     int gx, gy, zlen, nzc;   // refinement items (scalar engine)
     int v4, gx4, zlen4, nzc4;// Chebyshev items (vectorised if v4)
-    int flat, nch;           // flat-plane items (both phases): nch plane chunks per plane
+    int flat, nch, nchr;     // flat-plane items: plane chunks per plane (Chebyshev, refinement)
     int m;                   // Chebyshev iterations per round (even)
     int scheme;
     float gamma;
@@ -2190,7 +2342,11 @@ template <bool COH, class TS> __device__ __forceinline__ float bld(const TS *p, 
 template <class TS, bool COH>
 __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BItem &it, bool first,
                                                int round, int R, double *part, double *part_next) {
-    const Geo &g = d.g;
+    // the descriptor lives in global memory: copy what the sweep reads into registers
+    // (through a reference every store would force the compiler to reload it)
+    const Geo g = d.g;
+    const int scheme = d.scheme;
+    const DF cf_c = d.cfdf.c, cf_half_c = d.cfdf.half_c, cf_ce = d.cfdf.ce;
     const int f = it.zf / d.nzc;
     const int zc = it.zf - f * d.nzc;
     const int z0 = zc * d.zlen, z1 = min(g.nz, z0 + d.zlen);
@@ -2203,9 +2359,10 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     TS *r = d.R + off;
     TS *y1 = d.Ya + off;
     // the flat-plane engine or the 2.5D tile engine (the same arithmetic per cell)
+    const bool flat = d.flat != 0;
     auto engine = [&](auto produce, auto pre, auto consume) {
-        if (d.flat)
-            sweep_flat_at<DF>(g, it.bx, z0, z1, produce, pre, consume);
+        if (flat)
+            sweep_flat_at<DF, kFlatCptDF>(g, it.bx, z0, z1, produce, pre, consume);
         else
             sweep25_at<DF>(g, it.bx, it.by, z0, z1, produce, pre, consume);
     };
@@ -2216,10 +2373,10 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
             [&](int k) { return bld_df<COH>(u, k); }, [](int) { return NoPre{}; },
             [&](int k, DF v, DF sm, int nn, NoPre) {
                 DF lx = sm - df_mulf(v, (float)nn);
-                DF rk = df_mul(d.cfdf.c, lx);
+                DF rk = df_mul(cf_c, lx);
                 DF bk = v;
-                if (d.scheme == 1) {
-                    bk = v + df_mul(d.cfdf.half_c, lx);
+                if (scheme == 1) {
+                    bk = v + df_mul(cf_half_c, lx);
                     bo[k] = bk;
                 }
                 float bf = df_f(bk);
@@ -2231,7 +2388,7 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     } else {
         const DF *xin = (round == 1 ? d.U : ((round & 1) ? d.X2 : d.X1)) + off;
         DF *xout = (round == R ? d.U : ((round & 1) ? d.X1 : d.X2)) + off;
-        const DF *b = (d.scheme == 1 ? d.B : d.U) + off;
+        const DF *b = (scheme == 1 ? d.B : d.U) + off;
         DF *bo = d.B + off;
         const TS *dd = d.Yb + off;
         const bool next = part_next != nullptr;
@@ -2240,13 +2397,13 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
             [&](int k) { return bld_df<COH>(b, k); },
             [&](int k, DF v, DF sm, int nn, DF bk) {
                 xout[k] = v;
-                const DF ax = df_mul(sdg[nn], v) - df_mul(d.cfdf.ce, sm);
+                const DF ax = df_mul(sdg[nn], v) - df_mul(cf_ce, sm);
                 float rf = df_f(bk - ax);
                 acc = fmaf(rf, rf, acc);
                 if (next) {
                     DF cl = v - ax;                    // = theta c L v
                     DF bn = v;
-                    if (d.scheme == 1) {
+                    if (scheme == 1) {
                         bn = v + cl;                  // v + c/2 L v
                         cl = cl + cl;                 // c L v
                         bo[k] = bn;                   // read above at this cell only
@@ -2267,7 +2424,8 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
 
 template <class TS, bool COH>
 __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem &it, int k) {
-    const Geo &g = d.g;
+    const Geo g = d.g;   // register copies of the descriptor's fields (see batched_refine)
+    const float gamma = d.gamma, ce = d.cf32.ce;
     const int nzc = (d.v4 && !d.flat) ? d.nzc4 : d.nzc, zlen = (d.v4 && !d.flat) ? d.zlen4 : d.zlen;
     const int f = it.zf / nzc;
     const int zc = it.zf - f * nzc;
@@ -2283,13 +2441,7 @@ __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem 
     stage_table(sdg, d.cf32.dg);
     __syncthreads();
     if (d.flat) {
-        sweep_flat_at<float>(
-            g, it.bx, z0, z1, [&](int q) { return bld<COH>(yc, q); },
-            [&](int q) { return float2{yp ? bld<COH>(yp, q) : 0.0f, bld<COH>(r, q)}; },
-            [&](int q, float v, float sm, int nn, float2 pt) {
-                float ay = fmaf(sdg[nn], v, -d.cf32.ce * sm);
-                st(yo, q, fmaf(omega, v - pt.x + d.gamma * (pt.y - ay), pt.x));
-            });
+        cheb_flat_tile<TS, COH>(g, it.bx, z0, z1, ce, gamma, omega, sdg, yc, yp, r, yo);
     } else if (d.v4) {
         if constexpr (COH)
             cheb_v4_tile<TS, Vec4cg>(g, it.bx, it.by, z0, z1, d.cf32, sdg, d.gamma, omega, yc, yp, r, yo);
@@ -2387,7 +2539,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bcheb(const SnapDesc<TS> *__res
 // first: a step's first pass (||b||^2 partial to part[i]); else round `round` of R
 // (||r||^2 partial to part[i] when part, the next step's ||b||^2 to part_next[i]).
 template <class TS>
-__global__ void __launch_bounds__(kThreads, 2) k_brefine(const SnapDesc<TS> *__restrict__ sd,
+__global__ void __launch_bounds__(kThreads, 3) k_brefine(const SnapDesc<TS> *__restrict__ sd,
                                                       const BItem *__restrict__ ritems, int first,
                                                       int round, int R, double *part,
                                                       double *part_next) {
@@ -4073,7 +4225,8 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
         d.nzc = (m->nz + d.zlen - 1) / d.zlen;
         d.v4 = (m->nx % 4 == 0) ? 1 : 0;
         d.flat = m->nx <= kFlatMaxNx ? 1 : 0;
-        d.nch = (m->nx * m->ny + kFlatCells - 1) / kFlatCells;
+        d.nch = (m->nx * m->ny + kFlatCpt * kThreads - 1) / (kFlatCpt * kThreads);
+        d.nchr = (m->nx * m->ny + kFlatCptDF * kThreads - 1) / (kFlatCptDF * kThreads);
         d.gx4 = (m->nx + 4 * TX - 1) / (4 * TX);
         d.zlen4 = d.zlen;
         d.nzc4 = d.nzc;
@@ -4091,12 +4244,11 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
         d.cells = cells[s];
         for (int f = 0; f < nf; ++f) {
             P.first_item.push_back((int)P.ritems.size());
-            if (d.flat) {   // plane chunks x z-chunks, the same items for both phases
-                for (int zc = 0; zc < d.nzc; ++zc)
-                    for (int ch = 0; ch < d.nch; ++ch) {
-                        P.ritems.push_back(BItem{s, ch, 0, f * d.nzc + zc});
-                        P.citems.push_back(BItem{s, ch, 0, f * d.nzc + zc});
-                    }
+            if (d.flat) {   // plane chunks x z-chunks
+                for (int zc = 0; zc < d.nzc; ++zc) {
+                    for (int ch = 0; ch < d.nchr; ++ch) P.ritems.push_back(BItem{s, ch, 0, f * d.nzc + zc});
+                    for (int ch = 0; ch < d.nch; ++ch) P.citems.push_back(BItem{s, ch, 0, f * d.nzc + zc});
+                }
                 continue;
             }
             for (int zc = 0; zc < d.nzc; ++zc)
