@@ -242,7 +242,10 @@ cg_status cg_deposit(cg_mesh *mesh, int64_t n, const double *pos, int nfields, c
 cg_status cg_diffuse(cg_mesh *mesh, int nfields, double *cells, const cg_params *params,
                      cg_report *report, void *stream);
 
-/* cg_deposit followed by cg_diffuse (Section 2.6): the whole method. */
+/* cg_deposit followed by cg_diffuse (Section 2.6): the whole method.  An error in the
+ * deposition phase leaves cells_out untouched; an error in the diffusion phase
+ * (CG_ENOMEM, CG_ECUDA, or CG_ENOCONV / CG_ETIMEOUT with the last iterate) comes after
+ * cells_out has received the deposited field, which it then holds. */
 cg_status cg_coarse_grain(cg_mesh *mesh, int64_t n, const double *pos, int nfields,
                           const double *w, double *cells_out, const cg_params *params,
                           cg_report *report, void *stream);
@@ -374,6 +377,17 @@ int cg_profile_count(void);
  * algorithmic bytes.  Any out pointer may be NULL.  CG_EINVAL for a bad index. */
 cg_status cg_profile_get(int i, char *name, int name_len, long long *launches, double *ms,
                          double *bytes);
+
+/* Device workspace accounting (no counterpart in the paper).  cg_workspace_bytes: the
+ * device bytes the library's workspaces hold now, over all meshes and devices (caller
+ * arrays and the no-allocation entry point's static scratch not included).
+ * cg_set_workspace_limit: a process-wide cap on that total (0, the default: none); a
+ * call that would grow a workspace beyond it returns CG_ENOMEM before allocating and
+ * before writing any output, as a failed cudaMalloc does, and the library stays usable.
+ * Lets a caller budget device memory, and tests the allocation-failure path without
+ * exhausting a GPU.  CG_EINVAL for a negative limit. */
+cg_status cg_set_workspace_limit(long long bytes);
+long long cg_workspace_bytes(void);
 
 /* Number of kernels the library has launched in this process since the last reset
  * (counted whether or not profiling is enabled). */

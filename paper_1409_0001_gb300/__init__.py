@@ -111,6 +111,8 @@ def load_library(path: str | None = None):
         "cg_create_mesh_hex": (i32, [i32, i32, i32, vp, vp, vp, vp, P(vp)]),
         "cg_solid_velocity": (i32, [vp, i32, vp, vp, dbl, vp, vp]),
         "cg_coarse_grain_concurrent": (i32, [i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32]),
+        "cg_set_workspace_limit": (i32, [ctypes.c_longlong]),
+        "cg_workspace_bytes": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -129,7 +131,18 @@ def exported_symbols():
             "cg_profile_get", "cg_launch_count", "cg_launch_count_reset",
             "cg_deposit_fixed_noalloc", "cg_diffuse_batched", "cg_coarse_grain_batched",
             "cg_mesh_set_periodic", "cg_solid_velocity", "cg_create_mesh_hex",
-            "cg_coarse_grain_concurrent"]
+            "cg_coarse_grain_concurrent", "cg_set_workspace_limit", "cg_workspace_bytes"]
+
+
+def set_workspace_limit(nbytes: int) -> None:
+    """Cap the device bytes the library's workspaces may hold (0: no cap); a call that
+    would exceed it raises CGError CG_ENOMEM before allocating (cg_set_workspace_limit)."""
+    _check(load_library().cg_set_workspace_limit(int(nbytes)), "cg_set_workspace_limit")
+
+
+def workspace_bytes() -> int:
+    """Device bytes the library's workspaces hold now (cg_workspace_bytes)."""
+    return int(load_library().cg_workspace_bytes())
 
 
 def _check(status: int, where: str):

@@ -34,15 +34,27 @@ cg_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
     return e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA;
 }
 
+// Device bytes the library's workspaces hold (all meshes, all devices), and the cap set
+// by cg_set_workspace_limit (0: none).
+static std::atomic<long long> g_ws_bytes{0};
+static std::atomic<long long> g_ws_limit{0};
+
 cg_status DevBuf::ensure(size_t n) {
     if (n <= bytes) return CG_OK;
+    size_t want = n + n / 8;
+    const long long lim = g_ws_limit.load();
+    if (lim > 0 && g_ws_bytes.load() - (long long)bytes + (long long)want > lim)
+        return fail(CG_ENOMEM,
+                    "device workspace of %zu bytes refused: the library would hold %lld bytes, "
+                    "above the limit of %lld (cg_set_workspace_limit)",
+                    want, g_ws_bytes.load() - (long long)bytes + (long long)want, lim);
     if (p) {
         cudaError_t e = cudaFree(p);
         p = nullptr;
+        g_ws_bytes -= (long long)bytes;
         bytes = 0;
         if (e != cudaSuccess) return cuda_fail(e, "cudaFree", __FILE__, __LINE__);
     }
-    size_t want = n + n / 8;
     ++gen;
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
@@ -51,11 +63,15 @@ cg_status DevBuf::ensure(size_t n) {
         return fail(CG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
     }
     bytes = want;
+    g_ws_bytes += (long long)want;
     return CG_OK;
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        cudaFree(p);
+        g_ws_bytes -= (long long)bytes;
+    }
     p = nullptr;
     bytes = 0;
 }
@@ -298,6 +314,14 @@ cg_status cg_profile_enable(int on) {
 }
 
 long long cg_launch_count(void) { return g_launches.load(); }
+
+cg_status cg_set_workspace_limit(long long bytes) {
+    if (bytes < 0) return fail(CG_EINVAL, "the workspace limit must be >= 0 (0: no limit)");
+    g_ws_limit.store(bytes);
+    return CG_OK;
+}
+
+long long cg_workspace_bytes(void) { return g_ws_bytes.load(); }
 
 void cg_launch_count_reset(void) { g_launches.store(0); }
 

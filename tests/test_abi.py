@@ -131,3 +131,14 @@ def test_noalloc_deposition_refuses_bad_sizes_before_any_device_work(lib):
     big = (ctypes.c_double * 3)(1.7e308, 0.0, 0.0)        # origin + n dx overflows
     st = L.cg_deposit_fixed_noalloc(8, 8, 8, big, 1e307, 1, dummy, 1, dummy, dummy, None, None)
     assert st == 1 and b"finite" in L.cg_last_error()
+
+
+def test_workspace_limit_is_validated_without_a_gpu(lib):
+    """The workspace cap is host state: a negative limit is refused, 0 clears it, and no
+    workspace is held before any device call."""
+    import paper_1409_0001_gb300 as cg
+    L = cg.load_library()
+    assert L.cg_workspace_bytes() == 0
+    assert L.cg_set_workspace_limit(-1) == 1 and b"limit" in L.cg_last_error()
+    assert L.cg_set_workspace_limit(1 << 20) == 0
+    assert L.cg_set_workspace_limit(0) == 0
