@@ -314,10 +314,18 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(
 // each cell's segment sums the segment's weights in ascending particle index (FP64,
 // from +0.0) and writes eps = S / V_c.  Cells without particles keep the +0.0 the
 // output was cleared to (0.0 / V_c = +0.0).
+// eps = S / V_c with an IEEE division (Eq. (pcm-k)).  When every cell has the same volume
+// and it is an exact power of two, its reciprocal is exact too and S * (1 / V_c) is the
+// same correctly rounded value as S / V_c (scaling by a power of two, rounded once), at
+// the cost of one multiplication; inv_pow2 is that reciprocal, or 0 to divide.
+__device__ __forceinline__ double div_vc(double S, double v, double inv_pow2) {
+    return inv_pow2 != 0.0 ? __dmul_rn(S, inv_pow2) : __ddiv_rn(S, v);
+}
+
 __global__ void k_segment_heads(int64_t n, const uint32_t *__restrict__ keys,
                                 const uint32_t *__restrict__ sorted_idx, int nf,
                                 const double *__restrict__ w, int64_t ncells,
-                                const double *__restrict__ vc, double vc_uniform,
+                                const double *__restrict__ vc, double vc_uniform, double inv_pow2,
                                 double *__restrict__ out) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -330,7 +338,7 @@ __global__ void k_segment_heads(int64_t n, const uint32_t *__restrict__ keys,
             const double *wf = w + (int64_t)f * n;
             double acc = 0.0;
             for (int64_t q = p; q < e; ++q) acc = __dadd_rn(acc, wf[sorted_idx[q]]);
-            out[(int64_t)f * ncells + c] = __ddiv_rn(acc, v);
+            out[(int64_t)f * ncells + c] = div_vc(acc, v, inv_pow2);
         }
     }
 }
@@ -354,7 +362,7 @@ __global__ void k_scatter_cells(int64_t n, const int32_t *__restrict__ cell,
 __global__ void k_cell_sums(int64_t ncells, const uint32_t *__restrict__ off,
                             const uint32_t *__restrict__ idx, int nf,
                             const double *__restrict__ w, int64_t n,
-                            const double *__restrict__ vc, double vc_uniform,
+                            const double *__restrict__ vc, double vc_uniform, double inv_pow2,
                             double *__restrict__ out) {
     uint32_t s[kSegMax];
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
@@ -379,7 +387,7 @@ __global__ void k_cell_sums(int64_t ncells, const uint32_t *__restrict__ off,
             const double *wf = w + (int64_t)f * n;
             double acc = 0.0;
             for (int j = 0; j < k; ++j) acc = __dadd_rn(acc, wf[s[j]]);
-            out[(int64_t)f * ncells + c] = __ddiv_rn(acc, v);
+            out[(int64_t)f * ncells + c] = div_vc(acc, v, inv_pow2);
         }
     }
 }
@@ -419,7 +427,7 @@ __global__ void k_fixed_accum(int64_t n, const int32_t *__restrict__ cell, int n
 __global__ void k_fixed_finalize(int64_t ncells, int nf,
                                  const unsigned long long *__restrict__ acc,
                                  const double *__restrict__ unscale,
-                                 const double *__restrict__ vc, double vc_uniform,
+                                 const double *__restrict__ vc, double vc_uniform, double inv_pow2,
                                  double *__restrict__ out) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -427,7 +435,7 @@ __global__ void k_fixed_finalize(int64_t ncells, int nf,
         for (int f = 0; f < nf; ++f) {
             long long s = (long long)acc[(int64_t)f * ncells + c];
             double x = __dmul_rn(__ll2double_rn(s), unscale[f]);
-            out[(int64_t)f * ncells + c] = __ddiv_rn(x, v);
+            out[(int64_t)f * ncells + c] = div_vc(x, v, inv_pow2);
         }
     }
 }
@@ -514,6 +522,14 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
     const int mode = p->deposit_mode;
     const double *vc = m->kind != MESH_STRUCTURED ? m->tet.vc : nullptr;
     const double vcu = m->kind != MESH_STRUCTURED ? 0.0 : (m->dx * m->dx) * m->dx;
+    // a uniform cell volume that is a power of two (dx = 2^-k): divide by multiplying
+    double inv_pow2 = 0.0;
+    if (vc == nullptr && vcu > 0.0 && std::isfinite(vcu)) {
+        int e = 0;
+        const double mant = std::frexp(vcu, &e);
+        const double inv = std::ldexp(1.0, 1 - e);   // 1 / vcu when vcu = 2^(e-1)
+        if (mant == 0.5 && std::isnormal(inv)) inv_pow2 = inv;
+    }
 
     // workspace: cell[n] (int32); the ordered mode also counts particles per cell
     // (ncells + 1 counters, the last one staying 0 for the exclusive scan)
@@ -562,7 +578,7 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         }
         CGK_LAUNCH("cell_sums", (double)n * (4 + 8 * nf) + (double)ncells * (4 + 8 * nf), st,
                    k_cell_sums<<<grid_for(ncells), kThreads, 0, st>>>(ncells, off, idx, nf, w, n,
-                                                                      vc, vcu, out));
+                                                                      vc, vcu, inv_pow2, out));
         CGK_CUDA(cudaGetLastError());
         if (rep)
             for (int f = 0; f < nf && f < CG_REPORT_MAX_FIELDS; ++f) rep->fixed_point_bits[f] = 0;
@@ -607,7 +623,7 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         if (n > 0) {
             CGK_LAUNCH("segment_heads", (double)n * (8 + 8 * nf) + (double)ncells * 8 * nf, st,
                        k_segment_heads<<<grid_for(n), kThreads, 0, st>>>(
-                           n, kin, vin, nf, w, ncells, vc, vcu, out));
+                           n, kin, vin, nf, w, ncells, vc, vcu, inv_pow2, out));
             CGK_CUDA(cudaGetLastError());
         }
         if (rep)
@@ -649,7 +665,7 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         }
         CGK_LAUNCH("fixed_finalize", (double)ncells * nf * 16, st,
                    k_fixed_finalize<<<grid_for(ncells), kThreads, 0, st>>>(
-                       ncells, nf, acc, scales + 64, vc, vcu, out));
+                       ncells, nf, acc, scales + 64, vc, vcu, inv_pow2, out));
         CGK_CUDA(cudaGetLastError());
         // the host array hs must outlive the async copy
         CGK_CUDA(cudaStreamSynchronize(st));
