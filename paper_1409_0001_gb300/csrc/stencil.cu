@@ -2179,6 +2179,13 @@ __device__ __forceinline__ float fld(const TS *p) {
     }
 }
 
+// Shared segment of a flat-plane tile with padded rows: slot of plane cell q is
+// (q / nx - r0) (nx + 1) + q % nx + 1, so every row starts with a pad slot; the pad slots
+// and the rows outside the plane are zeroed once and never written, so a wall neighbour
+// (x- of x = 0, x+ of x = nx-1 through the next row's pad, y+-1 outside the plane) reads
+// +0.0 -- what the other engines add for a wall -- without a test.
+constexpr int kFlatSlots = kFlatCpt * kThreads + 4 * kFlatMaxNx + kFlatCpt * kThreads + 8;
+
 template <class TS, bool COH>
 __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, int z1, float ce,
                                                float gamma, float omega, const float *sdg,
@@ -2186,38 +2193,44 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, 
                                                TS *ynv) {
     constexpr int C = kFlatCpt;
     constexpr int S = kThreads;   // stride between a thread's cells
-    __shared__ float sp[C * S + 2 * kFlatMaxNx];
+    __shared__ float sp[kFlatSlots];
     const int t = threadIdx.y * TX + threadIdx.x;
     const int nx = g.nx, nxy = g.nxy, nz = g.nz;
+    const int P = nx + 1;
     const int q0 = chunk * (C * S);
-    unsigned nbits[C];
-    int nnxy[C];
-    bool own[C];
+    const int r0 = q0 / nx - 1;   // first row of the segment (may be -1)
+    auto slot = [&](int q) {
+        const int r = q / nx;
+        return (r - r0) * P + (q - r * nx) + 1;
+    };
+    const int nslots = ((q0 + C * S + nx - 1) / nx + 2 - r0) * P;
+    for (int i = t; i < nslots; i += S) sp[i] = 0.0f;
+    // per cell j: its segment slot, and (packed) whether it is in the plane and its
+    // number of x/y neighbours
+    int so[C];
+    unsigned ownm = 0u, nnp = 0u;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int q = q0 + t + S * j;
-        own[j] = q < nxy;
+        if (q < nxy) ownm |= 1u << j;
         const int iy = q / nx, ix = q - iy * nx;
-        nbits[j] = (ix > 0 ? 1u : 0u) | (ix + 1 < nx ? 2u : 0u) | (iy > 0 ? 4u : 0u) |
-                   (iy + 1 < g.ny ? 8u : 0u);
-        nnxy[j] = __popc(nbits[j]);
+        nnp |= (unsigned)((ix > 0) + (ix + 1 < nx) + (iy > 0) + (iy + 1 < g.ny)) << (3 * j);
+        so[j] = slot(q);
     }
+    auto own = [&](int j) { return (ownm >> j) & 1u; };
     const int lo0 = max(q0 - nx, 0);
     const int hi0 = q0 + C * S, hi1 = min(hi0 + nx, nxy);
     const bool hl0 = lo0 + t < q0, hl1 = lo0 + t + S < q0;
     const bool hh0 = hi0 + t < hi1, hh1 = hi0 + t + S < hi1;
-    // per-thread pointers at plane z (cell j at [S * j]); shared slots likewise
+    const int sl0 = slot(lo0 + t), sl1 = slot(lo0 + t + S);
+    const int sh0 = slot(hi0 + t), sh1 = slot(hi0 + t + S);
+    // per-thread pointers at plane z (cell j at [S * j])
     const size_t pz0 = (size_t)z0 * nxy;
     const TS *py = yv + pz0 + q0 + t;
     const TS *pp = ypv ? ypv + pz0 + q0 + t : nullptr;
     const TS *pr = rv + pz0 + q0 + t;
     TS *po = ynv + pz0 + q0 + t;
-    const TS *plo = yv + pz0 + lo0 + t;
-    const TS *phi = yv + pz0 + hi0 + t;
-    float *so = sp + nx + t;                  // own cells
-    float *sl = sp + nx + (lo0 - q0) + t;     // low halo
-    float *sh = sp + nx + (hi0 - q0) + t;     // high halo
-    const float *sym = so - nx, *syp = so + nx;
+    const int dlo = lo0 - q0, dhi = hi0 - q0;   // the halo cells relative to py
     float vdn[C], vc[C], vup[C], yp[C], rc[C], ha0 = 0.f, ha1 = 0.f, hb0 = 0.f, hb1 = 0.f;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -2230,19 +2243,20 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, 
     if (z0 < z1) {
 #pragma unroll
         for (int j = 0; j < C; ++j)
-            if (own[j]) {
+            if (own(j)) {
                 if (z0 > 0) vdn[j] = fld<TS, COH>(py - nxy + S * j);
                 vc[j] = fld<TS, COH>(py + S * j);
                 if (z0 + 1 < nz) vup[j] = fld<TS, COH>(py + nxy + S * j);
                 if (pp) yp[j] = fld<TS, COH>(pp + S * j);
                 rc[j] = fld<TS, COH>(pr + S * j);
             }
-        if (hl0) ha0 = fld<TS, COH>(plo);
-        if (hl1) ha1 = fld<TS, COH>(plo + S);
-        if (hh0) hb0 = fld<TS, COH>(phi);
-        if (hh1) hb1 = fld<TS, COH>(phi + S);
+        if (hl0) ha0 = fld<TS, COH>(py + dlo);
+        if (hl1) ha1 = fld<TS, COH>(py + dlo + S);
+        if (hh0) hb0 = fld<TS, COH>(py + dhi);
+        if (hh1) hb1 = fld<TS, COH>(py + dhi + S);
     }
-    for (int z = z0; z < z1; ++z) {
+    __syncthreads();   // the zeroed segment before the first plane is published
+for (int z = z0; z < z1; ++z) {
         // loads for plane z+1: y at z+2, y_prev and r at z+1, the halo at z+1
         float nup[C], nyp[C], nrc[C], na0 = 0.f, na1 = 0.f, nb0 = 0.f, nb1 = 0.f;
 #pragma unroll
@@ -2255,37 +2269,37 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, 
             const bool up2 = z + 2 < nz;
 #pragma unroll
             for (int j = 0; j < C; ++j)
-                if (own[j]) {
+                if (own(j)) {
                     if (up2) nup[j] = fld<TS, COH>(py + 2 * nxy + S * j);
                     if (pp) nyp[j] = fld<TS, COH>(pp + nxy + S * j);
                     nrc[j] = fld<TS, COH>(pr + nxy + S * j);
                 }
-            if (hl0) na0 = fld<TS, COH>(plo + nxy);
-            if (hl1) na1 = fld<TS, COH>(plo + nxy + S);
-            if (hh0) nb0 = fld<TS, COH>(phi + nxy);
-            if (hh1) nb1 = fld<TS, COH>(phi + nxy + S);
+            if (hl0) na0 = fld<TS, COH>(py + nxy + dlo);
+            if (hl1) na1 = fld<TS, COH>(py + nxy + dlo + S);
+            if (hh0) nb0 = fld<TS, COH>(py + nxy + dhi);
+            if (hh1) nb1 = fld<TS, COH>(py + nxy + dhi + S);
         }
 #pragma unroll
         for (int j = 0; j < C; ++j)
-            if (own[j]) so[S * j] = vc[j];
-        if (hl0) sl[0] = ha0;
-        if (hl1) sl[S] = ha1;
-        if (hh0) sh[0] = hb0;
-        if (hh1) sh[S] = hb1;
+            if (own(j)) sp[so[j]] = vc[j];
+        if (hl0) sp[sl0] = ha0;
+        if (hl1) sp[sl1] = ha1;
+        if (hh0) sp[sh0] = hb0;
+        if (hh1) sp[sh1] = hb1;
         __syncthreads();
         const int nnz = (z > 0) + (z + 1 < nz);
 #pragma unroll
         for (int j = 0; j < C; ++j)
-            if (own[j]) {
-                const unsigned b = nbits[j];
-                float sm = (b & 1u) ? so[S * j - 1] : 0.f;
-                sm += (b & 2u) ? so[S * j + 1] : 0.f;
-                sm += (b & 4u) ? sym[S * j] : 0.f;
-                sm += (b & 8u) ? syp[S * j] : 0.f;
+            if (own(j)) {
+                const float *c = sp + so[j];
+                float sm = c[-1];
+                sm += c[1];
+                sm += c[-P];
+                sm += c[P];
                 sm += vdn[j];
                 sm += vup[j];
                 const float v = vc[j];
-                const float ay = fmaf(sdg[nnxy[j] + nnz], v, -ce * sm);
+                const float ay = fmaf(sdg[((nnp >> (3 * j)) & 7u) + nnz], v, -ce * sm);
                 st(po + S * j, 0, fmaf(omega, v - yp[j] + gamma * (rc[j] - ay), yp[j]));
             }
         __syncthreads();
@@ -2305,8 +2319,6 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, 
         if (pp) pp += nxy;
         pr += nxy;
         po += nxy;
-        plo += nxy;
-        phi += nxy;
     }
 }
 
