@@ -638,6 +638,23 @@ __host__ __device__ constexpr size_t explicit_tb_smem(int K) {
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Asynchronous global -> shared copies of 16, 8 or 4 bytes (both addresses aligned to
+// the size); they land in the group the next cp_async_commit closes.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
 template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
@@ -1270,7 +1287,15 @@ __device__ __forceinline__ DF hi_df(float4 v) { return DF{v.z, v.w}; }
 __device__ __forceinline__ float4 pack_df(DF a, DF b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 __device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-template <class TS, int kMode>
+// RING (FP32 storage): the planes ahead arrive through a per-thread cp.async ring in shared
+// memory instead of registers -- each thread stages its own pair's x and d two planes
+// beyond the register queue, its b and its halo values beyond the next plane, and reads
+// back only what it staged (no barrier).  The pass is bound by memory latency, not by its
+// arithmetic, so deeper prefetch that costs no registers is what speeds it up; the
+// arithmetic and its order are unchanged (same bits).
+constexpr int kRefRing = 3;   // ring slots: two planes in flight beyond the one consumed
+
+template <class TS, int kMode, bool RING = false>
 __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int nzc, CoefDF cf,
                                                          int scheme, const DF *__restrict__ xin_all,
                                                          const TS *__restrict__ d_all,
@@ -1325,6 +1350,47 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     float4 vdn = f4z(), vc = f4z(), vup = f4z(), bc = f4z(), hlo = f4z(), hhi = f4z();
     DF hl = DF{0.f, 0.f}, hr = DF{0.f, 0.f};
     float rr = 0.0f, bb = 0.0f;
+    static_assert(!RING || sizeof(TS) == 4, "the ring stages FP32 corrections only");
+    constexpr int RS = RING ? kRefRing : 1;
+    __shared__ float4 rX[RS][kThreads];    // own pair's x (plane q + 2)
+    __shared__ float2 rD[RS][kThreads];    // own pair's d (plane q + 2)
+    __shared__ float4 rB[RS][kThreads];    // own pair's b (plane q + 1)
+    __shared__ float4 rhX[RS][2][TX];      // halo rows (plane q + 1): y - 1 (ty 0), y + 1 (ty TY-1)
+    __shared__ float2 rhD[RS][2][TX];
+    __shared__ DF rcX[RS][TY][2];          // halo columns (plane q + 1): x - 1, x + 2
+    __shared__ float rcD[RS][TY][2];
+    const int tid = ty * TX + tx, hrow = ty == 0 ? 0 : 1;
+    // the data step q consumes (what the register version loads at step q)
+    auto stage = [&](int q) {
+        if constexpr (RING) {
+            if (q + 1 < z1) {
+                const int sl = q % kRefRing;
+                const size_t kn = (size_t)kxy + (size_t)(q + 1) * g.nxy;
+                const DF *xg = xin_all + off;
+                if (own) {
+                    if (q + 2 < g.nz) {
+                        cp_async16(&rX[sl][tid], xg + kn + g.nxy);
+                        if (!kPlain) cp_async8(&rD[sl][tid], D + kn + g.nxy);
+                    }
+                    if (!kPlain) cp_async16(&rB[sl][tid], b_all + off + kn);
+                }
+                if (rowlo || rowhi) {
+                    const size_t kh = rowlo ? kn - g.nx : kn + g.nx;
+                    cp_async16(&rhX[sl][hrow][tx], xg + kh);
+                    if (!kPlain) cp_async8(&rhD[sl][hrow][tx], D + kh);
+                }
+                if (xl) {
+                    cp_async8(&rcX[sl][ty][0], xg + kn - 1);
+                    if (!kPlain) cp_async4(&rcD[sl][ty][0], D + kn - 1);
+                }
+                if (xr) {
+                    cp_async8(&rcX[sl][ty][1], xg + kn + 2);
+                    if (!kPlain) cp_async4(&rcD[sl][ty][1], D + kn + 2);
+                }
+            }
+            cp_async_commit();
+        }
+    };
     if (z0 < z1) {
         const size_t k0 = (size_t)kxy + (size_t)z0 * g.nxy;
         if (own) {
@@ -1338,12 +1404,46 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         if (xl) hl = val1(k0 - 1);
         if (xr) hr = val1(k0 + 2);
     }
+    if constexpr (RING) {
+#pragma unroll
+        for (int q = 0; q < kRefRing - 1; ++q) stage(z0 + q);
+    }
     #pragma unroll 4
     for (int z = z0; z < z1; ++z) {
         const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
         float4 nup = f4z(), nb_ = f4z(), nlo = f4z(), nhi = f4z();
         DF nl = DF{0.f, 0.f}, nr = DF{0.f, 0.f};
-        if (z + 1 < z1) {
+        if constexpr (RING) {
+            stage(z + kRefRing - 1);              // into the slot step z-1 consumed
+            cp_async_wait<kRefRing - 1>();        // step z's group has landed
+            if (z + 1 < z1) {
+                const int sl = z % kRefRing;
+                if (own) {
+                    if (z + 2 < g.nz) {
+                        const float4 xv = rX[sl][tid];
+                        if (kPlain) {
+                            nup = xv;
+                        } else {
+                            const float2 dv = rD[sl][tid];
+                            nup = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
+                        }
+                    }
+                    if (!kPlain) nb_ = rB[sl][tid];
+                }
+                if (rowlo || rowhi) {
+                    const float4 xv = rhX[sl][hrow][tx];
+                    float4 hv = xv;
+                    if (!kPlain) {
+                        const float2 dv = rhD[sl][hrow][tx];
+                        hv = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
+                    }
+                    if (rowlo) nlo = hv;
+                    else nhi = hv;
+                }
+                if (xl) nl = kPlain ? rcX[sl][ty][0] : df_add_f(rcX[sl][ty][0], rcD[sl][ty][0]);
+                if (xr) nr = kPlain ? rcX[sl][ty][1] : df_add_f(rcX[sl][ty][1], rcD[sl][ty][1]);
+            }
+        } else if (z + 1 < z1) {
             const size_t kn = kz + g.nxy;
             if (own) {
                 if (z + 2 < g.nz) nup = val2(kn + g.nxy);
@@ -1433,6 +1533,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         hl = nl;
         hr = nr;
     }
+    if constexpr (RING) cp_async_wait<0>();   // no copy outlives the block
     if (kMode == 3) return;   // the explicit step reduces nothing
     double vals[2] = {block_sum_f(rr), kMode != 1 ? block_sum_f(bb) : 0.0};
     double *partials = partials_all + (size_t)f * 2 * nb;
@@ -3086,8 +3187,8 @@ void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, i
     const dim3 blk(TX, TY);
     if (g.nx % 2 == 0 && g.per == 0) {
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
-        launch_chain(k_refine_df2<TS, kMode>, grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
-                     d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
+        launch_chain(k_refine_df2<TS, kMode, sizeof(TS) == 4>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
+                     scheme, xin, d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
     } else {
         launch_chain(k_refine_df<TS, kMode>, sw.grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
                      d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
@@ -3648,7 +3749,7 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
                    k_to_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, cells, A));
         for (int s = 0; s < p->nsteps; ++s) {
             CGK_LAUNCH("explicit_df", (double)n * nf * 16, st,
-                       launch_chain(k_refine_df2<float, 3>, grid, blk, st, g, sw.zlen, sw.nzc, cfdf,
+                       launch_chain(k_refine_df2<float, 3, true>, grid, blk, st, g, sw.zlen, sw.nzc, cfdf,
                                     p->scheme, (const DF *)A, (const float *)nullptr,
                                     (const DF *)nullptr, Bf, (DF *)nullptr, (float *)nullptr,
                                     (float *)nullptr, 0.0f, (double *)nullptr, (RefScal *)nullptr,
