@@ -2357,7 +2357,7 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, 
         if (hh1) hb1 = fld<TS, COH>(py + dhi + S);
     }
     __syncthreads();   // the zeroed segment before the first plane is published
-for (int z = z0; z < z1; ++z) {
+    for (int z = z0; z < z1; ++z) {
         // loads for plane z+1: y at z+2, y_prev and r at z+1, the halo at z+1
         float nup[C], nyp[C], nrc[C], na0 = 0.f, na1 = 0.f, nb0 = 0.f, nb1 = 0.f;
 #pragma unroll
