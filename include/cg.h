@@ -91,7 +91,8 @@ cg_status cg_mesh_cell_volumes(const cg_mesh *mesh, double *out_host);
  * two ends of the mesh along x, y, z neighbours of each other (on an axis of one cell,
  * of the cell itself); all zero restores the walls.  Deposition is unchanged.  With a
  * periodic axis the diffusion uses the z-marching or the vectorised sweeps and the
- * one-cell-per-thread refinement (params->sweep_shape must be 0, negative or 100 + z),
+ * one-cell-per-thread refinement (two cells per thread when only x is periodic and nx is
+ * even) (params->sweep_shape must be 0, negative or 100 + z),
  * and batched calls reject the mesh.  Drops the mesh's captured schedules and tuned shapes.  Errors: CG_EINVAL (NULL
  * or a tet mesh). */
 cg_status cg_mesh_set_periodic(cg_mesh *mesh, int px, int py, int pz);

@@ -1329,11 +1329,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     const bool own = (x < g.nx) && (y < g.ny);
     const bool rowlo = (ty == 0) && (y > 0) && (x < g.nx);
     const bool rowhi = (ty == TY - 1) && (y + 1 < g.ny) && (x < g.nx);
-    const bool xl = (tx == 0) && (x > 0) && (y < g.ny);
+    // a periodic x axis (the only periodic axis this kernel takes): the x halo cells wrap
+    // and every cell has both x neighbours
+    const bool px = (g.per & 1) != 0;
+    const bool xl = (tx == 0) && (x > 0 || px) && (y < g.ny);
     const int xlast = min(g.nx, x0 + 2 * TX) - 2;
-    const bool xr = (x == xlast) && (x + 2 < g.nx) && (y < g.ny);
+    const bool xr = (x == xlast) && (x + 2 < g.nx || px) && (y < g.ny);
+    const long long dxl = (px && x == 0) ? g.nx - 1 : -1;      // x - 1 of the pair's first cell
+    const long long dxr = (px && x + 2 >= g.nx) ? 2 - g.nx : 2;  // x + 1 of its second cell
     const int nyb = (y > 0) + (y + 1 < g.ny);
-    const int n0 = nyb + (x > 0) + 1, n1 = nyb + 1 + (x + 2 < g.nx);
+    const int n0 = nyb + ((x > 0 || px) ? 1 : 0) + 1, n1 = nyb + 1 + ((x + 2 < g.nx || px) ? 1 : 0);
     const int kxy = y * g.nx + x;
     // stencil value of a cell pair / of one cell
     auto val2 = [&](size_t k) -> float4 {
@@ -1380,12 +1385,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
                     if (!kPlain) cp_async8(&rhD[sl][hrow][tx], D + kh);
                 }
                 if (xl) {
-                    cp_async8(&rcX[sl][ty][0], xg + kn - 1);
-                    if (!kPlain) cp_async4(&rcD[sl][ty][0], D + kn - 1);
+                    const size_t kl = (size_t)((long long)kn + dxl);
+                    cp_async8(&rcX[sl][ty][0], xg + kl);
+                    if (!kPlain) cp_async4(&rcD[sl][ty][0], D + kl);
                 }
                 if (xr) {
-                    cp_async8(&rcX[sl][ty][1], xg + kn + 2);
-                    if (!kPlain) cp_async4(&rcD[sl][ty][1], D + kn + 2);
+                    const size_t kr = (size_t)((long long)kn + dxr);
+                    cp_async8(&rcX[sl][ty][1], xg + kr);
+                    if (!kPlain) cp_async4(&rcD[sl][ty][1], D + kr);
                 }
             }
             cp_async_commit();
@@ -1401,8 +1408,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         }
         if (rowlo) hlo = val2(k0 - g.nx);
         if (rowhi) hhi = val2(k0 + g.nx);
-        if (xl) hl = val1(k0 - 1);
-        if (xr) hr = val1(k0 + 2);
+        if (xl) hl = val1((size_t)((long long)k0 + dxl));
+        if (xr) hr = val1((size_t)((long long)k0 + dxr));
     }
     if constexpr (RING) {
 #pragma unroll
@@ -1451,8 +1458,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
             }
             if (rowlo) nlo = val2(kn - g.nx);
             if (rowhi) nhi = val2(kn + g.nx);
-            if (xl) nl = val1(kn - 1);
-            if (xr) nr = val1(kn + 2);
+            if (xl) nl = val1((size_t)((long long)kn + dxl));
+            if (xr) nr = val1((size_t)((long long)kn + dxr));
         }
         pl[ty + 1][tx] = vc;
         if (ty == 0) pl[0][tx] = hlo;
@@ -3177,15 +3184,15 @@ TS *cheb_pairs(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, do
 }
 
 // A double-float refinement pass of mode kMode: the two-cells-per-thread kernel when nx
-// is even (and no axis is periodic), the scalar one otherwise; both use the z-chunks of
-// sw (same partial slots).
+// is even (and no axis but x is periodic), the scalar one otherwise; both use the z-chunks
+// of sw (same partial slots).
 template <class TS, int kMode>
 void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, int scheme,
                       const DF *xin, const TS *d, const DF *b, DF *xout, DF *bout, TS *r, TS *y1,
                       float gamma, double *partials, RefScal *sc, RefScal *sc_next,
                       cudaStream_t st) {
     const dim3 blk(TX, TY);
-    if (g.nx % 2 == 0 && g.per == 0) {
+    if (g.nx % 2 == 0 && (g.per & ~1) == 0) {
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
         launch_chain(k_refine_df2<TS, kMode, sizeof(TS) == 4>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
                      scheme, xin, d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
