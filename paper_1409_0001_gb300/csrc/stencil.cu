@@ -1287,7 +1287,7 @@ __device__ __forceinline__ DF hi_df(float4 v) { return DF{v.z, v.w}; }
 __device__ __forceinline__ float4 pack_df(DF a, DF b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 __device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// RING (FP32 storage): the planes ahead arrive through a per-thread cp.async ring in shared
+// RING: the planes ahead arrive through a per-thread cp.async ring in shared
 // memory instead of registers -- each thread stages its own pair's x and d two planes
 // beyond the register queue, its b and its halo values beyond the next plane, and reads
 // back only what it staged (no barrier).  The pass is bound by memory latency, not by its
@@ -1355,15 +1355,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     float4 vdn = f4z(), vc = f4z(), vup = f4z(), bc = f4z(), hlo = f4z(), hhi = f4z();
     DF hl = DF{0.f, 0.f}, hr = DF{0.f, 0.f};
     float rr = 0.0f, bb = 0.0f;
-    static_assert(!RING || sizeof(TS) == 4, "the ring stages FP32 corrections only");
+    // d of a cell pair as stored (FP32: 8 bytes; BF16: 4 bytes); a halo column's d is
+    // staged as the aligned pair that holds it (BF16 has no 2-byte asynchronous copy)
+    using DPair = typename std::conditional<sizeof(TS) == 4, float2, __nv_bfloat162>::type;
     constexpr int RS = RING ? kRefRing : 1;
     __shared__ float4 rX[RS][kThreads];    // own pair's x (plane q + 2)
-    __shared__ float2 rD[RS][kThreads];    // own pair's d (plane q + 2)
+    __shared__ DPair rD[RS][kThreads];     // own pair's d (plane q + 2)
     __shared__ float4 rB[RS][kThreads];    // own pair's b (plane q + 1)
     __shared__ float4 rhX[RS][2][TX];      // halo rows (plane q + 1): y - 1 (ty 0), y + 1 (ty TY-1)
-    __shared__ float2 rhD[RS][2][TX];
+    __shared__ DPair rhD[RS][2][TX];
     __shared__ DF rcX[RS][TY][2];          // halo columns (plane q + 1): x - 1, x + 2
-    __shared__ float rcD[RS][TY][2];
+    __shared__ typename std::conditional<sizeof(TS) == 4, float, __nv_bfloat162>::type rcD[RS][TY][2];
+    auto cp_dpair = [&](void *dst, const TS *src) {
+        if constexpr (sizeof(TS) == 4) cp_async8(dst, src);
+        else cp_async4(dst, src);
+    };
+    auto dpair = [&](const DPair &v) -> float2 {
+        if constexpr (sizeof(TS) == 4) return v;
+        else return __bfloat1622float2(v);
+    };
     const int tid = ty * TX + tx, hrow = ty == 0 ? 0 : 1;
     // the data step q consumes (what the register version loads at step q)
     auto stage = [&](int q) {
@@ -1375,19 +1385,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
                 if (own) {
                     if (q + 2 < g.nz) {
                         cp_async16(&rX[sl][tid], xg + kn + g.nxy);
-                        if (!kPlain) cp_async8(&rD[sl][tid], D + kn + g.nxy);
+                        if (!kPlain) cp_dpair(&rD[sl][tid], D + kn + g.nxy);
                     }
                     if (!kPlain) cp_async16(&rB[sl][tid], b_all + off + kn);
                 }
                 if (rowlo || rowhi) {
                     const size_t kh = rowlo ? kn - g.nx : kn + g.nx;
                     cp_async16(&rhX[sl][hrow][tx], xg + kh);
-                    if (!kPlain) cp_async8(&rhD[sl][hrow][tx], D + kh);
+                    if (!kPlain) cp_dpair(&rhD[sl][hrow][tx], D + kh);
                 }
+                // (x - 1 is the odd cell of its pair, x + 2 the even one)
                 if (xl) {
                     const size_t kl = (size_t)((long long)kn + dxl);
                     cp_async8(&rcX[sl][ty][0], xg + kl);
-                    if (!kPlain) cp_async4(&rcD[sl][ty][0], D + kl);
+                    if (!kPlain) cp_async4(&rcD[sl][ty][0], D + (sizeof(TS) == 4 ? kl : kl - 1));
                 }
                 if (xr) {
                     const size_t kr = (size_t)((long long)kn + dxr);
@@ -1431,7 +1442,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
                         if (kPlain) {
                             nup = xv;
                         } else {
-                            const float2 dv = rD[sl][tid];
+                            const float2 dv = dpair(rD[sl][tid]);
                             nup = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
                         }
                     }
@@ -1441,14 +1452,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
                     const float4 xv = rhX[sl][hrow][tx];
                     float4 hv = xv;
                     if (!kPlain) {
-                        const float2 dv = rhD[sl][hrow][tx];
+                        const float2 dv = dpair(rhD[sl][hrow][tx]);
                         hv = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
                     }
                     if (rowlo) nlo = hv;
                     else nhi = hv;
                 }
-                if (xl) nl = kPlain ? rcX[sl][ty][0] : df_add_f(rcX[sl][ty][0], rcD[sl][ty][0]);
-                if (xr) nr = kPlain ? rcX[sl][ty][1] : df_add_f(rcX[sl][ty][1], rcD[sl][ty][1]);
+                if (xl) {
+                    if constexpr (sizeof(TS) == 4)
+                        nl = kPlain ? rcX[sl][ty][0] : df_add_f(rcX[sl][ty][0], rcD[sl][ty][0]);
+                    else
+                        nl = kPlain ? rcX[sl][ty][0]
+                                    : df_add_f(rcX[sl][ty][0], __high2float(rcD[sl][ty][0]));
+                }
+                if (xr) {
+                    if constexpr (sizeof(TS) == 4)
+                        nr = kPlain ? rcX[sl][ty][1] : df_add_f(rcX[sl][ty][1], rcD[sl][ty][1]);
+                    else
+                        nr = kPlain ? rcX[sl][ty][1]
+                                    : df_add_f(rcX[sl][ty][1], __low2float(rcD[sl][ty][1]));
+                }
             }
         } else if (z + 1 < z1) {
             const size_t kn = kz + g.nxy;
@@ -3194,7 +3217,7 @@ void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, i
     const dim3 blk(TX, TY);
     if (g.nx % 2 == 0 && (g.per & ~1) == 0) {
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
-        launch_chain(k_refine_df2<TS, kMode, sizeof(TS) == 4>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
+        launch_chain(k_refine_df2<TS, kMode, true>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
                      scheme, xin, d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
     } else {
         launch_chain(k_refine_df<TS, kMode>, sw.grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
