@@ -1287,15 +1287,15 @@ __device__ __forceinline__ DF hi_df(float4 v) { return DF{v.z, v.w}; }
 __device__ __forceinline__ float4 pack_df(DF a, DF b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 __device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// RING: the planes ahead arrive through a per-thread cp.async ring in shared
-// memory instead of registers -- each thread stages its own pair's x and d two planes
-// beyond the register queue, its b and its halo values beyond the next plane, and reads
-// back only what it staged (no barrier).  The pass is bound by memory latency, not by its
+// The planes ahead arrive through a per-thread cp.async ring in shared memory instead of
+// registers: each thread stages its own pair's x and d two planes beyond the register
+// queue, its b and its halo values beyond the next plane, and reads back only what it
+// staged (no barrier).  The pass is bound by memory latency, not by its
 // arithmetic, so deeper prefetch that costs no registers is what speeds it up; the
 // arithmetic and its order are unchanged (same bits).
 constexpr int kRefRing = 3;   // ring slots: two planes in flight beyond the one consumed
 
-template <class TS, int kMode, bool RING = false>
+template <class TS, int kMode>
 __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int nzc, CoefDF cf,
                                                          int scheme, const DF *__restrict__ xin_all,
                                                          const TS *__restrict__ d_all,
@@ -1358,7 +1358,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     // d of a cell pair as stored (FP32: 8 bytes; BF16: 4 bytes); a halo column's d is
     // staged as the aligned pair that holds it (BF16 has no 2-byte asynchronous copy)
     using DPair = typename std::conditional<sizeof(TS) == 4, float2, __nv_bfloat162>::type;
-    constexpr int RS = RING ? kRefRing : 1;
+    constexpr int RS = kRefRing;
     __shared__ float4 rX[RS][kThreads];    // own pair's x (plane q + 2)
     __shared__ DPair rD[RS][kThreads];     // own pair's d (plane q + 2)
     __shared__ float4 rB[RS][kThreads];    // own pair's b (plane q + 1)
@@ -1377,37 +1377,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     const int tid = ty * TX + tx, hrow = ty == 0 ? 0 : 1;
     // the data step q consumes (what the register version loads at step q)
     auto stage = [&](int q) {
-        if constexpr (RING) {
-            if (q + 1 < z1) {
-                const int sl = q % kRefRing;
-                const size_t kn = (size_t)kxy + (size_t)(q + 1) * g.nxy;
-                const DF *xg = xin_all + off;
-                if (own) {
-                    if (q + 2 < g.nz) {
-                        cp_async16(&rX[sl][tid], xg + kn + g.nxy);
-                        if (!kPlain) cp_dpair(&rD[sl][tid], D + kn + g.nxy);
-                    }
-                    if (!kPlain) cp_async16(&rB[sl][tid], b_all + off + kn);
+        if (q + 1 < z1) {
+            const int sl = q % kRefRing;
+            const size_t kn = (size_t)kxy + (size_t)(q + 1) * g.nxy;
+            const DF *xg = xin_all + off;
+            if (own) {
+                if (q + 2 < g.nz) {
+                    cp_async16(&rX[sl][tid], xg + kn + g.nxy);
+                    if (!kPlain) cp_dpair(&rD[sl][tid], D + kn + g.nxy);
                 }
-                if (rowlo || rowhi) {
-                    const size_t kh = rowlo ? kn - g.nx : kn + g.nx;
-                    cp_async16(&rhX[sl][hrow][tx], xg + kh);
-                    if (!kPlain) cp_dpair(&rhD[sl][hrow][tx], D + kh);
-                }
-                // (x - 1 is the odd cell of its pair, x + 2 the even one)
-                if (xl) {
-                    const size_t kl = (size_t)((long long)kn + dxl);
-                    cp_async8(&rcX[sl][ty][0], xg + kl);
-                    if (!kPlain) cp_async4(&rcD[sl][ty][0], D + (sizeof(TS) == 4 ? kl : kl - 1));
-                }
-                if (xr) {
-                    const size_t kr = (size_t)((long long)kn + dxr);
-                    cp_async8(&rcX[sl][ty][1], xg + kr);
-                    if (!kPlain) cp_async4(&rcD[sl][ty][1], D + kr);
-                }
+                if (!kPlain) cp_async16(&rB[sl][tid], b_all + off + kn);
             }
-            cp_async_commit();
+            if (rowlo || rowhi) {
+                const size_t kh = rowlo ? kn - g.nx : kn + g.nx;
+                cp_async16(&rhX[sl][hrow][tx], xg + kh);
+                if (!kPlain) cp_dpair(&rhD[sl][hrow][tx], D + kh);
+            }
+            // (x - 1 is the odd cell of its pair, x + 2 the even one)
+            if (xl) {
+                const size_t kl = (size_t)((long long)kn + dxl);
+                cp_async8(&rcX[sl][ty][0], xg + kl);
+                if (!kPlain) cp_async4(&rcD[sl][ty][0], D + (sizeof(TS) == 4 ? kl : kl - 1));
+            }
+            if (xr) {
+                const size_t kr = (size_t)((long long)kn + dxr);
+                cp_async8(&rcX[sl][ty][1], xg + kr);
+                if (!kPlain) cp_async4(&rcD[sl][ty][1], D + kr);
+            }
         }
+        cp_async_commit();
     };
     if (z0 < z1) {
         const size_t k0 = (size_t)kxy + (size_t)z0 * g.nxy;
@@ -1422,67 +1420,53 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         if (xl) hl = val1((size_t)((long long)k0 + dxl));
         if (xr) hr = val1((size_t)((long long)k0 + dxr));
     }
-    if constexpr (RING) {
 #pragma unroll
-        for (int q = 0; q < kRefRing - 1; ++q) stage(z0 + q);
-    }
-    #pragma unroll 4
+    for (int q = 0; q < kRefRing - 1; ++q) stage(z0 + q);
+#pragma unroll 4
     for (int z = z0; z < z1; ++z) {
         const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
         float4 nup = f4z(), nb_ = f4z(), nlo = f4z(), nhi = f4z();
         DF nl = DF{0.f, 0.f}, nr = DF{0.f, 0.f};
-        if constexpr (RING) {
-            stage(z + kRefRing - 1);              // into the slot step z-1 consumed
-            cp_async_wait<kRefRing - 1>();        // step z's group has landed
-            if (z + 1 < z1) {
-                const int sl = z % kRefRing;
-                if (own) {
-                    if (z + 2 < g.nz) {
-                        const float4 xv = rX[sl][tid];
-                        if (kPlain) {
-                            nup = xv;
-                        } else {
-                            const float2 dv = dpair(rD[sl][tid]);
-                            nup = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
-                        }
-                    }
-                    if (!kPlain) nb_ = rB[sl][tid];
-                }
-                if (rowlo || rowhi) {
-                    const float4 xv = rhX[sl][hrow][tx];
-                    float4 hv = xv;
-                    if (!kPlain) {
-                        const float2 dv = dpair(rhD[sl][hrow][tx]);
-                        hv = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
-                    }
-                    if (rowlo) nlo = hv;
-                    else nhi = hv;
-                }
-                if (xl) {
-                    if constexpr (sizeof(TS) == 4)
-                        nl = kPlain ? rcX[sl][ty][0] : df_add_f(rcX[sl][ty][0], rcD[sl][ty][0]);
-                    else
-                        nl = kPlain ? rcX[sl][ty][0]
-                                    : df_add_f(rcX[sl][ty][0], __high2float(rcD[sl][ty][0]));
-                }
-                if (xr) {
-                    if constexpr (sizeof(TS) == 4)
-                        nr = kPlain ? rcX[sl][ty][1] : df_add_f(rcX[sl][ty][1], rcD[sl][ty][1]);
-                    else
-                        nr = kPlain ? rcX[sl][ty][1]
-                                    : df_add_f(rcX[sl][ty][1], __low2float(rcD[sl][ty][1]));
-                }
-            }
-        } else if (z + 1 < z1) {
-            const size_t kn = kz + g.nxy;
+        stage(z + kRefRing - 1);              // into the slot step z-1 consumed
+        cp_async_wait<kRefRing - 1>();        // step z's group has landed
+        if (z + 1 < z1) {
+            const int sl = z % kRefRing;
             if (own) {
-                if (z + 2 < g.nz) nup = val2(kn + g.nxy);
-                if (!kPlain) nb_ = Bv[kn >> 1];
+                if (z + 2 < g.nz) {
+                    const float4 xv = rX[sl][tid];
+                    if (kPlain) {
+                        nup = xv;
+                    } else {
+                        const float2 dv = dpair(rD[sl][tid]);
+                        nup = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
+                    }
+                }
+                if (!kPlain) nb_ = rB[sl][tid];
             }
-            if (rowlo) nlo = val2(kn - g.nx);
-            if (rowhi) nhi = val2(kn + g.nx);
-            if (xl) nl = val1((size_t)((long long)kn + dxl));
-            if (xr) nr = val1((size_t)((long long)kn + dxr));
+            if (rowlo || rowhi) {
+                const float4 xv = rhX[sl][hrow][tx];
+                float4 hv = xv;
+                if (!kPlain) {
+                    const float2 dv = dpair(rhD[sl][hrow][tx]);
+                    hv = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
+                }
+                if (rowlo) nlo = hv;
+                else nhi = hv;
+            }
+            if (xl) {
+                if constexpr (sizeof(TS) == 4)
+                    nl = kPlain ? rcX[sl][ty][0] : df_add_f(rcX[sl][ty][0], rcD[sl][ty][0]);
+                else
+                    nl = kPlain ? rcX[sl][ty][0]
+                                : df_add_f(rcX[sl][ty][0], __high2float(rcD[sl][ty][0]));
+            }
+            if (xr) {
+                if constexpr (sizeof(TS) == 4)
+                    nr = kPlain ? rcX[sl][ty][1] : df_add_f(rcX[sl][ty][1], rcD[sl][ty][1]);
+                else
+                    nr = kPlain ? rcX[sl][ty][1]
+                                : df_add_f(rcX[sl][ty][1], __low2float(rcD[sl][ty][1]));
+            }
         }
         pl[ty + 1][tx] = vc;
         if (ty == 0) pl[0][tx] = hlo;
@@ -1563,7 +1547,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         hl = nl;
         hr = nr;
     }
-    if constexpr (RING) cp_async_wait<0>();   // no copy outlives the block
+    cp_async_wait<0>();   // no copy outlives the block
     if (kMode == 3) return;   // the explicit step reduces nothing
     double vals[2] = {block_sum_f(rr), kMode != 1 ? block_sum_f(bb) : 0.0};
     double *partials = partials_all + (size_t)f * 2 * nb;
@@ -3217,7 +3201,7 @@ void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, i
     const dim3 blk(TX, TY);
     if (g.nx % 2 == 0 && (g.per & ~1) == 0) {
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
-        launch_chain(k_refine_df2<TS, kMode, true>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
+        launch_chain(k_refine_df2<TS, kMode>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
                      scheme, xin, d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
     } else {
         launch_chain(k_refine_df<TS, kMode>, sw.grid, blk, st, g, sw.zlen, sw.nzc, cf, scheme, xin,
@@ -3779,7 +3763,7 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
                    k_to_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, cells, A));
         for (int s = 0; s < p->nsteps; ++s) {
             CGK_LAUNCH("explicit_df", (double)n * nf * 16, st,
-                       launch_chain(k_refine_df2<float, 3, true>, grid, blk, st, g, sw.zlen, sw.nzc, cfdf,
+                       launch_chain(k_refine_df2<float, 3>, grid, blk, st, g, sw.zlen, sw.nzc, cfdf,
                                     p->scheme, (const DF *)A, (const float *)nullptr,
                                     (const DF *)nullptr, Bf, (DF *)nullptr, (float *)nullptr,
                                     (float *)nullptr, 0.0f, (double *)nullptr, (RefScal *)nullptr,
