@@ -1154,6 +1154,97 @@ struct CoefDF {
     DF dg[7];
 };
 
+// ---- the same double-float operations on a cell pair, one packed instruction per pair
+// (the f32x2 add, multiply and fused multiply-add of sm_100 and later).  A DF2 holds the
+// hi parts of two cells in one float2 and their lo parts in another; every operation
+// below is, cell by cell, the IEEE operation of its scalar counterpart above, in the same
+// order, so the two cells' results are bit-identical to two scalar evaluations.
+// Negations that the scalar forms get for free as operand modifiers are folded instead:
+// a constant's negative is kept beside it, and an exact product error is carried negated
+// (p - c a is exact, so it equals -(c a - p) without rounding).
+struct DF2 {
+    float2 hi, lo;
+};
+struct DF2n {   // the pair value hi - nlo (a product with its error carried negated)
+    float2 hi, nlo;
+};
+struct DFc2 {   // a double-float constant broadcast to both cells, with its negative
+    float2 hi, lo, nhi, nlo;
+};
+__device__ __forceinline__ DFc2 dfc2(DF c) {
+    return DFc2{make_float2(c.hi, c.hi), make_float2(c.lo, c.lo), make_float2(-c.hi, -c.hi),
+                make_float2(-c.lo, -c.lo)};
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as one fused multiply-add, -1 * b + a: the exact product, then a single rounding
+// of the exact difference, i.e. the IEEE difference (CUDA has no packed subtract intrinsic)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ DF2 df2_two_sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return DF2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ DF2 df2_fast2sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return DF2{s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ DF2 df2_add(DF2 a, DF2 b) {   // operator+
+    DF2 s = df2_two_sum(a.hi, b.hi);
+    s.lo = add2(s.lo, add2(a.lo, b.lo));
+    return df2_fast2sum(s.hi, s.lo);
+}
+__device__ __forceinline__ void df2_acc(DF2 &a, DF2 b) {  // operator+= (the cascade)
+    const DF2 t = df2_two_sum(a.hi, b.hi);
+    a.hi = t.hi;
+    a.lo = add2(a.lo, add2(t.lo, b.lo));
+}
+__device__ __forceinline__ DF2 df2_add_f(DF2 a, float2 b) {
+    DF2 s = df2_two_sum(a.hi, b);
+    s.lo = add2(s.lo, a.lo);
+    return df2_fast2sum(s.hi, s.lo);
+}
+__device__ __forceinline__ float2 df2_f(DF2 a) { return add2(a.hi, a.lo); }
+__device__ __forceinline__ float2 df2_f(DF2n a) { return sub2(a.hi, a.nlo); }
+// c * a unnormalised (df_mul_un): the error terms are accumulated negated
+__device__ __forceinline__ DF2n df2_mul_un(const DFc2 &c, DF2 a) {
+    const float2 p = mul2(c.hi, a.hi);
+    float2 en = fma2(c.nhi, a.hi, p);
+    en = fma2(c.nhi, a.lo, en);
+    en = fma2(c.nlo, a.hi, en);
+    return DF2n{p, en};
+}
+__device__ __forceinline__ DF2 df2_mul(const DFc2 &c, DF2 a) {   // df_mul(c, a)
+    const DF2n q = df2_mul_un(c, a);
+    const float2 s = sub2(q.hi, q.nlo);
+    return DF2{s, sub2(sub2(q.hi, s), q.nlo)};
+}
+// df_lap: nn and its negative per cell
+__device__ __forceinline__ DF2 df2_lap(DF2 s, DF2 v, float2 nn, float2 nnn) {
+    const float2 np = mul2(nnn, v.hi);          // -(nn v.hi), rounded
+    const float2 ep = fma2(nn, v.hi, np);        // its exact error
+    const DF2 t = df2_two_sum(s.hi, np);
+    return DF2{t.hi, add2(sub2(s.lo, fma2(nn, v.lo, ep)), t.lo)};
+}
+// df_res: r = (b - v) + ce L
+__device__ __forceinline__ DF2 df2_res(DF2 b, DF2 v, const DFc2 &ce, DF2 L) {
+    const float2 s = sub2(b.hi, v.hi);
+    const float2 bb = sub2(s, b.hi);
+    const float2 e = sub2(sub2(b.hi, sub2(s, bb)), add2(v.hi, bb));
+    const float2 tl = add2(sub2(b.lo, v.lo), e);
+    const DF2n q = df2_mul_un(ce, L);
+    const DF2 u = df2_two_sum(s, q.hi);
+    return DF2{u.hi, add2(sub2(tl, q.nlo), u.lo)};
+}
+// a cell pair as the two-cells-per-thread kernels store it: (hi0, hi1, lo0, lo1)
+__device__ __forceinline__ DF2 df2_of(float4 v) {
+    return DF2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ float4 f4_of(DF2 a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
+
 __global__ void k_to_df(size_t n, const double *__restrict__ u, DF *__restrict__ x) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -1168,6 +1259,27 @@ __global__ void k_from_df(size_t n, const DF *__restrict__ x, double *__restrict
          i += (size_t)gridDim.x * blockDim.x) {
         DF v = x[i];
         u[i] = (double)v.hi + (double)v.lo;
+    }
+}
+
+// The same conversions in the pair layout of the two-cells-per-thread kernels: cells
+// 2i and 2i + 1 as one float4 (hi0, hi1, lo0, lo1).  Same values as k_to_df / k_from_df.
+__global__ void k_to_df_pairs(size_t npairs, const double *__restrict__ u, float4 *__restrict__ x) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double v0 = u[2 * i], v1 = u[2 * i + 1];
+        const float h0 = __double2float_rn(v0), h1 = __double2float_rn(v1);
+        x[i] = make_float4(h0, h1, __double2float_rn(v0 - (double)h0),
+                           __double2float_rn(v1 - (double)h1));
+    }
+}
+
+__global__ void k_from_df_pairs(size_t npairs, const float4 *__restrict__ x, double *__restrict__ u) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = x[i];
+        u[2 * i] = (double)v.x + (double)v.z;
+        u[2 * i + 1] = (double)v.y + (double)v.w;
     }
 }
 
@@ -1259,11 +1371,14 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
 }
 
 // The refinement pass of k_refine_df with two x-cells per thread (nx even): a float4
-// holds the two cells' double-float values, a warp row covers 64 cells; x neighbours
-// by shuffle (and two scalar loads at the tile edges), y neighbours from a shared plane,
-// z neighbours from a register queue with one-plane-ahead prefetch.  Modes 0-2 as in
-// k_refine_df; mode 3 is one explicit Euler step in double-float arithmetic,
-// xout = xin + c L xin (cf.c = dtau / dx^2), with no reduction.
+// holds a cell pair's double-float values in the pair layout (hi0, hi1, lo0, lo1), and
+// the pair's arithmetic is the packed DF2 form (one f32x2 instruction for both cells,
+// bit-identical to the scalar form); a warp row covers 64 cells; x neighbours by shuffle
+// (and the neighbouring pairs at the tile edges), y neighbours from a shared plane,
+// z neighbours from a register queue.  Modes 0-2 as in k_refine_df; mode 3 is one
+// explicit Euler step in double-float arithmetic, xout = xin + c L xin
+// (cf.c = dtau / dx^2), with no reduction.  The double-float vectors it reads and writes
+// (x, b) are in the pair layout (k_to_df_pairs / k_from_df_pairs).
 template <class TS> struct Pair;
 template <> struct Pair<float> {
     static __device__ __forceinline__ float2 load(const float *p, size_t i) {
@@ -1282,17 +1397,20 @@ template <> struct Pair<__nv_bfloat16> {
     }
 };
 
-__device__ __forceinline__ DF lo_df(float4 v) { return DF{v.x, v.y}; }
-__device__ __forceinline__ DF hi_df(float4 v) { return DF{v.z, v.w}; }
-__device__ __forceinline__ float4 pack_df(DF a, DF b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 __device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// x + d of a cell pair (pair layout in and out)
+__device__ __forceinline__ float4 pair_add(float4 xv, float2 dv) { return f4_of(df2_add_f(df2_of(xv), dv)); }
 
 // The planes ahead arrive through a per-thread cp.async ring in shared memory instead of
 // registers: each thread stages its own pair's x and d two planes beyond the register
 // queue, its b and its halo values beyond the next plane, and reads back only what it
-// staged (no barrier).  The pass is bound by memory latency, not by its
-// arithmetic, so deeper prefetch that costs no registers is what speeds it up; the
-// arithmetic and its order are unchanged (same bits).
+// staged (no barrier).  The pass is bound by memory latency and instruction issue, not
+// by its arithmetic, so deeper prefetch that costs no registers is what speeds it up.
+// The march is unrolled by the ring depth: a step's ring slot and shared plane buffer are
+// then compile-time constants, the three-plane register queue rotates by renaming (the
+// register of plane z-1 takes plane z+2 once the step has used it), and with one shared
+// plane buffer per slot a step needs a single barrier (a buffer is written again three
+// steps later, after two more barriers).
 constexpr int kRefRing = 3;   // ring slots: two planes in flight beyond the one consumed
 
 template <class TS, int kMode>
@@ -1317,12 +1435,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     const float4 *X = reinterpret_cast<const float4 *>(xin_all + off);   // cell pairs
     constexpr bool kPlain = kMode == 0 || kMode == 3;   // the stencil of x itself (no d)
     const TS *D = kPlain ? nullptr : d_all + off;
-    const float4 *Bv = reinterpret_cast<const float4 *>((kPlain ? xin_all : b_all) + off);
+    const float4 *Bp = reinterpret_cast<const float4 *>(kPlain ? nullptr : b_all + off);
     float4 *XO = reinterpret_cast<float4 *>(xout_all + off);
     float4 *BO = reinterpret_cast<float4 *>(bout_all ? bout_all + off : nullptr);
     TS *r = r_all + off;
     TS *y1 = y1_all + off;
-    __shared__ float4 pl[TY + 2][TX];
+    const DFc2 c2 = dfc2(cf.c), hc2 = dfc2(cf.half_c), ce2 = dfc2(cf.ce);
+    constexpr int RS = kRefRing;
+    __shared__ float4 pl[RS][TY + 2][TX];   // the plane's tile with its y halo rows, per slot
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * (2 * TX);
     const int x = x0 + 2 * tx, y = blockIdx.y * TY + ty;
@@ -1335,36 +1455,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     const bool xl = (tx == 0) && (x > 0 || px) && (y < g.ny);
     const int xlast = min(g.nx, x0 + 2 * TX) - 2;
     const bool xr = (x == xlast) && (x + 2 < g.nx || px) && (y < g.ny);
-    const long long dxl = (px && x == 0) ? g.nx - 1 : -1;      // x - 1 of the pair's first cell
-    const long long dxr = (px && x + 2 >= g.nx) ? 2 - g.nx : 2;  // x + 1 of its second cell
+    const int dxl = (px && x == 0) ? g.nx - 1 : -1;      // x - 1 of the pair's first cell
+    const int dxr = (px && x + 2 >= g.nx) ? 2 - g.nx : 2;  // x + 1 of its second cell
     const int nyb = (y > 0) + (y + 1 < g.ny);
     const int n0 = nyb + ((x > 0 || px) ? 1 : 0) + 1, n1 = nyb + 1 + ((x + 2 < g.nx || px) ? 1 : 0);
+    // the two cells' neighbour counts (and negatives) on planes with both z neighbours
+    const float2 nn_mid = make_float2((float)(n0 + 2), (float)(n1 + 2));
+    const float2 nnn_mid = make_float2(-nn_mid.x, -nn_mid.y);
     const int kxy = y * g.nx + x;
-    // stencil value of a cell pair / of one cell
-    auto val2 = [&](size_t k) -> float4 {
-        float4 xv = X[k >> 1];
+    // stencil value of a cell pair (pair layout) / of one cell
+    auto val2 = [&](int k) -> float4 {
+        const float4 xv = X[k >> 1];
         if (kPlain) return xv;
-        float2 dv = PR::load(D, k);
-        return pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
+        return pair_add(xv, PR::load(D, k));
     };
-    auto val1 = [&](size_t k) -> DF {
-        DF xv = xin_all[off + k];
+    auto val1 = [&](int k) -> DF {
+        const float4 pv = X[k >> 1];
+        const DF xv = (k & 1) ? DF{pv.y, pv.w} : DF{pv.x, pv.z};
         if (kPlain) return xv;
-        return df_add_f(xv, ld(D, (int)k));
+        return df_add_f(xv, ld(D, k));
     };
-    float4 vdn = f4z(), vc = f4z(), vup = f4z(), bc = f4z(), hlo = f4z(), hhi = f4z();
-    DF hl = DF{0.f, 0.f}, hr = DF{0.f, 0.f};
-    float rr = 0.0f, bb = 0.0f;
     // d of a cell pair as stored (FP32: 8 bytes; BF16: 4 bytes); a halo column's d is
     // staged as the aligned pair that holds it (BF16 has no 2-byte asynchronous copy)
     using DPair = typename std::conditional<sizeof(TS) == 4, float2, __nv_bfloat162>::type;
-    constexpr int RS = kRefRing;
     __shared__ float4 rX[RS][kThreads];    // own pair's x (plane q + 2)
     __shared__ DPair rD[RS][kThreads];     // own pair's d (plane q + 2)
     __shared__ float4 rB[RS][kThreads];    // own pair's b (plane q + 1)
     __shared__ float4 rhX[RS][2][TX];      // halo rows (plane q + 1): y - 1 (ty 0), y + 1 (ty TY-1)
     __shared__ DPair rhD[RS][2][TX];
-    __shared__ DF rcX[RS][TY][2];          // halo columns (plane q + 1): x - 1, x + 2
+    __shared__ float4 rcX[RS][TY][2];      // the pairs holding the halo columns (plane q + 1): x - 1, x + 2
     __shared__ typename std::conditional<sizeof(TS) == 4, float, __nv_bfloat162>::type rcD[RS][TY][2];
     auto cp_dpair = [&](void *dst, const TS *src) {
         if constexpr (sizeof(TS) == 4) cp_async8(dst, src);
@@ -1375,177 +1494,168 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
         else return __bfloat1622float2(v);
     };
     const int tid = ty * TX + tx, hrow = ty == 0 ? 0 : 1;
-    // the data step q consumes (what the register version loads at step q)
-    auto stage = [&](int q) {
+    // the data step q reads back for step q + 1 (own x, d of plane q + 2; b and the halo of
+    // plane q + 1), into ring slot sl
+    auto stage = [&](int q, int sl) {
         if (q + 1 < z1) {
-            const int sl = q % kRefRing;
-            const size_t kn = (size_t)kxy + (size_t)(q + 1) * g.nxy;
-            const DF *xg = xin_all + off;
+            const int kn = kxy + (q + 1) * g.nxy;
             if (own) {
                 if (q + 2 < g.nz) {
-                    cp_async16(&rX[sl][tid], xg + kn + g.nxy);
+                    cp_async16(&rX[sl][tid], X + ((kn + g.nxy) >> 1));
                     if (!kPlain) cp_dpair(&rD[sl][tid], D + kn + g.nxy);
                 }
-                if (!kPlain) cp_async16(&rB[sl][tid], b_all + off + kn);
+                if (!kPlain) cp_async16(&rB[sl][tid], Bp + (kn >> 1));
             }
             if (rowlo || rowhi) {
-                const size_t kh = rowlo ? kn - g.nx : kn + g.nx;
-                cp_async16(&rhX[sl][hrow][tx], xg + kh);
+                const int kh = rowlo ? kn - g.nx : kn + g.nx;
+                cp_async16(&rhX[sl][hrow][tx], X + (kh >> 1));
                 if (!kPlain) cp_dpair(&rhD[sl][hrow][tx], D + kh);
             }
             // (x - 1 is the odd cell of its pair, x + 2 the even one)
             if (xl) {
-                const size_t kl = (size_t)((long long)kn + dxl);
-                cp_async8(&rcX[sl][ty][0], xg + kl);
+                const int kl = kn + dxl;
+                cp_async16(&rcX[sl][ty][0], X + (kl >> 1));
                 if (!kPlain) cp_async4(&rcD[sl][ty][0], D + (sizeof(TS) == 4 ? kl : kl - 1));
             }
             if (xr) {
-                const size_t kr = (size_t)((long long)kn + dxr);
-                cp_async8(&rcX[sl][ty][1], xg + kr);
+                const int kr = kn + dxr;
+                cp_async16(&rcX[sl][ty][1], X + (kr >> 1));
                 if (!kPlain) cp_async4(&rcD[sl][ty][1], D + kr);
             }
         }
         cp_async_commit();
     };
+    // register state of the march: the plane queue (three registers that rotate by
+    // renaming), the cell pair's b and the halo values of the current plane
+    float4 qa = f4z(), qb = f4z(), qc = f4z(), bc = f4z(), hlo = f4z(), hhi = f4z();
+    DF hl = DF{0.f, 0.f}, hr = DF{0.f, 0.f};
+    float rr = 0.0f, bb = 0.0f;
     if (z0 < z1) {
-        const size_t k0 = (size_t)kxy + (size_t)z0 * g.nxy;
+        const int k0 = kxy + z0 * g.nxy;
         if (own) {
-            if (z0 > 0) vdn = val2(k0 - g.nxy);
-            vc = val2(k0);
-            if (z0 + 1 < g.nz) vup = val2(k0 + g.nxy);
-            if (!kPlain) bc = Bv[k0 >> 1];
+            if (z0 > 0) qa = val2(k0 - g.nxy);
+            qb = val2(k0);
+            if (z0 + 1 < g.nz) qc = val2(k0 + g.nxy);
+            if (!kPlain) bc = Bp[k0 >> 1];
         }
         if (rowlo) hlo = val2(k0 - g.nx);
         if (rowhi) hhi = val2(k0 + g.nx);
-        if (xl) hl = val1((size_t)((long long)k0 + dxl));
-        if (xr) hr = val1((size_t)((long long)k0 + dxr));
+        if (xl) hl = val1(k0 + dxl);
+        if (xr) hr = val1(k0 + dxr);
     }
-#pragma unroll
-    for (int q = 0; q < kRefRing - 1; ++q) stage(z0 + q);
-#pragma unroll 4
-    for (int z = z0; z < z1; ++z) {
-        const size_t kz = (size_t)kxy + (size_t)z * g.nxy;
-        float4 nup = f4z(), nb_ = f4z(), nlo = f4z(), nhi = f4z();
-        DF nl = DF{0.f, 0.f}, nr = DF{0.f, 0.f};
-        stage(z + kRefRing - 1);              // into the slot step z-1 consumed
-        cp_async_wait<kRefRing - 1>();        // step z's group has landed
-        if (z + 1 < z1) {
-            const int sl = z % kRefRing;
-            if (own) {
-                if (z + 2 < g.nz) {
-                    const float4 xv = rX[sl][tid];
-                    if (kPlain) {
-                        nup = xv;
-                    } else {
-                        const float2 dv = dpair(rD[sl][tid]);
-                        nup = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
-                    }
-                }
-                if (!kPlain) nb_ = rB[sl][tid];
-            }
-            if (rowlo || rowhi) {
-                const float4 xv = rhX[sl][hrow][tx];
-                float4 hv = xv;
-                if (!kPlain) {
-                    const float2 dv = dpair(rhD[sl][hrow][tx]);
-                    hv = pack_df(df_add_f(lo_df(xv), dv.x), df_add_f(hi_df(xv), dv.y));
-                }
-                if (rowlo) nlo = hv;
-                else nhi = hv;
-            }
-            if (xl) {
-                if constexpr (sizeof(TS) == 4)
-                    nl = kPlain ? rcX[sl][ty][0] : df_add_f(rcX[sl][ty][0], rcD[sl][ty][0]);
-                else
-                    nl = kPlain ? rcX[sl][ty][0]
-                                : df_add_f(rcX[sl][ty][0], __high2float(rcD[sl][ty][0]));
-            }
-            if (xr) {
-                if constexpr (sizeof(TS) == 4)
-                    nr = kPlain ? rcX[sl][ty][1] : df_add_f(rcX[sl][ty][1], rcD[sl][ty][1]);
-                else
-                    nr = kPlain ? rcX[sl][ty][1]
-                                : df_add_f(rcX[sl][ty][1], __low2float(rcD[sl][ty][1]));
-            }
-        }
-        pl[ty + 1][tx] = vc;
-        if (ty == 0) pl[0][tx] = hlo;
-        if (ty == TY - 1) pl[TY + 1][tx] = hhi;
-        DF left{__shfl_up_sync(0xffffffffu, vc.z, 1), __shfl_up_sync(0xffffffffu, vc.w, 1)};
-        DF right{__shfl_down_sync(0xffffffffu, vc.x, 1), __shfl_down_sync(0xffffffffu, vc.y, 1)};
+    stage(z0, 0);
+    stage(z0 + 1, 1);
+    // one plane: vdn, vc, vup = planes z - 1, z, z + 1; j = (z - z0) % 3 (its ring slot and
+    // plane buffer).  After the stencil vdn takes plane z + 2 from the ring.
+    auto step = [&](const int z, const int j, float4 &vdn, const float4 &vc, const float4 &vup) {
+        stage(z + RS - 1, (j + RS - 1) % RS);     // into the slot step z - 1 read
+        const int kz = kxy + z * g.nxy;
+        pl[j][ty + 1][tx] = vc;
+        if (ty == 0) pl[j][0][tx] = hlo;
+        if (ty == TY - 1) pl[j][TY + 1][tx] = hhi;
+        // cell x - 1 is the second cell of the pair to the left, x + 2 the first of the
+        // pair to the right
+        DF left{__shfl_up_sync(0xffffffffu, vc.y, 1), __shfl_up_sync(0xffffffffu, vc.w, 1)};
+        DF right{__shfl_down_sync(0xffffffffu, vc.x, 1), __shfl_down_sync(0xffffffffu, vc.z, 1)};
         if (tx == 0) left = hl;
         if (x == xlast) right = hr;
         __syncthreads();
         if (own) {
-            const float4 up = pl[ty][tx], dn = pl[ty + 2][tx];
-            const int nz_ = (z > 0) + (z + 1 < g.nz);
-            const DF v0 = lo_df(vc), v1 = hi_df(vc);
-            DF s0 = left;
-            s0 += v1;
-            s0 += lo_df(up);
-            s0 += lo_df(dn);
-            s0 += lo_df(vdn);
-            s0 += lo_df(vup);
-            DF s1 = v0;
-            s1 += right;
-            s1 += hi_df(up);
-            s1 += hi_df(dn);
-            s1 += hi_df(vdn);
-            s1 += hi_df(vup);
-            float rf0, rf1;
-            const DF l0 = df_lap(s0, v0, (float)(n0 + nz_));
-            const DF l1 = df_lap(s1, v1, (float)(n1 + nz_));
+            const DF2 V = df2_of(vc);
+            float2 nn = nn_mid, nnn = nnn_mid;
+            if (z == 0 || z + 1 == g.nz) {   // a z wall: fewer neighbours
+                const int nz_ = (z > 0) + (z + 1 < g.nz);
+                nn = make_float2((float)(n0 + nz_), (float)(n1 + nz_));
+                nnn = make_float2(-nn.x, -nn.y);
+            }
+            // each cell's neighbour sum in the order x - 1, x + 1, y - 1, y + 1, z - 1, z + 1
+            DF2 S{make_float2(left.hi, vc.x), make_float2(left.lo, vc.z)};
+            df2_acc(S, DF2{make_float2(vc.y, right.hi), make_float2(vc.w, right.lo)});
+            df2_acc(S, df2_of(pl[j][ty][tx]));
+            df2_acc(S, df2_of(pl[j][ty + 2][tx]));
+            df2_acc(S, df2_of(vdn));
+            df2_acc(S, df2_of(vup));
+            const DF2 L = df2_lap(S, V, nn, nnn);
             if (kMode == 3) {   // one explicit Euler step: x + c L x
-                XO[kz >> 1] = pack_df(v0 + df_mul(cf.c, l0), v1 + df_mul(cf.c, l1));
+                XO[kz >> 1] = f4_of(df2_add(V, df2_mul(c2, L)));
             } else if (kMode == 0) {
-                rf0 = df_f(df_mul_un(cf.c, l0));
-                rf1 = df_f(df_mul_un(cf.c, l1));
-                DF b0 = v0, b1 = v1;
+                const float2 rf = df2_f(df2_mul_un(c2, L));
+                DF2 B = V;
                 if (scheme == 1) {
-                    b0 = v0 + df_mul(cf.half_c, l0);
-                    b1 = v1 + df_mul(cf.half_c, l1);
-                    BO[kz >> 1] = pack_df(b0, b1);
+                    B = df2_add(V, df2_mul(hc2, L));
+                    BO[kz >> 1] = f4_of(B);
                 }
-                const float f0 = df_f(b0), f1 = df_f(b1);
-                bb = fmaf(f0, f0, fmaf(f1, f1, bb));
-                rr = fmaf(rf0, rf0, fmaf(rf1, rf1, rr));
-                PR::store(r, kz, rf0, rf1);
-                PR::store(y1, kz, gamma * rf0, gamma * rf1);
+                const float2 fb = df2_f(B);
+                bb = fmaf(fb.x, fb.x, fmaf(fb.y, fb.y, bb));
+                rr = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, rr));
+                PR::store(r, kz, rf.x, rf.y);
+                const float2 g1 = mul2(make_float2(gamma, gamma), rf);
+                PR::store(y1, kz, g1.x, g1.y);
             } else {
                 XO[kz >> 1] = vc;
-                rf0 = df_f(df_res(lo_df(bc), v0, cf.ce, l0));
-                rf1 = df_f(df_res(hi_df(bc), v1, cf.ce, l1));
-                rr = fmaf(rf0, rf0, fmaf(rf1, rf1, rr));
+                const float2 rf = df2_f(df2_res(df2_of(bc), V, ce2, L));
+                rr = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, rr));
                 if (kMode == 1) {
-                    PR::store(r, kz, rf0, rf1);
-                    PR::store(y1, kz, gamma * rf0, gamma * rf1);
+                    PR::store(r, kz, rf.x, rf.y);
+                    const float2 g1 = mul2(make_float2(gamma, gamma), rf);
+                    PR::store(y1, kz, g1.x, g1.y);
                 } else {
-                    DF c0 = df_mul(cf.ce, l0), c1 = df_mul(cf.ce, l1);   // theta c L v
-                    DF bn0 = v0, bn1 = v1;
+                    DF2 C = df2_mul(ce2, L);   // theta c L v
+                    DF2 Bn = V;
                     if (scheme == 1) {
-                        bn0 = v0 + c0;
-                        bn1 = v1 + c1;
-                        c0 = c0 + c0;
-                        c1 = c1 + c1;
-                        BO[kz >> 1] = pack_df(bn0, bn1);
+                        Bn = df2_add(V, C);      // v + c/2 L v
+                        C = df2_add(C, C);       // c L v
+                        BO[kz >> 1] = f4_of(Bn);
                     }
-                    const float f0 = df_f(bn0), f1 = df_f(bn1);
-                    bb = fmaf(f0, f0, fmaf(f1, f1, bb));
-                    const float q0 = df_f(c0), q1 = df_f(c1);
-                    PR::store(r, kz, q0, q1);
-                    PR::store(y1, kz, gamma * q0, gamma * q1);
+                    const float2 fb = df2_f(Bn);
+                    bb = fmaf(fb.x, fb.x, fmaf(fb.y, fb.y, bb));
+                    const float2 q = df2_f(C);
+                    PR::store(r, kz, q.x, q.y);
+                    const float2 g1 = mul2(make_float2(gamma, gamma), q);
+                    PR::store(y1, kz, g1.x, g1.y);
                 }
             }
         }
-        __syncthreads();
-        vdn = vc;
-        vc = vup;
-        vup = nup;
-        bc = nb_;
-        hlo = nlo;
-        hhi = nhi;
-        hl = nl;
-        hr = nr;
+        // the next step's planes, staged two steps ago (slot j)
+        cp_async_wait<RS - 1>();
+        if (z + 1 < z1) {
+            if (own) {
+                vdn = f4z();
+                if (z + 2 < g.nz) {
+                    const float4 xv = rX[j][tid];
+                    vdn = kPlain ? xv : pair_add(xv, dpair(rD[j][tid]));
+                }
+                if (!kPlain) bc = rB[j][tid];
+            }
+            if (rowlo || rowhi) {
+                const float4 xv = rhX[j][hrow][tx];
+                const float4 hv = kPlain ? xv : pair_add(xv, dpair(rhD[j][hrow][tx]));
+                if (rowlo) hlo = hv;
+                else hhi = hv;
+            }
+            if (xl) {
+                const float4 pv = rcX[j][ty][0];
+                const DF xv{pv.y, pv.w};
+                if constexpr (sizeof(TS) == 4)
+                    hl = kPlain ? xv : df_add_f(xv, rcD[j][ty][0]);
+                else
+                    hl = kPlain ? xv : df_add_f(xv, __high2float(rcD[j][ty][0]));
+            }
+            if (xr) {
+                const float4 pv = rcX[j][ty][1];
+                const DF xv{pv.x, pv.z};
+                if constexpr (sizeof(TS) == 4)
+                    hr = kPlain ? xv : df_add_f(xv, rcD[j][ty][1]);
+                else
+                    hr = kPlain ? xv : df_add_f(xv, __low2float(rcD[j][ty][1]));
+            }
+        }
+    };
+    static_assert(RS == 3, "the march below is unrolled for three ring slots");
+    for (int z = z0; z < z1; z += RS) {
+        step(z, 0, qa, qb, qc);
+        if (z + 1 < z1) step(z + 1, 1, qb, qc, qa);
+        if (z + 2 < z1) step(z + 2, 2, qc, qa, qb);
     }
     cp_async_wait<0>();   // no copy outlives the block
     if (kMode == 3) return;   // the explicit step reduces nothing
@@ -2771,6 +2881,24 @@ int stencil_grid(int n) {
     return b < cap ? (b < 1 ? 1 : b) : cap;
 }
 
+// The double-float vectors of a mesh are in the pair layout of the two-cells-per-thread
+// refinement kernel when that kernel runs (nx even, no periodic axis but x), else one
+// (hi, lo) per cell.  Conversions of n values (all fields) in the layout of geometry g:
+inline bool df_pairs(const Geo &g) { return g.nx % 2 == 0 && (g.per & ~1) == 0; }
+inline void launch_to_df(const Geo &g, size_t n, const double *u, DF *x, cudaStream_t st) {
+    if (df_pairs(g))
+        k_to_df_pairs<<<stencil_grid((int)(n / 2)), kThreads, 0, st>>>(n / 2, u, reinterpret_cast<float4 *>(x));
+    else
+        k_to_df<<<stencil_grid((int)n), kThreads, 0, st>>>(n, u, x);
+}
+inline void launch_from_df(const Geo &g, size_t n, const DF *x, double *u, cudaStream_t st) {
+    if (df_pairs(g))
+        k_from_df_pairs<<<stencil_grid((int)(n / 2)), kThreads, 0, st>>>(
+            n / 2, reinterpret_cast<const float4 *>(x), u);
+    else
+        k_from_df<<<stencil_grid((int)n), kThreads, 0, st>>>(n, x, u);
+}
+
 // Blocks of a cooperative launch: all must be co-resident (at most 4 per SM here).
 template <class K> int coop_blocks(K kernel) {
     int per_sm = 0;
@@ -3199,7 +3327,7 @@ void launch_refine_df(const Geo &g, const Sweep &sw, int nf, const CoefDF &cf, i
                       float gamma, double *partials, RefScal *sc, RefScal *sc_next,
                       cudaStream_t st) {
     const dim3 blk(TX, TY);
-    if (g.nx % 2 == 0 && (g.per & ~1) == 0) {
+    if (df_pairs(g)) {
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
         launch_chain(k_refine_df2<TS, kMode>, grid, blk, st, g, sw.zlen, sw.nzc, cf,
                      scheme, xin, d, b, xout, bout, r, y1, gamma, partials, sc, sc_next);
@@ -3760,7 +3888,7 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
         const CoefDF cfdf = coefdf(c, c);
         const dim3 grid((g.nx + 2 * TX - 1) / (2 * TX), sw.grid.y, sw.grid.z);
         CGK_LAUNCH("to_double_float", (double)n * nf * 16, st,
-                   k_to_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, cells, A));
+                   launch_to_df(g, (size_t)n * nf, cells, A, st));
         for (int s = 0; s < p->nsteps; ++s) {
             CGK_LAUNCH("explicit_df", (double)n * nf * 16, st,
                        launch_chain(k_refine_df2<float, 3>, grid, blk, st, g, sw.zlen, sw.nzc, cfdf,
@@ -3771,7 +3899,7 @@ static cg_status diffuse_explicit(cg_mesh *m, int nf, double *cells, const cg_pa
             std::swap(A, Bf);
         }
         CGK_LAUNCH("from_double_float", (double)n * nf * 16, st,
-                   k_from_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, A, cells));
+                   launch_from_df(g, (size_t)n * nf, A, cells, st));
         CGK_CUDA(cudaGetLastError());
         CGK_CUDA(cudaStreamSynchronize(st));
         if (rep) {
@@ -3981,8 +4109,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
                     cudaMemsetAsync(hist, 0, hist_n * sizeof(RefScal), cs);
                     if (resident) cudaMemsetAsync(rws + (size_t)rp.nblocks * 4, 0, 4, cs);
                     CGK_LAUNCH("to_double_float", (double)n * nf * 16, cs,
-                               k_to_df<<<stencil_grid(n * nf), kThreads, 0, cs>>>(
-                                   (size_t)n * nf, cells, (DF *)X0));
+                               launch_to_df(g, (size_t)n * nf, cells, (DF *)X0, cs));
                     XT *u = X0, *f1 = X1, *f2 = X2;
                     TS *y1_start = Ya;
                     for (int s2 = 0; s2 < p->nsteps; ++s2) {
@@ -4107,8 +4234,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             }
             if (ok) {
                 CGK_LAUNCH("from_double_float", (double)n * nf * 16, st,
-                           k_from_df<<<stencil_grid(n * nf), kThreads, 0, st>>>(
-                               (size_t)n * nf, (const DF *)result, cells));
+                           launch_from_df(g, (size_t)n * nf, (const DF *)result, cells, st));
                 CGK_CUDA(cudaGetLastError());
                 CGK_CUDA(cudaStreamSynchronize(st));
                 if (rep) {
@@ -4129,8 +4255,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             remembered->rounds = max_r;
             if (last_result) {   // leave the last iterate in place
                 CGK_LAUNCH("from_double_float", (double)n * nf * 16, st,
-                           k_from_df<<<stencil_grid(n * nf), kThreads, 0, st>>>(
-                               (size_t)n * nf, (const DF *)last_result, cells));
+                           launch_from_df(g, (size_t)n * nf, (const DF *)last_result, cells, st));
                 CGK_CUDA(cudaStreamSynchronize(st));
             }
             return fail(CG_ENOCONV, "cg_diffuse: refinement did not reach tol with %d rounds "
@@ -4145,8 +4270,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     XT *ubuf = (XT *)cells;                  // u^n (also b for implicit Euler)
     if (kDF) {
         CGK_LAUNCH("to_double_float", (double)n * nf * 16, st,
-                   k_to_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf, cells,
-                                                                      (DF *)X0));
+                   launch_to_df(g, (size_t)n * nf, cells, (DF *)X0, st));
         ubuf = X0;
     }
     XT *F1 = X1, *F2 = X2;                   // the two buffers not holding u^n
@@ -4279,8 +4403,7 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
     }
     if (kDF)
         CGK_LAUNCH("from_double_float", (double)n * nf * 16, st,
-                   k_from_df<<<stencil_grid(n * nf), kThreads, 0, st>>>((size_t)n * nf,
-                                                                        (const DF *)ubuf, cells));
+                   launch_from_df(g, (size_t)n * nf, (const DF *)ubuf, cells, st));
     else if ((double *)ubuf != cells)
         CGK_CUDA(cudaMemcpyAsync(cells, ubuf, (size_t)n * nf * 8, cudaMemcpyDeviceToDevice, st));
     CGK_CUDA(cudaStreamSynchronize(st));
