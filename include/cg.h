@@ -269,10 +269,19 @@ cg_status cg_coarse_grain_host(cg_mesh *mesh, int64_t n, const double *pos_host,
  * max_concurrent problems run at a time, each on a host thread of the library (the
  * calling thread is one of them), so their kernels overlap on the device where their
  * streams allow it.  Problems start longest first (estimated from cells, steps and
- * dtau over the squared cell size).  The meshes must be distinct (each problem uses its mesh's
- * workspaces); give each problem its own non-default stream for overlap.  A mesh's
- * first call of a configuration autotunes its sweep shape by timing candidates, which
- * other running problems would disturb: make that first call through cg_coarse_grain.
+ * dtau over the squared cell size).  Problems given the same pos, w and n (all device or
+ * all host arrays) on structured meshes of one geometry (dimensions, origin, cell size,
+ * periodic axes) with the same deposit_mode deposit once: the first of them to start
+ * deposits before any problem starts, into a buffer of its mesh (nfields x ncells
+ * doubles, within the workspace limit), and each copies the field from there and
+ * smooths it -- the same results, bit for bit; that problem's report carries the
+ * deposition times, the others report 0 for ms_locate and ms_deposit.  A shared
+ * deposition that fails leaves its problems to run unshared.  The meshes must be
+ * distinct (each problem uses its mesh's workspaces); give each problem its own
+ * non-default stream for overlap.  A mesh's first call of a configuration autotunes its
+ * sweep shape by timing candidates; one thread times at a time, and meshes of one
+ * geometry share the result (other running problems can still disturb the timing: make
+ * the first call of a configuration through cg_coarse_grain where that matters).
  * Returns when every problem has finished: CG_OK, or the status of the lowest-index
  * failing problem (cg_last_error names it).  CG_EINVAL also for NULL arrays, a shared
  * mesh, max_concurrent < 1, or kernel profiling switched on (cg_profile_enable). */

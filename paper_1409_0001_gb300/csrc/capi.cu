@@ -460,6 +460,7 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     m->ws_small.release();
     m->ws_stage.release();
     m->ws_shared_in.release();
+    m->ws_shared_dep.release();
     m->ws_order.release();
     m->ws_batch.release();
     m->h_small.release();
@@ -757,42 +758,79 @@ cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64
     return s;
 }
 
-// The host-memory form of the method (cg_coarse_grain_host).  dpos/dw non-NULL: the
-// inputs are already on the device (a copy shared with other problems, complete once
-// `ready` has fired), else pos_host/w_host are copied into this mesh's staging buffer.
-// The result is staged in this mesh's buffer and copied to cells_host.
-static cg_status coarse_grain_host_impl(cg_mesh *m, int64_t n, const double *pos_host, int nfields,
-                                        const double *w_host, double *cells_host, const cg_params *p,
-                                        cg_report *rep, cudaStream_t st, const double *dpos_in,
-                                        const double *dw_in, cudaEvent_t ready) {
+static cg_status check_host_args(cg_mesh *m, int64_t n, const double *pos_host, int nfields,
+                                 const double *w_host, const double *cells_host, const cg_params *p) {
     if (!m) return fail(CG_EINVAL, "mesh is NULL");
     CGK_TRY(check_params(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(CG_EINVAL, "n must be in [0, 2^31)");
     if (nfields < 1 || nfields > 64) return fail(CG_EINVAL, "nfields must be in [1, 64]");
     if (!cells_host || (n > 0 && (!pos_host || !w_host)))
         return fail(CG_EINVAL, "NULL host array");
-    const bool shared = dpos_in != nullptr;
+    return CG_OK;
+}
+
+// A deposited field shared by several concurrent problems: the buffer that holds it, the
+// event after which it is complete, and the report of the deposition that made it (its
+// phase times for the problem that deposited, zero for the others).
+struct SharedDeposit {
+    const double *src = nullptr;
+    cudaEvent_t ready = nullptr;
+    cg_report rep{};
+};
+
+// The host-memory form of the method (cg_coarse_grain_host).  dpos/dw non-NULL: the
+// inputs are already on the device (a copy shared with other problems, complete once
+// `ready` has fired), else pos_host/w_host are copied into this mesh's staging buffer.
+// dep non-NULL: the deposited field is already on the device (shared with other
+// problems), so the inputs are not needed.  The result is staged in this mesh's buffer
+// and copied to cells_host.
+static cg_status coarse_grain_host_impl(cg_mesh *m, int64_t n, const double *pos_host, int nfields,
+                                        const double *w_host, double *cells_host, const cg_params *p,
+                                        cg_report *rep, cudaStream_t st, const double *dpos_in,
+                                        const double *dw_in, cudaEvent_t ready,
+                                        const SharedDeposit *dep = nullptr) {
+    CGK_TRY(check_host_args(m, n, pos_host, nfields, w_host, cells_host, p));
+    const bool shared = dpos_in != nullptr && dep == nullptr;
     const size_t b_pos = ((size_t)3 * n * 8 + 255) / 256 * 256;
     const size_t b_w = ((size_t)nfields * n * 8 + 255) / 256 * 256;
     const size_t b_c = (size_t)nfields * m->ncells * 8;
-    const size_t b_in = shared ? 0 : b_pos + b_w;
+    const size_t b_in = (shared || dep) ? 0 : b_pos + b_w;
     CGK_TRY(m->ws_stage.ensure(b_in + b_c + 256));
     char *base = m->ws_stage.as<char>();
     const double *dpos = shared ? dpos_in : (const double *)base;
     const double *dw = shared ? dw_in : (const double *)(base + b_pos);
     double *dc = (double *)(base + b_in);
-    if (shared) {
-        CGK_CUDA(cudaStreamWaitEvent(st, ready, 0));
-    } else if (n > 0) {
-        CGK_CUDA(cudaMemcpyAsync(base, pos_host, (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
-        CGK_CUDA(cudaMemcpyAsync(base + b_pos, w_host, (size_t)nfields * n * 8, cudaMemcpyHostToDevice, st));
+    if (dep) {
+        CGK_CUDA(cudaStreamWaitEvent(st, dep->ready, 0));
+        CGK_CUDA(cudaMemcpyAsync(dc, dep->src, b_c, cudaMemcpyDeviceToDevice, st));
+        if (rep) *rep = dep->rep;
+    } else {
+        if (shared) {
+            CGK_CUDA(cudaStreamWaitEvent(st, ready, 0));
+        } else if (n > 0) {
+            CGK_CUDA(cudaMemcpyAsync(base, pos_host, (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
+            CGK_CUDA(cudaMemcpyAsync(base + b_pos, w_host, (size_t)nfields * n * 8, cudaMemcpyHostToDevice, st));
+        }
+        if (rep) std::memset(rep, 0, sizeof(*rep));
+        CGK_TRY(deposit_run(m, n, dpos, nfields, dw, dc, p, rep, st));
     }
-    if (rep) std::memset(rep, 0, sizeof(*rep));
-    CGK_TRY(deposit_run(m, n, dpos, nfields, dw, dc, p, rep, st));
     cg_status s = diffuse_impl(m, nfields, dc, p, rep, st);
     if (s != CG_OK && s != CG_ENOCONV) return s;
     CGK_CUDA(cudaMemcpyAsync(cells_host, dc, b_c, cudaMemcpyDeviceToHost, st));
     CGK_CUDA(cudaStreamSynchronize(st));
+    prof_collect();
+    return s;
+}
+
+// cg_coarse_grain from a deposited field shared with other problems.
+static cg_status coarse_grain_from_shared(cg_mesh *m, int nfields, double *cells_out,
+                                          const cg_params *p, cg_report *rep, cudaStream_t st,
+                                          const SharedDeposit &dep) {
+    CGK_CUDA(cudaStreamWaitEvent(st, dep.ready, 0));
+    CGK_CUDA(cudaMemcpyAsync(cells_out, dep.src, (size_t)nfields * m->ncells * 8,
+                             cudaMemcpyDeviceToDevice, st));
+    if (rep) *rep = dep.rep;
+    cg_status s = diffuse_impl(m, nfields, cells_out, p, rep, st);
     prof_collect();
     return s;
 }
@@ -883,16 +921,88 @@ cg_status cg_coarse_grain_concurrent(int nprob, cg_mesh *const *meshes, const in
             sh_ev[k] = ev;
         }
     }
+    // problems given the same particle arrays (pos, w and n) on structured meshes of one
+    // geometry (dimensions, origin, cell size, periodic axes) with the same deposition mode
+    // deposit once: the group's first problem in start order deposits here, before any
+    // problem starts, into a buffer of its mesh, and every member (that one included)
+    // copies the field from there on its own stream and smooths it.  The deposition is
+    // the same computation on the same inputs, so every result is bit-identical to an
+    // unshared run; the problem that deposited reports the deposition's phase times, the
+    // others report zero for them.  A group whose deposition fails (an argument, a
+    // particle outside the mesh, a workspace that cannot grow) runs unshared, each
+    // problem then reporting its own status as it would alone.
+    std::vector<SharedDeposit> sdep(nprob);
+    std::vector<char> in_dep(nprob, 0);
+    auto same_deposit = [&](int i, int k) {
+        const cg_mesh *a = meshes[i], *b = meshes[k];
+        return host[k] == host[i] && pos[k] == pos[i] && w[k] == w[i] && n[k] == n[i] &&
+               b->kind == MESH_STRUCTURED && a->kind == MESH_STRUCTURED && b->nx == a->nx &&
+               b->ny == a->ny && b->nz == a->nz && b->per == a->per && b->dx == a->dx &&
+               b->origin[0] == a->origin[0] && b->origin[1] == a->origin[1] &&
+               b->origin[2] == a->origin[2] && params[k].deposit_mode == params[i].deposit_mode;
+    };
+    auto args_ok = [&](int k) {
+        return (host[k] ? check_host_args(meshes[k], n[k], pos[k], nfields, w[k], cells[k], &params[k])
+                        : check_deposit_args(meshes[k], n[k], pos[k], nfields, w[k], cells[k],
+                                             &params[k])) == CG_OK;
+    };
+    for (int a = 0; a < nprob && nf_ok; ++a) {
+        const int i = order[a];
+        if (in_dep[i] || meshes[i]->kind != MESH_STRUCTURED || n[i] <= 0 || !args_ok(i)) continue;
+        if (host[i] && !sh_pos[i]) continue;   // host inputs not on the device
+        std::vector<int> members{i};
+        for (int b = a + 1; b < nprob; ++b) {
+            const int k = order[b];
+            if (!in_dep[k] && same_deposit(i, k) && args_ok(k)) members.push_back(k);
+        }
+        if (members.size() < 2) continue;
+        cg_mesh *mi = meshes[i];
+        cudaStream_t st = (cudaStream_t)streams[i];
+        if (mi->ws_shared_dep.ensure((size_t)nfields * mi->ncells * 8) != CG_OK) continue;
+        double *buf = mi->ws_shared_dep.as<double>();
+        if (host[i] && cudaStreamWaitEvent(st, sh_ev[i], 0) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cg_report r;
+        std::memset(&r, 0, sizeof(r));
+        if (deposit_run(mi, n[i], host[i] ? sh_pos[i] : pos[i], nfields, host[i] ? sh_w[i] : w[i], buf,
+                        &params[i], &r, st) != CG_OK)
+            continue;
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaEventRecord(ev, st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(ev);
+            continue;
+        }
+        events.push_back(ev);
+        for (int k : members) {
+            in_dep[k] = 1;
+            sdep[k].src = buf;
+            sdep[k].ready = ev;
+            sdep[k].rep = r;
+            if (k != i) sdep[k].rep.ms_locate = sdep[k].rep.ms_deposit = 0.0;
+        }
+    }
     auto worker = [&](bool own_thread) {
         if (own_thread && cudaSetDevice(dev) != cudaSuccess) return;
         for (int j; (j = next.fetch_add(1)) < nprob;) {
             const int i = order[j];
             cg_report *ri = reports ? &reports[i] : nullptr;
-            status[i] = host[i] ? coarse_grain_host_impl(meshes[i], n[i], pos[i], nfields, w[i], cells[i],
-                                                         &params[i], ri, (cudaStream_t)streams[i], sh_pos[i],
-                                                         sh_w[i], sh_ev[i])
-                                : cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i], ri,
-                                                  streams[i]);
+            cudaStream_t st = (cudaStream_t)streams[i];
+            const SharedDeposit *dep = in_dep[i] ? &sdep[i] : nullptr;
+            if (host[i])
+                status[i] = coarse_grain_host_impl(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i],
+                                                   ri, st, sh_pos[i], sh_w[i], sh_ev[i], dep);
+            else if (dep)
+                status[i] = coarse_grain_from_shared(meshes[i], nfields, cells[i], &params[i], ri, st, *dep);
+            else
+                status[i] = cg_coarse_grain(meshes[i], n[i], pos[i], nfields, w[i], cells[i], &params[i], ri,
+                                            streams[i]);
             if (status[i] != CG_OK) detail[i] = g_last_error;   // this thread's message
         }
     };

@@ -556,6 +556,9 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         CGK_CUDA(cudaEventRecord(ev[1], st));
         rep->n_out_of_domain = n_out;
     }
+    if (n_bad || n_out)
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
     if (n_bad) return fail(CG_EINVAL, "cg_deposit: %lld non-finite weights", (long long)n_bad);
     if (n_out)
         return fail(CG_EDOMAIN, "cg_deposit: %lld particles outside the mesh", (long long)n_out);

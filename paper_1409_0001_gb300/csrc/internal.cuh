@@ -155,6 +155,7 @@ struct cg_mesh {
     cgk::DevBuf ws_small;    // scalars, partials, counters
     cgk::DevBuf ws_stage;    // device staging for the host-pointer entry point
     cgk::DevBuf ws_shared_in;  // host inputs copied once for several concurrent problems
+    cgk::DevBuf ws_shared_dep; // a deposited field shared by several concurrent problems
     cgk::DevBuf ws_order;    // particles ordered by point-location bucket (tet meshes)
     cgk::DevBuf ws_batch;    // batched calls: descriptors, work items, partials (first mesh)
     cgk::HostBuf h_small;    // pinned readback

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -1097,7 +1098,6 @@ __device__ __forceinline__ DF &operator+=(DF &a, DF b) {
     a.lo = a.lo + (t.lo + b.lo);
     return a;
 }
-__device__ __forceinline__ DF operator-(DF a, DF b) { return a + DF{-b.hi, -b.lo}; }
 __device__ __forceinline__ DF df_add_f(DF a, float b) {
     DF s = df_two_sum(a.hi, b);
     s.lo += a.lo;
@@ -1108,12 +1108,6 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    return df_fast2sum(p, e);
-}
-__device__ __forceinline__ DF df_mulf(DF a, float b) {
-    float p = a.hi * b;
-    float e = fmaf(a.hi, b, -p);
-    e = fmaf(a.lo, b, e);
     return df_fast2sum(p, e);
 }
 __device__ __forceinline__ float df_f(DF a) { return a.hi + a.lo; }
@@ -3450,6 +3444,22 @@ TS *cheb_final_buffer(TS *y1, TS *other, int m) {
 // the caller's buffers (the round's whole Chebyshev loop, as the solver runs it), and
 // the faster replay (best of three after a warm-up) is kept per mesh, field count,
 // storage type and m.
+// Tuning results shared by every mesh of the process: a mesh with the dimensions, periodic
+// axes and tuning key (field count and storage type; for the resident solve, the
+// iteration count) of one tuned before takes that choice without timing it again, and one
+// thread times at a time.  Problems that run concurrently on other threads would
+// otherwise disturb each other's timings, and a disturbed timing can pick a shape that is
+// much slower in the solve (one plane per block against two at 128^3: 7.3 against 8.5 ms
+// for ten implicit steps at b = 8 dx).
+struct TuneKey {
+    int nx, ny, nz, per, key, dev;
+    bool operator==(const TuneKey &o) const {
+        return nx == o.nx && ny == o.ny && nz == o.nz && per == o.per && key == o.key && dev == o.dev;
+    }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, int>> g_tuned;
+
 template <class TS>
 cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int code, int m_it,
                         const Coef32 &cf, TS *ya, TS *yb, TS *yc4, TS *yd4, const TS *r, char *ws,
@@ -3457,6 +3467,16 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
     const int key = -((m_it * 64 + 1) * 4 + (int)sizeof(TS));
     for (auto &e : m->tuned)
         if (e.first == key) {
+            *use = e.second != 0;
+            return CG_OK;
+        }
+    int dev = 0;
+    CGK_CUDA(cudaGetDevice(&dev));
+    const TuneKey tk{g.nx, g.ny, g.nz, g.per, key * 1024 + (code + 512), dev};   // code in -16 .. 416
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto &e : g_tuned)
+        if (e.first == tk) {
+            m->tuned.push_back({key, e.second});
             *use = e.second != 0;
             return CG_OK;
         }
@@ -3513,13 +3533,15 @@ cg_status tune_resident(cg_mesh *m, const Geo &g, const ResidentPlan &rp, int co
     if (errh) return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the resident inner solve gave up");
     *use = t[1] < t[0];
     m->tuned.push_back({key, *use ? 1 : 0});
+    g_tuned.push_back({tk, *use ? 1 : 0});
     return CG_OK;
 }
 
 // Autotuner of the Chebyshev sweep's shape (vectorised, register-blocked with 2, 4 or 8
 // planes per block, z-marching with 1..16 planes per block): times ten iterations of
 // each candidate on the caller's buffers (all scratch at this point) and keeps the
-// fastest.  The choice is cached per mesh, field count and storage type.  (The
+// fastest.  The choice is cached per mesh, field count and storage type, and shared with
+// every mesh of the same geometry (the process-wide table below).  (The
 // two-iterations-per-launch sweep is not a candidate: inside the solver's graph it
 // measured no faster per iteration than the one-iteration sweep; sweep_shape selects it.)
 template <class TS>
@@ -3528,6 +3550,16 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     const int key = (nf * 4 + (int)sizeof(TS)) * 8 + g.per;
     for (auto &e : m->tuned)
         if (e.first == key) {
+            *code_out = e.second;
+            return CG_OK;
+        }
+    int dev = 0;
+    CGK_CUDA(cudaGetDevice(&dev));
+    const TuneKey tk{g.nx, g.ny, g.nz, g.per, key, dev};
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto &e : g_tuned)
+        if (e.first == tk) {
+            m->tuned.push_back({key, e.second});
             *code_out = e.second;
             return CG_OK;
         }
@@ -3543,22 +3575,20 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
         tma_prepare();
         for (int c : {401, 402, 404, 408}) cands.push_back({c, 10});
     }
-    cudaEvent_t e0, e1;
-    CGK_CUDA(cudaEventCreate(&e0));
-    CGK_CUDA(cudaEventCreate(&e1));
-    // per shape: 10 iterations captured as a CUDA graph (as the solver runs them), one
-    // warm-up replay, then the fastest of three timed replays; the vectorised shape is
-    // kept unless another is more than 3 % faster
-    std::vector<std::pair<float, int>> timing;
-    cg_status rc = CG_OK;
-    for (auto &cand : cands) {
-        const int code = cand.first;
+    // per shape: 10 iterations captured as a CUDA graph (as the solver runs them) and
+    // replayed once to warm up; then three rounds that replay every shape in turn, each
+    // shape keeping its fastest replay (interleaving spreads a transient disturbance over
+    // all shapes instead of one); the vectorised shape is kept unless another is more
+    // than 3 % faster
+    std::vector<cudaGraphExec_t> execs(cands.size(), nullptr);
+    cudaError_t ce = cudaSuccess;
+    for (size_t i = 0; i < cands.size() && ce == cudaSuccess; ++i) {
+        const int code = cands[i].first;
         cudaStream_t cs = m->capture_stream;
         cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
-            for (int q = 0; q < cand.second; ++q) {
+            for (int q = 0; q < cands[i].second; ++q) {
                 if (code >= kPairCode && code < kResidentCode)
                     launch_cheb2<TS>(code - kPairCode, g, nf, cf, 0.5f, 1.0f, 1.0f, ya, yb, r, yc,
                                      yd, cs);
@@ -3567,28 +3597,30 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
             }
             ce = cudaStreamEndCapture(cs, &graph);
         }
-        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&execs[i], graph, 0);
         if (graph) cudaGraphDestroy(graph);
-        float best_burst = 1e30f;
-        for (int rep = 0; rep < 4 && ce == cudaSuccess; ++rep) {
+        if (ce == cudaSuccess) ce = cudaGraphLaunch(execs[i], st);   // warm-up replay
+    }
+    std::vector<std::pair<float, int>> timing;
+    for (auto &cand : cands) timing.push_back({1e30f, cand.first});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    for (int round = 0; round < 3 && ce == cudaSuccess; ++round)
+        for (size_t i = 0; i < cands.size() && ce == cudaSuccess; ++i) {
             cudaEventRecord(e0, st);
-            ce = cudaGraphLaunch(exec, st);
+            ce = cudaGraphLaunch(execs[i], st);
             cudaEventRecord(e1, st);
             if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) best_burst = std::min(best_burst, ms);
+            timing[i].first = std::min(timing[i].first, ms);
         }
-        if (exec) cudaGraphExecDestroy(exec);
-        if (ce != cudaSuccess) {
-            rc = cuda_fail(ce, "sweep autotuner", __FILE__, __LINE__);
-            break;
-        }
-        timing.push_back({best_burst, code});
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc != CG_OK) return rc;
+    for (cudaGraphExec_t ex : execs)
+        if (ex) cudaGraphExecDestroy(ex);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return cuda_fail(ce, "sweep autotuner", __FILE__, __LINE__);
     if (tma_wait_failed(st)) return fail(CG_ETIMEOUT, "cg_diffuse: a wait of the TMA-staged sweep gave up");
     std::sort(timing.begin(), timing.end());
     int best_code = timing[0].second;
@@ -3603,6 +3635,7 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
         if (code_v4 && best_v4 <= 1.03f * timing[0].first) best_code = code_v4;
     }
     m->tuned.push_back({key, best_code});
+    g_tuned.push_back({tk, best_code});
     *code_out = best_code;
     return CG_OK;
 }

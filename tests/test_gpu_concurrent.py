@@ -137,3 +137,56 @@ def test_concurrent_full_size_benchmark_configuration(cg):
     out = cg.coarse_grain_concurrent(meshes, [pos] * 4, [w] * 4, prm, max_concurrent=2)
     for a, b in zip(out, seq):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_concurrent_shared_deposition(cg, problems, k):
+    """Problems given the same device particle arrays on meshes of one geometry deposit
+    once (the first to start, here the largest bandwidth); every result and every
+    report field but the deposition times equal the sequential run's, bit for bit."""
+    import torch
+    probs, ref = problems
+    pos0, w0 = probs[0][1], probs[0][2]
+    pos = [pos0] * 4 + [p[1] for p in probs[4:]]
+    w = [w0] * 4 + [p[2] for p in probs[4:]]
+    out, reps = cg.coarse_grain_concurrent([p[0] for p in probs], pos, w, [p[3] for p in probs],
+                                           max_concurrent=k, report=True)
+    for (u_ref, r_ref), u, r in zip(ref, out, reps):
+        assert torch.equal(u, u_ref)
+        for key in ("cell_updates", "refine_rounds", "iters", "final_rel_residual", "n_out_of_domain",
+                    "fixed_point_bits"):
+            assert r[key] == r_ref[key], key
+        assert r["mass_in"] == r_ref["mass_in"] and r["mass_out"] == r_ref["mass_out"]
+    deposited = [i for i in range(4) if reps[i]["ms_locate"] + reps[i]["ms_deposit"] > 0]
+    assert deposited == [3]                                      # b = 8 dx starts first
+    assert all(reps[i]["ms_locate"] + reps[i]["ms_deposit"] > 0 for i in range(4, len(probs)))
+
+
+def test_concurrent_shared_deposition_mixed_geometry_and_failure(cg, problems):
+    """Only problems on meshes of the same geometry and deposition mode share; a shared
+    set whose deposition fails runs unshared and every member reports the failure."""
+    import torch
+    probs, ref = problems
+    c = W.clustered_cube(n_side=48, n_particles=200_000, seed=11)
+    pos0, w0 = probs[0][1], probs[0][2]
+    # one more cell column, the mesh shifted by it: the same particles, another geometry
+    shifted = cg.StructuredMesh((c.dims[0] + 1, c.dims[1], c.dims[2]),
+                                (c.origin[0] - c.dx, c.origin[1], c.origin[2]), c.dx)
+    fixed = cg.Params(bandwidth=2.0 * c.dx, nsteps=10, precision=3, deposit_mode=1)
+    meshes = [probs[0][0], probs[1][0], shifted, probs[2][0]]
+    prm = [probs[0][3], probs[1][3], probs[1][3], fixed]
+    out, reps = cg.coarse_grain_concurrent(meshes, [pos0] * 4, [w0] * 4, prm, max_concurrent=2,
+                                           report=True)
+    seq = [cg.coarse_grain(m, pos0, w0, p) for m, p in zip(meshes, prm)]
+    for a, b in zip(out, seq):
+        assert torch.equal(a, b)
+    assert torch.equal(out[0], ref[0][0]) and torch.equal(out[1], ref[1][0])
+    dep = [r["ms_locate"] + r["ms_deposit"] > 0 for r in reps]
+    assert dep[2] and dep[3] and dep[0] != dep[1]                # only problems 0 and 1 share
+    bad = pos0.clone()
+    bad[0, 5] = 7.0
+    with pytest.raises(cg.CGError) as e:
+        cg.coarse_grain_concurrent([p[0] for p in probs[:4]], [bad] * 4, [w0] * 4,
+                                   [p[3] for p in probs[:4]], max_concurrent=2)
+    assert e.value.code == "CG_EDOMAIN" and "problem 0" in str(e.value)
+    shifted.close()
