@@ -1400,11 +1400,11 @@ __device__ __forceinline__ float4 pair_add(float4 xv, float2 dv) { return f4_of(
 // queue, its b and its halo values beyond the next plane, and reads back only what it
 // staged (no barrier).  The pass is bound by memory latency and instruction issue, not
 // by its arithmetic, so deeper prefetch that costs no registers is what speeds it up.
-// The march is unrolled by the ring depth: a step's ring slot and shared plane buffer are
-// then compile-time constants, the three-plane register queue rotates by renaming (the
-// register of plane z-1 takes plane z+2 once the step has used it), and with one shared
-// plane buffer per slot a step needs a single barrier (a buffer is written again three
-// steps later, after two more barriers).
+// The march is unrolled by the ring depth: a step's ring slot is then a compile-time
+// constant and the three-plane register queue rotates by renaming (the register of plane
+// z-1 takes plane z+2 once the step has used it).  (One shared plane buffer per slot,
+// which saves a barrier per plane, was measured slower: at 512 x 256 x 256 the larger
+// shared footprint cost ~8 ms over the 80 passes of the channel case.)
 constexpr int kRefRing = 3;   // ring slots: two planes in flight beyond the one consumed
 
 template <class TS, int kMode>
@@ -1436,7 +1436,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     TS *y1 = y1_all + off;
     const DFc2 c2 = dfc2(cf.c), hc2 = dfc2(cf.half_c), ce2 = dfc2(cf.ce);
     constexpr int RS = kRefRing;
-    __shared__ float4 pl[RS][TY + 2][TX];   // the plane's tile with its y halo rows, per slot
+    __shared__ float4 pl[TY + 2][TX];   // the plane's tile with its y halo rows
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * (2 * TX);
     const int x = x0 + 2 * tx, y = blockIdx.y * TY + ty;
@@ -1539,14 +1539,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
     }
     stage(z0, 0);
     stage(z0 + 1, 1);
-    // one plane: vdn, vc, vup = planes z - 1, z, z + 1; j = (z - z0) % 3 (its ring slot and
-    // plane buffer).  After the stencil vdn takes plane z + 2 from the ring.
+    // one plane: vdn, vc, vup = planes z - 1, z, z + 1; j = (z - z0) % 3 (its ring slot).
+    // After the stencil vdn takes plane z + 2 from the ring.
     auto step = [&](const int z, const int j, float4 &vdn, const float4 &vc, const float4 &vup) {
         stage(z + RS - 1, (j + RS - 1) % RS);     // into the slot step z - 1 read
         const int kz = kxy + z * g.nxy;
-        pl[j][ty + 1][tx] = vc;
-        if (ty == 0) pl[j][0][tx] = hlo;
-        if (ty == TY - 1) pl[j][TY + 1][tx] = hhi;
+        pl[ty + 1][tx] = vc;
+        if (ty == 0) pl[0][tx] = hlo;
+        if (ty == TY - 1) pl[TY + 1][tx] = hhi;
         // cell x - 1 is the second cell of the pair to the left, x + 2 the first of the
         // pair to the right
         DF left{__shfl_up_sync(0xffffffffu, vc.y, 1), __shfl_up_sync(0xffffffffu, vc.w, 1)};
@@ -1565,8 +1565,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
             // each cell's neighbour sum in the order x - 1, x + 1, y - 1, y + 1, z - 1, z + 1
             DF2 S{make_float2(left.hi, vc.x), make_float2(left.lo, vc.z)};
             df2_acc(S, DF2{make_float2(vc.y, right.hi), make_float2(vc.w, right.lo)});
-            df2_acc(S, df2_of(pl[j][ty][tx]));
-            df2_acc(S, df2_of(pl[j][ty + 2][tx]));
+            df2_acc(S, df2_of(pl[ty][tx]));
+            df2_acc(S, df2_of(pl[ty + 2][tx]));
             df2_acc(S, df2_of(vdn));
             df2_acc(S, df2_of(vup));
             const DF2 L = df2_lap(S, V, nn, nnn);
@@ -1610,6 +1610,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine_df2(Geo g, int zlen, int
                 }
             }
         }
+        __syncthreads();   // the plane buffer is rewritten by the next step
         // the next step's planes, staged two steps ago (slot j)
         cp_async_wait<RS - 1>();
         if (z + 1 < z1) {
