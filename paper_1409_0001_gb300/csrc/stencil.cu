@@ -222,9 +222,14 @@ constexpr int kFlatMaxNx = 512;
 constexpr int kFlatCpt = 4;     // cells per thread of the FP32 / BF16 sweeps
 constexpr int kFlatCptDF = 2;   // ... of the double-float refinement passes
 
-template <class T, int CPT, class Produce, class Pre, class Consume>
-__device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, int z1,
-                                              Produce produce, Pre pre, Consume consume) {
+//
+// load(k) returns a cell's raw operands and finish(raw) its stencil value: the loads for
+// plane z+1 are issued before plane z is computed, and finish() runs after it, so the
+// arithmetic that turns them into values (a double-float sum of the iterate and its
+// correction) does not wait on the loads in front of the plane's work.
+template <class T, int CPT, class Load, class Finish, class Pre, class Consume>
+__device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, int z1, Load load,
+                                              Finish finish, Pre pre, Consume consume) {
     constexpr int kFlatCells = CPT * kThreads;
     __shared__ T sp[kFlatCells + 2 * kFlatMaxNx];
     const int t = threadIdx.y * TX + threadIdx.x;
@@ -254,6 +259,8 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         hh[j] = hi0 + t + kThreads * j < hi1;
     }
     using P = decltype(pre(0));
+    using RAW = decltype(load(0));
+    auto produce = [&](int k) { return finish(load(k)); };
     T vdn[CPT], vc[CPT], vup[CPT], ha[2], hb[2];
     P pt[CPT];
 #pragma unroll
@@ -288,17 +295,17 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
     // segment slot of cell q: q - q0 + nx
     for (int z = z0; z < z1; ++z) {
         const int kz = z * nxy;
-        T nup[CPT], na[2], nbv[2];
+        RAW nup[CPT], na[2], nbv[2];   // raw operands of plane z+1's (z+2's) values
         P npt[CPT];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
-            nup[j] = T();
+            nup[j] = RAW{};
             npt[j] = P{};
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            na[j] = T();
-            nbv[j] = T();
+            na[j] = RAW{};
+            nbv[j] = RAW{};
         }
         if (z + 1 < z1) {
             const int kn = kz + nxy;
@@ -306,13 +313,13 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
             for (int j = 0; j < CPT; ++j)
                 if (own[j]) {
                     const int k = kn + q0 + t + kThreads * j;
-                    if (z + 2 < g.nz) nup[j] = produce(k + nxy);
+                    if (z + 2 < g.nz) nup[j] = load(k + nxy);
                     npt[j] = pre(k);
                 }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                if (hl[j]) na[j] = produce(kn + lo0 + t + kThreads * j);
-                if (hh[j]) nbv[j] = produce(kn + hi0 + t + kThreads * j);
+                if (hl[j]) na[j] = load(kn + lo0 + t + kThreads * j);
+                if (hh[j]) nbv[j] = load(kn + hi0 + t + kThreads * j);
             }
         }
 #pragma unroll
@@ -342,13 +349,13 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         for (int j = 0; j < CPT; ++j) {
             vdn[j] = vc[j];
             vc[j] = vup[j];
-            vup[j] = nup[j];
+            vup[j] = finish(nup[j]);   // a zero operand set finishes to a zero value
             pt[j] = npt[j];
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            ha[j] = na[j];
-            hb[j] = nbv[j];
+            ha[j] = finish(na[j]);
+            hb[j] = finish(nbv[j]);
         }
     }
 }
@@ -1158,6 +1165,10 @@ struct CoefDF {
 // (p - c a is exact, so it equals -(c a - p) without rounding).
 struct DF2 {
     float2 hi, lo;
+};
+struct DFd {    // a double-float iterate and its FP32 correction, not yet added
+    DF x;
+    float d;
 };
 struct DF2n {   // the pair value hi - nlo (a product with its error carried negated)
     float2 hi, nlo;
@@ -2620,17 +2631,18 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     TS *y1 = d.Ya + off;
     // the flat-plane engine or the 2.5D tile engine (the same arithmetic per cell)
     const bool flat = d.flat != 0;
-    auto engine = [&](auto produce, auto pre, auto consume) {
+    auto engine = [&](auto load, auto finish, auto pre, auto consume) {
         if (flat)
-            sweep_flat_at<DF, kFlatCptDF>(g, it.bx, z0, z1, produce, pre, consume);
+            sweep_flat_at<DF, kFlatCptDF>(g, it.bx, z0, z1, load, finish, pre, consume);
         else
-            sweep25_at<DF>(g, it.bx, it.by, z0, z1, produce, pre, consume);
+            sweep25_at<DF>(g, it.bx, it.by, z0, z1, [&](int k) { return finish(load(k)); }, pre,
+                           consume);
     };
     if (first) {
         const DF *u = d.U + off;
         DF *bo = d.B + off;
         engine(
-            [&](int k) { return bld_df<COH>(u, k); }, [](int) { return NoPre{}; },
+            [&](int k) { return bld_df<COH>(u, k); }, [](DF v) { return v; }, [](int) { return NoPre{}; },
             [&](int k, DF v, DF sm, int nn, NoPre) {
                 const DF lx = df_lap(sm, v, (float)nn);
                 DF bk = v;
@@ -2652,8 +2664,8 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
         const TS *dd = d.Yb + off;
         const bool next = part_next != nullptr;
         engine(
-            [&](int k) { return df_add_f(bld_df<COH>(xin, k), bld<COH>(dd, k)); },
-            [&](int k) { return bld_df<COH>(b, k); },
+            [&](int k) { return DFd{bld_df<COH>(xin, k), bld<COH>(dd, k)}; },
+            [](DFd v) { return df_add_f(v.x, v.d); }, [&](int k) { return bld_df<COH>(b, k); },
             [&](int k, DF v, DF sm, int nn, DF bk) {
                 xout[k] = v;
                 const DF lx = df_lap(sm, v, (float)nn);
