@@ -118,9 +118,13 @@ __device__ __forceinline__ BlockPos block_pos(const Geo &g, int zlen, int nzc) {
 // so it adds nothing to s, and it is not counted in nn (zero flux).
 struct NoPre {};
 
-template <class T, class Produce, class Pre, class Consume>
-__device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0, int z1,
-                                           Produce produce, Pre pre, Consume consume) {
+// load(k) returns a cell's raw operands and finish(raw) its stencil value; the next
+// plane's operands are loaded before the current plane is computed and finished after it
+// (a double-float sum of iterate and correction does not wait on its loads in front of
+// the plane's work).  sweep25_at below is the form with values that need no finishing.
+template <class T, class Load, class Finish, class Pre, class Consume>
+__device__ __forceinline__ void sweep25_lf(const Geo &g, int bx, int by, int z0, int z1, Load load,
+                                           Finish finish, Pre pre, Consume consume) {
     __shared__ T pl[TY + 2][TX + 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = bx * TX + tx, y = by * TY + ty;
@@ -147,6 +151,8 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
     __syncthreads();
 
     using P = decltype(pre(0));
+    using RAW = decltype(load(0));
+    auto produce = [&](int k) { return finish(load(k)); };
     T vdn = T(), vc = T(), vup = T();               // v(z-1), v(z), v(z+1) of the column
     T hxa = T(), hxb = T(), hya = T(), hyb = T();   // halo values of plane z
     P pt{};                                         // cell-local operands of plane z
@@ -165,19 +171,19 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
     }
     for (int z = z0; z < z1; ++z) {
         const int kz = kxy + z * g.nxy;
-        // loads for the next plane of this block
-        T nup = T(), nxa = T(), nxb = T(), nya = T(), nyb = T();
+        // loads for the next plane of this block (raw operands, finished below)
+        RAW nup{}, nxa{}, nxb{}, nya{}, nyb{};
         P npt{};
         if (z + 1 < z1) {
             const int kn = kz + g.nxy;
             if (own) {
-                if (z + 2 < g.nz || pz) nup = produce(kn + zup(z + 1));
+                if (z + 2 < g.nz || pz) nup = load(kn + zup(z + 1));
                 npt = pre(kn);
             }
-            if (hxl) nxa = produce(kn + dxl);
-            if (hxh) nxb = produce(kn + dxh);
-            if (hyl) nya = produce(kn + dyl);
-            if (hyh) nyb = produce(kn + dyh);
+            if (hxl) nxa = load(kn + dxl);
+            if (hxh) nxb = load(kn + dxh);
+            if (hyl) nya = load(kn + dyl);
+            if (hyh) nyb = load(kn + dyh);
         }
         // publish plane z and update its cells
         if (own) pl[ty + 1][tx + 1] = vc;
@@ -199,13 +205,19 @@ __device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0,
         __syncthreads();
         vdn = vc;
         vc = vup;
-        vup = nup;
+        vup = finish(nup);   // a zero operand set finishes to a zero value
         pt = npt;
-        hxa = nxa;
-        hxb = nxb;
-        hya = nya;
-        hyb = nyb;
+        hxa = finish(nxa);
+        hxb = finish(nxb);
+        hya = finish(nya);
+        hyb = finish(nyb);
     }
+}
+
+template <class T, class Produce, class Pre, class Consume>
+__device__ __forceinline__ void sweep25_at(const Geo &g, int bx, int by, int z0, int z1,
+                                           Produce produce, Pre pre, Consume consume) {
+    sweep25_lf<T>(g, bx, by, z0, z1, produce, [](T v) { return v; }, pre, consume);
 }
 
 // A flat-plane variant of the engine for meshes of short rows (nx <= kFlatMaxNx,
@@ -1334,9 +1346,9 @@ __global__ void __launch_bounds__(kThreads) k_refine_df(Geo g, int zlen, int nzc
         const TS *d = d_all + off;
         const DF *b = b_all + off;
         DF *xout = xout_all + off;
-        sweep25p<DF>(
-            g, bp.z0, bp.z1, [&](int k) { return df_add_f(xin[k], ld(d, k)); },
-            [&](int k) { return b[k]; },
+        sweep25_lf<DF>(
+            g, blockIdx.x, blockIdx.y, bp.z0, bp.z1, [&](int k) { return DFd{xin[k], ld(d, k)}; },
+            [](DFd v) { return df_add_f(v.x, v.d); }, [&](int k) { return b[k]; },
             [&](int k, DF v, DF s, int nn, DF bk) {
                 xout[k] = v;
                 const DF lx = df_lap(s, v, (float)nn);
@@ -2635,8 +2647,7 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
         if (flat)
             sweep_flat_at<DF, kFlatCptDF>(g, it.bx, z0, z1, load, finish, pre, consume);
         else
-            sweep25_at<DF>(g, it.bx, it.by, z0, z1, [&](int k) { return finish(load(k)); }, pre,
-                           consume);
+            sweep25_lf<DF>(g, it.bx, it.by, z0, z1, load, finish, pre, consume);
     };
     if (first) {
         const DF *u = d.U + off;
