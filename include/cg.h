@@ -323,7 +323,11 @@ cg_status cg_diffuse_batched(int nsnap, cg_mesh *const *meshes, int nfields,
 
 /* The whole method for a batch: cg_deposit of snapshot s (n[s] particles, pos[s]
  * device [3][n[s]], w[s] device [nfields][n[s]]) into cells[s], then
- * cg_diffuse_batched. */
+ * cg_diffuse_batched.  Every snapshot's particles are located before any deposited
+ * field is written: a snapshot with particles outside its mesh (CG_EDOMAIN) or
+ * non-finite weights (CG_EINVAL) fails the call with no cells written (cg_last_error
+ * names the first such snapshot).  report: ms_locate and ms_deposit are the device times
+ * of the two phases over the whole batch, n_out_of_domain the batch's total. */
 cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64_t *n,
                                   const double *const *pos, int nfields, const double *const *w,
                                   double *const *cells, const cg_params *params,

@@ -638,12 +638,13 @@ static cg_status batched_diffuse_impl(int nsnap, cg_mesh *const *meshes, int nfi
                        p->scheme != CG_SCHEME_EXPLICIT_EULER;
     double mass_in[CG_REPORT_MAX_FIELDS] = {0}, mass_out[CG_REPORT_MAX_FIELDS] = {0};
     const int nrep = nfields < CG_REPORT_MAX_FIELDS ? nfields : CG_REPORT_MAX_FIELDS;
-    if (rep)
-        for (int s = 0; s < nsnap; ++s) {
-            double mm[CG_REPORT_MAX_FIELDS];
-            CGK_TRY(field_mass(meshes[s], nrep, cells[s], mm, st));
-            for (int f = 0; f < nrep; ++f) mass_in[f] += mm[f];
-        }
+    std::vector<double> mm;   // per snapshot and field, one synchronisation for all
+    if (rep) {
+        mm.resize((size_t)nsnap * nrep);
+        CGK_TRY(field_mass_many(nsnap, meshes, nrep, cells, mm.data(), st));
+        for (int s = 0; s < nsnap; ++s)
+            for (int f = 0; f < nrep; ++f) mass_in[f] += mm[(size_t)s * nrep + f];
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rep) {
         CGK_CUDA(cudaEventCreate(&e0));
@@ -682,13 +683,12 @@ static cg_status batched_diffuse_impl(int nsnap, cg_mesh *const *meshes, int nfi
         rep->ms_diffuse = ms;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (s == CG_OK || s == CG_ENOCONV)
-            for (int q = 0; q < nsnap; ++q) {
-                double mm[CG_REPORT_MAX_FIELDS];
-                cg_status s2 = field_mass(meshes[q], nrep, cells[q], mm, st);
-                if (s2 != CG_OK) return s2;
-                for (int f = 0; f < nrep; ++f) mass_out[f] += mm[f];
-            }
+        if (s == CG_OK || s == CG_ENOCONV) {
+            cg_status s2 = field_mass_many(nsnap, meshes, nrep, cells, mm.data(), st);
+            if (s2 != CG_OK) return s2;
+            for (int q = 0; q < nsnap; ++q)
+                for (int f = 0; f < nrep; ++f) mass_out[f] += mm[(size_t)q * nrep + f];
+        }
         for (int f = 0; f < nrep; ++f) {
             rep->mass_in[f] = mass_in[f];
             rep->mass_out[f] = mass_out[f];
@@ -737,17 +737,9 @@ cg_status cg_coarse_grain_batched(int nsnap, cg_mesh *const *meshes, const int64
     if (!n || !pos || !w) return fail(CG_EINVAL, "NULL particle arrays");
     cudaStream_t st = (cudaStream_t)stream;
     if (rep) std::memset(rep, 0, sizeof(*rep));
-    for (int s = 0; s < nsnap; ++s) {
+    for (int s = 0; s < nsnap; ++s)
         CGK_TRY(check_deposit_args(meshes[s], n[s], pos[s], nfields, w[s], cells[s], p));
-        cg_report one;
-        std::memset(&one, 0, sizeof(one));
-        CGK_TRY(deposit_run(meshes[s], n[s], pos[s], nfields, w[s], cells[s], p, rep ? &one : nullptr, st));
-        if (rep) {
-            rep->ms_locate += one.ms_locate;
-            rep->ms_deposit += one.ms_deposit;
-            rep->n_out_of_domain += one.n_out_of_domain;
-        }
-    }
+    CGK_TRY(deposit_many(nsnap, meshes, n, pos, nfields, w, cells, p, rep, st));
     double keep_loc = rep ? rep->ms_locate : 0, keep_dep = rep ? rep->ms_deposit : 0;
     cg_status s = batched_diffuse_impl(nsnap, meshes, nfields, cells, p, bandwidths, rep, st);
     if (rep) {

@@ -468,9 +468,11 @@ cg_status tet_locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, co
                             int32_t *cell_out, uint32_t *counts, uint32_t *ranks,
                             unsigned long long *bad, cudaStream_t st);
 
-cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
-                     int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
-                     cudaStream_t st, uint32_t *max_count, uint32_t *ranks) {
+// The point location and its counters (outside particles, non-finite weights, the most
+// particles in one cell), copied to the mesh's pinned readback buffer; nothing is waited
+// for (locate_read takes the counters once the stream has synchronised).
+static cg_status locate_launch(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                               int32_t *cell_out, uint32_t *counts, uint32_t *ranks, cudaStream_t st) {
     CGK_TRY(m->ws_small.ensure(4096));
     CGK_TRY(m->h_small.ensure(4096));
     unsigned long long *bad = m->ws_small.as<unsigned long long>();
@@ -495,12 +497,24 @@ cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const dou
             CGK_TRY(tet_locate_launch(m, n, pos, nf, w, cell_out, counts, ranks, bad, st));
         }
     }
-    unsigned long long *hb = m->h_small.as<unsigned long long>();
-    CGK_CUDA(cudaMemcpyAsync(hb, bad, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    CGK_CUDA(cudaStreamSynchronize(st));
+    CGK_CUDA(cudaMemcpyAsync(m->h_small.as<unsigned long long>(), bad, 3 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    return CG_OK;
+}
+
+static void locate_read(const cg_mesh *m, int64_t *n_out, int64_t *n_nonfinite, uint32_t *max_count) {
+    const unsigned long long *hb = m->h_small.as<unsigned long long>();
     if (n_out) *n_out = (int64_t)hb[0];
     if (n_nonfinite) *n_nonfinite = (int64_t)hb[1];
     if (max_count) *max_count = (uint32_t)hb[2];
+}
+
+cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                     int32_t *cell_out, uint32_t *counts, int64_t *n_out, int64_t *n_nonfinite,
+                     cudaStream_t st, uint32_t *max_count, uint32_t *ranks) {
+    CGK_TRY(locate_launch(m, n, pos, nf, w, cell_out, counts, ranks, st));
+    CGK_CUDA(cudaStreamSynchronize(st));
+    locate_read(m, n_out, n_nonfinite, max_count);
     return CG_OK;
 }
 
@@ -516,8 +530,22 @@ static int fixed_bits(int64_t n, double maxabs) {
     return F > 1000 ? 1000 : (F < -1000 ? -1000 : F);
 }
 
-cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
-                      double *out, const cg_params *p, cg_report *rep, cudaStream_t st) {
+// The quantities of a deposition that both its phases use (workspace layout, cell volume).
+struct DepositPlan {
+    int64_t ncells;
+    int mode;
+    const double *vc;
+    double vcu, inv_pow2;
+    bool ordered;
+    size_t s_cell, s_cnt;
+    int32_t *cell;
+    uint32_t *counts, *ranks;
+};
+
+// Phase 1 of a deposition: the workspace, the cleared per-cell counters and the point
+// location (locate_launch); nothing is waited for.
+static cg_status deposit_begin(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                               const cg_params *p, cudaStream_t st, DepositPlan &dp) {
     const int64_t ncells = m->ncells;
     const int mode = p->deposit_mode;
     const double *vc = m->kind != MESH_STRUCTURED ? m->tet.vc : nullptr;
@@ -542,23 +570,26 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
     uint32_t *counts = ordered ? (uint32_t *)(m->ws_locate.as<char>() + s_cell) : nullptr;
     uint32_t *ranks = ordered ? (uint32_t *)(m->ws_locate.as<char>() + s_cell + s_cnt) : nullptr;
     if (counts) CGK_CUDA(cudaMemsetAsync(counts, 0, (size_t)(ncells + 1) * 4, st));
+    dp = DepositPlan{ncells, mode, vc, vcu, inv_pow2, ordered, s_cell, s_cnt, cell, counts, ranks};
+    return locate_launch(m, n, pos, nf, w, cell, counts, ranks, st);
+}
 
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    if (rep) {
-        for (auto &e : ev) CGK_CUDA(cudaEventCreate(&e));
-        CGK_CUDA(cudaEventRecord(ev[0], st));
-    }
+// Phase 2, once the stream has synchronised after phase 1: the location's counters are
+// checked (CG_EINVAL for non-finite weights, CG_EDOMAIN for particles outside the mesh,
+// before anything is written to out), then the per-cell sums run.
+static cg_status deposit_end(cg_mesh *m, int64_t n, int nf, const double *w, double *out,
+                             cg_report *rep, cudaStream_t st, const DepositPlan &dp) {
+    const int64_t ncells = dp.ncells;
+    const double *vc = dp.vc;
+    const double vcu = dp.vcu, inv_pow2 = dp.inv_pow2;
+    const bool ordered = dp.ordered;
+    const size_t s_cnt = dp.s_cnt;
+    int32_t *cell = dp.cell;
+    uint32_t *counts = dp.counts, *ranks = dp.ranks;
     int64_t n_out = 0, n_bad = 0;
     uint32_t max_count = 0;
-    CGK_TRY(locate_run(m, n, pos, nf, w, cell, counts, &n_out, &n_bad, st,
-                       counts ? &max_count : nullptr, ranks));
-    if (rep) {
-        CGK_CUDA(cudaEventRecord(ev[1], st));
-        rep->n_out_of_domain = n_out;
-    }
-    if (n_bad || n_out)
-        for (auto &e : ev)
-            if (e) cudaEventDestroy(e);
+    locate_read(m, &n_out, &n_bad, counts ? &max_count : nullptr);
+    if (rep) rep->n_out_of_domain = n_out;
     if (n_bad) return fail(CG_EINVAL, "cg_deposit: %lld non-finite weights", (long long)n_bad);
     if (n_out)
         return fail(CG_EDOMAIN, "cg_deposit: %lld particles outside the mesh", (long long)n_out);
@@ -673,17 +704,84 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
         // the host array hs must outlive the async copy
         CGK_CUDA(cudaStreamSynchronize(st));
     }
+    return CG_OK;
+}
+
+cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
+                      double *out, const cg_params *p, cg_report *rep, cudaStream_t st) {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    auto drop = [&]() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
     if (rep) {
-        CGK_CUDA(cudaEventRecord(ev[2], st));
-        CGK_CUDA(cudaEventSynchronize(ev[2]));
+        for (auto &e : ev) CGK_CUDA(cudaEventCreate(&e));
+        CGK_CUDA(cudaEventRecord(ev[0], st));
+    }
+    DepositPlan dp;
+    cg_status s = deposit_begin(m, n, pos, nf, w, p, st, dp);
+    if (s == CG_OK && cudaStreamSynchronize(st) != cudaSuccess)
+        s = cuda_fail(cudaGetLastError(), "deposition", __FILE__, __LINE__);
+    if (s == CG_OK && rep) cudaEventRecord(ev[1], st);
+    if (s == CG_OK) s = deposit_end(m, n, nf, w, out, rep, st, dp);
+    if (s == CG_OK && rep) {
+        cudaEventRecord(ev[2], st);
+        cudaEventSynchronize(ev[2]);
         float a = 0, b = 0;
         cudaEventElapsedTime(&a, ev[0], ev[1]);
         cudaEventElapsedTime(&b, ev[1], ev[2]);
         rep->ms_locate = a;
         rep->ms_deposit = b;
-        for (auto &e : ev) cudaEventDestroy(e);
     }
-    return CG_OK;
+    drop();
+    return s;
+}
+
+// The depositions of several distinct meshes: every point location is launched before
+// one synchronisation, every counter is checked before any output is written (the first
+// failing snapshot's status), then every sum runs.  rep (optional) gets the device time
+// of the two phases and the total count of outside particles.
+cg_status deposit_many(int nsnap, cg_mesh *const *meshes, const int64_t *n, const double *const *pos,
+                       int nf, const double *const *w, double *const *out, const cg_params *p,
+                       cg_report *rep, cudaStream_t st) {
+    std::vector<DepositPlan> dps((size_t)nsnap);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    auto drop = [&]() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    if (rep) {
+        for (auto &e : ev) CGK_CUDA(cudaEventCreate(&e));
+        CGK_CUDA(cudaEventRecord(ev[0], st));
+    }
+    cg_status s = CG_OK;
+    for (int q = 0; q < nsnap && s == CG_OK; ++q)
+        s = deposit_begin(meshes[q], n[q], pos[q], nf, w[q], p, st, dps[q]);
+    if (s == CG_OK && cudaStreamSynchronize(st) != cudaSuccess)
+        s = cuda_fail(cudaGetLastError(), "deposition", __FILE__, __LINE__);
+    if (s == CG_OK && rep) cudaEventRecord(ev[1], st);
+    long long n_out_total = 0;
+    for (int q = 0; q < nsnap && s == CG_OK; ++q) {
+        int64_t n_out = 0, n_bad = 0;
+        locate_read(meshes[q], &n_out, &n_bad, nullptr);
+        n_out_total += n_out;
+        if (n_bad) s = fail(CG_EINVAL, "batch snapshot %d: %lld non-finite weights", q, (long long)n_bad);
+        else if (n_out) s = fail(CG_EDOMAIN, "batch snapshot %d: %lld particles outside the mesh", q, (long long)n_out);
+    }
+    if (rep) rep->n_out_of_domain = n_out_total;
+    for (int q = 0; q < nsnap && s == CG_OK; ++q)
+        s = deposit_end(meshes[q], n[q], nf, w[q], out[q], nullptr, st, dps[q]);
+    if (s == CG_OK && rep) {
+        cudaEventRecord(ev[2], st);
+        cudaEventSynchronize(ev[2]);
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        rep->ms_locate = a;
+        rep->ms_deposit = b;
+    }
+    drop();
+    return s;
 }
 
 }  // namespace cgk

@@ -238,6 +238,10 @@ cg_status locate_run(cg_mesh *m, int64_t n, const double *pos, int nf, const dou
 // Deposition (Eq. (pcm-k)) given particles; validates and writes out[nf][ncells].
 cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const double *w,
                       double *out, const cg_params *p, cg_report *rep, cudaStream_t st);
+// The depositions of several distinct meshes with one synchronisation (see deposit.cu).
+cg_status deposit_many(int nsnap, cg_mesh *const *meshes, const int64_t *n, const double *const *pos,
+                       int nf, const double *const *w, double *const *out, const cg_params *p,
+                       cg_report *rep, cudaStream_t st);
 
 // Diffusion on a structured mesh (in place).
 cg_status diffuse_structured_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
@@ -256,6 +260,8 @@ cg_status diffuse_tet_run(cg_mesh *m, int nf, double *cells, const cg_params *p,
 // sum_k V_c,k u_f,k for each field (FP64, deterministic order), written to host.
 cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host,
                      cudaStream_t st);
+cg_status field_mass_many(int nmesh, cg_mesh *const *ms, int nf, const double *const *cells,
+                          double *mass_host, cudaStream_t st);
 
 // Tet mesh construction (host C++), fills m->tet and the host copies.
 cg_status tet_build(cg_mesh *m, int64_t nverts, const double *xyz, int64_t ntets,

@@ -3692,7 +3692,9 @@ cg_status solid_velocity_run(int64_t n, int ncomp, const double *eps, const doub
     return CG_OK;
 }
 
-cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host, cudaStream_t st) {
+// Launches the mass reduction of one mesh's fields and the copy of its result into the
+// mesh's pinned readback buffer (complete once the stream has synchronised).
+static cg_status field_mass_launch(cg_mesh *m, int nf, const double *cells, cudaStream_t st) {
     int n = (int)m->ncells;
     int G = stencil_grid(n);
     size_t need = align_up((size_t)nf * G * 8) + 64 * 8 + 64 * 4;
@@ -3709,8 +3711,22 @@ cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host,
     CGK_CUDA(cudaGetLastError());
     CGK_TRY(m->h_small.ensure(4096));
     CGK_CUDA(cudaMemcpyAsync(m->h_small.as<char>() + 2048, out, nf * 8, cudaMemcpyDeviceToHost, st));
+    return CG_OK;
+}
+
+cg_status field_mass(cg_mesh *m, int nf, const double *cells, double *mass_host, cudaStream_t st) {
+    return field_mass_many(1, &m, nf, &cells, mass_host, st);
+}
+
+// The masses of several meshes' fields (distinct meshes: each uses its own buffers): every
+// reduction is launched before one synchronisation; mass_host[s * nf + f].
+cg_status field_mass_many(int nmesh, cg_mesh *const *ms, int nf, const double *const *cells,
+                          double *mass_host, cudaStream_t st) {
+    for (int s = 0; s < nmesh; ++s) CGK_TRY(field_mass_launch(ms[s], nf, cells[s], st));
     CGK_CUDA(cudaStreamSynchronize(st));
-    for (int f = 0; f < nf; ++f) mass_host[f] = ((double *)(m->h_small.as<char>() + 2048))[f];
+    for (int s = 0; s < nmesh; ++s)
+        for (int f = 0; f < nf; ++f)
+            mass_host[(size_t)s * nf + f] = ((double *)(ms[s]->h_small.as<char>() + 2048))[f];
     return CG_OK;
 }
 

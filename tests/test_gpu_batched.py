@@ -231,3 +231,32 @@ def test_batched_degenerate_and_boundary_shapes(cg, orc):
     for d, u, got in zip(dims_list, u0, outs[0]):
         ref, _ = orc.diffuse_structured(u, d, dx, (2 * dx) ** 2 / 4, 10, tol=1e-14)
         assert maxrel(got.cpu().numpy(), ref) <= MIXED_TOL, d
+
+
+def test_batched_deposition_checks_every_snapshot_before_writing(cg):
+    """The batch locates every snapshot's particles before writing any deposited field: a
+    snapshot with a particle outside its mesh fails the call with CG_EDOMAIN, names that
+    snapshot, and leaves every snapshot's cells untouched; a valid batch reports the
+    batch's phase times."""
+    import torch
+    cases = small_batch()
+    meshes = [cg.StructuredMesh(c.dims, c.origin, c.dx) for c in cases]
+    pos = [dev(c.pos) for c in cases]
+    w = [dev(c.w) for c in cases]
+    bad = [p.clone() for p in pos]
+    bad[2][1, 3] = 2.5                               # outside the unit cube
+    out = [torch.full((c.w.shape[0], m.ncells), float("nan"), dtype=torch.float64, device="cuda")
+           for c, m in zip(cases, meshes)]
+    prm = cg.Params(nsteps=2, precision=3)
+    with pytest.raises(cg.CGError) as e:
+        cg.coarse_grain_batched(meshes, bad, w, prm, bandwidths=[c.b for c in cases], out=out)
+    assert e.value.code == "CG_EDOMAIN" and "snapshot 2" in str(e.value)
+    assert all(bool(torch.isnan(o).all()) for o in out)
+    # the same batch with valid particles: every deposition runs (the batch's parity
+    # against the oracle is checked above), the report covers the whole batch
+    _, rep = cg.coarse_grain_batched(meshes, pos, w, prm, bandwidths=[c.b for c in cases], out=out,
+                                     report=True)
+    assert not any(bool(torch.isnan(o).any()) for o in out)
+    assert rep["n_out_of_domain"] == 0 and rep["ms_locate"] > 0 and rep["ms_deposit"] > 0
+    for m in meshes:
+        m.close()
