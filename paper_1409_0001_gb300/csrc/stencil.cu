@@ -240,8 +240,8 @@ constexpr int kFlatCptDF = 2;   // ... of the double-float refinement passes
 // arithmetic that turns them into values (a double-float sum of the iterate and its
 // correction) does not wait on the loads in front of the plane's work.
 template <class T, int CPT, class Load, class Finish, class Pre, class Consume>
-__device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, int z1, Load load,
-                                              Finish finish, Pre pre, Consume consume) {
+__device__ __forceinline__ void sweep_flat_at(const Geo &g, int pts, int chunk, int z0, int z1,
+                                              Load load, Finish finish, Pre pre, Consume consume) {
     constexpr int kFlatCells = CPT * kThreads;
     __shared__ T sp[kFlatCells + 2 * kFlatMaxNx];
     const int t = threadIdx.y * TX + threadIdx.x;
@@ -271,8 +271,9 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         hh[j] = hi0 + t + kThreads * j < hi1;
     }
     using P = decltype(pre(0));
-    using RAW = decltype(load(0));
-    auto produce = [&](int k) { return finish(load(k)); };
+    using RAW = decltype(load(0, 0));
+    // a cell's index k in the dense field and kt in the inner vectors (planes pts apart)
+    auto produce = [&](int k, int kt) { return finish(load(k, kt)); };
     T vdn[CPT], vc[CPT], vup[CPT], ha[2], hb[2];
     P pt[CPT];
 #pragma unroll
@@ -288,25 +289,25 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
         hb[j] = T();
     }
     if (z0 < z1) {
-        const int kz = z0 * nxy;
+        const int kz = z0 * nxy, kzt = z0 * pts;
 #pragma unroll
         for (int j = 0; j < CPT; ++j)
             if (own[j]) {
-                const int k = kz + q0 + t + kThreads * j;
-                if (z0 > 0) vdn[j] = produce(k - nxy);
-                vc[j] = produce(k);
-                if (z0 + 1 < g.nz) vup[j] = produce(k + nxy);
+                const int k = kz + q0 + t + kThreads * j, kt = kzt + q0 + t + kThreads * j;
+                if (z0 > 0) vdn[j] = produce(k - nxy, kt - pts);
+                vc[j] = produce(k, kt);
+                if (z0 + 1 < g.nz) vup[j] = produce(k + nxy, kt + pts);
                 pt[j] = pre(k);
             }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            if (hl[j]) ha[j] = produce(kz + lo0 + t + kThreads * j);
-            if (hh[j]) hb[j] = produce(kz + hi0 + t + kThreads * j);
+            if (hl[j]) ha[j] = produce(kz + lo0 + t + kThreads * j, kzt + lo0 + t + kThreads * j);
+            if (hh[j]) hb[j] = produce(kz + hi0 + t + kThreads * j, kzt + hi0 + t + kThreads * j);
         }
     }
     // segment slot of cell q: q - q0 + nx
     for (int z = z0; z < z1; ++z) {
-        const int kz = z * nxy;
+        const int kz = z * nxy, kzt = z * pts;
         RAW nup[CPT], na[2], nbv[2];   // raw operands of plane z+1's (z+2's) values
         P npt[CPT];
 #pragma unroll
@@ -320,18 +321,18 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
             nbv[j] = RAW{};
         }
         if (z + 1 < z1) {
-            const int kn = kz + nxy;
+            const int kn = kz + nxy, knt = kzt + pts;
 #pragma unroll
             for (int j = 0; j < CPT; ++j)
                 if (own[j]) {
-                    const int k = kn + q0 + t + kThreads * j;
-                    if (z + 2 < g.nz) nup[j] = load(k + nxy);
+                    const int k = kn + q0 + t + kThreads * j, kt = knt + q0 + t + kThreads * j;
+                    if (z + 2 < g.nz) nup[j] = load(k + nxy, kt + pts);
                     npt[j] = pre(k);
                 }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                if (hl[j]) na[j] = load(kn + lo0 + t + kThreads * j);
-                if (hh[j]) nbv[j] = load(kn + hi0 + t + kThreads * j);
+                if (hl[j]) na[j] = load(kn + lo0 + t + kThreads * j, knt + lo0 + t + kThreads * j);
+                if (hh[j]) nbv[j] = load(kn + hi0 + t + kThreads * j, knt + hi0 + t + kThreads * j);
             }
         }
 #pragma unroll
@@ -354,7 +355,8 @@ __device__ __forceinline__ void sweep_flat_at(const Geo &g, int chunk, int z0, i
                 s += (nb[j] & 8u) ? sp[i + nx] : T();
                 s += vdn[j];
                 s += vup[j];
-                consume(kz + q0 + t + kThreads * j, vc[j], s, nnxy[j] + nnz, pt[j]);
+                consume(kz + q0 + t + kThreads * j, kzt + q0 + t + kThreads * j, vc[j], s, nnxy[j] + nnz,
+                        pt[j]);
             }
         __syncthreads();
 #pragma unroll
@@ -2405,11 +2407,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
 }
 
 // ---------------------------------------------------------------- flat-plane Chebyshev
-// The Chebyshev iteration of k_cheb_v4 on the flat-plane layout of sweep_flat_at (a
-// block owns kFlatCpt * kThreads consecutive cells of the flattened xy plane, thread t
-// the cells q0 + t + kThreads j), written with per-thread pointers that advance one
-// plane per step, so every load and store of a cell is an immediate offset from them
-// and the index arithmetic is paid once per plane rather than once per access.  The
+// The Chebyshev iteration of k_cheb_v4 on a flat-plane layout (a block owns
+// kFlatCpt * kThreads consecutive cells of the flattened xy plane, thread t the four
+// consecutive cells q0 + 4t .. q0 + 4t + 3, loaded and stored as one vector: the inner
+// vectors of a flat-plane snapshot are stored with planes pts = nxy rounded up to a
+// multiple of four cells apart), written with per-thread pointers that advance one plane
+// per step.  The
 // neighbour sum (x-, x+, y-, y+, z-, z+, a wall adding a zero) and the update are
 // those of the other sweeps: the same bits.  L is the load policy (Vec4-style
 // scalars: plain or L2-coherent).
@@ -2430,17 +2433,20 @@ __device__ __forceinline__ float fld(const TS *p) {
 constexpr int kFlatSlots = kFlatCpt * kThreads + 4 * kFlatMaxNx + kFlatCpt * kThreads + 8;
 
 template <class TS, bool COH>
-__device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, int z1, float ce,
-                                               float gamma, float omega, const float *sdg,
+__device__ __forceinline__ void cheb_flat_tile(const Geo &g, int pts, int chunk, int z0, int z1,
+                                               float ce, float gamma, float omega, const float *sdg,
                                                const TS *yv, const TS *ypv, const TS *rv,
                                                TS *ynv) {
+    using V = Vec4<TS>;
+    using LD = typename std::conditional<COH, Vec4cg<TS>, Vec4<TS>>::type;
     constexpr int C = kFlatCpt;
-    constexpr int S = kThreads;   // stride between a thread's cells
+    constexpr int S = kThreads;   // stride between the halo cells a thread loads
     __shared__ float sp[kFlatSlots];
     const int t = threadIdx.y * TX + threadIdx.x;
     const int nx = g.nx, nxy = g.nxy, nz = g.nz;
     const int P = nx + 1;
     const int q0 = chunk * (C * S);
+    const int qt = q0 + C * t;    // this thread's first cell (a multiple of four)
     const int r0 = q0 / nx - 1;   // first row of the segment (may be -1)
     auto slot = [&](int q) {
         const int r = q / nx;
@@ -2448,120 +2454,112 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int chunk, int z0, 
     };
     const int nslots = ((q0 + C * S + nx - 1) / nx + 2 - r0) * P;
     for (int i = t; i < nslots; i += S) sp[i] = 0.0f;
-    // per cell j: its segment slot, and (packed) whether it is in the plane and its
-    // number of x/y neighbours
+    // per cell j (cell qt + j): its segment slot, and (packed) whether it is in the plane
+    // and its number of x/y neighbours
     int so[C];
     unsigned ownm = 0u, nnp = 0u;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-        const int q = q0 + t + S * j;
+        const int q = qt + j;
         if (q < nxy) ownm |= 1u << j;
         const int iy = q / nx, ix = q - iy * nx;
         nnp |= (unsigned)((ix > 0) + (ix + 1 < nx) + (iy > 0) + (iy + 1 < g.ny)) << (3 * j);
         so[j] = slot(q);
     }
     auto own = [&](int j) { return (ownm >> j) & 1u; };
+    const bool any = ownm != 0u;   // the thread's vector holds cells of the plane
     const int lo0 = max(q0 - nx, 0);
     const int hi0 = q0 + C * S, hi1 = min(hi0 + nx, nxy);
     const bool hl0 = lo0 + t < q0, hl1 = lo0 + t + S < q0;
     const bool hh0 = hi0 + t < hi1, hh1 = hi0 + t + S < hi1;
     const int sl0 = slot(lo0 + t), sl1 = slot(lo0 + t + S);
     const int sh0 = slot(hi0 + t), sh1 = slot(hi0 + t + S);
-    // per-thread pointers at plane z (cell j at [S * j])
-    const size_t pz0 = (size_t)z0 * nxy;
-    const TS *py = yv + pz0 + q0 + t;
-    const TS *pp = ypv ? ypv + pz0 + q0 + t : nullptr;
-    const TS *pr = rv + pz0 + q0 + t;
-    TS *po = ynv + pz0 + q0 + t;
-    const int dlo = lo0 - q0, dhi = hi0 - q0;   // the halo cells relative to py
-    float vdn[C], vc[C], vup[C], yp[C], rc[C], ha0 = 0.f, ha1 = 0.f, hb0 = 0.f, hb1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        vdn[j] = 0.f;
-        vc[j] = 0.f;
-        vup[j] = 0.f;
-        yp[j] = 0.f;
-        rc[j] = 0.f;
-    }
+    // per-thread pointers at plane z (planes are pts apart, a multiple of four cells, so
+    // a thread's four cells are one aligned vector); the halo cells relative to ph
+    const size_t pz0 = (size_t)z0 * pts;
+    const TS *py = yv + pz0 + qt;
+    const TS *pp = ypv ? ypv + pz0 + qt : nullptr;
+    const TS *pr = rv + pz0 + qt;
+    TS *po = ynv + pz0 + qt;
+    const TS *ph = yv + pz0;
+    const int dl0 = lo0 + t, dl1 = lo0 + t + S, dh0 = hi0 + t, dh1 = hi0 + t + S;
+    float4 vdn = make_float4(0.f, 0.f, 0.f, 0.f), vc = vdn, vup = vdn, yp = vdn, rc = vdn;
+    float ha0 = 0.f, ha1 = 0.f, hb0 = 0.f, hb1 = 0.f;
     if (z0 < z1) {
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-            if (own(j)) {
-                if (z0 > 0) vdn[j] = fld<TS, COH>(py - nxy + S * j);
-                vc[j] = fld<TS, COH>(py + S * j);
-                if (z0 + 1 < nz) vup[j] = fld<TS, COH>(py + nxy + S * j);
-                if (pp) yp[j] = fld<TS, COH>(pp + S * j);
-                rc[j] = fld<TS, COH>(pr + S * j);
-            }
-        if (hl0) ha0 = fld<TS, COH>(py + dlo);
-        if (hl1) ha1 = fld<TS, COH>(py + dlo + S);
-        if (hh0) hb0 = fld<TS, COH>(py + dhi);
-        if (hh1) hb1 = fld<TS, COH>(py + dhi + S);
+        if (any) {
+            if (z0 > 0) vdn = LD::load(py - pts, 0);
+            vc = LD::load(py, 0);
+            if (z0 + 1 < nz) vup = LD::load(py + pts, 0);
+            if (pp) yp = LD::load(pp, 0);
+            rc = LD::load(pr, 0);
+        }
+        if (hl0) ha0 = fld<TS, COH>(ph + dl0);
+        if (hl1) ha1 = fld<TS, COH>(ph + dl1);
+        if (hh0) hb0 = fld<TS, COH>(ph + dh0);
+        if (hh1) hb1 = fld<TS, COH>(ph + dh1);
     }
     __syncthreads();   // the zeroed segment before the first plane is published
     for (int z = z0; z < z1; ++z) {
         // loads for plane z+1: y at z+2, y_prev and r at z+1, the halo at z+1
-        float nup[C], nyp[C], nrc[C], na0 = 0.f, na1 = 0.f, nb0 = 0.f, nb1 = 0.f;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            nup[j] = 0.f;
-            nyp[j] = 0.f;
-            nrc[j] = 0.f;
-        }
+        float4 nup = make_float4(0.f, 0.f, 0.f, 0.f), nyp = nup, nrc = nup;
+        float na0 = 0.f, na1 = 0.f, nb0 = 0.f, nb1 = 0.f;
         if (z + 1 < z1) {
-            const bool up2 = z + 2 < nz;
-#pragma unroll
-            for (int j = 0; j < C; ++j)
-                if (own(j)) {
-                    if (up2) nup[j] = fld<TS, COH>(py + 2 * nxy + S * j);
-                    if (pp) nyp[j] = fld<TS, COH>(pp + nxy + S * j);
-                    nrc[j] = fld<TS, COH>(pr + nxy + S * j);
-                }
-            if (hl0) na0 = fld<TS, COH>(py + nxy + dlo);
-            if (hl1) na1 = fld<TS, COH>(py + nxy + dlo + S);
-            if (hh0) nb0 = fld<TS, COH>(py + nxy + dhi);
-            if (hh1) nb1 = fld<TS, COH>(py + nxy + dhi + S);
+            if (any) {
+                if (z + 2 < nz) nup = LD::load(py + 2 * pts, 0);
+                if (pp) nyp = LD::load(pp + pts, 0);
+                nrc = LD::load(pr + pts, 0);
+            }
+            if (hl0) na0 = fld<TS, COH>(ph + pts + dl0);
+            if (hl1) na1 = fld<TS, COH>(ph + pts + dl1);
+            if (hh0) nb0 = fld<TS, COH>(ph + pts + dh0);
+            if (hh1) nb1 = fld<TS, COH>(ph + pts + dh1);
         }
+        const float vcs[C] = {vc.x, vc.y, vc.z, vc.w};
 #pragma unroll
         for (int j = 0; j < C; ++j)
-            if (own(j)) sp[so[j]] = vc[j];
+            if (own(j)) sp[so[j]] = vcs[j];
         if (hl0) sp[sl0] = ha0;
         if (hl1) sp[sl1] = ha1;
         if (hh0) sp[sh0] = hb0;
         if (hh1) sp[sh1] = hb1;
         __syncthreads();
-        const int nnz = (z > 0) + (z + 1 < nz);
+        if (any) {
+            const int nnz = (z > 0) + (z + 1 < nz);
+            const float vds[C] = {vdn.x, vdn.y, vdn.z, vdn.w}, vus[C] = {vup.x, vup.y, vup.z, vup.w};
+            const float yps[C] = {yp.x, yp.y, yp.z, yp.w}, rcs[C] = {rc.x, rc.y, rc.z, rc.w};
+            float o[C];
 #pragma unroll
-        for (int j = 0; j < C; ++j)
-            if (own(j)) {
+            for (int j = 0; j < C; ++j) {
+                // a lane beyond the plane computes from the zero slots and its padding
+                // values and is stored into the plane's padding, which nothing reads
                 const float *c = sp + so[j];
                 float sm = c[-1];
                 sm += c[1];
                 sm += c[-P];
                 sm += c[P];
-                sm += vdn[j];
-                sm += vup[j];
-                const float v = vc[j];
+                sm += vds[j];
+                sm += vus[j];
+                const float v = vcs[j];
                 const float ay = fmaf(sdg[((nnp >> (3 * j)) & 7u) + nnz], v, -ce * sm);
-                st(po + S * j, 0, fmaf(omega, v - yp[j] + gamma * (rc[j] - ay), yp[j]));
+                o[j] = fmaf(omega, v - yps[j] + gamma * (rcs[j] - ay), yps[j]);
             }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            vdn[j] = vc[j];
-            vc[j] = vup[j];
-            vup[j] = nup[j];
-            yp[j] = nyp[j];
-            rc[j] = nrc[j];
+            V::store(po, 0, make_float4(o[0], o[1], o[2], o[3]));
         }
+        __syncthreads();
+        vdn = vc;
+        vc = vup;
+        vup = nup;
+        yp = nyp;
+        rc = nrc;
         ha0 = na0;
         ha1 = na1;
         hb0 = nb0;
         hb1 = nb1;
-        py += nxy;
-        if (pp) pp += nxy;
-        pr += nxy;
-        po += nxy;
+        py += pts;
+        if (pp) pp += pts;
+        pr += pts;
+        po += pts;
+        ph += pts;
     }
 }
 
@@ -2583,6 +2581,8 @@ struct SnapDesc {
     int gx, gy, zlen, nzc;   // refinement items (scalar engine)
     int v4, gx4, zlen4, nzc4;// Chebyshev items (vectorised if v4)
     int flat, nch, nchr;     // flat-plane items: plane chunks per plane (Chebyshev, refinement)
+    int pts;                 // plane pitch of the inner (TS) vectors: nxy, rounded up to a
+                             // multiple of four cells on a flat-plane snapshot
     int m;                   // Chebyshev iterations per round (even)
     int scheme;
     float gamma;
@@ -2636,25 +2636,32 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
     const int f = it.zf / d.nzc;
     const int zc = it.zf - f * d.nzc;
     const int z0 = zc * d.zlen, z1 = min(g.nz, z0 + d.zlen);
-    const size_t off = (size_t)f * g.n;
+    const size_t off = (size_t)f * g.n;                 // the double-float vectors
+    const size_t off_ts = (size_t)f * g.nz * d.pts;     // the inner vectors
     float acc = 0.0f, acc_b = 0.0f;
     const float gamma = d.gamma;
-    TS *r = d.R + off;
-    TS *y1 = d.Ya + off;
-    // the flat-plane engine or the 2.5D tile engine (the same arithmetic per cell)
+    TS *r = d.R + off_ts;
+    TS *y1 = d.Ya + off_ts;
+    // the flat-plane engine or the 2.5D tile engine (the same arithmetic per cell); load
+    // and consume take a cell's index in the double-float and in the inner vectors (the
+    // same on the 2.5D engine's snapshots, whose inner planes are nxy apart)
     const bool flat = d.flat != 0;
+    const int pts = d.pts;
     auto engine = [&](auto load, auto finish, auto pre, auto consume) {
         if (flat)
-            sweep_flat_at<DF, kFlatCptDF>(g, it.bx, z0, z1, load, finish, pre, consume);
+            sweep_flat_at<DF, kFlatCptDF>(g, pts, it.bx, z0, z1, load, finish, pre, consume);
         else
-            sweep25_lf<DF>(g, it.bx, it.by, z0, z1, load, finish, pre, consume);
+            sweep25_lf<DF>(
+                g, it.bx, it.by, z0, z1, [&](int k) { return load(k, k); }, finish, pre,
+                [&](int k, DF v, DF sm, int nn, decltype(pre(0)) pt) { consume(k, k, v, sm, nn, pt); });
     };
     if (first) {
         const DF *u = d.U + off;
         DF *bo = d.B + off;
         engine(
-            [&](int k) { return bld_df<COH>(u, k); }, [](DF v) { return v; }, [](int) { return NoPre{}; },
-            [&](int k, DF v, DF sm, int nn, NoPre) {
+            [&](int k, int) { return bld_df<COH>(u, k); }, [](DF v) { return v; },
+            [](int) { return NoPre{}; },
+            [&](int k, int kt, DF v, DF sm, int nn, NoPre) {
                 const DF lx = df_lap(sm, v, (float)nn);
                 DF bk = v;
                 if (scheme == 1) {
@@ -2664,20 +2671,20 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
                 float bf = df_f(bk);
                 acc = fmaf(bf, bf, acc);
                 float rf = df_f(df_mul_un(cf_c, lx));
-                st(r, k, rf);
-                st(y1, k, gamma * rf);
+                st(r, kt, rf);
+                st(y1, kt, gamma * rf);
             });
     } else {
         const DF *xin = (round == 1 ? d.U : ((round & 1) ? d.X2 : d.X1)) + off;
         DF *xout = (round == R ? d.U : ((round & 1) ? d.X1 : d.X2)) + off;
         const DF *b = (scheme == 1 ? d.B : d.U) + off;
         DF *bo = d.B + off;
-        const TS *dd = d.Yb + off;
+        const TS *dd = d.Yb + off_ts;
         const bool next = part_next != nullptr;
         engine(
-            [&](int k) { return DFd{bld_df<COH>(xin, k), bld<COH>(dd, k)}; },
+            [&](int k, int kt) { return DFd{bld_df<COH>(xin, k), bld<COH>(dd, kt)}; },
             [](DFd v) { return df_add_f(v.x, v.d); }, [&](int k) { return bld_df<COH>(b, k); },
-            [&](int k, DF v, DF sm, int nn, DF bk) {
+            [&](int k, int kt, DF v, DF sm, int nn, DF bk) {
                 xout[k] = v;
                 const DF lx = df_lap(sm, v, (float)nn);
                 float rf = df_f(df_res(bk, v, cf_ce, lx));
@@ -2694,8 +2701,8 @@ __device__ __forceinline__ void batched_refine(const SnapDesc<TS> &d, const BIte
                     acc_b = fmaf(bf, bf, acc_b);
                     rf = df_f(cl);
                 }
-                st(r, k, rf);
-                st(y1, k, gamma * rf);
+                st(r, kt, rf);
+                st(y1, kt, gamma * rf);
             });
         const double tb = block_sum_f(acc_b);
         if (is_thread0() && next) *part_next = tb;
@@ -2712,7 +2719,7 @@ __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem 
     const int f = it.zf / nzc;
     const int zc = it.zf - f * nzc;
     const int z0 = zc * zlen, z1 = min(g.nz, z0 + zlen);
-    const size_t off = (size_t)f * g.n;
+    const size_t off = (size_t)f * g.nz * d.pts;   // inner vectors: planes pts apart
     // y_k lives in Ya for odd k, in Yb for even k; y_{k+1} overwrites y_{k-1}
     const TS *yc = ((k & 1) ? d.Ya : d.Yb) + off;
     TS *yo = ((k & 1) ? d.Yb : d.Ya) + off;
@@ -2723,7 +2730,7 @@ __device__ __forceinline__ void batched_cheb(const SnapDesc<TS> &d, const BItem 
     stage_table(sdg, d.cf32.dg);
     __syncthreads();
     if (d.flat) {
-        cheb_flat_tile<TS, COH>(g, it.bx, z0, z1, ce, gamma, omega, sdg, yc, yp, r, yo);
+        cheb_flat_tile<TS, COH>(g, d.pts, it.bx, z0, z1, ce, gamma, omega, sdg, yc, yp, r, yo);
     } else if (d.v4) {
         if constexpr (COH)
             cheb_v4_tile<TS, Vec4cg>(g, it.bx, it.by, z0, z1, d.cf32, sdg, d.gamma, omega, yc, yp, r, yo);
@@ -4580,8 +4587,10 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
         d.gx4 = (m->nx + 4 * TX - 1) / (4 * TX);
         d.zlen4 = d.zlen;
         d.nzc4 = d.nzc;
+        d.pts = d.flat ? (m->nx * m->ny + 3) / 4 * 4 : m->nx * m->ny;
         // per-snapshot solver vectors, owned by the snapshot's mesh
-        const size_t v64 = align_up((size_t)n * nf * 8), vts = align_up((size_t)n * nf * sizeof(TS));
+        const size_t v64 = align_up((size_t)n * nf * 8);
+        const size_t vts = align_up((size_t)m->nz * d.pts * nf * sizeof(TS));
         CGK_TRY(m->ws_diffuse.ensure(4 * v64 + 3 * vts));
         char *wb = m->ws_diffuse.as<char>();
         d.U = (DF *)wb;
