@@ -638,8 +638,10 @@ static cg_status batched_diffuse_impl(int nsnap, cg_mesh *const *meshes, int nfi
                        p->scheme != CG_SCHEME_EXPLICIT_EULER;
     double mass_in[CG_REPORT_MAX_FIELDS] = {0}, mass_out[CG_REPORT_MAX_FIELDS] = {0};
     const int nrep = nfields < CG_REPORT_MAX_FIELDS ? nfields : CG_REPORT_MAX_FIELDS;
-    std::vector<double> mm;   // per snapshot and field, one synchronisation for all
-    if (rep) {
+    // the masses before and after: the batched graph's run reports them itself; the
+    // per-snapshot loop below takes them here, one synchronisation for all snapshots
+    std::vector<double> mm;
+    if (rep && !fused) {
         mm.resize((size_t)nsnap * nrep);
         CGK_TRY(field_mass_many(nsnap, meshes, nrep, cells, mm.data(), st));
         for (int s = 0; s < nsnap; ++s)
@@ -683,15 +685,17 @@ static cg_status batched_diffuse_impl(int nsnap, cg_mesh *const *meshes, int nfi
         rep->ms_diffuse = ms;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (s == CG_OK || s == CG_ENOCONV) {
-            cg_status s2 = field_mass_many(nsnap, meshes, nrep, cells, mm.data(), st);
-            if (s2 != CG_OK) return s2;
-            for (int q = 0; q < nsnap; ++q)
-                for (int f = 0; f < nrep; ++f) mass_out[f] += mm[(size_t)q * nrep + f];
-        }
-        for (int f = 0; f < nrep; ++f) {
-            rep->mass_in[f] = mass_in[f];
-            rep->mass_out[f] = mass_out[f];
+        if (!fused) {
+            if (s == CG_OK || s == CG_ENOCONV) {
+                cg_status s2 = field_mass_many(nsnap, meshes, nrep, cells, mm.data(), st);
+                if (s2 != CG_OK) return s2;
+                for (int q = 0; q < nsnap; ++q)
+                    for (int f = 0; f < nrep; ++f) mass_out[f] += mm[(size_t)q * nrep + f];
+            }
+            for (int f = 0; f < nrep; ++f) {
+                rep->mass_in[f] = mass_in[f];
+                rep->mass_out[f] = mass_out[f];
+            }
         }
     }
     return s;

@@ -2583,6 +2583,7 @@ struct SnapDesc {
     int flat, nch, nchr;     // flat-plane items: plane chunks per plane (Chebyshev, refinement)
     int pts;                 // plane pitch of the inner (TS) vectors: nxy, rounded up to a
                              // multiple of four cells on a flat-plane snapshot
+    double vcu;              // the cell volume
     int m;                   // Chebyshev iterations per round (even)
     int scheme;
     float gamma;
@@ -2876,6 +2877,21 @@ __global__ void k_batched_final(const SnapDesc<TS> *__restrict__ sd, int nf, dou
         DF v = d.U[i];
         out[i] = (double)v.hi + (double)v.lo;
     }
+}
+
+// sum_k V_c u_k of every snapshot's field (the caller's FP64 arrays): one block per
+// (snapshot, field), out[s * nf + f]
+template <class TS>
+__global__ void k_mass_batched(const SnapDesc<TS> *__restrict__ sd, int nf, double *__restrict__ out) {
+    const int s = blockIdx.x / nf, f = blockIdx.x - s * nf;
+    const SnapDesc<TS> &d = sd[s];
+    const int n = d.g.n;
+    const double *u = d.cells + (size_t)f * n;
+    const double vcu = d.vcu;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += kThreads) acc += vcu * u[k];
+    const double v = block_sum(acc);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
 // sum_k V_c,k u_k per field (1-D grid-stride; any mesh)
@@ -4588,6 +4604,7 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
         d.zlen4 = d.zlen;
         d.nzc4 = d.nzc;
         d.pts = d.flat ? (m->nx * m->ny + 3) / 4 * 4 : m->nx * m->ny;
+        d.vcu = (m->dx * m->dx) * m->dx;
         // per-snapshot solver vectors, owned by the snapshot's mesh
         const size_t v64 = align_up((size_t)n * nf * 8);
         const size_t vts = align_up((size_t)m->nz * d.pts * nf * sizeof(TS));
@@ -4629,7 +4646,7 @@ static cg_status batch_plan(int nsnap, cg_mesh *const *meshes, int nf, double *c
 struct BatchArena {
     char *ab = nullptr;
     size_t o_desc = 0, o_om = 0, o_ri = 0, o_ci = 0, o_fi = 0, o_prr = 0, o_pbb = 0, o_hist = 0,
-           o_gb = 0, o_bad = 0, o_out = 0, total = 0;
+           o_gb = 0, o_bad = 0, o_out = 0, o_mass = 0, total = 0;
     size_t nh = 0;
 };
 
@@ -4649,7 +4666,8 @@ static BatchArena batch_layout(const BatchPlan<TS> &P, int nsnap, int nf, int ns
     A.o_gb = align_up(A.o_hist + A.nh * sizeof(double2));
     A.o_bad = align_up(A.o_gb + sizeof(GridBar));
     A.o_out = align_up(A.o_bad + sizeof(unsigned int));
-    A.total = align_up(A.o_out + (size_t)nsnap * sizeof(double *));
+    A.o_mass = align_up(A.o_out + (size_t)nsnap * sizeof(double *));
+    A.total = align_up(A.o_mass + 2 * (size_t)nsnap * nf * 8);
     return A;
 }
 
@@ -4876,9 +4894,30 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
     CGK_TRY(m0->ws_batch.ensure(A.total));
     CGK_TRY(batch_upload(P, A, m0->ws_batch.as<char>(), nsnap, cells, st));
     const size_t nh = A.nh;
-    CGK_TRY(m0->h_small.ensure(4096 + nh * sizeof(double2) + 64));
+    const size_t nm = (size_t)nsnap * nf;   // masses per snapshot-field, before and after
+    CGK_TRY(m0->h_small.ensure(4096 + nh * sizeof(double2) + 64 + 2 * nm * 8));
     double2 *hh = (double2 *)(m0->h_small.as<char>() + 4096);
     GridBar *hgb = (GridBar *)(hh + nh);
+    double *hmass = (double *)(m0->h_small.as<char>() + 4096 + nh * sizeof(double2) + 64);
+    const SnapDesc<TS> *dsd = (const SnapDesc<TS> *)(A.ab + A.o_desc);
+    double *dmass = (double *)(A.ab + A.o_mass);
+    // report: the fields' masses before the smoothing (and after it, below), one block per
+    // snapshot-field, read back with the residual history
+    if (rep)
+        CGK_LAUNCH("mass", 8.0 * P.cells_total * nf, st,
+                   k_mass_batched<TS><<<(unsigned)nm, kThreads, 0, st>>>(dsd, nf, dmass));
+    auto report_mass = [&]() {
+        const int nrep = nf < CG_REPORT_MAX_FIELDS ? nf : CG_REPORT_MAX_FIELDS;
+        for (int f = 0; f < nrep; ++f) {
+            double a = 0.0, b = 0.0;
+            for (int q = 0; q < nsnap; ++q) {
+                a += hmass[(size_t)q * nf + f];
+                b += hmass[nm + (size_t)q * nf + f];
+            }
+            rep->mass_in[f] = a;
+            rep->mass_out[f] = b;
+        }
+    };
     // rounds learned by an earlier call with the same signature
     std::vector<double> sig = {(double)nf, (double)p->precision, (double)p->scheme,
                                (double)p->nsteps, p->tol, p->T};
@@ -4954,8 +4993,12 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
             ge = &m0->graphs.back();
         }
         CGK_CUDA(cudaGraphLaunch(ge->exec, st));
+        if (rep)
+            CGK_LAUNCH("mass", 8.0 * P.cells_total * nf, st,
+                       k_mass_batched<TS><<<(unsigned)nm, kThreads, 0, st>>>(dsd, nf, dmass + nm));
         CGK_CUDA(cudaMemcpyAsync(hh, A.ab + A.o_hist, nh * sizeof(double2), cudaMemcpyDeviceToHost, st));
         CGK_CUDA(cudaMemcpyAsync(hgb, A.ab + A.o_gb, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+        if (rep) CGK_CUDA(cudaMemcpyAsync(hmass, dmass, 2 * nm * 8, cudaMemcpyDeviceToHost, st));
         CGK_CUDA(cudaStreamSynchronize(st));
         prof_account_replay(*ge);
         if (hgb->err)
@@ -4986,6 +5029,7 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
                 rep->final_rel_residual = worst;
                 rep->inner_iters_per_round = P.mmax;
                 rep->sweep_shape_used = code;
+                report_mass();
             }
             return CG_OK;
         }
@@ -4997,8 +5041,16 @@ static cg_status diffuse_batched_df(int nsnap, cg_mesh *const *meshes, int nf,
                            (const SnapDesc<TS> *)(A.ab + A.o_desc), nf,
                            (double *const *)(A.ab + A.o_out), bad));
             CGK_CUDA(cudaGetLastError());
+            if (rep) {
+                CGK_LAUNCH("mass", 8.0 * P.cells_total * nf, st,
+                           k_mass_batched<TS><<<(unsigned)nm, kThreads, 0, st>>>(dsd, nf, dmass + nm));
+                CGK_CUDA(cudaMemcpyAsync(hmass, dmass, 2 * nm * 8, cudaMemcpyDeviceToHost, st));
+            }
             CGK_CUDA(cudaStreamSynchronize(st));
-            if (rep) rep->final_rel_residual = worst;
+            if (rep) {
+                rep->final_rel_residual = worst;
+                report_mass();
+            }
             break;
         }
     }
