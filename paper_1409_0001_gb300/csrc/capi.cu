@@ -467,6 +467,7 @@ cg_status cg_destroy_mesh(cg_mesh *m) {
     for (auto &e : m->graphs) graph_release(e);
     m->graphs.clear();
     if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+    for (cudaStream_t a : m->aux_streams) cudaStreamDestroy(a);
     if (m->kind != MESH_STRUCTURED) tet_release(m);
     delete m;
     return CG_OK;

@@ -10,6 +10,7 @@
 // even) and adds with 64-bit integer atomics, which is exact and order-free.
 #include <cuda_runtime.h>
 #include <cmath>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 
@@ -739,24 +740,61 @@ cg_status deposit_run(cg_mesh *m, int64_t n, const double *pos, int nf, const do
 
 // The depositions of several distinct meshes: every point location is launched before
 // one synchronisation, every counter is checked before any output is written (the first
-// failing snapshot's status), then every sum runs.  rep (optional) gets the device time
-// of the two phases and the total count of outside particles.
+// failing snapshot's status), then every sum runs.  The snapshots' kernels are small, so
+// they are spread over a few streams of the first mesh (forked from and joined back to
+// st by events) and run side by side.  rep (optional) gets the device time of the two
+// phases and the total count of outside particles.
 cg_status deposit_many(int nsnap, cg_mesh *const *meshes, const int64_t *n, const double *const *pos,
                        int nf, const double *const *w, double *const *out, const cg_params *p,
                        cg_report *rep, cudaStream_t st) {
+    constexpr int kAux = 8;
+    cg_mesh *m0 = meshes[0];
+    while ((int)m0->aux_streams.size() < kAux) {
+        cudaStream_t a = nullptr;
+        CGK_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+        m0->aux_streams.push_back(a);
+    }
+    const int na = std::min(kAux, nsnap);
+    std::vector<cudaEvent_t> evs;
+    auto event = [&](cudaEvent_t *e) -> cg_status {
+        CGK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        evs.push_back(*e);
+        return CG_OK;
+    };
+    // the auxiliary streams start after what st holds, and st continues after them
+    auto fork = [&]() -> cg_status {
+        cudaEvent_t e;
+        CGK_TRY(event(&e));
+        CGK_CUDA(cudaEventRecord(e, st));
+        for (int a = 0; a < na; ++a) CGK_CUDA(cudaStreamWaitEvent(m0->aux_streams[a], e, 0));
+        return CG_OK;
+    };
+    auto join = [&]() -> cg_status {
+        for (int a = 0; a < na; ++a) {
+            cudaEvent_t e;
+            CGK_TRY(event(&e));
+            CGK_CUDA(cudaEventRecord(e, m0->aux_streams[a]));
+            CGK_CUDA(cudaStreamWaitEvent(st, e, 0));
+        }
+        return CG_OK;
+    };
     std::vector<DepositPlan> dps((size_t)nsnap);
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     auto drop = [&]() {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
     };
-    if (rep) {
-        for (auto &e : ev) CGK_CUDA(cudaEventCreate(&e));
-        CGK_CUDA(cudaEventRecord(ev[0], st));
-    }
     cg_status s = CG_OK;
+    if (rep) {
+        for (auto &e : ev)
+            if (s == CG_OK && cudaEventCreate(&e) != cudaSuccess) s = fail(CG_ECUDA, "event");
+        if (s == CG_OK) cudaEventRecord(ev[0], st);
+    }
+    if (s == CG_OK) s = fork();
     for (int q = 0; q < nsnap && s == CG_OK; ++q)
-        s = deposit_begin(meshes[q], n[q], pos[q], nf, w[q], p, st, dps[q]);
+        s = deposit_begin(meshes[q], n[q], pos[q], nf, w[q], p, m0->aux_streams[q % na], dps[q]);
+    if (s == CG_OK) s = join();
     if (s == CG_OK && cudaStreamSynchronize(st) != cudaSuccess)
         s = cuda_fail(cudaGetLastError(), "deposition", __FILE__, __LINE__);
     if (s == CG_OK && rep) cudaEventRecord(ev[1], st);
@@ -769,8 +807,10 @@ cg_status deposit_many(int nsnap, cg_mesh *const *meshes, const int64_t *n, cons
         else if (n_out) s = fail(CG_EDOMAIN, "batch snapshot %d: %lld particles outside the mesh", q, (long long)n_out);
     }
     if (rep) rep->n_out_of_domain = n_out_total;
+    if (s == CG_OK) s = fork();
     for (int q = 0; q < nsnap && s == CG_OK; ++q)
-        s = deposit_end(meshes[q], n[q], nf, w[q], out[q], nullptr, st, dps[q]);
+        s = deposit_end(meshes[q], n[q], nf, w[q], out[q], nullptr, m0->aux_streams[q % na], dps[q]);
+    if (s == CG_OK) s = join();
     if (s == CG_OK && rep) {
         cudaEventRecord(ev[2], st);
         cudaEventSynchronize(ev[2]);
@@ -779,6 +819,10 @@ cg_status deposit_many(int nsnap, cg_mesh *const *meshes, const int64_t *n, cons
         cudaEventElapsedTime(&b, ev[1], ev[2]);
         rep->ms_locate = a;
         rep->ms_deposit = b;
+    }
+    if (s != CG_OK) {   // nothing of this call stays in flight
+        for (int a = 0; a < na; ++a) cudaStreamSynchronize(m0->aux_streams[a]);
+        cudaStreamSynchronize(st);
     }
     drop();
     return s;

@@ -167,6 +167,7 @@ struct cg_mesh {
     std::vector<std::pair<double, double>> spectrum;   // unstructured: lower end of the
                                                        // Chebyshev interval per dte
     cudaStream_t capture_stream = nullptr;    // private stream used only for capture
+    std::vector<cudaStream_t> aux_streams;    // batched depositions: snapshots in parallel
 };
 
 namespace cgk {
