@@ -2457,13 +2457,15 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int pts, int chunk,
     // per cell j (cell qt + j): its segment slot, and (packed) whether it is in the plane
     // and its number of x/y neighbours
     int so[C];
-    unsigned ownm = 0u, nnp = 0u;
+    unsigned ownm = 0u, nnp = 0u, inl = 0u, inr = 0u;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int q = qt + j;
         if (q < nxy) ownm |= 1u << j;
         const int iy = q / nx, ix = q - iy * nx;
         nnp |= (unsigned)((ix > 0) + (ix + 1 < nx) + (iy > 0) + (iy + 1 < g.ny)) << (3 * j);
+        if (ix > 0) inl |= 1u << j;        // x - 1 is in the row (for j > 0: the thread's cell j - 1)
+        if (ix + 1 < nx) inr |= 1u << j;   // x + 1 is in the row (for j < 3: its cell j + 1)
         so[j] = slot(q);
     }
     auto own = [&](int j) { return (ownm >> j) & 1u; };
@@ -2532,9 +2534,11 @@ __device__ __forceinline__ void cheb_flat_tile(const Geo &g, int pts, int chunk,
             for (int j = 0; j < C; ++j) {
                 // a lane beyond the plane computes from the zero slots and its padding
                 // values and is stored into the plane's padding, which nothing reads
+                // x neighbours inside the thread's vector come from its registers (the same
+                // values the segment holds; a row end is a wall, zero as its pad slot)
                 const float *c = sp + so[j];
-                float sm = c[-1];
-                sm += c[1];
+                float sm = j == 0 ? c[-1] : (((inl >> j) & 1u) ? vcs[j - 1] : 0.0f);
+                sm += j == C - 1 ? c[1] : (((inr >> j) & 1u) ? vcs[j + 1] : 0.0f);
                 sm += c[-P];
                 sm += c[P];
                 sm += vds[j];
