@@ -1466,6 +1466,7 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
     const bool want_cheb = p->sweep_shape != 1 && sizeof(TS) == 4;
     const double rho_g = o.dte * m->tet.max_rate / (1.0 + o.dte * m->tet.max_rate);
     ChebSchedule cheb;
+    double cheb_sg = 0.0;   // the schedule's convergence rate per iteration
     bool have_cheb = false;
     const int max_rounds = p->max_rounds > 0 ? p->max_rounds : 12;
     const int max_inner = p->max_iter;
@@ -1510,6 +1511,8 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
         }
         cheb = cheb_schedule(a, 1.0 + rho_g, eps_in);
         have_cheb = cheb.iterations() <= max_inner;   // else PCG stays cheaper
+        const double kap = (1.0 + rho_g) / a;
+        cheb_sg = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
     }
     int s = 0;
     for (; s < p->nsteps; ++s) {
@@ -1537,7 +1540,21 @@ static cg_status tet_mixed(cg_mesh *m, int nf, double *cells, const cg_params *p
             CGK_LAUNCH(sizeof(TS) == 2 ? "tcheb_bf16" : "tcheb_fp32", (double)n * (4 + nf * 2.0 * sizeof(TS)), st,
                        (k_tcheb<TS, true><<<G, kThreads, 0, st>>>(o, nf, Rin, nullptr, nullptr, Cb[1],
                                                                               cheb.c0, 0.f)));
-            const int mi = cheb.iterations();
+            // a later round of a step needs only what is left to the tolerance: the last
+            // round's FP64 residual is on the host, so the round runs the schedule's first
+            // iterations that reduce it below tol ||b|| with a tenfold margin (the
+            // recurrence's coefficients do not depend on where it stops); a round that falls
+            // short is followed by another, as ever
+            int mi = cheb.iterations();
+            if (rounds > 0 && cheb_sg > 0.0 && cheb_sg < 1.0) {
+                double need = 1.0;
+                for (int f = 0; f < nf; ++f)
+                    if (hsc[f].rr > 0.0 && hsc[f].bb > 0.0)
+                        need = std::min(need, std::sqrt(tol2 * hsc[f].bb / hsc[f].rr));
+                const double eps = 0.1 * need;
+                if (eps > eps_in)
+                    mi = std::min(mi, std::max(1, (int)std::ceil(std::log(2.0 / eps) / -std::log(cheb_sg))));
+            }
             // blocks of (row width rounded to a warp, at most 256) x (256 / that) rows
             const int hbx = std::min(kThreads, (o.hx + 31) / 32 * 32);
             const dim3 hblk((unsigned)hbx, (unsigned)(kThreads / hbx));
