@@ -161,7 +161,10 @@ typedef struct {
     int sweep_shape;    /* hex Chebyshev sweep shape: 0 = autotuned per mesh (default);
                            100 + z = vectorised, 4 x-cells per thread, z planes per block
                            (needs nx % 4 == 0); 2, 4, 8 = register-blocked planes per
-                           block; -z = z-marching, z planes per block; 300 = resident:
+                           block; -z = z-marching, z planes per block; 200 + z = two
+                           iterations per launch (temporal blocking), z planes per block
+                           (nx % 4 == 0, nx <= 512, no periodic axis; the same results
+                           as 100 + z; the autotuner also weighs it); 300 = resident:
                            each round's inner solve in one cooperative launch that keeps
                            the mesh in the SMs' shared memory (one field, nx % 4 == 0, a
                            mesh that fits; the autotuner also weighs it); 400 + z =

@@ -70,12 +70,16 @@ __device__ __forceinline__ double finish_sum(const double *partials, int q, int 
 __device__ __forceinline__ bool is_thread0() { return threadIdx.x == 0 && threadIdx.y == 0; }
 
 // Copies a 7-entry diagonal table into shared memory (dynamic indexing of a kernel
-// parameter array would go through local memory).  Visible after the first barrier
-// of sweep25, before any consume().
+// parameter array would go through local memory).  One thread copies it with constant
+// indices: a thread-dependent index into the parameter array made every thread of the
+// kernel store a local copy of it first.  Visible after the first barrier of sweep25,
+// before any consume().
 template <class T>
 __device__ __forceinline__ void stage_table(T *dst, const T *src) {
-    const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    if (t < 7) dst[t] = src[t];
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) dst[i] = src[i];
+    }
 }
 
 

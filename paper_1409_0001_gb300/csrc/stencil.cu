@@ -2155,6 +2155,200 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
     }
 }
 
+// ---------------------------------------------------------------- two iterations per sweep, long rows
+// The pair recurrence of k_cheb2_v4 for rows of up to 512 cells (nx % 4 == 0), where one
+// warp no longer holds a row.  A block holds whole rows: W = nx/4 threads to a row,
+// rounded up to whole warps (at most four), and TYR = blockDim.y - 2 rows it writes, with
+// y_{k+1} recomputed on the row either side as in k_cheb2_v4.  A thread's x neighbours
+// come from the adjacent lanes by shuffle, and across a warp boundary from the staged
+// plane.  Instead of a register queue, y_k, y_{k-1} and r of the planes ahead are staged
+// in shared-memory rings by cp.async one plane ahead of the march: y_k in four slots
+// (planes q-1 .. q+2, all TYR + 4 rows), y_{k-1} in two (q, q+1), r in three (q-1 ..
+// q+1); planes and rows outside the mesh are staged as zeros.  A slot is refilled only
+// after the barrier that ends the step which last read it.  With the queue in shared
+// memory a block of 1024 threads fits the 64-register budget, one block per SM.  Per
+// cell the arithmetic and its order are those of k_cheb_v4, so the iterates are
+// bit-identical.  It pays where the sweep is bound by HBM: two iterations move 20 bytes
+// per cell (three reads, two writes) instead of 32.
+constexpr int kRowsThreads = 1024;
+constexpr int kRowsMaxNx = 512;
+
+// a row vector of four cells as stored: 16 bytes in FP32, 8 in BF16
+template <class TS> using RowV = typename std::conditional<sizeof(TS) == 4, float4, uint2>::type;
+template <class TS> __device__ __forceinline__ float4 rowv_f4(const RowV<TS> &v) {
+    if constexpr (sizeof(TS) == 4) {
+        return v;
+    } else {
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+// stage one row vector (ok) or zeros
+template <class TS> __device__ __forceinline__ void rowv_stage(RowV<TS> *dst, const TS *src, bool ok) {
+    if (ok) {
+        if constexpr (sizeof(TS) == 4) cp_async16(dst, src);
+        else cp_async8(dst, src);
+    } else {
+        *dst = RowV<TS>{};
+    }
+}
+// threads per row, rows per block and dynamic shared memory of a launch
+__host__ __device__ inline int rows_width(int nx) { return ((nx / 4 + 31) / 32) * 32; }
+inline int rows_per_block(int nx, int ny) { return std::max(1, std::min(kRowsThreads / rows_width(nx) - 2, ny)); }
+template <class TS> inline size_t rows_smem(int W, int tyr) {
+    return (size_t)W * ((size_t)(4 * (tyr + 4) + 5 * (tyr + 2)) * sizeof(RowV<TS>) + (size_t)(tyr + 2) * 16);
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kRowsThreads, 1)
+    k_cheb2_rows(Geo g, int zlen, int nzc, Coef32 cf, float gamma, float om1, float om2,
+                 const TS *__restrict__ yk_all, const TS *__restrict__ ykm_all,
+                 const TS *__restrict__ r_all, TS *__restrict__ c_all, TS *__restrict__ d_all) {
+    chain_wait();
+    chain_release();
+    using RV = RowV<TS>;
+    using V = Vec4<TS>;
+    extern __shared__ __align__(16) unsigned char rows_sm[];
+    __shared__ float sdg[8];
+    stage_table(sdg, cf.dg);
+    const int W = blockDim.x, TYR = blockDim.y - 2;
+    const int KR = TYR + 4, MR = TYR + 2;
+    RV *Kr = reinterpret_cast<RV *>(rows_sm);                   // y_k    [4][KR][W]
+    RV *Mr = Kr + 4 * KR * W;                                   // y_{k-1} [2][MR][W]
+    RV *Rr = Mr + 2 * MR * W;                                   // r      [3][MR][W]
+    float4 *Su = reinterpret_cast<float4 *>(Rr + 3 * MR * W);   // y_{k+1} of plane q-1 [MR][W]
+    const int f = blockIdx.z / nzc;
+    const int z0 = (blockIdx.z - f * nzc) * zlen, z1 = min(g.nz, z0 + zlen);
+    const size_t off = (size_t)f * g.n;
+    const TS *yk = yk_all + off;
+    const TS *ykm = ykm_all ? ykm_all + off : nullptr;
+    const TS *r = r_all + off;
+    TS *yc = c_all + off;
+    TS *yd = d_all + off;
+    const int tx = threadIdx.x, t = threadIdx.y, lane = tx & 31;
+    const int x = 4 * tx;
+    const int y0 = blockIdx.y * TYR, y = y0 - 1 + t;
+    const bool ownx = x < g.nx;
+    const bool rowin = y >= 0 && y < g.ny && ownx;
+    const bool inner = t >= 1 && t <= TYR && y < g.ny && ownx;   // rows this block writes
+    const bool hrow = t == 0 || t == TYR + 1;                    // also stages row y0-2 / y0+TYR+1
+    const int yh = t == 0 ? y0 - 2 : y0 + TYR + 1;
+    const bool hin = hrow && yh >= 0 && yh < g.ny && ownx;
+    const int hslot = t == 0 ? 0 : KR - 1;
+    const int nyb = (y > 0) + (y + 1 < g.ny);
+    const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx), n12 = nyb + 2;
+    // 32-bit offsets within a field (a field has fewer than 2^31 cells)
+    const int kown = rowin ? y * g.nx + x : 0, khalo = hin ? yh * g.nx + x : 0;
+    const int KW = KR * W, MW = MR * W;
+    auto kv = [&](int q, int row) -> RV * { return Kr + (q & 3) * KW + row * W + tx; };
+    auto mv = [&](int q) -> RV * { return Mr + (q & 1) * MW + t * W + tx; };
+    auto rv = [&](int q) -> RV * { return Rr + (q % 3) * MW + t * W + tx; };
+    // staging of plane p: y_k up to plane z1 + 1, y_{k-1} and r up to plane z1 (p >= -1)
+    auto stage_k = [&](int p) {
+        if (p > z1 + 1) return;
+        const bool pin = p >= 0 && p < g.nz;
+        const int kp = pin ? p * g.nxy : 0;
+        rowv_stage<TS>(kv(p, t + 1), yk + (kp + kown), pin && rowin);
+        if (hrow) rowv_stage<TS>(kv(p, hslot), yk + (kp + khalo), pin && hin);
+    };
+    auto stage_mr = [&](int p) {
+        if (p > z1) return;
+        const bool ok = p < g.nz && rowin;
+        const int kp = (ok ? p * g.nxy : 0) + kown;
+        if (ykm) rowv_stage<TS>(mv(p), ykm + kp, ok);
+        rowv_stage<TS>(rv(p), r + kp, ok);
+    };
+    const int qs = max(z0 - 1, 0);
+    stage_k(qs - 1);
+    stage_k(qs);
+    stage_k(qs + 1);
+    stage_mr(qs);
+    cp_async_commit();
+    __syncthreads();   // the diagonal table
+    // diagonals of the four cells on planes with both z neighbours (most planes)
+    const float d0i = sdg[n0 + 2], d12i = sdg[n12 + 2], d3i = sdg[n3 + 2];
+    float4 um = f4zero(), u0 = f4zero();
+    for (int q = qs; q <= z1; ++q) {
+        stage_k(q + 2);
+        stage_mr(q + 1);
+        cp_async_commit();
+        cp_async_wait<1>();   // this thread's copies of the planes step q reads
+        Su[t * W + tx] = u0;
+        __syncthreads();
+        const float4 vk0 = rowv_f4<TS>(*kv(q, t + 1));
+        const float4 vkm = rowv_f4<TS>(*kv(q - 1, t + 1));
+        // x neighbours of y_k (plane q) and of y_{k+1} (plane q-1): lanes, or across a warp
+        float kl = __shfl_up_sync(0xffffffffu, vk0.w, 1);
+        float kr = __shfl_down_sync(0xffffffffu, vk0.x, 1);
+        float ul = __shfl_up_sync(0xffffffffu, u0.w, 1);
+        float ur = __shfl_down_sync(0xffffffffu, u0.x, 1);
+        if (lane == 0 && tx > 0) {
+            kl = rowv_f4<TS>(*(kv(q, t + 1) - 1)).w;
+            ul = Su[t * W + tx - 1].w;
+        }
+        if (lane == 31 && tx + 1 < W) {
+            kr = rowv_f4<TS>(*(kv(q, t + 1) + 1)).x;
+            ur = Su[t * W + tx + 1].x;
+        }
+        // y_{k+1} on plane q
+        float4 un = f4zero();
+        if (q < g.nz && rowin) {
+            const float4 up = rowv_f4<TS>(*kv(q, t)), dn = rowv_f4<TS>(*kv(q, t + 2));
+            const float4 vkp = rowv_f4<TS>(*kv(q + 1, t + 1));
+            const float4 ypq = ykm ? rowv_f4<TS>(*mv(q)) : f4zero();
+            const float4 rq = rowv_f4<TS>(*rv(q));
+            const float left = tx == 0 ? 0.f : kl, right = x + 4 < g.nx ? kr : 0.f;
+            float d0 = d0i, d12 = d12i, d3 = d3i;
+            if (q == 0 || q + 1 == g.nz) {   // a z wall: fewer neighbours
+                const int nz_ = (q > 0) + (q + 1 < g.nz);
+                d0 = sdg[n0 + nz_];
+                d12 = sdg[n12 + nz_];
+                d3 = sdg[n3 + nz_];
+            }
+            float4 s;
+            s.x = left + vk0.y + up.x + dn.x + vkm.x + vkp.x;
+            s.y = vk0.x + vk0.z + up.y + dn.y + vkm.y + vkp.y;
+            s.z = vk0.y + vk0.w + up.z + dn.z + vkm.z + vkp.z;
+            s.w = vk0.z + right + up.w + dn.w + vkm.w + vkp.w;
+            un.x = fmaf(om1, vk0.x - ypq.x + gamma * (rq.x - fmaf(d0, vk0.x, -cf.ce * s.x)), ypq.x);
+            un.y = fmaf(om1, vk0.y - ypq.y + gamma * (rq.y - fmaf(d12, vk0.y, -cf.ce * s.y)), ypq.y);
+            un.z = fmaf(om1, vk0.z - ypq.z + gamma * (rq.z - fmaf(d12, vk0.z, -cf.ce * s.z)), ypq.z);
+            un.w = fmaf(om1, vk0.w - ypq.w + gamma * (rq.w - fmaf(d3, vk0.w, -cf.ce * s.w)), ypq.w);
+            un = as_stored<TS>(un);
+            if (inner && q >= z0 && q < z1) V::store(yc, q * g.nxy + kown, un);
+        }
+        // y_{k+2} on plane z = q-1
+        const int z = q - 1;
+        if (inner && z >= z0 && z < z1) {
+            const float4 up = Su[(t - 1) * W + tx], dn = Su[(t + 1) * W + tx];
+            const float4 rp = rowv_f4<TS>(*rv(z));
+            const float left = tx == 0 ? 0.f : ul, right = x + 4 < g.nx ? ur : 0.f;
+            float d0 = d0i, d12 = d12i, d3 = d3i;
+            if (z == 0 || z + 1 == g.nz) {
+                const int nz_ = (z > 0) + (z + 1 < g.nz);
+                d0 = sdg[n0 + nz_];
+                d12 = sdg[n12 + nz_];
+                d3 = sdg[n3 + nz_];
+            }
+            float4 s, o;
+            s.x = left + u0.y + up.x + dn.x + um.x + un.x;
+            s.y = u0.x + u0.z + up.y + dn.y + um.y + un.y;
+            s.z = u0.y + u0.w + up.z + dn.z + um.z + un.z;
+            s.w = u0.z + right + up.w + dn.w + um.w + un.w;
+            o.x = fmaf(om2, u0.x - vkm.x + gamma * (rp.x - fmaf(d0, u0.x, -cf.ce * s.x)), vkm.x);
+            o.y = fmaf(om2, u0.y - vkm.y + gamma * (rp.y - fmaf(d12, u0.y, -cf.ce * s.y)), vkm.y);
+            o.z = fmaf(om2, u0.z - vkm.z + gamma * (rp.z - fmaf(d12, u0.z, -cf.ce * s.z)), vkm.z);
+            o.w = fmaf(om2, u0.w - vkm.w + gamma * (rp.w - fmaf(d3, u0.w, -cf.ce * s.w)), vkm.w);
+            V::store(yd, z * g.nxy + kown, o);
+        }
+        __syncthreads();   // the slots step q read are refilled from step q + 1 on
+        um = u0;
+        u0 = un;
+    }
+    cp_async_wait<0>();   // no copy outlives the block
+}
+
 // ---------------------------------------------------------------- on-chip resident sweep
 constexpr int kResidentThreads = 1024;
 constexpr int kResidentMaxIters = 128;
@@ -3304,17 +3498,43 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
 }
 
 // Chebyshev iterations k and k+1 in one launch (k_cheb2_v4): zlen planes per block.
-inline bool cheb2_fits(const Geo &g) { return g.nx % 4 == 0 && g.nx <= 128; }
+inline bool cheb2_fits(const Geo &g) { return g.nx % 4 == 0 && g.nx <= kRowsMaxNx; }
 
+// The shared-memory limit of the long-row pair kernel, raised before any stream capture
+// that may launch it (a host call outside the stream; cheap, so it is simply repeated).
+template <class TS> cudaError_t rows_prepare() {
+    size_t mx = 0;
+    for (int W = 32; W <= rows_width(kRowsMaxNx); W += 32)
+        mx = std::max(mx, rows_smem<TS>(W, kRowsThreads / W - 2));
+    return cudaFuncSetAttribute(k_cheb2_rows<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+}
+
+// One launch of two iterations: rows of at most 128 cells as one warp each (k_cheb2_v4),
+// longer rows (up to 512 cells) as whole-row blocks with staged planes (k_cheb2_rows).
 template <class TS>
 void launch_cheb2(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, float om1,
                   float om2, const TS *yk, const TS *ykm, const TS *r, TS *yc, TS *yd,
                   cudaStream_t st) {
     zlen = std::max(1, std::min(zlen, g.nz));
     const int nzc = (g.nz + zlen - 1) / zlen;
-    const dim3 grid(1, (g.ny + TY2 - 1) / TY2, nzc * nf);
-    launch_chain(k_cheb2_v4<TS>, grid, dim3(32, TY2 + 2), st, g, zlen, nzc, cf, gamma, om1, om2,
-                 yk, ykm, r, yc, yd);
+    if (g.nx <= 128) {
+        const dim3 grid(1, (g.ny + TY2 - 1) / TY2, nzc * nf);
+        launch_chain(k_cheb2_v4<TS>, grid, dim3(32, TY2 + 2), st, g, zlen, nzc, cf, gamma, om1, om2,
+                     yk, ykm, r, yc, yd);
+        return;
+    }
+    const int W = rows_width(g.nx), tyr = rows_per_block(g.nx, g.ny);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, (g.ny + tyr - 1) / tyr, nzc * nf);
+    cfg.blockDim = dim3(W, tyr + 2);
+    cfg.dynamicSmemBytes = rows_smem<TS>(W, tyr);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_cheb2_rows<TS>, g, zlen, nzc, cf, gamma, om1, om2, yk, ykm, r, yc, yd);
 }
 
 // The m-1 Chebyshev iterations of a round from y1 (y_0 = 0), two per launch; a last odd
@@ -3625,6 +3845,23 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     if (sizeof(TS) == 4 && tma_sweep_fits(g)) {        // TMA-staged sweep: FP32 storage
         tma_prepare();
         for (int c : {401, 402, 404, 408}) cands.push_back({c, 10});
+    }
+    if (cheb2_fits(g) && g.per == 0) {   // two iterations per launch: five launches make ten
+        std::vector<int> zs = {8, 16, 32};
+        if (g.nx > 128) {   // long rows: one block per SM, so also a chunk that fills two waves
+            int sms = 0;
+            CGK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            const int tyr = rows_per_block(g.nx, g.ny);
+            const int yb = ((g.ny + tyr - 1) / tyr) * nf;
+            const int nzc = std::max(1, 2 * sms / yb);
+            zs.push_back((g.nz + nzc - 1) / nzc);
+        }
+        for (int z : zs) {
+            const int c = kPairCode + std::max(1, std::min({z, g.nz, 99}));
+            bool dup = false;
+            for (auto &cd : cands) dup = dup || cd.first == c;
+            if (!dup) cands.push_back({c, 5});
+        }
     }
     // per shape: 10 iterations captured as a CUDA graph (as the solver runs them) and
     // replayed once to warm up; then three rounds that replay every shape in turn, each
@@ -4120,14 +4357,17 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
             return fail(CG_EINVAL, "sweep_shape %d needs FP32 inner storage, nx %% 4 == 0, no periodic axis and "
                         "1..99 planes", cheb_code);
         if (cheb_code >= kPairCode && cheb_code < kResidentCode && (!cheb2_fits(g) || cheb_code - kPairCode < 1))
-            return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0, nx <= 128 and 1..99 planes",
-                        cheb_code);
+            return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0, nx <= %d and 1..99 planes",
+                        cheb_code, kRowsMaxNx);
         if (cheb_code >= 100 && cheb_code < kPairCode && (m->nx % 4 != 0 || cheb_code - 100 < 1))
             return fail(CG_EINVAL, "sweep_shape %d needs nx %% 4 == 0 and 1..99 planes", cheb_code);
         if (cheb_code != 0 && cheb_code != 2 && cheb_code != 4 && cheb_code != 8 && cheb_code > -1 &&
             cheb_code < 100)
             return fail(CG_EINVAL, "unknown sweep_shape %d", cheb_code);
         const bool auto_shape = cheb_code == 0;
+        // (before any capture that may launch the long-row pair kernel)
+        if (auto_shape || (cheb_code >= kPairCode && cheb_code < kResidentCode))
+            CGK_CUDA(rows_prepare<TS>());
         if (auto_shape) CGK_TRY(tune_cheb<TS>(m, g, nf, cf32, Ya, Yb, Yc, Yd, R, st, &cheb_code));
         if (auto_shape && rp.ok)
             CGK_TRY(tune_resident<TS>(m, g, rp, cheb_code, m_it, cf32, Ya, Yb, Yc, Yd, R, rws, st,

@@ -1,5 +1,6 @@
 """GPU parity of the two-iterations-per-launch Chebyshev sweep (sweep_shape 200 + z:
-iterations k and k+1 in one launch, rows of at most 128 cells, z planes per block).
+iterations k and k+1 in one launch, z planes per block; rows of at most 128 cells as one
+warp each, longer rows, up to 512 cells, as whole-row blocks with staged planes).
 
 Per cell it evaluates the same expression, in the same order, as the one-iteration
 vectorised sweep (sweep_shape 100 + z), so with the same z the two must agree bit for
@@ -111,8 +112,51 @@ def test_pairs_full_size_clustered_128(cg, orc):
     assert maxrel(outs[208], ref) <= MIXED_TOL
 
 
+# long rows: two warps (256), a second warp one lane wide (132), three and four warps with
+# idle lanes (388) and full (512); ragged last row block (ny not a multiple of the rows per
+# block: 6 at 512, 8 at 388, 14 at 256, 14 at 132); one plane per block, odd chunks, whole mesh
+@pytest.mark.parametrize("dims", [(256, 20, 13), (132, 17, 9), (388, 11, 6), (512, 14, 7)])
+@pytest.mark.parametrize("z", [1, 3, 16])
+@pytest.mark.parametrize("b_over_dx", [1, 3])
+def test_pairs_long_rows_bit_identical_to_single_sweep(cg, orc, dims, z, b_over_dx):
+    dx = 1.0 / dims[0]
+    u0 = field((2, int(np.prod(dims))), 53)
+    T = (b_over_dx * dx) ** 2 / 4
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx)
+    outs = {}
+    for shape in (200 + z, 100 + z):
+        u = dev(u0)
+        _, rep = cg.diffuse(mesh, u, cg.Params(T=T, nsteps=4, precision=3, sweep_shape=shape),
+                            report=True)
+        assert rep["sweep_shape_used"] == shape
+        assert rep["final_rel_residual"] <= 1e-13
+        outs[shape] = u.cpu().numpy()
+    assert np.array_equal(bits(outs[200 + z]), bits(outs[100 + z]))
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 4, tol=1e-15)
+    assert maxrel(outs[200 + z], ref) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,scheme", [(1, 0), (4, 0), (3, 1)])
+def test_pairs_long_rows_other_modes_bit_identical(cg, orc, precision, scheme):
+    """Long rows in IEEE-FP64 refinement, BF16 storage and Crank-Nicolson."""
+    dims = (320, 24, 10)
+    dx = 1.0 / 320
+    u0 = field((1, int(np.prod(dims))), 54)
+    T = (6 * dx) ** 2 / 4
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx)
+    outs = {}
+    for shape in (205, 105):
+        u = dev(u0)
+        cg.diffuse(mesh, u, cg.Params(T=T, nsteps=5, precision=precision, scheme=scheme,
+                                      sweep_shape=shape))
+        outs[shape] = u.cpu().numpy()
+    assert np.array_equal(bits(outs[205]), bits(outs[105]))
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 5, scheme=scheme, tol=1e-15)
+    assert maxrel(outs[205], ref) <= MIXED_TOL
+
+
 def test_pairs_reject_long_rows(cg):
-    for dims in ((132, 8, 8), (30, 8, 8)):
+    for dims in ((516, 8, 8), (30, 8, 8)):
         mesh = cg.StructuredMesh(dims, (0, 0, 0), 1.0 / dims[0])
         with pytest.raises(cg.CGError) as e:
             cg.diffuse(mesh, dev(np.zeros((1, int(np.prod(dims))))),

@@ -129,8 +129,8 @@ def test_autotuned_shape_is_reported(cg):
     u = dev(field((64, 64, 64), 42)[None])
     _, rep = cg.diffuse(mesh, u, cg.Params(bandwidth=3 / 64, precision=3), report=True)
     s = rep["sweep_shape_used"]
-    assert (s == RESIDENT or 101 <= s <= 116 or 201 <= s <= 216 or s in (2, 4, 8)
-            or -32 <= s <= -1)
+    assert (s == RESIDENT or 101 <= s <= 199 or 201 <= s <= 299 or 401 <= s <= 499
+            or s in (2, 4, 8) or -32 <= s <= -1)
 
 
 def test_resident_wait_budget_gives_etimeout_and_context_survives(cg):
