@@ -2070,7 +2070,8 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
     const bool hhi = t == TY2 + 1 && y0 + TY2 + 1 < g.ny && ownx;  // also loads row y0+TY2+1
     const int nyb = (y > 0) + (y + 1 < g.ny);
     const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx), n12 = nyb + 2;
-    auto at = [&](int q, int yy) -> size_t { return ((size_t)q * g.ny + yy) * g.nx + x; };
+    // 32-bit offsets within a field (a field has fewer than 2^31 cells)
+    auto at = [&](int q, int yy) -> int { return (q * g.ny + yy) * g.nx + x; };
     const int qs = max(z0 - 1, 0);
     // queues at q = qs
     float4 vkm = f4zero(), vk0 = f4zero(), vkp = f4zero(), hk = f4zero();
@@ -2084,6 +2085,9 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
     }
     if (hlo) hk = V::load(yk, at(qs, y0 - 2));
     if (hhi) hk = V::load(yk, at(qs, y0 + TY2 + 1));
+    __syncthreads();   // the diagonal table
+    // diagonals of the four cells on planes with both z neighbours (most planes)
+    const float d0i = sdg[n0 + 2], d12i = sdg[n12 + 2], d3i = sdg[n3 + 2];
     float4 um = f4zero(), u0 = f4zero();
     for (int q = qs; q <= z1; ++q) {
         // loads for plane q+1 (y_k two planes ahead)
@@ -2112,16 +2116,22 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
         if (q < g.nz && rowin) {
             const float4 up = Sk[t][tx], dn = Sk[t + 2][tx];
             const float left = tx == 0 ? 0.f : kl, right = x + 4 < g.nx ? kr : 0.f;
-            const int nz_ = (q > 0) + (q + 1 < g.nz);
+            float d0 = d0i, d12 = d12i, d3 = d3i;
+            if (q == 0 || q + 1 == g.nz) {   // a z wall: fewer neighbours
+                const int nz_ = (q > 0) + (q + 1 < g.nz);
+                d0 = sdg[n0 + nz_];
+                d12 = sdg[n12 + nz_];
+                d3 = sdg[n3 + nz_];
+            }
             float4 s;
             s.x = left + vk0.y + up.x + dn.x + vkm.x + vkp.x;
             s.y = vk0.x + vk0.z + up.y + dn.y + vkm.y + vkp.y;
             s.z = vk0.y + vk0.w + up.z + dn.z + vkm.z + vkp.z;
             s.w = vk0.z + right + up.w + dn.w + vkm.w + vkp.w;
-            un.x = fmaf(om1, vk0.x - ypq.x + gamma * (rq.x - fmaf(sdg[n0 + nz_], vk0.x, -cf.ce * s.x)), ypq.x);
-            un.y = fmaf(om1, vk0.y - ypq.y + gamma * (rq.y - fmaf(sdg[n12 + nz_], vk0.y, -cf.ce * s.y)), ypq.y);
-            un.z = fmaf(om1, vk0.z - ypq.z + gamma * (rq.z - fmaf(sdg[n12 + nz_], vk0.z, -cf.ce * s.z)), ypq.z);
-            un.w = fmaf(om1, vk0.w - ypq.w + gamma * (rq.w - fmaf(sdg[n3 + nz_], vk0.w, -cf.ce * s.w)), ypq.w);
+            un.x = fmaf(om1, vk0.x - ypq.x + gamma * (rq.x - fmaf(d0, vk0.x, -cf.ce * s.x)), ypq.x);
+            un.y = fmaf(om1, vk0.y - ypq.y + gamma * (rq.y - fmaf(d12, vk0.y, -cf.ce * s.y)), ypq.y);
+            un.z = fmaf(om1, vk0.z - ypq.z + gamma * (rq.z - fmaf(d12, vk0.z, -cf.ce * s.z)), ypq.z);
+            un.w = fmaf(om1, vk0.w - ypq.w + gamma * (rq.w - fmaf(d3, vk0.w, -cf.ce * s.w)), ypq.w);
             un = as_stored<TS>(un);
             if (inner && q >= z0 && q < z1) V::store(yc, at(q, y), un);
         }
@@ -2130,16 +2140,22 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
         if (inner && z >= z0 && z < z1) {
             const float4 up = Su[t - 1][tx], dn = Su[t + 1][tx];
             const float left = tx == 0 ? 0.f : ul, right = x + 4 < g.nx ? ur : 0.f;
-            const int nz_ = (z > 0) + (z + 1 < g.nz);
+            float d0 = d0i, d12 = d12i, d3 = d3i;
+            if (z == 0 || z + 1 == g.nz) {
+                const int nz_ = (z > 0) + (z + 1 < g.nz);
+                d0 = sdg[n0 + nz_];
+                d12 = sdg[n12 + nz_];
+                d3 = sdg[n3 + nz_];
+            }
             float4 s, o;
             s.x = left + u0.y + up.x + dn.x + um.x + un.x;
             s.y = u0.x + u0.z + up.y + dn.y + um.y + un.y;
             s.z = u0.y + u0.w + up.z + dn.z + um.z + un.z;
             s.w = u0.z + right + up.w + dn.w + um.w + un.w;
-            o.x = fmaf(om2, u0.x - vkm.x + gamma * (rprev.x - fmaf(sdg[n0 + nz_], u0.x, -cf.ce * s.x)), vkm.x);
-            o.y = fmaf(om2, u0.y - vkm.y + gamma * (rprev.y - fmaf(sdg[n12 + nz_], u0.y, -cf.ce * s.y)), vkm.y);
-            o.z = fmaf(om2, u0.z - vkm.z + gamma * (rprev.z - fmaf(sdg[n12 + nz_], u0.z, -cf.ce * s.z)), vkm.z);
-            o.w = fmaf(om2, u0.w - vkm.w + gamma * (rprev.w - fmaf(sdg[n3 + nz_], u0.w, -cf.ce * s.w)), vkm.w);
+            o.x = fmaf(om2, u0.x - vkm.x + gamma * (rprev.x - fmaf(d0, u0.x, -cf.ce * s.x)), vkm.x);
+            o.y = fmaf(om2, u0.y - vkm.y + gamma * (rprev.y - fmaf(d12, u0.y, -cf.ce * s.y)), vkm.y);
+            o.z = fmaf(om2, u0.z - vkm.z + gamma * (rprev.z - fmaf(d12, u0.z, -cf.ce * s.z)), vkm.z);
+            o.w = fmaf(om2, u0.w - vkm.w + gamma * (rprev.w - fmaf(d3, u0.w, -cf.ce * s.w)), vkm.w);
             V::store(yd, at(z, y), o);
         }
         __syncthreads();
@@ -3846,9 +3862,12 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
         tma_prepare();
         for (int c : {401, 402, 404, 408}) cands.push_back({c, 10});
     }
-    if (cheb2_fits(g) && g.per == 0) {   // two iterations per launch: five launches make ten
+    // two iterations per launch (five launches make ten) where the rows are longer than one
+    // warp holds: there a sweep leaves L2 sooner and the whole-row kernel halves its traffic
+    // (on rows of a warp, where the working set stays in L2, whole solves measured no gain)
+    if (cheb2_fits(g) && g.per == 0 && g.nx > 128) {
         std::vector<int> zs = {8, 16, 32};
-        if (g.nx > 128) {   // long rows: one block per SM, so also a chunk that fills two waves
+        {   // one block per SM, so also a chunk that fills two waves
             int sms = 0;
             CGK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             const int tyr = rows_per_block(g.nx, g.ny);
