@@ -163,8 +163,9 @@ typedef struct {
                            (needs nx % 4 == 0); 2, 4, 8 = register-blocked planes per
                            block; -z = z-marching, z planes per block; 200 + z = two
                            iterations per launch (temporal blocking), z planes per block
-                           (nx % 4 == 0, nx <= 512, no periodic axis; the same results
-                           as 100 + z; the autotuner also weighs it); 300 = resident:
+                           (nx % 4 == 0, nx <= 512, no periodic axis but x; the same
+                           results as 100 + z; the autotuner also weighs it on rows over
+                           128 cells); 300 = resident:
                            each round's inner solve in one cooperative launch that keeps
                            the mesh in the SMs' shared memory (one field, nx % 4 == 0, a
                            mesh that fits; the autotuner also weighs it); 400 + z =

@@ -2185,7 +2185,8 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
 // memory a block of 1024 threads fits the 64-register budget, one block per SM.  Per
 // cell the arithmetic and its order are those of k_cheb_v4, so the iterates are
 // bit-identical.  It pays where the sweep is bound by HBM: two iterations move 20 bytes
-// per cell (three reads, two writes) instead of 32.
+// per cell (three reads, two writes) instead of 32.  A periodic x axis wraps within the
+// block's rows (y and z must be walls).
 constexpr int kRowsThreads = 1024;
 constexpr int kRowsMaxNx = 512;
 
@@ -2252,8 +2253,12 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
     const int yh = t == 0 ? y0 - 2 : y0 + TYR + 1;
     const bool hin = hrow && yh >= 0 && yh < g.ny && ownx;
     const int hslot = t == 0 ? 0 : KR - 1;
+    // a periodic x axis (the only periodic axis this kernel takes): a row's first and last
+    // cells are neighbours, both held by the block
+    const bool px = (g.per & 1) != 0;
+    const int xlast = g.nx / 4 - 1;   // the thread holding a row's last four cells
     const int nyb = (y > 0) + (y + 1 < g.ny);
-    const int n0 = nyb + (x > 0) + 1, n3 = nyb + 1 + (x + 4 < g.nx), n12 = nyb + 2;
+    const int n0 = nyb + (px || x > 0) + 1, n3 = nyb + 1 + (px || x + 4 < g.nx), n12 = nyb + 2;
     // 32-bit offsets within a field (a field has fewer than 2^31 cells)
     const int kown = rowin ? y * g.nx + x : 0, khalo = hin ? yh * g.nx + x : 0;
     const int KW = KR * W, MW = MR * W;
@@ -2307,6 +2312,14 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
             kr = rowv_f4<TS>(*(kv(q, t + 1) + 1)).x;
             ur = Su[t * W + tx + 1].x;
         }
+        if (px && tx == 0) {       // cell nx - 1
+            kl = rowv_f4<TS>(*(kv(q, t + 1) + xlast)).w;
+            ul = Su[t * W + xlast].w;
+        }
+        if (px && tx == xlast) {   // cell 0
+            kr = rowv_f4<TS>(*(kv(q, t + 1) - tx)).x;
+            ur = Su[t * W].x;
+        }
         // y_{k+1} on plane q
         float4 un = f4zero();
         if (q < g.nz && rowin) {
@@ -2314,7 +2327,7 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
             const float4 vkp = rowv_f4<TS>(*kv(q + 1, t + 1));
             const float4 ypq = ykm ? rowv_f4<TS>(*mv(q)) : f4zero();
             const float4 rq = rowv_f4<TS>(*rv(q));
-            const float left = tx == 0 ? 0.f : kl, right = x + 4 < g.nx ? kr : 0.f;
+            const float left = (px || tx > 0) ? kl : 0.f, right = (px || x + 4 < g.nx) ? kr : 0.f;
             float d0 = d0i, d12 = d12i, d3 = d3i;
             if (q == 0 || q + 1 == g.nz) {   // a z wall: fewer neighbours
                 const int nz_ = (q > 0) + (q + 1 < g.nz);
@@ -2339,7 +2352,7 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
         if (inner && z >= z0 && z < z1) {
             const float4 up = Su[(t - 1) * W + tx], dn = Su[(t + 1) * W + tx];
             const float4 rp = rowv_f4<TS>(*rv(z));
-            const float left = tx == 0 ? 0.f : ul, right = x + 4 < g.nx ? ur : 0.f;
+            const float left = (px || tx > 0) ? ul : 0.f, right = (px || x + 4 < g.nx) ? ur : 0.f;
             float d0 = d0i, d12 = d12i, d3 = d3i;
             if (z == 0 || z + 1 == g.nz) {
                 const int nz_ = (z > 0) + (z + 1 < g.nz);
@@ -3514,7 +3527,9 @@ void launch_cheb(int code, const Geo &g, int nf, const Coef32 &cf, float gamma, 
 }
 
 // Chebyshev iterations k and k+1 in one launch (k_cheb2_v4): zlen planes per block.
-inline bool cheb2_fits(const Geo &g) { return g.nx % 4 == 0 && g.nx <= kRowsMaxNx; }
+inline bool cheb2_fits(const Geo &g) {
+    return g.nx % 4 == 0 && g.nx <= kRowsMaxNx && (g.per & ~1) == 0;   // periodic: x only
+}
 
 // The shared-memory limit of the long-row pair kernel, raised before any stream capture
 // that may launch it (a host call outside the stream; cheap, so it is simply repeated).
@@ -3526,14 +3541,15 @@ template <class TS> cudaError_t rows_prepare() {
 }
 
 // One launch of two iterations: rows of at most 128 cells as one warp each (k_cheb2_v4),
-// longer rows (up to 512 cells) as whole-row blocks with staged planes (k_cheb2_rows).
+// longer rows (up to 512 cells) and x-periodic meshes as whole-row blocks with staged
+// planes (k_cheb2_rows).
 template <class TS>
 void launch_cheb2(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma, float om1,
                   float om2, const TS *yk, const TS *ykm, const TS *r, TS *yc, TS *yd,
                   cudaStream_t st) {
     zlen = std::max(1, std::min(zlen, g.nz));
     const int nzc = (g.nz + zlen - 1) / zlen;
-    if (g.nx <= 128) {
+    if (g.nx <= 128 && g.per == 0) {
         const dim3 grid(1, (g.ny + TY2 - 1) / TY2, nzc * nf);
         launch_chain(k_cheb2_v4<TS>, grid, dim3(32, TY2 + 2), st, g, zlen, nzc, cf, gamma, om1, om2,
                      yk, ykm, r, yc, yd);
@@ -3865,15 +3881,26 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
     // two iterations per launch (five launches make ten) where the rows are longer than one
     // warp holds: there a sweep leaves L2 sooner and the whole-row kernel halves its traffic
     // (on rows of a warp, where the working set stays in L2, whole solves measured no gain)
-    if (cheb2_fits(g) && g.per == 0 && g.nx > 128) {
+    if (cheb2_fits(g) && g.nx > 128) {
         std::vector<int> zs = {8, 16, 32};
-        {   // one block per SM, so also a chunk that fills two waves
+        {   // one block per SM, so also the chunk that minimises waves of blocks x planes a
+            // block marches (its chunk and the plane either side)
             int sms = 0;
             CGK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             const int tyr = rows_per_block(g.nx, g.ny);
-            const int yb = ((g.ny + tyr - 1) / tyr) * nf;
-            const int nzc = std::max(1, 2 * sms / yb);
-            zs.push_back((g.nz + nzc - 1) / nzc);
+            const long long yb = (long long)((g.ny + tyr - 1) / tyr) * nf;
+            int best_z = g.nz;
+            long long best_cost = -1;
+            for (int c = 1; c <= g.nz; ++c) {
+                const int zc = (g.nz + c - 1) / c;
+                const long long blocks = yb * ((g.nz + zc - 1) / zc);
+                const long long cost = (blocks + sms - 1) / sms * (zc + 2);
+                if (best_cost < 0 || cost < best_cost) {
+                    best_cost = cost;
+                    best_z = zc;
+                }
+            }
+            zs.push_back(best_z);
         }
         for (int z : zs) {
             const int c = kPairCode + std::max(1, std::min({z, g.nz, 99}));
@@ -4359,9 +4386,11 @@ static cg_status diffuse_mixed(cg_mesh *m, int nf, double *cells, const cg_param
 
     int cheb_code = p->sweep_shape;
     bool resident = false;
-    if (m->per && cheb_code > 0 && !(cheb_code >= 100 && cheb_code < kPairCode))
+    if (m->per && cheb_code > 0 && !(cheb_code >= 100 && cheb_code < kPairCode) &&
+        !(m->per == 1 && cheb_code >= kPairCode && cheb_code < kResidentCode))
         return fail(CG_EINVAL, "sweep_shape %d: with periodic axes only the z-marching and vectorised "
-                    "sweeps (sweep_shape < 0 or 100 + z, or 0 for autotuning) apply", cheb_code);
+                    "sweeps (sweep_shape < 0 or 100 + z, or 0 for autotuning) apply, and two "
+                    "iterations per launch (200 + z) with x the only periodic axis", cheb_code);
     if (cheb_code == kResidentCode) {
         if (!rp.ok)
             return fail(CG_EINVAL, "sweep_shape %d needs one field, nx %% 4 == 0, at most %d inner "

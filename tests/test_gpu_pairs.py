@@ -155,6 +155,29 @@ def test_pairs_long_rows_other_modes_bit_identical(cg, orc, precision, scheme):
     assert maxrel(outs[205], ref) <= MIXED_TOL
 
 
+# a periodic x axis: whole-row blocks wrap the row within the block (rows of 4, 36, 132,
+# 256 and 512 cells; two fields, one of them signed)
+@pytest.mark.parametrize("dims", [(4, 6, 5), (36, 13, 7), (132, 9, 6), (256, 15, 5), (512, 8, 6)])
+@pytest.mark.parametrize("z", [1, 4])
+def test_pairs_periodic_x_bit_identical_to_single_sweep(cg, orc, dims, z):
+    rng = np.random.default_rng(57)
+    n = int(np.prod(dims))
+    u0 = np.vstack([rng.random(n), rng.random(n) - 0.4])
+    dx = 1.0 / dims[0]
+    T = (3 * dx) ** 2 / 4
+    mesh = cg.StructuredMesh(dims, (0, 0, 0), dx, periodic=(True, False, False))
+    outs = {}
+    for shape in (200 + z, 100 + z):
+        u = dev(u0)
+        _, rep = cg.diffuse(mesh, u, cg.Params(T=T, nsteps=4, precision=3, sweep_shape=shape),
+                            report=True)
+        assert rep["sweep_shape_used"] == shape
+        outs[shape] = u.cpu().numpy()
+    assert np.array_equal(bits(outs[200 + z]), bits(outs[100 + z]))
+    ref, _ = orc.diffuse_structured(u0, dims, dx, T, 4, tol=1e-15, periodic=(True, False, False))
+    assert maxrel(outs[200 + z], ref) <= MIXED_TOL
+
+
 def test_pairs_reject_long_rows(cg):
     for dims in ((516, 8, 8), (30, 8, 8)):
         mesh = cg.StructuredMesh(dims, (0, 0, 0), 1.0 / dims[0])

@@ -81,8 +81,8 @@ def test_periodic_other_schemes(cg, orc, scheme):
 
 def test_periodic_shapes_and_reset(cg):
     """Shapes other than the z-marching and vectorised sweeps are refused on a periodic
-    mesh; clearing the periodic axes restores the wall results bit for bit (cached
-    schedules are dropped)."""
+    mesh (two iterations per launch only take a periodic x axis); clearing the periodic
+    axes restores the wall results bit for bit (cached schedules are dropped)."""
     dims = (32, 24, 16)
     rng = np.random.default_rng(72)
     u0 = rng.random((1, int(np.prod(dims))))
