@@ -2179,10 +2179,12 @@ __global__ void __launch_bounds__(kCheb2Threads, 2)
 // come from the adjacent lanes by shuffle, and across a warp boundary from the staged
 // plane.  Instead of a register queue, y_k, y_{k-1} and r of the planes ahead are staged
 // in shared-memory rings by cp.async one plane ahead of the march: y_k in four slots
-// (planes q-1 .. q+2, all TYR + 4 rows), y_{k-1} in two (q, q+1), r in three (q-1 ..
-// q+1); planes and rows outside the mesh are staged as zeros.  A slot is refilled only
-// after the barrier that ends the step which last read it.  With the queue in shared
-// memory a block of 1024 threads fits the 64-register budget, one block per SM.  Per
+// (planes q-1 .. q+2, all TYR + 4 rows), y_{k-1} in two (q, q+1), r in four (three in use,
+// q-1 .. q+1); planes and rows outside the mesh are staged as zeros.  A slot is refilled
+// only after the barrier that ends the step which last read it.  The row width W is a
+// template parameter and the march is unrolled by four, so every slot offset is a
+// constant.  With the queue in shared memory a block of 1024 threads fits the
+// 64-register budget, one block per SM.  Per
 // cell the arithmetic and its order are those of k_cheb_v4, so the iterates are
 // bit-identical.  It pays where the sweep is bound by HBM: two iterations move 20 bytes
 // per cell (three reads, two writes) instead of 32.  A periodic x axis wraps within the
@@ -2212,12 +2214,12 @@ template <class TS> __device__ __forceinline__ void rowv_stage(RowV<TS> *dst, co
 }
 // threads per row, rows per block and dynamic shared memory of a launch
 __host__ __device__ inline int rows_width(int nx) { return ((nx / 4 + 31) / 32) * 32; }
-inline int rows_per_block(int nx, int ny) { return std::max(1, std::min(kRowsThreads / rows_width(nx) - 2, ny)); }
+inline int rows_per_block(int nx) { return kRowsThreads / rows_width(nx) - 2; }
 template <class TS> inline size_t rows_smem(int W, int tyr) {
-    return (size_t)W * ((size_t)(4 * (tyr + 4) + 5 * (tyr + 2)) * sizeof(RowV<TS>) + (size_t)(tyr + 2) * 16);
+    return (size_t)W * ((size_t)(4 * (tyr + 4) + 6 * (tyr + 2)) * sizeof(RowV<TS>) + (size_t)(tyr + 2) * 16);
 }
 
-template <class TS>
+template <class TS, int W>
 __global__ void __launch_bounds__(kRowsThreads, 1)
     k_cheb2_rows(Geo g, int zlen, int nzc, Coef32 cf, float gamma, float om1, float om2,
                  const TS *__restrict__ yk_all, const TS *__restrict__ ykm_all,
@@ -2229,12 +2231,12 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
     extern __shared__ __align__(16) unsigned char rows_sm[];
     __shared__ float sdg[8];
     stage_table(sdg, cf.dg);
-    const int W = blockDim.x, TYR = blockDim.y - 2;
-    const int KR = TYR + 4, MR = TYR + 2;
+    constexpr int TYR = kRowsThreads / W - 2;   // rows written per block
+    constexpr int KR = TYR + 4, MR = TYR + 2;
     RV *Kr = reinterpret_cast<RV *>(rows_sm);                   // y_k    [4][KR][W]
     RV *Mr = Kr + 4 * KR * W;                                   // y_{k-1} [2][MR][W]
-    RV *Rr = Mr + 2 * MR * W;                                   // r      [3][MR][W]
-    float4 *Su = reinterpret_cast<float4 *>(Rr + 3 * MR * W);   // y_{k+1} of plane q-1 [MR][W]
+    RV *Rr = Mr + 2 * MR * W;                                   // r      [4][MR][W]
+    float4 *Su = reinterpret_cast<float4 *>(Rr + 4 * MR * W);   // y_{k+1} of plane q-1 [MR][W]
     const int f = blockIdx.z / nzc;
     const int z0 = (blockIdx.z - f * nzc) * zlen, z1 = min(g.nz, z0 + zlen);
     const size_t off = (size_t)f * g.n;
@@ -2261,72 +2263,82 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
     const int n0 = nyb + (px || x > 0) + 1, n3 = nyb + 1 + (px || x + 4 < g.nx), n12 = nyb + 2;
     // 32-bit offsets within a field (a field has fewer than 2^31 cells)
     const int kown = rowin ? y * g.nx + x : 0, khalo = hin ? yh * g.nx + x : 0;
-    const int KW = KR * W, MW = MR * W;
-    auto kv = [&](int q, int row) -> RV * { return Kr + (q & 3) * KW + row * W + tx; };
-    auto mv = [&](int q) -> RV * { return Mr + (q & 1) * MW + t * W + tx; };
-    auto rv = [&](int q) -> RV * { return Rr + (q % 3) * MW + t * W + tx; };
-    // staging of plane p: y_k up to plane z1 + 1, y_{k-1} and r up to plane z1 (p >= -1)
-    auto stage_k = [&](int p) {
+    constexpr int KW = KR * W, MW = MR * W;
+    // ring slots: plane p sits in slot (p - qs + 1) mod 4 of the y_k and r rings and mod 2 of
+    // the y_{k-1} ring; the march is unrolled by four, so every slot index is a constant
+    const int qs = max(z0 - 1, 0);
+    RV *const kown_s = Kr + (t + 1) * W + tx;   // this thread's row in slot 0 of the y_k ring
+    RV *const mown_s = Mr + t * W + tx;
+    RV *const rown_s = Rr + t * W + tx;
+    // staging of plane p (slot s): y_k up to plane z1 + 1, y_{k-1} and r up to plane z1
+    auto stage_k = [&](int p, int sl) __attribute__((always_inline)) {
         if (p > z1 + 1) return;
         const bool pin = p >= 0 && p < g.nz;
         const int kp = pin ? p * g.nxy : 0;
-        rowv_stage<TS>(kv(p, t + 1), yk + (kp + kown), pin && rowin);
-        if (hrow) rowv_stage<TS>(kv(p, hslot), yk + (kp + khalo), pin && hin);
+        rowv_stage<TS>(kown_s + sl * KW, yk + (kp + kown), pin && rowin);
+        if (hrow) rowv_stage<TS>(Kr + sl * KW + hslot * W + tx, yk + (kp + khalo), pin && hin);
     };
-    auto stage_mr = [&](int p) {
+    auto stage_mr = [&](int p, int sm, int sr) __attribute__((always_inline)) {
         if (p > z1) return;
         const bool ok = p < g.nz && rowin;
         const int kp = (ok ? p * g.nxy : 0) + kown;
-        if (ykm) rowv_stage<TS>(mv(p), ykm + kp, ok);
-        rowv_stage<TS>(rv(p), r + kp, ok);
+        if (ykm) rowv_stage<TS>(mown_s + sm * MW, ykm + kp, ok);
+        rowv_stage<TS>(rown_s + sr * MW, r + kp, ok);
     };
-    const int qs = max(z0 - 1, 0);
-    stage_k(qs - 1);
-    stage_k(qs);
-    stage_k(qs + 1);
-    stage_mr(qs);
+    stage_k(qs - 1, 0);
+    stage_k(qs, 1);
+    stage_k(qs + 1, 2);
+    stage_mr(qs, 1, 1);
     cp_async_commit();
     __syncthreads();   // the diagonal table
     // diagonals of the four cells on planes with both z neighbours (most planes)
     const float d0i = sdg[n0 + 2], d12i = sdg[n12 + 2], d3i = sdg[n3 + 2];
+    // y_{k+1} of planes q - 2 and q - 1
     float4 um = f4zero(), u0 = f4zero();
-    for (int q = qs; q <= z1; ++q) {
-        stage_k(q + 2);
-        stage_mr(q + 1);
+    // step q (the march's step j of four, j = (q - qs) mod 4): y_{k+1} on plane q, y_{k+2} on
+    // plane q - 1
+    auto step = [&](const int q, auto jc) __attribute__((always_inline)) {
+        constexpr int j = decltype(jc)::value;
+        constexpr int sk_m = j, sk_0 = (j + 1) & 3, sk_p = (j + 2) & 3, sk_pp = (j + 3) & 3;
+        constexpr int sm_0 = (j + 1) & 1, sm_p = j & 1;
+        constexpr int sr_m = j, sr_0 = (j + 1) & 3, sr_p = (j + 2) & 3;
+        stage_k(q + 2, sk_pp);
+        stage_mr(q + 1, sm_p, sr_p);
         cp_async_commit();
         cp_async_wait<1>();   // this thread's copies of the planes step q reads
         Su[t * W + tx] = u0;
         __syncthreads();
-        const float4 vk0 = rowv_f4<TS>(*kv(q, t + 1));
-        const float4 vkm = rowv_f4<TS>(*kv(q - 1, t + 1));
+        RV *const k0 = kown_s + sk_0 * KW;   // this thread's vector of plane q
+        const float4 vk0 = rowv_f4<TS>(*k0);
+        const float4 vkm = rowv_f4<TS>(*(kown_s + sk_m * KW));
         // x neighbours of y_k (plane q) and of y_{k+1} (plane q-1): lanes, or across a warp
         float kl = __shfl_up_sync(0xffffffffu, vk0.w, 1);
         float kr = __shfl_down_sync(0xffffffffu, vk0.x, 1);
         float ul = __shfl_up_sync(0xffffffffu, u0.w, 1);
         float ur = __shfl_down_sync(0xffffffffu, u0.x, 1);
         if (lane == 0 && tx > 0) {
-            kl = rowv_f4<TS>(*(kv(q, t + 1) - 1)).w;
+            kl = rowv_f4<TS>(*(k0 - 1)).w;
             ul = Su[t * W + tx - 1].w;
         }
         if (lane == 31 && tx + 1 < W) {
-            kr = rowv_f4<TS>(*(kv(q, t + 1) + 1)).x;
+            kr = rowv_f4<TS>(*(k0 + 1)).x;
             ur = Su[t * W + tx + 1].x;
         }
         if (px && tx == 0) {       // cell nx - 1
-            kl = rowv_f4<TS>(*(kv(q, t + 1) + xlast)).w;
+            kl = rowv_f4<TS>(*(k0 + xlast)).w;
             ul = Su[t * W + xlast].w;
         }
         if (px && tx == xlast) {   // cell 0
-            kr = rowv_f4<TS>(*(kv(q, t + 1) - tx)).x;
+            kr = rowv_f4<TS>(*(k0 - tx)).x;
             ur = Su[t * W].x;
         }
         // y_{k+1} on plane q
         float4 un = f4zero();
         if (q < g.nz && rowin) {
-            const float4 up = rowv_f4<TS>(*kv(q, t)), dn = rowv_f4<TS>(*kv(q, t + 2));
-            const float4 vkp = rowv_f4<TS>(*kv(q + 1, t + 1));
-            const float4 ypq = ykm ? rowv_f4<TS>(*mv(q)) : f4zero();
-            const float4 rq = rowv_f4<TS>(*rv(q));
+            const float4 up = rowv_f4<TS>(*(k0 - W)), dn = rowv_f4<TS>(*(k0 + W));
+            const float4 vkp = rowv_f4<TS>(*(kown_s + sk_p * KW));
+            const float4 ypq = ykm ? rowv_f4<TS>(*(mown_s + sm_0 * MW)) : f4zero();
+            const float4 rq = rowv_f4<TS>(*(rown_s + sr_0 * MW));
             const float left = (px || tx > 0) ? kl : 0.f, right = (px || x + 4 < g.nx) ? kr : 0.f;
             float d0 = d0i, d12 = d12i, d3 = d3i;
             if (q == 0 || q + 1 == g.nz) {   // a z wall: fewer neighbours
@@ -2351,7 +2363,7 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
         const int z = q - 1;
         if (inner && z >= z0 && z < z1) {
             const float4 up = Su[(t - 1) * W + tx], dn = Su[(t + 1) * W + tx];
-            const float4 rp = rowv_f4<TS>(*rv(z));
+            const float4 rp = rowv_f4<TS>(*(rown_s + sr_m * MW));
             const float left = (px || tx > 0) ? ul : 0.f, right = (px || x + 4 < g.nx) ? ur : 0.f;
             float d0 = d0i, d12 = d12i, d3 = d3i;
             if (z == 0 || z + 1 == g.nz) {
@@ -2374,6 +2386,16 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
         __syncthreads();   // the slots step q read are refilled from step q + 1 on
         um = u0;
         u0 = un;
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    for (int q = qs; q <= z1; q += 4) {
+        step(q, I0{});
+        if (q + 1 <= z1) step(q + 1, I1{});
+        if (q + 2 <= z1) step(q + 2, I2{});
+        if (q + 3 <= z1) step(q + 3, I3{});
     }
     cp_async_wait<0>();   // no copy outlives the block
 }
@@ -3534,10 +3556,17 @@ inline bool cheb2_fits(const Geo &g) {
 // The shared-memory limit of the long-row pair kernel, raised before any stream capture
 // that may launch it (a host call outside the stream; cheap, so it is simply repeated).
 template <class TS> cudaError_t rows_prepare() {
-    size_t mx = 0;
-    for (int W = 32; W <= rows_width(kRowsMaxNx); W += 32)
-        mx = std::max(mx, rows_smem<TS>(W, kRowsThreads / W - 2));
-    return cudaFuncSetAttribute(k_cheb2_rows<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    cudaError_t e = cudaSuccess;
+    auto raise = [&](auto kernel, int W) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rows_smem<TS>(W, kRowsThreads / W - 2));
+    };
+    raise(k_cheb2_rows<TS, 32>, 32);
+    raise(k_cheb2_rows<TS, 64>, 64);
+    raise(k_cheb2_rows<TS, 96>, 96);
+    raise(k_cheb2_rows<TS, 128>, 128);
+    return e;
 }
 
 // One launch of two iterations: rows of at most 128 cells as one warp each (k_cheb2_v4),
@@ -3555,7 +3584,7 @@ void launch_cheb2(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma,
                      yk, ykm, r, yc, yd);
         return;
     }
-    const int W = rows_width(g.nx), tyr = rows_per_block(g.nx, g.ny);
+    const int W = rows_width(g.nx), tyr = rows_per_block(g.nx);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, (g.ny + tyr - 1) / tyr, nzc * nf);
     cfg.blockDim = dim3(W, tyr + 2);
@@ -3566,7 +3595,12 @@ void launch_cheb2(int zlen, const Geo &g, int nf, const Coef32 &cf, float gamma,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_cheb2_rows<TS>, g, zlen, nzc, cf, gamma, om1, om2, yk, ykm, r, yc, yd);
+    switch (W) {
+    case 32: cudaLaunchKernelEx(&cfg, k_cheb2_rows<TS, 32>, g, zlen, nzc, cf, gamma, om1, om2, yk, ykm, r, yc, yd); break;
+    case 64: cudaLaunchKernelEx(&cfg, k_cheb2_rows<TS, 64>, g, zlen, nzc, cf, gamma, om1, om2, yk, ykm, r, yc, yd); break;
+    case 96: cudaLaunchKernelEx(&cfg, k_cheb2_rows<TS, 96>, g, zlen, nzc, cf, gamma, om1, om2, yk, ykm, r, yc, yd); break;
+    default: cudaLaunchKernelEx(&cfg, k_cheb2_rows<TS, 128>, g, zlen, nzc, cf, gamma, om1, om2, yk, ykm, r, yc, yd); break;
+    }
 }
 
 // The m-1 Chebyshev iterations of a round from y1 (y_0 = 0), two per launch; a last odd
@@ -3887,7 +3921,7 @@ cg_status tune_cheb(cg_mesh *m, const Geo &g, int nf, const Coef32 &cf, TS *ya, 
             // block marches (its chunk and the plane either side)
             int sms = 0;
             CGK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            const int tyr = rows_per_block(g.nx, g.ny);
+            const int tyr = rows_per_block(g.nx);
             const long long yb = (long long)((g.ny + tyr - 1) / tyr) * nf;
             int best_z = g.nz;
             long long best_cost = -1;
