@@ -53,3 +53,27 @@ def test_host_cpu_description():
     h = b.host_cpu()
     assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
     assert isinstance(h["machine"], str) and h["machine"]
+
+
+def test_kernel_roofline_takes_the_dominant_kernel_and_its_capture():
+    """The roofline is the kernel with the most event time; achieved = its algorithmic bytes
+    / its time; traffic (and, for a capture of one launch of a mixed group, that launch's
+    algorithmic bytes) comes from the committed record named by the traffic key."""
+    b = load_bench()
+    kern = {"cheb2_fp32": {"ms": 50.0, "bytes": 4.0e11, "launches": 400},
+            "refine_df": {"ms": 10.0, "bytes": 5.0e10, "launches": 41}}
+    peaks = {"hbm_gbs": 8000.0}
+    r = b.kernel_roofline(kern, peaks, "measured", traffic_key="cheb2_fp32_channel512")
+    assert r["kernel"] == "cheb2_fp32"
+    assert abs(r["achieved"] - 4.0e11 / 50e-3 / 1e9) <= 1e-9 * r["achieved"]
+    assert r["frac"] == r["achieved"] / 8000.0
+    assert r["algorithmic_bytes_per_launch"] == 1.0e9
+    assert abs(r["share_of_kernel_time"] - 50.0 / 60.0) <= 1e-15
+    rec = b.ncu_record("cheb2_fp32_channel512")
+    assert rec is not None
+    assert r["traffic"] == rec["dram_bytes_per_launch"]
+    assert r["traffic_launch_algorithmic_bytes"] == rec["algorithmic_bytes_of_captured_launch"]
+    # no record under the key: no traffic, and no captured-launch bytes
+    r2 = b.kernel_roofline(kern, peaks, "measured", traffic_key="no_such_capture")
+    assert r2["traffic"] is None and "traffic_launch_algorithmic_bytes" not in r2
+    assert b.kernel_roofline({}, peaks, "measured") is None
