@@ -14,7 +14,8 @@ order is the generation order, which matters for ordered deposition):
 * ``clustered_cube``: the 128^3 unit-cube case -- 2,000,000 spheres of d = 0.004 in
   20 Gaussian clusters (sigma 0.05, centres U[0.1,0.9]^3), at most 8 centroids per
   128^3 cell (local volume fraction <= 0.562); a centroid outside the cube or in a
-  full cell is redrawn from its cluster, after 64 tries from U[0,1]^3.
+  full cell is redrawn from its cluster, after 64 tries from U[0,1]^3 (until it lands in
+  a cell with room).
 * ``kuhn_tet_mesh``: an n^3 hex grid of the unit cube, each hex split into 6 tets
   along its v000-v111 diagonal (one per axis permutation, lexicographic order),
   interior vertices jittered by U(-0.2 dx, 0.2 dx) per coordinate.
@@ -96,7 +97,8 @@ def clustered_cube(n_side=128, n_particles=2_000_000, d=0.004, n_clusters=20, si
     pos = centres[which].T + sigma * rng.standard_normal((3, n_particles))
     occupancy = np.zeros(n_side ** 3, dtype=np.int64)     # accepted centroids per bin
     todo = np.arange(n_particles)                          # not yet accepted, in order
-    for attempt in range(max_tries + 1):
+    attempt = 0
+    while len(todo):
         p = pos[:, todo]
         inside = np.all((p >= 0.0) & (p <= 1.0), axis=0)
         ijk = np.clip(np.floor(np.where(inside, p, 0.0) * n_side).astype(np.int64), 0, n_side - 1)
@@ -113,10 +115,13 @@ def clustered_cube(n_side=128, n_particles=2_000_000, d=0.004, n_clusters=20, si
         todo = todo[~ok]
         if len(todo) == 0:
             break
-        if attempt == max_tries:
+        attempt += 1
+        if attempt > max_tries:   # from U[0,1]^3 now, still under the cap
+            if attempt > max_tries + 10_000 or occupancy.sum() + len(todo) > cap * n_side ** 3:
+                raise ValueError("clustered_cube: the cap leaves no room for the particles")
             pos[:, todo] = rng.random((3, len(todo)))
-            break
-        pos[:, todo] = centres[which[todo]].T + sigma * rng.standard_normal((3, len(todo)))
+        else:
+            pos[:, todo] = centres[which[todo]].T + sigma * rng.standard_normal((3, len(todo)))
     w = np.full((1, n_particles), vp)
     return StructuredCase("clustered_cube_%d" % n_side, (n_side,) * 3, (0.0, 0.0, 0.0), dx, pos, w,
                           b_over_dx * dx, nsteps, {"cap": cap, "sigma": sigma})
